@@ -1,0 +1,140 @@
+"""Preconditioned conjugate gradients, textbook form (oracle, FP64).
+
+Sec. 3.1 of the paper: the pressure system is solved by a Preconditioned
+Conjugate Gradient (PCG) solver with either a simplified Diagonal-based
+Incomplete Cholesky (DIC) or a Jacobi preconditioner; Table 1 names the
+pieces (spmv, precondition, dot, vector add/scale).  This module writes out
+Hestenes-Stiefel PCG with ``numpy.dot`` for the inner products and the CSR
+SpMV of ``operators``.
+
+Stopping rule (the paper defines none; reading): stop when the recurrence
+residual satisfies ||r|| <= rtol ||b||, then recompute the true residual
+b - A x; if it also passes, the solve has converged, otherwise CG restarts
+from the true residual (p = M^-1 r).  ||b|| = 0 returns x = 0 after zero
+iterations.  The iteration cap counts CG iterations (SpMVs with p).
+
+``fixed_iters`` replays a given number of iterations with no stopping test;
+parity tests use it to follow the iteration counts of the CUDA path, because
+two correct CGs whose sums run in different orders may stop one iteration
+apart.
+
+DIC reading: d_i = a_ii - sum_{j < i, a_ij != 0} a_ij^2 / d_j and
+M = (D + L) D^-1 (D + L^T) with L the strict lower triangle of A (the
+"simplified" form keeps the sparsity of A).  On the singular Neumann
+pressure matrix the last pivot vanishes, so DIC is only applied here to
+nonsingular matrices.
+
+Pins (tests/test_oracle_solver.py): dense pseudo-inverse solves on grids up
+to 6^3, exactly one iteration for a single DCT mode and two for two modes,
+the manufactured cosine solution in closed form, the O(h^2) rate on a
+polynomial solution, and DIC = exact factorisation on tridiagonal matrices
+(one PCG iteration).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg  # noqa: F401  (spsolve_triangular)
+
+
+@dataclass
+class SolveStats:
+    iters: int = 0
+    restarts: int = 0
+    converged: bool = False
+    breakdown: bool = False
+    rel_resid: float = 0.0   # true ||b - A x|| / ||b|| at exit
+
+
+def identity_precond(r):
+    return r.copy()
+
+
+def jacobi_precond(A: sp.csr_matrix):
+    inv_d = 1.0 / A.diagonal()
+    return lambda r: inv_d * r
+
+
+def dic_precond(A: sp.csr_matrix):
+    """Simplified diagonal-based incomplete Cholesky (Sec. 3.1), sequential."""
+    A = A.tocsr()
+    n = A.shape[0]
+    d = np.zeros(n)
+    indptr, indices, data = A.indptr, A.indices, A.data
+    for i in range(n):
+        s = 0.0
+        aii = 0.0
+        for t in range(indptr[i], indptr[i + 1]):
+            j = indices[t]
+            if j < i:
+                s += data[t] * data[t] / d[j]
+            elif j == i:
+                aii = data[t]
+        d[i] = aii - s
+    lower = sp.tril(A, k=-1).tocsr()
+    DL = (sp.diags(d) + lower).tocsr()
+    DU = (sp.diags(d) + lower.T).tocsr()
+
+    def apply(r):
+        y = sp.linalg.spsolve_triangular(DL, r, lower=True)
+        return sp.linalg.spsolve_triangular(DU, d * y, lower=False)
+
+    return apply, d
+
+
+def pcg(A, b, x0=None, rtol=1e-8, max_iters=1000, precond=identity_precond,
+        fixed_iters=None, max_restarts=8):
+    """Solve A x = b; returns (x, SolveStats)."""
+    n = b.size
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    st = SolveStats()
+    bb = float(np.dot(b, b))
+    if bb == 0.0:
+        st.converged = True
+        return np.zeros(n), st
+    tol2 = rtol * rtol * bb
+    r = b - A @ x
+    z = precond(r)
+    p = z.copy()
+    rz = float(np.dot(r, z))
+    rr = float(np.dot(r, r))
+    while True:
+        if fixed_iters is not None:
+            if st.iters == fixed_iters:
+                break
+        else:
+            if rr <= tol2:
+                rt = b - A @ x
+                rrt = float(np.dot(rt, rt))
+                if rrt <= tol2:
+                    st.converged = True
+                    break
+                st.restarts += 1
+                if st.restarts > max_restarts:
+                    break
+                r = rt
+                z = precond(r)
+                p = z.copy()
+                rz = float(np.dot(r, z))
+                rr = rrt
+            if st.iters == max_iters:
+                break
+        q = A @ p
+        pq = float(np.dot(p, q))
+        if not pq > 0.0:
+            st.breakdown = True
+            break
+        alpha = rz / pq
+        x += alpha * p
+        r -= alpha * q
+        z = precond(r)
+        rz_new = float(np.dot(r, z))
+        rr = float(np.dot(r, r))
+        beta = rz_new / rz
+        rz = rz_new
+        p = z + beta * p
+        st.iters += 1
+    st.rel_resid = float(np.linalg.norm(b - A @ x) / np.sqrt(bb))
+    return x, st

@@ -1,0 +1,147 @@
+"""Pins of the oracle's PCG (Sec. 3.1) against brute force and closed forms."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle.krylov import dic_precond, jacobi_precond, pcg
+from oracle.operators import poisson_csr
+from paper_2504_03697_gb300.synthetic import uniform_field
+
+
+def _dense_zero_mean_solve(A, b):
+    """Zero-mean solution of the singular Neumann system by a dense LU solve
+    of the nonsingular A + 1 1^T / n (same solution when sum(b) = 0)."""
+    Ad = A.toarray()
+    n = Ad.shape[0]
+    return np.linalg.solve(Ad + np.ones((n, n)) / n, b)
+
+
+@pytest.mark.parametrize("shape", [(2, 2, 2), (1, 1, 6), (3, 4, 5), (6, 6, 6)])
+def test_cg_matches_dense_pseudo_inverse(shape):
+    A = poisson_csr(*shape)
+    b = uniform_field(shape[::-1], seed=11).ravel()
+    b -= b.mean()
+    x, st = pcg(A, b, rtol=1e-14, max_iters=10000)
+    assert st.converged and not st.breakdown
+    ref = _dense_zero_mean_solve(A, b)
+    assert np.linalg.norm(x - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def _mode(shape, k):
+    nx, ny, nz = shape
+    kk, jj, ii = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    m = (np.cos(np.pi * k[0] * (ii + 0.5) / nx) * np.cos(np.pi * k[1] * (jj + 0.5) / ny)
+         * np.cos(np.pi * k[2] * (kk + 0.5) / nz)).ravel()
+    lam = sum(4 * np.sin(np.pi * kd / (2 * nd)) ** 2 for kd, nd in zip(k, shape))
+    return m, lam
+
+
+def test_single_mode_one_iteration():
+    shape = (12, 10, 8)
+    A = poisson_csr(*shape)
+    m, lam = _mode(shape, (2, 1, 3))
+    x, st = pcg(A, m, rtol=1e-10)
+    assert st.converged and st.iters == 1
+    np.testing.assert_allclose(x, m / lam, rtol=1e-12, atol=1e-14)
+
+
+def test_two_modes_two_iterations():
+    shape = (12, 10, 8)
+    A = poisson_csr(*shape)
+    m1, l1 = _mode(shape, (2, 1, 3))
+    m2, l2 = _mode(shape, (5, 0, 1))
+    x, st = pcg(A, m1 + 0.5 * m2, rtol=1e-10)
+    assert st.converged and st.iters == 2
+    np.testing.assert_allclose(x, m1 / l1 + 0.5 * m2 / l2, rtol=1e-10, atol=1e-12)
+
+
+def test_zero_rhs_zero_iterations():
+    A = poisson_csr(4, 4, 4)
+    x, st = pcg(A, np.zeros(64), rtol=1e-8)
+    assert st.iters == 0 and st.converged and np.all(x == 0)
+
+
+@pytest.mark.parametrize("n,err", [(16, 3.2e-3), (64, 2.0e-4)])
+def test_manufactured_cosine(n, err):
+    """p = cos(pi x) cos(pi y) cos(pi z): the sampled field is the (1,1,1)
+    discrete mode, so A x = 3 pi^2 h^2 p_s has x = (3 pi^2 h^2 / lambda) p_s;
+    the relative discretisation error |3 pi^2 h^2 / lambda - 1| is O(h^2)."""
+    h = 1.0 / n
+    c = (np.arange(n) + 0.5) * h
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    ps = (np.cos(np.pi * X) * np.cos(np.pi * Y) * np.cos(np.pi * Z)).ravel()
+    lam = 3 * 4 * np.sin(np.pi / (2 * n)) ** 2
+    A = poisson_csr(n, n, n)
+    x, st = pcg(A, 3 * np.pi ** 2 * h * h * ps, rtol=1e-12)
+    assert st.converged
+    np.testing.assert_allclose(x, (3 * np.pi ** 2 * h * h / lam) * ps, rtol=0, atol=1e-10)
+    rel = np.linalg.norm(x - ps) / np.linalg.norm(ps)
+    assert abs(rel - err) < 0.05 * err
+
+
+def test_polynomial_solution_second_order():
+    """P = q(x) + q(y) + q(z), q = x^2 (1-x)^2 (zero normal derivative at
+    both walls); -lap P = -(q''(x) + q''(y) + q''(z)).  Error ratio ~4 per
+    halving of h confirms the O(h^2) discretisation."""
+    errs = []
+    for n in (8, 16, 32):
+        h = 1.0 / n
+        c = (np.arange(n) + 0.5) * h
+        Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+        q = lambda s: s ** 2 * (1 - s) ** 2
+        qpp = lambda s: 12 * s ** 2 - 12 * s + 2
+        P = (q(X) + q(Y) + q(Z)).ravel()
+        f = (-(qpp(X) + qpp(Y) + qpp(Z))).ravel() * h * h
+        f -= f.mean()
+        x, st = pcg(poisson_csr(n, n, n), f, rtol=1e-12)
+        assert st.converged
+        d = (x - x.mean()) - (P - P.mean())
+        errs.append(np.sqrt(np.mean(d * d)))  # RMS error (the max-norm ratio
+        # reaches 4 more slowly because the wall rows are first order)
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.7 < r1 < 4.1 and 3.9 < r2 < 4.05
+
+
+def test_dic_exact_on_tridiagonal():
+    """With no fill-in to drop, DIC is the exact LDL^T factorisation, so PCG
+    converges in one iteration and d equals the LDL^T pivots."""
+    n = 9
+    main = 2.0 + 0.3 * np.arange(n) / n
+    T = sp.diags([-np.ones(n - 1), main, -np.ones(n - 1)], [-1, 0, 1], format="csr")
+    apply, d = dic_precond(T)
+    L = np.linalg.cholesky(T.toarray())
+    np.testing.assert_allclose(d, np.diag(L) ** 2, rtol=1e-13)
+    b = np.sin(np.arange(n) + 1.0)
+    x, st = pcg(T, b, rtol=1e-12, precond=apply)
+    assert st.converged and st.iters == 1
+    np.testing.assert_allclose(x, np.linalg.solve(T.toarray(), b), rtol=1e-12)
+
+
+def test_jacobi_on_diagonal_matrix_one_iteration():
+    D = sp.diags(np.arange(1.0, 11.0), format="csr")
+    b = np.cos(np.arange(10.0))
+    x, st = pcg(D, b, rtol=1e-12, precond=jacobi_precond(D))
+    assert st.iters == 1
+    np.testing.assert_allclose(x, b / np.arange(1.0, 11.0), rtol=1e-14)
+
+
+def test_jacobi_pcg_matches_dense():
+    shape = (5, 4, 6)
+    A = poisson_csr(*shape)
+    b = uniform_field(shape[::-1], seed=3).ravel()
+    b -= b.mean()
+    x, st = pcg(A, b, rtol=1e-14, precond=jacobi_precond(A), max_iters=5000)
+    assert st.converged
+    ref = _dense_zero_mean_solve(A, b)
+    xc = x - x.mean()
+    assert np.linalg.norm(xc - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def test_fixed_iteration_replay():
+    A = poisson_csr(6, 5, 4)
+    b = uniform_field((4, 5, 6), seed=5).ravel()
+    b -= b.mean()
+    x1, s1 = pcg(A, b, rtol=1e-8)
+    x2, s2 = pcg(A, b, rtol=1e-8, fixed_iters=s1.iters)
+    assert s2.iters == s1.iters
+    np.testing.assert_array_equal(x1, x2)
