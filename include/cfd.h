@@ -1,0 +1,192 @@
+/*
+ * cfd.h -- C-ABI of the GB300 (sm_103a) lid-driven-cavity projection path.
+ *
+ * The operation is the time step of a 3D lid-driven cavity on a staggered
+ * (MAC) grid, advanced by the fractional-step method of arXiv 2504.03697
+ * ("cfdSCOPE"), Sec. 3 and 3.1: external forces, semi-Lagrangian advection,
+ * a pressure Poisson solve by (preconditioned) conjugate gradients, and the
+ * pressure correction; Table 1 names the same phases (applyForces,
+ * solveAdvection, solvePressureCorrection / pcg, applyPressureCorrection).
+ * A backward-Euler viscosity substep (not in the paper's inviscid model) runs
+ * between advection and projection when nu > 0.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Grid: nx * ny * nz cubic cells of edge h = length / nx.  Arrays are
+ * float64, x fastest, then y, then z:
+ *   U: (nx+1) * ny * nz   V: nx * (ny+1) * nz   W: nx * ny * (nz+1)
+ *   P: nx * ny * nz       (cell centres)
+ * The lid is the y = ny*h wall, moving in +x at lid_u; every other wall is
+ * at rest.  Normal velocity on the walls is zero.
+ *
+ * Memory ownership: the caller owns all device memory.  It asks for the
+ * workspace size with cfd_workspace_bytes, allocates one device buffer of at
+ * least that many bytes (256-byte aligned), and passes it to cfd_create; the
+ * library never allocates device memory.  The handle itself lives in host
+ * memory (malloc) and is freed by cfd_destroy, which does not touch the
+ * workspace.
+ *
+ * Streams: every call enqueues its work on the stream given to cfd_create
+ * (or cfd_set_stream).  Calls that return statistics or copy to host memory
+ * synchronise that stream before returning; the others are asynchronous.
+ *
+ * Errors: every int-returning call returns one of the CFD_* codes below;
+ * cfd_last_error(h) returns a static, human-readable description of the
+ * last failure on that handle (h may be NULL for failures before a handle
+ * exists).  Solver outcomes (not converged, breakdown, device-wait timeout)
+ * leave the fields holding the last iterate.
+ */
+#ifndef CFD_GB300_H
+#define CFD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* cudaStream_t (a CUstream_st pointer); pass torch.cuda.current_stream().cuda_stream */
+typedef struct CUstream_st *cfd_stream_t;
+typedef struct cfd_handle cfd_handle;
+
+enum {
+  CFD_OK = 0,
+  CFD_ERR_INVALID_ARG = -1,
+  CFD_ERR_CUDA = -2,
+  CFD_ERR_NOT_CONVERGED = -3,      /* iteration cap reached; fields hold the last iterate */
+  CFD_ERR_BREAKDOWN = -4,          /* NaN/Inf or p^T A p <= 0 inside CG */
+  CFD_ERR_TIMEOUT = -5,            /* a bounded device-side wait gave up */
+  CFD_ERR_WORKSPACE_TOO_SMALL = -6
+};
+
+enum { CFD_FIELD_U = 0, CFD_FIELD_V = 1, CFD_FIELD_W = 2, CFD_FIELD_P = 3 };
+
+/* Pressure solver (Sec. 3.1: PCG with an optional preconditioner).
+ *   CG      unpreconditioned conjugate gradients, FP64
+ *   JACOBI  Jacobi-preconditioned CG, FP64 (the paper's optimised variant)
+ *   IR      FP32 inner CG with FP64 iterative refinement (outer residual,
+ *           norms and the correction in FP64)                            */
+enum { CFD_SOLVER_CG = 0, CFD_SOLVER_JACOBI = 1, CFD_SOLVER_IR = 2 };
+
+/* Substeps for cfd_substep (kernel-level access to one phase of the step). */
+enum {
+  CFD_SUBSTEP_FORCES = 0,   /* applyForces: top-layer faces += dt * g            */
+  CFD_SUBSTEP_ADVECT = 1,   /* solveAdvection: semi-Lagrangian, old -> new field  */
+  CFD_SUBSTEP_DIFFUSE = 2,  /* backward-Euler viscosity (three CG solves)         */
+  CFD_SUBSTEP_PROJECT = 3   /* divergence, pressure solve, correction, gauge      */
+};
+
+typedef struct {
+  int32_t nx, ny, nz;       /* cells per axis, each >= 1                          */
+  double length;            /* box edge along x (h = length / nx), > 0            */
+  double dt;                /* time step, > 0                                     */
+  double rho;               /* density, > 0                                       */
+  double nu;                /* kinematic viscosity, >= 0 (0: no diffusion step)   */
+  double lid_u;             /* lid speed along +x                                 */
+  double g[3];              /* forcing offset per unit time on the top cell layer */
+  int32_t solver;           /* CFD_SOLVER_*                                       */
+  double rtol;              /* ||b - A x||_2 <= rtol ||b||_2 (true FP64 residual)  */
+  int32_t max_iters;        /* CG iteration cap per solve; 0 -> 20 * max(n)       */
+  int32_t warm_start;       /* 1: start the pressure solve from the previous p    */
+  double inner_rtol;        /* IR inner FP32 tolerance; 0 -> 1e-4                 */
+  int32_t reserved[8];      /* must be zero                                       */
+} cfd_params;
+
+typedef struct {
+  int32_t iters;            /* pressure CG iterations (IR: inner, summed)         */
+  int32_t outer_iters;      /* IR refinement steps (0 for CG / JACOBI)            */
+  int32_t restarts;         /* restarts from the true residual                   */
+  int32_t status;           /* CFD_OK or the solver code of this solve            */
+  int32_t diff_iters[3];    /* diffusion CG iterations for u, v, w (0 if nu = 0)  */
+  int32_t diff_status;      /* worst status of the three diffusion solves         */
+  double rel_resid;         /* true ||b - A x|| / ||b|| of the pressure solve     */
+  double b_norm;            /* ||b||_2 of the pressure right-hand side            */
+} cfd_solve_stats;
+
+/* Size in bytes of the device workspace cfd_create needs for these params.
+ * Returns CFD_ERR_INVALID_ARG for an invalid parameter set. */
+int cfd_workspace_bytes(const cfd_params *params, size_t *bytes);
+
+/* Create a cavity on the given workspace (device pointer, >= the size from
+ * cfd_workspace_bytes, 256-byte aligned).  The initial state is v = 0,
+ * p = 1 (Sec. 3, eq. 3).  On success *out holds a new handle. */
+int cfd_create(const cfd_params *params, void *dev_ws, size_t bytes, cfd_stream_t stream,
+               cfd_handle **out);
+
+/* Free the host-side handle.  The workspace stays the caller's. */
+void cfd_destroy(cfd_handle *h);
+
+/* Static description of the last failure on h (or of the last failure
+ * without a handle when h is NULL).  Never returns NULL. */
+const char *cfd_last_error(const cfd_handle *h);
+
+/* Change the stream subsequent calls enqueue on. */
+int cfd_set_stream(cfd_handle *h, cfd_stream_t stream);
+
+/* Copy a whole field (layout above) into the cavity.  src is a device
+ * pointer when src_on_device != 0, else a host pointer (pinned memory gives
+ * an asynchronous copy).  Wall-normal velocity faces are forced to zero. */
+int cfd_set_field(cfd_handle *h, int field, const double *src, int src_on_device);
+
+/* Copy a whole field out; dims_out (nullable) receives its (x, y, z) sizes.
+ * A host destination synchronises the stream. */
+int cfd_read_field(cfd_handle *h, int field, double *dst, int dst_on_device, int64_t dims_out[3]);
+
+/* Advance nsteps fractional steps (Sec. 3.1).  per_step (nullable) receives
+ * nsteps entries; when given, the call synchronises and returns the worst
+ * solver status seen; otherwise it returns after enqueueing. */
+int cfd_step(cfd_handle *h, int nsteps, cfd_solve_stats *per_step);
+
+/* Run one substep (CFD_SUBSTEP_*) of the step on the current state.
+ * stats (nullable) as for cfd_step. */
+int cfd_substep(cfd_handle *h, int which, cfd_solve_stats *stats);
+
+/* Standalone Neumann-Poisson solve A x = b with the handle's solver, rtol
+ * and grid (the pressure system of Sec. 3.1; A = -h^2 * 7-point Laplacian).
+ * b_dev, x_dev: device arrays of nx*ny*nz float64.  b is read only; the
+ * mean of b is removed internally.  x is overwritten (cold start from 0,
+ * or from its contents when warm_start = 1); no gauge shift is applied.
+ * stats (nullable) receives iterations and the true residual; the call
+ * synchronises when stats is given. */
+int cfd_solve_pressure(cfd_handle *h, const double *b_dev, double *x_dev, cfd_solve_stats *stats);
+
+/* y = A x for the Neumann pressure matrix A (scaled by h^2: row c has
+ * n_c on the diagonal and -1 for each of its n_c neighbours).  x_dev and
+ * y_dev: device arrays of nx*ny*nz float64, not overlapping.  This is the
+ * paper's SpMV (Sec. 3.1, Table 1 "spmv"), matrix-free. */
+int cfd_apply_poisson(cfd_handle *h, const double *x_dev, double *y_dev);
+
+/* Number of kernel launches this handle has issued since creation
+ * (for launch accounting in benchmarks). */
+int64_t cfd_launch_count(const cfd_handle *h);
+
+/* Phase timers, mirroring the call tree of the paper's Table 1
+ * (applyForces, solveAdvection, solvePressureCorrection -> pcg,
+ * applyPressureCorrection) plus the diffusion substep.  CFD_PHASE_PCG
+ * brackets exactly the pressure-solve kernel launch. */
+enum {
+  CFD_PHASE_FORCES = 0,
+  CFD_PHASE_ADVECT = 1,
+  CFD_PHASE_DIFFUSE = 2,
+  CFD_PHASE_DIVERGENCE = 3,
+  CFD_PHASE_PCG = 4,
+  CFD_PHASE_CORRECT = 5,
+  CFD_PHASE_COUNT = 6
+};
+
+/* on != 0: record a CUDA event pair on the handle's stream around every
+ * phase of later calls (host-side event objects; no device allocation).
+ * on == 0: stop recording (pending pairs stay until queried). */
+int cfd_enable_timing(cfd_handle *h, int on);
+
+/* Synchronise the stream, write the summed device time (ms) and the number
+ * of recorded calls of each phase since the last query into ms_out /
+ * calls_out (CFD_PHASE_COUNT entries each, nullable), and reset them. */
+int cfd_phase_times(cfd_handle *h, double *ms_out, int64_t *calls_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CFD_GB300_H */

@@ -1,0 +1,241 @@
+"""ctypes binding of ``include/cfd.h`` (argument marshalling only).
+
+Every function of the C-ABI is exposed under its own name; ``Cavity`` wraps
+a handle together with the device workspace it owns (a torch uint8 tensor:
+PyTorch supplies device memory and streams, the library does all compute).
+
+The binding loads ``lib/libcfdgb.so`` built in-tree by ``build.py``.  There
+is no fallback: without the library (or without a CUDA device) the calls
+raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "lib", "libcfdgb.so")
+
+CFD_OK = 0
+CFD_ERR_INVALID_ARG = -1
+CFD_ERR_CUDA = -2
+CFD_ERR_NOT_CONVERGED = -3
+CFD_ERR_BREAKDOWN = -4
+CFD_ERR_TIMEOUT = -5
+CFD_ERR_WORKSPACE_TOO_SMALL = -6
+
+FIELD = {"u": 0, "v": 1, "w": 2, "p": 3}
+SOLVER = {"cg": 0, "jacobi": 1, "ir": 2}
+SUBSTEP = {"forces": 0, "advect": 1, "diffuse": 2, "project": 3}
+PHASES = ["applyForces", "solveAdvection", "diffuse", "divergence", "pcg", "applyPressureCorrection"]
+
+
+class cfd_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("length", ctypes.c_double), ("dt", ctypes.c_double), ("rho", ctypes.c_double),
+                ("nu", ctypes.c_double), ("lid_u", ctypes.c_double), ("g", ctypes.c_double * 3),
+                ("solver", ctypes.c_int32), ("rtol", ctypes.c_double), ("max_iters", ctypes.c_int32),
+                ("warm_start", ctypes.c_int32), ("inner_rtol", ctypes.c_double),
+                ("reserved", ctypes.c_int32 * 8)]
+
+
+class cfd_solve_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("outer_iters", ctypes.c_int32),
+                ("restarts", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("diff_iters", ctypes.c_int32 * 3), ("diff_status", ctypes.c_int32),
+                ("rel_resid", ctypes.c_double), ("b_norm", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"iters": self.iters, "outer_iters": self.outer_iters, "restarts": self.restarts,
+                "status": self.status, "diff_iters": list(self.diff_iters),
+                "diff_status": self.diff_status, "rel_resid": self.rel_resid, "b_norm": self.b_norm}
+
+
+class CfdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"cfd error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(path: Optional[str] = None):
+    """Load libcfdgb.so (once) and declare the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or _LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: run `python -c 'import __graft_entry__ as g; g.build()'` first")
+    lib = ctypes.CDLL(p)
+    P = ctypes.POINTER
+    vp = ctypes.c_void_p
+    sig = {
+        "cfd_workspace_bytes": (ctypes.c_int, [P(cfd_params), P(ctypes.c_size_t)]),
+        "cfd_create": (ctypes.c_int, [P(cfd_params), vp, ctypes.c_size_t, vp, P(vp)]),
+        "cfd_destroy": (None, [vp]),
+        "cfd_last_error": (ctypes.c_char_p, [vp]),
+        "cfd_set_stream": (ctypes.c_int, [vp, vp]),
+        "cfd_set_field": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int]),
+        "cfd_read_field": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, P(ctypes.c_int64)]),
+        "cfd_step": (ctypes.c_int, [vp, ctypes.c_int, P(cfd_solve_stats)]),
+        "cfd_substep": (ctypes.c_int, [vp, ctypes.c_int, P(cfd_solve_stats)]),
+        "cfd_solve_pressure": (ctypes.c_int, [vp, vp, vp, P(cfd_solve_stats)]),
+        "cfd_apply_poisson": (ctypes.c_int, [vp, vp, vp]),
+        "cfd_launch_count": (ctypes.c_int64, [vp]),
+        "cfd_enable_timing": (ctypes.c_int, [vp, ctypes.c_int]),
+        "cfd_phase_times": (ctypes.c_int, [vp, P(ctypes.c_double), P(ctypes.c_int64)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def make_params(nx, ny, nz, length=1.0, dt=0.01, rho=1.0, nu=0.0, lid_u=1.0, g=(0.0, 0.0, 0.0),
+                solver="cg", rtol=1e-8, max_iters=0, warm_start=False, inner_rtol=0.0) -> cfd_params:
+    prm = cfd_params()
+    prm.nx, prm.ny, prm.nz = int(nx), int(ny), int(nz)
+    prm.length, prm.dt, prm.rho, prm.nu, prm.lid_u = float(length), float(dt), float(rho), float(nu), float(lid_u)
+    for i in range(3):
+        prm.g[i] = float(g[i])
+    prm.solver = SOLVER[solver] if isinstance(solver, str) else int(solver)
+    prm.rtol = float(rtol)
+    prm.max_iters = int(max_iters)
+    prm.warm_start = 1 if warm_start else 0
+    prm.inner_rtol = float(inner_rtol)
+    return prm
+
+
+def cfd_workspace_bytes(prm: cfd_params) -> int:
+    lib = load_library()
+    n = ctypes.c_size_t(0)
+    rc = lib.cfd_workspace_bytes(ctypes.byref(prm), ctypes.byref(n))
+    if rc != CFD_OK:
+        raise CfdError(rc, lib.cfd_last_error(None).decode())
+    return int(n.value)
+
+
+def _stream_ptr(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class Cavity:
+    """One cavity: a handle plus the device workspace it lives in."""
+
+    def __init__(self, prm: cfd_params, stream=None, device=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (the library has no CPU path)")
+        self.lib = load_library()
+        self.prm = prm
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        nbytes = cfd_workspace_bytes(prm)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream
+        h = ctypes.c_void_p(0)
+        rc = self.lib.cfd_create(ctypes.byref(prm), ctypes.c_void_p(self.workspace.data_ptr()),
+                                 ctypes.c_size_t(nbytes), ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h))
+        if rc != CFD_OK:
+            raise CfdError(rc, self.lib.cfd_last_error(None).decode())
+        self.h = h
+
+    # -- helpers ----------------------------------------------------------
+    def _check(self, rc, allow=()):
+        if rc != CFD_OK and rc not in allow:
+            raise CfdError(rc, self.lib.cfd_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.cfd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def dims(self, field):
+        nx, ny, nz = self.prm.nx, self.prm.ny, self.prm.nz
+        return {"u": (nx + 1, ny, nz), "v": (nx, ny + 1, nz), "w": (nx, ny, nz + 1), "p": (nx, ny, nz)}[field]
+
+    def shape(self, field):
+        dx, dy, dz = self.dims(field)
+        return (dz, dy, dx)
+
+    # -- C-ABI calls --------------------------------------------------------
+    def set_field(self, field, src):
+        """src: a CUDA float64 tensor or a host array/tensor of the field's shape."""
+        if isinstance(src, torch.Tensor) and src.is_cuda:
+            t = src.contiguous().to(torch.float64)
+            rc = self.lib.cfd_set_field(self.h, FIELD[field], ctypes.c_void_p(t.data_ptr()), 1)
+            self._keep = t
+        else:
+            t = torch.as_tensor(src, dtype=torch.float64).contiguous()
+            if tuple(t.shape) != self.shape(field) and t.numel() != int(torch.tensor(self.shape(field)).prod()):
+                raise ValueError(f"{field}: expected shape {self.shape(field)}, got {tuple(t.shape)}")
+            rc = self.lib.cfd_set_field(self.h, FIELD[field], ctypes.c_void_p(t.data_ptr()), 0)
+            torch.cuda.current_stream().synchronize() if self.stream is None else self.stream.synchronize()
+        return self._check(rc)
+
+    def read_field(self, field, out=None, device=False):
+        """Return the field as a (z, y, x) float64 tensor (host unless device=True)."""
+        if out is None:
+            out = torch.empty(self.shape(field), dtype=torch.float64, device=self.device if device else "cpu")
+        dims = (ctypes.c_int64 * 3)()
+        rc = self.lib.cfd_read_field(self.h, FIELD[field], ctypes.c_void_p(out.data_ptr()), 1 if out.is_cuda else 0, dims)
+        self._check(rc)
+        return out
+
+    def step(self, nsteps=1, stats=True):
+        if stats:
+            arr = (cfd_solve_stats * max(1, nsteps))()
+            rc = self.lib.cfd_step(self.h, int(nsteps), arr)
+            self._check(rc, allow=(CFD_ERR_NOT_CONVERGED, CFD_ERR_BREAKDOWN, CFD_ERR_TIMEOUT))
+            return rc, [arr[i].as_dict() for i in range(nsteps)]
+        rc = self.lib.cfd_step(self.h, int(nsteps), None)
+        self._check(rc)
+        return rc, None
+
+    def substep(self, which, stats=True):
+        st = cfd_solve_stats()
+        rc = self.lib.cfd_substep(self.h, SUBSTEP[which], ctypes.byref(st) if stats else None)
+        self._check(rc, allow=(CFD_ERR_NOT_CONVERGED, CFD_ERR_BREAKDOWN, CFD_ERR_TIMEOUT))
+        return rc, st.as_dict()
+
+    def solve_pressure(self, b: torch.Tensor, x: torch.Tensor, stats=True):
+        assert b.is_cuda and x.is_cuda and b.dtype == torch.float64 and x.dtype == torch.float64
+        st = cfd_solve_stats()
+        rc = self.lib.cfd_solve_pressure(self.h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                         ctypes.byref(st) if stats else None)
+        self._check(rc, allow=(CFD_ERR_NOT_CONVERGED, CFD_ERR_BREAKDOWN, CFD_ERR_TIMEOUT))
+        return rc, st.as_dict()
+
+    def apply_poisson(self, x: torch.Tensor, y: torch.Tensor):
+        assert x.is_cuda and y.is_cuda and x.dtype == torch.float64 and y.dtype == torch.float64
+        return self._check(self.lib.cfd_apply_poisson(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr())))
+
+    def launch_count(self) -> int:
+        return int(self.lib.cfd_launch_count(self.h))
+
+    def set_stream(self, stream):
+        self.stream = stream
+        return self._check(self.lib.cfd_set_stream(self.h, ctypes.c_void_p(_stream_ptr(stream))))
+
+    def enable_timing(self, on=True):
+        return self._check(self.lib.cfd_enable_timing(self.h, 1 if on else 0))
+
+    def phase_times(self):
+        """{phase: (total_ms, calls)} since the last query (synchronises)."""
+        ms = (ctypes.c_double * len(PHASES))()
+        calls = (ctypes.c_int64 * len(PHASES))()
+        self._check(self.lib.cfd_phase_times(self.h, ms, calls))
+        return {name: (ms[i], int(calls[i])) for i, name in enumerate(PHASES)}

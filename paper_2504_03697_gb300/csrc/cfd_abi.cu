@@ -1,0 +1,583 @@
+// C-ABI of the cavity projection path: handle, workspace layout, step
+// driver.  Declared in include/cfd.h; the functions below follow the
+// paper's statement of the problem (Sec. 3 / 3.1 of arXiv 2504.03697):
+// parameters and initial state (v0 = 0, p0 = 1), the fractional step
+// (forces, advection, pressure correction), and reading the fields.
+//
+// The library never allocates device memory: every array lives in the
+// caller's workspace, carved up by ws_layout below (256-byte aligned).
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/cfd.h"
+#include "cfd_internal.h"
+
+using namespace cfd;
+
+namespace {
+
+constexpr int kStatsCap = 1024;   // per-step statistics slots in the workspace
+constexpr int kMaxRestarts = 8;
+constexpr unsigned long long kTimeoutNs = 2000000000ull;  // 2 s per device wait
+
+thread_local char g_last_error[256] = "no error";
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Layout {
+  size_t u, v, w, ua, va, wa, p;
+  size_t b, r, d0, d1, q;
+  size_t r32, d32, p0_32, p1_32, q32;
+  size_t partials, ctrl, stats;
+  size_t total;
+};
+
+size_t face_count(const cfd_params& p, int comp) {
+  return size_t(p.nx + (comp == 0)) * size_t(p.ny + (comp == 1)) * size_t(p.nz + (comp == 2));
+}
+
+Layout ws_layout(const cfd_params& p, int max_blocks) {
+  Layout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align256(off + bytes);
+    return o;
+  };
+  const size_t cells = size_t(p.nx) * p.ny * p.nz;
+  size_t vec = cells;
+  for (int c = 0; c < 3; ++c) vec = vec > face_count(p, c) ? vec : face_count(p, c);
+  L.u = take(face_count(p, 0) * 8);
+  L.v = take(face_count(p, 1) * 8);
+  L.w = take(face_count(p, 2) * 8);
+  L.ua = take(face_count(p, 0) * 8);
+  L.va = take(face_count(p, 1) * 8);
+  L.wa = take(face_count(p, 2) * 8);
+  L.p = take(cells * 8);
+  L.b = take(vec * 8);
+  L.r = take(vec * 8);
+  L.d0 = take(vec * 8);
+  L.d1 = take(vec * 8);
+  L.q = take(vec * 8);
+  if (p.solver == CFD_SOLVER_IR) {
+    L.r32 = take(cells * 4);
+    L.d32 = take(cells * 4);
+    L.p0_32 = take(cells * 4);
+    L.p1_32 = take(cells * 4);
+    L.q32 = take(cells * 4);
+  }
+  L.partials = take(size_t(max_blocks) * kMaxPartials * 8);
+  L.ctrl = take(sizeof(SolveCtrl));
+  L.stats = take(size_t(kStatsCap) * sizeof(DevStepStats));
+  L.total = off;
+  return L;
+}
+
+// Upper bound on the co-resident block count used for sizing partials; the
+// real count is capped by the device at create time.
+constexpr int kMaxBlocksBound = 4096;
+
+}  // namespace
+
+struct cfd_handle {
+  cfd_params prm;
+  cudaStream_t stream;
+  char* ws;
+  size_t ws_bytes;
+  Layout L;
+  double *u, *v, *w, *ua, *va, *wa, *p;
+  double *b, *r, *d0, *d1, *q;
+  float *r32, *d32, *p0_32, *p1_32, *q32;
+  double* partials;
+  SolveCtrl* ctrl;
+  DevStepStats* stats;
+  LaunchGeom lg;
+  int64_t launches;
+  char err[256];
+  // phase timers (host-side CUDA events)
+  bool timing;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_next;
+  struct Pending { int phase; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+};
+
+namespace {
+
+int set_err(cfd_handle* h, int code, const char* fmt, ...) {
+  char buf[256];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (h) std::memcpy(h->err, buf, sizeof(buf));
+  std::memcpy(g_last_error, buf, sizeof(buf));
+  return code;
+}
+
+int cuda_check(cfd_handle* h, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return CFD_OK;
+  return set_err(h, CFD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Event pair around one phase when timing is on (begin returns the pair index).
+int phase_begin(cfd_handle* h, int phase) {
+  if (!h->timing) return -1;
+  if (h->ev_next + 2 > h->ev_pool.size()) {
+    for (int i = 0; i < 2; ++i) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      h->ev_pool.push_back(e);
+    }
+  }
+  cudaEvent_t a = h->ev_pool[h->ev_next], b = h->ev_pool[h->ev_next + 1];
+  h->ev_next += 2;
+  cudaEventRecord(a, h->stream);
+  h->pending.push_back({phase, a, b});
+  return int(h->pending.size()) - 1;
+}
+
+void phase_end(cfd_handle* h, int slot) {
+  if (slot < 0) return;
+  cudaEventRecord(h->pending[size_t(slot)].b, h->stream);
+}
+
+int validate(const cfd_params* p) {
+  if (!p) return set_err(nullptr, CFD_ERR_INVALID_ARG, "params is NULL");
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return set_err(nullptr, CFD_ERR_INVALID_ARG, "grid sizes must be >= 1");
+  if (double(p->nx + 1) * p->ny * p->nz > 2.0e9 || double(p->nx) * (p->ny + 1) * p->nz > 2.0e9 ||
+      double(p->nx) * p->ny * (p->nz + 1) > 2.0e9)
+    return set_err(nullptr, CFD_ERR_INVALID_ARG, "grid too large");
+  if (!(p->length > 0) || !(p->dt > 0) || !(p->rho > 0) || !(p->nu >= 0))
+    return set_err(nullptr, CFD_ERR_INVALID_ARG, "length, dt, rho must be > 0 and nu >= 0");
+  if (!std::isfinite(p->lid_u) || !std::isfinite(p->g[0]) || !std::isfinite(p->g[1]) || !std::isfinite(p->g[2]))
+    return set_err(nullptr, CFD_ERR_INVALID_ARG, "lid_u and g must be finite");
+  if (p->solver < CFD_SOLVER_CG || p->solver > CFD_SOLVER_IR)
+    return set_err(nullptr, CFD_ERR_INVALID_ARG, "unknown solver %d", p->solver);
+  if (!(p->rtol > 0) || p->rtol >= 1) return set_err(nullptr, CFD_ERR_INVALID_ARG, "rtol must be in (0, 1)");
+  if (p->max_iters < 0) return set_err(nullptr, CFD_ERR_INVALID_ARG, "max_iters must be >= 0");
+  if (p->inner_rtol < 0 || p->inner_rtol >= 1) return set_err(nullptr, CFD_ERR_INVALID_ARG, "inner_rtol must be in [0, 1)");
+  for (int i = 0; i < 8; ++i)
+    if (p->reserved[i] != 0) return set_err(nullptr, CFD_ERR_INVALID_ARG, "reserved fields must be zero");
+  return CFD_OK;
+}
+
+int iter_cap(const cfd_params& p) {
+  if (p.max_iters > 0) return p.max_iters;
+  int m = p.nx > p.ny ? p.nx : p.ny;
+  m = m > p.nz ? m : p.nz;
+  return 20 * m;
+}
+
+PhysArgs phys(const cfd_handle* h) {
+  PhysArgs a{};
+  a.nx = h->prm.nx; a.ny = h->prm.ny; a.nz = h->prm.nz;
+  a.h = h->prm.length / h->prm.nx;
+  a.inv_h = 1.0 / a.h;
+  a.dt = h->prm.dt; a.rho = h->prm.rho; a.nu = h->prm.nu; a.lid_u = h->prm.lid_u;
+  a.g[0] = h->prm.g[0]; a.g[1] = h->prm.g[1]; a.g[2] = h->prm.g[2];
+  a.u = h->u; a.v = h->v; a.w = h->w; a.ua = h->ua; a.va = h->va; a.wa = h->wa;
+  a.p = h->p; a.b = h->b;
+  return a;
+}
+
+int tz_for(int mz) {
+  // cells per thread along z in the stencil tiles
+  if (mz >= 256) return 16;
+  if (mz >= 64) return 8;
+  return 4;
+}
+
+// Velocity diffusion solve for component comp (x = intermediate velocity).
+int run_diffusion(cfd_handle* h, int comp, DevSolveStats* st) {
+  PhysArgs pa = phys(h);
+  int rc = cuda_check(h, launch_diffusion_rhs(pa, comp, h->stream, &h->launches), "diffusion rhs");
+  if (rc) return rc;
+  CgArgs a{};
+  a.g = GridDims{h->prm.nx + (comp == 0), h->prm.ny + (comp == 1), h->prm.nz + (comp == 2)};
+  a.kind = kOpVelU + comp;
+  a.precond = 0;
+  a.c = h->prm.nu * h->prm.dt / (pa.h * pa.h);
+  a.x = comp == 0 ? h->ua : (comp == 1 ? h->va : h->wa);
+  a.b = h->b; a.r = h->r; a.d0 = h->d0; a.d1 = h->d1; a.q = h->q;
+  a.zero_x0 = 0; a.remove_mean = 0; a.gauge = 0; a.gauge_value = 0.0;
+  a.rtol = h->prm.rtol;
+  a.max_iters = iter_cap(h->prm);
+  a.max_restarts = kMaxRestarts;
+  a.timeout_ns = kTimeoutNs;
+  a.ctrl = h->ctrl; a.partials = h->partials; a.stats = st;
+  a.tz = tz_for(a.g.mz);
+  rc = cuda_check(h, cudaMemsetAsync(h->ctrl, 0, sizeof(SolveCtrl), h->stream), "memset ctrl");
+  if (rc) return rc;
+  return cuda_check(h, launch_cg(a, h->lg, h->stream, &h->launches), "diffusion CG launch");
+}
+
+// Pressure solve A x = b on the handle's workspace b (already filled).
+int run_pressure(cfd_handle* h, double* x, int zero_x0, int gauge, DevSolveStats* st) {
+  int rc = cuda_check(h, cudaMemsetAsync(h->ctrl, 0, sizeof(SolveCtrl), h->stream), "memset ctrl");
+  if (rc) return rc;
+  GridDims g{h->prm.nx, h->prm.ny, h->prm.nz};
+  if (h->prm.solver == CFD_SOLVER_IR) {
+    IrArgs a{};
+    a.g = g;
+    a.x = x; a.b = h->b; a.r = h->r;
+    a.r32 = h->r32; a.d32 = h->d32; a.p0_32 = h->p0_32; a.p1_32 = h->p1_32; a.q32 = h->q32;
+    a.zero_x0 = zero_x0; a.remove_mean = 1; a.gauge = gauge; a.gauge_value = 1.0;
+    a.rtol = h->prm.rtol;
+    a.inner_rtol = h->prm.inner_rtol > 0 ? h->prm.inner_rtol : 1e-4;
+    a.max_iters = iter_cap(h->prm);
+    a.max_outer = 30;
+    a.timeout_ns = kTimeoutNs;
+    a.ctrl = h->ctrl; a.partials = h->partials; a.stats = st;
+    a.tz = tz_for(g.mz);
+    const int t = phase_begin(h, CFD_PHASE_PCG);
+    rc = cuda_check(h, launch_ir(a, h->lg, h->stream, &h->launches), "IR launch");
+    phase_end(h, t);
+    return rc;
+  }
+  CgArgs a{};
+  a.g = g;
+  a.kind = kOpPressure;
+  a.precond = h->prm.solver == CFD_SOLVER_JACOBI ? 1 : 0;
+  a.c = 0.0;
+  a.x = x; a.b = h->b; a.r = h->r; a.d0 = h->d0; a.d1 = h->d1; a.q = h->q;
+  a.zero_x0 = zero_x0; a.remove_mean = 1; a.gauge = gauge; a.gauge_value = 1.0;
+  a.rtol = h->prm.rtol;
+  a.max_iters = iter_cap(h->prm);
+  a.max_restarts = kMaxRestarts;
+  a.timeout_ns = kTimeoutNs;
+  a.ctrl = h->ctrl; a.partials = h->partials; a.stats = st;
+  a.tz = tz_for(g.mz);
+  const int t = phase_begin(h, CFD_PHASE_PCG);
+  rc = cuda_check(h, launch_cg(a, h->lg, h->stream, &h->launches), "pressure CG launch");
+  phase_end(h, t);
+  return rc;
+}
+
+int run_substep(cfd_handle* h, int which, DevStepStats* st) {
+  PhysArgs pa = phys(h);
+  int rc = CFD_OK;
+  switch (which) {
+    case CFD_SUBSTEP_FORCES:
+      if (h->prm.g[0] != 0.0 || h->prm.g[1] != 0.0 || h->prm.g[2] != 0.0) {
+        const int t = phase_begin(h, CFD_PHASE_FORCES);
+        rc = cuda_check(h, launch_forces(pa, h->stream, &h->launches), "forces");
+        phase_end(h, t);
+      }
+      return rc;
+    case CFD_SUBSTEP_ADVECT: {
+      // (u, v, w) -> (ua, va, wa)
+      const int t = phase_begin(h, CFD_PHASE_ADVECT);
+      rc = cuda_check(h, launch_advect(pa, h->stream, &h->launches), "advect");
+      phase_end(h, t);
+      return rc;
+    }
+    case CFD_SUBSTEP_DIFFUSE:
+      if (h->prm.nu > 0.0) {
+        const int t = phase_begin(h, CFD_PHASE_DIFFUSE);
+        for (int c = 0; c < 3 && !rc; ++c) rc = run_diffusion(h, c, &st->d[c]);
+        phase_end(h, t);
+      }
+      return rc;
+    case CFD_SUBSTEP_PROJECT: {
+      int t = phase_begin(h, CFD_PHASE_DIVERGENCE);
+      rc = cuda_check(h, launch_divergence(pa, h->stream, &h->launches), "divergence");
+      phase_end(h, t);
+      if (rc) return rc;
+      rc = run_pressure(h, h->p, h->prm.warm_start ? 0 : 1, 1, &st->p);
+      if (rc) return rc;
+      t = phase_begin(h, CFD_PHASE_CORRECT);
+      rc = cuda_check(h, launch_correct(pa, h->stream, &h->launches), "correct");
+      phase_end(h, t);
+      return rc;
+    }
+  }
+  return set_err(h, CFD_ERR_INVALID_ARG, "unknown substep %d", which);
+}
+
+// Clear a stats slot so that skipped solves read as zero iterations / OK.
+int clear_stats(cfd_handle* h, DevStepStats* st, int n) {
+  return cuda_check(h, cudaMemsetAsync(st, 0, sizeof(DevStepStats) * size_t(n), h->stream), "memset stats");
+}
+
+int worst(int a, int b) {
+  // more negative codes are not "worse" in general; prefer the first failure
+  return a != CFD_OK ? a : b;
+}
+
+void to_public(const DevStepStats& d, cfd_solve_stats* o) {
+  std::memset(o, 0, sizeof(*o));
+  o->iters = d.p.iters;
+  o->outer_iters = d.p.outer_iters;
+  o->restarts = d.p.restarts;
+  o->status = d.p.status;
+  for (int c = 0; c < 3; ++c) o->diff_iters[c] = d.d[c].iters;
+  int ds = CFD_OK;
+  for (int c = 0; c < 3; ++c) ds = worst(ds, d.d[c].status);
+  o->diff_status = ds;
+  o->rel_resid = d.p.rel_resid;
+  o->b_norm = d.p.b_norm;
+}
+
+// Copy n stats slots back (synchronising), convert, and return the worst status.
+int gather_stats(cfd_handle* h, int n, cfd_solve_stats* out) {
+  DevStepStats* host = static_cast<DevStepStats*>(std::malloc(sizeof(DevStepStats) * size_t(n)));
+  if (!host) return set_err(h, CFD_ERR_INVALID_ARG, "out of host memory");
+  int rc = cuda_check(h, cudaMemcpyAsync(host, h->stats, sizeof(DevStepStats) * size_t(n), cudaMemcpyDeviceToHost, h->stream),
+                      "copy stats");
+  if (!rc) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "synchronize");
+  SolveCtrl ctrl{};
+  if (!rc) rc = cuda_check(h, cudaMemcpy(&ctrl, h->ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost), "copy ctrl");
+  int status = CFD_OK;
+  if (!rc) {
+    for (int i = 0; i < n; ++i) {
+      if (out) to_public(host[i], &out[i]);
+      status = worst(status, host[i].p.status);
+      for (int c = 0; c < 3; ++c) status = worst(status, host[i].d[c].status);
+    }
+    if (ctrl.error != 0) status = worst(status, ctrl.error);
+  }
+  std::free(host);
+  if (rc) return rc;
+  if (status != CFD_OK)
+    set_err(h, status, "solver status %d (%s)", status,
+            status == CFD_ERR_NOT_CONVERGED ? "not converged"
+            : status == CFD_ERR_BREAKDOWN ? "CG breakdown"
+            : status == CFD_ERR_TIMEOUT ? "device wait timed out" : "error");
+  return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cfd_workspace_bytes(const cfd_params* params, size_t* bytes) {
+  int rc = validate(params);
+  if (rc) return rc;
+  if (!bytes) return set_err(nullptr, CFD_ERR_INVALID_ARG, "bytes is NULL");
+  *bytes = ws_layout(*params, kMaxBlocksBound).total;
+  return CFD_OK;
+}
+
+int cfd_create(const cfd_params* params, void* dev_ws, size_t bytes, cfd_stream_t stream, cfd_handle** out) {
+  int rc = validate(params);
+  if (rc) return rc;
+  if (!out) return set_err(nullptr, CFD_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!dev_ws) return set_err(nullptr, CFD_ERR_INVALID_ARG, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(dev_ws) & 255) return set_err(nullptr, CFD_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+  Layout L = ws_layout(*params, kMaxBlocksBound);
+  if (bytes < L.total)
+    return set_err(nullptr, CFD_ERR_WORKSPACE_TOO_SMALL, "workspace %zu bytes < required %zu", bytes, L.total);
+  cudaPointerAttributes attr{};
+  if (cudaPointerGetAttributes(&attr, dev_ws) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    return set_err(nullptr, CFD_ERR_INVALID_ARG, "workspace is not device memory");
+  }
+  cfd_handle* h = new (std::nothrow) cfd_handle();
+  if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "out of host memory");
+  h->prm = *params;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  h->ws = static_cast<char*>(dev_ws);
+  h->ws_bytes = bytes;
+  h->L = L;
+  auto D = [&](size_t o) { return reinterpret_cast<double*>(h->ws + o); };
+  auto F = [&](size_t o) { return reinterpret_cast<float*>(h->ws + o); };
+  h->u = D(L.u); h->v = D(L.v); h->w = D(L.w);
+  h->ua = D(L.ua); h->va = D(L.va); h->wa = D(L.wa); h->p = D(L.p);
+  h->b = D(L.b); h->r = D(L.r); h->d0 = D(L.d0); h->d1 = D(L.d1); h->q = D(L.q);
+  if (params->solver == CFD_SOLVER_IR) {
+    h->r32 = F(L.r32); h->d32 = F(L.d32); h->p0_32 = F(L.p0_32); h->p1_32 = F(L.p1_32); h->q32 = F(L.q32);
+  }
+  h->partials = D(L.partials);
+  h->ctrl = reinterpret_cast<SolveCtrl*>(h->ws + L.ctrl);
+  h->stats = reinterpret_cast<DevStepStats*>(h->ws + L.stats);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&h->lg.num_sms, cudaDevAttrMultiProcessorCount, dev);
+  h->lg.blocks = cg_max_coresident_blocks(params->solver == CFD_SOLVER_IR);
+  if (h->lg.blocks > kMaxBlocksBound) h->lg.blocks = kMaxBlocksBound;
+  if (h->lg.blocks < 1) {
+    delete h;
+    return set_err(nullptr, CFD_ERR_CUDA, "cannot place the solve kernel on this device");
+  }
+  std::snprintf(h->err, sizeof(h->err), "no error");
+  // initial state (Sec. 3, eq. 3): v0 = 0, p0 = 1
+  rc = cuda_check(h, cudaMemsetAsync(h->ws, 0, L.total, h->stream), "memset workspace");
+  if (!rc) rc = cuda_check(h, launch_fill(h->p, size_t(params->nx) * params->ny * params->nz, 1.0, h->stream, &h->launches),
+                          "fill p");
+  if (rc) {
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return CFD_OK;
+}
+
+void cfd_destroy(cfd_handle* h) {
+  if (!h) return;
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  delete h;
+}
+
+const char* cfd_last_error(const cfd_handle* h) { return h ? h->err : g_last_error; }
+
+int cfd_set_stream(cfd_handle* h, cfd_stream_t stream) {
+  if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  return CFD_OK;
+}
+
+static int field_ptr(cfd_handle* h, int field, double** ptr, size_t* count, int64_t dims[3]) {
+  const cfd_params& p = h->prm;
+  switch (field) {
+    case CFD_FIELD_U: *ptr = h->u; dims[0] = p.nx + 1; dims[1] = p.ny; dims[2] = p.nz; break;
+    case CFD_FIELD_V: *ptr = h->v; dims[0] = p.nx; dims[1] = p.ny + 1; dims[2] = p.nz; break;
+    case CFD_FIELD_W: *ptr = h->w; dims[0] = p.nx; dims[1] = p.ny; dims[2] = p.nz + 1; break;
+    case CFD_FIELD_P: *ptr = h->p; dims[0] = p.nx; dims[1] = p.ny; dims[2] = p.nz; break;
+    default: return set_err(h, CFD_ERR_INVALID_ARG, "unknown field %d", field);
+  }
+  *count = size_t(dims[0]) * dims[1] * dims[2];
+  return CFD_OK;
+}
+
+int cfd_set_field(cfd_handle* h, int field, const double* src, int src_on_device) {
+  if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
+  if (!src) return set_err(h, CFD_ERR_INVALID_ARG, "src is NULL");
+  double* dst;
+  size_t n;
+  int64_t dims[3];
+  int rc = field_ptr(h, field, &dst, &n, dims);
+  if (rc) return rc;
+  rc = cuda_check(h, cudaMemcpyAsync(dst, src, n * 8, src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream),
+                  "set_field copy");
+  if (rc) return rc;
+  if (field != CFD_FIELD_P) rc = cuda_check(h, launch_zero_wall_faces(phys(h), h->stream, &h->launches), "zero wall faces");
+  return rc;
+}
+
+int cfd_read_field(cfd_handle* h, int field, double* dst, int dst_on_device, int64_t dims_out[3]) {
+  if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
+  double* src;
+  size_t n;
+  int64_t dims[3];
+  int rc = field_ptr(h, field, &src, &n, dims);
+  if (rc) return rc;
+  if (dims_out) { dims_out[0] = dims[0]; dims_out[1] = dims[1]; dims_out[2] = dims[2]; }
+  if (!dst) return dims_out ? CFD_OK : set_err(h, CFD_ERR_INVALID_ARG, "dst is NULL");
+  rc = cuda_check(h, cudaMemcpyAsync(dst, src, n * 8, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream),
+                  "read_field copy");
+  if (rc) return rc;
+  if (!dst_on_device) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "synchronize");
+  return rc;
+}
+
+int cfd_step(cfd_handle* h, int nsteps, cfd_solve_stats* per_step) {
+  if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
+  if (nsteps < 0) return set_err(h, CFD_ERR_INVALID_ARG, "nsteps must be >= 0");
+  int status = CFD_OK;
+  int done = 0;
+  while (done < nsteps) {
+    const int chunk = (nsteps - done) < kStatsCap ? (nsteps - done) : kStatsCap;
+    int rc = clear_stats(h, h->stats, chunk);
+    if (rc) return rc;
+    for (int s = 0; s < chunk; ++s) {
+      DevStepStats* st = h->stats + s;
+      for (int which = CFD_SUBSTEP_FORCES; which <= CFD_SUBSTEP_PROJECT; ++which) {
+        rc = run_substep(h, which, st);
+        if (rc) return rc;
+      }
+    }
+    if (per_step) {
+      rc = gather_stats(h, chunk, per_step + done);
+      if (rc != CFD_OK && rc != CFD_ERR_NOT_CONVERGED && rc != CFD_ERR_BREAKDOWN && rc != CFD_ERR_TIMEOUT) return rc;
+      status = worst(status, rc);
+    }
+    done += chunk;
+  }
+  return status;
+}
+
+int cfd_substep(cfd_handle* h, int which, cfd_solve_stats* stats) {
+  if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
+  if (which < CFD_SUBSTEP_FORCES || which > CFD_SUBSTEP_PROJECT) return set_err(h, CFD_ERR_INVALID_ARG, "unknown substep %d", which);
+  int rc = clear_stats(h, h->stats, 1);
+  if (rc) return rc;
+  // Inside a step the diffusion and projection read the intermediate
+  // velocity (ua, va, wa); a standalone substep starts from and ends in the
+  // current velocity (u, v, w).
+  auto copy_vel = [&](bool to_intermediate) {
+    int r2 = CFD_OK;
+    for (int c = 0; c < 3 && !r2; ++c) {
+      double* cur = c == 0 ? h->u : (c == 1 ? h->v : h->w);
+      double* mid = c == 0 ? h->ua : (c == 1 ? h->va : h->wa);
+      const size_t n = face_count(h->prm, c);
+      r2 = cuda_check(h, cudaMemcpyAsync(to_intermediate ? mid : cur, to_intermediate ? cur : mid, n * 8,
+                                         cudaMemcpyDeviceToDevice, h->stream), "substep copy");
+    }
+    return r2;
+  };
+  if (which == CFD_SUBSTEP_DIFFUSE || which == CFD_SUBSTEP_PROJECT) rc = copy_vel(true);
+  if (!rc) rc = run_substep(h, which, h->stats);
+  if (!rc && (which == CFD_SUBSTEP_ADVECT || which == CFD_SUBSTEP_DIFFUSE)) rc = copy_vel(false);
+  if (rc) return rc;
+  if (stats) return gather_stats(h, 1, stats);
+  return CFD_OK;
+}
+
+int cfd_solve_pressure(cfd_handle* h, const double* b_dev, double* x_dev, cfd_solve_stats* stats) {
+  if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
+  if (!b_dev || !x_dev) return set_err(h, CFD_ERR_INVALID_ARG, "b or x is NULL");
+  const size_t n = size_t(h->prm.nx) * h->prm.ny * h->prm.nz;
+  int rc = clear_stats(h, h->stats, 1);
+  if (!rc) rc = cuda_check(h, cudaMemcpyAsync(h->b, b_dev, n * 8, cudaMemcpyDeviceToDevice, h->stream), "copy b");
+  if (!rc) rc = run_pressure(h, x_dev, h->prm.warm_start ? 0 : 1, 0, &h->stats->p);
+  if (rc) return rc;
+  if (stats) return gather_stats(h, 1, stats);
+  return CFD_OK;
+}
+
+int cfd_apply_poisson(cfd_handle* h, const double* x_dev, double* y_dev) {
+  if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
+  if (!x_dev || !y_dev) return set_err(h, CFD_ERR_INVALID_ARG, "x or y is NULL");
+  GridDims g{h->prm.nx, h->prm.ny, h->prm.nz};
+  return cuda_check(h, launch_apply_poisson(g, x_dev, y_dev, tz_for(g.mz), h->stream, &h->launches), "apply_poisson");
+}
+
+int64_t cfd_launch_count(const cfd_handle* h) { return h ? h->launches : 0; }
+
+int cfd_enable_timing(cfd_handle* h, int on) {
+  if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
+  h->timing = on != 0;
+  return CFD_OK;
+}
+
+int cfd_phase_times(cfd_handle* h, double* ms_out, int64_t* calls_out) {
+  if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
+  int rc = cuda_check(h, cudaStreamSynchronize(h->stream), "synchronize");
+  if (rc) return rc;
+  double ms[CFD_PHASE_COUNT] = {0};
+  int64_t calls[CFD_PHASE_COUNT] = {0};
+  for (const auto& p : h->pending) {
+    float t = 0.f;
+    rc = cuda_check(h, cudaEventElapsedTime(&t, p.a, p.b), "event elapsed");
+    if (rc) return rc;
+    ms[p.phase] += t;
+    calls[p.phase] += 1;
+  }
+  h->pending.clear();
+  h->ev_next = 0;
+  for (int i = 0; i < CFD_PHASE_COUNT; ++i) {
+    if (ms_out) ms_out[i] = ms[i];
+    if (calls_out) calls_out[i] = calls[i];
+  }
+  return CFD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,116 @@
+// Host-side interface between the C-ABI layer and the kernel translation
+// units.  Not part of the public ABI (include/cfd.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "cfd_common.cuh"
+
+namespace cfd {
+
+// Operator kinds of the stencil solves.
+enum OpKind : int {
+  kOpPressure = 0,  // Neumann 7-point, A = -h^2 Laplacian (scaled), singular
+  kOpVelU = 1,      // I + c L for the u faces (x walls are known rows)
+  kOpVelV = 2,      // ... v faces
+  kOpVelW = 3       // ... w faces
+};
+
+struct GridDims {
+  int mx, my, mz;
+  size_t count() const { return size_t(mx) * my * mz; }
+};
+
+// Geometry of one persistent solve launch.
+struct LaunchGeom {
+  int blocks;       // co-resident blocks of the cooperative launch
+  int tz;           // cells per thread along z in the stencil tiles
+  int num_sms;
+};
+
+// Arguments of the persistent FP64 CG solve.
+struct CgArgs {
+  GridDims g;
+  int kind;              // OpKind
+  int precond;           // 0 none, 1 Jacobi (pressure only)
+  double c;              // Helmholtz coefficient nu*dt/h^2 (velocity kinds)
+  double* x;             // solution, in/out
+  double* b;             // right-hand side, modified in place (mean removal)
+  double* r;
+  double* d0;
+  double* d1;
+  double* q;
+  int zero_x0;           // 1: x0 = 0
+  int remove_mean;       // 1: b -= mean(b) first
+  int gauge;             // 1: after the solve, x += gauge_value - mean(x)
+  double gauge_value;
+  double rtol;
+  int max_iters;
+  int max_restarts;
+  unsigned long long timeout_ns;
+  SolveCtrl* ctrl;       // zeroed by the host before the launch
+  double* partials;      // blocks * kMaxPartials doubles
+  DevSolveStats* stats;  // written by block 0 at exit
+  int tz;
+};
+
+// Arguments of the FP32-inner / FP64-outer iterative-refinement solve.
+struct IrArgs {
+  GridDims g;
+  double* x;       // FP64 solution (out)
+  double* b;       // FP64 rhs (mean removed in place)
+  double* r;       // FP64 outer residual
+  float* r32;      // FP32 inner vectors
+  float* d32;      // inner solution increment
+  float* p0_32;
+  float* p1_32;
+  float* q32;
+  int zero_x0;
+  int remove_mean;
+  int gauge;
+  double gauge_value;
+  double rtol;
+  double inner_rtol;
+  int max_iters;   // cap on the total inner iterations
+  int max_outer;
+  unsigned long long timeout_ns;
+  SolveCtrl* ctrl;
+  double* partials;
+  DevSolveStats* stats;
+  int tz;
+};
+
+struct PhysArgs {
+  int nx, ny, nz;
+  double h, inv_h, dt, rho, nu, lid_u;
+  double g[3];
+  double* u; double* v; double* w;       // current velocity
+  double* ua; double* va; double* wa;    // intermediate velocity
+  double* p;                             // pressure (cells)
+  double* b;                             // solver rhs scratch
+};
+
+// Kernel launchers (return the CUDA error of the launch).  Each adds the
+// number of kernels it launched to *launches.
+cudaError_t launch_cg(const CgArgs& a, const LaunchGeom& lg, cudaStream_t s, int64_t* launches);
+cudaError_t launch_ir(const IrArgs& a, const LaunchGeom& lg, cudaStream_t s, int64_t* launches);
+cudaError_t launch_apply_poisson(GridDims g, const double* x, double* y, int tz, cudaStream_t s,
+                                 int64_t* launches);
+cudaError_t launch_forces(const PhysArgs& a, cudaStream_t s, int64_t* launches);
+cudaError_t launch_advect(const PhysArgs& a, cudaStream_t s, int64_t* launches);
+cudaError_t launch_diffusion_rhs(const PhysArgs& a, int comp, cudaStream_t s, int64_t* launches);
+cudaError_t launch_divergence(const PhysArgs& a, cudaStream_t s, int64_t* launches);
+cudaError_t launch_correct(const PhysArgs& a, cudaStream_t s, int64_t* launches);
+cudaError_t launch_zero_wall_faces(const PhysArgs& a, cudaStream_t s, int64_t* launches);
+cudaError_t launch_fill(double* p, size_t n, double value, cudaStream_t s, int64_t* launches);
+
+// Co-resident block count for the persistent solve kernels on this device.
+int cg_max_coresident_blocks(int kind_is_ir);
+
+constexpr int kTileX = 32;
+constexpr int kTileY = 8;
+constexpr int kSolveThreads = kTileX * kTileY;
+
+}  // namespace cfd
