@@ -1,0 +1,397 @@
+#!/usr/bin/env python3
+"""Benchmark: cell-steps/s of the lid-driven-cavity fractional step on GB300.
+
+Workload (default): the FP64 cavity of Sec. 3 / 3.1 of arXiv 2504.03697 at
+64^3 cells, lid 1.0, nu 1e-3, dt 1e-2, pressure by unpreconditioned CG to
+rtol 1e-8 (true FP64 residual), velocity initialised to the seeded
+uniform[-1e-3, 1e-3] perturbation (seed 2 + rank).  One bench "step" is one
+time step: applyForces, advection, implicit diffusion (3 CG solves),
+divergence, pressure CG, correction.  Inputs are synthetic and resident in
+HBM when the timed region starts; L2 is flushed (256 MiB write) between
+timed steps, outside the timed events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun: one independent cavity per rank (weak scaling,
+no data-path collective); the timed region is bracketed by a barrier and a
+synchronize and its maximum over ranks is reported.  ``--impl reference``
+times the FP64 CPU oracle on the host cores instead (rank 0 only).
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "cavity64": dict(n=64, nu=1e-3, dt=1e-2, lid_u=1.0, seed=2, amp=1e-3,
+                     desc="lid-driven cavity 64^3 cells, FP64, lid 1.0, nu 1e-3, dt 1e-2, "
+                          "pressure CG to rtol 1e-8, seeded 1e-3 perturbation"),
+    "cavity16": dict(n=16, nu=1e-2, dt=1e-2, lid_u=1.0, seed=1, amp=1e-3,
+                     desc="lid-driven cavity 16^3 cells, FP64, lid 1.0, nu 1e-2, dt 1e-2, "
+                          "pressure CG to rtol 1e-8, seeded 1e-3 perturbation"),
+}
+
+# Algorithmic work of one pressure-CG iteration per cell (FP64, matrix-free):
+# p = z + beta p (2), q = A p (5 adds + 6 x_c - sum: 7), p.q (2), x += a p (2),
+# r -= a q (2), r.r (2)  -> 17 flops; bytes: read r, p_old, write p, q (32) +
+# read x, p, r, q, write x, r (48) -> 80 B.  Setup + true residual + gauge per
+# solve: ~14 flops and ~72 B per cell.
+CG_FLOPS_PER_CELL_ITER = 17
+CG_BYTES_PER_CELL_ITER = 80
+CG_FLOPS_PER_CELL_SOLVE = 14
+CG_BYTES_PER_CELL_SOLVE = 72
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cavity64")
+    ap.add_argument("--solver", default="cg")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--max-seconds", type=float, default=150.0, help=argparse.SUPPRESS)
+    return ap.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (measurement only: barrier + max of the timed region)
+# ---------------------------------------------------------------------------
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def init_dist(backend):
+    import torch.distributed as dist
+    rank, world, _ = dist_env()
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return dist if world > 1 else None
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def reduce_max(dist, value, device=None):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(cells_per_rank, steps, world, max_seconds):
+    """Whole-job throughput: all ranks' cell-steps over the slowest rank's time."""
+    return cells_per_rank * steps * world / max_seconds
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def physical_gpu(local):
+    """nvidia-smi index (or UUID) of this process's CUDA device."""
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "").strip()
+    if cvd:
+        parts = [p.strip() for p in cvd.split(",") if p.strip()]
+        if local < len(parts):
+            return parts[local]
+    return local
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (CPU baseline / reference arm): runs in a child process
+# ---------------------------------------------------------------------------
+def oracle_sample_main(args):
+    """Child process: time the FP64 oracle on the workload for a bounded
+    number of steps; print one JSON object."""
+    from oracle import fractional_step as fs
+    from oracle.mac import Cavity
+    from paper_2504_03697_gb300.synthetic import cavity_perturbation
+
+    wl = WORKLOADS[args.workload]
+    n = wl["n"]
+    cav = Cavity(n, n, n, dt=wl["dt"], nu=wl["nu"], lid_u=wl["lid_u"])
+    st = fs.initial_state(cav, cavity_perturbation(n, n, n, wl["seed"], wl["amp"]))
+    for _ in range(args.warmup):
+        st, _ = fs.step(cav, st)
+    t0 = time.perf_counter()
+    done = 0
+    per_step = []
+    while done < args.steps:
+        a = time.perf_counter()
+        st, _ = fs.step(cav, st)
+        per_step.append(time.perf_counter() - a)
+        done += 1
+        if time.perf_counter() - t0 > args.max_seconds:
+            break
+    el = time.perf_counter() - t0
+    print(json.dumps({"steps": done, "seconds": el, "cells": n ** 3, "per_step_s": per_step}))
+
+
+def run_oracle_child(workload, steps, warmup, max_seconds):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "LOCAL_WORLD_SIZE", "GROUP_RANK", "ROLE_RANK"):
+        env.pop(k, None)
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", "--workload", workload,
+           "--steps", str(steps), "--warmup", str(warmup), "--max-seconds", str(max_seconds)]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+# ---------------------------------------------------------------------------
+# reference arm
+# ---------------------------------------------------------------------------
+def main_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    wl = WORKLOADS[args.workload]
+    res = run_oracle_child(args.workload, args.steps, min(args.warmup, 1), args.max_seconds)
+    value = res["cells"] * res["steps"] / res["seconds"]
+    sample = (f"{res['steps']} time steps of the {wl['n']}^3 cavity (of {args.steps} requested; capped at "
+              f"{args.max_seconds:.0f} s), FP64 numpy/scipy oracle, single thread, after "
+              f"{min(args.warmup, 1)} warm-up step")
+    line = {"metric": "cell-steps/s", "value": value, "unit": "cell-steps/s", "impl": "reference",
+            "n_gpus": args.gpus, "steps": res["steps"], "warmup": min(args.warmup, 1),
+            "ms_per_step": 1e3 * res["seconds"] / max(res["steps"], 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["desc"], "n": wl["n"], "parallelism": "host oracle, rank 0 only"},
+            "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": sample, "cpu": cpu_model(), "host_cores": os.cpu_count()},
+            "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = init_dist("nccl")
+
+    from paper_2504_03697_gb300 import build as B
+    B.build()
+    from paper_2504_03697_gb300 import cfd
+    from paper_2504_03697_gb300.synthetic import cavity_perturbation
+
+    wl = WORKLOADS[args.workload]
+    n = wl["n"]
+    cells = n ** 3
+    prm = cfd.make_params(n, n, n, dt=wl["dt"], nu=wl["nu"], lid_u=wl["lid_u"], solver=args.solver)
+    stream = torch.cuda.current_stream(device)
+    cav = cfd.Cavity(prm, device=device)
+    init = cavity_perturbation(n, n, n, wl["seed"] + rank, wl["amp"])
+    for name, f in zip("uvw", init):
+        cav.set_field(name, f)
+
+    # warm-up
+    if args.warmup > 0:
+        rc, _ = cav.step(args.warmup, stats=True)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=device)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+
+    cav.phase_times()  # reset
+    cav.enable_timing(True)
+    launches0 = cav.launch_count()
+    sampler = ClockSampler(physical_gpu(local)) if rank == 0 else None
+    barrier(dist, device)
+    torch.cuda.synchronize(device)
+    wall0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.zero_()  # L2 flush, outside the timed events
+        starts[s].record(stream)
+        cav.step(1, stats=False)
+        ends[s].record(stream)
+    torch.cuda.synchronize(device)
+    wall = time.perf_counter() - wall0
+    barrier(dist, device)
+    clocks = sampler.stop() if sampler else None
+    launches = cav.launch_count() - launches0
+    cav.enable_timing(False)
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    t_local = sum(step_ms) / 1e3
+    t_max = reduce_max(dist, t_local, device)
+    phases = cav.phase_times()
+    rc, stats = cav.recent_stats(args.steps)
+    iters = [s["iters"] for s in stats]
+    worst_resid = max(s["rel_resid"] for s in stats)
+    ok = rc == cfd.CFD_OK and worst_resid <= 1e-8 * 1.0000001
+
+    value = aggregate(cells, args.steps, world, t_max)
+    pcg_ms, pcg_calls = phases["pcg"]
+    pcg_avg_s = pcg_ms / max(pcg_calls, 1) / 1e3
+    mean_iters = float(np.mean(iters))
+    flops_per_launch = cells * (CG_FLOPS_PER_CELL_ITER * mean_iters + CG_FLOPS_PER_CELL_SOLVE)
+    bytes_per_launch = cells * (CG_BYTES_PER_CELL_ITER * mean_iters + CG_BYTES_PER_CELL_SOLVE)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    fp64_peak_tflops = 1.20  # FP64 FMA pipe, derived in the design doc (152 SMs x 2 DFMA/clk x 2 flops x ~2 GHz)
+    achieved_tflops = flops_per_launch / pcg_avg_s / 1e12
+    roofline = {"bound": "alu", "kernel": "cg_fp64_kernel (pressure PCG, persistent)",
+                "achieved": achieved_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved_tflops / fp64_peak_tflops, "traffic": None,
+                "peak_source": "FP64 FMA rate from the recipe's unit counts and clocks (1.2-1.25 TFLOP/s)",
+                "hbm_achieved_gbs": bytes_per_launch / pcg_avg_s / 1e9,
+                "hbm_peak_gbs": hbm_peak, "hbm_frac_of_measured": bytes_per_launch / pcg_avg_s / 1e9 / hbm_peak,
+                "launch_ms": pcg_avg_s * 1e3, "flops_per_launch": flops_per_launch,
+                "bytes_per_launch": bytes_per_launch}
+    phase_ms_per_step = {k: v[0] / max(args.steps, 1) for k, v in phases.items()}
+
+    # end-to-end through the C-ABI with host buffers (state round-trips per step)
+    e2e = None
+    if args.e2e_steps > 0:
+        host = {f: torch.empty(cav.shape(f), dtype=torch.float64).pin_memory() for f in "uvwp"}
+        for f in "uvwp":
+            cav.read_field(f, out=host[f])
+        bytes_io = sum(host[f].numel() * 8 for f in "uvwp")
+        barrier(dist, device)
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for f in "uvwp":
+                cav.lib.cfd_set_field(cav.h, cfd.FIELD[f], host[f].data_ptr(), 0)
+            cav.step(1, stats=False)
+            for f in "uvwp":
+                cav.read_field(f, out=host[f])
+        torch.cuda.synchronize(device)
+        te = reduce_max(dist, time.perf_counter() - t0, device)
+        e2e = {"value": aggregate(cells, args.e2e_steps, world, te), "unit": "cell-steps/s",
+               "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io, "steps": args.e2e_steps,
+               "how": "per step: cfd_set_field(u,v,w,p) from pinned host, cfd_step(1), cfd_read_field(u,v,w,p) "
+                      "to pinned host; wall clock"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res = run_oracle_child(args.workload, 10 ** 6, 0, args.cpu_seconds)
+        cpu = {"value": res["cells"] * res["steps"] / res["seconds"], "unit": "cell-steps/s", "cores": 1,
+               "kind": "oracle",
+               "sample": f"first {res['steps']} time steps of the same {n}^3 cavity ({res['seconds']:.1f} s), "
+                         f"FP64 numpy/scipy oracle, single thread",
+               "cpu": cpu_model(), "host_cores": os.cpu_count()}
+
+    if rank == 0:
+        line = {"metric": "cell-steps/s", "value": value, "unit": "cell-steps/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": wl["desc"], "n": n, "cells": cells, "solver": args.solver,
+                           "steps_per_rank": args.steps, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                           "l2": "flushed between timed steps (256 MiB write outside the timed events)"},
+                "solve": {"pcg_iters_mean": mean_iters, "pcg_iters_min": min(iters), "pcg_iters_max": max(iters),
+                          "time_to_rtol_ms_mean": pcg_avg_s * 1e3, "rel_resid_max": worst_resid,
+                          "all_converged": bool(ok)},
+                "phase_ms_per_step": phase_ms_per_step,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks, "wall_s_timed": wall}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0 if ok else 1
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.oracle_sample:
+        oracle_sample_main(args)
+        return 0
+    if args.impl == "reference":
+        return main_reference(args)
+    return main_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -138,6 +138,12 @@ int cfd_read_field(cfd_handle *h, int field, double *dst, int dst_on_device, int
  * solver status seen; otherwise it returns after enqueueing. */
 int cfd_step(cfd_handle *h, int nsteps, cfd_solve_stats *per_step);
 
+/* Statistics of the last n steps taken by cfd_step (oldest first; n at
+ * most 1024 and at most the number of steps taken).  Synchronises the
+ * stream; returns the worst solver status among them.  Lets a caller run
+ * steps asynchronously (per_step = NULL) and inspect them afterwards. */
+int cfd_recent_stats(cfd_handle *h, int n, cfd_solve_stats *out);
+
 /* Run one substep (CFD_SUBSTEP_*) of the step on the current state.
  * stats (nullable) as for cfd_step. */
 int cfd_substep(cfd_handle *h, int which, cfd_solve_stats *stats);

@@ -87,6 +87,7 @@ def load_library(path: Optional[str] = None):
         "cfd_solve_pressure": (ctypes.c_int, [vp, vp, vp, P(cfd_solve_stats)]),
         "cfd_apply_poisson": (ctypes.c_int, [vp, vp, vp]),
         "cfd_launch_count": (ctypes.c_int64, [vp]),
+        "cfd_recent_stats": (ctypes.c_int, [vp, ctypes.c_int, P(cfd_solve_stats)]),
         "cfd_enable_timing": (ctypes.c_int, [vp, ctypes.c_int]),
         "cfd_phase_times": (ctypes.c_int, [vp, P(ctypes.c_double), P(ctypes.c_int64)]),
     }
@@ -229,6 +230,12 @@ class Cavity:
     def set_stream(self, stream):
         self.stream = stream
         return self._check(self.lib.cfd_set_stream(self.h, ctypes.c_void_p(_stream_ptr(stream))))
+
+    def recent_stats(self, n):
+        arr = (cfd_solve_stats * max(1, n))()
+        rc = self.lib.cfd_recent_stats(self.h, int(n), arr)
+        self._check(rc, allow=(CFD_ERR_NOT_CONVERGED, CFD_ERR_BREAKDOWN, CFD_ERR_TIMEOUT))
+        return rc, [arr[i].as_dict() for i in range(n)]
 
     def enable_timing(self, on=True):
         return self._check(self.lib.cfd_enable_timing(self.h, 1 if on else 0))

@@ -74,7 +74,7 @@ Layout ws_layout(const cfd_params& p, int max_blocks) {
   }
   L.partials = take(size_t(max_blocks) * kMaxPartials * 8);
   L.ctrl = take(sizeof(SolveCtrl));
-  L.stats = take(size_t(kStatsCap) * sizeof(DevStepStats));
+  L.stats = take(size_t(kStatsCap + 1) * sizeof(DevStepStats));  // ring + one slot for substep/solve calls
   L.total = off;
   return L;
 }
@@ -106,6 +106,7 @@ struct cfd_handle {
   size_t ev_next;
   struct Pending { int phase; cudaEvent_t a, b; };
   std::vector<Pending> pending;
+  int64_t ring;  // steps taken so far (statistics ring position)
 };
 
 namespace {
@@ -326,14 +327,15 @@ void to_public(const DevStepStats& d, cfd_solve_stats* o) {
 }
 
 // Copy n stats slots back (synchronising), convert, and return the worst status.
-int gather_stats(cfd_handle* h, int n, cfd_solve_stats* out) {
-  DevStepStats* host = static_cast<DevStepStats*>(std::malloc(sizeof(DevStepStats) * size_t(n)));
+int gather_stats(cfd_handle* h, const DevStepStats* src, int n, cfd_solve_stats* out) {
+  DevStepStats* host = static_cast<DevStepStats*>(std::malloc(sizeof(DevStepStats) * size_t(n > 0 ? n : 1)));
   if (!host) return set_err(h, CFD_ERR_INVALID_ARG, "out of host memory");
-  int rc = cuda_check(h, cudaMemcpyAsync(host, h->stats, sizeof(DevStepStats) * size_t(n), cudaMemcpyDeviceToHost, h->stream),
+  int rc = cuda_check(h, cudaMemcpyAsync(host, src, sizeof(DevStepStats) * size_t(n), cudaMemcpyDeviceToHost, h->stream),
                       "copy stats");
   if (!rc) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "synchronize");
   SolveCtrl ctrl{};
-  if (!rc) rc = cuda_check(h, cudaMemcpy(&ctrl, h->ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost), "copy ctrl");
+  if (!rc) rc = cuda_check(h, cudaMemcpyAsync(&ctrl, h->ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost, h->stream), "copy ctrl");
+  if (!rc) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "synchronize");
   int status = CFD_OK;
   if (!rc) {
     for (int i = 0; i < n; ++i) {
@@ -484,18 +486,23 @@ int cfd_step(cfd_handle* h, int nsteps, cfd_solve_stats* per_step) {
   int status = CFD_OK;
   int done = 0;
   while (done < nsteps) {
-    const int chunk = (nsteps - done) < kStatsCap ? (nsteps - done) : kStatsCap;
-    int rc = clear_stats(h, h->stats, chunk);
+    // steps fill the statistics ring in order; a chunk never wraps past the
+    // end of the ring so that it can be gathered with one copy
+    const int ring_pos = int(h->ring % kStatsCap);
+    int chunk = nsteps - done;
+    if (chunk > kStatsCap - ring_pos) chunk = kStatsCap - ring_pos;
+    DevStepStats* base = h->stats + ring_pos;
+    int rc = clear_stats(h, base, chunk);
     if (rc) return rc;
     for (int s = 0; s < chunk; ++s) {
-      DevStepStats* st = h->stats + s;
       for (int which = CFD_SUBSTEP_FORCES; which <= CFD_SUBSTEP_PROJECT; ++which) {
-        rc = run_substep(h, which, st);
+        rc = run_substep(h, which, base + s);
         if (rc) return rc;
       }
     }
+    h->ring += chunk;
     if (per_step) {
-      rc = gather_stats(h, chunk, per_step + done);
+      rc = gather_stats(h, base, chunk, per_step + done);
       if (rc != CFD_OK && rc != CFD_ERR_NOT_CONVERGED && rc != CFD_ERR_BREAKDOWN && rc != CFD_ERR_TIMEOUT) return rc;
       status = worst(status, rc);
     }
@@ -504,10 +511,30 @@ int cfd_step(cfd_handle* h, int nsteps, cfd_solve_stats* per_step) {
   return status;
 }
 
+int cfd_recent_stats(cfd_handle* h, int n, cfd_solve_stats* out) {
+  if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
+  if (n < 0 || n > kStatsCap || int64_t(n) > h->ring || !out)
+    return set_err(h, CFD_ERR_INVALID_ARG, "n must be in [0, min(steps taken, %d)] and out non-NULL", kStatsCap);
+  // the last n ring slots, oldest first (at most two contiguous pieces)
+  const int64_t first = h->ring - n;
+  int status = CFD_OK;
+  int done = 0;
+  while (done < n) {
+    const int pos = int((first + done) % kStatsCap);
+    int len = n - done;
+    if (len > kStatsCap - pos) len = kStatsCap - pos;
+    int rc = gather_stats(h, h->stats + pos, len, out + done);
+    if (rc != CFD_OK && rc != CFD_ERR_NOT_CONVERGED && rc != CFD_ERR_BREAKDOWN && rc != CFD_ERR_TIMEOUT) return rc;
+    status = worst(status, rc);
+    done += len;
+  }
+  return status;
+}
+
 int cfd_substep(cfd_handle* h, int which, cfd_solve_stats* stats) {
   if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
   if (which < CFD_SUBSTEP_FORCES || which > CFD_SUBSTEP_PROJECT) return set_err(h, CFD_ERR_INVALID_ARG, "unknown substep %d", which);
-  int rc = clear_stats(h, h->stats, 1);
+  int rc = clear_stats(h, h->stats + kStatsCap, 1);
   if (rc) return rc;
   // Inside a step the diffusion and projection read the intermediate
   // velocity (ua, va, wa); a standalone substep starts from and ends in the
@@ -524,10 +551,10 @@ int cfd_substep(cfd_handle* h, int which, cfd_solve_stats* stats) {
     return r2;
   };
   if (which == CFD_SUBSTEP_DIFFUSE || which == CFD_SUBSTEP_PROJECT) rc = copy_vel(true);
-  if (!rc) rc = run_substep(h, which, h->stats);
+  if (!rc) rc = run_substep(h, which, h->stats + kStatsCap);
   if (!rc && (which == CFD_SUBSTEP_ADVECT || which == CFD_SUBSTEP_DIFFUSE)) rc = copy_vel(false);
   if (rc) return rc;
-  if (stats) return gather_stats(h, 1, stats);
+  if (stats) return gather_stats(h, h->stats + kStatsCap, 1, stats);
   return CFD_OK;
 }
 
@@ -535,11 +562,11 @@ int cfd_solve_pressure(cfd_handle* h, const double* b_dev, double* x_dev, cfd_so
   if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
   if (!b_dev || !x_dev) return set_err(h, CFD_ERR_INVALID_ARG, "b or x is NULL");
   const size_t n = size_t(h->prm.nx) * h->prm.ny * h->prm.nz;
-  int rc = clear_stats(h, h->stats, 1);
+  int rc = clear_stats(h, h->stats + kStatsCap, 1);
   if (!rc) rc = cuda_check(h, cudaMemcpyAsync(h->b, b_dev, n * 8, cudaMemcpyDeviceToDevice, h->stream), "copy b");
-  if (!rc) rc = run_pressure(h, x_dev, h->prm.warm_start ? 0 : 1, 0, &h->stats->p);
+  if (!rc) rc = run_pressure(h, x_dev, h->prm.warm_start ? 0 : 1, 0, &(h->stats + kStatsCap)->p);
   if (rc) return rc;
-  if (stats) return gather_stats(h, 1, stats);
+  if (stats) return gather_stats(h, h->stats + kStatsCap, 1, stats);
   return CFD_OK;
 }
 
