@@ -191,6 +191,37 @@ int cfd_enable_timing(cfd_handle *h, int on);
  * calls_out (CFD_PHASE_COUNT entries each, nullable), and reset them. */
 int cfd_phase_times(cfd_handle *h, double *ms_out, int64_t *calls_out);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free standalone pressure solve.  The paper has no counterpart:
+ * this entry point exists for callers that may not allocate device memory
+ * at all (code inside host callbacks, plug-ins whose host application owns
+ * every allocation, runtimes that reserve all device memory up front), so
+ * they cannot provide the workspace cfd_create needs.
+ *
+ * Solves the same Neumann system as cfd_solve_pressure with plain FP64 CG
+ * (cold start, mean of b removed, no gauge shift): b_dev and x_dev are
+ * device arrays of nx*ny*nz doubles (x fastest), b is read only, x is
+ * overwritten.  rtol in (0, 1); max_iters = 0 means 20 * max(n).  stats
+ * (nullable) as for cfd_solve_pressure; when given, the call synchronises
+ * the stream.
+ *
+ * Its scratch vectors live in one fixed-size __device__ array inside this
+ * library instead of a workspace, so it never calls an allocator.  Limits:
+ *  - at most CFD_NOALLOC_MAX_CELLS cells (e.g. 64^3); larger grids return
+ *    CFD_ERR_INVALID_ARG with a message from cfd_last_error(NULL);
+ *  - every GPU that loads the library holds that array (about 10.8 MB)
+ *    until the process exits;
+ *  - all calls on a device share the array and it keeps the last call's
+ *    contents, so calls whose GPU work overlaps (other streams, other host
+ *    threads) race: serialise them on one stream;
+ *  - the first call on each device looks up the array's device address
+ *    (with that device current); make that first call before any stream
+ *    capture.
+ * Errors are reported through cfd_last_error(NULL). */
+#define CFD_NOALLOC_MAX_CELLS 262144
+int cfd_poisson_solve_noalloc(int32_t nx, int32_t ny, int32_t nz, const double *b_dev, double *x_dev,
+                              double rtol, int32_t max_iters, cfd_stream_t stream, cfd_solve_stats *stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -88,6 +88,8 @@ def load_library(path: Optional[str] = None):
         "cfd_apply_poisson": (ctypes.c_int, [vp, vp, vp]),
         "cfd_launch_count": (ctypes.c_int64, [vp]),
         "cfd_recent_stats": (ctypes.c_int, [vp, ctypes.c_int, P(cfd_solve_stats)]),
+        "cfd_poisson_solve_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, vp,
+                                                     ctypes.c_double, ctypes.c_int32, vp, P(cfd_solve_stats)]),
         "cfd_enable_timing": (ctypes.c_int, [vp, ctypes.c_int]),
         "cfd_phase_times": (ctypes.c_int, [vp, P(ctypes.c_double), P(ctypes.c_int64)]),
     }

@@ -608,3 +608,19 @@ int cfd_phase_times(cfd_handle* h, double* ms_out, int64_t* calls_out) {
 }
 
 }  // extern "C"
+
+namespace cfd {
+
+int solve_tile_depth(int mz) { return tz_for(mz); }
+
+int cfd_internal_error(int code, const char* fmt, ...) {
+  char buf[256];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  std::memcpy(g_last_error, buf, sizeof(buf));
+  return code;
+}
+
+}  // namespace cfd

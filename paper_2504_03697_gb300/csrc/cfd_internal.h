@@ -109,6 +109,12 @@ cudaError_t launch_fill(double* p, size_t n, double value, cudaStream_t s, int64
 // Co-resident block count for the persistent solve kernels on this device.
 int cg_max_coresident_blocks(int kind_is_ir);
 
+// Stencil tile depth (cells per thread along z) used for a grid of mz planes.
+int solve_tile_depth(int mz);
+
+// Record a printf-style message as cfd_last_error(NULL) and return code.
+int cfd_internal_error(int code, const char* fmt, ...);
+
 constexpr int kTileX = 32;
 constexpr int kTileY = 8;
 constexpr int kSolveThreads = kTileX * kTileY;
