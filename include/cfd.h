@@ -167,6 +167,21 @@ int cfd_apply_poisson(cfd_handle *h, const double *x_dev, double *y_dev);
  * (for launch accounting in benchmarks). */
 int64_t cfd_launch_count(const cfd_handle *h);
 
+/* Launch shape of the persistent CG solves (the knobs the autotuner
+ * searches): blocks per SM (1..the co-resident maximum) and stencil tile
+ * depth (cells per thread along z: 1, 2, 4 or 8).  0 selects the built-in
+ * heuristic, which prefers the register path on small grids (each block
+ * keeps its cells' search direction and operator output in registers
+ * between the two phases of an iteration).  Applies to later solves.
+ * Results are bitwise reproducible for a fixed shape; different shapes sum
+ * the reductions in different orders. */
+int cfd_set_solver_shape(cfd_handle *h, int blocks_per_sm, int tile_depth);
+
+/* The shape the next solve of `kind` (0 pressure, 1..3 diffusion of u, v,
+ * w) would use: grid size, tile depth, and whether the register path is
+ * taken.  Each output pointer may be NULL. */
+int cfd_get_solver_shape(cfd_handle *h, int kind, int *blocks, int *tile_depth, int *register_path);
+
 /* Phase timers, mirroring the call tree of the paper's Table 1
  * (applyForces, solveAdvection, solvePressureCorrection -> pcg,
  * applyPressureCorrection) plus the diffusion substep.  CFD_PHASE_PCG
@@ -209,7 +224,7 @@ int cfd_phase_times(cfd_handle *h, double *ms_out, int64_t *calls_out);
  * library instead of a workspace, so it never calls an allocator.  Limits:
  *  - at most CFD_NOALLOC_MAX_CELLS cells (e.g. 64^3); larger grids return
  *    CFD_ERR_INVALID_ARG with a message from cfd_last_error(NULL);
- *  - every GPU that loads the library holds that array (about 10.8 MB)
+ *  - every GPU that loads the library holds that array (about 11 MB)
  *    until the process exits;
  *  - all calls on a device share the array and it keeps the last call's
  *    contents, so calls whose GPU work overlaps (other streams, other host

@@ -90,6 +90,8 @@ def load_library(path: Optional[str] = None):
         "cfd_recent_stats": (ctypes.c_int, [vp, ctypes.c_int, P(cfd_solve_stats)]),
         "cfd_poisson_solve_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, vp,
                                                      ctypes.c_double, ctypes.c_int32, vp, P(cfd_solve_stats)]),
+        "cfd_set_solver_shape": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
+        "cfd_get_solver_shape": (ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]),
         "cfd_enable_timing": (ctypes.c_int, [vp, ctypes.c_int]),
         "cfd_phase_times": (ctypes.c_int, [vp, P(ctypes.c_double), P(ctypes.c_int64)]),
     }
@@ -238,6 +240,14 @@ class Cavity:
         rc = self.lib.cfd_recent_stats(self.h, int(n), arr)
         self._check(rc, allow=(CFD_ERR_NOT_CONVERGED, CFD_ERR_BREAKDOWN, CFD_ERR_TIMEOUT))
         return rc, [arr[i].as_dict() for i in range(n)]
+
+    def set_solver_shape(self, blocks_per_sm=0, tile_depth=0):
+        return self._check(self.lib.cfd_set_solver_shape(self.h, int(blocks_per_sm), int(tile_depth)))
+
+    def solver_shape(self, kind=0):
+        b, t, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.cfd_get_solver_shape(self.h, int(kind), ctypes.byref(b), ctypes.byref(t), ctypes.byref(r)))
+        return {"blocks": b.value, "tile_depth": t.value, "register_path": bool(r.value)}
 
     def enable_timing(self, on=True):
         return self._check(self.lib.cfd_enable_timing(self.h, 1 if on else 0))

@@ -72,7 +72,7 @@ Layout ws_layout(const cfd_params& p, int max_blocks) {
     L.p1_32 = take(cells * 4);
     L.q32 = take(cells * 4);
   }
-  L.partials = take(size_t(max_blocks) * kMaxPartials * 8);
+  L.partials = take(2 * size_t(max_blocks) * kMaxPartials * 8);  // double-buffered
   L.ctrl = take(sizeof(SolveCtrl));
   L.stats = take(size_t(kStatsCap + 1) * sizeof(DevStepStats));  // ring + one slot for substep/solve calls
   L.total = off;
@@ -189,10 +189,10 @@ PhysArgs phys(const cfd_handle* h) {
 }
 
 int tz_for(int mz) {
-  // cells per thread along z in the stencil tiles
-  if (mz >= 256) return 16;
-  if (mz >= 64) return 8;
-  return 4;
+  // cells per thread along z in the stencil tiles: 0 lets the solver pick
+  // the deepest tile that still spreads over every SM
+  (void)mz;
+  return 0;
 }
 
 // Velocity diffusion solve for component comp (x = intermediate velocity).
@@ -578,6 +578,26 @@ int cfd_apply_poisson(cfd_handle* h, const double* x_dev, double* y_dev) {
 }
 
 int64_t cfd_launch_count(const cfd_handle* h) { return h ? h->launches : 0; }
+
+int cfd_set_solver_shape(cfd_handle* h, int blocks_per_sm, int tile_depth) {
+  if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
+  if (blocks_per_sm < 0 || blocks_per_sm > 32 || tile_depth < 0 || tile_depth > 64)
+    return set_err(h, CFD_ERR_INVALID_ARG, "blocks_per_sm in [0, 32] and tile_depth in [0, 64]");
+  h->lg.bps_req = blocks_per_sm;
+  h->lg.tz_req = tile_depth;
+  return CFD_OK;
+}
+
+int cfd_get_solver_shape(cfd_handle* h, int kind, int* blocks, int* tile_depth, int* register_path) {
+  if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
+  if (kind < 0 || kind > 3) return set_err(h, CFD_ERR_INVALID_ARG, "kind must be 0 (pressure) or 1..3 (u, v, w)");
+  GridDims g{h->prm.nx + (kind == 1), h->prm.ny + (kind == 2), h->prm.nz + (kind == 3)};
+  const SolveShape s = pick_solve_shape(g, h->lg.blocks, h->lg.bps_req, h->lg.tz_req);
+  if (blocks) *blocks = s.blocks;
+  if (tile_depth) *tile_depth = s.tz;
+  if (register_path) *register_path = s.rtz > 0;
+  return CFD_OK;
+}
 
 int cfd_enable_timing(cfd_handle* h, int on) {
   if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");

@@ -11,14 +11,12 @@ namespace cfd {
 
 constexpr int kMaxPartials = 8;  // scalars one grid reduction can carry
 
-// Control block of one persistent solve: grid-barrier counters and the
-// reduced scalars published by the last block to arrive.
+// Control block of one persistent solve (zeroed by the host before each
+// launch): the grid all-reduce counter and the error flag.
 struct __align__(64) SolveCtrl {
-  unsigned int arrive;
-  unsigned int gen;
+  unsigned int arrive;  // monotonic arrival counter of the grid all-reduce
   int error;            // CFD_ERR_* of a device-side failure, 0 if none
-  int pad0;
-  double red[kMaxPartials];
+  int pad[14];
 };
 
 // Per-solve statistics written by the device (mirrors cfd_solve_stats).
@@ -95,72 +93,83 @@ __device__ __forceinline__ void block_reduce(double (&v)[NV], double* scratch) {
   __syncthreads();
 }
 
+__device__ __forceinline__ void red_add_release_gpu(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // ---------------------------------------------------------------------------
-// Grid-wide reduction + barrier for a cooperatively launched (all blocks
-// co-resident) persistent kernel.
+// Grid-wide all-reduce + barrier for a cooperatively launched persistent
+// kernel (all blocks co-resident).
 //
-// Every block contributes NV partial sums; the last block to arrive sums the
-// per-block partials in block order (deterministic, independent of arrival
-// order), publishes the totals in ctrl->red and releases the others.  Every
-// wait is bounded: after `timeout_ns` a waiter records CFD_ERR_TIMEOUT in
-// ctrl->error and all blocks return false; they also return false as soon as
-// any block has recorded an error.  On success the totals are in out[].
+// Each block publishes NV partial sums in a double-buffered array (buffer
+// round & 1) and arrives on a monotonically increasing counter with a
+// release reduction.  Once the counter reaches (round + 1) * gridDim.x,
+// every block sums all block partials itself, in block order with the same
+// thread/tree shape, so every block obtains bitwise the same totals and the
+// result does not depend on arrival order.  Double buffering is enough: a
+// block can only overwrite buffer (round & 1) again after the next round's
+// barrier, which every block reaches only after finishing this round's sum.
+//
+// Memory ordering: partial stores, then red.release on the counter; the
+// waiting thread 0 acquires the counter; bar.sync carries that to the other
+// threads, which read the partials through L2 (ld.global.cg).
+//
+// Every wait is bounded: after timeout_ns the waiter records
+// CFD_ERR_TIMEOUT in ctrl->error and returns false; any block that sees a
+// recorded error also returns false.  `round` is the caller's per-block
+// count of completed all-reduces (identical in every block).
 // ---------------------------------------------------------------------------
 template <int NV>
 __device__ bool grid_allreduce(double (&v)[NV], double (&out)[NV], SolveCtrl* ctrl, double* partials,
-                               double* scratch, unsigned long long timeout_ns) {
-  __shared__ int s_flag;
-  __shared__ unsigned int s_gen;
+                               double* scratch, unsigned long long timeout_ns, unsigned int& round) {
+  __shared__ int s_ok;
+  __shared__ double s_bcast[kMaxPartials];
   block_reduce<NV>(v, scratch);
+  double* buf = partials + size_t(round & 1u) * gridDim.x * kMaxPartials;
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int a = 0; a < NV; ++a) partials[size_t(blockIdx.x) * kMaxPartials + a] = v[a];
-    s_gen = ld_volatile_u32(&ctrl->gen);
-    __threadfence();
-    unsigned int ticket = atomicAdd(&ctrl->arrive, 1u);
-    s_flag = (ticket == gridDim.x - 1) ? 1 : 0;
-  }
-  __syncthreads();
-  if (s_flag) {
-    // last block: fixed-order sum of all block partials
-    __threadfence();
-    double acc[NV];
-#pragma unroll
-    for (int a = 0; a < NV; ++a) acc[a] = 0.0;
-    for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
-#pragma unroll
-      for (int a = 0; a < NV; ++a) acc[a] += __ldcg(&partials[size_t(b) * kMaxPartials + a]);
-    }
-    block_reduce<NV>(acc, scratch);
-    if (threadIdx.x == 0) {
-#pragma unroll
-      for (int a = 0; a < NV; ++a) ctrl->red[a] = acc[a];
-      ctrl->arrive = 0u;
-      __threadfence();
-      atomicAdd(&ctrl->gen, 1u);
-    }
-  } else if (threadIdx.x == 0) {
+    for (int a = 0; a < NV; ++a) buf[size_t(blockIdx.x) * kMaxPartials + a] = v[a];
+    red_add_release_gpu(&ctrl->arrive, 1u);
+    const unsigned int target = (round + 1u) * gridDim.x;
     const unsigned long long t0 = global_ns();
     int ok = 1;
-    unsigned int ns = 32;
-    while (ld_volatile_u32(&ctrl->gen) == s_gen) {
-      if (ld_volatile_s32(&ctrl->error) != 0) { ok = 0; break; }
-      if (global_ns() - t0 > timeout_ns) {
-        atomicCAS(&ctrl->error, 0, kErrTimeout);
-        ok = 0;
-        break;
+    unsigned int polls = 0;
+    while (int(ld_acquire_gpu(&ctrl->arrive) - target) < 0) {
+      if ((++polls & 63u) == 0) {
+        if (ld_volatile_s32(&ctrl->error) != 0) { ok = 0; break; }
+        if (global_ns() - t0 > timeout_ns) {
+          atomicCAS(&ctrl->error, 0, kErrTimeout);
+          ok = 0;
+          break;
+        }
       }
-      __nanosleep(ns);
-      if (ns < 256) ns <<= 1;
     }
-    s_flag = ok ? 2 : 3;
+    s_ok = ok;
+  }
+  ++round;
+  __syncthreads();
+  if (!s_ok) return false;
+  double acc[NV];
+#pragma unroll
+  for (int a = 0; a < NV; ++a) acc[a] = 0.0;
+  for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) acc[a] += __ldcg(&buf[size_t(b) * kMaxPartials + a]);
+  }
+  block_reduce<NV>(acc, scratch);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) s_bcast[a] = acc[a];
   }
   __syncthreads();
-  if (s_flag == 3) return false;
-  __threadfence();
 #pragma unroll
-  for (int a = 0; a < NV; ++a) out[a] = __ldcg(&ctrl->red[a]);
-  __syncthreads();  // s_flag is rewritten by the next call
+  for (int a = 0; a < NV; ++a) out[a] = s_bcast[a];
   return true;
 }
 

@@ -25,10 +25,21 @@ struct GridDims {
 
 // Geometry of one persistent solve launch.
 struct LaunchGeom {
-  int blocks;       // co-resident blocks of the cooperative launch
-  int tz;           // cells per thread along z in the stencil tiles
+  int blocks;       // maximum co-resident blocks of the cooperative launch
+  int tz;           // unused (kept for layout compatibility)
   int num_sms;
+  int bps_req;      // requested blocks per SM (0: automatic)
+  int tz_req;       // requested tile depth (0: automatic)
 };
+
+// Launch shape picked for one solve.
+struct SolveShape {
+  int blocks;       // grid size
+  int tz;           // tile depth (cells per thread along z)
+  int rtz;          // > 0: register path with this depth; 0: memory path
+};
+
+SolveShape pick_solve_shape(GridDims g, int max_blocks, int bps_req, int tz_req);
 
 // Arguments of the persistent FP64 CG solve.
 struct CgArgs {
@@ -51,7 +62,7 @@ struct CgArgs {
   int max_restarts;
   unsigned long long timeout_ns;
   SolveCtrl* ctrl;       // zeroed by the host before the launch
-  double* partials;      // blocks * kMaxPartials doubles
+  double* partials;      // 2 * blocks * kMaxPartials doubles (double-buffered)
   DevSolveStats* stats;  // written by block 0 at exit
   int tz;
 };

@@ -12,7 +12,7 @@
 // Limits and sharing rules (also stated in include/cfd.h):
 //  * at most CFD_NOALLOC_MAX_CELLS cells; larger grids are rejected with
 //    CFD_ERR_INVALID_ARG;
-//  * every GPU that loads this library holds the array (about 10.8 MB) until
+//  * every GPU that loads this library holds the array (about 11 MB) until
 //    the process exits;
 //  * all calls share the one array per device, so calls whose GPU work
 //    overlaps (different streams, or different host threads on one device)
@@ -39,7 +39,7 @@ constexpr size_t kOffD0 = kOffR + kVecBytes;
 constexpr size_t kOffD1 = kOffD0 + kVecBytes;
 constexpr size_t kOffQ = kOffD1 + kVecBytes;
 constexpr size_t kOffPartials = kOffQ + kVecBytes;
-constexpr size_t kOffCtrl = kOffPartials + size_t(kNoallocMaxBlocks) * kMaxPartials * sizeof(double);
+constexpr size_t kOffCtrl = kOffPartials + 2 * size_t(kNoallocMaxBlocks) * kMaxPartials * sizeof(double);
 constexpr size_t kOffStats = kOffCtrl + 256;
 constexpr size_t kNoallocBytes = kOffStats + 256;
 

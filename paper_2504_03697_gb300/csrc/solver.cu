@@ -20,14 +20,18 @@
 // GB300, whose FP64 pipe is far slower than its HBM.
 //
 // CG layout.  One persistent, cooperatively launched kernel runs the whole
-// solve with two grid-wide reductions per iteration:
+// solve with two grid-wide all-reduces per iteration:
 //   phase D (tiled stencil): p_new = z + beta p_old on a shared-memory tile
-//     with halo (z = r, or r / diag for Jacobi), write p_new, q = A p_new,
+//     with halo (z = r, or r / diag for Jacobi), store p_new, q = A p_new,
 //     partial p.q;
-//   phase U (flat):  x += alpha p_new, r -= alpha q, partial r.r (and r.z).
-// The x/y halo lives in shared memory; each thread marches along z keeping
-// the z-1 / z / z+1 values in registers.  Reductions are deterministic (see
-// cfd_common.cuh), so a solve is bitwise reproducible run to run.
+//   phase U:  x += alpha p_new, r -= alpha q, partial r.r (and r.z).
+// Tiles are kTileX x kTileY x tz cells; tile t belongs to block t mod grid.
+// When every block owns at most kRegCells / tz tiles ("register path", the
+// small grids where the solve is latency-bound), the block keeps p_new and q
+// of its own cells in registers from phase D to phase U: q is never stored
+// and phase U touches only x and r.  Otherwise q goes through memory and
+// phase U is a flat pass.  Reductions are deterministic (cfd_common.cuh), so
+// a solve is bitwise reproducible run to run for a given launch shape.
 
 #include <cmath>
 
@@ -43,6 +47,9 @@ constexpr int kModeDir = 2;    // p_new = z + beta p_old; q = A p_new; partial p
 
 constexpr int kTileW = kTileX + 2;
 constexpr int kTileH = kTileY + 2;
+constexpr int kMaxTz = 8;     // deepest tile (cells per thread along z)
+constexpr int kTileSlots = kTileW * kTileH * (kMaxTz + 2);
+constexpr int kRegCells = 8;  // own cells per thread kept in registers (register path)
 
 template <typename T>
 __device__ __forceinline__ T stencil_row(int kind, T c, int i, int j, int k, int mx, int my, int mz, T xc,
@@ -106,10 +113,10 @@ struct Source {
 struct TileShape {
   int mx, my, mz, tz;
   int ntx, nty, ntz;
-  __device__ __forceinline__ int count() const { return ntx * nty * ntz; }
+  __host__ __device__ __forceinline__ int count() const { return ntx * nty * ntz; }
 };
 
-__device__ __forceinline__ TileShape make_tiles(int mx, int my, int mz, int tz) {
+__host__ __device__ __forceinline__ TileShape make_tiles(int mx, int my, int mz, int tz) {
   TileShape t;
   t.mx = mx; t.my = my; t.mz = mz; t.tz = tz;
   t.ntx = (mx + kTileX - 1) / kTileX;
@@ -121,7 +128,7 @@ __device__ __forceinline__ TileShape make_tiles(int mx, int my, int mz, int tz) 
 // Outputs / accumulators of one stencil pass.
 template <typename T>
 struct Sink {
-  T* y;          // apply: y; resid: r; dir: q
+  T* y;          // apply: y; resid: r; dir: q (nullptr on the register path)
   T* pnew;       // dir
   T* b;          // resid: right-hand side (read, optionally rewritten)
   T bshift;      // resid: subtracted from b
@@ -130,63 +137,153 @@ struct Sink {
   T c;
 };
 
-// Tiled 7-point pass over all tiles owned by this block (tile t -> block
-// t mod gridDim.x).  acc[0..2] receive the partial sums of the mode.
+// Evaluate tile t and its one-cell halo (edges and corners excluded: the
+// 7-point stencil never reads them) into shared memory, all loads in flight
+// at once.  Ends with a block barrier.
+template <typename T, int MODE, int PRECOND>
+__device__ __forceinline__ void load_tile(const TileShape& ts, int t, const Source<T, MODE, PRECOND>& src, T* s,
+                                          int& x0, int& y0, int& z0) {
+  const int bx = t % ts.ntx;
+  const int rest = t / ts.ntx;
+  const int by = rest % ts.nty;
+  const int bz = rest / ts.nty;
+  x0 = bx * kTileX;
+  y0 = by * kTileY;
+  z0 = bz * ts.tz;
+  const int D = ts.tz + 2;
+  const int slots = kTileW * kTileH * D;
+  for (int l = threadIdx.x; l < slots; l += kSolveThreads) {
+    const int lx = l % kTileW;
+    const int r2 = l / kTileW;
+    const int ly = r2 % kTileH;
+    const int lz = r2 / kTileH;
+    const int gi = x0 + lx - 1, gj = y0 + ly - 1, gk = z0 + lz - 1;
+    const int halo = (lx == 0 || lx == kTileW - 1) + (ly == 0 || ly == kTileH - 1) + (lz == 0 || lz == D - 1);
+    T v = T(0);
+    if (halo <= 1 && gi >= 0 && gi < ts.mx && gj >= 0 && gj < ts.my && gk >= 0 && gk < ts.mz)
+      v = src(idx3(gi, gj, gk, ts.mx, ts.my), gi, gj, gk);
+    s[l] = v;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ int tile_cell(int kz, int tx, int ty) {
+  return ((kz + 1) * kTileH + (ty + 1)) * kTileW + (tx + 1);
+}
+
+template <typename T>
+__device__ __forceinline__ T row_from_smem(const Sink<T>& out, const T* s, int c, int i, int j, int k, int mx, int my,
+                                           int mz) {
+  return stencil_row<T>(out.kind, out.c, i, j, k, mx, my, mz, s[c], s[c - 1], s[c + 1], s[c - kTileW], s[c + kTileW],
+                        s[c - kTileW * kTileH], s[c + kTileW * kTileH]);
+}
+
+// Memory-path stencil pass over all tiles of this block.  Partial sums
+// accumulate per thread in T (FP64 solves: double; the FP32 inner solve:
+// float, a handful of terms per thread) and are reduced across threads and
+// blocks in FP64 by the caller.  Resid mode: acc = {b.b, r.r, r.z (Jacobi)
+// or sum(r) (no preconditioner)}.
 template <typename T, int MODE, int PRECOND>
 __device__ void stencil_tiles(const TileShape& ts, const Source<T, MODE, PRECOND>& src, const Sink<T>& out,
-                              double (&acc)[3], T* s) {
+                              T (&acc)[3], T* s) {
   const int tx = threadIdx.x % kTileX, ty = threadIdx.x / kTileX;
   const int mx = ts.mx, my = ts.my, mz = ts.mz;
   const int ntiles = ts.count();
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int bx = t % ts.ntx;
-    const int rest = t / ts.ntx;
-    const int by = rest % ts.nty;
-    const int bz = rest / ts.nty;
-    const int i = bx * kTileX + tx, j = by * kTileY + ty;
-    const int z0 = bz * ts.tz, z1 = min(z0 + ts.tz, mz);
-    const bool inx = i < mx, iny = j < my, own = inx && iny;
-    T pm = T(0), pc = T(0), pn = T(0);
-    if (own) {
-      pc = src(idx3(i, j, z0, mx, my), i, j, z0);
-      if (z0 > 0) pm = src(idx3(i, j, z0 - 1, mx, my), i, j, z0 - 1);
-    }
-    for (int k = z0; k < z1; ++k) {
-      pn = (own && k + 1 < mz) ? src(idx3(i, j, k + 1, mx, my), i, j, k + 1) : T(0);
-      if (ty == 0) s[tx + 1] = (inx && j > 0) ? src(idx3(i, j - 1, k, mx, my), i, j - 1, k) : T(0);
-      if (ty == kTileY - 1)
-        s[(kTileY + 1) * kTileW + tx + 1] = (inx && j + 1 < my) ? src(idx3(i, j + 1, k, mx, my), i, j + 1, k) : T(0);
-      if (tx == 0) s[(ty + 1) * kTileW] = (iny && i > 0) ? src(idx3(i - 1, j, k, mx, my), i - 1, j, k) : T(0);
-      if (tx == kTileX - 1)
-        s[(ty + 1) * kTileW + kTileX + 1] = (iny && i + 1 < mx) ? src(idx3(i + 1, j, k, mx, my), i + 1, j, k) : T(0);
-      s[(ty + 1) * kTileW + tx + 1] = pc;
-      __syncthreads();
-      if (own) {
-        const T xm = s[(ty + 1) * kTileW + tx];
-        const T xp = s[(ty + 1) * kTileW + tx + 2];
-        const T ym = s[ty * kTileW + tx + 1];
-        const T yp = s[(ty + 2) * kTileW + tx + 1];
-        const T y = stencil_row<T>(out.kind, out.c, i, j, k, mx, my, mz, pc, xm, xp, ym, yp, pm, pn);
+    int x0, y0, z0;
+    load_tile<T, MODE, PRECOND>(ts, t, src, s, x0, y0, z0);
+    const int i = x0 + tx, j = y0 + ty;
+    if (i < mx && j < my) {
+      const int z1 = min(z0 + ts.tz, mz);
+      for (int k = z0; k < z1; ++k) {
+        const int c = tile_cell(k - z0, tx, ty);
+        const T pc = s[c];
+        const T y = row_from_smem<T>(out, s, c, i, j, k, mx, my, mz);
         const size_t e = idx3(i, j, k, mx, my);
         if (MODE == kModeApply) {
           out.y[e] = y;
         } else if (MODE == kModeDir) {
           out.pnew[e] = pc;
           out.y[e] = y;
-          acc[0] = fma(double(pc), double(y), acc[0]);
+          acc[0] = fma(pc, y, acc[0]);
         } else {  // resid
           T bv = out.b[e] - out.bshift;
           if (out.write_b) out.b[e] = bv;
           const T r = bv - y;
           out.y[e] = r;
-          acc[0] = fma(double(bv), double(bv), acc[0]);
-          acc[1] = fma(double(r), double(r), acc[1]);
-          if (PRECOND) acc[2] = fma(double(r) * double(r), double(src.invd[neighbour_count(i, j, k, mx, my, mz)]), acc[2]);
+          acc[0] = fma(bv, bv, acc[0]);
+          acc[1] = fma(r, r, acc[1]);
+          if (PRECOND) acc[2] = fma(r * r, src.invd[neighbour_count(i, j, k, mx, my, mz)], acc[2]);
+          else acc[2] += r;
         }
       }
-      __syncthreads();
-      pm = pc;
-      pc = pn;
+    }
+    __syncthreads();
+  }
+}
+
+// Register-path phase D: tiles of compile-time depth RTZ, at most
+// kRegCells / RTZ per block; p_new is stored (neighbours need it next
+// iteration), p_new and q of own cells stay in preg / qreg.
+template <int RTZ, int PRECOND>
+__device__ void dir_tiles_reg(const TileShape& ts, const Source<double, kModeDir, PRECOND>& src, double* pnew,
+                              const Sink<double>& out, double (&acc)[3], double* s, double (&preg)[kRegCells],
+                              double (&qreg)[kRegCells]) {
+  const int tx = threadIdx.x % kTileX, ty = threadIdx.x / kTileX;
+  const int mx = ts.mx, my = ts.my, mz = ts.mz;
+  const int ntiles = ts.count();
+#pragma unroll
+  for (int kt = 0; kt < kRegCells / RTZ; ++kt) {
+    const int t = blockIdx.x + kt * gridDim.x;
+    if (t >= ntiles) break;
+    int x0, y0, z0;
+    load_tile<double, kModeDir, PRECOND>(ts, t, src, s, x0, y0, z0);
+    const int i = x0 + tx, j = y0 + ty;
+#pragma unroll
+    for (int kz = 0; kz < RTZ; ++kz) {
+      const int k = z0 + kz;
+      double pc = 0.0, y = 0.0;
+      if (i < mx && j < my && k < mz) {
+        const int c = tile_cell(kz, tx, ty);
+        pc = s[c];
+        y = row_from_smem<double>(out, s, c, i, j, k, mx, my, mz);
+        pnew[idx3(i, j, k, mx, my)] = pc;
+        acc[0] = fma(pc, y, acc[0]);
+      }
+      preg[kt * RTZ + kz] = pc;
+      qreg[kt * RTZ + kz] = y;
+    }
+    __syncthreads();
+  }
+}
+
+// Register-path phase U over the same own cells.
+template <int RTZ, int PRECOND>
+__device__ void update_reg(const TileShape& ts, double alpha, double* x, double* r, const double* invd,
+                           double (&acc)[3], const double (&preg)[kRegCells], const double (&qreg)[kRegCells]) {
+  const int tx = threadIdx.x % kTileX, ty = threadIdx.x / kTileX;
+  const int mx = ts.mx, my = ts.my, mz = ts.mz;
+  const int ntiles = ts.count();
+#pragma unroll
+  for (int kt = 0; kt < kRegCells / RTZ; ++kt) {
+    const int t = blockIdx.x + kt * gridDim.x;
+    if (t >= ntiles) break;
+    const int bx = t % ts.ntx;
+    const int rest = t / ts.ntx;
+    const int by = rest % ts.nty;
+    const int bz = rest / ts.nty;
+    const int i = bx * kTileX + tx, j = by * kTileY + ty, z0 = bz * RTZ;
+    if (i >= mx || j >= my) continue;
+#pragma unroll
+    for (int kz = 0; kz < RTZ; ++kz) {
+      const int k = z0 + kz;
+      if (k >= mz) break;
+      const size_t e = idx3(i, j, k, mx, my);
+      x[e] = fma(alpha, preg[kt * RTZ + kz], x[e]);
+      const double re = fma(-alpha, qreg[kt * RTZ + kz], r[e]);
+      r[e] = re;
+      acc[0] = fma(re, re, acc[0]);
+      if (PRECOND) acc[1] = fma(re * re, invd[neighbour_count(i, j, k, mx, my, mz)], acc[1]);
     }
   }
 }
@@ -195,11 +292,12 @@ __device__ __forceinline__ size_t gtid() { return size_t(blockIdx.x) * blockDim.
 __device__ __forceinline__ size_t gstride() { return size_t(gridDim.x) * blockDim.x; }
 
 // ---------------------------------------------------------------------------
-// Persistent FP64 (P)CG.  PRECOND: 0 none, 1 Jacobi.
+// Persistent FP64 (P)CG.  PRECOND: 0 none, 1 Jacobi.  RTZ: 0 memory path
+// (runtime tile depth a.tz), else register path with tile depth RTZ.
 // ---------------------------------------------------------------------------
-template <int PRECOND>
+template <int PRECOND, int RTZ>
 __global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(CgArgs a) {
-  __shared__ double s_tile[kTileH * kTileW];
+  __shared__ double s_tile[kTileSlots];
   __shared__ double s_red[32 * 3];
   __shared__ double s_invd[8];
   if (threadIdx.x < 8) s_invd[threadIdx.x] = threadIdx.x == 0 ? 0.0 : 1.0 / double(threadIdx.x);
@@ -207,9 +305,10 @@ __global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(CgArgs a) {
 
   const int mx = a.g.mx, my = a.g.my, mz = a.g.mz;
   const size_t n = size_t(mx) * my * mz;
-  const TileShape ts = make_tiles(mx, my, mz, a.tz);
+  const TileShape ts = make_tiles(mx, my, mz, RTZ > 0 ? RTZ : a.tz);
   const double c = a.c;
   DevSolveStats* st = a.stats;
+  unsigned int round = 0;
 
   auto fail = [&]() {
     if (threadIdx.x == 0) {
@@ -217,15 +316,19 @@ __global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(CgArgs a) {
       st->status = e != 0 ? e : kErrTimeout;
     }
   };
+  auto allreduce = [&](double (&v)[3], double (&o)[3]) {
+    return grid_allreduce<3>(v, o, a.ctrl, a.partials, s_red, a.timeout_ns, round);
+  };
 
   double acc[3], tot[3];
+  double preg[kRegCells], qreg[kRegCells];
 
   // ---- mean of b (pressure systems are only solvable for zero-mean b) ----
   double shift = 0.0;
   if (a.remove_mean) {
     acc[0] = acc[1] = acc[2] = 0.0;
     for (size_t e = gtid(); e < n; e += gstride()) acc[0] += a.b[e];
-    if (!grid_allreduce<3>(acc, tot, a.ctrl, a.partials, s_red, a.timeout_ns)) return fail();
+    if (!allreduce(acc, tot)) return fail();
     shift = tot[0] / double(n);
   }
 
@@ -249,7 +352,7 @@ __global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(CgArgs a) {
     Sink<double> out{a.r, nullptr, a.b, shift, a.remove_mean != 0, a.kind, c};
     stencil_tiles<double, kModeResid, PRECOND>(ts, src, out, acc, s_tile);
   }
-  if (!grid_allreduce<3>(acc, tot, a.ctrl, a.partials, s_red, a.timeout_ns)) return fail();
+  if (!allreduce(acc, tot)) return fail();
   const double bb = tot[0];
   double rr = tot[1];
   double rz = PRECOND ? tot[2] : tot[1];
@@ -272,7 +375,7 @@ __global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(CgArgs a) {
         Source<double, kModeResid, PRECOND> src{a.x, nullptr, 0.0, false, s_invd, mx, my, mz};
         Sink<double> out{a.r, nullptr, a.b, 0.0, false, a.kind, c};
         stencil_tiles<double, kModeResid, PRECOND>(ts, src, out, acc, s_tile);
-        if (!grid_allreduce<3>(acc, tot, a.ctrl, a.partials, s_red, a.timeout_ns)) return fail();
+        if (!allreduce(acc, tot)) return fail();
         rr_true = tot[1];
         if (rr_true <= tol2) {
           status = kOk;
@@ -291,10 +394,15 @@ __global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(CgArgs a) {
       acc[0] = acc[1] = acc[2] = 0.0;
       {
         Source<double, kModeDir, PRECOND> src{a.r, pold, beta, first, s_invd, mx, my, mz};
-        Sink<double> out{a.q, pnew, nullptr, 0.0, false, a.kind, c};
-        stencil_tiles<double, kModeDir, PRECOND>(ts, src, out, acc, s_tile);
+        if (RTZ > 0) {
+          Sink<double> out{nullptr, pnew, nullptr, 0.0, false, a.kind, c};
+          dir_tiles_reg<(RTZ > 0 ? RTZ : 1), PRECOND>(ts, src, pnew, out, acc, s_tile, preg, qreg);
+        } else {
+          Sink<double> out{a.q, pnew, nullptr, 0.0, false, a.kind, c};
+          stencil_tiles<double, kModeDir, PRECOND>(ts, src, out, acc, s_tile);
+        }
       }
-      if (!grid_allreduce<3>(acc, tot, a.ctrl, a.partials, s_red, a.timeout_ns)) return fail();
+      if (!allreduce(acc, tot)) return fail();
       const double pq = tot[0];
       if (!(pq > 0.0) || !isfinite(pq) || !isfinite(rz)) {
         status = kErrBreakdown;
@@ -303,19 +411,23 @@ __global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(CgArgs a) {
       const double alpha = rz / pq;
       // phase U: x += alpha p, r -= alpha q, partial r.r (and r.z)
       acc[0] = acc[1] = acc[2] = 0.0;
-      for (size_t e = gtid(); e < n; e += gstride()) {
-        const double pe = pnew[e];
-        const double qe = a.q[e];
-        a.x[e] = fma(alpha, pe, a.x[e]);
-        const double re = fma(-alpha, qe, a.r[e]);
-        a.r[e] = re;
-        acc[0] = fma(re, re, acc[0]);
-        if (PRECOND) {
-          const int i = int(e % mx), j = int((e / mx) % my), k = int(e / (size_t(mx) * my));
-          acc[1] = fma(re * re, s_invd[neighbour_count(i, j, k, mx, my, mz)], acc[1]);
+      if (RTZ > 0) {
+        update_reg<(RTZ > 0 ? RTZ : 1), PRECOND>(ts, alpha, a.x, a.r, s_invd, acc, preg, qreg);
+      } else {
+        for (size_t e = gtid(); e < n; e += gstride()) {
+          const double pe = pnew[e];
+          const double qe = a.q[e];
+          a.x[e] = fma(alpha, pe, a.x[e]);
+          const double re = fma(-alpha, qe, a.r[e]);
+          a.r[e] = re;
+          acc[0] = fma(re, re, acc[0]);
+          if (PRECOND) {
+            const int i = int(e % mx), j = int((e / mx) % my), k = int(e / (size_t(mx) * my));
+            acc[1] = fma(re * re, s_invd[neighbour_count(i, j, k, mx, my, mz)], acc[1]);
+          }
         }
       }
-      if (!grid_allreduce<3>(acc, tot, a.ctrl, a.partials, s_red, a.timeout_ns)) return fail();
+      if (!allreduce(acc, tot)) return fail();
       rr = tot[0];
       const double rz_new = PRECOND ? tot[1] : tot[0];
       beta = rz_new / rz;
@@ -330,7 +442,7 @@ __global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(CgArgs a) {
       Source<double, kModeResid, PRECOND> src{a.x, nullptr, 0.0, false, s_invd, mx, my, mz};
       Sink<double> out{a.r, nullptr, a.b, 0.0, false, a.kind, c};
       stencil_tiles<double, kModeResid, PRECOND>(ts, src, out, acc, s_tile);
-      if (!grid_allreduce<3>(acc, tot, a.ctrl, a.partials, s_red, a.timeout_ns)) return fail();
+      if (!allreduce(acc, tot)) return fail();
       rr_true = tot[1];
     }
   }
@@ -339,7 +451,7 @@ __global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(CgArgs a) {
   if (a.gauge) {
     acc[0] = acc[1] = acc[2] = 0.0;
     for (size_t e = gtid(); e < n; e += gstride()) acc[0] += a.x[e];
-    if (!grid_allreduce<3>(acc, tot, a.ctrl, a.partials, s_red, a.timeout_ns)) return fail();
+    if (!allreduce(acc, tot)) return fail();
     const double sh = a.gauge_value - tot[0] / double(n);
     for (size_t e = gtid(); e < n; e += gstride()) a.x[e] += sh;
   }
@@ -356,7 +468,7 @@ __global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(CgArgs a) {
 
 // One-shot y = A x (non-persistent; one block per tile).
 __global__ void __launch_bounds__(kSolveThreads) apply_poisson_kernel(GridDims g, const double* x, double* y, int tz) {
-  __shared__ double s_tile[kTileH * kTileW];
+  __shared__ double s_tile[kTileSlots];
   const TileShape ts = make_tiles(g.mx, g.my, g.mz, tz);
   double acc[3] = {0.0, 0.0, 0.0};
   Source<double, kModeApply, 0> src{x, nullptr, 0.0, false, nullptr, g.mx, g.my, g.mz};
@@ -364,30 +476,319 @@ __global__ void __launch_bounds__(kSolveThreads) apply_poisson_kernel(GridDims g
   stencil_tiles<double, kModeApply, 0>(ts, src, out, acc, s_tile);
 }
 
-int tiles_of(GridDims g, int tz) {
-  return ((g.mx + kTileX - 1) / kTileX) * ((g.my + kTileY - 1) / kTileY) * ((g.mz + tz - 1) / tz);
+// ---------------------------------------------------------------------------
+// Mixed-precision iterative refinement (persistent; pressure operator).
+//
+// Outer loop in FP64: r = b - A x (true residual, FP64 stencil), stop when
+// ||r|| <= rtol ||b||.  Inner solve in FP32: CG on A d = (r - mean(r)) /
+// ||r|| from d = 0 until its recurrence residual falls by inner_rtol (or the
+// iteration budget ends), every vector and the stencil in FP32; per-thread
+// partial sums in FP32, their cross-thread / cross-block reduction and the
+// CG scalars (alpha, beta) in FP64.  Then x += ||r|| d in FP64.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSolveThreads) ir_kernel(IrArgs a) {
+  __shared__ double s_raw[kTileSlots];
+  __shared__ double s_red[32 * 3];
+  double* s64 = s_raw;
+  float* s32 = reinterpret_cast<float*>(s_raw);
+
+  const int mx = a.g.mx, my = a.g.my, mz = a.g.mz;
+  const size_t n = size_t(mx) * my * mz;
+  const TileShape ts = make_tiles(mx, my, mz, a.tz);
+  DevSolveStats* st = a.stats;
+  unsigned int round = 0;
+
+  auto fail = [&]() {
+    if (threadIdx.x == 0) {
+      int e = ld_volatile_s32(&a.ctrl->error);
+      st->status = e != 0 ? e : kErrTimeout;
+    }
+  };
+  auto allreduce = [&](double (&v)[3], double (&o)[3]) {
+    return grid_allreduce<3>(v, o, a.ctrl, a.partials, s_red, a.timeout_ns, round);
+  };
+
+  double acc[3], tot[3];
+
+  double shift = 0.0;
+  if (a.remove_mean) {
+    acc[0] = acc[1] = acc[2] = 0.0;
+    for (size_t e = gtid(); e < n; e += gstride()) acc[0] += a.b[e];
+    if (!allreduce(acc, tot)) return fail();
+    shift = tot[0] / double(n);
+  }
+
+  // r = b - A x0, partials b.b, r.r, sum(r)
+  acc[0] = acc[1] = acc[2] = 0.0;
+  if (a.zero_x0) {
+    for (size_t e = gtid(); e < n; e += gstride()) {
+      const double bv = a.b[e] - shift;
+      if (a.remove_mean) a.b[e] = bv;
+      a.x[e] = 0.0;
+      a.r[e] = bv;
+      acc[0] = fma(bv, bv, acc[0]);
+      acc[2] += bv;
+    }
+    acc[1] = acc[0];
+  } else {
+    Source<double, kModeResid, 0> src{a.x, nullptr, 0.0, false, nullptr, mx, my, mz};
+    Sink<double> out{a.r, nullptr, a.b, shift, a.remove_mean != 0, kOpPressure, 0.0};
+    stencil_tiles<double, kModeResid, 0>(ts, src, out, acc, s64);
+  }
+  if (!allreduce(acc, tot)) return fail();
+  const double bb = tot[0];
+  double rr = tot[1], rsum = tot[2];
+
+  int status = kErrNotConverged, outer = 0, inner_total = 0;
+  if (bb == 0.0) {
+    for (size_t e = gtid(); e < n; e += gstride()) a.x[e] = 0.0;
+    status = kOk;
+    rr = 0.0;
+  } else {
+    const double tol2 = a.rtol * a.rtol * bb;
+    while (true) {
+      if (rr <= tol2) {
+        status = kOk;
+        break;
+      }
+      if (outer >= a.max_outer || inner_total >= a.max_iters) break;
+      // inner right-hand side: (r - mean r) / ||r|| in FP32, d = 0
+      const double rnorm = sqrt(rr);
+      const double scale = 1.0 / rnorm;
+      const double rmean = rsum / double(n);
+      float f32[3] = {0.f, 0.f, 0.f};
+      for (size_t e = gtid(); e < n; e += gstride()) {
+        const float v = float((a.r[e] - rmean) * scale);
+        a.r32[e] = v;
+        a.d32[e] = 0.f;
+        f32[0] = fmaf(v, v, f32[0]);
+      }
+      acc[0] = f32[0];
+      acc[1] = acc[2] = 0.0;
+      if (!allreduce(acc, tot)) return fail();
+      double rz = tot[0];
+      const double itol2 = a.inner_rtol * a.inner_rtol * rz;
+      bool first = true;
+      float beta = 0.f;
+      int cur = 0, it = 0;
+      bool stalled = false;
+      while (rz > itol2 && inner_total < a.max_iters) {
+        float* pnew = cur ? a.p1_32 : a.p0_32;
+        const float* pold = cur ? a.p0_32 : a.p1_32;
+        float q32acc[3] = {0.f, 0.f, 0.f};
+        {
+          Source<float, kModeDir, 0> src{a.r32, pold, beta, first, nullptr, mx, my, mz};
+          Sink<float> out{a.q32, pnew, nullptr, 0.f, false, kOpPressure, 0.f};
+          stencil_tiles<float, kModeDir, 0>(ts, src, out, q32acc, s32);
+        }
+        acc[0] = q32acc[0];
+        acc[1] = acc[2] = 0.0;
+        if (!allreduce(acc, tot)) return fail();
+        const double pq = tot[0];
+        if (!(pq > 0.0) || !isfinite(pq)) {
+          stalled = true;
+          break;
+        }
+        const float alpha = float(rz / pq);
+        float racc = 0.f;
+        for (size_t e = gtid(); e < n; e += gstride()) {
+          a.d32[e] = fmaf(alpha, pnew[e], a.d32[e]);
+          const float re = fmaf(-alpha, a.q32[e], a.r32[e]);
+          a.r32[e] = re;
+          racc = fmaf(re, re, racc);
+        }
+        acc[0] = racc;
+        acc[1] = acc[2] = 0.0;
+        if (!allreduce(acc, tot)) return fail();
+        beta = float(tot[0] / rz);
+        rz = tot[0];
+        first = false;
+        cur ^= 1;
+        ++it;
+        ++inner_total;
+      }
+      if (it == 0) {
+        if (stalled) status = kErrBreakdown;
+        break;
+      }
+      // x += ||r|| d (FP64), then a grid barrier: the residual stencil below
+      // reads neighbouring x values written by other blocks
+      for (size_t e = gtid(); e < n; e += gstride()) a.x[e] = fma(rnorm, double(a.d32[e]), a.x[e]);
+      acc[0] = acc[1] = acc[2] = 0.0;
+      if (!allreduce(acc, tot)) return fail();
+      // true FP64 residual
+      acc[0] = acc[1] = acc[2] = 0.0;
+      {
+        Source<double, kModeResid, 0> src{a.x, nullptr, 0.0, false, nullptr, mx, my, mz};
+        Sink<double> out{a.r, nullptr, a.b, 0.0, false, kOpPressure, 0.0};
+        stencil_tiles<double, kModeResid, 0>(ts, src, out, acc, s64);
+      }
+      if (!allreduce(acc, tot)) return fail();
+      rr = tot[1];
+      rsum = tot[2];
+      ++outer;
+    }
+  }
+
+  if (a.gauge) {
+    acc[0] = acc[1] = acc[2] = 0.0;
+    for (size_t e = gtid(); e < n; e += gstride()) acc[0] += a.x[e];
+    if (!allreduce(acc, tot)) return fail();
+    const double sh = a.gauge_value - tot[0] / double(n);
+    for (size_t e = gtid(); e < n; e += gstride()) a.x[e] += sh;
+  }
+
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->iters = inner_total;
+    st->outer_iters = outer;
+    st->restarts = 0;
+    st->status = status;
+    st->b_norm = sqrt(bb);
+    st->rel_resid = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+  }
+}
+
+int tiles_of(GridDims g, int tz) { return make_tiles(g.mx, g.my, g.mz, tz).count(); }
+
+int num_sms() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+typedef void (*CgKernel)(CgArgs);
+
+CgKernel cg_kernel_for(int precond, int rtz) {
+  if (precond) {
+    switch (rtz) {
+      case 1: return cg_fp64_kernel<1, 1>;
+      case 2: return cg_fp64_kernel<1, 2>;
+      case 4: return cg_fp64_kernel<1, 4>;
+      case 8: return cg_fp64_kernel<1, 8>;
+      default: return cg_fp64_kernel<1, 0>;
+    }
+  }
+  switch (rtz) {
+    case 1: return cg_fp64_kernel<0, 1>;
+    case 2: return cg_fp64_kernel<0, 2>;
+    case 4: return cg_fp64_kernel<0, 4>;
+    case 8: return cg_fp64_kernel<0, 8>;
+    default: return cg_fp64_kernel<0, 0>;
+  }
 }
 
 }  // namespace
 
-int cg_max_coresident_blocks(int kind_is_ir) {
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  (void)kind_is_ir;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_fp64_kernel<0>, kSolveThreads, 0);
-  int p1 = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, cg_fp64_kernel<1>, kSolveThreads, 0);
-  per_sm = per_sm < p1 ? per_sm : p1;
-  if (per_sm > 4) per_sm = 4;
-  return per_sm * sms;
+// Co-resident blocks per SM of one kernel variant (both preconditioner
+// instantiations), capped at 4.
+int variant_blocks_per_sm(int rtz) {
+  int per_sm = 1 << 30;
+  for (int p = 0; p < 2; ++p) {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cg_kernel_for(p, rtz), kSolveThreads, 0);
+    per_sm = b < per_sm ? b : per_sm;
+  }
+  return per_sm > 4 ? 4 : per_sm;
 }
 
-cudaError_t launch_cg(const CgArgs& a, const LaunchGeom& lg, cudaStream_t s, int64_t* launches) {
-  const size_t n = a.g.count();
-  int blocks = lg.blocks;
-  const int tiles = tiles_of(a.g, a.tz);
-  const int flat = int((n + kSolveThreads - 1) / kSolveThreads);
+int cg_max_coresident_blocks(int kind_is_ir) {
+  (void)kind_is_ir;
+  int best = 0;
+  for (int rtz : {0, 1, 2, 4, 8}) {
+    const int b = variant_blocks_per_sm(rtz);
+    best = b > best ? b : best;
+  }
+  return best * num_sms();
+}
+
+// Launch shape of one solve: blocks per SM and tile depth.  Requested values
+// (> 0) are honoured (clamped to what the kernel variant can keep
+// co-resident); otherwise the register path is preferred with the fewest
+// blocks that fits it (fewest all-reduce participants), and the memory path
+// falls back to the deepest tile that still gives every SM two tiles, with
+// as many blocks per SM as fit (latency hiding).
+SolveShape pick_solve_shape(GridDims g, int max_blocks, int bps_req, int tz_req) {
+  const int sms = num_sms();
+  auto consider = [&](int bps, int tz, bool allow_reg) {
+    const int tiles = tiles_of(g, tz);
+    const int reg_cap = variant_blocks_per_sm(tz) * sms;
+    const int mem_cap = variant_blocks_per_sm(0) * sms;
+    int blocks = bps * sms;
+    blocks = blocks < max_blocks ? blocks : max_blocks;
+    int b_reg = blocks < reg_cap ? blocks : reg_cap;
+    b_reg = b_reg < tiles ? b_reg : tiles;
+    b_reg = b_reg > 0 ? b_reg : 1;
+    const int tpb = (tiles + b_reg - 1) / b_reg;
+    if (allow_reg && tpb * tz <= kRegCells) return SolveShape{b_reg, tz, tz};
+    int b_mem = blocks < mem_cap ? blocks : mem_cap;
+    b_mem = b_mem > 0 ? b_mem : 1;
+    return SolveShape{b_mem, tz, 0};
+  };
+  if (bps_req > 0 || tz_req > 0) {
+    const int bps = bps_req > 0 ? bps_req : 1;
+    int tz = tz_req > 0 ? tz_req : 2;
+    tz = tz < 2 ? 1 : (tz < 4 ? 2 : (tz < 8 ? 4 : 8));
+    return consider(bps, tz, true);
+  }
+  for (int bps = 1; bps <= 4; bps <<= 1) {
+    for (int tz = kMaxTz; tz >= 1; tz >>= 1) {
+      const SolveShape s = consider(bps, tz, true);
+      if (s.rtz > 0) return s;
+    }
+  }
+  for (int tz = kMaxTz; tz > 1; tz >>= 1)
+    if (tiles_of(g, tz) >= 2 * sms) return consider(4, tz, false);
+  return consider(4, 1, false);
+}
+
+cudaError_t launch_cg(const CgArgs& a_in, const LaunchGeom& lg, cudaStream_t s, int64_t* launches) {
+  CgArgs a = a_in;
+  const SolveShape sh = pick_solve_shape(a.g, lg.blocks, lg.bps_req, lg.tz_req);
+  a.tz = sh.tz;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(sh.blocks);
+  cfg.blockDim = dim3(kSolveThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t err = cudaLaunchKernelEx(&cfg, cg_kernel_for(a.precond, sh.rtz), a);
+  if (launches) *launches += 1;
+  return err;
+}
+
+cudaError_t launch_apply_poisson(GridDims g, const double* x, double* y, int tz, cudaStream_t s,
+                                 int64_t* launches) {
+  if (tz < 1 || tz > kMaxTz) tz = 4;
+  const int tiles = tiles_of(g, tz);
+  apply_poisson_kernel<<<tiles, kSolveThreads, 0, s>>>(g, x, y, tz);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ir(const IrArgs& a_in, const LaunchGeom& lg, cudaStream_t s, int64_t* launches) {
+  IrArgs a = a_in;
+  const int sms = num_sms();
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ir_kernel, kSolveThreads, 0);
+  per_sm = per_sm > 4 ? 4 : (per_sm < 1 ? 1 : per_sm);
+  int bps = lg.bps_req > 0 ? (lg.bps_req < per_sm ? lg.bps_req : per_sm) : per_sm;
+  int tz = lg.tz_req;
+  if (tz <= 0) {
+    tz = 1;
+    for (int t = kMaxTz; t > 1; t >>= 1)
+      if (tiles_of(a.g, t) >= 2 * sms) { tz = t; break; }
+  }
+  tz = tz < 2 ? 1 : (tz < 4 ? 2 : (tz < 8 ? 4 : 8));
+  a.tz = tz;
+  int blocks = bps * sms;
+  if (blocks > lg.blocks) blocks = lg.blocks;
+  const int tiles = tiles_of(a.g, tz);
+  const int flat = int((a.g.count() + kSolveThreads - 1) / kSolveThreads);
   const int want = tiles > flat ? tiles : flat;
   if (blocks > want) blocks = want;
   if (blocks < 1) blocks = 1;
@@ -401,23 +802,9 @@ cudaError_t launch_cg(const CgArgs& a, const LaunchGeom& lg, cudaStream_t s, int
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t err;
-  if (a.precond) err = cudaLaunchKernelEx(&cfg, cg_fp64_kernel<1>, a);
-  else err = cudaLaunchKernelEx(&cfg, cg_fp64_kernel<0>, a);
+  cudaError_t err = cudaLaunchKernelEx(&cfg, ir_kernel, a);
   if (launches) *launches += 1;
   return err;
-}
-
-cudaError_t launch_apply_poisson(GridDims g, const double* x, double* y, int tz, cudaStream_t s,
-                                 int64_t* launches) {
-  const int tiles = tiles_of(g, tz);
-  apply_poisson_kernel<<<tiles, kSolveThreads, 0, s>>>(g, x, y, tz);
-  if (launches) *launches += 1;
-  return cudaGetLastError();
-}
-
-cudaError_t launch_ir(const IrArgs&, const LaunchGeom&, cudaStream_t, int64_t*) {
-  return cudaErrorNotSupported;
 }
 
 }  // namespace cfd
