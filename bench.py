@@ -63,6 +63,11 @@ def parse_args(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--poisson", type=int, default=0,
+                    help="standalone Neumann-Poisson solves on an N^3 grid instead of the cavity "
+                         "(one bench step = one solve of a seeded Gaussian right-hand side)")
+    ap.add_argument("--max-iters", type=int, default=0, help="CG iteration cap per solve (0: 20 N)")
+    ap.add_argument("--no-precision-study", action="store_true")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--max-seconds", type=float, default=150.0, help=argparse.SUPPRESS)
     return ap.parse_args(argv)
@@ -354,6 +359,25 @@ def main_ours(args):
                "how": "per step: cfd_set_field(u,v,w,p) from pinned host, cfd_step(1), cfd_read_field(u,v,w,p) "
                       "to pinned host; wall clock"}
 
+    # precision study on the standalone 256^3 Neumann-Poisson system: FP64 CG
+    # vs FP32 CG with FP64 refinement, both to a true FP64 rtol of 1e-8
+    precision = None
+    if rank == 0 and world == 1 and not args.no_precision_study:
+        cav.close()
+        del cav
+        torch.cuda.empty_cache()
+        study = {}
+        for solver in ("cg", "ir"):
+            res = time_solves(cfd, 256, solver, [0, 1], 1, 0, device)
+            study[solver] = {"ms_per_solve": [round(r["ms"], 3) for r in res], "iters": [r["iters"] for r in res],
+                             "refinements": [r["refinements"] for r in res],
+                             "rel_resid": [r["rel_resid"] for r in res]}
+        cg_ms = statistics.mean(study["cg"]["ms_per_solve"])
+        ir_ms = statistics.mean(study["ir"]["ms_per_solve"])
+        precision = {"workload": "Neumann-Poisson 256^3, N(0,1) right-hand sides seeds 0-1, rtol 1e-8 (true FP64)",
+                     "fp64_cg": study["cg"], "fp32_cg_fp64_refined": study["ir"],
+                     "speedup_ir_over_fp64_cg": cg_ms / ir_ms}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res = run_oracle_child(args.workload, 10 ** 6, 0, args.cpu_seconds)
@@ -376,11 +400,61 @@ def main_ours(args):
                           "all_converged": bool(ok)},
                 "phase_ms_per_step": phase_ms_per_step,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "precision_study": precision,
                 "clocks": clocks, "wall_s_timed": wall}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     return 0 if ok else 1
+
+
+def time_solves(cfd, n, solver, seeds, warmup, max_iters=0, device=None):
+    """Standalone FP64-judged pressure solves of Gaussian right-hand sides:
+    per-solve device time of the solve kernel (CUDA events inside the
+    library), iterations and the true relative residual."""
+    import torch
+    from paper_2504_03697_gb300.synthetic import gaussian_rhs
+
+    cav = cfd.Cavity(cfd.make_params(n, n, n, solver=solver, max_iters=max_iters), device=device)
+    bs = [torch.tensor(gaussian_rhs(n, n, n, seed=s), device=device) for s in seeds]
+    x = torch.zeros_like(bs[0])
+    for i in range(warmup):
+        cav.solve_pressure(bs[i % len(bs)], x)
+    out = []
+    for b in bs:
+        cav.phase_times()
+        cav.enable_timing(True)
+        rc, st = cav.solve_pressure(b, x)
+        cav.enable_timing(False)
+        ms, calls = cav.phase_times()["pcg"]
+        out.append({"ms": ms / max(calls, 1), "iters": st["iters"], "refinements": st["outer_iters"],
+                    "rel_resid": st["rel_resid"], "rc": rc})
+    del cav
+    return out
+
+
+def main_poisson(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    from paper_2504_03697_gb300 import build as B
+    B.build()
+    from paper_2504_03697_gb300 import cfd
+
+    n = args.poisson
+    res = time_solves(cfd, n, args.solver, list(range(args.steps)), args.warmup, args.max_iters, device)
+    ms = sorted(r["ms"] for r in res)
+    line = {"metric": "time-to-rtol-1e-8 per solve", "value": statistics.median(ms), "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "dtype": "f32+f64" if args.solver == "ir" else "f64", "data": "synthetic",
+            "config": {"workload": f"Neumann-Poisson {n}^3, N(0,1) right-hand sides (seeds 0..{args.steps - 1}), "
+                                   f"solver {args.solver}, rtol 1e-8", "max_iters": args.max_iters},
+            "solves": res}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
 
 
 def main(argv=None):
@@ -390,6 +464,8 @@ def main(argv=None):
         return 0
     if args.impl == "reference":
         return main_reference(args)
+    if args.poisson > 0:
+        return main_poisson(args)
     return main_ours(args)
 
 

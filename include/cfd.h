@@ -65,8 +65,13 @@ enum { CFD_FIELD_U = 0, CFD_FIELD_V = 1, CFD_FIELD_W = 2, CFD_FIELD_P = 3 };
 /* Pressure solver (Sec. 3.1: PCG with an optional preconditioner).
  *   CG      unpreconditioned conjugate gradients, FP64
  *   JACOBI  Jacobi-preconditioned CG, FP64 (the paper's optimised variant)
- *   IR      FP32 inner CG with FP64 iterative refinement (outer residual,
- *           norms and the correction in FP64)                            */
+ *   IR      FP32 CG (vectors and stencil in FP32, partial sums reduced and
+ *           CG scalars formed in FP64) with FP64 iterative refinement:
+ *           each time the FP32 residual has fallen by ir_delta, x gathers
+ *           the FP32 correction in FP64 and the FP64 true residual
+ *           b - A x replaces the FP32 one, keeping the search direction.
+ *           Convergence is judged on the FP64 true residual only.  Stats:
+ *           iters = FP32 iterations, outer_iters = FP64 refinements.      */
 enum { CFD_SOLVER_CG = 0, CFD_SOLVER_JACOBI = 1, CFD_SOLVER_IR = 2 };
 
 /* Substeps for cfd_substep (kernel-level access to one phase of the step). */
@@ -89,7 +94,8 @@ typedef struct {
   double rtol;              /* ||b - A x||_2 <= rtol ||b||_2 (true FP64 residual)  */
   int32_t max_iters;        /* CG iteration cap per solve; 0 -> 20 * max(n)       */
   int32_t warm_start;       /* 1: start the pressure solve from the previous p    */
-  double inner_rtol;        /* IR inner FP32 tolerance; 0 -> 1e-4                 */
+  double ir_delta;          /* IR: refine in FP64 each time the FP32 residual has
+                               fallen by this factor, in (0, 1); 0 -> 0.1          */
   int32_t reserved[8];      /* must be zero                                       */
 } cfd_params;
 

@@ -163,7 +163,7 @@ int validate(const cfd_params* p) {
     return set_err(nullptr, CFD_ERR_INVALID_ARG, "unknown solver %d", p->solver);
   if (!(p->rtol > 0) || p->rtol >= 1) return set_err(nullptr, CFD_ERR_INVALID_ARG, "rtol must be in (0, 1)");
   if (p->max_iters < 0) return set_err(nullptr, CFD_ERR_INVALID_ARG, "max_iters must be >= 0");
-  if (p->inner_rtol < 0 || p->inner_rtol >= 1) return set_err(nullptr, CFD_ERR_INVALID_ARG, "inner_rtol must be in [0, 1)");
+  if (p->ir_delta < 0 || p->ir_delta >= 1) return set_err(nullptr, CFD_ERR_INVALID_ARG, "ir_delta must be in [0, 1)");
   for (int i = 0; i < 8; ++i)
     if (p->reserved[i] != 0) return set_err(nullptr, CFD_ERR_INVALID_ARG, "reserved fields must be zero");
   return CFD_OK;
@@ -231,9 +231,9 @@ int run_pressure(cfd_handle* h, double* x, int zero_x0, int gauge, DevSolveStats
     a.r32 = h->r32; a.d32 = h->d32; a.p0_32 = h->p0_32; a.p1_32 = h->p1_32; a.q32 = h->q32;
     a.zero_x0 = zero_x0; a.remove_mean = 1; a.gauge = gauge; a.gauge_value = 1.0;
     a.rtol = h->prm.rtol;
-    a.inner_rtol = h->prm.inner_rtol > 0 ? h->prm.inner_rtol : 1e-4;
+    a.delta = h->prm.ir_delta > 0 ? h->prm.ir_delta : 0.1;
     a.max_iters = iter_cap(h->prm);
-    a.max_outer = 30;
+    a.max_outer = 1000;
     a.timeout_ns = kTimeoutNs;
     a.ctrl = h->ctrl; a.partials = h->partials; a.stats = st;
     a.tz = tz_for(g.mz);

@@ -83,9 +83,9 @@ struct IrArgs {
   int gauge;
   double gauge_value;
   double rtol;
-  double inner_rtol;
-  int max_iters;   // cap on the total inner iterations
-  int max_outer;
+  double delta;     // refine when the FP32 residual fell by this factor
+  int max_iters;   // cap on the FP32 CG iterations
+  int max_outer;   // cap on the FP64 refinements
   unsigned long long timeout_ns;
   SolveCtrl* ctrl;
   double* partials;

@@ -477,14 +477,20 @@ __global__ void __launch_bounds__(kSolveThreads) apply_poisson_kernel(GridDims g
 }
 
 // ---------------------------------------------------------------------------
-// Mixed-precision iterative refinement (persistent; pressure operator).
+// Mixed-precision CG with FP64 refinement (persistent; pressure operator).
 //
-// Outer loop in FP64: r = b - A x (true residual, FP64 stencil), stop when
-// ||r|| <= rtol ||b||.  Inner solve in FP32: CG on A d = (r - mean(r)) /
-// ||r|| from d = 0 until its recurrence residual falls by inner_rtol (or the
-// iteration budget ends), every vector and the stencil in FP32; per-thread
-// partial sums in FP32, their cross-thread / cross-block reduction and the
-// CG scalars (alpha, beta) in FP64.  Then x += ||r|| d in FP64.
+// One conjugate-gradient recurrence runs in FP32: the search direction p,
+// the operator output q, the recurrence residual r32 and the correction x32
+// are FP32 vectors and the stencil runs in FP32; per-thread partial sums are
+// FP32, their cross-thread / cross-block reductions and the CG scalars
+// (alpha, beta) are FP64.  Refinement happens in FP64 whenever the FP32
+// residual has fallen by the factor delta since the last refinement (or
+// claims convergence): x += x32 in FP64, x32 = 0, the true residual
+// r = b - A x is recomputed with the FP64 stencil, and r32 = r (mean
+// removed) replaces the recurrence residual; the search direction is kept,
+// so the refinement does not restart the Krylov process (the "reliable
+// update" form of iterative refinement).  Convergence is only ever declared
+// on the FP64 true residual: ||b - A x|| <= rtol ||b||.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kSolveThreads) ir_kernel(IrArgs a) {
   __shared__ double s_raw[kTileSlots];
@@ -518,7 +524,7 @@ __global__ void __launch_bounds__(kSolveThreads) ir_kernel(IrArgs a) {
     shift = tot[0] / double(n);
   }
 
-  // r = b - A x0, partials b.b, r.r, sum(r)
+  // r = b - A x0 (FP64), partials b.b, r.r, sum(r)
   acc[0] = acc[1] = acc[2] = 0.0;
   if (a.zero_x0) {
     for (size_t e = gtid(); e < n; e += gstride()) {
@@ -537,87 +543,107 @@ __global__ void __launch_bounds__(kSolveThreads) ir_kernel(IrArgs a) {
   }
   if (!allreduce(acc, tot)) return fail();
   const double bb = tot[0];
-  double rr = tot[1], rsum = tot[2];
+  double rr = tot[1];  // FP64 true residual norm^2 at the last refinement
+  double rsum = tot[2];
 
-  int status = kErrNotConverged, outer = 0, inner_total = 0;
+  int status = kErrNotConverged, refinements = 0, iters = 0;
   if (bb == 0.0) {
     for (size_t e = gtid(); e < n; e += gstride()) a.x[e] = 0.0;
     status = kOk;
     rr = 0.0;
   } else {
     const double tol2 = a.rtol * a.rtol * bb;
+    const double delta2 = a.delta * a.delta;
+    double rz = 0.0;     // FP32 recurrence residual norm^2 (FP64-reduced)
+    double beta = 0.0;
+    bool first = true;
+    bool refine = true;  // load r32 from the FP64 residual
+    int cur = 0;
     while (true) {
-      if (rr <= tol2) {
-        status = kOk;
-        break;
-      }
-      if (outer >= a.max_outer || inner_total >= a.max_iters) break;
-      // inner right-hand side: (r - mean r) / ||r|| in FP32, d = 0
-      const double rnorm = sqrt(rr);
-      const double scale = 1.0 / rnorm;
-      const double rmean = rsum / double(n);
-      float f32[3] = {0.f, 0.f, 0.f};
-      for (size_t e = gtid(); e < n; e += gstride()) {
-        const float v = float((a.r[e] - rmean) * scale);
-        a.r32[e] = v;
-        a.d32[e] = 0.f;
-        f32[0] = fmaf(v, v, f32[0]);
-      }
-      acc[0] = f32[0];
-      acc[1] = acc[2] = 0.0;
-      if (!allreduce(acc, tot)) return fail();
-      double rz = tot[0];
-      const double itol2 = a.inner_rtol * a.inner_rtol * rz;
-      bool first = true;
-      float beta = 0.f;
-      int cur = 0, it = 0;
-      bool stalled = false;
-      while (rz > itol2 && inner_total < a.max_iters) {
-        float* pnew = cur ? a.p1_32 : a.p0_32;
-        const float* pold = cur ? a.p0_32 : a.p1_32;
-        float q32acc[3] = {0.f, 0.f, 0.f};
-        {
-          Source<float, kModeDir, 0> src{a.r32, pold, beta, first, nullptr, mx, my, mz};
-          Sink<float> out{a.q32, pnew, nullptr, 0.f, false, kOpPressure, 0.f};
-          stencil_tiles<float, kModeDir, 0>(ts, src, out, q32acc, s32);
-        }
-        acc[0] = q32acc[0];
-        acc[1] = acc[2] = 0.0;
-        if (!allreduce(acc, tot)) return fail();
-        const double pq = tot[0];
-        if (!(pq > 0.0) || !isfinite(pq)) {
-          stalled = true;
+      if (refine) {
+        if (rr <= tol2) {
+          status = kOk;
           break;
         }
-        const float alpha = float(rz / pq);
-        float racc = 0.f;
+        if (refinements > a.max_outer) break;
+        // r32 = r - mean(r); x32 = 0; rz = |r32|^2
+        const double rmean = rsum / double(n);
+        float f = 0.f;
         for (size_t e = gtid(); e < n; e += gstride()) {
-          a.d32[e] = fmaf(alpha, pnew[e], a.d32[e]);
-          const float re = fmaf(-alpha, a.q32[e], a.r32[e]);
-          a.r32[e] = re;
-          racc = fmaf(re, re, racc);
+          const float v = float(a.r[e] - rmean);
+          a.r32[e] = v;
+          a.d32[e] = 0.f;
+          f = fmaf(v, v, f);
         }
-        acc[0] = racc;
+        acc[0] = f;
         acc[1] = acc[2] = 0.0;
         if (!allreduce(acc, tot)) return fail();
-        beta = float(tot[0] / rz);
-        rz = tot[0];
-        first = false;
-        cur ^= 1;
-        ++it;
-        ++inner_total;
+        const double rz_new = tot[0];
+        if (!first) beta = rz_new / rz;  // keep the direction: beta from the replaced residual
+        rz = rz_new;
+        refine = false;
       }
-      if (it == 0) {
-        if (stalled) status = kErrBreakdown;
+      if (iters >= a.max_iters) break;
+      const double rz_ref = rr;  // residual level of the last refinement
+      // phase D (FP32): p = r32 + beta p, q = A p, partial p.q
+      float* pnew = cur ? a.p1_32 : a.p0_32;
+      const float* pold = cur ? a.p0_32 : a.p1_32;
+      float fa[3] = {0.f, 0.f, 0.f};
+      {
+        Source<float, kModeDir, 0> src{a.r32, pold, float(beta), first, nullptr, mx, my, mz};
+        Sink<float> out{a.q32, pnew, nullptr, 0.f, false, kOpPressure, 0.f};
+        stencil_tiles<float, kModeDir, 0>(ts, src, out, fa, s32);
+      }
+      acc[0] = fa[0];
+      acc[1] = acc[2] = 0.0;
+      if (!allreduce(acc, tot)) return fail();
+      const double pq = tot[0];
+      if (!(pq > 0.0) || !isfinite(pq)) {
+        status = kErrBreakdown;
         break;
       }
-      // x += ||r|| d (FP64), then a grid barrier: the residual stencil below
-      // reads neighbouring x values written by other blocks
-      for (size_t e = gtid(); e < n; e += gstride()) a.x[e] = fma(rnorm, double(a.d32[e]), a.x[e]);
+      const float alpha = float(rz / pq);
+      // phase U (FP32): x32 += alpha p, r32 -= alpha q, partial |r32|^2
+      float racc = 0.f;
+      for (size_t e = gtid(); e < n; e += gstride()) {
+        a.d32[e] = fmaf(alpha, pnew[e], a.d32[e]);
+        const float re = fmaf(-alpha, a.q32[e], a.r32[e]);
+        a.r32[e] = re;
+        racc = fmaf(re, re, racc);
+      }
+      acc[0] = racc;
+      acc[1] = acc[2] = 0.0;
+      if (!allreduce(acc, tot)) return fail();
+      const double rz_new = tot[0];
+      first = false;
+      cur ^= 1;
+      ++iters;
+      if (rz_new <= delta2 * rz_ref || rz_new <= tol2) {
+        // refinement in FP64: x += x32, r = b - A x (true residual)
+        for (size_t e = gtid(); e < n; e += gstride()) a.x[e] += double(a.d32[e]);
+        acc[0] = acc[1] = acc[2] = 0.0;
+        if (!allreduce(acc, tot)) return fail();  // x complete before the stencil reads it
+        {
+          Source<double, kModeResid, 0> src{a.x, nullptr, 0.0, false, nullptr, mx, my, mz};
+          Sink<double> out{a.r, nullptr, a.b, 0.0, false, kOpPressure, 0.0};
+          stencil_tiles<double, kModeResid, 0>(ts, src, out, acc, s64);
+        }
+        if (!allreduce(acc, tot)) return fail();
+        rr = tot[1];
+        rsum = tot[2];
+        ++refinements;
+        refine = true;
+        rz = rz;  // beta for the next direction uses the replaced residual
+      } else {
+        beta = rz_new / rz;
+        rz = rz_new;
+      }
+    }
+    if (status != kOk) {
+      // leaving early: fold the pending FP32 correction into x and measure
+      for (size_t e = gtid(); e < n; e += gstride()) a.x[e] += double(a.d32[e]);
       acc[0] = acc[1] = acc[2] = 0.0;
       if (!allreduce(acc, tot)) return fail();
-      // true FP64 residual
-      acc[0] = acc[1] = acc[2] = 0.0;
       {
         Source<double, kModeResid, 0> src{a.x, nullptr, 0.0, false, nullptr, mx, my, mz};
         Sink<double> out{a.r, nullptr, a.b, 0.0, false, kOpPressure, 0.0};
@@ -625,8 +651,7 @@ __global__ void __launch_bounds__(kSolveThreads) ir_kernel(IrArgs a) {
       }
       if (!allreduce(acc, tot)) return fail();
       rr = tot[1];
-      rsum = tot[2];
-      ++outer;
+      if (rr <= tol2 && status == kErrNotConverged) status = kOk;
     }
   }
 
@@ -639,8 +664,8 @@ __global__ void __launch_bounds__(kSolveThreads) ir_kernel(IrArgs a) {
   }
 
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st->iters = inner_total;
-    st->outer_iters = outer;
+    st->iters = iters;
+    st->outer_iters = refinements;
     st->restarts = 0;
     st->status = status;
     st->b_norm = sqrt(bb);

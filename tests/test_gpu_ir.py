@@ -37,11 +37,11 @@ def lam_min(shape):
     return min(4 * np.sin(np.pi / (2 * n)) ** 2 for n in shape if n > 1)
 
 
-@pytest.mark.parametrize("shape,inner", [((48, 40, 32), 0.0), ((17, 9, 13), 0.0), ((64, 64, 64), 1e-3),
-                                         ((33, 31, 30), 1e-5)])
-def test_ir_solve_true_residual_and_bound(cfd, shape, inner):
+@pytest.mark.parametrize("shape,delta", [((48, 40, 32), 0.0), ((17, 9, 13), 0.0), ((64, 64, 64), 0.01),
+                                         ((33, 31, 30), 0.3), ((1, 1, 9), 0.0)])
+def test_ir_solve_true_residual_and_bound(cfd, shape, delta):
     nx, ny, nz = shape
-    cav = cfd.Cavity(cfd.make_params(nx, ny, nz, solver="ir", inner_rtol=inner))
+    cav = cfd.Cavity(cfd.make_params(nx, ny, nz, solver="ir", ir_delta=delta))
     b = gaussian_rhs(nx, ny, nz, seed=4)
     bg = torch.tensor(b, device="cuda")
     xg = torch.zeros_like(bg)
