@@ -72,7 +72,7 @@ Layout ws_layout(const cfd_params& p, int max_blocks) {
     L.p1_32 = take(cells * 4);
     L.q32 = take(cells * 4);
   }
-  L.partials = take(2 * size_t(max_blocks) * kMaxPartials * 8);  // double-buffered
+  L.partials = take(partials_doubles(max_blocks) * 8);  // double-buffered block + group partials
   L.ctrl = take(sizeof(SolveCtrl));
   L.stats = take(size_t(kStatsCap + 1) * sizeof(DevStepStats));  // ring + one slot for substep/solve calls
   L.total = off;

@@ -9,15 +9,25 @@
 
 namespace cfd {
 
-constexpr int kMaxPartials = 8;  // scalars one grid reduction can carry
+constexpr int kMaxPartials = 8;   // scalars one grid reduction can carry
+constexpr int kFlatMaxBlocks = 1024;  // up to this grid size every block reads every partial
+constexpr int kGroupSize = 32;      // blocks per group of the two-level all-reduce
+constexpr int kMaxGroups = 128;     // groups (so at most 4096 blocks)
 
 // Control block of one persistent solve (zeroed by the host before each
-// launch): the grid all-reduce counter and the error flag.
+// launch): the grid all-reduce counters and the error flag.
 struct __align__(64) SolveCtrl {
-  unsigned int arrive;  // monotonic arrival counter of the grid all-reduce
+  unsigned int arrive;  // monotonic arrival counter (flat) / group-sum counter (two-level)
   int error;            // CFD_ERR_* of a device-side failure, 0 if none
   int pad[14];
+  unsigned int group[kMaxGroups];  // monotonic per-group arrival counters (two-level)
 };
+
+// Doubles of the partial-sum scratch a grid of `blocks` blocks needs:
+// double-buffered block partials, then double-buffered group partials.
+__host__ __device__ constexpr size_t partials_doubles(int blocks) {
+  return 2 * size_t(blocks) * kMaxPartials + 2 * size_t(kMaxGroups) * kMaxPartials;
+}
 
 // Per-solve statistics written by the device (mirrors cfd_solve_stats).
 struct DevSolveStats {
@@ -103,64 +113,122 @@ __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
   return v;
 }
 
+__device__ __forceinline__ unsigned int atom_add_acq_rel_gpu(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+// Bounded wait (thread 0) until the monotonic counter reaches target.
+// Returns false, recording CFD_ERR_TIMEOUT, after timeout_ns, and also when
+// another block has recorded an error.
+__device__ __forceinline__ bool wait_counter(SolveCtrl* ctrl, const unsigned int* counter, unsigned int target,
+                                             unsigned long long timeout_ns) {
+  const unsigned long long t0 = global_ns();
+  unsigned int polls = 0;
+  while (int(ld_acquire_gpu(counter) - target) < 0) {
+    if ((++polls & 63u) == 0) {
+      if (ld_volatile_s32(&ctrl->error) != 0) return false;
+      if (global_ns() - t0 > timeout_ns) {
+        atomicCAS(&ctrl->error, 0, kErrTimeout);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
 // ---------------------------------------------------------------------------
 // Grid-wide all-reduce + barrier for a cooperatively launched persistent
-// kernel (all blocks co-resident).
+// kernel (all blocks co-resident).  Every block obtains bitwise the same
+// totals, independent of arrival order: all sums run in a fixed order with
+// a fixed thread/tree shape.
 //
-// Each block publishes NV partial sums in a double-buffered array (buffer
-// round & 1) and arrives on a monotonically increasing counter with a
-// release reduction.  Once the counter reaches (round + 1) * gridDim.x,
-// every block sums all block partials itself, in block order with the same
-// thread/tree shape, so every block obtains bitwise the same totals and the
-// result does not depend on arrival order.  Double buffering is enough: a
-// block can only overwrite buffer (round & 1) again after the next round's
-// barrier, which every block reaches only after finishing this round's sum.
+// Flat form (grid <= kFlatMaxBlocks): each block stores its NV partials in a
+// double-buffered array (buffer round & 1), arrives on a monotonic counter
+// with a release reduction, waits until the counter reaches
+// (round + 1) * grid, then sums all block partials itself.
 //
-// Memory ordering: partial stores, then red.release on the counter; the
-// waiting thread 0 acquires the counter; bar.sync carries that to the other
-// threads, which read the partials through L2 (ld.global.cg).
+// Two-level form (larger grids): blocks arrive on their group's counter
+// (groups of kGroupSize consecutive blocks) with an acq_rel atomic; the last
+// arriver of a group sums the group's partials in block order, stores the
+// group partial and arrives on the top counter; every block waits for all
+// groups and sums the group partials in group order.  This keeps the reads
+// per all-reduce linear in the grid size.
 //
-// Every wait is bounded: after timeout_ns the waiter records
-// CFD_ERR_TIMEOUT in ctrl->error and returns false; any block that sees a
-// recorded error also returns false.  `round` is the caller's per-block
+// Double buffering is enough: a buffer is written again two rounds later,
+// after a barrier that every block reaches only once it has read this round.
+// Memory ordering: partial stores precede a release (red.release or the
+// release half of atom.acq_rel) on the counter they arrive at; readers
+// acquire that counter in thread 0, bar.sync carries it to the block, and
+// partials are read through L2 (ld.global.cg).
+//
+// Every wait is bounded (wait_counter).  `round` is the caller's per-block
 // count of completed all-reduces (identical in every block).
 // ---------------------------------------------------------------------------
 template <int NV>
 __device__ bool grid_allreduce(double (&v)[NV], double (&out)[NV], SolveCtrl* ctrl, double* partials,
                                double* scratch, unsigned long long timeout_ns, unsigned int& round) {
   __shared__ int s_ok;
+  __shared__ int s_last;
   __shared__ double s_bcast[kMaxPartials];
   block_reduce<NV>(v, scratch);
-  double* buf = partials + size_t(round & 1u) * gridDim.x * kMaxPartials;
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int a = 0; a < NV; ++a) buf[size_t(blockIdx.x) * kMaxPartials + a] = v[a];
-    red_add_release_gpu(&ctrl->arrive, 1u);
-    const unsigned int target = (round + 1u) * gridDim.x;
-    const unsigned long long t0 = global_ns();
-    int ok = 1;
-    unsigned int polls = 0;
-    while (int(ld_acquire_gpu(&ctrl->arrive) - target) < 0) {
-      if ((++polls & 63u) == 0) {
-        if (ld_volatile_s32(&ctrl->error) != 0) { ok = 0; break; }
-        if (global_ns() - t0 > timeout_ns) {
-          atomicCAS(&ctrl->error, 0, kErrTimeout);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    s_ok = ok;
-  }
-  ++round;
-  __syncthreads();
-  if (!s_ok) return false;
+  const unsigned int G = gridDim.x;
+  const unsigned int r = round++;
+  double* buf = partials + size_t(r & 1u) * G * kMaxPartials;
   double acc[NV];
 #pragma unroll
   for (int a = 0; a < NV; ++a) acc[a] = 0.0;
-  for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+
+  if (G <= unsigned(kFlatMaxBlocks)) {
+    if (threadIdx.x == 0) {
 #pragma unroll
-    for (int a = 0; a < NV; ++a) acc[a] += __ldcg(&buf[size_t(b) * kMaxPartials + a]);
+      for (int a = 0; a < NV; ++a) buf[size_t(blockIdx.x) * kMaxPartials + a] = v[a];
+      red_add_release_gpu(&ctrl->arrive, 1u);
+      s_ok = wait_counter(ctrl, &ctrl->arrive, (r + 1u) * G, timeout_ns) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!s_ok) return false;
+    for (unsigned int b = threadIdx.x; b < G; b += blockDim.x) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) acc[a] += __ldcg(&buf[size_t(b) * kMaxPartials + a]);
+    }
+  } else {
+    const unsigned int ngroups = (G + kGroupSize - 1) / kGroupSize;
+    const unsigned int g = blockIdx.x / kGroupSize;
+    const unsigned int g0 = g * kGroupSize;
+    const unsigned int gsize = (G - g0) < unsigned(kGroupSize) ? (G - g0) : unsigned(kGroupSize);
+    double* gbuf = partials + 2 * size_t(G) * kMaxPartials + size_t(r & 1u) * kMaxGroups * kMaxPartials;
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) buf[size_t(blockIdx.x) * kMaxPartials + a] = v[a];
+      const unsigned int old = atom_add_acq_rel_gpu(&ctrl->group[g], 1u);
+      s_last = (old == (r + 1u) * gsize - 1u) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_last) {
+      // last of its group: sum the group's block partials in block order
+      double gacc[NV];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) gacc[a] = 0.0;
+      if (threadIdx.x < gsize) {
+#pragma unroll
+        for (int a = 0; a < NV; ++a) gacc[a] = __ldcg(&buf[size_t(g0 + threadIdx.x) * kMaxPartials + a]);
+      }
+      block_reduce<NV>(gacc, scratch);
+      if (threadIdx.x == 0) {
+#pragma unroll
+        for (int a = 0; a < NV; ++a) gbuf[size_t(g) * kMaxPartials + a] = gacc[a];
+        red_add_release_gpu(&ctrl->arrive, 1u);
+      }
+    }
+    if (threadIdx.x == 0) s_ok = wait_counter(ctrl, &ctrl->arrive, (r + 1u) * ngroups, timeout_ns) ? 1 : 0;
+    __syncthreads();
+    if (!s_ok) return false;
+    for (unsigned int q = threadIdx.x; q < ngroups; q += blockDim.x) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) acc[a] += __ldcg(&gbuf[size_t(q) * kMaxPartials + a]);
+    }
   }
   block_reduce<NV>(acc, scratch);
   if (threadIdx.x == 0) {

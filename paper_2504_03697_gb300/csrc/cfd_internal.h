@@ -2,6 +2,7 @@
 // units.  Not part of the public ABI (include/cfd.h is).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -30,6 +31,7 @@ struct LaunchGeom {
   int num_sms;
   int bps_req;      // requested blocks per SM (0: automatic)
   int tz_req;       // requested tile depth (0: automatic)
+  int no_tma;       // 1: never take the TMA stencil path
 };
 
 // Launch shape picked for one solve.
@@ -91,7 +93,24 @@ struct IrArgs {
   double* partials;
   DevSolveStats* stats;
   int tz;
+  // TMA path of the FP32 stencil phase (use_tma != 0): 3D tensor maps over
+  // r32, p0_32, p1_32 with a (kTmaBoxW x kTmaBoxH x 1) box, z-chunk depth.
+  int use_tma;
+  int tma_zl;
+  CUtensorMap map_r32;
+  CUtensorMap map_p0;
+  CUtensorMap map_p1;
 };
+
+// TMA slab box of the FP32 stencil: a 32 x 8 tile plus a 4-float-aligned x
+// halo (x from x0-4, 40 floats = 160 B) and a one-row y halo.
+constexpr int kTmaBoxW = 40;
+constexpr int kTmaBoxH = 10;
+
+// Encode a 3D FP32 tensor map (mx, my, mz; x fastest) for the FP32 stencil
+// box.  Returns false when the grid does not meet TMA's stride rules (mx a
+// multiple of 4) or the driver entry point is unavailable.
+bool encode_f32_grid_map(CUtensorMap* map, const float* base, int mx, int my, int mz);
 
 struct PhysArgs {
   int nx, ny, nz;

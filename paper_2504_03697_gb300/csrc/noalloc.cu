@@ -39,8 +39,10 @@ constexpr size_t kOffD0 = kOffR + kVecBytes;
 constexpr size_t kOffD1 = kOffD0 + kVecBytes;
 constexpr size_t kOffQ = kOffD1 + kVecBytes;
 constexpr size_t kOffPartials = kOffQ + kVecBytes;
-constexpr size_t kOffCtrl = kOffPartials + 2 * size_t(kNoallocMaxBlocks) * kMaxPartials * sizeof(double);
-constexpr size_t kOffStats = kOffCtrl + 256;
+constexpr size_t kOffCtrl = kOffPartials + partials_doubles(kNoallocMaxBlocks) * sizeof(double);
+constexpr size_t kCtrlBytes = 1024;
+static_assert(sizeof(SolveCtrl) <= kCtrlBytes, "control block does not fit");
+constexpr size_t kOffStats = kOffCtrl + kCtrlBytes;
 constexpr size_t kNoallocBytes = kOffStats + 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
@@ -99,7 +101,7 @@ extern "C" int cfd_poisson_solve_noalloc(int32_t nx, int32_t ny, int32_t nz, con
   // the array keeps the previous call's contents: the copy of b overwrites
   // its part, the control block and statistics must start at zero
   e = cudaMemcpyAsync(b, b_dev, cells * sizeof(double), cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ctrl, 0, 512, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctrl, 0, kCtrlBytes + 256, s);
   if (e != cudaSuccess) return cfd_internal_error(CFD_ERR_CUDA, "noalloc: %s", cudaGetErrorString(e));
 
   CgArgs a{};

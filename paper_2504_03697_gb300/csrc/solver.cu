@@ -33,7 +33,10 @@
 // phase U is a flat pass.  Reductions are deterministic (cfd_common.cuh), so
 // a solve is bitwise reproducible run to run for a given launch shape.
 
+#include <cudaTypedefs.h>
+
 #include <cmath>
+#include <mutex>
 
 #include "cfd_internal.h"
 
@@ -477,6 +480,145 @@ __global__ void __launch_bounds__(kSolveThreads) apply_poisson_kernel(GridDims g
 }
 
 // ---------------------------------------------------------------------------
+// TMA z-marching stencil for the FP32 direction phase.
+//
+// Work item = a kTileX x kTileY column of the grid over tma_zl planes.  One
+// thread streams plane slabs of r32 and p_old (box kTmaBoxW x kTmaBoxH, x
+// from x0 - 4 so that every copy starts on a 16-byte boundary; out-of-box
+// elements are filled with zeros by the copy engine) into a ring of
+// kTmaStages shared-memory stages with cp.async.bulk.tensor, each stage
+// completing on its own mbarrier.  All threads compute plane k from the
+// slabs of planes k-1, k, k+1 while planes k+2.. are in flight; the stage of
+// plane k-1 is refilled once every thread is past the block barrier.  Every
+// mbarrier wait is bounded (kTmaWaitNs); a give-up records
+// CFD_ERR_TIMEOUT.  Each call issues and consumes the same planes, so no
+// copy is in flight when it returns.
+// ---------------------------------------------------------------------------
+constexpr int kTmaStages = 4;
+constexpr int kTmaSlabP = 416;  // floats per stage slab: 40 x 10 padded to 128-byte multiples
+constexpr unsigned long long kTmaWaitNs = 1000000000ull;
+static_assert(2 * kTmaStages * kTmaSlabP * 4 <= kTileSlots * 8, "TMA ring must fit in the tile buffer");
+
+struct TmaRing {
+  float* sr;        // kTmaStages slabs of r32
+  float* sp;        // kTmaStages slabs of p_old
+  uint64_t* full;   // one mbarrier per stage
+  unsigned int gp;  // planes issued so far (ring position)
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity) {
+  const unsigned long long t0 = global_ns();
+  for (unsigned i = 0;; ++i) {
+    unsigned done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((i & 255u) == 255u && global_ns() - t0 > kTmaWaitNs) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(float* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_issue_plane(const IrArgs& a, const CUtensorMap* mp, TmaRing& ring, unsigned g,
+                                                int x0, int y0, int z) {
+  const int s = int(g % kTmaStages);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_expect_tx(&ring.full[s], 2 * kTmaBoxW * kTmaBoxH * 4);
+  tma_load_3d(ring.sr + s * kTmaSlabP, &a.map_r32, x0 - 4, y0 - 1, z, &ring.full[s]);
+  tma_load_3d(ring.sp + s * kTmaSlabP, mp, x0 - 4, y0 - 1, z, &ring.full[s]);
+}
+
+// p_new = r32 + beta p_old (r32 alone on the first iteration), q = A p_new
+// (Neumann pressure operator), partial p.q; returns false on a wait timeout.
+__device__ bool dir_tma_f32(const IrArgs& a, const CUtensorMap* mp, float beta, bool first, float* pnew, float* q,
+                            float& acc, TmaRing& ring) {
+  const int mx = a.g.mx, my = a.g.my, mz = a.g.mz;
+  const int tx = threadIdx.x % kTileX, ty = threadIdx.x / kTileX;
+  const int zl = a.tma_zl;
+  const int ntx = (mx + kTileX - 1) / kTileX, nty = (my + kTileY - 1) / kTileY, nzc = (mz + zl - 1) / zl;
+  const int items = ntx * nty * nzc;
+  if (threadIdx.x == 0) asm volatile("fence.proxy.async.global;" ::: "memory");  // generic writes -> TMA reads
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int bx = it % ntx, rest = it / ntx, by = rest % nty, bz = rest / nty;
+    const int x0 = bx * kTileX, y0 = by * kTileY, z0 = bz * zl;
+    const int z1 = min(z0 + zl, mz);
+    const int np = (z1 - z0) + 2;  // planes z0-1 .. z1
+    const unsigned base = ring.gp;
+    if (threadIdx.x == 0)
+      for (int lp = 0; lp < kTmaStages && lp < np; ++lp) tma_issue_plane(a, mp, ring, base + lp, x0, y0, z0 - 1 + lp);
+    ring.gp += np;
+    for (int lp = 0; lp < 2; ++lp) {
+      const unsigned g = base + lp;
+      if (!mbar_wait(&ring.full[g % kTmaStages], (g / kTmaStages) & 1u)) {
+        atomicCAS(&a.ctrl->error, 0, kErrTimeout);
+        return false;
+      }
+    }
+    const int i = x0 + tx, j = y0 + ty;
+    for (int kz = 0; kz < z1 - z0; ++kz) {
+      const int lp = kz + 1;
+      {
+        const unsigned g = base + lp + 1;
+        if (!mbar_wait(&ring.full[g % kTmaStages], (g / kTmaStages) & 1u)) {
+          atomicCAS(&a.ctrl->error, 0, kErrTimeout);
+          return false;
+        }
+      }
+      if (i < mx && j < my) {
+        const int k = z0 + kz;
+        const float* rm = ring.sr + ((base + lp - 1) % kTmaStages) * kTmaSlabP;
+        const float* rc = ring.sr + ((base + lp) % kTmaStages) * kTmaSlabP;
+        const float* rq = ring.sr + ((base + lp + 1) % kTmaStages) * kTmaSlabP;
+        const float* pm = ring.sp + ((base + lp - 1) % kTmaStages) * kTmaSlabP;
+        const float* pc_ = ring.sp + ((base + lp) % kTmaStages) * kTmaSlabP;
+        const float* pq = ring.sp + ((base + lp + 1) % kTmaStages) * kTmaSlabP;
+        const int c = (ty + 1) * kTmaBoxW + (tx + 4);
+        auto V = [&](const float* rs, const float* ps, int o) { return first ? rs[o] : fmaf(beta, ps[o], rs[o]); };
+        const float pc = V(rc, pc_, c);
+        float xm = V(rc, pc_, c - 1), xp = V(rc, pc_, c + 1);
+        float ym = V(rc, pc_, c - kTmaBoxW), yp = V(rc, pc_, c + kTmaBoxW);
+        float zm = V(rm, pm, c), zp = V(rq, pq, c);
+        if (i == 0) xm = pc;
+        if (i == mx - 1) xp = pc;
+        if (j == 0) ym = pc;
+        if (j == my - 1) yp = pc;
+        if (k == 0) zm = pc;
+        if (k == mz - 1) zp = pc;
+        const float y = 6.f * pc - (((((xm + xp) + ym) + yp) + zm) + zp);
+        const size_t e = idx3(i, j, k, mx, my);
+        pnew[e] = pc;
+        q[e] = y;
+        acc = fmaf(pc, y, acc);
+      }
+      __syncthreads();  // every thread is past plane lp-1's stage
+      const int nxt = lp - 1 + kTmaStages;
+      if (threadIdx.x == 0 && nxt < np) tma_issue_plane(a, mp, ring, base + nxt, x0, y0, z0 - 1 + nxt);
+    }
+  }
+  __syncthreads();  // the ring aliases the tile buffer used by later phases
+  return true;
+}
+
+// ---------------------------------------------------------------------------
 // Mixed-precision CG with FP64 refinement (persistent; pressure operator).
 //
 // One conjugate-gradient recurrence runs in FP32: the search direction p,
@@ -492,11 +634,21 @@ __global__ void __launch_bounds__(kSolveThreads) apply_poisson_kernel(GridDims g
 // update" form of iterative refinement).  Convergence is only ever declared
 // on the FP64 true residual: ||b - A x|| <= rtol ||b||.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSolveThreads) ir_kernel(IrArgs a) {
-  __shared__ double s_raw[kTileSlots];
+__global__ void __launch_bounds__(kSolveThreads, 4) ir_kernel(const __grid_constant__ IrArgs a) {
+  __shared__ __align__(128) double s_raw[kTileSlots];
   __shared__ double s_red[32 * 3];
+  __shared__ __align__(8) uint64_t s_full[kTmaStages];
   double* s64 = s_raw;
   float* s32 = reinterpret_cast<float*>(s_raw);
+  // the TMA ring aliases the tile buffer: the two are never live at once
+  TmaRing ring{s32, s32 + kTmaStages * kTmaSlabP, s_full, 0u};
+  if (a.use_tma) {
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < kTmaStages; ++s) mbar_init(&s_full[s], 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+  }
 
   const int mx = a.g.mx, my = a.g.my, mz = a.g.mz;
   const size_t n = size_t(mx) * my * mz;
@@ -589,7 +741,9 @@ __global__ void __launch_bounds__(kSolveThreads) ir_kernel(IrArgs a) {
       float* pnew = cur ? a.p1_32 : a.p0_32;
       const float* pold = cur ? a.p0_32 : a.p1_32;
       float fa[3] = {0.f, 0.f, 0.f};
-      {
+      if (a.use_tma) {
+        if (!dir_tma_f32(a, cur ? &a.map_p0 : &a.map_p1, float(beta), first, pnew, a.q32, fa[0], ring)) return fail();
+      } else {
         Source<float, kModeDir, 0> src{a.r32, pold, float(beta), first, nullptr, mx, my, mz};
         Sink<float> out{a.q32, pnew, nullptr, 0.f, false, kOpPressure, 0.f};
         stencil_tiles<float, kModeDir, 0>(ts, src, out, fa, s32);
@@ -603,13 +757,39 @@ __global__ void __launch_bounds__(kSolveThreads) ir_kernel(IrArgs a) {
         break;
       }
       const float alpha = float(rz / pq);
-      // phase U (FP32): x32 += alpha p, r32 -= alpha q, partial |r32|^2
+      // phase U (FP32): x32 += alpha p, r32 -= alpha q, partial |r32|^2;
+      // 16-byte vector accesses (the FP32 vectors are 256-byte aligned)
       float racc = 0.f;
-      for (size_t e = gtid(); e < n; e += gstride()) {
-        a.d32[e] = fmaf(alpha, pnew[e], a.d32[e]);
-        const float re = fmaf(-alpha, a.q32[e], a.r32[e]);
-        a.r32[e] = re;
-        racc = fmaf(re, re, racc);
+      {
+        const size_t n4 = n / 4;
+        const float4* p4 = reinterpret_cast<const float4*>(pnew);
+        const float4* q4 = reinterpret_cast<const float4*>(a.q32);
+        float4* d4 = reinterpret_cast<float4*>(a.d32);
+        float4* r4 = reinterpret_cast<float4*>(a.r32);
+        for (size_t e = gtid(); e < n4; e += gstride()) {
+          const float4 pv = p4[e], qv = q4[e];
+          float4 dv = d4[e], rv = r4[e];
+          dv.x = fmaf(alpha, pv.x, dv.x);
+          dv.y = fmaf(alpha, pv.y, dv.y);
+          dv.z = fmaf(alpha, pv.z, dv.z);
+          dv.w = fmaf(alpha, pv.w, dv.w);
+          rv.x = fmaf(-alpha, qv.x, rv.x);
+          rv.y = fmaf(-alpha, qv.y, rv.y);
+          rv.z = fmaf(-alpha, qv.z, rv.z);
+          rv.w = fmaf(-alpha, qv.w, rv.w);
+          d4[e] = dv;
+          r4[e] = rv;
+          racc = fmaf(rv.x, rv.x, racc);
+          racc = fmaf(rv.y, rv.y, racc);
+          racc = fmaf(rv.z, rv.z, racc);
+          racc = fmaf(rv.w, rv.w, racc);
+        }
+        for (size_t e = 4 * n4 + gtid(); e < n; e += gstride()) {
+          a.d32[e] = fmaf(alpha, pnew[e], a.d32[e]);
+          const float re = fmaf(-alpha, a.q32[e], a.r32[e]);
+          a.r32[e] = re;
+          racc = fmaf(re, re, racc);
+        }
       }
       acc[0] = racc;
       acc[1] = acc[2] = 0.0;
@@ -718,10 +898,15 @@ int variant_blocks_per_sm(int rtz) {
 }
 
 int cg_max_coresident_blocks(int kind_is_ir) {
-  (void)kind_is_ir;
   int best = 0;
   for (int rtz : {0, 1, 2, 4, 8}) {
     const int b = variant_blocks_per_sm(rtz);
+    best = b > best ? b : best;
+  }
+  if (kind_is_ir) {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ir_kernel, kSolveThreads, 0);
+    b = b > 8 ? 8 : b;
     best = b > best ? b : best;
   }
   return best * num_sms();
@@ -795,13 +980,49 @@ cudaError_t launch_apply_poisson(GridDims g, const double* x, double* y, int tz,
   return cudaGetLastError();
 }
 
+bool encode_f32_grid_map(CUtensorMap* map, const float* base, int mx, int my, int mz) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  });
+  // TMA: row stride a multiple of 16 bytes, 16-byte aligned base; the box is
+  // only used on grids at least as large as it
+  if (!encode || mx % 4 != 0 || mx < kTmaBoxW || my < kTmaBoxH || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+  cuuint64_t dims[3] = {cuuint64_t(mx), cuuint64_t(my), cuuint64_t(mz)};
+  cuuint64_t strides[2] = {cuuint64_t(mx) * 4, cuuint64_t(mx) * cuuint64_t(my) * 4};
+  cuuint32_t box[3] = {cuuint32_t(kTmaBoxW), cuuint32_t(kTmaBoxH), 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t launch_ir(const IrArgs& a_in, const LaunchGeom& lg, cudaStream_t s, int64_t* launches) {
   IrArgs a = a_in;
   const int sms = num_sms();
+  a.use_tma = 0;
+  if (!lg.no_tma && encode_f32_grid_map(&a.map_r32, a.r32, a.g.mx, a.g.my, a.g.mz) &&
+      encode_f32_grid_map(&a.map_p0, a.p0_32, a.g.mx, a.g.my, a.g.mz) &&
+      encode_f32_grid_map(&a.map_p1, a.p1_32, a.g.mx, a.g.my, a.g.mz)) {
+    a.use_tma = 1;
+    const int cols = ((a.g.mx + kTileX - 1) / kTileX) * ((a.g.my + kTileY - 1) / kTileY);
+    a.tma_zl = 8;
+    for (int zl = 64; zl >= 8; zl >>= 1)
+      if (cols * ((a.g.mz + zl - 1) / zl) >= 4 * sms) {
+        a.tma_zl = zl;
+        break;
+      }
+  }
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ir_kernel, kSolveThreads, 0);
-  per_sm = per_sm > 4 ? 4 : (per_sm < 1 ? 1 : per_sm);
-  int bps = lg.bps_req > 0 ? (lg.bps_req < per_sm ? lg.bps_req : per_sm) : per_sm;
+  per_sm = per_sm > 8 ? 8 : (per_sm < 1 ? 1 : per_sm);
+  int bps = lg.bps_req > 0 ? (lg.bps_req < per_sm ? lg.bps_req : per_sm) : (per_sm < 4 ? per_sm : 4);
   int tz = lg.tz_req;
   if (tz <= 0) {
     tz = 1;
