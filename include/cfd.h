@@ -213,6 +213,45 @@ int cfd_enable_timing(cfd_handle *h, int on);
 int cfd_phase_times(cfd_handle *h, double *ms_out, int64_t *calls_out);
 
 /* ---------------------------------------------------------------------------
+ * Batches of independent cavities (uneven sizes allowed) advanced together.
+ * Each cavity is a full cfd_handle living in its own slice of the batch
+ * workspace (set / read its fields through cfd_batch_cavity).  Per step the
+ * sweeps run per cavity, and each family of solves (diffusion of u, v, w;
+ * the pressure) is ONE cooperative persistent launch in which every cavity
+ * owns a contiguous range of blocks sized in proportion to cells^(4/3) and
+ * runs its own CG with its own reductions (cavities never wait on each
+ * other).  All cavities of a batch use the same solver.  The number of
+ * cavities is limited by the co-resident blocks of one launch (one block per
+ * cavity at least).  Ownership and errors as for single cavities; errors
+ * are described by cfd_batch_last_error. */
+typedef struct cfd_batch cfd_batch;
+
+int cfd_batch_workspace_bytes(int n, const cfd_params *per_cavity, size_t *bytes);
+int cfd_batch_create(int n, const cfd_params *per_cavity, void *dev_ws, size_t bytes, cfd_stream_t stream,
+                     cfd_batch **out);
+void cfd_batch_destroy(cfd_batch *b);
+const char *cfd_batch_last_error(const cfd_batch *b);
+
+/* The handle of cavity i (owned by the batch; do not destroy it). */
+cfd_handle *cfd_batch_cavity(cfd_batch *b, int i);
+
+/* Advance every cavity nsteps steps.  per_cavity (nullable, n entries)
+ * receives each cavity's solver statistics of the LAST step; when given the
+ * call synchronises and returns the worst status. */
+int cfd_batch_step(cfd_batch *b, int nsteps, cfd_solve_stats *per_cavity);
+
+/* on != 0: capture one whole batch step into a CUDA graph at the next
+ * cfd_batch_step and replay it for every later step (falls back to direct
+ * launches if the capture is not possible; see cfd_batch_graph_active). */
+int cfd_batch_use_graph(cfd_batch *b, int on);
+int cfd_batch_graph_active(const cfd_batch *b);
+
+/* Blocks of the batched launch `kind` (0..2 diffusion u, v, w; 3 pressure
+ * CG; 4 pressure IR) and kernel launches issued so far. */
+int cfd_batch_blocks(const cfd_batch *b, int kind, int *total_blocks);
+int64_t cfd_batch_launch_count(const cfd_batch *b);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free standalone pressure solve.  The paper has no counterpart:
  * this entry point exists for callers that may not allocate device memory
  * at all (code inside host callbacks, plug-ins whose host application owns

@@ -92,6 +92,16 @@ def load_library(path: Optional[str] = None):
                                                      ctypes.c_double, ctypes.c_int32, vp, P(cfd_solve_stats)]),
         "cfd_set_solver_shape": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
         "cfd_get_solver_shape": (ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]),
+        "cfd_batch_workspace_bytes": (ctypes.c_int, [ctypes.c_int, P(cfd_params), P(ctypes.c_size_t)]),
+        "cfd_batch_create": (ctypes.c_int, [ctypes.c_int, P(cfd_params), vp, ctypes.c_size_t, vp, P(vp)]),
+        "cfd_batch_destroy": (None, [vp]),
+        "cfd_batch_last_error": (ctypes.c_char_p, [vp]),
+        "cfd_batch_cavity": (vp, [vp, ctypes.c_int]),
+        "cfd_batch_step": (ctypes.c_int, [vp, ctypes.c_int, P(cfd_solve_stats)]),
+        "cfd_batch_use_graph": (ctypes.c_int, [vp, ctypes.c_int]),
+        "cfd_batch_graph_active": (ctypes.c_int, [vp]),
+        "cfd_batch_blocks": (ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_int)]),
+        "cfd_batch_launch_count": (ctypes.c_int64, [vp]),
         "cfd_enable_timing": (ctypes.c_int, [vp, ctypes.c_int]),
         "cfd_phase_times": (ctypes.c_int, [vp, P(ctypes.c_double), P(ctypes.c_int64)]),
     }
@@ -258,3 +268,85 @@ class Cavity:
         calls = (ctypes.c_int64 * len(PHASES))()
         self._check(self.lib.cfd_phase_times(self.h, ms, calls))
         return {name: (ms[i], int(calls[i])) for i, name in enumerate(PHASES)}
+
+
+class _CavityView(Cavity):
+    """A cavity owned by a Batch (no workspace or handle ownership)."""
+
+    def __init__(self, lib, handle, prm, device, stream):  # noqa: D401  (no Cavity.__init__)
+        self.lib = lib
+        self.h = handle
+        self.prm = prm
+        self.device = device
+        self.stream = stream
+
+    def close(self):
+        self.h = None
+
+
+class Batch:
+    """Independent cavities (uneven sizes allowed) advanced together; see
+    cfd_batch_* in include/cfd.h."""
+
+    def __init__(self, prms, stream=None, device=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (the library has no CPU path)")
+        self.lib = load_library()
+        self.prms = list(prms)
+        self.n = len(self.prms)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self._arr = (cfd_params * self.n)(*self.prms)
+        nb = ctypes.c_size_t(0)
+        rc = self.lib.cfd_batch_workspace_bytes(self.n, self._arr, ctypes.byref(nb))
+        if rc != CFD_OK:
+            raise CfdError(rc, self.lib.cfd_last_error(None).decode())
+        self.workspace = torch.empty(int(nb.value), dtype=torch.uint8, device=self.device)
+        self.stream = stream
+        b = ctypes.c_void_p(0)
+        rc = self.lib.cfd_batch_create(self.n, self._arr, ctypes.c_void_p(self.workspace.data_ptr()),
+                                       ctypes.c_size_t(int(nb.value)), ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(b))
+        if rc != CFD_OK:
+            raise CfdError(rc, self.lib.cfd_batch_last_error(None).decode())
+        self.b = b
+        self.cavities = [_CavityView(self.lib, ctypes.c_void_p(self.lib.cfd_batch_cavity(self.b, i)), self.prms[i],
+                                     self.device, stream) for i in range(self.n)]
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.cfd_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def cavity(self, i) -> Cavity:
+        return self.cavities[i]
+
+    def step(self, nsteps=1, stats=True):
+        if stats:
+            arr = (cfd_solve_stats * self.n)()
+            rc = self.lib.cfd_batch_step(self.b, int(nsteps), arr)
+            if rc not in (CFD_OK, CFD_ERR_NOT_CONVERGED, CFD_ERR_BREAKDOWN, CFD_ERR_TIMEOUT):
+                raise CfdError(rc, self.lib.cfd_batch_last_error(self.b).decode())
+            return rc, [arr[i].as_dict() for i in range(self.n)]
+        rc = self.lib.cfd_batch_step(self.b, int(nsteps), None)
+        if rc != CFD_OK:
+            raise CfdError(rc, self.lib.cfd_batch_last_error(self.b).decode())
+        return rc, None
+
+    def use_graph(self, on=True):
+        return self.lib.cfd_batch_use_graph(self.b, 1 if on else 0)
+
+    def graph_active(self) -> bool:
+        return bool(self.lib.cfd_batch_graph_active(self.b))
+
+    def blocks(self, kind):
+        v = ctypes.c_int()
+        self.lib.cfd_batch_blocks(self.b, int(kind), ctypes.byref(v))
+        return v.value
+
+    def launch_count(self) -> int:
+        return int(self.lib.cfd_batch_launch_count(self.b))

@@ -7,6 +7,7 @@
 // The library never allocates device memory: every array lives in the
 // caller's workspace, carved up by ws_layout below (256-byte aligned).
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -195,16 +196,15 @@ int tz_for(int mz) {
   return 0;
 }
 
-// Velocity diffusion solve for component comp (x = intermediate velocity).
-int run_diffusion(cfd_handle* h, int comp, DevSolveStats* st) {
-  PhysArgs pa = phys(h);
-  int rc = cuda_check(h, launch_diffusion_rhs(pa, comp, h->stream, &h->launches), "diffusion rhs");
-  if (rc) return rc;
+// Arguments of the backward-Euler diffusion solve of component comp on the
+// intermediate velocity (x0 = the advected field, b from diffusion_rhs).
+CgArgs diffusion_args(const cfd_handle* h, int comp, DevSolveStats* st, SolveCtrl* ctrl) {
+  const double hh = h->prm.length / h->prm.nx;
   CgArgs a{};
   a.g = GridDims{h->prm.nx + (comp == 0), h->prm.ny + (comp == 1), h->prm.nz + (comp == 2)};
   a.kind = kOpVelU + comp;
   a.precond = 0;
-  a.c = h->prm.nu * h->prm.dt / (pa.h * pa.h);
+  a.c = h->prm.nu * h->prm.dt / (hh * hh);
   a.x = comp == 0 ? h->ua : (comp == 1 ? h->va : h->wa);
   a.b = h->b; a.r = h->r; a.d0 = h->d0; a.d1 = h->d1; a.q = h->q;
   a.zero_x0 = 0; a.remove_mean = 0; a.gauge = 0; a.gauge_value = 0.0;
@@ -212,38 +212,15 @@ int run_diffusion(cfd_handle* h, int comp, DevSolveStats* st) {
   a.max_iters = iter_cap(h->prm);
   a.max_restarts = kMaxRestarts;
   a.timeout_ns = kTimeoutNs;
-  a.ctrl = h->ctrl; a.partials = h->partials; a.stats = st;
+  a.ctrl = ctrl; a.partials = h->partials; a.stats = st;
   a.tz = tz_for(a.g.mz);
-  rc = cuda_check(h, cudaMemsetAsync(h->ctrl, 0, sizeof(SolveCtrl), h->stream), "memset ctrl");
-  if (rc) return rc;
-  return cuda_check(h, launch_cg(a, h->lg, h->stream, &h->launches), "diffusion CG launch");
+  return a;
 }
 
-// Pressure solve A x = b on the handle's workspace b (already filled).
-int run_pressure(cfd_handle* h, double* x, int zero_x0, int gauge, DevSolveStats* st) {
-  int rc = cuda_check(h, cudaMemsetAsync(h->ctrl, 0, sizeof(SolveCtrl), h->stream), "memset ctrl");
-  if (rc) return rc;
-  GridDims g{h->prm.nx, h->prm.ny, h->prm.nz};
-  if (h->prm.solver == CFD_SOLVER_IR) {
-    IrArgs a{};
-    a.g = g;
-    a.x = x; a.b = h->b; a.r = h->r;
-    a.r32 = h->r32; a.d32 = h->d32; a.p0_32 = h->p0_32; a.p1_32 = h->p1_32; a.q32 = h->q32;
-    a.zero_x0 = zero_x0; a.remove_mean = 1; a.gauge = gauge; a.gauge_value = 1.0;
-    a.rtol = h->prm.rtol;
-    a.delta = h->prm.ir_delta > 0 ? h->prm.ir_delta : 0.1;
-    a.max_iters = iter_cap(h->prm);
-    a.max_outer = 1000;
-    a.timeout_ns = kTimeoutNs;
-    a.ctrl = h->ctrl; a.partials = h->partials; a.stats = st;
-    a.tz = tz_for(g.mz);
-    const int t = phase_begin(h, CFD_PHASE_PCG);
-    rc = cuda_check(h, launch_ir(a, h->lg, h->stream, &h->launches), "IR launch");
-    phase_end(h, t);
-    return rc;
-  }
+// Arguments of the FP64 pressure CG (or Jacobi PCG) on the workspace b.
+CgArgs pressure_cg_args(const cfd_handle* h, double* x, int zero_x0, int gauge, DevSolveStats* st, SolveCtrl* ctrl) {
   CgArgs a{};
-  a.g = g;
+  a.g = GridDims{h->prm.nx, h->prm.ny, h->prm.nz};
   a.kind = kOpPressure;
   a.precond = h->prm.solver == CFD_SOLVER_JACOBI ? 1 : 0;
   a.c = 0.0;
@@ -253,8 +230,51 @@ int run_pressure(cfd_handle* h, double* x, int zero_x0, int gauge, DevSolveStats
   a.max_iters = iter_cap(h->prm);
   a.max_restarts = kMaxRestarts;
   a.timeout_ns = kTimeoutNs;
-  a.ctrl = h->ctrl; a.partials = h->partials; a.stats = st;
-  a.tz = tz_for(g.mz);
+  a.ctrl = ctrl; a.partials = h->partials; a.stats = st;
+  a.tz = tz_for(a.g.mz);
+  return a;
+}
+
+// Arguments of the FP32-CG / FP64-refinement pressure solve.
+IrArgs pressure_ir_args(const cfd_handle* h, double* x, int zero_x0, int gauge, DevSolveStats* st, SolveCtrl* ctrl) {
+  IrArgs a{};
+  a.g = GridDims{h->prm.nx, h->prm.ny, h->prm.nz};
+  a.x = x; a.b = h->b; a.r = h->r;
+  a.r32 = h->r32; a.d32 = h->d32; a.p0_32 = h->p0_32; a.p1_32 = h->p1_32; a.q32 = h->q32;
+  a.zero_x0 = zero_x0; a.remove_mean = 1; a.gauge = gauge; a.gauge_value = 1.0;
+  a.rtol = h->prm.rtol;
+  a.delta = h->prm.ir_delta > 0 ? h->prm.ir_delta : 0.1;
+  a.max_iters = iter_cap(h->prm);
+  a.max_outer = 1000;
+  a.timeout_ns = kTimeoutNs;
+  a.ctrl = ctrl; a.partials = h->partials; a.stats = st;
+  a.tz = tz_for(a.g.mz);
+  return a;
+}
+
+// Velocity diffusion solve for component comp (x = intermediate velocity).
+int run_diffusion(cfd_handle* h, int comp, DevSolveStats* st) {
+  PhysArgs pa = phys(h);
+  int rc = cuda_check(h, launch_diffusion_rhs(pa, comp, h->stream, &h->launches), "diffusion rhs");
+  if (rc) return rc;
+  const CgArgs a = diffusion_args(h, comp, st, h->ctrl);
+  rc = cuda_check(h, cudaMemsetAsync(h->ctrl, 0, sizeof(SolveCtrl), h->stream), "memset ctrl");
+  if (rc) return rc;
+  return cuda_check(h, launch_cg(a, h->lg, h->stream, &h->launches), "diffusion CG launch");
+}
+
+// Pressure solve A x = b on the handle's workspace b (already filled).
+int run_pressure(cfd_handle* h, double* x, int zero_x0, int gauge, DevSolveStats* st) {
+  int rc = cuda_check(h, cudaMemsetAsync(h->ctrl, 0, sizeof(SolveCtrl), h->stream), "memset ctrl");
+  if (rc) return rc;
+  if (h->prm.solver == CFD_SOLVER_IR) {
+    const IrArgs a = pressure_ir_args(h, x, zero_x0, gauge, st, h->ctrl);
+    const int t = phase_begin(h, CFD_PHASE_PCG);
+    rc = cuda_check(h, launch_ir(a, h->lg, h->stream, &h->launches), "IR launch");
+    phase_end(h, t);
+    return rc;
+  }
+  const CgArgs a = pressure_cg_args(h, x, zero_x0, gauge, st, h->ctrl);
   const int t = phase_begin(h, CFD_PHASE_PCG);
   rc = cuda_check(h, launch_cg(a, h->lg, h->stream, &h->launches), "pressure CG launch");
   phase_end(h, t);
@@ -626,6 +646,345 @@ int cfd_phase_times(cfd_handle* h, double* ms_out, int64_t* calls_out) {
   }
   return CFD_OK;
 }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches of independent cavities.
+//
+// Every cavity keeps its own handle and workspace slice.  The sweeps run as
+// one launch per cavity; each family of solves (diffusion of u, of v, of w,
+// and the pressure) runs as ONE cooperative persistent launch in which
+// cavity i owns a contiguous range of blocks, sized in proportion to
+// cells^(4/3) (CG work grows like cells x N), with its own control block and
+// all-reduces, so cavities never wait on each other.  A whole step can be
+// captured once into a CUDA graph and replayed.
+// ---------------------------------------------------------------------------
+struct cfd_batch {
+  int n;
+  cudaStream_t stream;
+  char* ws;
+  size_t bytes;
+  std::vector<cfd_handle*> cav;
+  int solver;
+  // device tables inside the batch workspace
+  CgArgs* d_cg;            // [4][n]: diffusion u, v, w (first nd entries), pressure CG
+  IrArgs* d_ir;            // [n]
+  int* d_starts;           // [5][n + 1]
+  SolveCtrl* d_ctrl;       // [4][n]
+  DevSolveStats* d_stats;  // [4][n]
+  std::vector<int> diff_idx;  // cavities with nu > 0
+  int total_blocks[5];
+  int precond;
+  int64_t launches;
+  bool use_graph;
+  bool graph_ok;
+  cudaGraphExec_t graph;
+  int64_t graph_launches;  // kernel launches per replay
+  char err[256];
+};
+
+namespace {
+
+struct BatchLayout {
+  size_t cg, ir, starts, ctrl, stats, cav0;
+  std::vector<size_t> cav;
+  size_t total;
+};
+
+BatchLayout batch_layout(int n, const cfd_params* prm) {
+  BatchLayout L;
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    const size_t o = off;
+    off = align256(off + b);
+    return o;
+  };
+  L.cg = take(sizeof(CgArgs) * 4 * size_t(n));
+  L.ir = take(sizeof(IrArgs) * size_t(n));
+  L.starts = take(sizeof(int) * 5 * size_t(n + 1));
+  L.ctrl = take(sizeof(SolveCtrl) * 4 * size_t(n));
+  L.stats = take(sizeof(DevSolveStats) * 4 * size_t(n));
+  L.cav0 = off;
+  for (int i = 0; i < n; ++i) L.cav.push_back(take(ws_layout(prm[i], kMaxBlocksBound).total));
+  L.total = off;
+  return L;
+}
+
+int batch_err(cfd_batch* b, int code, const char* fmt, ...) {
+  char buf[256];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (b) std::memcpy(b->err, buf, sizeof(buf));
+  std::memcpy(g_last_error, buf, sizeof(buf));
+  return code;
+}
+
+// Split `total` blocks over problems in proportion to weight (at least one
+// each); returns prefix starts (size n + 1) or an empty vector if n > total.
+std::vector<int> split_blocks(const std::vector<double>& w, int total) {
+  const int n = int(w.size());
+  std::vector<int> starts(size_t(n) + 1, 0);
+  if (n == 0) return starts;
+  if (n > total) return {};
+  double W = 0.0;
+  for (double x : w) W += x;
+  std::vector<int> nb = std::vector<int>(static_cast<size_t>(n));
+  int sum = 0;
+  for (int i = 0; i < n; ++i) {
+    nb[size_t(i)] = std::max(1, int(double(total) * w[size_t(i)] / W));
+    sum += nb[size_t(i)];
+  }
+  while (sum > total) {  // trim the largest allocations
+    int k = 0;
+    for (int i = 1; i < n; ++i)
+      if (nb[size_t(i)] > nb[size_t(k)]) k = i;
+    if (nb[size_t(k)] <= 1) return {};
+    --nb[size_t(k)];
+    --sum;
+  }
+  for (int i = 0; i < n; ++i) starts[size_t(i) + 1] = starts[size_t(i)] + nb[size_t(i)];
+  return starts;
+}
+
+// Enqueue one step of every cavity.
+int batch_enqueue_step(cfd_batch* b) {
+  const int n = b->n;
+  int rc = CFD_OK;
+  auto ck = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && rc == CFD_OK) rc = batch_err(b, CFD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return rc == CFD_OK;
+  };
+  for (int i = 0; i < n && rc == CFD_OK; ++i) {
+    cfd_handle* h = b->cav[size_t(i)];
+    PhysArgs pa = phys(h);
+    if (h->prm.g[0] != 0.0 || h->prm.g[1] != 0.0 || h->prm.g[2] != 0.0) ck(launch_forces(pa, b->stream, &b->launches), "forces");
+    ck(launch_advect(pa, b->stream, &b->launches), "advect");
+  }
+  const int nd = int(b->diff_idx.size());
+  for (int c = 0; c < 3 && nd > 0 && rc == CFD_OK; ++c) {
+    for (int k = 0; k < nd; ++k) ck(launch_diffusion_rhs(phys(b->cav[size_t(b->diff_idx[size_t(k)])]), c, b->stream, &b->launches), "diffusion rhs");
+    ck(cudaMemsetAsync(b->d_ctrl + size_t(c) * n, 0, sizeof(SolveCtrl) * size_t(nd), b->stream), "memset ctrl");
+    ck(launch_cg_multi(b->d_cg + size_t(c) * n, b->d_starts + size_t(c) * (n + 1), nd, b->total_blocks[c], 0, b->stream,
+                       &b->launches),
+       "batched diffusion launch");
+  }
+  for (int i = 0; i < n && rc == CFD_OK; ++i) ck(launch_divergence(phys(b->cav[size_t(i)]), b->stream, &b->launches), "divergence");
+  ck(cudaMemsetAsync(b->d_ctrl + size_t(3) * n, 0, sizeof(SolveCtrl) * size_t(n), b->stream), "memset ctrl");
+  if (b->solver == CFD_SOLVER_IR)
+    ck(launch_ir_multi(b->d_ir, b->d_starts + size_t(4) * (n + 1), n, b->total_blocks[4], b->stream, &b->launches),
+       "batched pressure launch");
+  else
+    ck(launch_cg_multi(b->d_cg + size_t(3) * n, b->d_starts + size_t(3) * (n + 1), n, b->total_blocks[3], b->precond,
+                       b->stream, &b->launches),
+       "batched pressure launch");
+  for (int i = 0; i < n && rc == CFD_OK; ++i) ck(launch_correct(phys(b->cav[size_t(i)]), b->stream, &b->launches), "correct");
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cfd_batch_workspace_bytes(int n, const cfd_params* per_cavity, size_t* bytes) {
+  if (n < 1 || !per_cavity || !bytes) return batch_err(nullptr, CFD_ERR_INVALID_ARG, "n >= 1, params and bytes required");
+  for (int i = 0; i < n; ++i) {
+    int rc = validate(&per_cavity[i]);
+    if (rc) return rc;
+  }
+  *bytes = batch_layout(n, per_cavity).total;
+  return CFD_OK;
+}
+
+int cfd_batch_create(int n, const cfd_params* per_cavity, void* dev_ws, size_t bytes, cfd_stream_t stream,
+                     cfd_batch** out) {
+  if (!out) return batch_err(nullptr, CFD_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  size_t need = 0;
+  int rc = cfd_batch_workspace_bytes(n, per_cavity, &need);
+  if (rc) return rc;
+  if (!dev_ws || (reinterpret_cast<uintptr_t>(dev_ws) & 255))
+    return batch_err(nullptr, CFD_ERR_INVALID_ARG, "workspace NULL or not 256-byte aligned");
+  if (bytes < need) return batch_err(nullptr, CFD_ERR_WORKSPACE_TOO_SMALL, "batch workspace %zu < %zu", bytes, need);
+  const int solver = per_cavity[0].solver;
+  for (int i = 1; i < n; ++i)
+    if (per_cavity[i].solver != solver) return batch_err(nullptr, CFD_ERR_INVALID_ARG, "all cavities of a batch use one solver");
+  const BatchLayout L = batch_layout(n, per_cavity);
+  cfd_batch* b = new (std::nothrow) cfd_batch();
+  if (!b) return batch_err(nullptr, CFD_ERR_INVALID_ARG, "out of host memory");
+  b->n = n;
+  b->stream = reinterpret_cast<cudaStream_t>(stream);
+  b->ws = static_cast<char*>(dev_ws);
+  b->bytes = bytes;
+  b->solver = solver;
+  b->precond = solver == CFD_SOLVER_JACOBI ? 1 : 0;
+  b->d_cg = reinterpret_cast<CgArgs*>(b->ws + L.cg);
+  b->d_ir = reinterpret_cast<IrArgs*>(b->ws + L.ir);
+  b->d_starts = reinterpret_cast<int*>(b->ws + L.starts);
+  b->d_ctrl = reinterpret_cast<SolveCtrl*>(b->ws + L.ctrl);
+  b->d_stats = reinterpret_cast<DevSolveStats*>(b->ws + L.stats);
+  std::snprintf(b->err, sizeof(b->err), "no error");
+  auto fail = [&](int code) {
+    for (cfd_handle* h : b->cav) cfd_destroy(h);
+    delete b;
+    return code;
+  };
+  for (int i = 0; i < n; ++i) {
+    cfd_handle* h = nullptr;
+    rc = cfd_create(&per_cavity[i], b->ws + L.cav[size_t(i)], L.cav.size() > size_t(i) + 1 ? L.cav[size_t(i) + 1] - L.cav[size_t(i)]
+                                                                                            : L.total - L.cav[size_t(i)],
+                    stream, &h);
+    if (rc) return fail(rc);
+    b->cav.push_back(h);
+    if (per_cavity[i].nu > 0.0) b->diff_idx.push_back(i);
+  }
+  // block split and solve tables
+  const int sms = batch_num_sms();
+  std::vector<CgArgs> cg(4 * size_t(n));
+  std::vector<IrArgs> ir = std::vector<IrArgs>(static_cast<size_t>(n));
+  std::vector<int> starts(5 * size_t(n + 1), 0);
+  auto weights = [&](const std::vector<int>& idx, int comp) {
+    std::vector<double> w;
+    for (int i : idx) {
+      const cfd_params& p = per_cavity[i];
+      const double cells = double(p.nx + (comp == 0)) * double(p.ny + (comp == 1)) * double(p.nz + (comp == 2));
+      w.push_back(std::pow(cells, 4.0 / 3.0));
+    }
+    return w;
+  };
+  std::vector<int> all = std::vector<int>(static_cast<size_t>(n));
+  for (int i = 0; i < n; ++i) all[size_t(i)] = i;
+  for (int kind = 0; kind < 5; ++kind) {
+    const bool is_ir = kind == 4;
+    const std::vector<int>& idx = kind < 3 ? b->diff_idx : all;
+    const int total = batch_blocks_per_sm(is_ir) * sms;
+    std::vector<int> st = split_blocks(weights(idx, kind < 3 ? kind : 3), total);
+    if (st.empty()) {
+      rc = batch_err(nullptr, CFD_ERR_INVALID_ARG, "%zu cavities exceed the %d co-resident blocks of one launch", idx.size(), total);
+      return fail(rc);
+    }
+    b->total_blocks[kind] = st.back();
+    for (size_t k = 0; k < st.size(); ++k) starts[size_t(kind) * (n + 1) + k] = st[k];
+    for (size_t k = 0; k < idx.size(); ++k) {
+      cfd_handle* h = b->cav[size_t(idx[k])];
+      const int nbk = st[k + 1] - st[k];
+      if (kind < 3) {
+        CgArgs a = diffusion_args(h, kind, b->d_stats + size_t(kind) * n + size_t(idx[k]), b->d_ctrl + size_t(kind) * n + k);
+        a.tz = solve_tile_depth_for(a.g, nbk);
+        cg[size_t(kind) * n + k] = a;
+      } else if (kind == 3) {
+        CgArgs a = pressure_cg_args(h, h->p, h->prm.warm_start ? 0 : 1, 1, b->d_stats + size_t(3) * n + k, b->d_ctrl + size_t(3) * n + k);
+        a.tz = solve_tile_depth_for(a.g, nbk);
+        cg[size_t(3) * n + k] = a;
+      } else {
+        IrArgs a = pressure_ir_args(h, h->p, h->prm.warm_start ? 0 : 1, 1, b->d_stats + size_t(3) * n + k, b->d_ctrl + size_t(3) * n + k);
+        a.tz = solve_tile_depth_for(a.g, nbk);
+        a.use_tma = 0;
+        ir[k] = a;
+      }
+    }
+  }
+  rc = cuda_check(nullptr, cudaMemcpyAsync(b->d_cg, cg.data(), sizeof(CgArgs) * cg.size(), cudaMemcpyHostToDevice, b->stream), "copy tables");
+  if (!rc) rc = cuda_check(nullptr, cudaMemcpyAsync(b->d_ir, ir.data(), sizeof(IrArgs) * ir.size(), cudaMemcpyHostToDevice, b->stream), "copy tables");
+  if (!rc) rc = cuda_check(nullptr, cudaMemcpyAsync(b->d_starts, starts.data(), sizeof(int) * starts.size(), cudaMemcpyHostToDevice, b->stream), "copy tables");
+  if (!rc) rc = cuda_check(nullptr, cudaMemsetAsync(b->d_stats, 0, sizeof(DevSolveStats) * 4 * size_t(n), b->stream), "memset stats");
+  if (!rc) rc = cuda_check(nullptr, cudaStreamSynchronize(b->stream), "synchronize");
+  if (rc) return fail(rc);
+  *out = b;
+  return CFD_OK;
+}
+
+void cfd_batch_destroy(cfd_batch* b) {
+  if (!b) return;
+  if (b->graph_ok) cudaGraphExecDestroy(b->graph);
+  for (cfd_handle* h : b->cav) cfd_destroy(h);
+  delete b;
+}
+
+const char* cfd_batch_last_error(const cfd_batch* b) { return b ? b->err : g_last_error; }
+
+cfd_handle* cfd_batch_cavity(cfd_batch* b, int i) {
+  if (!b || i < 0 || i >= b->n) return nullptr;
+  return b->cav[size_t(i)];
+}
+
+int cfd_batch_blocks(const cfd_batch* b, int kind, int* total_blocks) {
+  if (!b || kind < 0 || kind > 4 || !total_blocks) return batch_err(nullptr, CFD_ERR_INVALID_ARG, "bad arguments");
+  *total_blocks = b->total_blocks[kind];
+  return CFD_OK;
+}
+
+int cfd_batch_use_graph(cfd_batch* b, int on) {
+  if (!b) return batch_err(nullptr, CFD_ERR_INVALID_ARG, "batch is NULL");
+  b->use_graph = on != 0;
+  return CFD_OK;
+}
+
+int cfd_batch_step(cfd_batch* b, int nsteps, cfd_solve_stats* per_cavity) {
+  if (!b) return batch_err(nullptr, CFD_ERR_INVALID_ARG, "batch is NULL");
+  if (nsteps < 0) return batch_err(b, CFD_ERR_INVALID_ARG, "nsteps must be >= 0");
+  int rc = CFD_OK;
+  if (b->use_graph && !b->graph_ok && nsteps > 0) {
+    // capture one step once; replay it afterwards
+    // (captured on a private stream: the caller's may be the legacy default
+    // stream, which cannot be captured; the graph is launched on the caller's)
+    cudaGraph_t g = nullptr;
+    const int64_t l0 = b->launches;
+    cudaStream_t user = b->stream, cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      b->stream = cs;
+      const int erc = batch_enqueue_step(b);
+      b->stream = user;
+      e = cudaStreamEndCapture(cs, &g);
+      if (erc == CFD_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(&b->graph, g, 0);
+      if (erc == CFD_OK && e == cudaSuccess && g) {
+        b->graph_ok = true;
+        b->graph_launches = b->launches - l0;
+      }
+      if (g) cudaGraphDestroy(g);
+    }
+    if (cs) cudaStreamDestroy(cs);
+    b->launches = l0;
+    if (!b->graph_ok) {
+      batch_err(b, CFD_OK, "graph capture not possible (%s); using direct launches", cudaGetErrorString(e));
+      b->use_graph = false;
+    }
+    cudaGetLastError();
+  }
+  for (int s = 0; s < nsteps && rc == CFD_OK; ++s) {
+    if (b->graph_ok) {
+      const cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+      if (e != cudaSuccess) rc = batch_err(b, CFD_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
+      b->launches += b->graph_launches;
+    } else {
+      rc = batch_enqueue_step(b);
+    }
+  }
+  if (rc || !per_cavity) return rc;
+  std::vector<DevSolveStats> st(4 * size_t(b->n));
+  rc = cuda_check(nullptr, cudaMemcpyAsync(st.data(), b->d_stats, sizeof(DevSolveStats) * st.size(), cudaMemcpyDeviceToHost, b->stream), "copy stats");
+  if (!rc) rc = cuda_check(nullptr, cudaStreamSynchronize(b->stream), "synchronize");
+  if (rc) return batch_err(b, rc, "%s", g_last_error);
+  int status = CFD_OK;
+  for (int i = 0; i < b->n; ++i) {
+    DevStepStats d{};
+    d.p = st[size_t(3) * b->n + size_t(i)];
+    for (int c = 0; c < 3; ++c) d.d[c] = st[size_t(c) * b->n + size_t(i)];
+    to_public(d, &per_cavity[i]);
+    status = worst(status, d.p.status);
+    for (int c = 0; c < 3; ++c) status = worst(status, d.d[c].status);
+  }
+  if (status != CFD_OK) batch_err(b, status, "solver status %d in the batch", status);
+  return status;
+}
+
+int64_t cfd_batch_launch_count(const cfd_batch* b) { return b ? b->launches : 0; }
+
+int cfd_batch_graph_active(const cfd_batch* b) { return b && b->graph_ok ? 1 : 0; }
 
 }  // extern "C"
 

@@ -166,14 +166,22 @@ __device__ __forceinline__ bool wait_counter(SolveCtrl* ctrl, const unsigned int
 // Every wait is bounded (wait_counter).  `round` is the caller's per-block
 // count of completed all-reduces (identical in every block).
 // ---------------------------------------------------------------------------
+// The blocks of one problem inside a (possibly multi-problem) launch: this
+// block's index among them and their count.  Independent problems of one
+// launch never synchronise with each other.
+struct VBlock {
+  int bid;
+  int nb;
+};
+
 template <int NV>
 __device__ bool grid_allreduce(double (&v)[NV], double (&out)[NV], SolveCtrl* ctrl, double* partials,
-                               double* scratch, unsigned long long timeout_ns, unsigned int& round) {
+                               double* scratch, unsigned long long timeout_ns, unsigned int& round, VBlock vb) {
   __shared__ int s_ok;
   __shared__ int s_last;
   __shared__ double s_bcast[kMaxPartials];
   block_reduce<NV>(v, scratch);
-  const unsigned int G = gridDim.x;
+  const unsigned int G = unsigned(vb.nb);
   const unsigned int r = round++;
   double* buf = partials + size_t(r & 1u) * G * kMaxPartials;
   double acc[NV];
@@ -183,7 +191,7 @@ __device__ bool grid_allreduce(double (&v)[NV], double (&out)[NV], SolveCtrl* ct
   if (G <= unsigned(kFlatMaxBlocks)) {
     if (threadIdx.x == 0) {
 #pragma unroll
-      for (int a = 0; a < NV; ++a) buf[size_t(blockIdx.x) * kMaxPartials + a] = v[a];
+      for (int a = 0; a < NV; ++a) buf[size_t(vb.bid) * kMaxPartials + a] = v[a];
       red_add_release_gpu(&ctrl->arrive, 1u);
       s_ok = wait_counter(ctrl, &ctrl->arrive, (r + 1u) * G, timeout_ns) ? 1 : 0;
     }
@@ -195,13 +203,13 @@ __device__ bool grid_allreduce(double (&v)[NV], double (&out)[NV], SolveCtrl* ct
     }
   } else {
     const unsigned int ngroups = (G + kGroupSize - 1) / kGroupSize;
-    const unsigned int g = blockIdx.x / kGroupSize;
+    const unsigned int g = unsigned(vb.bid) / kGroupSize;
     const unsigned int g0 = g * kGroupSize;
     const unsigned int gsize = (G - g0) < unsigned(kGroupSize) ? (G - g0) : unsigned(kGroupSize);
     double* gbuf = partials + 2 * size_t(G) * kMaxPartials + size_t(r & 1u) * kMaxGroups * kMaxPartials;
     if (threadIdx.x == 0) {
 #pragma unroll
-      for (int a = 0; a < NV; ++a) buf[size_t(blockIdx.x) * kMaxPartials + a] = v[a];
+      for (int a = 0; a < NV; ++a) buf[size_t(vb.bid) * kMaxPartials + a] = v[a];
       const unsigned int old = atom_add_acq_rel_gpu(&ctrl->group[g], 1u);
       s_last = (old == (r + 1u) * gsize - 1u) ? 1 : 0;
     }

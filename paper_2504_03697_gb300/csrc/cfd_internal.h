@@ -139,6 +139,19 @@ cudaError_t launch_fill(double* p, size_t n, double value, cudaStream_t s, int64
 // Co-resident block count for the persistent solve kernels on this device.
 int cg_max_coresident_blocks(int kind_is_ir);
 
+// Multi-problem persistent solves: problem p owns blocks d_starts[p] ..
+// d_starts[p+1] of a cooperative grid of total_blocks = d_starts[nprob]
+// blocks; problems never synchronise with each other.  Tables live in device
+// memory.  Memory path only (per-problem runtime tile depth), no TMA.
+cudaError_t launch_cg_multi(const CgArgs* d_table, const int* d_starts, int nprob, int total_blocks, int precond,
+                            cudaStream_t s, int64_t* launches);
+cudaError_t launch_ir_multi(const IrArgs* d_table, const int* d_starts, int nprob, int total_blocks, cudaStream_t s,
+                            int64_t* launches);
+int batch_blocks_per_sm(int ir);
+int batch_num_sms();
+// Deepest tile depth that still gives `blocks` blocks two tiles each.
+int solve_tile_depth_for(GridDims g, int blocks);
+
 // Stencil tile depth (cells per thread along z) used for a grid of mz planes.
 int solve_tile_depth(int mz);
 

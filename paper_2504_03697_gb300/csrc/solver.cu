@@ -188,11 +188,11 @@ __device__ __forceinline__ T row_from_smem(const Sink<T>& out, const T* s, int c
 // or sum(r) (no preconditioner)}.
 template <typename T, int MODE, int PRECOND>
 __device__ void stencil_tiles(const TileShape& ts, const Source<T, MODE, PRECOND>& src, const Sink<T>& out,
-                              T (&acc)[3], T* s) {
+                              T (&acc)[3], T* s, VBlock vb) {
   const int tx = threadIdx.x % kTileX, ty = threadIdx.x / kTileX;
   const int mx = ts.mx, my = ts.my, mz = ts.mz;
   const int ntiles = ts.count();
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  for (int t = vb.bid; t < ntiles; t += vb.nb) {
     int x0, y0, z0;
     load_tile<T, MODE, PRECOND>(ts, t, src, s, x0, y0, z0);
     const int i = x0 + tx, j = y0 + ty;
@@ -231,13 +231,13 @@ __device__ void stencil_tiles(const TileShape& ts, const Source<T, MODE, PRECOND
 template <int RTZ, int PRECOND>
 __device__ void dir_tiles_reg(const TileShape& ts, const Source<double, kModeDir, PRECOND>& src, double* pnew,
                               const Sink<double>& out, double (&acc)[3], double* s, double (&preg)[kRegCells],
-                              double (&qreg)[kRegCells]) {
+                              double (&qreg)[kRegCells], VBlock vb) {
   const int tx = threadIdx.x % kTileX, ty = threadIdx.x / kTileX;
   const int mx = ts.mx, my = ts.my, mz = ts.mz;
   const int ntiles = ts.count();
 #pragma unroll
   for (int kt = 0; kt < kRegCells / RTZ; ++kt) {
-    const int t = blockIdx.x + kt * gridDim.x;
+    const int t = vb.bid + kt * vb.nb;
     if (t >= ntiles) break;
     int x0, y0, z0;
     load_tile<double, kModeDir, PRECOND>(ts, t, src, s, x0, y0, z0);
@@ -263,13 +263,14 @@ __device__ void dir_tiles_reg(const TileShape& ts, const Source<double, kModeDir
 // Register-path phase U over the same own cells.
 template <int RTZ, int PRECOND>
 __device__ void update_reg(const TileShape& ts, double alpha, double* x, double* r, const double* invd,
-                           double (&acc)[3], const double (&preg)[kRegCells], const double (&qreg)[kRegCells]) {
+                           double (&acc)[3], const double (&preg)[kRegCells], const double (&qreg)[kRegCells],
+                           VBlock vb) {
   const int tx = threadIdx.x % kTileX, ty = threadIdx.x / kTileX;
   const int mx = ts.mx, my = ts.my, mz = ts.mz;
   const int ntiles = ts.count();
 #pragma unroll
   for (int kt = 0; kt < kRegCells / RTZ; ++kt) {
-    const int t = blockIdx.x + kt * gridDim.x;
+    const int t = vb.bid + kt * vb.nb;
     if (t >= ntiles) break;
     const int bx = t % ts.ntx;
     const int rest = t / ts.ntx;
@@ -291,15 +292,38 @@ __device__ void update_reg(const TileShape& ts, double alpha, double* x, double*
   }
 }
 
-__device__ __forceinline__ size_t gtid() { return size_t(blockIdx.x) * blockDim.x + threadIdx.x; }
-__device__ __forceinline__ size_t gstride() { return size_t(gridDim.x) * blockDim.x; }
+// Multi-problem launches: starts[p] .. starts[p+1] are problem p's blocks.
+// Returns this block's problem (0 for a single-problem launch, -1 for a
+// block past the last problem) and narrows vb to that problem's blocks.
+__device__ __forceinline__ int find_problem(const int* starts, int nprob, VBlock& vb) {
+  if (nprob <= 0) return 0;
+  const int b = int(blockIdx.x);
+  if (b >= starts[nprob]) return -1;
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (starts[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  vb.bid = b - starts[lo];
+  vb.nb = starts[lo + 1] - starts[lo];
+  return lo;
+}
+
+__device__ __forceinline__ size_t gtid(VBlock vb) { return size_t(vb.bid) * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ size_t gstride(VBlock vb) { return size_t(vb.nb) * blockDim.x; }
 
 // ---------------------------------------------------------------------------
 // Persistent FP64 (P)CG.  PRECOND: 0 none, 1 Jacobi.  RTZ: 0 memory path
 // (runtime tile depth a.tz), else register path with tile depth RTZ.
 // ---------------------------------------------------------------------------
-template <int PRECOND, int RTZ>
-__global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(CgArgs a) {
+template <int PRECOND, int RTZ, bool MULTI>
+__global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(const __grid_constant__ CgArgs a0, const CgArgs* table,
+                                                                const int* starts, int nprob) {
+  VBlock vb{int(blockIdx.x), int(gridDim.x)};
+  const int prob = MULTI ? find_problem(starts, nprob, vb) : 0;
+  if (prob < 0) return;
+  const CgArgs& a = MULTI ? table[prob] : a0;
   __shared__ double s_tile[kTileSlots];
   __shared__ double s_red[32 * 3];
   __shared__ double s_invd[8];
@@ -320,7 +344,7 @@ __global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(CgArgs a) {
     }
   };
   auto allreduce = [&](double (&v)[3], double (&o)[3]) {
-    return grid_allreduce<3>(v, o, a.ctrl, a.partials, s_red, a.timeout_ns, round);
+    return grid_allreduce<3>(v, o, a.ctrl, a.partials, s_red, a.timeout_ns, round, vb);
   };
 
   double acc[3], tot[3];
@@ -330,7 +354,7 @@ __global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(CgArgs a) {
   double shift = 0.0;
   if (a.remove_mean) {
     acc[0] = acc[1] = acc[2] = 0.0;
-    for (size_t e = gtid(); e < n; e += gstride()) acc[0] += a.b[e];
+    for (size_t e = gtid(vb); e < n; e += gstride(vb)) acc[0] += a.b[e];
     if (!allreduce(acc, tot)) return fail();
     shift = tot[0] / double(n);
   }
@@ -338,7 +362,7 @@ __global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(CgArgs a) {
   // ---- initial residual r = b - A x0 ----
   acc[0] = acc[1] = acc[2] = 0.0;
   if (a.zero_x0) {
-    for (size_t e = gtid(); e < n; e += gstride()) {
+    for (size_t e = gtid(vb); e < n; e += gstride(vb)) {
       const double bv = a.b[e] - shift;
       if (a.remove_mean) a.b[e] = bv;
       a.x[e] = 0.0;
@@ -353,7 +377,7 @@ __global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(CgArgs a) {
   } else {
     Source<double, kModeResid, PRECOND> src{a.x, nullptr, 0.0, false, s_invd, mx, my, mz};
     Sink<double> out{a.r, nullptr, a.b, shift, a.remove_mean != 0, a.kind, c};
-    stencil_tiles<double, kModeResid, PRECOND>(ts, src, out, acc, s_tile);
+    stencil_tiles<double, kModeResid, PRECOND>(ts, src, out, acc, s_tile, vb);
   }
   if (!allreduce(acc, tot)) return fail();
   const double bb = tot[0];
@@ -363,7 +387,7 @@ __global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(CgArgs a) {
   int status = kErrNotConverged, iters = 0, restarts = 0;
   double rr_true = -1.0;
   if (bb == 0.0) {
-    for (size_t e = gtid(); e < n; e += gstride()) a.x[e] = 0.0;
+    for (size_t e = gtid(vb); e < n; e += gstride(vb)) a.x[e] = 0.0;
     status = kOk;
     rr_true = 0.0;
   } else {
@@ -377,7 +401,7 @@ __global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(CgArgs a) {
         acc[0] = acc[1] = acc[2] = 0.0;
         Source<double, kModeResid, PRECOND> src{a.x, nullptr, 0.0, false, s_invd, mx, my, mz};
         Sink<double> out{a.r, nullptr, a.b, 0.0, false, a.kind, c};
-        stencil_tiles<double, kModeResid, PRECOND>(ts, src, out, acc, s_tile);
+        stencil_tiles<double, kModeResid, PRECOND>(ts, src, out, acc, s_tile, vb);
         if (!allreduce(acc, tot)) return fail();
         rr_true = tot[1];
         if (rr_true <= tol2) {
@@ -399,10 +423,10 @@ __global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(CgArgs a) {
         Source<double, kModeDir, PRECOND> src{a.r, pold, beta, first, s_invd, mx, my, mz};
         if (RTZ > 0) {
           Sink<double> out{nullptr, pnew, nullptr, 0.0, false, a.kind, c};
-          dir_tiles_reg<(RTZ > 0 ? RTZ : 1), PRECOND>(ts, src, pnew, out, acc, s_tile, preg, qreg);
+          dir_tiles_reg<(RTZ > 0 ? RTZ : 1), PRECOND>(ts, src, pnew, out, acc, s_tile, preg, qreg, vb);
         } else {
           Sink<double> out{a.q, pnew, nullptr, 0.0, false, a.kind, c};
-          stencil_tiles<double, kModeDir, PRECOND>(ts, src, out, acc, s_tile);
+          stencil_tiles<double, kModeDir, PRECOND>(ts, src, out, acc, s_tile, vb);
         }
       }
       if (!allreduce(acc, tot)) return fail();
@@ -415,9 +439,9 @@ __global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(CgArgs a) {
       // phase U: x += alpha p, r -= alpha q, partial r.r (and r.z)
       acc[0] = acc[1] = acc[2] = 0.0;
       if (RTZ > 0) {
-        update_reg<(RTZ > 0 ? RTZ : 1), PRECOND>(ts, alpha, a.x, a.r, s_invd, acc, preg, qreg);
+        update_reg<(RTZ > 0 ? RTZ : 1), PRECOND>(ts, alpha, a.x, a.r, s_invd, acc, preg, qreg, vb);
       } else {
-        for (size_t e = gtid(); e < n; e += gstride()) {
+        for (size_t e = gtid(vb); e < n; e += gstride(vb)) {
           const double pe = pnew[e];
           const double qe = a.q[e];
           a.x[e] = fma(alpha, pe, a.x[e]);
@@ -444,7 +468,7 @@ __global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(CgArgs a) {
       acc[0] = acc[1] = acc[2] = 0.0;
       Source<double, kModeResid, PRECOND> src{a.x, nullptr, 0.0, false, s_invd, mx, my, mz};
       Sink<double> out{a.r, nullptr, a.b, 0.0, false, a.kind, c};
-      stencil_tiles<double, kModeResid, PRECOND>(ts, src, out, acc, s_tile);
+      stencil_tiles<double, kModeResid, PRECOND>(ts, src, out, acc, s_tile, vb);
       if (!allreduce(acc, tot)) return fail();
       rr_true = tot[1];
     }
@@ -453,13 +477,13 @@ __global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(CgArgs a) {
   // ---- gauge: shift x to the requested mean ----
   if (a.gauge) {
     acc[0] = acc[1] = acc[2] = 0.0;
-    for (size_t e = gtid(); e < n; e += gstride()) acc[0] += a.x[e];
+    for (size_t e = gtid(vb); e < n; e += gstride(vb)) acc[0] += a.x[e];
     if (!allreduce(acc, tot)) return fail();
     const double sh = a.gauge_value - tot[0] / double(n);
-    for (size_t e = gtid(); e < n; e += gstride()) a.x[e] += sh;
+    for (size_t e = gtid(vb); e < n; e += gstride(vb)) a.x[e] += sh;
   }
 
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (vb.bid == 0 && threadIdx.x == 0) {
     st->iters = iters;
     st->outer_iters = 0;
     st->restarts = restarts;
@@ -476,7 +500,7 @@ __global__ void __launch_bounds__(kSolveThreads) apply_poisson_kernel(GridDims g
   double acc[3] = {0.0, 0.0, 0.0};
   Source<double, kModeApply, 0> src{x, nullptr, 0.0, false, nullptr, g.mx, g.my, g.mz};
   Sink<double> out{y, nullptr, nullptr, 0.0, false, kOpPressure, 0.0};
-  stencil_tiles<double, kModeApply, 0>(ts, src, out, acc, s_tile);
+  stencil_tiles<double, kModeApply, 0>(ts, src, out, acc, s_tile, VBlock{int(blockIdx.x), int(gridDim.x)});
 }
 
 // ---------------------------------------------------------------------------
@@ -550,14 +574,14 @@ __device__ __forceinline__ void tma_issue_plane(const IrArgs& a, const CUtensorM
 // p_new = r32 + beta p_old (r32 alone on the first iteration), q = A p_new
 // (Neumann pressure operator), partial p.q; returns false on a wait timeout.
 __device__ bool dir_tma_f32(const IrArgs& a, const CUtensorMap* mp, float beta, bool first, float* pnew, float* q,
-                            float& acc, TmaRing& ring) {
+                            float& acc, TmaRing& ring, VBlock vb) {
   const int mx = a.g.mx, my = a.g.my, mz = a.g.mz;
   const int tx = threadIdx.x % kTileX, ty = threadIdx.x / kTileX;
   const int zl = a.tma_zl;
   const int ntx = (mx + kTileX - 1) / kTileX, nty = (my + kTileY - 1) / kTileY, nzc = (mz + zl - 1) / zl;
   const int items = ntx * nty * nzc;
   if (threadIdx.x == 0) asm volatile("fence.proxy.async.global;" ::: "memory");  // generic writes -> TMA reads
-  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+  for (int it = vb.bid; it < items; it += vb.nb) {
     const int bx = it % ntx, rest = it / ntx, by = rest % nty, bz = rest / nty;
     const int x0 = bx * kTileX, y0 = by * kTileY, z0 = bz * zl;
     const int z1 = min(z0 + zl, mz);
@@ -634,7 +658,13 @@ __device__ bool dir_tma_f32(const IrArgs& a, const CUtensorMap* mp, float beta, 
 // update" form of iterative refinement).  Convergence is only ever declared
 // on the FP64 true residual: ||b - A x|| <= rtol ||b||.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSolveThreads, 4) ir_kernel(const __grid_constant__ IrArgs a) {
+template <bool MULTI>
+__global__ void __launch_bounds__(kSolveThreads, 4) ir_kernel(const __grid_constant__ IrArgs a0, const IrArgs* table,
+                                                             const int* starts, int nprob) {
+  VBlock vb{int(blockIdx.x), int(gridDim.x)};
+  const int prob = MULTI ? find_problem(starts, nprob, vb) : 0;
+  if (prob < 0) return;
+  const IrArgs& a = MULTI ? table[prob] : a0;
   __shared__ __align__(128) double s_raw[kTileSlots];
   __shared__ double s_red[32 * 3];
   __shared__ __align__(8) uint64_t s_full[kTmaStages];
@@ -663,7 +693,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) ir_kernel(const __grid_const
     }
   };
   auto allreduce = [&](double (&v)[3], double (&o)[3]) {
-    return grid_allreduce<3>(v, o, a.ctrl, a.partials, s_red, a.timeout_ns, round);
+    return grid_allreduce<3>(v, o, a.ctrl, a.partials, s_red, a.timeout_ns, round, vb);
   };
 
   double acc[3], tot[3];
@@ -671,7 +701,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) ir_kernel(const __grid_const
   double shift = 0.0;
   if (a.remove_mean) {
     acc[0] = acc[1] = acc[2] = 0.0;
-    for (size_t e = gtid(); e < n; e += gstride()) acc[0] += a.b[e];
+    for (size_t e = gtid(vb); e < n; e += gstride(vb)) acc[0] += a.b[e];
     if (!allreduce(acc, tot)) return fail();
     shift = tot[0] / double(n);
   }
@@ -679,7 +709,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) ir_kernel(const __grid_const
   // r = b - A x0 (FP64), partials b.b, r.r, sum(r)
   acc[0] = acc[1] = acc[2] = 0.0;
   if (a.zero_x0) {
-    for (size_t e = gtid(); e < n; e += gstride()) {
+    for (size_t e = gtid(vb); e < n; e += gstride(vb)) {
       const double bv = a.b[e] - shift;
       if (a.remove_mean) a.b[e] = bv;
       a.x[e] = 0.0;
@@ -691,7 +721,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) ir_kernel(const __grid_const
   } else {
     Source<double, kModeResid, 0> src{a.x, nullptr, 0.0, false, nullptr, mx, my, mz};
     Sink<double> out{a.r, nullptr, a.b, shift, a.remove_mean != 0, kOpPressure, 0.0};
-    stencil_tiles<double, kModeResid, 0>(ts, src, out, acc, s64);
+    stencil_tiles<double, kModeResid, 0>(ts, src, out, acc, s64, vb);
   }
   if (!allreduce(acc, tot)) return fail();
   const double bb = tot[0];
@@ -700,7 +730,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) ir_kernel(const __grid_const
 
   int status = kErrNotConverged, refinements = 0, iters = 0;
   if (bb == 0.0) {
-    for (size_t e = gtid(); e < n; e += gstride()) a.x[e] = 0.0;
+    for (size_t e = gtid(vb); e < n; e += gstride(vb)) a.x[e] = 0.0;
     status = kOk;
     rr = 0.0;
   } else {
@@ -721,7 +751,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) ir_kernel(const __grid_const
         // r32 = r - mean(r); x32 = 0; rz = |r32|^2
         const double rmean = rsum / double(n);
         float f = 0.f;
-        for (size_t e = gtid(); e < n; e += gstride()) {
+        for (size_t e = gtid(vb); e < n; e += gstride(vb)) {
           const float v = float(a.r[e] - rmean);
           a.r32[e] = v;
           a.d32[e] = 0.f;
@@ -742,11 +772,11 @@ __global__ void __launch_bounds__(kSolveThreads, 4) ir_kernel(const __grid_const
       const float* pold = cur ? a.p0_32 : a.p1_32;
       float fa[3] = {0.f, 0.f, 0.f};
       if (a.use_tma) {
-        if (!dir_tma_f32(a, cur ? &a.map_p0 : &a.map_p1, float(beta), first, pnew, a.q32, fa[0], ring)) return fail();
+        if (!dir_tma_f32(a, cur ? &a.map_p0 : &a.map_p1, float(beta), first, pnew, a.q32, fa[0], ring, vb)) return fail();
       } else {
         Source<float, kModeDir, 0> src{a.r32, pold, float(beta), first, nullptr, mx, my, mz};
         Sink<float> out{a.q32, pnew, nullptr, 0.f, false, kOpPressure, 0.f};
-        stencil_tiles<float, kModeDir, 0>(ts, src, out, fa, s32);
+        stencil_tiles<float, kModeDir, 0>(ts, src, out, fa, s32, vb);
       }
       acc[0] = fa[0];
       acc[1] = acc[2] = 0.0;
@@ -766,7 +796,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) ir_kernel(const __grid_const
         const float4* q4 = reinterpret_cast<const float4*>(a.q32);
         float4* d4 = reinterpret_cast<float4*>(a.d32);
         float4* r4 = reinterpret_cast<float4*>(a.r32);
-        for (size_t e = gtid(); e < n4; e += gstride()) {
+        for (size_t e = gtid(vb); e < n4; e += gstride(vb)) {
           const float4 pv = p4[e], qv = q4[e];
           float4 dv = d4[e], rv = r4[e];
           dv.x = fmaf(alpha, pv.x, dv.x);
@@ -784,7 +814,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) ir_kernel(const __grid_const
           racc = fmaf(rv.z, rv.z, racc);
           racc = fmaf(rv.w, rv.w, racc);
         }
-        for (size_t e = 4 * n4 + gtid(); e < n; e += gstride()) {
+        for (size_t e = 4 * n4 + gtid(vb); e < n; e += gstride(vb)) {
           a.d32[e] = fmaf(alpha, pnew[e], a.d32[e]);
           const float re = fmaf(-alpha, a.q32[e], a.r32[e]);
           a.r32[e] = re;
@@ -800,13 +830,13 @@ __global__ void __launch_bounds__(kSolveThreads, 4) ir_kernel(const __grid_const
       ++iters;
       if (rz_new <= delta2 * rz_ref || rz_new <= tol2) {
         // refinement in FP64: x += x32, r = b - A x (true residual)
-        for (size_t e = gtid(); e < n; e += gstride()) a.x[e] += double(a.d32[e]);
+        for (size_t e = gtid(vb); e < n; e += gstride(vb)) a.x[e] += double(a.d32[e]);
         acc[0] = acc[1] = acc[2] = 0.0;
         if (!allreduce(acc, tot)) return fail();  // x complete before the stencil reads it
         {
           Source<double, kModeResid, 0> src{a.x, nullptr, 0.0, false, nullptr, mx, my, mz};
           Sink<double> out{a.r, nullptr, a.b, 0.0, false, kOpPressure, 0.0};
-          stencil_tiles<double, kModeResid, 0>(ts, src, out, acc, s64);
+          stencil_tiles<double, kModeResid, 0>(ts, src, out, acc, s64, vb);
         }
         if (!allreduce(acc, tot)) return fail();
         rr = tot[1];
@@ -821,13 +851,13 @@ __global__ void __launch_bounds__(kSolveThreads, 4) ir_kernel(const __grid_const
     }
     if (status != kOk) {
       // leaving early: fold the pending FP32 correction into x and measure
-      for (size_t e = gtid(); e < n; e += gstride()) a.x[e] += double(a.d32[e]);
+      for (size_t e = gtid(vb); e < n; e += gstride(vb)) a.x[e] += double(a.d32[e]);
       acc[0] = acc[1] = acc[2] = 0.0;
       if (!allreduce(acc, tot)) return fail();
       {
         Source<double, kModeResid, 0> src{a.x, nullptr, 0.0, false, nullptr, mx, my, mz};
         Sink<double> out{a.r, nullptr, a.b, 0.0, false, kOpPressure, 0.0};
-        stencil_tiles<double, kModeResid, 0>(ts, src, out, acc, s64);
+        stencil_tiles<double, kModeResid, 0>(ts, src, out, acc, s64, vb);
       }
       if (!allreduce(acc, tot)) return fail();
       rr = tot[1];
@@ -837,13 +867,13 @@ __global__ void __launch_bounds__(kSolveThreads, 4) ir_kernel(const __grid_const
 
   if (a.gauge) {
     acc[0] = acc[1] = acc[2] = 0.0;
-    for (size_t e = gtid(); e < n; e += gstride()) acc[0] += a.x[e];
+    for (size_t e = gtid(vb); e < n; e += gstride(vb)) acc[0] += a.x[e];
     if (!allreduce(acc, tot)) return fail();
     const double sh = a.gauge_value - tot[0] / double(n);
-    for (size_t e = gtid(); e < n; e += gstride()) a.x[e] += sh;
+    for (size_t e = gtid(vb); e < n; e += gstride(vb)) a.x[e] += sh;
   }
 
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (vb.bid == 0 && threadIdx.x == 0) {
     st->iters = iters;
     st->outer_iters = refinements;
     st->restarts = 0;
@@ -862,25 +892,30 @@ int num_sms() {
   return sms > 0 ? sms : 1;
 }
 
-typedef void (*CgKernel)(CgArgs);
+typedef void (*CgKernel)(const CgArgs, const CgArgs*, const int*, int);
 
-CgKernel cg_kernel_for(int precond, int rtz) {
+template <bool MULTI>
+CgKernel cg_kernel_for_t(int precond, int rtz) {
   if (precond) {
     switch (rtz) {
-      case 1: return cg_fp64_kernel<1, 1>;
-      case 2: return cg_fp64_kernel<1, 2>;
-      case 4: return cg_fp64_kernel<1, 4>;
-      case 8: return cg_fp64_kernel<1, 8>;
-      default: return cg_fp64_kernel<1, 0>;
+      case 1: return cg_fp64_kernel<1, 1, MULTI>;
+      case 2: return cg_fp64_kernel<1, 2, MULTI>;
+      case 4: return cg_fp64_kernel<1, 4, MULTI>;
+      case 8: return cg_fp64_kernel<1, 8, MULTI>;
+      default: return cg_fp64_kernel<1, 0, MULTI>;
     }
   }
   switch (rtz) {
-    case 1: return cg_fp64_kernel<0, 1>;
-    case 2: return cg_fp64_kernel<0, 2>;
-    case 4: return cg_fp64_kernel<0, 4>;
-    case 8: return cg_fp64_kernel<0, 8>;
-    default: return cg_fp64_kernel<0, 0>;
+    case 1: return cg_fp64_kernel<0, 1, MULTI>;
+    case 2: return cg_fp64_kernel<0, 2, MULTI>;
+    case 4: return cg_fp64_kernel<0, 4, MULTI>;
+    case 8: return cg_fp64_kernel<0, 8, MULTI>;
+    default: return cg_fp64_kernel<0, 0, MULTI>;
   }
+}
+
+CgKernel cg_kernel_for(int precond, int rtz, bool multi = false) {
+  return multi ? cg_kernel_for_t<true>(precond, rtz) : cg_kernel_for_t<false>(precond, rtz);
 }
 
 }  // namespace
@@ -905,7 +940,7 @@ int cg_max_coresident_blocks(int kind_is_ir) {
   }
   if (kind_is_ir) {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ir_kernel, kSolveThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ir_kernel<false>, kSolveThreads, 0);
     b = b > 8 ? 8 : b;
     best = b > best ? b : best;
   }
@@ -966,9 +1001,65 @@ cudaError_t launch_cg(const CgArgs& a_in, const LaunchGeom& lg, cudaStream_t s, 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t err = cudaLaunchKernelEx(&cfg, cg_kernel_for(a.precond, sh.rtz), a);
+  cudaError_t err = cudaLaunchKernelEx(&cfg, cg_kernel_for(a.precond, sh.rtz), a, (const CgArgs*)nullptr,
+                                       (const int*)nullptr, 0);
   if (launches) *launches += 1;
   return err;
+}
+
+int batch_blocks_per_sm(int ir) {
+  int b = 0;
+  if (ir) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ir_kernel<true>, kSolveThreads, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cg_kernel_for(1, 0, true), kSolveThreads, 0);
+  int b0 = 0;
+  if (!ir) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, cg_kernel_for(0, 0, true), kSolveThreads, 0);
+    b = b0 < b ? b0 : b;
+  }
+  return b > 4 ? 4 : b;
+}
+
+int batch_num_sms() { return num_sms(); }
+
+static cudaError_t launch_coop(void (*kern)(const CgArgs, const CgArgs*, const int*, int), const CgArgs* t,
+                               const int* starts, int nprob, int blocks, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(kSolveThreads);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, CgArgs{}, t, starts, nprob);
+}
+
+cudaError_t launch_cg_multi(const CgArgs* d_table, const int* d_starts, int nprob, int total_blocks, int precond,
+                            cudaStream_t s, int64_t* launches) {
+  if (launches) *launches += 1;
+  return launch_coop(cg_kernel_for(precond, 0, true), d_table, d_starts, nprob, total_blocks, s);
+}
+
+cudaError_t launch_ir_multi(const IrArgs* d_table, const int* d_starts, int nprob, int total_blocks, cudaStream_t s,
+                            int64_t* launches) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(total_blocks);
+  cfg.blockDim = dim3(kSolveThreads);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (launches) *launches += 1;
+  return cudaLaunchKernelEx(&cfg, ir_kernel<true>, IrArgs{}, d_table, d_starts, nprob);
+}
+
+int solve_tile_depth_for(GridDims g, int blocks) {
+  for (int tz = kMaxTz; tz > 1; tz >>= 1)
+    if (tiles_of(g, tz) >= 2 * blocks) return tz;
+  return 1;
 }
 
 cudaError_t launch_apply_poisson(GridDims g, const double* x, double* y, int tz, cudaStream_t s,
@@ -1020,7 +1111,7 @@ cudaError_t launch_ir(const IrArgs& a_in, const LaunchGeom& lg, cudaStream_t s, 
       }
   }
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ir_kernel, kSolveThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ir_kernel<false>, kSolveThreads, 0);
   per_sm = per_sm > 8 ? 8 : (per_sm < 1 ? 1 : per_sm);
   int bps = lg.bps_req > 0 ? (lg.bps_req < per_sm ? lg.bps_req : per_sm) : (per_sm < 4 ? per_sm : 4);
   int tz = lg.tz_req;
@@ -1048,7 +1139,7 @@ cudaError_t launch_ir(const IrArgs& a_in, const LaunchGeom& lg, cudaStream_t s, 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t err = cudaLaunchKernelEx(&cfg, ir_kernel, a);
+  cudaError_t err = cudaLaunchKernelEx(&cfg, ir_kernel<false>, a, (const IrArgs*)nullptr, (const int*)nullptr, 0);
   if (launches) *launches += 1;
   return err;
 }
