@@ -68,6 +68,9 @@ def parse_args(argv=None):
                          "(one bench step = one solve of a seeded Gaussian right-hand side)")
     ap.add_argument("--max-iters", type=int, default=0, help="CG iteration cap per solve (0: 20 N)")
     ap.add_argument("--no-precision-study", action="store_true")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="benchmark N batched uneven cavities (edges from {32,48,64,96}) instead of one cavity")
+    ap.add_argument("--no-batch-study", action="store_true")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--max-seconds", type=float, default=150.0, help=argparse.SUPPRESS)
     return ap.parse_args(argv)
@@ -378,6 +381,11 @@ def main_ours(args):
                      "fp64_cg": study["cg"], "fp32_cg_fp64_refined": study["ir"],
                      "speedup_ir_over_fp64_cg": cg_ms / ir_ms}
 
+    # batched uneven cavities: FP64 CG vs mixed precision, graph-replayed
+    batch = None
+    if rank == 0 and world == 1 and not args.no_batch_study:
+        batch = {s: time_batch(cfd, 64, s, 3, 1, device) for s in ("cg", "ir")}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res = run_oracle_child(args.workload, 10 ** 6, 0, args.cpu_seconds)
@@ -400,7 +408,7 @@ def main_ours(args):
                           "all_converged": bool(ok)},
                 "phase_ms_per_step": phase_ms_per_step,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "precision_study": precision,
+                "precision_study": precision, "batch_study": batch,
                 "clocks": clocks, "wall_s_timed": wall}
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -430,6 +438,46 @@ def time_solves(cfd, n, solver, seeds, warmup, max_iters=0, device=None):
         out.append({"ms": ms / max(calls, 1), "iters": st["iters"], "refinements": st["outer_iters"],
                     "rel_resid": st["rel_resid"], "rc": rc})
     del cav
+    return out
+
+
+def time_batch(cfd, n_cav, solver, steps, warmup, device, graph=True, seed=5):
+    """Batched uneven cavities (edges from {32, 48, 64, 96}, seed 5), lid 1.0,
+    nu 1e-3, dt 1e-2; per-step device time with L2 flushed between steps."""
+    import torch
+    from paper_2504_03697_gb300.synthetic import batch_edges, cavity_perturbation
+
+    edges = batch_edges(n_cav, seed)
+    prms = [cfd.make_params(e, e, e, dt=1e-2, nu=1e-3, lid_u=1.0, solver=solver) for e in edges]
+    b = cfd.Batch(prms, device=device)
+    for i, e in enumerate(edges):
+        for name, f in zip("uvw", cavity_perturbation(e, e, e, 100 + i, 1e-3)):
+            b.cavity(i).set_field(name, f)
+    if graph:
+        b.use_graph(True)
+    if warmup:
+        b.step(warmup, stats=False)
+    stream = torch.cuda.current_stream(device)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=device)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    l0 = b.launch_count()
+    torch.cuda.synchronize(device)
+    for s in range(steps):
+        flush.zero_()
+        ev[s][0].record(stream)
+        b.step(1, stats=False)
+        ev[s][1].record(stream)
+    torch.cuda.synchronize(device)
+    ms = [a.elapsed_time(z) for a, z in ev]
+    rc, st = b.step(1, stats=True)  # one more step to read converged statistics
+    cells = sum(e ** 3 for e in edges)
+    out = {"cavities": n_cav, "edges_hist": {str(k): edges.count(k) for k in (32, 48, 64, 96)}, "cells": cells,
+           "solver": solver, "graph": b.graph_active(), "steps": steps, "ms_per_step": sum(ms) / steps,
+           "cell_steps_per_s": cells * steps / (sum(ms) / 1e3), "launches_per_step": (b.launch_count() - l0) / steps,
+           "pressure_blocks": b.blocks(4 if solver == "ir" else 3),
+           "all_converged": rc == cfd.CFD_OK and all(x["rel_resid"] <= 1e-8 for x in st),
+           "pressure_iters_max": max(x["iters"] for x in st)}
+    b.close()
     return out
 
 
@@ -466,7 +514,32 @@ def main(argv=None):
         return main_reference(args)
     if args.poisson > 0:
         return main_poisson(args)
+    if args.batch > 0:
+        return main_batch(args)
     return main_ours(args)
+
+
+def main_batch(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    from paper_2504_03697_gb300 import build as B
+    B.build()
+    from paper_2504_03697_gb300 import cfd
+
+    res = time_batch(cfd, args.batch, args.solver, args.steps, args.warmup, device)
+    line = {"metric": "cell-steps/s", "value": res["cell_steps_per_s"], "unit": "cell-steps/s",
+            "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["ms_per_step"], "dtype": "f32+f64" if args.solver == "ir" else "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.batch} batched uneven cavities (edges from {{32,48,64,96}}, seed 5), "
+                                   f"nu 1e-3, lid 1.0, dt 1e-2, solver {args.solver}, graph-replayed steps"},
+            "batch": res}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
 
 
 if __name__ == "__main__":

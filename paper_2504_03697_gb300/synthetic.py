@@ -89,6 +89,14 @@ def gaussian_rhs(nx: int, ny: int, nz: int, seed: int) -> np.ndarray:
     return g.reshape(nz, ny, nx)
 
 
+def batch_edges(n: int, seed: int = 5, choices=(32, 48, 64, 96)):
+    """Edge lengths of n cubic cavities drawn uniformly from ``choices``
+    (stream 7 of the counter-based generator)."""
+    u = uniform01(seed, 7, np.arange(n, dtype=np.uint64))
+    idx = np.minimum((u * len(choices)).astype(np.int64), len(choices) - 1)
+    return [int(choices[i]) for i in idx]
+
+
 def uniform_field(shape, seed: int, stream: int = 0, lo: float = -1.0, hi: float = 1.0):
     """Uniform[lo, hi) field of the given shape (for operator parity tests)."""
     n = int(np.prod(shape))
