@@ -282,6 +282,97 @@ int64_t cfd_batch_launch_count(const cfd_batch *b);
 int cfd_poisson_solve_noalloc(int32_t nx, int32_t ny, int32_t nz, const double *b_dev, double *x_dev,
                               double rtol, int32_t max_iters, cfd_stream_t stream, cfd_solve_stats *stats);
 
+/* Pressure right-hand side of the projection (Sec. 3.1 "Projection"): the
+ * scaled divergence -(rho h / dt) * sum of face differences of the current
+ * velocity (u, v, w), one value per cell, written to b_dev (nx*ny*nz float64,
+ * device).  The mean is NOT removed (the solvers remove it).  Asynchronous on
+ * the handle's stream.  Used to harvest pressure systems from a run. */
+int cfd_pressure_rhs(cfd_handle *h, double *b_dev);
+
+/* ------------------------------------------------------------------------
+ * Learned preconditioner (flexible PCG with a U-Net, Sec. 5 "other
+ * preconditioners"; the paper itself uses DIC / Jacobi, Sec. 3.1).
+ * ------------------------------------------------------------------------ */
+
+/* One stride-1 3D convolution on the tensor cores (BF16 operands, FP32
+ * accumulation), the U-Net's building block, exposed for direct checks.
+ * Grid nx x ny x nz (x fastest), zero padding.  src0: device BF16 [V][c0]
+ * (channels-last); src1: [V][c1] concatenated after src0 (c1 = 0: unused;
+ * c1 > 0 needs c0 % 16 == 0).  ks = 3 or 1.  weights: device BF16
+ * [ks^3][nout_pad][cin_pad] (cin_pad = c0 + c1 rounded up to 16, tap index
+ * kx + 3 ky + 9 kz, zero-filled padding), or for c0 = 1, c1 = 0, ks = 3 the
+ * tap-packed [nout_pad][32] (taps 0..26, zeros after).  bias: device FP32
+ * [cout] or NULL.  cout <= nout_pad in {16, 32, 64}.  Output: dst_bf16
+ * [V][cout] BF16, or dst_f32 [V][cout] FP32 when dst_f32 is non-NULL.
+ * err_dev: device int set to 1 if a bounded device-side wait timed out.
+ * Asynchronous on stream; returns a negative code on invalid arguments. */
+int cfd_conv3d_bf16(int nx, int ny, int nz, const void *src0, int c0, const void *src1, int c1, int ks,
+                    const void *weights, const float *bias, int cout, int nout_pad, void *dst_bf16,
+                    float *dst_f32, int *err_dev, void *stream);
+
+typedef struct cfd_unet cfd_unet;
+
+/* Workspace of a U-Net preconditioner for an nx x ny x nz grid (each a
+ * multiple of 4): parameters, Adam moments, BF16 activations and their
+ * gradients, and the flexible-CG vectors (about 450 bytes per cell). */
+int cfd_unet_workspace_bytes(int nx, int ny, int nz, size_t *bytes);
+
+/* Create on a caller-owned device workspace (256-byte aligned, at least
+ * cfd_unet_workspace_bytes); parameters are initialised from seed
+ * (uniform +-sqrt(3 / fan_in), zero biases).  All work runs on stream. */
+int cfd_unet_create(int nx, int ny, int nz, void *dev_ws, size_t bytes, cfd_stream_t stream, uint64_t seed,
+                    cfd_unet **out);
+void cfd_unet_destroy(cfd_unet *u);
+
+/* Number of FP32 parameters (u may be NULL: the count is grid independent).
+ * Layout: for each layer in order L0a, L0b, L1a, L1b, L2a, L2b, L1c, L0c,
+ * head: weights [taps][cout][cin] (tap = kx + 3 ky + 9 kz), then bias
+ * [cout]. */
+int64_t cfd_unet_param_count(const cfd_unet *u);
+int cfd_unet_get_params(cfd_unet *u, float *host, int64_t n);
+int cfd_unet_set_params(cfd_unet *u, const float *host, int64_t n);
+
+/* z = M(r) = U(s r) / s - mean, s = sqrt(V) / ||r||: r_dev, z_dev device
+ * float64 [V].  Asynchronous. */
+int cfd_unet_apply(cfd_unet *u, const double *r_dev, double *z_dev);
+
+/* One Adam step (lr, beta 0.9 / 0.999, eps 1e-8) on the mean over npairs
+ * pairs of the loss |U(s r) - s e|^2 / V, r_dev and e_dev device float64
+ * [npairs][V].  *loss (nullable) receives the mean loss before the step.
+ * Synchronises the stream. */
+int cfd_unet_train_step(cfd_unet *u, const double *r_dev, const double *e_dev, int npairs, float lr, float *loss);
+
+/* Tensor read-back for checks (synchronous).  which in 0..25: the BF16
+ * channels-last tensors xin, a0, s0, p0, a1, s1, p1, a2, s2, u1, d1, u0, d0
+ * (activations of the last forward pass) and gz, g_d0, g_s0, g_u0, g_d1,
+ * g_s1, g_u1, g_s2, g_a2, g_p1, g_a1, g_p0, g_a0 (their gradients from the
+ * last backward pass); or one of the CFD_UNET_T_* below.  count must equal
+ * the tensor's element count. */
+enum {
+  CFD_UNET_T_OUT = 100,     /* FP32 [V] head output of the last forward pass  */
+  CFD_UNET_T_TARGET = 101,  /* FP32 [V] scaled target s e of the last pair     */
+  CFD_UNET_T_GRAD = 102,    /* FP32 [params] accumulated gradient (last step)  */
+  CFD_UNET_T_ADAM_M = 103,  /* FP32 [params] Adam first moment                 */
+  CFD_UNET_T_ADAM_V = 104   /* FP32 [params] Adam second moment                */
+};
+int cfd_unet_read_tensor(cfd_unet *u, int which, void *host, int64_t count);
+
+/* Flexible PCG on the Neumann pressure system of the U-Net's grid (the
+ * operator of cfd_apply_poisson) with z = M(r) and the Polak-Ribiere beta
+ * z_{k+1}.(r_{k+1} - r_k) / (z_k.r_k).  Cold start x = 0; the mean of b is
+ * removed; no gauge shift.  Converged when the FP64 TRUE residual satisfies
+ * ||b - A x|| <= rtol ||b||.  On breakdown (p.q <= 0, z.r <= 0, non-finite)
+ * or stagnation (50 iterations without the residual norm halving) it
+ * continues as plain CG from the current iterate.  max_iters = 0 means
+ * 20 * max(n).  stats (nullable): iters (all iterations), outer_iters (the
+ * plain-CG ones), restarts, status, rel_resid, b_norm.  Synchronises the
+ * stream; returns the status (CFD_OK, CFD_ERR_NOT_CONVERGED, ...). */
+int cfd_unet_fpcg_solve(cfd_unet *u, const double *b_dev, double *x_dev, double rtol, int32_t max_iters,
+                        cfd_solve_stats *stats);
+
+int64_t cfd_unet_launch_count(const cfd_unet *u);
+const char *cfd_unet_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

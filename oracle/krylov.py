@@ -29,6 +29,13 @@ to 6^3, exactly one iteration for a single DCT mode and two for two modes,
 the manufactured cosine solution in closed form, the O(h^2) rate on a
 polynomial solution, and DIC = exact factorisation on tridiagonal matrices
 (one PCG iteration).
+
+``fpcg`` (flexible PCG for a preconditioner that may vary between
+iterations) is pinned by tests/test_oracle_unet.py: with M = identity or a
+fixed SPD M it takes the iterates of ``pcg`` (the Polak-Ribiere beta equals
+the Fletcher-Reeves one when z_{k+1}.r_k = 0), with M = the exact inverse on
+the zero-mean subspace it converges in one iteration, and with an
+indefinite M (z = -r) it falls back to plain CG and still converges.
 """
 from __future__ import annotations
 
@@ -136,5 +143,105 @@ def pcg(A, b, x0=None, rtol=1e-8, max_iters=1000, precond=identity_precond,
         rz = rz_new
         p = z + beta * p
         st.iters += 1
+    st.rel_resid = float(np.linalg.norm(b - A @ x) / np.sqrt(bb))
+    return x, st
+
+
+@dataclass
+class FlexStats:
+    iters: int = 0
+    plain_iters: int = 0      # iterations after the switch to plain CG
+    restarts: int = 0
+    converged: bool = False
+    fell_back: bool = False
+    rel_resid: float = 0.0
+
+
+def fpcg(A, b, precond, rtol=1e-8, max_iters=1000, stagnation=50, max_restarts=8):
+    """Flexible PCG with the Polak-Ribiere beta (learned preconditioner, a
+    reading of the paper's "other preconditioners", Sec. 5).
+
+    b has its mean removed first (Neumann system, consistent right-hand side).
+    One iteration: q = A p, alpha = (r.z)/(p.q), x += alpha p, r -= alpha q,
+    z' = M(r), beta = z'.(r_new - r_old)/(r_old.z_old), p = z' + beta p.  A
+    non-positive or non-finite p.q or z.r, or `stagnation` iterations without
+    the residual norm halving, switches to plain CG (M = identity) restarted
+    from the true residual of the current x.  Convergence is judged by the
+    true residual ||b - A x|| <= rtol ||b||; when the recurrence passes but
+    the true residual does not, the iteration restarts from it.
+    Returns (x, FlexStats)."""
+    b = b - b.mean()
+    n = b.size
+    st = FlexStats()
+    bb = float(np.dot(b, b))
+    x = np.zeros(n)
+    if bb == 0.0:
+        st.converged = True
+        return x, st
+    tol2 = rtol * rtol * bb
+    plain = False
+    M = precond
+
+    def start():
+        r = b - A @ x
+        z = r.copy() if plain else M(r)
+        return r, z, z.copy(), float(np.dot(z, r))
+
+    r, z, p, rz = start()
+    best = bb
+    since = 0
+    while True:
+        bad = not (rz > 0.0 and np.isfinite(rz))
+        if not bad:
+            if st.iters >= max_iters:
+                break
+            q = A @ p
+            pq = float(np.dot(p, q))
+            bad = not (pq > 0.0 and np.isfinite(pq))
+        if bad:
+            if plain:
+                break
+            plain = True
+            st.fell_back = True
+            st.restarts += 1
+            r, z, p, rz = start()
+            continue
+        alpha = rz / pq
+        x = x + alpha * p
+        r_old = r
+        r = r - alpha * q
+        st.iters += 1
+        if plain:
+            st.plain_iters += 1
+        rr = float(np.dot(r, r))
+        if rr <= tol2:
+            rt = b - A @ x
+            if float(np.dot(rt, rt)) <= tol2:
+                st.converged = True
+                break
+            st.restarts += 1
+            if st.restarts > max_restarts:
+                break
+            r = rt
+            z = r.copy() if plain else M(r)
+            p = z.copy()
+            rz = float(np.dot(z, r))
+            continue
+        if rr < 0.25 * best:
+            best, since = rr, 0
+        else:
+            since += 1
+            if not plain and since >= stagnation:
+                plain = True
+                st.fell_back = True
+                st.restarts += 1
+                r, z, p, rz = start()
+                continue
+        z_new = r.copy() if plain else M(r)
+        rz_new = float(np.dot(z_new, r))
+        beta = float(np.dot(z_new, r - r_old)) / rz
+        rz = rz_new
+        z = z_new
+        p = z + beta * p
     st.rel_resid = float(np.linalg.norm(b - A @ x) / np.sqrt(bb))
     return x, st

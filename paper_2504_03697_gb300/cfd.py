@@ -104,6 +104,21 @@ def load_library(path: Optional[str] = None):
         "cfd_batch_launch_count": (ctypes.c_int64, [vp]),
         "cfd_enable_timing": (ctypes.c_int, [vp, ctypes.c_int]),
         "cfd_phase_times": (ctypes.c_int, [vp, P(ctypes.c_double), P(ctypes.c_int64)]),
+        "cfd_pressure_rhs": (ctypes.c_int, [vp, vp]),
+        "cfd_conv3d_bf16": (ctypes.c_int, [ctypes.c_int] * 3 + [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, vp,
+                                                                ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]),
+        "cfd_unet_workspace_bytes": (ctypes.c_int, [ctypes.c_int] * 3 + [P(ctypes.c_size_t)]),
+        "cfd_unet_create": (ctypes.c_int, [ctypes.c_int] * 3 + [vp, ctypes.c_size_t, vp, ctypes.c_uint64, P(vp)]),
+        "cfd_unet_destroy": (None, [vp]),
+        "cfd_unet_param_count": (ctypes.c_int64, [vp]),
+        "cfd_unet_get_params": (ctypes.c_int, [vp, vp, ctypes.c_int64]),
+        "cfd_unet_set_params": (ctypes.c_int, [vp, vp, ctypes.c_int64]),
+        "cfd_unet_apply": (ctypes.c_int, [vp, vp, vp]),
+        "cfd_unet_train_step": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_float, P(ctypes.c_float)]),
+        "cfd_unet_read_tensor": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int64]),
+        "cfd_unet_fpcg_solve": (ctypes.c_int, [vp, vp, vp, ctypes.c_double, ctypes.c_int32, P(cfd_solve_stats)]),
+        "cfd_unet_launch_count": (ctypes.c_int64, [vp]),
+        "cfd_unet_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -241,6 +256,11 @@ class Cavity:
     def launch_count(self) -> int:
         return int(self.lib.cfd_launch_count(self.h))
 
+    def pressure_rhs(self, b: torch.Tensor):
+        """Projection right-hand side of the current velocity (mean kept)."""
+        assert b.is_cuda and b.dtype == torch.float64 and b.numel() == self.prm.nx * self.prm.ny * self.prm.nz
+        return self._check(self.lib.cfd_pressure_rhs(self.h, ctypes.c_void_p(b.data_ptr())))
+
     def set_stream(self, stream):
         self.stream = stream
         return self._check(self.lib.cfd_set_stream(self.h, ctypes.c_void_p(_stream_ptr(stream))))
@@ -350,3 +370,110 @@ class Batch:
 
     def launch_count(self) -> int:
         return int(self.lib.cfd_batch_launch_count(self.b))
+
+
+# names of the BF16 tensors readable with UNet.read_tensor (indices 0..25)
+UNET_TENSORS = ["xin", "a0", "s0", "p0", "a1", "s1", "p1", "a2", "s2", "u1", "d1", "u0", "d0",
+                "gz", "g_d0", "g_s0", "g_u0", "g_d1", "g_s1", "g_u1", "g_s2", "g_a2", "g_p1", "g_a1", "g_p0", "g_a0"]
+UNET_CHANNELS = [1, 16, 16, 16, 32, 32, 32, 64, 64, 64, 32, 32, 16,
+                 1, 16, 16, 32, 32, 32, 64, 64, 64, 32, 32, 16, 16]
+UNET_LEVELS = [0, 0, 0, 1, 1, 1, 2, 2, 2, 1, 1, 0, 0,
+               0, 0, 0, 0, 1, 1, 1, 2, 2, 2, 1, 1, 0]
+UNET_T_OUT, UNET_T_TARGET, UNET_T_GRAD, UNET_T_ADAM_M, UNET_T_ADAM_V = 100, 101, 102, 103, 104
+
+# layer table: (name, level, c0, c1, cout, ks), in parameter order
+UNET_LAYERS = [("L0a", 0, 1, 0, 16, 3), ("L0b", 0, 16, 0, 16, 3), ("L1a", 1, 16, 0, 32, 3), ("L1b", 1, 32, 0, 32, 3),
+               ("L2a", 2, 32, 0, 64, 3), ("L2b", 2, 64, 0, 64, 3), ("L1c", 1, 32, 64, 32, 3),
+               ("L0c", 0, 16, 32, 16, 3), ("head", 0, 16, 0, 1, 1)]
+
+
+class UNet:
+    """Learned preconditioner on an nx x ny x nz grid (each a multiple of 4);
+    see cfd_unet_* in include/cfd.h."""
+
+    def __init__(self, nx, ny, nz, seed=0, stream=None, device=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (the library has no CPU path)")
+        self.lib = load_library()
+        self.shape = (int(nx), int(ny), int(nz))
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        nb = ctypes.c_size_t(0)
+        self._check(self.lib.cfd_unet_workspace_bytes(*self.shape, ctypes.byref(nb)))
+        self.workspace = torch.empty(int(nb.value), dtype=torch.uint8, device=self.device)
+        self.stream = stream
+        u = ctypes.c_void_p(0)
+        self._check(self.lib.cfd_unet_create(*self.shape, ctypes.c_void_p(self.workspace.data_ptr()),
+                                             ctypes.c_size_t(int(nb.value)), ctypes.c_void_p(_stream_ptr(stream)),
+                                             ctypes.c_uint64(int(seed)), ctypes.byref(u)))
+        self.u = u
+        self.nparams = int(self.lib.cfd_unet_param_count(self.u))
+
+    def _check(self, rc, allow=()):
+        if rc != CFD_OK and rc not in allow:
+            raise CfdError(rc, self.lib.cfd_unet_last_error().decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "u", None):
+            self.lib.cfd_unet_destroy(self.u)
+            self.u = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def cells(self):
+        return self.shape[0] * self.shape[1] * self.shape[2]
+
+    def get_params(self) -> torch.Tensor:
+        out = torch.empty(self.nparams, dtype=torch.float32)
+        self._check(self.lib.cfd_unet_get_params(self.u, ctypes.c_void_p(out.data_ptr()), self.nparams))
+        return out
+
+    def set_params(self, params: torch.Tensor):
+        p = params.detach().to(torch.float32).contiguous().cpu()
+        assert p.numel() == self.nparams
+        self._check(self.lib.cfd_unet_set_params(self.u, ctypes.c_void_p(p.data_ptr()), self.nparams))
+
+    def apply(self, r: torch.Tensor, z: torch.Tensor):
+        assert r.is_cuda and z.is_cuda and r.dtype == torch.float64 and z.dtype == torch.float64
+        self._check(self.lib.cfd_unet_apply(self.u, ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(z.data_ptr())))
+
+    def train_step(self, r: torch.Tensor, e: torch.Tensor, lr=1e-3) -> float:
+        assert r.is_cuda and e.is_cuda and r.dtype == torch.float64 and e.dtype == torch.float64
+        assert r.numel() == e.numel() and r.numel() % self.cells == 0
+        loss = ctypes.c_float(0.0)
+        self._check(self.lib.cfd_unet_train_step(self.u, ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(e.data_ptr()),
+                                                 r.numel() // self.cells, ctypes.c_float(lr), ctypes.byref(loss)))
+        return float(loss.value)
+
+    def read_tensor(self, which) -> torch.Tensor:
+        """Host copy of a model tensor: a name from UNET_TENSORS (BF16,
+        shape [cells of its level, channels]) or a UNET_T_* code."""
+        if isinstance(which, str):
+            which = UNET_TENSORS.index(which)
+        nx, ny, nz = self.shape
+        if 0 <= which < 26:
+            lv = UNET_LEVELS[which]
+            vox = (nx >> lv) * (ny >> lv) * (nz >> lv)
+            out = torch.empty(vox, UNET_CHANNELS[which], dtype=torch.bfloat16)
+        elif which in (UNET_T_OUT, UNET_T_TARGET):
+            out = torch.empty(self.cells, dtype=torch.float32)
+        else:
+            out = torch.empty(self.nparams, dtype=torch.float32)
+        self._check(self.lib.cfd_unet_read_tensor(self.u, int(which), ctypes.c_void_p(out.data_ptr()), out.numel()))
+        return out
+
+    def fpcg_solve(self, b: torch.Tensor, x: torch.Tensor, rtol=1e-8, max_iters=0):
+        assert b.is_cuda and x.is_cuda and b.dtype == torch.float64 and x.dtype == torch.float64
+        st = cfd_solve_stats()
+        rc = self.lib.cfd_unet_fpcg_solve(self.u, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                          ctypes.c_double(rtol), int(max_iters), ctypes.byref(st))
+        self._check(rc, allow=(CFD_ERR_NOT_CONVERGED, CFD_ERR_BREAKDOWN, CFD_ERR_TIMEOUT))
+        return rc, st.as_dict()
+
+    def launch_count(self) -> int:
+        return int(self.lib.cfd_unet_launch_count(self.u))

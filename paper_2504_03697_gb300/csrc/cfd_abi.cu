@@ -597,6 +597,17 @@ int cfd_apply_poisson(cfd_handle* h, const double* x_dev, double* y_dev) {
   return cuda_check(h, launch_apply_poisson(g, x_dev, y_dev, tz_for(g.mz), h->stream, &h->launches), "apply_poisson");
 }
 
+int cfd_pressure_rhs(cfd_handle* h, double* b_dev) {
+  if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
+  if (!b_dev) return set_err(h, CFD_ERR_INVALID_ARG, "b is NULL");
+  // the divergence sweep reads the intermediate-velocity slots: point them
+  // at the current velocity and its output at the caller's array
+  PhysArgs pa = phys(h);
+  pa.ua = h->u; pa.va = h->v; pa.wa = h->w;
+  pa.b = b_dev;
+  return cuda_check(h, launch_divergence(pa, h->stream, &h->launches), "divergence");
+}
+
 int64_t cfd_launch_count(const cfd_handle* h) { return h ? h->launches : 0; }
 
 int cfd_set_solver_shape(cfd_handle* h, int blocks_per_sm, int tile_depth) {
