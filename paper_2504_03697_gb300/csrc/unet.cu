@@ -25,9 +25,12 @@
 //   * 2x average pooling and nearest 2x up-sampling (and their adjoints).
 
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "cfd_internal.h"
 #include "tc_common.cuh"
@@ -209,10 +212,316 @@ __global__ void __launch_bounds__(kConvThreads) conv3d_tc_kernel(const ConvArgs 
   if (t < 32) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
+// ---------------------------------------------------------------------------
+// Tiled 3x3x3 convolution: one TMA-staged input tile per 16-channel block,
+// every tap read in place by shifting the A descriptor.
+//
+// A CTA owns an output box of xc x ty x tz voxels.  For each 16-channel
+// block, two TMA loads bring the input box with a one-voxel halo ((xc + 2) x
+// (ty + 2) x (tz + 2) voxels, zero outside the grid) into two shared-memory
+// planes, one per 8-channel K-half; voxel (x, y, z) of the box is "row" r =
+// (z (ty + 2) + y)(xc + 2) + x at byte r * 16 of each plane.  Read with a
+// stride byte offset of 128 (8-row groups back to back) and a leading byte
+// offset of the plane distance, any 128 consecutive rows form a valid K-major
+// A operand, so the operand of tap (dx, dy, dz) for output rows [s, s + 128)
+// is simply rows [s + dz (ty+2)(xc+2) + dy (xc+2) + dx, ...): one tile load
+// serves all 27 taps.  Output rows are taken in M-blocks of 128 consecutive
+// rows (one x-line each when xc = 126 ... 128, "line mode"; otherwise
+// consecutive rows from the first interior row); rows that fall on halo
+// voxels are computed and discarded.  M-block j accumulates in TMEM columns
+// [j NOUT, (j + 1) NOUT).  The weights of the channel block (27 taps x NOUT
+// rows x 16) are copied to shared memory as K-major core matrices.
+// ---------------------------------------------------------------------------
+
+constexpr int kTileMaxMB = 8;
+constexpr int kTileSmemMax = 210 * 1024;  // dynamic shared memory cap (static use is about 1 KB)
+
+struct ConvTileArgs {
+  CUtensorMap map0;            // src0 [nz][ny][nx][c0], box {8, bx, by, bz}
+  CUtensorMap map1;            // src1 (concatenation) or unused
+  int nx, ny, nz;
+  int c0, c1;
+  int xc, ty, tz;              // output box
+  int bx, by, bz;              // input box (output box + halo)
+  int line_mode;
+  int mb;                      // M-blocks per CTA
+  int plane;                   // bytes between the two K-half planes (16-multiple)
+  int tiles_x, tiles_y;
+  const __nv_bfloat16* w;      // [27][NOUT][cin_pad]
+  int cin_pad;
+  const float* bias;
+  int cout;
+  __nv_bfloat16* dst0;
+  __nv_bfloat16* dst1;
+  int split;
+  int* err;
+};
+
+__device__ __forceinline__ int tile_block_start(const ConvTileArgs& a, int j) {
+  if (a.line_mode) return ((1 + j / a.ty) * a.by + 1 + j % a.ty) * a.bx + 1;
+  return (a.by + 1) * a.bx + 1 + 128 * j;
+}
+
+template <int NOUT>
+__global__ void __launch_bounds__(kConvThreads) conv3d_tile_kernel(const __grid_constant__ ConvTileArgs a) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  __shared__ __align__(8) uint64_t bar_tma, bar_mma;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+  constexpr int kBTap = NOUT * 32;  // bytes of one tap's B operand
+  unsigned char* plane0 = dsm;
+  unsigned char* plane1 = dsm + a.plane;
+  unsigned char* sb = dsm + 2 * a.plane;
+
+  const int t = threadIdx.x;
+  const int tx = blockIdx.x % a.tiles_x;
+  const int ty_ = (blockIdx.x / a.tiles_x) % a.tiles_y;
+  const int tz_ = blockIdx.x / (a.tiles_x * a.tiles_y);
+  const int x0 = tx * a.xc, y0 = ty_ * a.ty, z0 = tz_ * a.tz;
+  const int cb0 = a.c0 / 16;
+  const int ncb = cb0 + a.c1 / 16;
+  const uint32_t tmem_cols = (a.mb * NOUT <= 32) ? 32u : (a.mb * NOUT <= 64 ? 64u : (a.mb * NOUT <= 128 ? 128u : (a.mb * NOUT <= 256 ? 256u : 512u)));
+  const unsigned box_bytes = unsigned(a.bx) * a.by * a.bz * 16;
+
+  if (t == 0) {
+    tc::mbar_init(&bar_tma, 1);
+    tc::mbar_init(&bar_mma, 1);
+    tc::mbar_fence_init();
+    s_fail = 0;
+  }
+  if (t < 32) tc::tmem_alloc(&s_tmem, tmem_cols);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = s_tmem;
+  const uint32_t idesc = tc::idesc_bf16_f32(128, NOUT);
+  const int row_z = a.by * a.bx;
+
+  bool tma_pending = false;
+  for (int cb = 0; cb < ncb; ++cb) {
+    if (cb > 0) {
+      // the MMAs of the previous channel block read these buffers
+      if (!tc::mbar_wait(&bar_mma, unsigned((cb - 1) & 1), kConvWaitNs)) s_fail = 1;
+    }
+    // weights of this channel block: [tap][NOUT][16] as K-major core matrices
+    for (int i = t; i < 27 * NOUT * 2; i += kConvThreads) {
+      const int h = i & 1, o = (i >> 1) % NOUT, tap = (i >> 1) / NOUT;
+      const uint4 v = *reinterpret_cast<const uint4*>(a.w + (size_t(tap) * NOUT + o) * a.cin_pad + 16 * cb + 8 * h);
+      store16B(sb + tap * kBTap + tc::core_offset(o, h), v);
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (s_fail) break;
+    if (t == 0) {
+      const void* map = cb < cb0 ? static_cast<const void*>(&a.map0) : static_cast<const void*>(&a.map1);
+      const int c = 16 * (cb < cb0 ? cb : cb - cb0);
+      tc::mbar_expect_tx(&bar_tma, 2 * box_bytes);
+      tc::tma_load_4d(plane0, map, c, x0 - 1, y0 - 1, z0 - 1, &bar_tma);
+      tc::tma_load_4d(plane1, map, c + 8, x0 - 1, y0 - 1, z0 - 1, &bar_tma);
+    }
+    tma_pending = true;
+    if (!tc::mbar_wait(&bar_tma, unsigned(cb & 1), kConvWaitNs)) {
+      s_fail = 1;
+      break;
+    }
+    tma_pending = false;
+    tc::fence_after_sync();
+    if (t == 0) {
+      const uint32_t pa = tc::smem_addr(plane0), pb = tc::smem_addr(sb);
+      for (int tap = 0; tap < 27; ++tap) {
+        const int off = (tap / 9 - 1) * row_z + ((tap / 3) % 3 - 1) * a.bx + (tap % 3 - 1);
+        const uint64_t bdesc = tc::smem_desc(pb + uint32_t(tap * kBTap), 128, 256);
+        for (int j = 0; j < a.mb; ++j) {
+          const int row = tile_block_start(a, j) + off;
+          tc::mma_bf16(tmem + uint32_t(j * NOUT), tc::smem_desc(pa + uint32_t(row) * 16u, uint32_t(a.plane), 128), bdesc,
+                       idesc, (cb | tap) != 0);
+        }
+      }
+      tc::mma_commit(&bar_mma);
+    }
+  }
+  __syncthreads();
+  if (!s_fail && ncb > 0) {
+    if (!tc::mbar_wait(&bar_mma, unsigned((ncb - 1) & 1), kConvWaitNs)) s_fail = 1;
+  }
+  __syncthreads();
+  tc::fence_after_sync();
+  if (s_fail) {
+    if (t == 0) atomicExch(a.err, 1);
+    // let a copy still in flight land before the CTA's shared memory goes away
+    if (tma_pending) tc::mbar_wait(&bar_tma, unsigned((ncb - 1) & 1), kConvWaitNs);
+  } else {
+    const int w = t / 32;
+    const int bxby = a.bx * a.by;
+    for (int j = 0; j < a.mb; ++j) {
+      const int row = tile_block_start(a, j) + t;  // this thread's TMEM lane = row t of block j
+      const int zq = row / bxby, rem = row - zq * bxby;
+      const int yq = rem / a.bx, xq = rem - yq * a.bx;
+      const int gx = x0 + xq - 1, gy = y0 + yq - 1, gz = z0 + zq - 1;
+      const bool valid = xq >= 1 && xq <= a.xc && yq >= 1 && yq <= a.ty && zq >= 1 && zq <= a.tz && gx < a.nx &&
+                         gy < a.ny && gz < a.nz;
+      const size_t v = (size_t(gz) * a.ny + gy) * a.nx + gx;
+#pragma unroll
+      for (int c0 = 0; c0 < NOUT; c0 += 16) {
+        float acc[16];
+        tc::tmem_ld16(tmem + (uint32_t(w * 32) << 16) + uint32_t(j * NOUT + c0), acc);
+        if (valid && c0 < a.cout) {
+#pragma unroll
+          for (int half = 0; half < 2; ++half) {
+            const int cbase = c0 + 8 * half;
+            if (cbase >= a.cout) break;
+            __nv_bfloat16 o8[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) o8[k] = __float2bfloat16(acc[8 * half + k] + (a.bias ? a.bias[cbase + k] : 0.f));
+            __nv_bfloat16* dst = cbase < a.split ? a.dst0 + v * a.split + cbase
+                                                 : a.dst1 + v * (a.cout - a.split) + (cbase - a.split);
+            *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<uint4*>(o8);
+          }
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (t < 32) tc::tmem_dealloc(tmem, tmem_cols);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  });
+  return encode;
+}
+
+// channels-last BF16 grid [nz][ny][nx][C] with an {8, bx, by, bz} box
+bool encode_cl_map(CUtensorMap* m, const __nv_bfloat16* base, int C, int nx, int ny, int nz, int bx, int by, int bz) {
+  auto encode = tensor_map_encoder();
+  if (!encode || C % 8 != 0 || (reinterpret_cast<uintptr_t>(base) & 15) || bx > 256 || by > 256 || bz > 256) return false;
+  cuuint64_t dims[4] = {cuuint64_t(C), cuuint64_t(nx), cuuint64_t(ny), cuuint64_t(nz)};
+  cuuint64_t strides[3] = {cuuint64_t(C) * 2, cuuint64_t(C) * nx * 2, cuuint64_t(C) * nx * ny * 2};
+  cuuint32_t box[4] = {8, cuuint32_t(bx), cuuint32_t(by), cuuint32_t(bz)};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  return encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(base), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Output box of the tiled kernel for an nx-wide grid: full x-lines of up to
+// 128 voxels (line mode for 126..128) or consecutive 128-row blocks.
+bool pick_tile(ConvTileArgs& t, int nout) {
+  t.xc = t.nx >= 128 ? 128 : t.nx;
+  t.bx = t.xc + 2;
+  t.line_mode = t.xc == 128 ? 1 : 0;
+  const int max_mb = std::min(kTileMaxMB, 512 / nout);
+  int best_ty = 1, best_tz = 1, best_mb = 0;
+  double best_eff = -1.0;
+  for (int tz = 1; tz <= 4; tz *= 2) {
+    for (int ty = 1; ty <= 8; ty *= 2) {
+      if (ty > t.ny || tz > t.nz) continue;
+      int mb;
+      if (t.line_mode) {
+        mb = ty * tz;
+      } else {
+        const int by = ty + 2, first = (by + 1) * t.bx + 1, last = (tz * by + ty) * t.bx + t.xc;
+        mb = (last - first + 1 + 127) / 128;
+      }
+      if (mb > max_mb) continue;
+      const int rows = t.bx * (ty + 2) * (tz + 2);
+      const size_t smem = 2 * size_t((rows * 16 + 2048 + 127) / 128 * 128) + size_t(27) * nout * 32;
+      if (smem > 200 * 1024) continue;
+      // useful outputs per unit of (MMA rows + loaded rows)
+      const double eff = double(t.xc * ty * tz) / double(mb * 128 * 27 + rows * 4);
+      if (eff > best_eff + 1e-12) {
+        best_eff = eff;
+        best_ty = ty;
+        best_tz = tz;
+        best_mb = mb;
+      }
+    }
+  }
+  if (best_mb == 0) return false;
+  t.ty = best_ty;
+  t.tz = best_tz;
+  t.by = t.ty + 2;
+  t.bz = t.tz + 2;
+  t.mb = best_mb;
+  // plane: the box rows plus slack for M-blocks that run past the last row
+  // (contiguous mode reads up to 127 rows + one z-slab beyond it)
+  const int rows = t.bx * t.by * t.bz;
+  const int slack = t.line_mode ? 0 : 128 + t.bx * t.by + t.bx + 1;
+  t.plane = (rows + slack) * 16;
+  t.plane = (t.plane + 127) / 128 * 128;
+  t.tiles_x = (t.nx + t.xc - 1) / t.xc;
+  t.tiles_y = (t.ny + t.ty - 1) / t.ty;
+  return true;
+}
+
+template <int NOUT>
+cudaError_t launch_tile(const ConvArgs& a, cudaStream_t s, bool& taken) {
+  taken = false;
+  ConvTileArgs t{};
+  t.nx = a.nx; t.ny = a.ny; t.nz = a.nz;
+  t.c0 = a.c0; t.c1 = a.c1;
+  if (!pick_tile(t, NOUT)) return cudaSuccess;
+  if (!encode_cl_map(&t.map0, a.src0, a.c0, a.nx, a.ny, a.nz, t.bx, t.by, t.bz)) return cudaSuccess;
+  if (a.c1 > 0 && !encode_cl_map(&t.map1, a.src1, a.c1, a.nx, a.ny, a.nz, t.bx, t.by, t.bz)) return cudaSuccess;
+  t.w = a.w;
+  t.cin_pad = (a.c0 + a.c1 + 15) / 16 * 16;
+  t.bias = a.bias;
+  t.cout = a.cout;
+  t.dst0 = a.dst0; t.dst1 = a.dst1; t.split = a.split;
+  t.err = a.err;
+  const size_t smem = 2 * size_t(t.plane) + size_t(27) * NOUT * 32;
+  // TMEM: at most 512 / cols CTAs may share an SM; pad the shared-memory
+  // request so that no more than that many fit
+  const int need = t.mb * NOUT;
+  const int cols = need <= 32 ? 32 : (need <= 64 ? 64 : (need <= 128 ? 128 : (need <= 256 ? 256 : 512)));
+  const int max_ctas = 512 / cols;
+  size_t req = smem;
+  const size_t sm_total = 228 * 1024;
+  if ((req + 1024) * size_t(max_ctas + 1) <= sm_total) req = sm_total / size_t(max_ctas + 1) - 1024 + 16;
+  if (req > kTileSmemMax) return cudaSuccess;
+  static int configured = 0;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(conv3d_tile_kernel<NOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemMax);
+    if (e != cudaSuccess) return e;
+    configured = 1;
+  }
+  const unsigned grid = unsigned(t.tiles_x) * unsigned(t.tiles_y) * unsigned((t.nz + t.tz - 1) / t.tz);
+  conv3d_tile_kernel<NOUT><<<grid, kConvThreads, req, s>>>(t);
+  taken = true;
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+bool conv3d_tile_eligible(const ConvArgs& a) {
+  return a.ks == 3 && !a.packed && a.c0 % 16 == 0 && a.c1 % 16 == 0 && !a.dst_f32 && a.cout % 8 == 0 &&
+         a.split % 8 == 0 && !(reinterpret_cast<uintptr_t>(a.w) & 15) && !(reinterpret_cast<uintptr_t>(a.dst0) & 15) &&
+         !(a.dst1 && (reinterpret_cast<uintptr_t>(a.dst1) & 15));
+}
 
 cudaError_t launch_conv3d(const ConvArgs& a, int nout_pad, cudaStream_t s) {
   const size_t V = size_t(a.nx) * a.ny * a.nz;
+  if (conv3d_tile_eligible(a) && !a.no_tile) {
+    bool taken = false;
+    cudaError_t e = cudaSuccess;
+    switch (nout_pad) {
+      case 16: e = launch_tile<16>(a, s, taken); break;
+      case 32: e = launch_tile<32>(a, s, taken); break;
+      case 64: e = launch_tile<64>(a, s, taken); break;
+      default: break;
+    }
+    if (e != cudaSuccess || taken) return e;
+  }
   const unsigned grid = unsigned((V + 127) / 128);
   switch (nout_pad) {
     case 16: conv3d_tc_kernel<16><<<grid, kConvThreads, 0, s>>>(a); break;

@@ -24,8 +24,13 @@ struct ConvArgs {
   int split;                     // == cout when dst1 is null
   float* dst_f32;                // if non-null: FP32 [V][cout] output instead of dst0/dst1
   int* err;                      // set to 1 on a device-side wait timeout
+  int no_tile;                   // 1: never take the TMA-tiled kernel
 };
 
+// Launch the convolution: the TMA-tiled kernel for 3x3x3 layers whose
+// sources have 16k channels (see conv3d_tile_eligible), else the gathering
+// kernel.
 cudaError_t launch_conv3d(const ConvArgs& a, int nout_pad, cudaStream_t s);
+bool conv3d_tile_eligible(const ConvArgs& a);
 
 }  // namespace cfd

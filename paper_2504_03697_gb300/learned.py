@@ -1,0 +1,235 @@
+"""Harvest, training and evaluation of the learned U-Net preconditioner.
+
+The paper preconditions its pressure CG with DIC or Jacobi (Sec. 3.1) and
+names other preconditioners as future work (Sec. 5); this module trains the
+U-Net of ``cfd_unet_*`` for flexible PCG on the cavity's pressure systems.
+
+Training data (a reading; the paper has no learned component): lid-driven
+cavities at n^3 with nu ~ log-uniform[1e-4, 1e-2] and lid speed ~
+uniform[0.5, 2] drawn from the seed, dt 0.01, started from the seeded
+perturbation.  At selected steps the projection's right-hand side b is
+taken after forces, advection and diffusion (``cfd_pressure_rhs``), solved
+to rtol 1e-12 for x*, and the CG iterates x_k (k = 1, 2, 4, ...) give the
+pairs r_k = b - A x_k, e_k = x* - x_k (mean removed).  The whole data set
+stays resident in HBM; each Adam step takes a minibatch of pairs.
+
+Everything here goes through the C-ABI (the solves, the network, its
+training step); torch only holds device memory and gathers minibatches.
+
+Command line:
+    python -m paper_2504_03697_gb300.learned train [--n 128] [--out FILE]
+    python -m paper_2504_03697_gb300.learned eval  [--n 128] [--weights FILE]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import time
+
+import numpy as np
+import torch
+
+from . import cfd
+from .synthetic import cavity_perturbation, gaussian_rhs, uniform01
+
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "unet_cavity128.f32")
+TRAIN_SEEDS = tuple(range(100, 116))
+EVAL_SEEDS = tuple(range(200, 204))
+
+
+def cavity_config(seed: int):
+    """nu ~ log-uniform[1e-4, 1e-2], lid speed ~ uniform[0.5, 2] from the seed."""
+    u = uniform01(seed, 7, np.arange(2, dtype=np.uint64))
+    return {"nu": float(10.0 ** (-4.0 + 2.0 * u[0])), "lid_u": float(0.5 + 1.5 * u[1])}
+
+
+def new_cavity(n: int, seed: int, solver="cg"):
+    c = cavity_config(seed)
+    cav = cfd.Cavity(cfd.make_params(n, n, n, dt=0.01, nu=c["nu"], lid_u=c["lid_u"], solver=solver, rtol=1e-8))
+    for name, f in zip("uvw", cavity_perturbation(n, n, n, seed)):
+        cav.set_field(name, f)
+    return cav
+
+
+def pressure_systems(n: int, seed: int, at_steps):
+    """Yield (step, b): the projection right-hand side of the cavity of this
+    seed at each of the given steps (1-based), taken after forces, advection
+    and diffusion of that step; the run continues through the projection."""
+    cav = new_cavity(n, seed)
+    b = torch.empty(n ** 3, dtype=torch.float64, device="cuda")
+    for s in range(1, max(at_steps) + 1):
+        if s in at_steps:
+            for which in ("forces", "advect", "diffuse"):
+                cav.substep(which, stats=False)
+            cav.pressure_rhs(b)
+            yield s, b.clone()
+            cav.substep("project", stats=False)
+        else:
+            cav.step(1, stats=False)
+    cav.close()
+
+
+class Harvester:
+    """Pressure systems and CG-iterate pairs of one grid size."""
+
+    def __init__(self, n: int, ks=(1, 2, 4, 8, 16, 32, 64, 128)):
+        self.n = n
+        self.ks = tuple(ks)
+        self.exact = cfd.Cavity(cfd.make_params(n, n, n, rtol=1e-12, max_iters=50 * n))
+        self.capped = {k: cfd.Cavity(cfd.make_params(n, n, n, rtol=1e-15, max_iters=k)) for k in self.ks}
+
+    def pairs(self, b: torch.Tensor):
+        """(R, E) [len(ks), V] for one system."""
+        V = b.numel()
+        bm = b - b.mean()
+        xs = torch.zeros_like(bm)
+        self.exact.solve_pressure(bm, xs, stats=False)
+        R = torch.empty(len(self.ks), V, dtype=torch.float64, device="cuda")
+        E = torch.empty_like(R)
+        xk = torch.empty_like(bm)
+        for i, k in enumerate(self.ks):
+            xk.zero_()
+            self.capped[k].solve_pressure(bm, xk, stats=False)
+            self.exact.apply_poisson(xk, R[i])
+            R[i].neg_().add_(bm)
+            E[i].copy_(xs).sub_(xk)
+            E[i].sub_(E[i].mean())
+        return R, E
+
+
+def harvest(n: int, seeds, at_steps, ks, log=print):
+    h = Harvester(n, ks)
+    Rs, Es = [], []
+    t0 = time.time()
+    for seed in seeds:
+        for step, b in pressure_systems(n, seed, set(at_steps)):
+            R, E = h.pairs(b)
+            Rs.append(R)
+            Es.append(E)
+        log(f"  harvested seed {seed}: {sum(r.shape[0] for r in Rs)} pairs, {time.time() - t0:.1f}s")
+    return torch.cat(Rs), torch.cat(Es)
+
+
+def train(net: cfd.UNet, R: torch.Tensor, E: torch.Tensor, iters: int, batch: int, lr: float, seed=0, log=print,
+          log_every=50):
+    g = torch.Generator().manual_seed(seed)
+    P = R.shape[0]
+    losses = []
+    t0 = time.time()
+    for it in range(iters):
+        idx = torch.randperm(P, generator=g)[:batch].cuda()
+        rb = R.index_select(0, idx).contiguous()
+        eb = E.index_select(0, idx).contiguous()
+        cur_lr = lr * (0.1 if it >= int(0.8 * iters) else 1.0)
+        losses.append(net.train_step(rb, eb, lr=cur_lr))
+        if log_every and (it % log_every == 0 or it == iters - 1):
+            log(f"  iter {it:5d}  loss {np.mean(losses[-log_every:]):.5g}  {time.time() - t0:.1f}s")
+    return losses
+
+
+def save_params(params: torch.Tensor, path: str, meta: dict):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    params.detach().cpu().to(torch.float32).numpy().astype("<f4").tofile(path)
+    with open(path + ".json", "w") as f:
+        json.dump(meta, f, indent=1, sort_keys=True)
+
+
+def load_params(path: str = WEIGHTS) -> torch.Tensor:
+    return torch.from_numpy(np.fromfile(path, dtype="<f4").astype(np.float32))
+
+
+def eval_systems(n: int, seeds=EVAL_SEEDS, step=10, gaussian_seeds=(0,)):
+    """Held-out pressure systems: step `step` of each seed, plus Gaussian
+    right-hand sides (out of distribution)."""
+    out = []
+    for seed in seeds:
+        for s, b in pressure_systems(n, seed, {step}):
+            out.append((f"cavity seed {seed} step {s}", b))
+    for gs in gaussian_seeds:
+        out.append((f"gaussian seed {gs}", torch.from_numpy(gaussian_rhs(n, n, n, gs).reshape(-1)).cuda()))
+    return out
+
+
+def time_call(fn, reps=1):
+    st = torch.cuda.Event(enable_timing=True)
+    en = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    st.record()
+    for _ in range(reps):
+        out = fn()
+    en.record()
+    torch.cuda.synchronize()
+    return st.elapsed_time(en) / reps, out
+
+
+def evaluate(n: int, params: torch.Tensor, systems, rtol=1e-8, log=print):
+    """FPCG with the network vs FP64 CG and the FP32/FP64 refined solve on
+    the same systems; time to the FP64 true-residual rtol."""
+    net = cfd.UNet(n, n, n, seed=0)
+    net.set_params(params)
+    cg = cfd.Cavity(cfd.make_params(n, n, n, rtol=rtol, solver="cg"))
+    ir = cfd.Cavity(cfd.make_params(n, n, n, rtol=rtol, solver="ir"))
+    x = torch.zeros(n ** 3, dtype=torch.float64, device="cuda")
+    z = torch.empty_like(x)
+    t_apply, _ = time_call(lambda: net.apply(systems[0][1], z), reps=5)
+    rows = []
+    for name, b in systems:
+        row = {"system": name}
+        for label, fn in (("cg", lambda: cg.solve_pressure(b, x)), ("ir", lambda: ir.solve_pressure(b, x)),
+                          ("fpcg", lambda: net.fpcg_solve(b, x, rtol=rtol))):
+            fn()  # warm-up
+            ms, (rc, st) = time_call(fn)
+            row[label] = {"ms": ms, "iters": st["iters"], "plain_iters": st["outer_iters"], "status": st["status"],
+                          "rel_resid": st["rel_resid"]}
+        rows.append(row)
+        log(f"  {name}: " + ", ".join(f"{k} {row[k]['ms']:.1f} ms / {row[k]['iters']} it"
+                                       for k in ("cg", "ir", "fpcg")))
+    return {"n": n, "unet_apply_ms": t_apply, "rows": rows}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("mode", choices=["train", "eval"])
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--seeds", type=int, default=len(TRAIN_SEEDS))
+    ap.add_argument("--steps", type=str, default="2,5,10,15,20")
+    ap.add_argument("--iters", type=int, default=2000)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--out", default=WEIGHTS)
+    ap.add_argument("--weights", default=WEIGHTS)
+    ap.add_argument("--eval-n", type=str, default="128")
+    ap.add_argument("--json", default=None)
+    a = ap.parse_args(argv)
+    from . import build
+    build.build()
+    result = {}
+    if a.mode == "train":
+        at = [int(s) for s in a.steps.split(",")]
+        print(f"harvest: {a.seeds} cavities at {a.n}^3, steps {at}")
+        R, E = harvest(a.n, TRAIN_SEEDS[:a.seeds], at, (1, 2, 4, 8, 16, 32, 64, 128))
+        print(f"{R.shape[0]} pairs ({R.numel() * 16 / 1e9:.1f} GB resident)")
+        net = cfd.UNet(a.n, a.n, a.n, seed=0)
+        t0 = time.time()
+        losses = train(net, R, E, a.iters, a.batch, a.lr)
+        params = net.get_params()
+        meta = {"n": a.n, "train_seeds": list(TRAIN_SEEDS[:a.seeds]), "steps": at, "iters": a.iters,
+                "batch": a.batch, "lr": a.lr, "pairs": int(R.shape[0]), "first_loss": losses[0],
+                "final_loss": float(np.mean(losses[-50:])), "train_seconds": time.time() - t0}
+        save_params(params, a.out, meta)
+        print(json.dumps(meta))
+        result["train"] = meta
+        del R, E
+        a.weights = a.out
+    params = load_params(a.weights)
+    for n in [int(s) for s in a.eval_n.split(",") if s]:
+        print(f"evaluate at {n}^3")
+        result[f"eval_{n}"] = evaluate(n, params, eval_systems(n))
+    if a.json:
+        with open(a.json, "w") as f:
+            json.dump(result, f, indent=1)
+
+
+if __name__ == "__main__":
+    main()
