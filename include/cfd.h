@@ -296,14 +296,17 @@ int cfd_pressure_rhs(cfd_handle *h, double *b_dev);
 
 /* One stride-1 3D convolution on the tensor cores (BF16 operands, FP32
  * accumulation), the U-Net's building block, exposed for direct checks.
- * Grid nx x ny x nz (x fastest), zero padding.  src0: device BF16 [V][c0]
- * (channels-last); src1: [V][c1] concatenated after src0 (c1 = 0: unused;
- * c1 > 0 needs c0 % 16 == 0).  ks = 3 or 1.  weights: device BF16
+ * Grid nx x ny x nz (x fastest, V cells), zero padding.  Activations are
+ * BF16 "channel-octet planes": a tensor of C channels is ceil(C / W) planes
+ * of [V][W], W = min(C, 8), so channel c of cell v is element
+ * (c / W) V W + v W + c % W.  src0: c0 channels; src1: c1 channels
+ * concatenated after src0 (c1 = 0: unused; c1 > 0 needs c0 % 16 == 0).  ks = 3 or 1.  weights: device BF16
  * [ks^3][nout_pad][cin_pad] (cin_pad = c0 + c1 rounded up to 16, tap index
  * kx + 3 ky + 9 kz, zero-filled padding), or for c0 = 1, c1 = 0, ks = 3 the
  * tap-packed [nout_pad][32] (taps 0..26, zeros after).  bias: device FP32
  * [cout] or NULL.  cout <= nout_pad in {16, 32, 64}.  Output: dst_bf16
- * [V][cout] BF16, or dst_f32 [V][cout] FP32 when dst_f32 is non-NULL.
+ * (cout channels, octet planes), or dst_f32 [V][cout] FP32 when dst_f32
+ * is non-NULL.  All pointers 16-byte aligned.
  * err_dev: device int set to 1 if a bounded device-side wait timed out.
  * Asynchronous on stream; returns a negative code on invalid arguments. */
 int cfd_conv3d_bf16(int nx, int ny, int nz, const void *src0, int c0, const void *src1, int c1, int ks,
@@ -337,13 +340,21 @@ int cfd_unet_set_params(cfd_unet *u, const float *host, int64_t n);
 int cfd_unet_apply(cfd_unet *u, const double *r_dev, double *z_dev);
 
 /* One Adam step (lr, beta 0.9 / 0.999, eps 1e-8) on the mean over npairs
- * pairs of the loss |U(s r) - s e|^2 / V, r_dev and e_dev device float64
+ * pairs of the loss (cfd_unet_set_loss; default |U(s r) - s e|^2 / V), with
+ * s = sqrt(V) / ||r|| per pair; r_dev and e_dev device float64
  * [npairs][V].  *loss (nullable) receives the mean loss before the step.
  * Synchronises the stream. */
 int cfd_unet_train_step(cfd_unet *u, const double *r_dev, const double *e_dev, int npairs, float lr, float *loss);
 
+/* Training loss of cfd_unet_train_step (per pair, with d = U(s r) - s e):
+ *   MSE    |d|^2 / V                 (the default)
+ *   ANORM  d.(A d) / V, A the operator of cfd_apply_poisson (the error
+ *          measured in the energy norm CG minimises)                    */
+enum { CFD_UNET_LOSS_MSE = 0, CFD_UNET_LOSS_ANORM = 1 };
+int cfd_unet_set_loss(cfd_unet *u, int kind);
+
 /* Tensor read-back for checks (synchronous).  which in 0..25: the BF16
- * channels-last tensors xin, a0, s0, p0, a1, s1, p1, a2, s2, u1, d1, u0, d0
+ * tensors (octet planes) xin, a0, s0, p0, a1, s1, p1, a2, s2, u1, d1, u0, d0
  * (activations of the last forward pass) and gz, g_d0, g_s0, g_u0, g_d1,
  * g_s1, g_u1, g_s2, g_a2, g_p1, g_a1, g_p0, g_a0 (their gradients from the
  * last backward pass); or one of the CFD_UNET_T_* below.  count must equal

@@ -15,8 +15,9 @@ reading of that item (architecture, scaling and loss are not in the paper):
     head 1^3 16 -> 1
   every convolution stride 1, zero padding ("same"), with bias;
 * preconditioner M(r) = U(s r) / s minus its mean, s = sqrt(V) / ||r||;
-* training loss on one pair (r, e): mean over cells of (U(s r) - s e)^2, Adam
-  (beta 0.9 / 0.999, eps 1e-8) on the mean loss over a batch of pairs.
+* training loss on one pair (r, e), d = U(s r) - s e: mean over cells of
+  d^2, or the energy norm d.(A d) / V (A the Neumann pressure operator);
+  Adam (beta 0.9 / 0.999, eps 1e-8) on the mean loss over a batch of pairs.
 
 Parameters travel as one flat float vector: per layer in the order above,
 weights [taps][cout][cin] with tap = kx + 3 ky + 9 kz, then bias [cout].
@@ -27,7 +28,8 @@ and the two are adjoint up to the factor 8; a centre-tap identity kernel
 reproduces its input and a one-tap kernel shifts it with zero fill; a
 hand-set network whose layers pass channel 0 through computes x +
 up(pool x) + up(up(pool(pool x))), checked against block means computed with
-numpy reshapes; gradients against finite differences; one Adam step from
+numpy reshapes; the loss operator against the assembled CSR matrix and its
+null space; gradients against finite differences; one Adam step from
 zero moments moves every weight by lr * sign(g) (|g| >> eps); M is
 invariant to the scale of r.  This module is test infrastructure (see the
 package header).
@@ -119,9 +121,31 @@ def precondition(layers, r: np.ndarray) -> np.ndarray:
     return z - z.mean()
 
 
-def loss_and_grad(flat, pairs):
-    """Mean over pairs of mean((U(s r) - s e)^2) and its gradient w.r.t. the
-    flat parameters (autograd)."""
+def neumann_apply(d):
+    """(A d) for the Neumann 7-point pressure operator on a (Z, Y, X) field:
+    sum over the neighbours inside the grid of (d_c - d_n)."""
+    out = torch.zeros_like(d)
+    for ax in range(3):
+        n = d.shape[ax]
+        if n < 2:
+            continue
+        diff = d.narrow(ax, 1, n - 1) - d.narrow(ax, 0, n - 1)
+        out = out + F.pad(-diff, _pad_spec(ax, 0, 1)) + F.pad(diff, _pad_spec(ax, 1, 0))
+    return out
+
+
+def _pad_spec(ax, before, after):
+    # F.pad lists (last dim first) pairs; a (Z, Y, X) tensor has ax 0 = Z
+    spec = [0, 0, 0, 0, 0, 0]
+    k = 2 * (2 - ax)
+    spec[k], spec[k + 1] = before, after
+    return spec
+
+
+def loss_and_grad(flat, pairs, loss="mse"):
+    """Mean over pairs of the training loss and its gradient w.r.t. the flat
+    parameters (autograd).  With d = U(s r) - s e: "mse" = mean(d^2),
+    "anorm" = d.(A d) / V."""
     p = torch.as_tensor(flat, dtype=torch.float64).clone().requires_grad_(True)
     layers = unflatten(p)
     total = 0.0
@@ -129,7 +153,11 @@ def loss_and_grad(flat, pairs):
         s = scale_of(r)
         z, _ = forward(layers, torch.from_numpy(r * s)[None])
         t = torch.from_numpy(e * s)[None]
-        total = total + ((z - t) ** 2).mean()
+        d = (z - t)[0]
+        if loss == "anorm":
+            total = total + (d * neumann_apply(d)).sum() / d.numel()
+        else:
+            total = total + (d ** 2).mean()
     total = total / len(pairs)
     total.backward()
     return float(total.detach()), p.grad.detach().clone()

@@ -116,6 +116,7 @@ def load_library(path: Optional[str] = None):
         "cfd_unet_apply": (ctypes.c_int, [vp, vp, vp]),
         "cfd_unet_train_step": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_float, P(ctypes.c_float)]),
         "cfd_unet_read_tensor": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int64]),
+        "cfd_unet_set_loss": (ctypes.c_int, [vp, ctypes.c_int]),
         "cfd_unet_fpcg_solve": (ctypes.c_int, [vp, vp, vp, ctypes.c_double, ctypes.c_int32, P(cfd_solve_stats)]),
         "cfd_unet_launch_count": (ctypes.c_int64, [vp]),
         "cfd_unet_last_error": (ctypes.c_char_p, []),
@@ -372,6 +373,21 @@ class Batch:
         return int(self.lib.cfd_batch_launch_count(self.b))
 
 
+def to_octets(x: torch.Tensor) -> torch.Tensor:
+    """Channels-last [V, C] -> the library's activation layout: ceil(C / W)
+    planes of [V][W], W = min(C, 8) (flat)."""
+    V, C = x.shape
+    W = min(C, 8)
+    return x.reshape(V, C // W, W).permute(1, 0, 2).contiguous().reshape(-1)
+
+
+def from_octets(flat: torch.Tensor, C: int) -> torch.Tensor:
+    """Inverse of to_octets: flat octet planes -> channels-last [V, C]."""
+    W = min(C, 8)
+    V = flat.numel() // C
+    return flat.reshape(C // W, V, W).permute(1, 0, 2).reshape(V, C)
+
+
 # names of the BF16 tensors readable with UNet.read_tensor (indices 0..25)
 UNET_TENSORS = ["xin", "a0", "s0", "p0", "a1", "s1", "p1", "a2", "s2", "u1", "d1", "u0", "d0",
                 "gz", "g_d0", "g_s0", "g_u0", "g_d1", "g_s1", "g_u1", "g_s2", "g_a2", "g_p1", "g_a1", "g_p0", "g_a0"]
@@ -450,21 +466,28 @@ class UNet:
                                                  r.numel() // self.cells, ctypes.c_float(lr), ctypes.byref(loss)))
         return float(loss.value)
 
+    def set_loss(self, kind: str):
+        """'mse' (|d|^2 / V) or 'anorm' (d.(A d) / V), d = U(s r) - s e."""
+        self._check(self.lib.cfd_unet_set_loss(self.u, {"mse": 0, "anorm": 1}[kind]))
+
     def read_tensor(self, which) -> torch.Tensor:
         """Host copy of a model tensor: a name from UNET_TENSORS (BF16,
-        shape [cells of its level, channels]) or a UNET_T_* code."""
+        returned channels-last [cells of its level, channels]) or a UNET_T_*
+        code."""
         if isinstance(which, str):
             which = UNET_TENSORS.index(which)
         nx, ny, nz = self.shape
         if 0 <= which < 26:
             lv = UNET_LEVELS[which]
             vox = (nx >> lv) * (ny >> lv) * (nz >> lv)
-            out = torch.empty(vox, UNET_CHANNELS[which], dtype=torch.bfloat16)
+            out = torch.empty(vox * UNET_CHANNELS[which], dtype=torch.bfloat16)
         elif which in (UNET_T_OUT, UNET_T_TARGET):
             out = torch.empty(self.cells, dtype=torch.float32)
         else:
             out = torch.empty(self.nparams, dtype=torch.float32)
         self._check(self.lib.cfd_unet_read_tensor(self.u, int(which), ctypes.c_void_p(out.data_ptr()), out.numel()))
+        if 0 <= which < 26:
+            return from_octets(out, UNET_CHANNELS[which])
         return out
 
     def fpcg_solve(self, b: torch.Tensor, x: torch.Tensor, rtol=1e-8, max_iters=0):

@@ -121,6 +121,16 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const void* map, int c0, 
       : "memory");
 }
 
+// 5D tiled TMA load (coordinates innermost first) completing on bar.
+__device__ __forceinline__ void tma_load_5d(void* dst, const void* map, int c0, int c1, int c2, int c3, int c4,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+      "%6}], [%7];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_addr(bar))
+      : "memory");
+}
+
 // Byte offset of (row, K-half) in the no-swizzle K-major core-matrix layout.
 __device__ __forceinline__ int core_offset(int row, int khalf) { return (row >> 3) * 256 + khalf * 128 + (row & 7) * 16; }
 

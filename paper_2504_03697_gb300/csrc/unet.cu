@@ -8,7 +8,7 @@
 // Convolution = implicit GEMM on the 5th-generation tensor cores: one CTA
 // computes a tile of 128 output voxels x Cout channels; the K dimension runs
 // over (tap, 16-channel block).  For every K chunk all 128 threads gather
-// the shifted input rows (channels-last BF16, zero outside the grid) and the
+// the shifted input rows (BF16 octet planes, zero outside the grid) and the
 // weight rows into a shared-memory stage laid out as K-major core matrices,
 // one thread issues tcgen05.mma (M = 128, N = Cout, K = 16, FP32
 // accumulation in tensor memory) and commits it to the stage's mbarrier, so
@@ -79,6 +79,7 @@ __device__ __forceinline__ void gather_row(const ConvArgs& a, int x, int y, int 
   }
   const int xx = x + dx, yy = y + dy, zz = z + dz;
   if (xx < 0 || xx >= a.nx || yy < 0 || yy >= a.ny || zz < 0 || zz >= a.nz) return;
+  const size_t V = size_t(a.nx) * a.ny * a.nz;
   const size_t nb = (size_t(zz) * a.ny + yy) * a.nx + xx;
   const int c = 16 * cb;
   const __nv_bfloat16* src;
@@ -92,15 +93,15 @@ __device__ __forceinline__ void gather_row(const ConvArgs& a, int x, int y, int 
     cs = a.c1;
     cc = c - a.c0;
   }
-  if (cs % 16 == 0) {
-    const uint4* p = reinterpret_cast<const uint4*>(src + nb * cs + cc);
-    lo = p[0];
-    hi = p[1];
+  if (cs % 8 == 0) {
+    // two octet planes: channels cc .. cc + 7 and cc + 8 .. cc + 15
+    lo = *reinterpret_cast<const uint4*>(src + oct_index(nb, cc, cs, V));
+    if (cc + 8 < cs) hi = *reinterpret_cast<const uint4*>(src + oct_index(nb, cc + 8, cs, V));
   } else {
-    // narrow source (fewer than 16 channels): element loads, zero padding
+    // narrow source (fewer than 8 channels): element loads, zero padding
     __nv_bfloat16 vals[16];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) vals[j] = (cc + j < cs) ? src[nb * cs + cc + j] : __float2bfloat16(0.f);
+    for (int j = 0; j < 16; ++j) vals[j] = (cc + j < cs) ? src[oct_index(nb, cc + j, cs, V)] : __float2bfloat16(0.f);
     lo = *reinterpret_cast<uint4*>(&vals[0]);
     hi = *reinterpret_cast<uint4*>(&vals[8]);
   }
@@ -199,9 +200,9 @@ __global__ void __launch_bounds__(kConvThreads) conv3d_tc_kernel(const ConvArgs 
           if (a.dst_f32) {
             a.dst_f32[v * a.cout + c] = val;
           } else if (c < a.split) {
-            a.dst0[v * a.split + c] = __float2bfloat16(val);
+            a.dst0[oct_index(v, c, a.split, V)] = __float2bfloat16(val);
           } else {
-            a.dst1[v * (a.cout - a.split) + (c - a.split)] = __float2bfloat16(val);
+            a.dst1[oct_index(v, c - a.split, a.cout - a.split, V)] = __float2bfloat16(val);
           }
         }
       }
@@ -268,6 +269,7 @@ __global__ void __launch_bounds__(kConvThreads) conv3d_tile_kernel(const __grid_
   __shared__ __align__(8) uint64_t bar_tma, bar_mma;
   __shared__ uint32_t s_tmem;
   __shared__ int s_fail;
+  __shared__ int s_start[kTileMaxMB];  // first row of each M-block
   constexpr int kBTap = NOUT * 32;  // bytes of one tap's B operand
   unsigned char* plane0 = dsm;
   unsigned char* plane1 = dsm + a.plane;
@@ -289,6 +291,7 @@ __global__ void __launch_bounds__(kConvThreads) conv3d_tile_kernel(const __grid_
     tc::mbar_fence_init();
     s_fail = 0;
   }
+  if (t < kTileMaxMB) s_start[t] = t < a.mb ? tile_block_start(a, t) : 0;
   if (t < 32) tc::tmem_alloc(&s_tmem, tmem_cols);
   tc::fence_before_sync();
   __syncthreads();
@@ -315,10 +318,10 @@ __global__ void __launch_bounds__(kConvThreads) conv3d_tile_kernel(const __grid_
     if (s_fail) break;
     if (t == 0) {
       const void* map = cb < cb0 ? static_cast<const void*>(&a.map0) : static_cast<const void*>(&a.map1);
-      const int c = 16 * (cb < cb0 ? cb : cb - cb0);
+      const int oct = 2 * (cb < cb0 ? cb : cb - cb0);
       tc::mbar_expect_tx(&bar_tma, 2 * box_bytes);
-      tc::tma_load_4d(plane0, map, c, x0 - 1, y0 - 1, z0 - 1, &bar_tma);
-      tc::tma_load_4d(plane1, map, c + 8, x0 - 1, y0 - 1, z0 - 1, &bar_tma);
+      tc::tma_load_5d(plane0, map, 0, x0 - 1, y0 - 1, z0 - 1, oct, &bar_tma);
+      tc::tma_load_5d(plane1, map, 0, x0 - 1, y0 - 1, z0 - 1, oct + 1, &bar_tma);
     }
     tma_pending = true;
     if (!tc::mbar_wait(&bar_tma, unsigned(cb & 1), kConvWaitNs)) {
@@ -328,14 +331,25 @@ __global__ void __launch_bounds__(kConvThreads) conv3d_tile_kernel(const __grid_
     tma_pending = false;
     tc::fence_after_sync();
     if (t == 0) {
-      const uint32_t pa = tc::smem_addr(plane0), pb = tc::smem_addr(sb);
-      for (int tap = 0; tap < 27; ++tap) {
-        const int off = (tap / 9 - 1) * row_z + ((tap / 3) % 3 - 1) * a.bx + (tap % 3 - 1);
-        const uint64_t bdesc = tc::smem_desc(pb + uint32_t(tap * kBTap), 128, 256);
-        for (int j = 0; j < a.mb; ++j) {
-          const int row = tile_block_start(a, j) + off;
-          tc::mma_bf16(tmem + uint32_t(j * NOUT), tc::smem_desc(pa + uint32_t(row) * 16u, uint32_t(a.plane), 128), bdesc,
-                       idesc, (cb | tap) != 0);
+      // One thread issues 27 x mb MMAs; the descriptors differ only in their
+      // start-address field (address >> 4 in the low bits), so they are
+      // formed by adding row / tap offsets to two base descriptors.
+      const uint64_t adesc0 = tc::smem_desc(tc::smem_addr(plane0), uint32_t(a.plane), 128);
+      const uint64_t bdesc0 = tc::smem_desc(tc::smem_addr(sb), 128, 256);
+      int st[kTileMaxMB];
+#pragma unroll
+      for (int j = 0; j < kTileMaxMB; ++j) st[j] = s_start[j];
+      int tap = 0;
+      for (int dz = -1; dz <= 1; ++dz) {
+        for (int dy = -1; dy <= 1; ++dy) {
+          for (int dx = -1; dx <= 1; ++dx, ++tap) {
+            const int off = dz * row_z + dy * a.bx + dx;
+            const uint64_t bdesc = bdesc0 + uint64_t(tap * (kBTap >> 4));
+            const bool acc = (cb | tap) != 0;
+#pragma unroll
+            for (int j = 0; j < kTileMaxMB; ++j)
+              if (j < a.mb) tc::mma_bf16(tmem + uint32_t(j * NOUT), adesc0 + uint64_t(st[j] + off), bdesc, idesc, acc);
+          }
         }
       }
       tc::mma_commit(&bar_mma);
@@ -354,8 +368,9 @@ __global__ void __launch_bounds__(kConvThreads) conv3d_tile_kernel(const __grid_
   } else {
     const int w = t / 32;
     const int bxby = a.bx * a.by;
+    const size_t Vt = size_t(a.nx) * a.ny * a.nz;
     for (int j = 0; j < a.mb; ++j) {
-      const int row = tile_block_start(a, j) + t;  // this thread's TMEM lane = row t of block j
+      const int row = s_start[j] + t;  // this thread's TMEM lane = row t of block j
       const int zq = row / bxby, rem = row - zq * bxby;
       const int yq = rem / a.bx, xq = rem - yq * a.bx;
       const int gx = x0 + xq - 1, gy = y0 + yq - 1, gz = z0 + zq - 1;
@@ -374,8 +389,8 @@ __global__ void __launch_bounds__(kConvThreads) conv3d_tile_kernel(const __grid_
             __nv_bfloat16 o8[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) o8[k] = __float2bfloat16(acc[8 * half + k] + (a.bias ? a.bias[cbase + k] : 0.f));
-            __nv_bfloat16* dst = cbase < a.split ? a.dst0 + v * a.split + cbase
-                                                 : a.dst1 + v * (a.cout - a.split) + (cbase - a.split);
+            __nv_bfloat16* dst = cbase < a.split ? a.dst0 + oct_index(v, cbase, a.split, Vt)
+                                                 : a.dst1 + oct_index(v, cbase - a.split, a.cout - a.split, Vt);
             *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<uint4*>(o8);
           }
         }
@@ -401,15 +416,18 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return encode;
 }
 
-// channels-last BF16 grid [nz][ny][nx][C] with an {8, bx, by, bz} box
-bool encode_cl_map(CUtensorMap* m, const __nv_bfloat16* base, int C, int nx, int ny, int nz, int bx, int by, int bz) {
+// octet-plane BF16 tensor of C channels: dims {8, nx, ny, nz, C / 8}, box
+// {8, bx, by, bz, 1} (one plane, contiguous x-runs of bx * 16 bytes)
+bool encode_oct_map(CUtensorMap* m, const __nv_bfloat16* base, int C, int nx, int ny, int nz, int bx, int by, int bz) {
   auto encode = tensor_map_encoder();
   if (!encode || C % 8 != 0 || (reinterpret_cast<uintptr_t>(base) & 15) || bx > 256 || by > 256 || bz > 256) return false;
-  cuuint64_t dims[4] = {cuuint64_t(C), cuuint64_t(nx), cuuint64_t(ny), cuuint64_t(nz)};
-  cuuint64_t strides[3] = {cuuint64_t(C) * 2, cuuint64_t(C) * nx * 2, cuuint64_t(C) * nx * ny * 2};
-  cuuint32_t box[4] = {8, cuuint32_t(bx), cuuint32_t(by), cuuint32_t(bz)};
-  cuuint32_t estr[4] = {1, 1, 1, 1};
-  return encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(base), dims, strides, box, estr,
+  cuuint64_t dims[5] = {8, cuuint64_t(nx), cuuint64_t(ny), cuuint64_t(nz), cuuint64_t(C / 8)};
+  const cuuint64_t row = 16;  // bytes per voxel and plane
+  // byte strides of dims 1..4 (x, y, z, plane); dim 0 (8 channels) is dense
+  cuuint64_t strides[4] = {row, row * nx, row * nx * ny, row * nx * ny * nz};
+  cuuint32_t box[5] = {8, cuuint32_t(bx), cuuint32_t(by), cuuint32_t(bz), 1};
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  return encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16*>(base), dims, strides, box, estr,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -471,8 +489,8 @@ cudaError_t launch_tile(const ConvArgs& a, cudaStream_t s, bool& taken) {
   t.nx = a.nx; t.ny = a.ny; t.nz = a.nz;
   t.c0 = a.c0; t.c1 = a.c1;
   if (!pick_tile(t, NOUT)) return cudaSuccess;
-  if (!encode_cl_map(&t.map0, a.src0, a.c0, a.nx, a.ny, a.nz, t.bx, t.by, t.bz)) return cudaSuccess;
-  if (a.c1 > 0 && !encode_cl_map(&t.map1, a.src1, a.c1, a.nx, a.ny, a.nz, t.bx, t.by, t.bz)) return cudaSuccess;
+  if (!encode_oct_map(&t.map0, a.src0, a.c0, a.nx, a.ny, a.nz, t.bx, t.by, t.bz)) return cudaSuccess;
+  if (a.c1 > 0 && !encode_oct_map(&t.map1, a.src1, a.c1, a.nx, a.ny, a.nz, t.bx, t.by, t.bz)) return cudaSuccess;
   t.w = a.w;
   t.cin_pad = (a.c0 + a.c1 + 15) / 16 * 16;
   t.bias = a.bias;

@@ -7,20 +7,31 @@
 
 namespace cfd {
 
-// One stride-1 3D convolution on a channels-last BF16 grid (see unet.cu).
+// Activation layout ("channel-octet planes"): a tensor of C channels on V
+// voxels (x fastest) is stored as ceil(C / W) planes of [V][W] BF16, W =
+// min(C, 8).  Eight channels of a voxel are one 16-byte vector, and within a
+// plane consecutive voxels are consecutive 16-byte vectors, so a box of
+// voxels of one plane is a set of contiguous x-runs (what a TMA copy moves
+// efficiently) and a warp's stores of consecutive voxels coalesce.
+__host__ __device__ inline size_t oct_index(size_t v, int c, int C, size_t V) {
+  const int W = C < 8 ? C : 8;
+  return (size_t(c / W) * V + v) * size_t(W) + size_t(c % W);
+}
+
+// One stride-1 3D convolution on a BF16 grid in octet planes (see unet.cu).
 struct ConvArgs {
   int nx, ny, nz;                // grid of input and output
-  const __nv_bfloat16* src0;     // [V][c0]
+  const __nv_bfloat16* src0;     // c0 channels, octet planes (oct_index)
   int c0;
-  const __nv_bfloat16* src1;     // [V][c1] (channel-concatenated after src0) or null
+  const __nv_bfloat16* src1;     // c1 channels (concatenated after src0) or null
   int c1;
   int ks;                        // 3 or 1
   int packed;                    // 1: c0 == 1, ks == 3: K = 27 taps padded to 32
   const __nv_bfloat16* w;        // [ks^3][nout_pad][cin_pad] or packed [nout_pad][32]
   const float* bias;             // [cout] or null
   int cout;                      // output channels (<= nout_pad)
-  __nv_bfloat16* dst0;           // [V][split]: channels [0, split)
-  __nv_bfloat16* dst1;           // [V][cout - split]: channels [split, cout), or null
+  __nv_bfloat16* dst0;           // channels [0, split), octet planes
+  __nv_bfloat16* dst1;           // channels [split, cout), octet planes, or null
   int split;                     // == cout when dst1 is null
   float* dst_f32;                // if non-null: FP32 [V][cout] output instead of dst0/dst1
   int* err;                      // set to 1 on a device-side wait timeout

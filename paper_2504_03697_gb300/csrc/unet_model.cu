@@ -17,7 +17,7 @@
 // pair (r, e) trains it as (s r, s e)), and the output is projected to zero
 // mean (the Neumann null space).
 //
-// Activations and activation gradients are channels-last BF16; master
+// Activations and activation gradients are BF16 octet planes (unet.h); master
 // weights, gradients and Adam moments are FP32; the convolutions (forward
 // and input gradients) run on the tensor cores (unet.cu); weight gradients
 // are FP32 reductions on the CUDA cores, summed in a fixed order.
@@ -76,6 +76,23 @@ int grid_for(size_t n) {
 
 // ---- elementwise kernels --------------------------------------------------
 
+// fixed-order sum of nb partials by one block of kThreads threads
+__device__ double block_sum(const double* partials, int nb) {
+  __shared__ double sh[kThreads];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += kThreads) s += partials[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if (int(threadIdx.x) < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+
 // partial sums of r^2 per block (for the input scale)
 __global__ void sumsq_kernel(const double* r, size_t n, double* partials) {
   __shared__ double sh[32];
@@ -92,12 +109,16 @@ __global__ void sumsq_kernel(const double* r, size_t n, double* partials) {
 }
 
 // scale[0] = sqrt(V) / ||r|| (0 if r = 0), fixed-order sum of the partials
-__global__ void scale_kernel(const double* partials, int nparts, size_t V, double* scale) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < nparts; ++i) s += partials[i];
-    scale[0] = s > 0.0 ? sqrt(double(V) / s) : 0.0;
-  }
+// (one block of kThreads threads)
+__global__ void __launch_bounds__(kThreads) scale_kernel(const double* partials, int nparts, size_t V, double* scale) {
+  const double s = block_sum(partials, nparts);
+  if (threadIdx.x == 0) scale[0] = s > 0.0 ? sqrt(double(V) / s) : 0.0;
+}
+
+// scale[1] = mean of the head output (one block), for the projection below
+__global__ void __launch_bounds__(kThreads) mean_kernel(const double* partials, int nparts, size_t V, double* scale) {
+  const double s = block_sum(partials, nparts);
+  if (threadIdx.x == 0) scale[1] = s / double(V);
 }
 
 __global__ void normalize_kernel(const double* r, size_t n, const double* scale, __nv_bfloat16* out) {
@@ -125,18 +146,10 @@ __global__ void sum_f32_kernel(const float* z, size_t n, double* partials) {
   }
 }
 
-__global__ void denorm_kernel(const float* z, size_t n, const double* scale, const double* partials, int nparts,
-                              double* out) {
-  __shared__ double s_mean;
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < nparts; ++i) s += partials[i];
-    s_mean = s / double(n);
-  }
-  __syncthreads();
-  const double sc = scale[0];
+__global__ void denorm_kernel(const float* z, size_t n, const double* scale, double* out) {
+  const double sc = scale[0], mean = scale[1];
   const double inv = sc > 0.0 ? 1.0 / sc : 0.0;
-  for (size_t e = gtid(); e < n; e += gstride()) out[e] = (double(z[e]) - s_mean) * inv;
+  for (size_t e = gtid(); e < n; e += gstride()) out[e] = (double(z[e]) - mean) * inv;
 }
 
 // loss = sum (z - t)^2 / V; gz = 2 (z - t) / V (BF16, one channel)
@@ -159,62 +172,203 @@ __global__ void loss_kernel(const float* z, const float* t, size_t n, __nv_bfloa
   }
 }
 
-// 2x average pooling, channels-last; fine grid (fx, fy, fz) all even
+// A-norm loss: d = z - t; loss = d.(A d) / V, gz = 2 A d / V with A the
+// Neumann 7-point pressure operator (n_c on the diagonal, -1 per neighbour;
+// the operator of cfd_apply_poisson), FP32 stencil, FP64 loss partials.
+__global__ void loss_anorm_kernel(const float* z, const float* t, int nx, int ny, int nz, __nv_bfloat16* gz,
+                                  double* partials) {
+  __shared__ double sh[32];
+  const size_t n = size_t(nx) * ny * nz;
+  const float k = 2.0f / float(n);
+  double acc = 0.0;
+  for (size_t e = gtid(); e < n; e += gstride()) {
+    const int x = int(e % nx), y = int((e / nx) % ny), zc = int(e / (size_t(nx) * ny));
+    const float dc = z[e] - t[e];
+    float ad = 0.f;
+    auto nbr = [&](size_t f) { ad += dc - (z[f] - t[f]); };
+    if (x > 0) nbr(e - 1);
+    if (x < nx - 1) nbr(e + 1);
+    if (y > 0) nbr(e - nx);
+    if (y < ny - 1) nbr(e + nx);
+    if (zc > 0) nbr(e - size_t(nx) * ny);
+    if (zc < nz - 1) nbr(e + size_t(nx) * ny);
+    gz[e] = __float2bfloat16(k * ad);
+    acc = fma(double(dc), double(ad), acc);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < int(blockDim.x / 32); ++w) s += sh[w];
+    partials[blockIdx.x] = s / double(n);
+  }
+}
+
+// Resampling kernels on octet planes (C a multiple of 8): one thread per
+// (plane, voxel), 8 channels as one 16-byte vector, FP32 arithmetic.
+__device__ __forceinline__ void ld8(const __nv_bfloat16* p, float (&f)[8]) {
+  const uint4 u = *reinterpret_cast<const uint4*>(p);
+  const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&u);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) f[k] = __bfloat162float(h[k]);
+}
+__device__ __forceinline__ void st8(__nv_bfloat16* p, const float (&f)[8]) {
+  uint4 u;
+  __nv_bfloat16* h = reinterpret_cast<__nv_bfloat16*>(&u);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) h[k] = __float2bfloat16(f[k]);
+  *reinterpret_cast<uint4*>(p) = u;
+}
+
+// 2x average pooling; fine grid (fx, fy, fz) all even
 __global__ void pool2_kernel(const __nv_bfloat16* in, int fx, int fy, int fz, int C, __nv_bfloat16* out) {
   const int cx = fx / 2, cy = fy / 2, cz = fz / 2;
-  const size_t n = size_t(cx) * cy * cz * C;
+  const size_t nc = size_t(cx) * cy * cz, nf = size_t(fx) * fy * fz;
+  const size_t n = nc * size_t(C / 8);
   for (size_t e = gtid(); e < n; e += gstride()) {
-    const int c = int(e % C);
-    const size_t v = e / C;
+    const size_t p = e / nc, v = e % nc;
     const int x = int(v % cx), y = int((v / cx) % cy), z = int(v / (size_t(cx) * cy));
-    float s = 0.f;
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int d = 0; d < 8; ++d) {
       const int xx = 2 * x + (d & 1), yy = 2 * y + ((d >> 1) & 1), zz = 2 * z + (d >> 2);
-      s += __bfloat162float(in[((size_t(zz) * fy + yy) * fx + xx) * C + c]);
+      float f[8];
+      ld8(in + (p * nf + (size_t(zz) * fy + yy) * fx + xx) * 8, f);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) s[k] += f[k];
     }
-    out[e] = __float2bfloat16(0.125f * s);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s[k] *= 0.125f;
+    st8(out + e * 8, s);
   }
 }
 
 // adjoint of pooling: g_in[fine] += g_out[coarse] / 8
 __global__ void pool2_adj_kernel(const __nv_bfloat16* gout, int fx, int fy, int fz, int C, __nv_bfloat16* gin) {
-  const size_t n = size_t(fx) * fy * fz * C;
-  const int cx = fx / 2, cy = fy / 2;
+  const int cx = fx / 2, cy = fy / 2, cz = fz / 2;
+  const size_t nc = size_t(cx) * cy * cz, nf = size_t(fx) * fy * fz;
+  const size_t n = nf * size_t(C / 8);
   for (size_t e = gtid(); e < n; e += gstride()) {
-    const int c = int(e % C);
-    const size_t v = e / C;
+    const size_t p = e / nf, v = e % nf;
     const int x = int(v % fx), y = int((v / fx) % fy), z = int(v / (size_t(fx) * fy));
     const size_t cv = (size_t(z / 2) * cy + y / 2) * cx + x / 2;
-    gin[e] = __float2bfloat16(__bfloat162float(gin[e]) + 0.125f * __bfloat162float(gout[cv * C + c]));
+    float a[8], b[8];
+    ld8(gin + e * 8, a);
+    ld8(gout + (p * nc + cv) * 8, b);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] += 0.125f * b[k];
+    st8(gin + e * 8, a);
   }
 }
 
 // nearest 2x up-sampling to the fine grid
 __global__ void up2_kernel(const __nv_bfloat16* in, int fx, int fy, int fz, int C, __nv_bfloat16* out) {
-  const size_t n = size_t(fx) * fy * fz * C;
-  const int cx = fx / 2, cy = fy / 2;
+  const int cx = fx / 2, cy = fy / 2, cz = fz / 2;
+  const size_t nc = size_t(cx) * cy * cz, nf = size_t(fx) * fy * fz;
+  const size_t n = nf * size_t(C / 8);
   for (size_t e = gtid(); e < n; e += gstride()) {
-    const int c = int(e % C);
-    const size_t v = e / C;
+    const size_t p = e / nf, v = e % nf;
     const int x = int(v % fx), y = int((v / fx) % fy), z = int(v / (size_t(fx) * fy));
-    out[e] = in[((size_t(z / 2) * cy + y / 2) * cx + x / 2) * C + c];
+    const size_t cv = (size_t(z / 2) * cy + y / 2) * cx + x / 2;
+    *reinterpret_cast<uint4*>(out + e * 8) = *reinterpret_cast<const uint4*>(in + (p * nc + cv) * 8);
   }
 }
 
 // adjoint of up-sampling: g_coarse = sum of the 8 fine children
 __global__ void up2_adj_kernel(const __nv_bfloat16* gout, int fx, int fy, int fz, int C, __nv_bfloat16* gin) {
   const int cx = fx / 2, cy = fy / 2, cz = fz / 2;
-  const size_t n = size_t(cx) * cy * cz * C;
+  const size_t nc = size_t(cx) * cy * cz, nf = size_t(fx) * fy * fz;
+  const size_t n = nc * size_t(C / 8);
   for (size_t e = gtid(); e < n; e += gstride()) {
-    const int c = int(e % C);
-    const size_t v = e / C;
+    const size_t p = e / nc, v = e % nc;
     const int x = int(v % cx), y = int((v / cx) % cy), z = int(v / (size_t(cx) * cy));
-    float s = 0.f;
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int d = 0; d < 8; ++d) {
       const int xx = 2 * x + (d & 1), yy = 2 * y + ((d >> 1) & 1), zz = 2 * z + (d >> 2);
-      s += __bfloat162float(gout[((size_t(zz) * fy + yy) * fx + xx) * C + c]);
+      float f[8];
+      ld8(gout + (p * nf + (size_t(zz) * fy + yy) * fx + xx) * 8, f);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) s[k] += f[k];
     }
-    gin[e] = __float2bfloat16(s);
+    st8(gin + e * 8, s);
+  }
+}
+
+// ---- first layer and head on the CUDA cores -------------------------------
+// The first layer (1 -> 16 channels, 27 taps) and the 1x1x1 head (16 -> 1)
+// are too narrow to be tensor-core contractions: FP32 FMAs over the
+// BF16-rounded weights, summed sequentially in tap / channel order.
+
+// a0 = conv3x3x3(xin) + b: xin [V] BF16, w packed [16][32] BF16 (taps 0..26),
+// out 16 channels as 2 octet planes.
+__global__ void first_layer_kernel(const __nv_bfloat16* xin, int nx, int ny, int nz, const __nv_bfloat16* w,
+                                   const float* bias, __nv_bfloat16* out) {
+  __shared__ float ws[27][16];
+  __shared__ float bs[16];
+  for (int i = threadIdx.x; i < 27 * 16; i += blockDim.x) ws[i / 16][i % 16] = __bfloat162float(w[(i % 16) * 32 + i / 16]);
+  if (threadIdx.x < 16) bs[threadIdx.x] = bias[threadIdx.x];
+  __syncthreads();
+  const size_t V = size_t(nx) * ny * nz;
+  for (size_t v = gtid(); v < V; v += gstride()) {
+    const int x = int(v % nx), y = int((v / nx) % ny), z = int(v / (size_t(nx) * ny));
+    float acc[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[c] = 0.f;
+    int tap = 0;
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx, ++tap) {
+          const int xx = x + dx, yy = y + dy, zz = z + dz;
+          if (xx < 0 || xx >= nx || yy < 0 || yy >= ny || zz < 0 || zz >= nz) continue;
+          const float xv = __bfloat162float(xin[(size_t(zz) * ny + yy) * nx + xx]);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) acc[c] = fmaf(ws[tap][c], xv, acc[c]);
+        }
+    float o[8];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) o[k] = acc[8 * h + k] + bs[8 * h + k];
+      st8(out + (size_t(h) * V + v) * 8, o);
+    }
+  }
+}
+
+// z = w . d0 + b (FP32 [V]); d0 16 channels in 2 octet planes, w = row 0 of
+// the head's [1][16][16] BF16 forward weights.
+__global__ void head_kernel(const __nv_bfloat16* d0, size_t V, const __nv_bfloat16* w, const float* bias, float* z) {
+  float wv[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) wv[c] = __bfloat162float(w[c]);
+  const float b = bias[0];
+  for (size_t v = gtid(); v < V; v += gstride()) {
+    float a[8], c8[8];
+    ld8(d0 + v * 8, a);
+    ld8(d0 + (V + v) * 8, c8);
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s = fmaf(wv[k], a[k], s);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s = fmaf(wv[8 + k], c8[k], s);
+    z[v] = s + b;
+  }
+}
+
+// input gradient of the head: g_d0[v][c] = w[c] gz[v] (one exact product,
+// rounded to BF16), w from the forward weights.
+__global__ void head_dgrad_kernel(const __nv_bfloat16* gz, size_t V, const __nv_bfloat16* w, __nv_bfloat16* gd0) {
+  float wv[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) wv[c] = __bfloat162float(w[c]);
+  for (size_t v = gtid(); v < V; v += gstride()) {
+    const float g = __bfloat162float(gz[v]);
+    float o[8];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) o[k] = wv[8 * h + k] * g;
+      st8(gd0 + (size_t(h) * V + v) * 8, o);
+    }
   }
 }
 
@@ -253,24 +407,54 @@ __global__ void __launch_bounds__(kThreads) wgrad_kernel(const WgradArgs a) {
 #pragma unroll
   for (int k = 0; k < 16; ++k) acc[k] = 0.f;
   float bacc = 0.f;
+  __shared__ long long s_nb[32];
   for (size_t vb = v0; vb < v1; vb += 32) {
-    for (int i = threadIdx.x; i < 32 * a.cout; i += kThreads) {
-      const int vv = i / a.cout, co = i % a.cout;
-      const size_t v = vb + vv;
-      gs[vv][co] = v < v1 ? __bfloat162float(a.g[v * a.cout + co]) : 0.f;
-    }
-    for (int i = threadIdx.x; i < 32 * cin; i += kThreads) {
-      const int vv = i / cin, ci = i % cin;
-      const size_t v = vb + vv;
-      float val = 0.f;
+    if (threadIdx.x < 32) {
+      const size_t v = vb + threadIdx.x;
+      long long nb = -1;
       if (v < v1) {
         const int x = int(v % a.nx) + dx, y = int((v / a.nx) % a.ny) + dy, z = int(v / (size_t(a.nx) * a.ny)) + dz;
-        if (x >= 0 && x < a.nx && y >= 0 && y < a.ny && z >= 0 && z < a.nz) {
-          const size_t nb = (size_t(z) * a.ny + y) * a.nx + x;
-          val = ci < a.c0 ? __bfloat162float(a.src0[nb * a.c0 + ci]) : __bfloat162float(a.src1[nb * a.c1 + (ci - a.c0)]);
-        }
+        if (x >= 0 && x < a.nx && y >= 0 && y < a.ny && z >= 0 && z < a.nz) nb = (long long)((size_t(z) * a.ny + y) * a.nx + x);
       }
-      xs[vv][ci] = val;
+      s_nb[threadIdx.x] = nb;
+    }
+    // output gradient rows: one 16-byte octet per work item (C >= 8), else elements
+    if (a.cout >= 8) {
+      for (int i = threadIdx.x; i < 32 * (a.cout / 8); i += kThreads) {
+        const int vv = i % 32, q = i / 32;
+        const size_t v = vb + vv;
+        float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (v < v1) ld8(a.g + (size_t(q) * V + v) * 8, f);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) gs[vv][8 * q + k] = f[k];
+      }
+    } else {
+      for (int i = threadIdx.x; i < 32 * a.cout; i += kThreads) {
+        const int vv = i % 32, co = i / 32;
+        const size_t v = vb + vv;
+        gs[vv][co] = v < v1 ? __bfloat162float(a.g[oct_index(v, co, a.cout, V)]) : 0.f;
+      }
+    }
+    __syncthreads();
+    const int oct0 = a.c0 >= 8 ? a.c0 / 8 : 0;
+    if (a.c0 >= 8) {
+      for (int i = threadIdx.x; i < 32 * (cin / 8); i += kThreads) {
+        const int vv = i % 32, q = i / 32;
+        const long long nb = s_nb[vv];
+        float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (nb >= 0) {
+          if (q < oct0) ld8(a.src0 + (size_t(q) * V + size_t(nb)) * 8, f);
+          else ld8(a.src1 + (size_t(q - oct0) * V + size_t(nb)) * 8, f);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) xs[vv][8 * q + k] = f[k];
+      }
+    } else {
+      for (int i = threadIdx.x; i < 32 * cin; i += kThreads) {
+        const int vv = i % 32, ci = i / 32;
+        const long long nb = s_nb[vv];
+        xs[vv][ci] = nb >= 0 ? __bfloat162float(a.src0[oct_index(size_t(nb), ci, a.c0, V)]) : 0.f;
+      }
     }
     __syncthreads();
 #pragma unroll
@@ -405,22 +589,6 @@ __global__ void __launch_bounds__(kThreads) dot2_kernel(const double* a, const d
   }
 }
 
-// fixed-order sum of nb partials by one block of kThreads threads
-__device__ double block_sum(const double* partials, int nb) {
-  __shared__ double sh[kThreads];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < nb; i += kThreads) s += partials[i];
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = kThreads / 2; o > 0; o >>= 1) {
-    if (int(threadIdx.x) < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
-  }
-  const double r = sh[0];
-  __syncthreads();
-  return r;
-}
-
 enum FpcgOp : int { kOpMean = 0, kOpBB = 1, kOpRZ = 2, kOpAlpha = 3, kOpRR = 4, kOpBeta = 5 };
 
 __global__ void __launch_bounds__(kThreads) fpcg_scalar_kernel(int op, const double* partials, int nb, size_t n,
@@ -533,6 +701,7 @@ struct cfd_unet {
   // tensor table for cfd_unet_read_tensor (activations and their gradients)
   __nv_bfloat16* tens[26];
   size_t tens_count[26];
+  int loss_kind;  // CFD_UNET_LOSS_*
   int adam_t;
   int64_t launches;
 };
@@ -744,9 +913,10 @@ int forward(cfd_unet* u) {
   int fx, fy, fz;
   int rc = CFD_OK;
   auto ok = [&](int r) { if (r && !rc) rc = r; return rc == CFD_OK; };
-  const int C = 0;
-  (void)C;
-  if (!ok(conv(u, 0, u->xin, nullptr, u->a0, nullptr, 16, nullptr))) return rc;
+  level_dims(u, 0, fx, fy, fz);
+  first_layer_kernel<<<grid_for(size_t(fx) * fy * fz), kThreads, 0, u->stream>>>(u->xin, fx, fy, fz, u->wf[0],
+                                                                                  u->w + u->boff[0], u->a0);
+  if (!ok(klaunch(u, "first layer"))) return rc;
   if (!ok(conv(u, 1, u->a0, nullptr, u->s0, nullptr, 16, nullptr))) return rc;
   level_dims(u, 0, fx, fy, fz);
   pool2_kernel<<<grid_for(size_t(fx) * fy * fz * 2), kThreads, 0, u->stream>>>(u->s0, fx, fy, fz, 16, u->p0);
@@ -766,7 +936,9 @@ int forward(cfd_unet* u) {
   up2_kernel<<<grid_for(size_t(fx) * fy * fz * 32), kThreads, 0, u->stream>>>(u->d1, fx, fy, fz, 32, u->u0);
   if (!ok(klaunch(u, "up"))) return rc;
   if (!ok(conv(u, 7, u->s0, u->u0, u->d0, nullptr, 16, nullptr))) return rc;
-  ok(conv(u, 8, u->d0, nullptr, nullptr, nullptr, 1, u->z));
+  const size_t V0 = size_t(u->nx) * u->ny * u->nz;
+  head_kernel<<<grid_for(V0), kThreads, 0, u->stream>>>(u->d0, V0, u->wf[8], u->w + u->boff[8], u->z);
+  ok(klaunch(u, "head"));
   return rc;
 }
 
@@ -777,7 +949,11 @@ int backward(cfd_unet* u) {
   int fx, fy, fz;
   // head
   if (!ok(wgrad(u, 8, u->d0, nullptr, u->gz))) return rc;
-  if (!ok(conv_dgrad(u, 8, 0, u->gz, 16, u->g_d0, nullptr, 16))) return rc;
+  {
+    const size_t V0 = size_t(u->nx) * u->ny * u->nz;
+    head_dgrad_kernel<<<grid_for(V0), kThreads, 0, u->stream>>>(u->gz, V0, u->wf[8], u->g_d0);
+    if (!ok(klaunch(u, "head dgrad"))) return rc;
+  }
   // L0c: input = s0 (16) + u0 (32)
   if (!ok(wgrad(u, 7, u->s0, u->u0, u->g_d0))) return rc;
   if (!ok(conv_dgrad(u, 7, 0, u->g_d0, 48, u->g_s0, u->g_u0, 16))) return rc;
@@ -822,7 +998,7 @@ int input_scale(cfd_unet* u, const double* r) {
   sumsq_kernel<<<nb, kThreads, 0, u->stream>>>(r, V, u->parts);
   int rc = klaunch(u, "sumsq");
   if (rc) return rc;
-  scale_kernel<<<1, 32, 0, u->stream>>>(u->parts, nb, V, u->scale);
+  scale_kernel<<<1, kThreads, 0, u->stream>>>(u->parts, nb, V, u->scale);
   rc = klaunch(u, "scale");
   if (rc) return rc;
   normalize_kernel<<<grid_for(V), kThreads, 0, u->stream>>>(r, V, u->scale, u->xin);
@@ -924,7 +1100,10 @@ int cfd_unet_apply(cfd_unet* u, const double* r_dev, double* z_dev) {
   sum_f32_kernel<<<nb, kThreads, 0, u->stream>>>(u->z, V, u->parts);
   rc = klaunch(u, "sum");
   if (rc) return rc;
-  denorm_kernel<<<grid_for(V), kThreads, 0, u->stream>>>(u->z, V, u->scale, u->parts, nb, z_dev);
+  mean_kernel<<<1, kThreads, 0, u->stream>>>(u->parts, nb, V, u->scale);
+  rc = klaunch(u, "mean");
+  if (rc) return rc;
+  denorm_kernel<<<grid_for(V), kThreads, 0, u->stream>>>(u->z, V, u->scale, z_dev);
   return klaunch(u, "denorm");
 }
 
@@ -944,7 +1123,10 @@ int cfd_unet_train_step(cfd_unet* u, const double* r_dev, const double* e_dev, i
     rc = klaunch(u, "target");
     if (!rc) rc = forward(u);
     if (rc) break;
-    loss_kernel<<<nb, kThreads, 0, u->stream>>>(u->z, u->tgt, V, u->gz, u->lossp);
+    if (u->loss_kind == CFD_UNET_LOSS_ANORM)
+      loss_anorm_kernel<<<nb, kThreads, 0, u->stream>>>(u->z, u->tgt, u->nx, u->ny, u->nz, u->gz, u->lossp);
+    else
+      loss_kernel<<<nb, kThreads, 0, u->stream>>>(u->z, u->tgt, V, u->gz, u->lossp);
     rc = klaunch(u, "loss");
     if (!rc) rc = backward(u);
     if (!rc) rc = uck(u, cudaMemcpyAsync(lp.data(), u->lossp, size_t(nb) * 8, cudaMemcpyDeviceToHost, u->stream), "copy loss");
@@ -965,6 +1147,12 @@ int cfd_unet_train_step(cfd_unet* u, const double* r_dev, const double* e_dev, i
   if (!rc && herr) rc = uerr(CFD_ERR_TIMEOUT, "unet: a tensor-core wait timed out");
   if (loss) *loss = float(total / npairs);
   return rc;
+}
+
+int cfd_unet_set_loss(cfd_unet* u, int kind) {
+  if (!u || (kind != CFD_UNET_LOSS_MSE && kind != CFD_UNET_LOSS_ANORM)) return uerr(CFD_ERR_INVALID_ARG, "unet: bad loss kind");
+  u->loss_kind = kind;
+  return CFD_OK;
 }
 
 int cfd_unet_read_tensor(cfd_unet* u, int which, void* host, int64_t count) {

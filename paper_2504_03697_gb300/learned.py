@@ -197,6 +197,7 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=2000)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--loss", choices=["mse", "anorm"], default="anorm")
     ap.add_argument("--out", default=WEIGHTS)
     ap.add_argument("--weights", default=WEIGHTS)
     ap.add_argument("--eval-n", type=str, default="128")
@@ -211,11 +212,12 @@ def main(argv=None):
         R, E = harvest(a.n, TRAIN_SEEDS[:a.seeds], at, (1, 2, 4, 8, 16, 32, 64, 128))
         print(f"{R.shape[0]} pairs ({R.numel() * 16 / 1e9:.1f} GB resident)")
         net = cfd.UNet(a.n, a.n, a.n, seed=0)
+        net.set_loss(a.loss)
         t0 = time.time()
         losses = train(net, R, E, a.iters, a.batch, a.lr)
         params = net.get_params()
         meta = {"n": a.n, "train_seeds": list(TRAIN_SEEDS[:a.seeds]), "steps": at, "iters": a.iters,
-                "batch": a.batch, "lr": a.lr, "pairs": int(R.shape[0]), "first_loss": losses[0],
+                "batch": a.batch, "lr": a.lr, "loss": a.loss, "pairs": int(R.shape[0]), "first_loss": losses[0],
                 "final_loss": float(np.mean(losses[-50:])), "train_seconds": time.time() - t0}
         save_params(params, a.out, meta)
         print(json.dumps(meta))

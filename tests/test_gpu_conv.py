@@ -49,7 +49,7 @@ def run_conv(lib, shape, c0, c1, cout, ks, nout, f32=True, seed=0):
     ref = ref.permute(1, 2, 3, 0).reshape(V, cout)
     ref_abs = torch.nn.functional.conv3d(xin.abs().permute(3, 0, 1, 2)[None], w.double().abs(), bias.double().abs(),
                                          padding=ks // 2)[0].permute(1, 2, 3, 0).reshape(V, cout)
-    # device operands: channels-last activations, weights [tap][nout][cin_pad] (or packed [nout][32])
+    # device operands: activations as octet planes, weights [tap][nout][cin_pad] (or packed [nout][32])
     packed = c0 == 1 and c1 == 0 and ks == 3
     if packed:
         wk = torch.zeros(nout, 32, dtype=torch.bfloat16)
@@ -58,13 +58,14 @@ def run_conv(lib, shape, c0, c1, cout, ks, nout, f32=True, seed=0):
         cin_pad = (cin + 15) // 16 * 16
         wk = torch.zeros(ks ** 3, nout, cin_pad, dtype=torch.bfloat16)
         wk[:, :cout, :cin] = w.permute(2, 3, 4, 0, 1).reshape(ks ** 3, cout, cin)
-    dx0 = x0.reshape(V, c0).contiguous().cuda()
-    dx1 = x1.reshape(V, c1).contiguous().cuda() if c1 else None
+    from paper_2504_03697_gb300.cfd import from_octets, to_octets
+    dx0 = to_octets(x0.reshape(V, c0)).cuda()
+    dx1 = to_octets(x1.reshape(V, c1)).cuda() if c1 else None
     dw = wk.contiguous().cuda()
     db = bias.cuda()
     err = torch.zeros(1, dtype=torch.int32, device="cuda")
     out32 = torch.full((V, cout), float("nan"), device="cuda") if f32 else None
-    out16 = torch.zeros((V, cout), dtype=torch.bfloat16, device="cuda") if not f32 else None
+    out16 = torch.zeros(V * cout, dtype=torch.bfloat16, device="cuda") if not f32 else None
     rc = lib.cfd_conv3d_bf16(nx, ny, nz, dx0.data_ptr(), c0, dx1.data_ptr() if c1 else None, c1, ks, dw.data_ptr(),
                              db.data_ptr(), cout, nout, out16.data_ptr() if out16 is not None else None,
                              out32.data_ptr() if out32 is not None else None, err.data_ptr(),
@@ -72,7 +73,7 @@ def run_conv(lib, shape, c0, c1, cout, ks, nout, f32=True, seed=0):
     assert rc == 0
     torch.cuda.synchronize()
     assert int(err.item()) == 0
-    got = (out32 if f32 else out16.float()).double().cpu()
+    got = (out32 if f32 else from_octets(out16.reshape(-1).cpu(), cout).float()).double().cpu()
     chunks = 2 if packed else ks ** 3 * ((cin + 15) // 16)
     return got, ref, ref_abs, chunks
 

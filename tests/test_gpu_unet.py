@@ -68,10 +68,13 @@ def check(got, ref, bound, what):
                                 f"{float(((got - ref).abs() / bound.clamp_min(1e-300)).max()):.3g}"
 
 
-def conv_check(got, x, w, b, what, bf16_out=True):
+def conv_check(got, x, w, b, what, bf16_out=True, ch=None):
+    """ch: number of FP32 roundings of the accumulation (default: the tensor
+    core's 16-deep K chunks; the CUDA-core first layer and head sum their 27
+    taps / 16 channels one term at a time)."""
     ref = ou.conv(x, w, b)
     terms = ou.conv(x.abs(), w.abs(), b.abs() if b is not None else None)
-    ch = chunks_of(x.shape[0], w.shape[-1])
+    ch = chunks_of(x.shape[0], w.shape[-1]) if ch is None else ch
     bound = 4 * (ch + 1) * E * terms + (U * ref.abs() if bf16_out else 0)
     check(got, ref, bound, what)
 
@@ -103,7 +106,7 @@ def test_forward_layerwise(cfd):
     s = np.sqrt(r.size) / np.linalg.norm(r)
     xin_ref = torch.from_numpy(r * s)[None]
     check(T["xin"], xin_ref, U * xin_ref.abs() + 1e-12, "xin")
-    conv_check(T["a0"], T["xin"], *L[0], "L0a")
+    conv_check(T["a0"], T["xin"], *L[0], "L0a", ch=27)
     conv_check(T["s0"], T["a0"], *L[1], "L0b")
     p0 = ou.pool2(T["s0"])
     check(T["p0"], p0, U * p0.abs() + 8 * E * ou.pool2(T["s0"].abs()), "pool0")
@@ -118,7 +121,7 @@ def test_forward_layerwise(cfd):
     assert torch.equal(T["u0"], ou.up2(T["d1"]))
     conv_check(T["d0"], torch.cat([T["s0"], T["u0"]]), *L[7], "L0c")
     z = grid(net.read_tensor(cfd.UNET_T_OUT), SHAPE, 0)
-    conv_check(z, T["d0"], *L[8], "head", bf16_out=False)
+    conv_check(z, T["d0"], *L[8], "head", bf16_out=False, ch=16)
 
 
 def test_apply_output_is_scaled_zero_mean(cfd):
@@ -192,6 +195,30 @@ def test_backward_layerwise(cfd):
         gb = outs[li].sum(dim=(1, 2, 3))
         tb = outs[li].abs().sum(dim=(1, 2, 3))
         check(grads[li][1], gb, 2 * (Vl / 32 + 34) * E * tb + 1e-30, f"{name} bias gradient")
+
+
+def test_anorm_loss_gradient(cfd):
+    nx, ny, nz = SHAPE
+    net = cfd.UNet(nx, ny, nz, seed=19)
+    net.set_loss("anorm")
+    r = torch.from_numpy(uniform_field((nz, ny, nx), 51)).cuda()
+    e = torch.from_numpy(uniform_field((nz, ny, nx), 52)).cuda()
+    loss = net.train_step(r, e, lr=0.0)
+    z = net.read_tensor(cfd.UNET_T_OUT).double().reshape(nz, ny, nx)
+    t = net.read_tensor(cfd.UNET_T_TARGET).double().reshape(nz, ny, nx)
+    d = z - t
+    ad = ou.neumann_apply(d)
+    V = d.numel()
+    assert abs(loss - float((d * ad).sum()) / V) <= 1e-4 * abs(loss)
+    ref = 2.0 / V * ad
+    # sum of |terms| of a stencil row: n_c |d_c| + sum_n |d_n| = 2 n_c |d_c| - (A |d|)_c,
+    # n_c the number of in-grid neighbours
+    zz, yy, xx = (torch.arange(k) for k in d.shape)
+    deg = sum(((c > 0).double() + (c < c.numel() - 1).double()).reshape(shape)
+              for c, shape in ((zz, (-1, 1, 1)), (yy, (1, -1, 1)), (xx, (1, 1, -1))))
+    terms = 2.0 / V * (2 * deg * d.abs() - ou.neumann_apply(d.abs()))
+    gz = net.read_tensor("gz").double().reshape(nz, ny, nx)
+    check(gz, ref, U * ref.abs() + 8 * E * terms + 1e-300, "A-norm gz")
 
 
 def test_gradient_sums_over_pairs(cfd):

@@ -94,6 +94,31 @@ def test_gradient_matches_finite_differences():
         assert abs(fd - float(grad[idx])) <= 1e-6 * max(1.0, abs(fd)), (idx, fd, float(grad[idx]))
 
 
+def test_neumann_apply_matches_csr_and_null_space():
+    rng = np.random.default_rng(12)
+    d = rng.standard_normal((3, 4, 5))
+    got = unet.neumann_apply(torch.from_numpy(d)).numpy().reshape(-1)
+    ref = operators.poisson_csr(5, 4, 3) @ d.reshape(-1)
+    assert np.allclose(got, ref, atol=1e-13)
+    assert np.allclose(unet.neumann_apply(torch.full((3, 4, 5), 2.5, dtype=torch.float64)).numpy(), 0.0)
+
+
+def test_anorm_gradient_matches_finite_differences():
+    rng = np.random.default_rng(13)
+    flat = torch.from_numpy(rng.standard_normal(unet.param_count()) * 0.1)
+    r = rng.standard_normal((4, 4, 8))
+    e = rng.standard_normal((4, 4, 8))
+    loss, grad = unet.loss_and_grad(flat, [(r, e)], loss="anorm")
+    assert loss > 0
+    for idx in [3, 9000, unet.param_count() - 2]:
+        dlt = torch.zeros_like(flat)
+        dlt[idx] = 1e-6
+        fp, _ = unet.loss_and_grad(flat + dlt, [(r, e)], loss="anorm")
+        fm, _ = unet.loss_and_grad(flat - dlt, [(r, e)], loss="anorm")
+        fd = (fp - fm) / 2e-6
+        assert abs(fd - float(grad[idx])) <= 1e-6 * max(1.0, abs(fd))
+
+
 def test_adam_first_step_is_sign():
     g = torch.tensor([3.0, -0.5, 1e-2, -7.0], dtype=torch.float64)
     w = torch.tensor([1.0, 2.0, 3.0, 4.0], dtype=torch.float64)
