@@ -349,8 +349,11 @@ int cfd_unet_train_step(cfd_unet *u, const double *r_dev, const double *e_dev, i
 /* Training loss of cfd_unet_train_step (per pair, with d = U(s r) - s e):
  *   MSE    |d|^2 / V                 (the default)
  *   ANORM  d.(A d) / V, A the operator of cfd_apply_poisson (the error
- *          measured in the energy norm CG minimises)                    */
-enum { CFD_UNET_LOSS_MSE = 0, CFD_UNET_LOSS_ANORM = 1 };
+ *          measured in the energy norm CG minimises)
+ *   COS    1 - (z.A t) / sqrt((z.A z)(t.A t)), z = U(s r), t = s e: one
+ *          minus the energy-norm cosine, invariant to a positive scale of
+ *          z (as flexible CG is)                                         */
+enum { CFD_UNET_LOSS_MSE = 0, CFD_UNET_LOSS_ANORM = 1, CFD_UNET_LOSS_COS = 2 };
 int cfd_unet_set_loss(cfd_unet *u, int kind);
 
 /* Tensor read-back for checks (synchronous).  which in 0..25: the BF16
@@ -372,9 +375,11 @@ int cfd_unet_read_tensor(cfd_unet *u, int which, void *host, int64_t count);
  * operator of cfd_apply_poisson) with z = M(r) and the Polak-Ribiere beta
  * z_{k+1}.(r_{k+1} - r_k) / (z_k.r_k).  Cold start x = 0; the mean of b is
  * removed; no gauge shift.  Converged when the FP64 TRUE residual satisfies
- * ||b - A x|| <= rtol ||b||.  On breakdown (p.q <= 0, z.r <= 0, non-finite)
- * or stagnation (50 iterations without the residual norm halving) it
- * continues as plain CG from the current iterate.  max_iters = 0 means
+ * ||b - A x|| <= rtol ||b||.  z.r < 0 is allowed (alpha = z.r / p.q is
+ * then negative, still the exact line search along p).  On breakdown (p.q
+ * <= 0, z.r = 0, a non-finite value) or stagnation (50 iterations without
+ * the residual norm halving) it continues as plain CG from the current
+ * iterate.  max_iters = 0 means
  * 20 * max(n).  stats (nullable): iters (all iterations), outer_iters (the
  * plain-CG ones), restarts, status, rel_resid, b_norm.  Synchronises the
  * stream; returns the status (CFD_OK, CFD_ERR_NOT_CONVERGED, ...). */

@@ -33,9 +33,11 @@ polynomial solution, and DIC = exact factorisation on tridiagonal matrices
 ``fpcg`` (flexible PCG for a preconditioner that may vary between
 iterations) is pinned by tests/test_oracle_unet.py: with M = identity or a
 fixed SPD M it takes the iterates of ``pcg`` (the Polak-Ribiere beta equals
-the Fletcher-Reeves one when z_{k+1}.r_k = 0), with M = the exact inverse on
-the zero-mean subspace it converges in one iteration, and with an
-indefinite M (z = -r) it falls back to plain CG and still converges.
+the Fletcher-Reeves one when z_{k+1}.r_k = 0), M = -I gives the same iterates
+as M = I (flexible CG is invariant to the preconditioner's scale), with M =
+the exact inverse on the zero-mean subspace it converges in one iteration,
+and a preconditioner returning zero (breakdown) or a fixed vector
+(stagnation) makes it fall back to plain CG and still converge.
 """
 from __future__ import annotations
 
@@ -163,10 +165,13 @@ def fpcg(A, b, precond, rtol=1e-8, max_iters=1000, stagnation=50, max_restarts=8
 
     b has its mean removed first (Neumann system, consistent right-hand side).
     One iteration: q = A p, alpha = (r.z)/(p.q), x += alpha p, r -= alpha q,
-    z' = M(r), beta = z'.(r_new - r_old)/(r_old.z_old), p = z' + beta p.  A
-    non-positive or non-finite p.q or z.r, or `stagnation` iterations without
-    the residual norm halving, switches to plain CG (M = identity) restarted
-    from the true residual of the current x.  Convergence is judged by the
+    z' = M(r), beta = z'.(r_new - r_old)/(r_old.z_old), p = z' + beta p.
+    A preconditioner that is not positive definite may give z.r < 0; alpha
+    then is negative and still the exact line search along p (r.p = r.z), so
+    only z.r = 0, a non-positive p.q or a non-finite value is a breakdown.
+    A breakdown, or `stagnation` iterations without the residual norm
+    halving, switches to plain CG (M = identity) restarted from the true
+    residual of the current x.  Convergence is judged by the
     true residual ||b - A x|| <= rtol ||b||; when the recurrence passes but
     the true residual does not, the iteration restarts from it.
     Returns (x, FlexStats)."""
@@ -191,7 +196,7 @@ def fpcg(A, b, precond, rtol=1e-8, max_iters=1000, stagnation=50, max_restarts=8
     best = bb
     since = 0
     while True:
-        bad = not (rz > 0.0 and np.isfinite(rz))
+        bad = not (rz != 0.0 and np.isfinite(rz))
         if not bad:
             if st.iters >= max_iters:
                 break

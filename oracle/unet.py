@@ -16,7 +16,9 @@ reading of that item (architecture, scaling and loss are not in the paper):
   every convolution stride 1, zero padding ("same"), with bias;
 * preconditioner M(r) = U(s r) / s minus its mean, s = sqrt(V) / ||r||;
 * training loss on one pair (r, e), d = U(s r) - s e: mean over cells of
-  d^2, or the energy norm d.(A d) / V (A the Neumann pressure operator);
+  d^2, the energy norm d.(A d) / V (A the Neumann pressure operator), or one
+  minus the energy-norm cosine of U(s r) and s e (invariant to a positive
+  scale of the output);
   Adam (beta 0.9 / 0.999, eps 1e-8) on the mean loss over a batch of pairs.
 
 Parameters travel as one flat float vector: per layer in the order above,
@@ -144,8 +146,8 @@ def _pad_spec(ax, before, after):
 
 def loss_and_grad(flat, pairs, loss="mse"):
     """Mean over pairs of the training loss and its gradient w.r.t. the flat
-    parameters (autograd).  With d = U(s r) - s e: "mse" = mean(d^2),
-    "anorm" = d.(A d) / V."""
+    parameters (autograd).  With z = U(s r), t = s e, d = z - t: "mse" =
+    mean(d^2), "anorm" = d.(A d) / V, "cos" = 1 - (z.A t) / sqrt((z.A z)(t.A t))."""
     p = torch.as_tensor(flat, dtype=torch.float64).clone().requires_grad_(True)
     layers = unflatten(p)
     total = 0.0
@@ -156,6 +158,10 @@ def loss_and_grad(flat, pairs, loss="mse"):
         d = (z - t)[0]
         if loss == "anorm":
             total = total + (d * neumann_apply(d)).sum() / d.numel()
+        elif loss == "cos":
+            zz, tt = z[0], t[0]
+            at = neumann_apply(tt)
+            total = total + 1.0 - (zz * at).sum() / torch.sqrt((zz * neumann_apply(zz)).sum() * (tt * at).sum())
         else:
             total = total + (d ** 2).mean()
     total = total / len(pairs)

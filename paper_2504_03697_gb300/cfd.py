@@ -467,8 +467,9 @@ class UNet:
         return float(loss.value)
 
     def set_loss(self, kind: str):
-        """'mse' (|d|^2 / V) or 'anorm' (d.(A d) / V), d = U(s r) - s e."""
-        self._check(self.lib.cfd_unet_set_loss(self.u, {"mse": 0, "anorm": 1}[kind]))
+        """'mse' (|d|^2 / V), 'anorm' (d.(A d) / V), d = U(s r) - s e, or 'cos'
+        (one minus the energy-norm cosine of U(s r) and s e)."""
+        self._check(self.lib.cfd_unet_set_loss(self.u, {"mse": 0, "anorm": 1, "cos": 2}[kind]))
 
     def read_tensor(self, which) -> torch.Tensor:
         """Host copy of a model tensor: a name from UNET_TENSORS (BF16,

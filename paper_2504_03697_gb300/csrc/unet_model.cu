@@ -205,6 +205,79 @@ __global__ void loss_anorm_kernel(const float* z, const float* t, int nx, int ny
   }
 }
 
+// Scale-invariant energy-norm loss ("cos"): with a = z.Az, b = z.At, T =
+// t.At (FP32 stencils, FP64 sums), L = 1 - b / sqrt(a T), one minus the
+// energy-norm cosine of z and t.  Flexible CG is invariant to a positive
+// scale of the preconditioner, so only the direction of z is trained; the
+// sign is kept (a negative multiple of t would make z.r < 0).  dL/dz =
+// (c Az - At) / sqrt(a T) with c = b / a.
+__device__ __forceinline__ float neumann_at(const float* f, size_t e, int x, int y, int zc, int nx, int ny, int nz) {
+  const float c = f[e];
+  float s = 0.f;
+  if (x > 0) s += c - f[e - 1];
+  if (x < nx - 1) s += c - f[e + 1];
+  if (y > 0) s += c - f[e - nx];
+  if (y < ny - 1) s += c - f[e + nx];
+  if (zc > 0) s += c - f[e - size_t(nx) * ny];
+  if (zc < nz - 1) s += c - f[e + size_t(nx) * ny];
+  return s;
+}
+
+__global__ void cos_dots_kernel(const float* z, const float* t, int nx, int ny, int nz, double* partials) {
+  __shared__ double sh[3][32];
+  const size_t n = size_t(nx) * ny * nz;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (size_t e = gtid(); e < n; e += gstride()) {
+    const int x = int(e % nx), y = int((e / nx) % ny), zc = int(e / (size_t(nx) * ny));
+    const float az = neumann_at(z, e, x, y, zc, nx, ny, nz), at = neumann_at(t, e, x, y, zc, nx, ny, nz);
+    s0 = fma(double(z[e]), double(az), s0);
+    s1 = fma(double(z[e]), double(at), s1);
+    s2 = fma(double(t[e]), double(at), s2);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_down_sync(0xffffffffu, s0, o);
+    s1 += __shfl_down_sync(0xffffffffu, s1, o);
+    s2 += __shfl_down_sync(0xffffffffu, s2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][threadIdx.x >> 5] = s0;
+    sh[1][threadIdx.x >> 5] = s1;
+    sh[2][threadIdx.x >> 5] = s2;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double v = 0.0;
+    for (int w = 0; w < int(blockDim.x / 32); ++w) v += sh[threadIdx.x][w];
+    partials[size_t(threadIdx.x) * gridDim.x + blockIdx.x] = v;
+  }
+}
+
+// one block: sc[2] = c, sc[3] = 1 / sqrt(a T); partials[0] = L, partials[1 .. nb) = 0
+__global__ void __launch_bounds__(kThreads) cos_finalize_kernel(double* partials, int nb, double* sc) {
+  const double a = block_sum(partials, nb), b = block_sum(partials + nb, nb), T = block_sum(partials + 2 * nb, nb);
+  __syncthreads();
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) partials[i] = 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const bool ok = a > 0.0 && T > 0.0;
+    const double c = ok ? b / a : 0.0;
+    sc[2] = c;
+    sc[3] = ok ? 1.0 / sqrt(a * T) : 0.0;
+    partials[0] = ok ? 1.0 - b / sqrt(a * T) : 1.0;
+  }
+}
+
+__global__ void cos_grad_kernel(const float* z, const float* t, int nx, int ny, int nz, const double* sc,
+                                __nv_bfloat16* gz) {
+  const size_t n = size_t(nx) * ny * nz;
+  const float c = float(sc[2]), k = float(sc[3]);
+  for (size_t e = gtid(); e < n; e += gstride()) {
+    const int x = int(e % nx), y = int((e / nx) % ny), zc = int(e / (size_t(nx) * ny));
+    const float az = neumann_at(z, e, x, y, zc, nx, ny, nz), at = neumann_at(t, e, x, y, zc, nx, ny, nz);
+    gz[e] = __float2bfloat16(k * (c * az - at));
+  }
+}
+
 // Resampling kernels on octet planes (C a multiple of 8): one thread per
 // (plane, voxel), 8 channels as one 16-byte vector, FP32 arithmetic.
 __device__ __forceinline__ void ld8(const __nv_bfloat16* p, float (&f)[8]) {
@@ -552,7 +625,7 @@ struct FpcgScalars {
   double pq;
   double bb;     // ||b||^2 after mean removal
   double mean;   // mean of b (removed)
-  int flag;      // 1: p.q <= 0 or non-finite; 2: z.r <= 0 or non-finite
+  int flag;      // 1: p.q <= 0 or non-finite; 2: z.r = 0 or non-finite
   int pad;
 };
 
@@ -601,7 +674,7 @@ __global__ void __launch_bounds__(kThreads) fpcg_scalar_kernel(int op, const dou
     case kOpBB: sc->bb = s0; sc->rr = s0; break;
     case kOpRZ:
       sc->rz = s0;
-      if (!(s0 > 0.0) || !isfinite(s0)) sc->flag = 2;
+      if (s0 == 0.0 || !isfinite(s0)) sc->flag = 2;
       break;
     case kOpAlpha:
       sc->pq = s0;
@@ -615,8 +688,10 @@ __global__ void __launch_bounds__(kThreads) fpcg_scalar_kernel(int op, const dou
     case kOpRR: sc->rr = s0; break;
     case kOpBeta: {
       // Polak-Ribiere: beta = z_{k+1} . (r_{k+1} - r_k) / (z_k . r_k), with
-      // r_{k+1} - r_k = -alpha q_k
-      if (!(s0 > 0.0) || !isfinite(s0) || !isfinite(s1)) {
+      // r_{k+1} - r_k = -alpha q_k.  z.r < 0 (a preconditioner that is not
+      // positive definite) is allowed: alpha = z.r / p.q is then negative and
+      // still the exact line search along p, since r.p = r.z.
+      if (s0 == 0.0 || !isfinite(s0) || !isfinite(s1)) {
         sc->flag = 2;
         sc->beta = 0.0;
       } else {
@@ -769,7 +844,7 @@ size_t carve(cfd_unet* u, int nx, int ny, int nz, char* base) {
   float* bpart = reinterpret_cast<float*>(take(size_t(kWgradChunks) * 64 * 4));
   double* parts = reinterpret_cast<double*>(take(size_t(152 * 8) * 8));
   double* scale = reinterpret_cast<double*>(take(64));
-  double* lossp = reinterpret_cast<double*>(take(size_t(152 * 8) * 8));
+  double* lossp = reinterpret_cast<double*>(take(size_t(3 * 152 * 8) * 8));
   int* err = reinterpret_cast<int*>(take(64));
   double* cgv[5];
   for (int i = 0; i < 5; ++i) cgv[i] = reinterpret_cast<double*>(take(V0 * 8));
@@ -1123,11 +1198,20 @@ int cfd_unet_train_step(cfd_unet* u, const double* r_dev, const double* e_dev, i
     rc = klaunch(u, "target");
     if (!rc) rc = forward(u);
     if (rc) break;
-    if (u->loss_kind == CFD_UNET_LOSS_ANORM)
+    if (u->loss_kind == CFD_UNET_LOSS_COS) {
+      cos_dots_kernel<<<nb, kThreads, 0, u->stream>>>(u->z, u->tgt, u->nx, u->ny, u->nz, u->lossp);
+      rc = klaunch(u, "loss dots");
+      if (!rc) {
+        cos_finalize_kernel<<<1, kThreads, 0, u->stream>>>(u->lossp, nb, u->scale);
+        rc = klaunch(u, "loss finalize");
+      }
+      if (!rc) cos_grad_kernel<<<nb, kThreads, 0, u->stream>>>(u->z, u->tgt, u->nx, u->ny, u->nz, u->scale, u->gz);
+    } else if (u->loss_kind == CFD_UNET_LOSS_ANORM) {
       loss_anorm_kernel<<<nb, kThreads, 0, u->stream>>>(u->z, u->tgt, u->nx, u->ny, u->nz, u->gz, u->lossp);
-    else
+    } else {
       loss_kernel<<<nb, kThreads, 0, u->stream>>>(u->z, u->tgt, V, u->gz, u->lossp);
-    rc = klaunch(u, "loss");
+    }
+    if (!rc) rc = klaunch(u, "loss");
     if (!rc) rc = backward(u);
     if (!rc) rc = uck(u, cudaMemcpyAsync(lp.data(), u->lossp, size_t(nb) * 8, cudaMemcpyDeviceToHost, u->stream), "copy loss");
     if (!rc) rc = uck(u, cudaStreamSynchronize(u->stream), "synchronize");
@@ -1150,7 +1234,7 @@ int cfd_unet_train_step(cfd_unet* u, const double* r_dev, const double* e_dev, i
 }
 
 int cfd_unet_set_loss(cfd_unet* u, int kind) {
-  if (!u || (kind != CFD_UNET_LOSS_MSE && kind != CFD_UNET_LOSS_ANORM)) return uerr(CFD_ERR_INVALID_ARG, "unet: bad loss kind");
+  if (!u || kind < CFD_UNET_LOSS_MSE || kind > CFD_UNET_LOSS_COS) return uerr(CFD_ERR_INVALID_ARG, "unet: bad loss kind");
   u->loss_kind = kind;
   return CFD_OK;
 }
@@ -1261,7 +1345,7 @@ int cfd_unet_fpcg_solve(cfd_unet* u, const double* b_dev, double* x_dev, double 
     while (!rc) {
       if (!read_scalars()) break;
       if (h.flag) {
-        // breakdown of the preconditioned recurrence (p.q <= 0, z.r <= 0 or
+        // breakdown of the preconditioned recurrence (p.q <= 0, z.r = 0 or
         // non-finite): continue as plain CG from the current iterate
         if (plain) { status = CFD_ERR_BREAKDOWN; break; }
         plain = true;

@@ -197,7 +197,7 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=2000)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=1e-3)
-    ap.add_argument("--loss", choices=["mse", "anorm"], default="anorm")
+    ap.add_argument("--loss", choices=["mse", "anorm", "cos"], default="cos")
     ap.add_argument("--out", default=WEIGHTS)
     ap.add_argument("--weights", default=WEIGHTS)
     ap.add_argument("--eval-n", type=str, default="128")

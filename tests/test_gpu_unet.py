@@ -221,6 +221,32 @@ def test_anorm_loss_gradient(cfd):
     check(gz, ref, U * ref.abs() + 8 * E * terms + 1e-300, "A-norm gz")
 
 
+def test_cos_loss_gradient(cfd):
+    nx, ny, nz = SHAPE
+    net = cfd.UNet(nx, ny, nz, seed=23)
+    net.set_loss("cos")
+    r = torch.from_numpy(uniform_field((nz, ny, nx), 61)).cuda()
+    e = torch.from_numpy(uniform_field((nz, ny, nx), 62)).cuda()
+    loss = net.train_step(r, e, lr=0.0)
+    z = net.read_tensor(cfd.UNET_T_OUT).double().reshape(nz, ny, nx)
+    t = net.read_tensor(cfd.UNET_T_TARGET).double().reshape(nz, ny, nx)
+    az, at = ou.neumann_apply(z), ou.neumann_apply(t)
+    a, b, T = float((z * az).sum()), float((z * at).sum()), float((t * at).sum())
+    assert abs(loss - (1 - b / np.sqrt(a * T))) <= 1e-5
+    c = b / a
+    k = 1 / np.sqrt(a * T)
+    ref = k * (c * az - at)
+    zz, yy, xx = (torch.arange(m) for m in z.shape)
+    deg = sum(((q > 0).double() + (q < q.numel() - 1).double()).reshape(shape)
+              for q, shape in ((zz, (-1, 1, 1)), (yy, (1, -1, 1)), (xx, (1, 1, -1))))
+    terms_z = 2 * deg * z.abs() - ou.neumann_apply(z.abs())
+    terms_t = 2 * deg * t.abs() - ou.neumann_apply(t.abs())
+    # FP32 stencils (8 roundings), c and k from FP32-based FP64 sums (1e-5 relative), BF16 output
+    bound = U * ref.abs() + abs(k) * (abs(c) * terms_z + terms_t) * 8 * E + 1e-5 * abs(k) * ((c * az).abs() + at.abs())
+    gz = net.read_tensor("gz").double().reshape(nz, ny, nx)
+    check(gz, ref, bound, "cos-loss gz")
+
+
 def test_gradient_sums_over_pairs(cfd):
     nx, ny, nz = SHAPE
     r = torch.from_numpy(np.stack([uniform_field((nz, ny, nx), 20 + k) for k in range(2)])).cuda()
@@ -291,22 +317,42 @@ def test_fpcg_solves_to_true_residual(cfd, shape):
           f"oracle CG {so.iters}")
 
 
-def test_fpcg_falls_back_on_indefinite_preconditioner(cfd):
-    nx, ny, nz = 16, 16, 16
-    net = cfd.UNet(nx, ny, nz, seed=2)
-    # every layer passes channel 0 and the head negates it: M(r) = -(r + B2 r + B4 r),
-    # negative definite, so z.r < 0 at the first iteration
-    p = torch.zeros(net.nparams, dtype=torch.float32)
+def passthrough_params(head_sign=1.0):
+    """Every layer passes channel 0 (centre tap); the head multiplies by
+    head_sign: M(r) = head_sign (r + B2 r + B4 r) up to the mean."""
     layers = []
     for name, _, c0, c1, cout, ks in ou.LAYERS:
         w = torch.zeros(cout, c0 + c1, ks, ks, ks, dtype=torch.float64)
         m = ks // 2
-        w[0, 0, m, m, m] = -1.0 if name == "head" else 1.0
+        w[0, 0, m, m, m] = head_sign if name == "head" else 1.0
         if c1:
             w[0, c0, m, m, m] = 1.0
         layers.append((w, torch.zeros(cout, dtype=torch.float64)))
-    p[:] = ou.flatten(layers).float()
-    net.set_params(p)
+    return ou.flatten(layers).float()
+
+
+def test_fpcg_negative_preconditioner_scale_is_harmless(cfd):
+    # M and -M give the same flexible-CG iterates (exactly: BF16 negation is
+    # exact and every step is sign-symmetric), with no fallback
+    nx, ny, nz = 16, 16, 16
+    b = torch.from_numpy(gaussian_rhs(nx, ny, nz, 22)).cuda()
+    out = []
+    for sign in (1.0, -1.0):
+        net = cfd.UNet(nx, ny, nz, seed=2)
+        net.set_params(passthrough_params(sign))
+        x = torch.zeros_like(b)
+        rc, st = net.fpcg_solve(b, x, rtol=1e-8)
+        assert rc == 0 and st["outer_iters"] == 0 and st["rel_resid"] <= 1e-8, st
+        out.append((st["iters"], x.cpu()))
+    assert out[0][0] == out[1][0]
+    assert torch.allclose(out[0][1], out[1][1], rtol=0, atol=1e-12 * float(out[0][1].abs().max()))
+
+
+def test_fpcg_falls_back_on_breakdown(cfd):
+    # an all-zero network gives z = 0, so z.r = 0 at once: plain CG from there
+    nx, ny, nz = 16, 16, 16
+    net = cfd.UNet(nx, ny, nz, seed=2)
+    net.set_params(torch.zeros(net.nparams))
     b = torch.from_numpy(gaussian_rhs(nx, ny, nz, 22)).cuda()
     x = torch.zeros_like(b)
     rc, st = net.fpcg_solve(b, x, rtol=1e-8)

@@ -119,6 +119,34 @@ def test_anorm_gradient_matches_finite_differences():
         assert abs(fd - float(grad[idx])) <= 1e-6 * max(1.0, abs(fd))
 
 
+def test_cos_loss_gradient_and_invariance():
+    rng = np.random.default_rng(14)
+    flat = torch.from_numpy(rng.standard_normal(unet.param_count()) * 0.1)
+    r = rng.standard_normal((4, 4, 8))
+    e = rng.standard_normal((4, 4, 8))
+    loss, grad = unet.loss_and_grad(flat, [(r, e)], loss="cos")
+    assert 0.0 <= loss <= 2.0
+    for idx in [5, 12000, unet.param_count() - 3]:
+        dlt = torch.zeros_like(flat)
+        dlt[idx] = 1e-6
+        fp, _ = unet.loss_and_grad(flat + dlt, [(r, e)], loss="cos")
+        fm, _ = unet.loss_and_grad(flat - dlt, [(r, e)], loss="cos")
+        fd = (fp - fm) / 2e-6
+        assert abs(fd - float(grad[idx])) <= 1e-6 * max(1.0, abs(fd))
+    # the loss ignores the scale of the network output (head weights and bias x 3)
+    layers = unet.unflatten(flat)
+    layers[-1] = (layers[-1][0] * 3.0, layers[-1][1] * 3.0)
+    l3, _ = unet.loss_and_grad(unet.flatten(layers), [(r, e)], loss="cos")
+    assert abs(l3 - loss) <= 1e-12
+    # a target that is a positive multiple of the network's output has zero
+    # loss, a negative multiple the maximum 2
+    s = unet.scale_of(r)
+    z, _ = unet.forward(unet.unflatten(flat), torch.from_numpy(r * s)[None])
+    l0, _ = unet.loss_and_grad(flat, [(r, 2.0 * z[0].detach().numpy() / s)], loss="cos")
+    l2, _ = unet.loss_and_grad(flat, [(r, -2.0 * z[0].detach().numpy() / s)], loss="cos")
+    assert abs(l0) <= 1e-12 and abs(l2 - 2.0) <= 1e-12
+
+
 def test_adam_first_step_is_sign():
     g = torch.tensor([3.0, -0.5, 1e-2, -7.0], dtype=torch.float64)
     w = torch.tensor([1.0, 2.0, 3.0, 4.0], dtype=torch.float64)
@@ -178,11 +206,31 @@ def test_fpcg_exact_inverse_one_iteration():
     assert st.converged and st.iters == 1
 
 
-def test_fpcg_indefinite_preconditioner_falls_back():
+def test_fpcg_negative_scale_is_harmless():
     A = operators.poisson_csr(6, 6, 6)
     b = rhs(A.shape[0], 9)
-    x, st = krylov.fpcg(A, b, lambda r: -r, rtol=1e-8)
-    assert st.fell_back and st.converged
+    x1, s1 = krylov.fpcg(A, b, lambda r: -3.0 * r, rtol=1e-8)
+    x2, s2 = krylov.fpcg(A, b, lambda r: r.copy(), rtol=1e-8)
+    assert s1.converged and not s1.fell_back and s1.iters == s2.iters
+    assert np.linalg.norm(x1 - x2) <= 1e-10 * np.linalg.norm(x2)
+
+
+def test_fpcg_breakdown_falls_back():
+    A = operators.poisson_csr(6, 6, 6)
+    b = rhs(A.shape[0], 9)
+    x, st = krylov.fpcg(A, b, lambda r: np.zeros_like(r), rtol=1e-8)
+    assert st.fell_back and st.converged and st.plain_iters == st.iters
+    assert st.rel_resid <= 1e-8
+
+
+def test_fpcg_stagnation_falls_back():
+    A = operators.poisson_csr(8, 8, 8)
+    b = rhs(A.shape[0], 15)
+    # a fresh random direction on every call: z.r != 0, but 50 steps along
+    # random directions of a 512-dimensional space do not halve the residual
+    rng = np.random.default_rng(16)
+    x, st = krylov.fpcg(A, b, lambda r: rng.standard_normal(r.size), rtol=1e-8, stagnation=50)
+    assert st.fell_back and st.converged and st.iters - st.plain_iters >= 50
     assert st.rel_resid <= 1e-8
 
 
