@@ -71,6 +71,10 @@ def parse_args(argv=None):
     ap.add_argument("--batch", type=int, default=0,
                     help="benchmark N batched uneven cavities (edges from {32,48,64,96}) instead of one cavity")
     ap.add_argument("--no-batch-study", action="store_true")
+    ap.add_argument("--unet", type=int, default=0,
+                    help="time the learned preconditioner's U-Net application on an N^3 grid (N % 4 == 0) "
+                         "instead of the cavity")
+    ap.add_argument("--unet-weights", default="", help="FP32 parameter file for --unet (default: seeded init)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--max-seconds", type=float, default=150.0, help=argparse.SUPPRESS)
     return ap.parse_args(argv)
@@ -516,6 +520,8 @@ def main(argv=None):
         return main_poisson(args)
     if args.batch > 0:
         return main_batch(args)
+    if args.unet > 0:
+        return main_unet(args)
     return main_ours(args)
 
 
@@ -544,3 +550,57 @@ def main_batch(args):
 
 if __name__ == "__main__":
     sys.exit(main())
+
+
+# U-Net layers (level, c_in, c_out, taps) in application order; MACs per
+# fine-grid voxel = sum over layers of taps * c_in * c_out / 8^level
+UNET_LAYERS = [(0, 1, 16, 27), (0, 16, 16, 27), (1, 16, 32, 27), (1, 32, 32, 27), (2, 32, 64, 27), (2, 64, 64, 27),
+               (1, 96, 32, 27), (0, 48, 16, 27), (0, 16, 1, 1)]
+UNET_TC_LAYERS = [1, 2, 3, 4, 5, 6, 7]  # the ones on the tensor cores
+
+
+def main_unet(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    from paper_2504_03697_gb300 import build as B
+    B.build()
+    from paper_2504_03697_gb300 import cfd
+
+    n = args.unet
+    net = cfd.UNet(n, n, n, seed=0)
+    if args.unet_weights:
+        net.set_params(torch.from_numpy(np.fromfile(args.unet_weights, dtype="<f4")))
+    V = n ** 3
+    from paper_2504_03697_gb300.synthetic import gaussian_rhs
+    r = torch.from_numpy(gaussian_rhs(n, n, n, 0).reshape(-1)).to(device)
+    z = torch.empty_like(r)
+    for _ in range(args.warmup):
+        net.apply(r, z)
+    torch.cuda.synchronize()
+    l0 = net.launch_count()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    stream = torch.cuda.current_stream()
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        net.apply(r, z)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / max(args.steps, 1)
+    macs = sum(t * ci * co / 8 ** lv for lv, ci, co, t in UNET_LAYERS) * V
+    tc_macs = sum(UNET_LAYERS[i][3] * UNET_LAYERS[i][1] * UNET_LAYERS[i][2] / 8 ** UNET_LAYERS[i][0]
+                  for i in UNET_TC_LAYERS) * V
+    line = {"metric": "U-Net application time", "value": ms, "unit": "ms", "higher_is_better": False,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "bf16 (fp32 accumulate)",
+            "data": "synthetic",
+            "config": {"workload": f"3-level linear U-Net (16/32/64 channels) applied to an N(0,1) field on {n}^3 "
+                                   f"cells, {'trained weights' if args.unet_weights else 'seeded init'}"},
+            "flops_per_apply": 2 * macs, "tensor_core_flops_per_apply": 2 * tc_macs,
+            "achieved_tflops": 2 * macs / (ms * 1e-3) / 1e12,
+            "gpu_launches": (net.launch_count() - l0)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0

@@ -183,6 +183,22 @@ int64_t cfd_launch_count(const cfd_handle *h);
  * the reductions in different orders. */
 int cfd_set_solver_shape(cfd_handle *h, int blocks_per_sm, int tile_depth);
 
+/* Autotuner of the solver shape for this handle's grid and solver: times
+ * fixed-length pressure solves (iters iterations, a deterministic hashed
+ * right-hand side) with the automatic shape and with every blocks_per_sm in
+ * {1, 2, 3, 4} x tile_depth in {1, 2, 4, 8}, keeps the fastest (as by
+ * cfd_set_solver_shape; 0 / 0 when the automatic one wins) and reports it.
+ * Uses the intermediate-velocity scratch; the state (u, v, w, p) is not
+ * touched.  Call between steps; synchronises the stream. */
+typedef struct {
+  int32_t blocks_per_sm;    /* chosen (0: automatic)                            */
+  int32_t tile_depth;       /* chosen (0: automatic)                            */
+  int32_t candidates;       /* shapes timed                                     */
+  float ms_auto;            /* ms per fixed-length solve, automatic shape       */
+  float ms_best;            /* ms per fixed-length solve, chosen shape          */
+} cfd_tune_report;
+int cfd_autotune_solver(cfd_handle *h, int32_t iters, cfd_tune_report *rep);
+
 /* The shape the next solve of `kind` (0 pressure, 1..3 diffusion of u, v,
  * w) would use: grid size, tile depth, and whether the register path is
  * taken.  Each output pointer may be NULL. */

@@ -42,6 +42,11 @@ class cfd_params(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 8)]
 
 
+class cfd_tune_report(ctypes.Structure):
+    _fields_ = [("blocks_per_sm", ctypes.c_int32), ("tile_depth", ctypes.c_int32), ("candidates", ctypes.c_int32),
+                ("ms_auto", ctypes.c_float), ("ms_best", ctypes.c_float)]
+
+
 class cfd_solve_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("outer_iters", ctypes.c_int32),
                 ("restarts", ctypes.c_int32), ("status", ctypes.c_int32),
@@ -105,6 +110,7 @@ def load_library(path: Optional[str] = None):
         "cfd_enable_timing": (ctypes.c_int, [vp, ctypes.c_int]),
         "cfd_phase_times": (ctypes.c_int, [vp, P(ctypes.c_double), P(ctypes.c_int64)]),
         "cfd_pressure_rhs": (ctypes.c_int, [vp, vp]),
+        "cfd_autotune_solver": (ctypes.c_int, [vp, ctypes.c_int32, P(cfd_tune_report)]),
         "cfd_conv3d_bf16": (ctypes.c_int, [ctypes.c_int] * 3 + [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, vp,
                                                                 ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]),
         "cfd_unet_workspace_bytes": (ctypes.c_int, [ctypes.c_int] * 3 + [P(ctypes.c_size_t)]),
@@ -256,6 +262,12 @@ class Cavity:
 
     def launch_count(self) -> int:
         return int(self.lib.cfd_launch_count(self.h))
+
+    def autotune(self, iters=50) -> dict:
+        """Pick the fastest solver shape for this grid (cfd_autotune_solver)."""
+        rep = cfd_tune_report()
+        self._check(self.lib.cfd_autotune_solver(self.h, int(iters), ctypes.byref(rep)))
+        return {k: getattr(rep, k) for k, _ in cfd_tune_report._fields_}
 
     def pressure_rhs(self, b: torch.Tensor):
         """Projection right-hand side of the current velocity (mean kept)."""

@@ -597,6 +597,91 @@ int cfd_apply_poisson(cfd_handle* h, const double* x_dev, double* y_dev) {
   return cuda_check(h, launch_apply_poisson(g, x_dev, y_dev, tz_for(g.mz), h->stream, &h->launches), "apply_poisson");
 }
 
+namespace {
+// deterministic right-hand side for shape tuning: hashed values in [-1, 1)
+__global__ void tune_rhs_kernel(double* b, size_t n) {
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
+    uint64_t z = (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    b[i] = double(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  }
+}
+}  // namespace
+
+int cfd_autotune_solver(cfd_handle* h, int32_t iters, cfd_tune_report* rep) {
+  if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
+  if (iters < 1 || iters > 100000) return set_err(h, CFD_ERR_INVALID_ARG, "iters in [1, 100000]");
+  const size_t n = size_t(h->prm.nx) * h->prm.ny * h->prm.nz;
+  const cfd_params saved = h->prm;
+  const int bps0 = h->lg.bps_req, tz0 = h->lg.tz_req;
+  // fixed-length solves: rtol far below reach, cap = iters; x in the
+  // intermediate-velocity slot (scratch between steps), state untouched
+  h->prm.rtol = 1e-300;
+  h->prm.max_iters = iters;
+  double* x = h->ua;
+  DevSolveStats* st = &(h->stats + kStatsCap)->p;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = cuda_check(h, cudaEventCreate(&e0), "event");
+  if (!rc) rc = cuda_check(h, cudaEventCreate(&e1), "event");
+  auto time_shape = [&](int bps, int tz, float& best_ms) -> int {
+    h->lg.bps_req = bps;
+    h->lg.tz_req = tz;
+    best_ms = 1e30f;
+    for (int rep_i = 0; rep_i < 3; ++rep_i) {  // first run warms up
+      tune_rhs_kernel<<<1216, 256, 0, h->stream>>>(h->b, n);
+      int r = cuda_check(h, cudaGetLastError(), "tune rhs");
+      if (!r) r = cuda_check(h, cudaEventRecord(e0, h->stream), "event record");
+      if (!r) r = run_pressure(h, x, 1, 0, st);
+      if (!r) r = cuda_check(h, cudaEventRecord(e1, h->stream), "event record");
+      if (!r) r = cuda_check(h, cudaEventSynchronize(e1), "event sync");
+      if (r) return r;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep_i > 0 && ms < best_ms) best_ms = ms;
+    }
+    return CFD_OK;
+  };
+  float ms_auto = 0.f, ms_best = 0.f;
+  int best_bps = 0, best_tz = 0, tried = 0;
+  if (!rc) rc = time_shape(0, 0, ms_auto);
+  ms_best = ms_auto;
+  ++tried;
+  const int bps_list[4] = {1, 2, 3, 4};
+  const int tz_list[4] = {1, 2, 4, 8};
+  for (int i = 0; i < 4 && !rc; ++i) {
+    for (int j = 0; j < 4 && !rc; ++j) {
+      float ms = 0.f;
+      rc = time_shape(bps_list[i], tz_list[j], ms);
+      ++tried;
+      if (!rc && ms < ms_best) {
+        ms_best = ms;
+        best_bps = bps_list[i];
+        best_tz = tz_list[j];
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  h->prm = saved;
+  if (rc) {
+    h->lg.bps_req = bps0;
+    h->lg.tz_req = tz0;
+    return rc;
+  }
+  h->lg.bps_req = best_bps;
+  h->lg.tz_req = best_tz;
+  if (rep) {
+    rep->blocks_per_sm = best_bps;
+    rep->tile_depth = best_tz;
+    rep->candidates = tried;
+    rep->ms_auto = ms_auto;
+    rep->ms_best = ms_best;
+  }
+  return CFD_OK;
+}
+
 int cfd_pressure_rhs(cfd_handle* h, double* b_dev) {
   if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
   if (!b_dev) return set_err(h, CFD_ERR_INVALID_ARG, "b is NULL");
