@@ -71,6 +71,7 @@ def parse_args(argv=None):
     ap.add_argument("--batch", type=int, default=0,
                     help="benchmark N batched uneven cavities (edges from {32,48,64,96}) instead of one cavity")
     ap.add_argument("--no-batch-study", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the automatic solver shape")
     ap.add_argument("--unet", type=int, default=0,
                     help="time the learned preconditioner's U-Net application on an N^3 grid (N % 4 == 0) "
                          "instead of the cavity")
@@ -283,6 +284,9 @@ def main_ours(args):
     init = cavity_perturbation(n, n, n, wl["seed"] + rank, wl["amp"])
     for name, f in zip("uvw", init):
         cav.set_field(name, f)
+    # solver shape for this grid (blocks per SM x tile depth), picked by
+    # timing fixed-length solves; outside the timed region, state untouched
+    tune = None if args.no_autotune else cav.autotune(iters=50)
 
     # warm-up
     if args.warmup > 0:
@@ -406,7 +410,8 @@ def main_ours(args):
                 "data": "synthetic",
                 "config": {"workload": wl["desc"], "n": n, "cells": cells, "solver": args.solver,
                            "steps_per_rank": args.steps, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                           "l2": "flushed between timed steps (256 MiB write outside the timed events)"},
+                           "l2": "flushed between timed steps (256 MiB write outside the timed events)",
+                           "solver_shape": tune if tune is not None else "automatic"},
                 "solve": {"pcg_iters_mean": mean_iters, "pcg_iters_min": min(iters), "pcg_iters_max": max(iters),
                           "time_to_rtol_ms_mean": pcg_avg_s * 1e3, "rel_resid_max": worst_resid,
                           "all_converged": bool(ok)},
@@ -420,14 +425,17 @@ def main_ours(args):
     return 0 if ok else 1
 
 
-def time_solves(cfd, n, solver, seeds, warmup, max_iters=0, device=None):
+def time_solves(cfd, n, solver, seeds, warmup, max_iters=0, device=None, autotune=True):
     """Standalone FP64-judged pressure solves of Gaussian right-hand sides:
     per-solve device time of the solve kernel (CUDA events inside the
-    library), iterations and the true relative residual."""
+    library), iterations and the true relative residual.  The solver shape
+    is autotuned for the grid first (outside the timed solves)."""
     import torch
     from paper_2504_03697_gb300.synthetic import gaussian_rhs
 
     cav = cfd.Cavity(cfd.make_params(n, n, n, solver=solver, max_iters=max_iters), device=device)
+    if autotune:
+        cav.autotune(iters=30)
     bs = [torch.tensor(gaussian_rhs(n, n, n, seed=s), device=device) for s in seeds]
     x = torch.zeros_like(bs[0])
     for i in range(warmup):
@@ -548,9 +556,6 @@ def main_batch(args):
     return 0
 
 
-if __name__ == "__main__":
-    sys.exit(main())
-
 
 # U-Net layers (level, c_in, c_out, taps) in application order; MACs per
 # fine-grid voxel = sum over layers of taps * c_in * c_out / 8^level
@@ -604,3 +609,7 @@ def main_unet(args):
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
