@@ -72,6 +72,8 @@ def parse_args(argv=None):
                     help="benchmark N batched uneven cavities (edges from {32,48,64,96}) instead of one cavity")
     ap.add_argument("--no-batch-study", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the automatic solver shape")
+    ap.add_argument("--cg-variant", choices=["single", "two"], default="single",
+                    help="FP64 CG form: one grid reduction per iteration (default) or the textbook two")
     ap.add_argument("--unet", type=int, default=0,
                     help="time the learned preconditioner's U-Net application on an N^3 grid (N % 4 == 0) "
                          "instead of the cavity")
@@ -284,6 +286,7 @@ def main_ours(args):
     init = cavity_perturbation(n, n, n, wl["seed"] + rank, wl["amp"])
     for name, f in zip("uvw", init):
         cav.set_field(name, f)
+    cav.set_cg_variant(args.cg_variant)
     # solver shape for this grid (blocks per SM x tile depth), picked by
     # timing fixed-length solves; outside the timed region, state untouched
     tune = None if args.no_autotune else cav.autotune(iters=50)
@@ -411,7 +414,8 @@ def main_ours(args):
                 "config": {"workload": wl["desc"], "n": n, "cells": cells, "solver": args.solver,
                            "steps_per_rank": args.steps, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "l2": "flushed between timed steps (256 MiB write outside the timed events)",
-                           "solver_shape": tune if tune is not None else "automatic"},
+                           "solver_shape": tune if tune is not None else "automatic",
+                           "cg_variant": args.cg_variant},
                 "solve": {"pcg_iters_mean": mean_iters, "pcg_iters_min": min(iters), "pcg_iters_max": max(iters),
                           "time_to_rtol_ms_mean": pcg_avg_s * 1e3, "rel_resid_max": worst_resid,
                           "all_converged": bool(ok)},

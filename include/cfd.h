@@ -183,6 +183,17 @@ int64_t cfd_launch_count(const cfd_handle *h);
  * the reductions in different orders. */
 int cfd_set_solver_shape(cfd_handle *h, int blocks_per_sm, int tile_depth);
 
+/* Form of the unpreconditioned FP64 CG solves (CFD_SOLVER_CG pressure
+ * solves and the diffusion solves); both give the same iterates in exact
+ * arithmetic (Sec. 3.1 CG):
+ *   SINGLE_REDUCTION  (default) Chronopoulos-Gear form: w = A r and s = A p
+ *                     carried by recurrence, r.r and w.r reduced together,
+ *                     one grid-wide reduction per iteration;
+ *   TWO_REDUCTIONS    textbook form, p.q then r.r (two per iteration).
+ * Jacobi-preconditioned and batched solves always use the textbook form. */
+enum { CFD_CG_SINGLE_REDUCTION = 0, CFD_CG_TWO_REDUCTIONS = 1 };
+int cfd_set_cg_variant(cfd_handle *h, int variant);
+
 /* Autotuner of the solver shape for this handle's grid and solver: times
  * fixed-length pressure solves (iters iterations, a deterministic hashed
  * right-hand side) with the automatic shape and with every blocks_per_sm in

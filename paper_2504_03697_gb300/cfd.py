@@ -111,6 +111,7 @@ def load_library(path: Optional[str] = None):
         "cfd_phase_times": (ctypes.c_int, [vp, P(ctypes.c_double), P(ctypes.c_int64)]),
         "cfd_pressure_rhs": (ctypes.c_int, [vp, vp]),
         "cfd_autotune_solver": (ctypes.c_int, [vp, ctypes.c_int32, P(cfd_tune_report)]),
+        "cfd_set_cg_variant": (ctypes.c_int, [vp, ctypes.c_int]),
         "cfd_conv3d_bf16": (ctypes.c_int, [ctypes.c_int] * 3 + [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, vp,
                                                                 ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]),
         "cfd_unet_workspace_bytes": (ctypes.c_int, [ctypes.c_int] * 3 + [P(ctypes.c_size_t)]),
@@ -262,6 +263,10 @@ class Cavity:
 
     def launch_count(self) -> int:
         return int(self.lib.cfd_launch_count(self.h))
+
+    def set_cg_variant(self, variant: str):
+        """'single' (one reduction per iteration, default) or 'two' (textbook)."""
+        return self._check(self.lib.cfd_set_cg_variant(self.h, {"single": 0, "two": 1}[variant]))
 
     def autotune(self, iters=50) -> dict:
         """Pick the fastest solver shape for this grid (cfd_autotune_solver)."""

@@ -34,6 +34,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 struct Layout {
   size_t u, v, w, ua, va, wa, p;
   size_t b, r, d0, d1, q;
+  size_t e0, e1, e2;
   size_t r32, d32, p0_32, p1_32, q32;
   size_t partials, ctrl, stats;
   size_t total;
@@ -66,6 +67,10 @@ Layout ws_layout(const cfd_params& p, int max_blocks) {
   L.d0 = take(vec * 8);
   L.d1 = take(vec * 8);
   L.q = take(vec * 8);
+  // extra vectors of the single-reduction CG (double-buffered r and s, p)
+  L.e0 = take(vec * 8);
+  L.e1 = take(vec * 8);
+  L.e2 = take(vec * 8);
   if (p.solver == CFD_SOLVER_IR) {
     L.r32 = take(cells * 4);
     L.d32 = take(cells * 4);
@@ -94,6 +99,7 @@ struct cfd_handle {
   Layout L;
   double *u, *v, *w, *ua, *va, *wa, *p;
   double *b, *r, *d0, *d1, *q;
+  double *e0, *e1, *e2;
   float *r32, *d32, *p0_32, *p1_32, *q32;
   double* partials;
   SolveCtrl* ctrl;
@@ -207,6 +213,8 @@ CgArgs diffusion_args(const cfd_handle* h, int comp, DevSolveStats* st, SolveCtr
   a.c = h->prm.nu * h->prm.dt / (hh * hh);
   a.x = comp == 0 ? h->ua : (comp == 1 ? h->va : h->wa);
   a.b = h->b; a.r = h->r; a.d0 = h->d0; a.d1 = h->d1; a.q = h->q;
+  a.e0 = h->e0; a.e1 = h->e1; a.e2 = h->e2;
+  a.variant = h->lg.cg_variant;
   a.zero_x0 = 0; a.remove_mean = 0; a.gauge = 0; a.gauge_value = 0.0;
   a.rtol = h->prm.rtol;
   a.max_iters = iter_cap(h->prm);
@@ -225,6 +233,8 @@ CgArgs pressure_cg_args(const cfd_handle* h, double* x, int zero_x0, int gauge, 
   a.precond = h->prm.solver == CFD_SOLVER_JACOBI ? 1 : 0;
   a.c = 0.0;
   a.x = x; a.b = h->b; a.r = h->r; a.d0 = h->d0; a.d1 = h->d1; a.q = h->q;
+  a.e0 = h->e0; a.e1 = h->e1; a.e2 = h->e2;
+  a.variant = h->lg.cg_variant;
   a.zero_x0 = zero_x0; a.remove_mean = 1; a.gauge = gauge; a.gauge_value = 1.0;
   a.rtol = h->prm.rtol;
   a.max_iters = iter_cap(h->prm);
@@ -414,6 +424,7 @@ int cfd_create(const cfd_params* params, void* dev_ws, size_t bytes, cfd_stream_
   h->u = D(L.u); h->v = D(L.v); h->w = D(L.w);
   h->ua = D(L.ua); h->va = D(L.va); h->wa = D(L.wa); h->p = D(L.p);
   h->b = D(L.b); h->r = D(L.r); h->d0 = D(L.d0); h->d1 = D(L.d1); h->q = D(L.q);
+  h->e0 = D(L.e0); h->e1 = D(L.e1); h->e2 = D(L.e2);
   if (params->solver == CFD_SOLVER_IR) {
     h->r32 = F(L.r32); h->d32 = F(L.d32); h->p0_32 = F(L.p0_32); h->p1_32 = F(L.p1_32); h->q32 = F(L.q32);
   }
@@ -609,6 +620,14 @@ __global__ void tune_rhs_kernel(double* b, size_t n) {
   }
 }
 }  // namespace
+
+int cfd_set_cg_variant(cfd_handle* h, int variant) {
+  if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
+  if (variant != CFD_CG_SINGLE_REDUCTION && variant != CFD_CG_TWO_REDUCTIONS)
+    return set_err(h, CFD_ERR_INVALID_ARG, "unknown CG variant %d", variant);
+  h->lg.cg_variant = variant;
+  return CFD_OK;
+}
 
 int cfd_autotune_solver(cfd_handle* h, int32_t iters, cfd_tune_report* rep) {
   if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");

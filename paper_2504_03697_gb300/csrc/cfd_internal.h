@@ -32,6 +32,7 @@ struct LaunchGeom {
   int bps_req;      // requested blocks per SM (0: automatic)
   int tz_req;       // requested tile depth (0: automatic)
   int no_tma;       // 1: never take the TMA stencil path
+  int cg_variant;   // CgArgs::variant for the handle's FP64 solves
 };
 
 // Launch shape picked for one solve.
@@ -55,6 +56,10 @@ struct CgArgs {
   double* d0;
   double* d1;
   double* q;
+  double* e0;            // extra vectors of the single-reduction variant
+  double* e1;            // (all three non-null to allow it)
+  double* e2;
+  int variant;           // 0: single-reduction CG when allowed, 1: two all-reduces per iteration
   int zero_x0;           // 1: x0 = 0
   int remove_mean;       // 1: b -= mean(b) first
   int gauge;             // 1: after the solve, x += gauge_value - mean(x)

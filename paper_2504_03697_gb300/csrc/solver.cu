@@ -493,6 +493,357 @@ __global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(const __grid_con
   }
 }
 
+// ---------------------------------------------------------------------------
+// Single-reduction FP64 CG (Chronopoulos-Gear form): one grid all-reduce per
+// iteration instead of two.  With w = A r and s = A p carried by recurrence,
+//   beta_k = g_k / g_{k-1},  alpha_k = g_k / (d_k - beta_k g_k / alpha_{k-1})
+//   p_k = r_k + beta_k p_{k-1},  s_k = w_k + beta_k s_{k-1}
+//   x_{k+1} = x_k + alpha_k p_k,  r_{k+1} = r_k - alpha_k s_k
+//   w_{k+1} = A r_{k+1},  g_{k+1} = r_{k+1}.r_{k+1},  d_{k+1} = w_{k+1}.r_{k+1}
+// (g_0 = r_0.r_0, d_0 = w_0.r_0, beta_0 = 0, alpha_0 = g_0 / d_0): the same
+// iterates as the two-reduction form in exact arithmetic.  One tiled pass
+// per iteration: each block evaluates r_{k+1} on its tile AND its halo from
+// r_k, w_k, s_{k-1} (all written before the previous all-reduce), so the
+// stencil w_{k+1} = A r_{k+1} needs no barrier of its own.  r, w and s are
+// double-buffered (neighbours read iteration k's values while this block
+// writes k+1's); p and x belong to one block only and stay in registers on
+// the register path (RTZ > 0) or in memory otherwise.  Unpreconditioned
+// only; the convergence test, true-residual restarts, gauge and statistics
+// follow the two-reduction kernel.
+// ---------------------------------------------------------------------------
+
+// r_{k+1} = r_k - alpha (w_k + beta s_{k-1}) at any cell (tile or halo)
+struct NextResidual {
+  const double* r;
+  const double* w;
+  const double* s;
+  double alpha, beta;
+  bool first;
+  __device__ __forceinline__ double operator()(size_t e, int, int, int) const {
+    const double se = first ? w[e] : fma(beta, s[e], w[e]);
+    return fma(-alpha, se, r[e]);
+  }
+};
+
+struct PlainValue {
+  const double* in;
+  __device__ __forceinline__ double operator()(size_t e, int, int, int) const { return in[e]; }
+};
+
+// load_tile for any value functor (see load_tile)
+template <typename F>
+__device__ __forceinline__ void load_tile_fn(const TileShape& ts, int t, const F& src, double* s, int& x0, int& y0,
+                                             int& z0) {
+  const int bx = t % ts.ntx;
+  const int rest = t / ts.ntx;
+  const int by = rest % ts.nty;
+  const int bz = rest / ts.nty;
+  x0 = bx * kTileX;
+  y0 = by * kTileY;
+  z0 = bz * ts.tz;
+  const int D = ts.tz + 2;
+  const int slots = kTileW * kTileH * D;
+  for (int l = threadIdx.x; l < slots; l += kSolveThreads) {
+    const int lx = l % kTileW;
+    const int r2 = l / kTileW;
+    const int ly = r2 % kTileH;
+    const int lz = r2 / kTileH;
+    const int gi = x0 + lx - 1, gj = y0 + ly - 1, gk = z0 + lz - 1;
+    const int halo = (lx == 0 || lx == kTileW - 1) + (ly == 0 || ly == kTileH - 1) + (lz == 0 || lz == D - 1);
+    double v = 0.0;
+    if (halo <= 1 && gi >= 0 && gi < ts.mx && gj >= 0 && gj < ts.my && gk >= 0 && gk < ts.mz)
+      v = src(idx3(gi, gj, gk, ts.mx, ts.my), gi, gj, gk);
+    s[l] = v;
+  }
+  __syncthreads();
+}
+
+// w = A r on this block's tiles; acc += {r.r, w.r}
+__device__ void apply_dot_tiles(const TileShape& ts, const double* r, double* w, int kind, double c, double (&acc)[3],
+                                double* s, VBlock vb) {
+  const int tx = threadIdx.x % kTileX, ty = threadIdx.x / kTileX;
+  const int ntiles = ts.count();
+  Sink<double> out{nullptr, nullptr, nullptr, 0.0, false, kind, c};
+  for (int t = vb.bid; t < ntiles; t += vb.nb) {
+    int x0, y0, z0;
+    load_tile_fn(ts, t, PlainValue{r}, s, x0, y0, z0);
+    const int i = x0 + tx, j = y0 + ty;
+    if (i < ts.mx && j < ts.my) {
+      const int z1 = min(z0 + ts.tz, ts.mz);
+      for (int k = z0; k < z1; ++k) {
+        const int cl = tile_cell(k - z0, tx, ty);
+        const double rv = s[cl];
+        const double wv = row_from_smem<double>(out, s, cl, i, j, k, ts.mx, ts.my, ts.mz);
+        w[idx3(i, j, k, ts.mx, ts.my)] = wv;
+        acc[0] = fma(rv, rv, acc[0]);
+        acc[1] = fma(wv, rv, acc[1]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int RTZ>
+__global__ void __launch_bounds__(kSolveThreads, RTZ > 0 ? 1 : 3) cg1_fp64_kernel(const __grid_constant__ CgArgs a) {
+  VBlock vb{int(blockIdx.x), int(gridDim.x)};
+  __shared__ double s_tile[kTileSlots];
+  __shared__ double s_red[32 * 3];
+  __shared__ double s_invd[8];
+  if (threadIdx.x < 8) s_invd[threadIdx.x] = threadIdx.x == 0 ? 0.0 : 1.0 / double(threadIdx.x);
+  __syncthreads();
+
+  const int mx = a.g.mx, my = a.g.my, mz = a.g.mz;
+  const size_t n = size_t(mx) * my * mz;
+  const TileShape ts = make_tiles(mx, my, mz, RTZ > 0 ? RTZ : a.tz);
+  const int ntiles = ts.count();
+  const double c = a.c;
+  DevSolveStats* st = a.stats;
+  unsigned int round = 0;
+  const int tx = threadIdx.x % kTileX, ty = threadIdx.x / kTileX;
+  // double-buffered r, w, s; p in memory on the memory path
+  auto rb = [&](int i) { return i ? a.e0 : a.r; };
+  auto wb = [&](int i) { return i ? a.d1 : a.d0; };
+  auto sb = [&](int i) { return i ? a.e1 : a.q; };
+  double* pm = a.e2;
+
+  auto fail = [&]() {
+    if (threadIdx.x == 0) {
+      int e = ld_volatile_s32(&a.ctrl->error);
+      st->status = e != 0 ? e : kErrTimeout;
+    }
+  };
+  auto allreduce = [&](double (&v)[3], double (&o)[3]) {
+    return grid_allreduce<3>(v, o, a.ctrl, a.partials, s_red, a.timeout_ns, round, vb);
+  };
+
+  double acc[3], tot[3];
+  double xreg[kRegCells], preg[kRegCells];
+#pragma unroll
+  for (int q = 0; q < kRegCells; ++q) xreg[q] = preg[q] = 0.0;
+
+  // own cells of the register path: tile t = bid + kt nb, depth RTZ
+  auto own_cell = [&](int kt, int kz, size_t& e) -> bool {
+    const int t = vb.bid + kt * vb.nb;
+    if (t >= ntiles) return false;
+    const int bx = t % ts.ntx, rest = t / ts.ntx, by = rest % ts.nty, bz = rest / ts.nty;
+    const int i = bx * kTileX + tx, j = by * kTileY + ty, k = bz * ts.tz + kz;
+    if (i >= mx || j >= my || k >= mz) return false;
+    e = idx3(i, j, k, mx, my);
+    return true;
+  };
+  // register path: x of own cells to / from memory
+  auto store_x = [&]() {
+    if (RTZ > 0) {
+#pragma unroll
+      for (int kt = 0; kt < kRegCells / (RTZ > 0 ? RTZ : 1); ++kt)
+#pragma unroll
+        for (int kz = 0; kz < (RTZ > 0 ? RTZ : 1); ++kz) {
+          size_t e;
+          if (own_cell(kt, kz, e)) a.x[e] = xreg[kt * RTZ + kz];
+        }
+    }
+  };
+
+  // ---- mean of b ----
+  double shift = 0.0;
+  if (a.remove_mean) {
+    acc[0] = acc[1] = acc[2] = 0.0;
+    for (size_t e = gtid(vb); e < n; e += gstride(vb)) acc[0] += a.b[e];
+    if (!allreduce(acc, tot)) return fail();
+    shift = tot[0] / double(n);
+  }
+
+  // ---- r_0 = b - A x_0 into rb(0); b.b ----
+  acc[0] = acc[1] = acc[2] = 0.0;
+  if (a.zero_x0) {
+    for (size_t e = gtid(vb); e < n; e += gstride(vb)) {
+      const double bv = a.b[e] - shift;
+      if (a.remove_mean) a.b[e] = bv;
+      a.x[e] = 0.0;
+      rb(0)[e] = bv;
+      acc[0] = fma(bv, bv, acc[0]);
+    }
+  } else {
+    Source<double, kModeResid, 0> src{a.x, nullptr, 0.0, false, s_invd, mx, my, mz};
+    Sink<double> out{rb(0), nullptr, a.b, shift, a.remove_mean != 0, a.kind, c};
+    stencil_tiles<double, kModeResid, 0>(ts, src, out, acc, s_tile, vb);
+  }
+  if (!allreduce(acc, tot)) return fail();
+  const double bb = tot[0];
+  if (RTZ > 0) {
+#pragma unroll
+    for (int kt = 0; kt < kRegCells / (RTZ > 0 ? RTZ : 1); ++kt)
+#pragma unroll
+      for (int kz = 0; kz < (RTZ > 0 ? RTZ : 1); ++kz) {
+        size_t e;
+        if (own_cell(kt, kz, e)) xreg[kt * RTZ + kz] = a.x[e];
+      }
+  }
+
+  int status = kErrNotConverged, iters = 0, restarts = 0;
+  double rr_true = -1.0;
+  int cur = 0;
+  if (bb == 0.0) {
+    for (size_t e = gtid(vb); e < n; e += gstride(vb)) a.x[e] = 0.0;
+#pragma unroll
+    for (int q = 0; q < kRegCells; ++q) xreg[q] = 0.0;
+    status = kOk;
+    rr_true = 0.0;
+  } else {
+    const double tol2 = a.rtol * a.rtol * bb;
+    // w_0 = A r_0; g = r.r, d = w.r
+    acc[0] = acc[1] = acc[2] = 0.0;
+    apply_dot_tiles(ts, rb(0), wb(0), a.kind, c, acc, s_tile, vb);
+    if (!allreduce(acc, tot)) return fail();
+    double g = tot[0], d = tot[1];
+    double g_prev = 0.0, alpha_prev = 0.0;
+    bool first = true;
+    while (true) {
+      if (g <= tol2) {
+        // the recurrence says converged: confirm with the true residual
+        store_x();
+        acc[0] = acc[1] = acc[2] = 0.0;
+        if (!allreduce(acc, tot)) return fail();  // x of every block stored
+        Source<double, kModeResid, 0> src{a.x, nullptr, 0.0, false, s_invd, mx, my, mz};
+        Sink<double> out{rb(cur), nullptr, a.b, 0.0, false, a.kind, c};
+        stencil_tiles<double, kModeResid, 0>(ts, src, out, acc, s_tile, vb);
+        if (!allreduce(acc, tot)) return fail();
+        rr_true = tot[1];
+        if (rr_true <= tol2) {
+          status = kOk;
+          break;
+        }
+        if (++restarts > a.max_restarts) break;
+        rr_true = -1.0;
+        acc[0] = acc[1] = acc[2] = 0.0;
+        apply_dot_tiles(ts, rb(cur), wb(cur), a.kind, c, acc, s_tile, vb);
+        if (!allreduce(acc, tot)) return fail();
+        g = tot[0];
+        d = tot[1];
+        first = true;
+      }
+      if (iters >= a.max_iters) break;
+      double alpha, beta;
+      if (first) {
+        beta = 0.0;
+        alpha = g / d;
+      } else {
+        beta = g / g_prev;
+        alpha = g / (d - beta * g / alpha_prev);
+      }
+      if (!(alpha > 0.0) || !isfinite(alpha) || !isfinite(beta)) {
+        status = kErrBreakdown;
+        break;
+      }
+      const double* r0 = rb(cur);
+      const double* w0 = wb(cur);
+      const double* s0 = sb(cur);
+      double* r1 = rb(cur ^ 1);
+      double* w1 = wb(cur ^ 1);
+      double* s1 = sb(cur ^ 1);
+      const NextResidual src{r0, w0, s0, alpha, beta, first};
+      Sink<double> out{nullptr, nullptr, nullptr, 0.0, false, a.kind, c};
+      acc[0] = acc[1] = acc[2] = 0.0;
+      if (RTZ > 0) {
+#pragma unroll
+        for (int kt = 0; kt < kRegCells / (RTZ > 0 ? RTZ : 1); ++kt) {
+          const int t = vb.bid + kt * vb.nb;
+          if (t >= ntiles) break;
+          int x0, y0, z0;
+          load_tile_fn(ts, t, src, s_tile, x0, y0, z0);
+          const int i = x0 + tx, j = y0 + ty;
+#pragma unroll
+          for (int kz = 0; kz < (RTZ > 0 ? RTZ : 1); ++kz) {
+            const int k = z0 + kz;
+            if (i < mx && j < my && k < mz) {
+              const size_t e = idx3(i, j, k, mx, my);
+              const int cl = tile_cell(kz, tx, ty);
+              const double rk = r0[e];
+              const double sk = first ? w0[e] : fma(beta, s0[e], w0[e]);
+              const double pk = first ? rk : fma(beta, preg[kt * RTZ + kz], rk);
+              preg[kt * RTZ + kz] = pk;
+              xreg[kt * RTZ + kz] = fma(alpha, pk, xreg[kt * RTZ + kz]);
+              const double rn = s_tile[cl];
+              const double wn = row_from_smem<double>(out, s_tile, cl, i, j, k, mx, my, mz);
+              r1[e] = rn;
+              w1[e] = wn;
+              s1[e] = sk;
+              acc[0] = fma(rn, rn, acc[0]);
+              acc[1] = fma(wn, rn, acc[1]);
+            }
+          }
+          __syncthreads();
+        }
+      } else {
+        for (int t = vb.bid; t < ntiles; t += vb.nb) {
+          int x0, y0, z0;
+          load_tile_fn(ts, t, src, s_tile, x0, y0, z0);
+          const int i = x0 + tx, j = y0 + ty;
+          if (i < mx && j < my) {
+            const int z1 = min(z0 + ts.tz, mz);
+            for (int k = z0; k < z1; ++k) {
+              const size_t e = idx3(i, j, k, mx, my);
+              const int cl = tile_cell(k - z0, tx, ty);
+              const double rk = r0[e];
+              const double sk = first ? w0[e] : fma(beta, s0[e], w0[e]);
+              const double pk = first ? rk : fma(beta, pm[e], rk);
+              pm[e] = pk;
+              a.x[e] = fma(alpha, pk, a.x[e]);
+              const double rn = s_tile[cl];
+              const double wn = row_from_smem<double>(out, s_tile, cl, i, j, k, mx, my, mz);
+              r1[e] = rn;
+              w1[e] = wn;
+              s1[e] = sk;
+              acc[0] = fma(rn, rn, acc[0]);
+              acc[1] = fma(wn, rn, acc[1]);
+            }
+          }
+          __syncthreads();
+        }
+      }
+      if (!allreduce(acc, tot)) return fail();
+      g_prev = g;
+      alpha_prev = alpha;
+      g = tot[0];
+      d = tot[1];
+      first = false;
+      cur ^= 1;
+      ++iters;
+    }
+    if (rr_true < 0.0) {
+      // left without a true-residual check (cap, breakdown, restarts): measure it
+      store_x();
+      acc[0] = acc[1] = acc[2] = 0.0;
+      if (!allreduce(acc, tot)) return fail();
+      Source<double, kModeResid, 0> src{a.x, nullptr, 0.0, false, s_invd, mx, my, mz};
+      Sink<double> out{rb(cur), nullptr, a.b, 0.0, false, a.kind, c};
+      stencil_tiles<double, kModeResid, 0>(ts, src, out, acc, s_tile, vb);
+      if (!allreduce(acc, tot)) return fail();
+      rr_true = tot[1];
+    }
+  }
+  store_x();
+
+  // ---- gauge: shift x to the requested mean ----
+  if (a.gauge) {
+    acc[0] = acc[1] = acc[2] = 0.0;
+    if (!allreduce(acc, tot)) return fail();  // every block's x stored
+    for (size_t e = gtid(vb); e < n; e += gstride(vb)) acc[0] += a.x[e];
+    if (!allreduce(acc, tot)) return fail();
+    const double sh = a.gauge_value - tot[0] / double(n);
+    for (size_t e = gtid(vb); e < n; e += gstride(vb)) a.x[e] += sh;
+  }
+
+  if (vb.bid == 0 && threadIdx.x == 0) {
+    st->iters = iters;
+    st->outer_iters = 0;
+    st->restarts = restarts;
+    st->status = status;
+    st->b_norm = sqrt(bb);
+    st->rel_resid = bb > 0.0 ? sqrt(rr_true / bb) : 0.0;
+  }
+}
+
 // One-shot y = A x (non-persistent; one block per tile).
 __global__ void __launch_bounds__(kSolveThreads) apply_poisson_kernel(GridDims g, const double* x, double* y, int tz) {
   __shared__ double s_tile[kTileSlots];
@@ -918,6 +1269,20 @@ CgKernel cg_kernel_for(int precond, int rtz, bool multi = false) {
   return multi ? cg_kernel_for_t<true>(precond, rtz) : cg_kernel_for_t<false>(precond, rtz);
 }
 
+using Cg1Kernel = void (*)(CgArgs);
+
+Cg1Kernel cg1_kernel_for(int rtz) {
+  switch (rtz) {
+    case 1: return cg1_fp64_kernel<1>;
+    case 2: return cg1_fp64_kernel<2>;
+    case 4: return cg1_fp64_kernel<4>;
+    case 8: return cg1_fp64_kernel<8>;
+    default: return cg1_fp64_kernel<0>;
+  }
+}
+
+bool cg1_allowed(const CgArgs& a) { return a.variant == 0 && a.precond == 0 && a.e0 && a.e1 && a.e2; }
+
 }  // namespace
 
 // Co-resident blocks per SM of one kernel variant (both preconditioner
@@ -929,6 +1294,9 @@ int variant_blocks_per_sm(int rtz) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cg_kernel_for(p, rtz), kSolveThreads, 0);
     per_sm = b < per_sm ? b : per_sm;
   }
+  int b1 = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, cg1_kernel_for(rtz), kSolveThreads, 0);
+  per_sm = b1 < per_sm ? b1 : per_sm;
   return per_sm > 4 ? 4 : per_sm;
 }
 
@@ -1001,8 +1369,9 @@ cudaError_t launch_cg(const CgArgs& a_in, const LaunchGeom& lg, cudaStream_t s, 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t err = cudaLaunchKernelEx(&cfg, cg_kernel_for(a.precond, sh.rtz), a, (const CgArgs*)nullptr,
-                                       (const int*)nullptr, 0);
+  cudaError_t err = cg1_allowed(a) ? cudaLaunchKernelEx(&cfg, cg1_kernel_for(sh.rtz), a)
+                                    : cudaLaunchKernelEx(&cfg, cg_kernel_for(a.precond, sh.rtz), a,
+                                                         (const CgArgs*)nullptr, (const int*)nullptr, 0);
   if (launches) *launches += 1;
   return err;
 }

@@ -84,6 +84,30 @@ def test_pressure_solve_parity(cfd, shape, solver):
     np.testing.assert_allclose(np.linalg.norm(bo), st["b_norm"], rtol=1e-12)
 
 
+@pytest.mark.parametrize("variant", ["single", "two"])
+@pytest.mark.parametrize("shape,bps,tz", [((48, 40, 32), 0, 0), ((17, 9, 13), 0, 0), ((64, 64, 64), 1, 8),
+                                          ((96, 96, 96), 1, 1), ((33, 8, 3), 2, 2)])
+def test_cg_variants_parity(cfd, variant, shape, bps, tz):
+    # the single-reduction (Chronopoulos-Gear) and textbook forms against the
+    # oracle's textbook CG, on the register path (small grids / deep tiles)
+    # and the memory path (96^3 with one block per SM and depth-1 tiles)
+    nx, ny, nz = shape
+    cav, _ = make(cfd, shape)
+    cav.set_cg_variant(variant)
+    cav.set_solver_shape(bps, tz)
+    b = gaussian_rhs(nx, ny, nz, seed=4)
+    bg = torch.tensor(b, device="cuda")
+    xg = torch.zeros_like(bg)
+    rc, st = cav.solve_pressure(bg, xg)
+    assert rc == cfd.CFD_OK and st["rel_resid"] <= 1e-8, st
+    A = poisson_csr(nx, ny, nz)
+    bo = b.ravel() - b.mean()
+    x_rep, _ = pcg(A, bo, rtol=1e-8, max_iters=10 ** 6, fixed_iters=st["iters"])
+    assert rel_err(xg.cpu().numpy().ravel(), x_rep) < FP64_TOL
+    x_own, s_own = pcg(A, bo, rtol=1e-8, max_iters=10 ** 6)
+    assert abs(s_own.iters - st["iters"]) <= 2
+
+
 def test_zero_rhs_solve(cfd):
     cav, _ = make(cfd, (8, 8, 8))
     bg = torch.zeros((8, 8, 8), dtype=torch.float64, device="cuda")
