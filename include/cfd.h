@@ -197,16 +197,19 @@ int cfd_set_cg_variant(cfd_handle *h, int variant);
 /* Autotuner of the solver shape for this handle's grid and solver: times
  * fixed-length pressure solves (iters iterations, a deterministic hashed
  * right-hand side) with the automatic shape and with every blocks_per_sm in
- * {1, 2, 3, 4} x tile_depth in {1, 2, 4, 8}, keeps the fastest (as by
- * cfd_set_solver_shape; 0 / 0 when the automatic one wins) and reports it.
- * Uses the intermediate-velocity scratch; the state (u, v, w, p) is not
- * touched.  Call between steps; synchronises the stream. */
+ * {1, 2, 3, 4} x tile_depth in {1, 2, 4, 8} -- for CFD_SOLVER_CG under both
+ * CG forms (cfd_set_cg_variant) -- keeps the fastest (as by
+ * cfd_set_solver_shape and cfd_set_cg_variant; shape 0 / 0 when the
+ * automatic one wins) and reports it.  Uses the intermediate-velocity
+ * scratch; the state (u, v, w, p) is not touched.  Call between steps;
+ * synchronises the stream. */
 typedef struct {
   int32_t blocks_per_sm;    /* chosen (0: automatic)                            */
   int32_t tile_depth;       /* chosen (0: automatic)                            */
-  int32_t candidates;       /* shapes timed                                     */
+  int32_t candidates;       /* configurations timed                             */
   float ms_auto;            /* ms per fixed-length solve, automatic shape       */
-  float ms_best;            /* ms per fixed-length solve, chosen shape          */
+  float ms_best;            /* ms per fixed-length solve, chosen configuration  */
+  int32_t cg_variant;       /* chosen CFD_CG_* form                             */
 } cfd_tune_report;
 int cfd_autotune_solver(cfd_handle *h, int32_t iters, cfd_tune_report *rep);
 

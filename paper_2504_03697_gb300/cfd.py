@@ -44,7 +44,7 @@ class cfd_params(ctypes.Structure):
 
 class cfd_tune_report(ctypes.Structure):
     _fields_ = [("blocks_per_sm", ctypes.c_int32), ("tile_depth", ctypes.c_int32), ("candidates", ctypes.c_int32),
-                ("ms_auto", ctypes.c_float), ("ms_best", ctypes.c_float)]
+                ("ms_auto", ctypes.c_float), ("ms_best", ctypes.c_float), ("cg_variant", ctypes.c_int32)]
 
 
 class cfd_solve_stats(ctypes.Structure):

@@ -644,7 +644,9 @@ int cfd_autotune_solver(cfd_handle* h, int32_t iters, cfd_tune_report* rep) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc = cuda_check(h, cudaEventCreate(&e0), "event");
   if (!rc) rc = cuda_check(h, cudaEventCreate(&e1), "event");
-  auto time_shape = [&](int bps, int tz, float& best_ms) -> int {
+  const int var0 = h->lg.cg_variant;
+  auto time_shape = [&](int variant, int bps, int tz, float& best_ms) -> int {
+    h->lg.cg_variant = variant;
     h->lg.bps_req = bps;
     h->lg.tz_req = tz;
     best_ms = 1e30f;
@@ -662,22 +664,31 @@ int cfd_autotune_solver(cfd_handle* h, int32_t iters, cfd_tune_report* rep) {
     }
     return CFD_OK;
   };
+  // the CG form is a candidate too when the solves are unpreconditioned FP64 CG
+  const int nvar = h->prm.solver == CFD_SOLVER_CG ? 2 : 1;
   float ms_auto = 0.f, ms_best = 0.f;
-  int best_bps = 0, best_tz = 0, tried = 0;
-  if (!rc) rc = time_shape(0, 0, ms_auto);
+  int best_bps = 0, best_tz = 0, best_var = var0, tried = 0;
+  if (!rc) rc = time_shape(var0, 0, 0, ms_auto);
   ms_best = ms_auto;
   ++tried;
   const int bps_list[4] = {1, 2, 3, 4};
   const int tz_list[4] = {1, 2, 4, 8};
-  for (int i = 0; i < 4 && !rc; ++i) {
-    for (int j = 0; j < 4 && !rc; ++j) {
-      float ms = 0.f;
-      rc = time_shape(bps_list[i], tz_list[j], ms);
-      ++tried;
-      if (!rc && ms < ms_best) {
-        ms_best = ms;
-        best_bps = bps_list[i];
-        best_tz = tz_list[j];
+  for (int v = 0; v < nvar && !rc; ++v) {
+    const int variant = nvar == 1 ? var0 : v;
+    for (int i = -1; i < 4 && !rc; ++i) {
+      for (int j = 0; j < 4 && !rc; ++j) {
+        if (i < 0 && j > 0) break;
+        if (i < 0 && variant == var0) continue;  // the automatic shape of var0 is timed above
+        const int bps = i < 0 ? 0 : bps_list[i], tz = i < 0 ? 0 : tz_list[j];
+        float ms = 0.f;
+        rc = time_shape(variant, bps, tz, ms);
+        ++tried;
+        if (!rc && ms < ms_best) {
+          ms_best = ms;
+          best_bps = bps;
+          best_tz = tz;
+          best_var = variant;
+        }
       }
     }
   }
@@ -687,16 +698,19 @@ int cfd_autotune_solver(cfd_handle* h, int32_t iters, cfd_tune_report* rep) {
   if (rc) {
     h->lg.bps_req = bps0;
     h->lg.tz_req = tz0;
+    h->lg.cg_variant = var0;
     return rc;
   }
   h->lg.bps_req = best_bps;
   h->lg.tz_req = best_tz;
+  h->lg.cg_variant = best_var;
   if (rep) {
     rep->blocks_per_sm = best_bps;
     rep->tile_depth = best_tz;
     rep->candidates = tried;
     rep->ms_auto = ms_auto;
     rep->ms_best = ms_best;
+    rep->cg_variant = best_var;
   }
   return CFD_OK;
 }

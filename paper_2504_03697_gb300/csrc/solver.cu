@@ -1294,10 +1294,14 @@ int variant_blocks_per_sm(int rtz) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cg_kernel_for(p, rtz), kSolveThreads, 0);
     per_sm = b < per_sm ? b : per_sm;
   }
-  int b1 = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, cg1_kernel_for(rtz), kSolveThreads, 0);
-  per_sm = b1 < per_sm ? b1 : per_sm;
   return per_sm > 4 ? 4 : per_sm;
+}
+
+// Co-resident blocks per SM of the single-reduction variant.
+int cg1_blocks_per_sm(int rtz) {
+  int b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cg1_kernel_for(rtz), kSolveThreads, 0);
+  return b > 4 ? 4 : b;
 }
 
 int cg_max_coresident_blocks(int kind_is_ir) {
@@ -1357,8 +1361,20 @@ SolveShape pick_solve_shape(GridDims g, int max_blocks, int bps_req, int tz_req)
 
 cudaError_t launch_cg(const CgArgs& a_in, const LaunchGeom& lg, cudaStream_t s, int64_t* launches) {
   CgArgs a = a_in;
-  const SolveShape sh = pick_solve_shape(a.g, lg.blocks, lg.bps_req, lg.tz_req);
+  SolveShape sh = pick_solve_shape(a.g, lg.blocks, lg.bps_req, lg.tz_req);
   a.tz = sh.tz;
+  // the single-reduction kernel must keep the whole grid co-resident too: the
+  // memory path shrinks the grid to its capacity, the register path (whose
+  // tiles per block are fixed by the grid size) falls back to the textbook
+  // kernel instead
+  bool single = cg1_allowed(a);
+  if (single) {
+    const int cap = cg1_blocks_per_sm(sh.rtz) * num_sms();
+    if (sh.blocks > cap) {
+      if (sh.rtz > 0) single = false;
+      else sh.blocks = cap;
+    }
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(sh.blocks);
   cfg.blockDim = dim3(kSolveThreads);
@@ -1369,7 +1385,7 @@ cudaError_t launch_cg(const CgArgs& a_in, const LaunchGeom& lg, cudaStream_t s, 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t err = cg1_allowed(a) ? cudaLaunchKernelEx(&cfg, cg1_kernel_for(sh.rtz), a)
+  cudaError_t err = single ? cudaLaunchKernelEx(&cfg, cg1_kernel_for(sh.rtz), a)
                                     : cudaLaunchKernelEx(&cfg, cg_kernel_for(a.precond, sh.rtz), a,
                                                          (const CgArgs*)nullptr, (const int*)nullptr, 0);
   if (launches) *launches += 1;
