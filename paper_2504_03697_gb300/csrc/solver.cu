@@ -584,7 +584,7 @@ __device__ void apply_dot_tiles(const TileShape& ts, const double* r, double* w,
 }
 
 template <int RTZ>
-__global__ void __launch_bounds__(kSolveThreads, RTZ > 0 ? 1 : 3) cg1_fp64_kernel(const __grid_constant__ CgArgs a) {
+__global__ void __launch_bounds__(kSolveThreads, RTZ > 0 ? 2 : 3) cg1_fp64_kernel(const __grid_constant__ CgArgs a) {
   VBlock vb{int(blockIdx.x), int(gridDim.x)};
   __shared__ double s_tile[kTileSlots];
   __shared__ double s_red[32 * 3];
