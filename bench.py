@@ -338,9 +338,12 @@ def main_ours(args):
     except (OSError, ValueError):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    fp64_peak_tflops = 1.20  # FP64 FMA pipe, derived in the design doc (152 SMs x 2 DFMA/clk x 2 flops x ~2 GHz)
+    fp64_peak_tflops = 1.20  # FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (measured with DFMA chains)
     achieved_tflops = flops_per_launch / pcg_avg_s / 1e12
-    roofline = {"bound": "alu", "kernel": "cg_fp64_kernel (pressure PCG, persistent)",
+    variant = tune["cg_variant"] if tune is not None else (0 if args.cg_variant == "single" else 1)
+    roofline = {"bound": "alu",
+                "kernel": ("cg1_fp64_kernel (pressure CG, single reduction per iteration, persistent)" if variant == 0
+                           else "cg_fp64_kernel (pressure CG, two reductions per iteration, persistent)"),
                 "achieved": achieved_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved_tflops / fp64_peak_tflops, "traffic": None,
                 "peak_source": "FP64 FMA rate from the recipe's unit counts and clocks (1.2-1.25 TFLOP/s)",
