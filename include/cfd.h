@@ -312,6 +312,22 @@ int64_t cfd_batch_launch_count(const cfd_batch *b);
 int cfd_poisson_solve_noalloc(int32_t nx, int32_t ny, int32_t nz, const double *b_dev, double *x_dev,
                               double rtol, int32_t max_iters, cfd_stream_t stream, cfd_solve_stats *stats);
 
+/* Snapshot output (Sec. 3.2: the proxy app writes a CSV file of the state
+ * each step for ParaView).  cfd_snapshot enqueues device->host copies of
+ * u, v, w, p into a pinned host buffer owned by the handle (allocated on
+ * first use, freed by cfd_destroy) on the handle's stream and returns; the
+ * caller may enqueue the next cfd_step at once, so the copy and the
+ * formatting below overlap the GPU work.  cfd_snapshot_write_csv waits for
+ * that copy and writes the file: a header "x,y,z,u,v,w,p", then one line per
+ * cell (x fastest): the cell centre ((i + 1/2) h, (j + 1/2) h, (k + 1/2) h),
+ * the cell-centred velocity (the mean of the two faces along each axis) and
+ * p, each printed with 17 significant digits (exact round trip).  nthreads
+ * host threads format z-slabs in parallel (<= 0: all hardware threads).
+ * Returns CFD_ERR_INVALID_ARG without a pending snapshot or if the file
+ * cannot be written. */
+int cfd_snapshot(cfd_handle *h);
+int cfd_snapshot_write_csv(cfd_handle *h, const char *path, int nthreads);
+
 /* Pressure right-hand side of the projection (Sec. 3.1 "Projection"): the
  * scaled divergence -(rho h / dt) * sum of face differences of the current
  * velocity (u, v, w), one value per cell, written to b_dev (nx*ny*nz float64,

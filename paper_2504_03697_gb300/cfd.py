@@ -112,6 +112,8 @@ def load_library(path: Optional[str] = None):
         "cfd_pressure_rhs": (ctypes.c_int, [vp, vp]),
         "cfd_autotune_solver": (ctypes.c_int, [vp, ctypes.c_int32, P(cfd_tune_report)]),
         "cfd_set_cg_variant": (ctypes.c_int, [vp, ctypes.c_int]),
+        "cfd_snapshot": (ctypes.c_int, [vp]),
+        "cfd_snapshot_write_csv": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_int]),
         "cfd_conv3d_bf16": (ctypes.c_int, [ctypes.c_int] * 3 + [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, vp,
                                                                 ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]),
         "cfd_unet_workspace_bytes": (ctypes.c_int, [ctypes.c_int] * 3 + [P(ctypes.c_size_t)]),
@@ -263,6 +265,14 @@ class Cavity:
 
     def launch_count(self) -> int:
         return int(self.lib.cfd_launch_count(self.h))
+
+    def snapshot(self):
+        """Start an asynchronous host copy of (u, v, w, p) (cfd_snapshot)."""
+        return self._check(self.lib.cfd_snapshot(self.h))
+
+    def write_csv(self, path: str, threads: int = 0):
+        """Write the last snapshot as CSV (cfd_snapshot_write_csv)."""
+        return self._check(self.lib.cfd_snapshot_write_csv(self.h, os.fsencode(path), int(threads)))
 
     def set_cg_variant(self, variant: str):
         """'single' (one reduction per iteration, default) or 'two' (textbook)."""

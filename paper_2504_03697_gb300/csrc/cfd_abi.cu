@@ -14,6 +14,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/cfd.h"
@@ -114,6 +116,10 @@ struct cfd_handle {
   struct Pending { int phase; cudaEvent_t a, b; };
   std::vector<Pending> pending;
   int64_t ring;  // steps taken so far (statistics ring position)
+  // host snapshot of u, v, w, p for CSV output (pinned host memory)
+  double* snap = nullptr;
+  cudaEvent_t snap_ev = nullptr;
+  bool snap_pending = false;
 };
 
 namespace {
@@ -456,7 +462,95 @@ int cfd_create(const cfd_params* params, void* dev_ws, size_t bytes, cfd_stream_
 void cfd_destroy(cfd_handle* h) {
   if (!h) return;
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  if (h->snap_ev) {
+    cudaEventSynchronize(h->snap_ev);
+    cudaEventDestroy(h->snap_ev);
+  }
+  if (h->snap) cudaFreeHost(h->snap);
   delete h;
+}
+
+int cfd_snapshot(cfd_handle* h) {
+  if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
+  const size_t nu = face_count(h->prm, 0), nv = face_count(h->prm, 1), nw = face_count(h->prm, 2);
+  const size_t nc = size_t(h->prm.nx) * h->prm.ny * h->prm.nz;
+  if (!h->snap) {
+    void* p = nullptr;
+    int rc = cuda_check(h, cudaMallocHost(&p, (nu + nv + nw + nc) * 8), "snapshot host buffer");
+    if (rc) return rc;
+    h->snap = static_cast<double*>(p);
+  }
+  if (!h->snap_ev) {
+    int rc = cuda_check(h, cudaEventCreateWithFlags(&h->snap_ev, cudaEventDisableTiming), "snapshot event");
+    if (rc) return rc;
+  }
+  if (h->snap_pending) {
+    // the previous snapshot's copies may still be reading into the buffer
+    int rc = cuda_check(h, cudaEventSynchronize(h->snap_ev), "snapshot wait");
+    if (rc) return rc;
+  }
+  double* dst = h->snap;
+  const double* src[4] = {h->u, h->v, h->w, h->p};
+  const size_t cnt[4] = {nu, nv, nw, nc};
+  for (int f = 0; f < 4; ++f) {
+    int rc = cuda_check(h, cudaMemcpyAsync(dst, src[f], cnt[f] * 8, cudaMemcpyDeviceToHost, h->stream), "snapshot copy");
+    if (rc) return rc;
+    dst += cnt[f];
+  }
+  int rc = cuda_check(h, cudaEventRecord(h->snap_ev, h->stream), "snapshot record");
+  if (rc) return rc;
+  h->snap_pending = true;
+  return CFD_OK;
+}
+
+int cfd_snapshot_write_csv(cfd_handle* h, const char* path, int nthreads) {
+  if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
+  if (!path) return set_err(h, CFD_ERR_INVALID_ARG, "path is NULL");
+  if (!h->snap_pending) return set_err(h, CFD_ERR_INVALID_ARG, "no snapshot taken (cfd_snapshot)");
+  int rc = cuda_check(h, cudaEventSynchronize(h->snap_ev), "snapshot wait");
+  if (rc) return rc;
+  const int nx = h->prm.nx, ny = h->prm.ny, nz = h->prm.nz;
+  const double hh = h->prm.length / nx;
+  const size_t nu = face_count(h->prm, 0), nv = face_count(h->prm, 1), nw = face_count(h->prm, 2);
+  const double* u = h->snap;
+  const double* v = u + nu;
+  const double* w = v + nv;
+  const double* p = w + nw;
+  if (nthreads <= 0) nthreads = int(std::thread::hardware_concurrency());
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > nz) nthreads = nz;
+  // each thread formats a contiguous range of z-planes into its own buffer
+  std::vector<std::string> parts = std::vector<std::string>(size_t(nthreads));
+  auto format = [&](int t) {
+    const int k0 = int(int64_t(nz) * t / nthreads), k1 = int(int64_t(nz) * (t + 1) / nthreads);
+    std::string& out = parts[size_t(t)];
+    out.reserve(size_t(k1 - k0) * size_t(nx) * ny * 120);
+    char line[256];
+    for (int k = k0; k < k1; ++k)
+      for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+          // cell-centred velocity: mean of the two faces along each axis
+          const double uc = 0.5 * (u[(size_t(k) * ny + j) * (nx + 1) + i] + u[(size_t(k) * ny + j) * (nx + 1) + i + 1]);
+          const double vc = 0.5 * (v[(size_t(k) * (ny + 1) + j) * nx + i] + v[(size_t(k) * (ny + 1) + j + 1) * nx + i]);
+          const double wc = 0.5 * (w[(size_t(k) * ny + j) * nx + i] + w[(size_t(k + 1) * ny + j) * nx + i]);
+          const double pc = p[(size_t(k) * ny + j) * nx + i];
+          const int len = std::snprintf(line, sizeof(line), "%.17g,%.17g,%.17g,%.17g,%.17g,%.17g,%.17g\n",
+                                        (i + 0.5) * hh, (j + 0.5) * hh, (k + 0.5) * hh, uc, vc, wc, pc);
+          out.append(line, size_t(len));
+        }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nthreads; ++t) pool.emplace_back(format, t);
+  format(0);
+  for (auto& th : pool) th.join();
+  std::FILE* f = std::fopen(path, "wb");
+  if (!f) return set_err(h, CFD_ERR_INVALID_ARG, "cannot open %s for writing", path);
+  static const char header[] = "x,y,z,u,v,w,p\n";
+  bool ok = std::fwrite(header, 1, sizeof(header) - 1, f) == sizeof(header) - 1;
+  for (const auto& s2 : parts) ok = ok && std::fwrite(s2.data(), 1, s2.size(), f) == s2.size();
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return set_err(h, CFD_ERR_INVALID_ARG, "writing %s failed", path);
+  return CFD_OK;
 }
 
 const char* cfd_last_error(const cfd_handle* h) { return h ? h->err : g_last_error; }
