@@ -20,9 +20,10 @@ apart.
 
 DIC reading: d_i = a_ii - sum_{j < i, a_ij != 0} a_ij^2 / d_j and
 M = (D + L) D^-1 (D + L^T) with L the strict lower triangle of A (the
-"simplified" form keeps the sparsity of A).  On the singular Neumann
-pressure matrix the last pivot vanishes, so DIC is only applied here to
-nonsingular matrices.
+"simplified" form keeps the sparsity of A).  The incomplete factor drops
+the fill that would make the last pivot of the singular Neumann pressure
+matrix vanish, so every pivot stays positive (about 2.07 in the interior)
+and M is SPD; DIC applies to the pressure system directly.
 
 Pins (tests/test_oracle_solver.py): dense pseudo-inverse solves on grids up
 to 6^3, exactly one iteration for a single DCT mode and two for two modes,

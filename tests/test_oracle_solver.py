@@ -117,6 +117,43 @@ def test_dic_exact_on_tridiagonal():
     np.testing.assert_allclose(x, np.linalg.solve(T.toarray(), b), rtol=1e-12)
 
 
+def test_dic_pivots_on_the_neumann_pressure_matrix():
+    """DIC of the 3D Neumann matrix: deep interior pivots reach the fixed
+    point of d = 6 - 3/d, i.e. 3 + sqrt(6); every pivot of a small grid
+    equals the textbook IC(0) computed densely (fill outside the pattern of
+    A dropped); all pivots positive, so M is SPD although A is singular."""
+    n = 24
+    A = poisson_csr(n, n, n)
+    _, d = dic_precond(A)
+    assert abs(d.reshape(n, n, n)[12, 12, 12] - (3.0 + np.sqrt(6.0))) < 1e-12
+    assert d.min() > 1.5
+    A3 = poisson_csr(3, 4, 3)
+    Ad = A3.toarray()
+    m = Ad.shape[0]
+    L = np.zeros((m, m))
+    for i in range(m):  # IC(0): Cholesky restricted to the pattern of A
+        for j in range(i + 1):
+            if Ad[i, j] == 0.0:
+                continue
+            s = Ad[i, j] - L[i, :j] @ L[j, :j]
+            L[i, j] = np.sqrt(s) if i == j else s / L[j, j]
+    _, d3 = dic_precond(A3)
+    # with the lower-triangle pattern of A, IC(0) = (D + L_A) D^-1/2: its diagonal squared is d
+    np.testing.assert_allclose(d3, np.diag(L) ** 2, rtol=1e-13)
+
+
+def test_dic_pcg_on_the_pressure_system_beats_cg():
+    n = 16
+    A = poisson_csr(n, n, n)
+    b = np.random.default_rng(3).standard_normal(n ** 3)
+    b -= b.mean()
+    apply, _ = dic_precond(A)
+    x, st = pcg(A, b, rtol=1e-8, precond=apply, max_iters=2000)
+    _, st_cg = pcg(A, b, rtol=1e-8, max_iters=2000)
+    assert st.converged and st.rel_resid <= 1e-8
+    assert st.iters < 0.5 * st_cg.iters
+
+
 def test_jacobi_on_diagonal_matrix_one_iteration():
     D = sp.diags(np.arange(1.0, 11.0), format="csr")
     b = np.cos(np.arange(10.0))
