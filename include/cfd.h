@@ -71,8 +71,15 @@ enum { CFD_FIELD_U = 0, CFD_FIELD_V = 1, CFD_FIELD_W = 2, CFD_FIELD_P = 3 };
  *           the FP32 correction in FP64 and the FP64 true residual
  *           b - A x replaces the FP32 one, keeping the search direction.
  *           Convergence is judged on the FP64 true residual only.  Stats:
- *           iters = FP32 iterations, outer_iters = FP64 refinements.      */
-enum { CFD_SOLVER_CG = 0, CFD_SOLVER_JACOBI = 1, CFD_SOLVER_IR = 2 };
+ *           iters = FP32 iterations, outer_iters = FP64 refinements.
+ *   DIC     CG preconditioned by the simplified diagonal-based incomplete
+ *           Cholesky factorisation (the paper's default): pivots d_c = n_c
+ *           - sum of 1/d over the x-1, y-1, z-1 neighbours, M = (D + L)
+ *           D^-1 (D + L^T), applied by two hyperplane-wavefront triangular
+ *           sweeps (exactly the sequential recurrences).  FP64, host-driven
+ *           iteration; calls using it synchronise the stream.  Pressure only
+ *           (the diffusion solves use CG); not available in batches.      */
+enum { CFD_SOLVER_CG = 0, CFD_SOLVER_JACOBI = 1, CFD_SOLVER_IR = 2, CFD_SOLVER_DIC = 3 };
 
 /* Substeps for cfd_substep (kernel-level access to one phase of the step). */
 enum {

@@ -49,7 +49,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .krylov import identity_precond, jacobi_precond, pcg
+from .krylov import dic_precond, identity_precond, jacobi_precond, pcg
 from .mac import Cavity, ghosted, interior_mask
 from .operators import diffusion_csr, poisson_csr
 
@@ -189,7 +189,10 @@ def pressure_rhs(cav: Cavity, u, v, w):
 
 def solve_pressure(cav: Cavity, b, precond="none", fixed_iters=None):
     A = poisson_csr(cav.nx, cav.ny, cav.nz)
-    pc = identity_precond if precond == "none" else jacobi_precond(A)
+    if precond == "dic":
+        pc = dic_precond(A)[0]
+    else:
+        pc = identity_precond if precond == "none" else jacobi_precond(A)
     x, st = pcg(A, b.ravel(), x0=None, rtol=cav.rtol, max_iters=cav.iter_cap,
                 precond=pc, fixed_iters=fixed_iters)
     return x.reshape(cav.cell_shape), st

@@ -28,7 +28,7 @@ CFD_ERR_TIMEOUT = -5
 CFD_ERR_WORKSPACE_TOO_SMALL = -6
 
 FIELD = {"u": 0, "v": 1, "w": 2, "p": 3}
-SOLVER = {"cg": 0, "jacobi": 1, "ir": 2}
+SOLVER = {"cg": 0, "jacobi": 1, "ir": 2, "dic": 3}
 SUBSTEP = {"forces": 0, "advect": 1, "diffuse": 2, "project": 3}
 PHASES = ["applyForces", "solveAdvection", "diffuse", "divergence", "pcg", "applyPressureCorrection"]
 

@@ -20,6 +20,7 @@
 
 #include "../../include/cfd.h"
 #include "cfd_internal.h"
+#include "dic.h"
 
 using namespace cfd;
 
@@ -37,6 +38,7 @@ struct Layout {
   size_t u, v, w, ua, va, wa, p;
   size_t b, r, d0, d1, q;
   size_t e0, e1, e2;
+  size_t dicd;
   size_t r32, d32, p0_32, p1_32, q32;
   size_t partials, ctrl, stats;
   size_t total;
@@ -73,6 +75,7 @@ Layout ws_layout(const cfd_params& p, int max_blocks) {
   L.e0 = take(vec * 8);
   L.e1 = take(vec * 8);
   L.e2 = take(vec * 8);
+  if (p.solver == CFD_SOLVER_DIC) L.dicd = take(cells * 8);  // DIC pivots of the pressure matrix
   if (p.solver == CFD_SOLVER_IR) {
     L.r32 = take(cells * 4);
     L.d32 = take(cells * 4);
@@ -102,6 +105,8 @@ struct cfd_handle {
   double *u, *v, *w, *ua, *va, *wa, *p;
   double *b, *r, *d0, *d1, *q;
   double *e0, *e1, *e2;
+  double* dicd = nullptr;
+  bool dic_ready = false;
   float *r32, *d32, *p0_32, *p1_32, *q32;
   double* partials;
   SolveCtrl* ctrl;
@@ -172,7 +177,7 @@ int validate(const cfd_params* p) {
     return set_err(nullptr, CFD_ERR_INVALID_ARG, "length, dt, rho must be > 0 and nu >= 0");
   if (!std::isfinite(p->lid_u) || !std::isfinite(p->g[0]) || !std::isfinite(p->g[1]) || !std::isfinite(p->g[2]))
     return set_err(nullptr, CFD_ERR_INVALID_ARG, "lid_u and g must be finite");
-  if (p->solver < CFD_SOLVER_CG || p->solver > CFD_SOLVER_IR)
+  if (p->solver < CFD_SOLVER_CG || p->solver > CFD_SOLVER_DIC)
     return set_err(nullptr, CFD_ERR_INVALID_ARG, "unknown solver %d", p->solver);
   if (!(p->rtol > 0) || p->rtol >= 1) return set_err(nullptr, CFD_ERR_INVALID_ARG, "rtol must be in (0, 1)");
   if (p->max_iters < 0) return set_err(nullptr, CFD_ERR_INVALID_ARG, "max_iters must be >= 0");
@@ -283,6 +288,33 @@ int run_diffusion(cfd_handle* h, int comp, DevSolveStats* st) {
 int run_pressure(cfd_handle* h, double* x, int zero_x0, int gauge, DevSolveStats* st) {
   int rc = cuda_check(h, cudaMemsetAsync(h->ctrl, 0, sizeof(SolveCtrl), h->stream), "memset ctrl");
   if (rc) return rc;
+  if (h->prm.solver == CFD_SOLVER_DIC) {
+    DicArgs a{};
+    a.g = GridDims{h->prm.nx, h->prm.ny, h->prm.nz};
+    a.x = x; a.b = h->b; a.r = h->r; a.z = h->d0; a.p = h->d1; a.q = h->q; a.t = h->e0; a.d = h->dicd;
+    a.scratch = h->partials;
+    a.setup = h->dic_ready ? 0 : 1;
+    a.zero_x0 = zero_x0; a.remove_mean = 1; a.gauge = gauge; a.gauge_value = 1.0;
+    a.rtol = h->prm.rtol;
+    a.max_iters = iter_cap(h->prm);
+    a.max_restarts = kMaxRestarts;
+    DicResult res{};
+    const int t = phase_begin(h, CFD_PHASE_PCG);
+    rc = cuda_check(h, run_dic_pcg(a, h->stream, &h->launches, &res), "DIC-PCG");
+    phase_end(h, t);
+    if (rc) return rc;
+    h->dic_ready = true;
+    DevSolveStats ds{};
+    ds.iters = res.iters;
+    ds.outer_iters = 0;
+    ds.restarts = res.restarts;
+    ds.status = res.status;
+    ds.rel_resid = res.rel_resid;
+    ds.b_norm = res.b_norm;
+    rc = cuda_check(h, cudaMemcpyAsync(st, &ds, sizeof(ds), cudaMemcpyHostToDevice, h->stream), "DIC stats");
+    if (!rc) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "synchronize");
+    return rc;
+  }
   if (h->prm.solver == CFD_SOLVER_IR) {
     const IrArgs a = pressure_ir_args(h, x, zero_x0, gauge, st, h->ctrl);
     const int t = phase_begin(h, CFD_PHASE_PCG);
@@ -431,6 +463,7 @@ int cfd_create(const cfd_params* params, void* dev_ws, size_t bytes, cfd_stream_
   h->ua = D(L.ua); h->va = D(L.va); h->wa = D(L.wa); h->p = D(L.p);
   h->b = D(L.b); h->r = D(L.r); h->d0 = D(L.d0); h->d1 = D(L.d1); h->q = D(L.q);
   h->e0 = D(L.e0); h->e1 = D(L.e1); h->e2 = D(L.e2);
+  if (params->solver == CFD_SOLVER_DIC) h->dicd = D(L.dicd);
   if (params->solver == CFD_SOLVER_IR) {
     h->r32 = F(L.r32); h->d32 = F(L.d32); h->p0_32 = F(L.p0_32); h->p1_32 = F(L.p1_32); h->q32 = F(L.q32);
   }
@@ -1032,6 +1065,7 @@ int cfd_batch_create(int n, const cfd_params* per_cavity, void* dev_ws, size_t b
     return batch_err(nullptr, CFD_ERR_INVALID_ARG, "workspace NULL or not 256-byte aligned");
   if (bytes < need) return batch_err(nullptr, CFD_ERR_WORKSPACE_TOO_SMALL, "batch workspace %zu < %zu", bytes, need);
   const int solver = per_cavity[0].solver;
+  if (solver == CFD_SOLVER_DIC) return batch_err(nullptr, CFD_ERR_INVALID_ARG, "batches do not support the DIC solver");
   for (int i = 1; i < n; ++i)
     if (per_cavity[i].solver != solver) return batch_err(nullptr, CFD_ERR_INVALID_ARG, "all cavities of a batch use one solver");
   const BatchLayout L = batch_layout(n, per_cavity);

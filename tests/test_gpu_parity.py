@@ -12,7 +12,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 from oracle import fractional_step as fs  # noqa: E402
-from oracle.krylov import jacobi_precond, pcg  # noqa: E402
+from oracle.krylov import dic_precond, jacobi_precond, pcg  # noqa: E402
 from oracle.mac import Cavity as OCav  # noqa: E402
 from oracle.operators import poisson_csr  # noqa: E402
 from paper_2504_03697_gb300.synthetic import cavity_perturbation, gaussian_rhs, uniform_field  # noqa: E402
@@ -315,3 +315,51 @@ def test_csv_snapshot_matches_state(cfd, tmp_path):
     got = np.loadtxt(path, delimiter=",", skiprows=1)
     ref = cell_table(ocav, fields["u"], fields["v"], fields["w"], fields["p"])
     np.testing.assert_array_equal(got, ref)  # 17 significant digits round-trip exactly
+
+
+# ----------------------------------------------------------------------------
+# DIC-preconditioned CG (the paper's default preconditioner)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(16, 16, 16), (17, 9, 13), (24, 20, 28), (2, 3, 2)])
+def test_dic_solve_parity(cfd, shape):
+    nx, ny, nz = shape
+    cav, _ = make(cfd, shape, solver="dic")
+    b = gaussian_rhs(nx, ny, nz, seed=6)
+    bg = torch.tensor(b, device="cuda")
+    xg = torch.zeros_like(bg)
+    rc, st = cav.solve_pressure(bg, xg)
+    assert rc == cfd.CFD_OK and st["rel_resid"] <= 1e-8, st
+    A = poisson_csr(nx, ny, nz)
+    apply, _ = dic_precond(A)
+    bo = b.ravel() - b.mean()
+    x_rep, _ = pcg(A, bo, rtol=1e-8, max_iters=10 ** 6, precond=apply, fixed_iters=st["iters"])
+    assert rel_err(xg.cpu().numpy().ravel(), x_rep) < FP64_TOL
+    x_own, s_own = pcg(A, bo, rtol=1e-8, max_iters=10 ** 6, precond=apply)
+    assert abs(s_own.iters - st["iters"]) <= 2
+    _, s_cg = pcg(A, bo, rtol=1e-8, max_iters=10 ** 6)
+    print(f"{shape}: DIC-PCG {st['iters']} iterations, CG {s_cg.iters}")
+
+
+def test_dic_cavity_steps(cfd):
+    shape, steps = (16, 16, 16), 5
+    cav, ocav = make(cfd, shape, dt=0.01, nu=0.01, lid_u=1.0, solver="dic")
+    init = cavity_perturbation(*shape, seed=1, amp=1e-3)
+    _load(cav, init)
+    rc, stats = cav.step(steps)
+    assert rc == cfd.CFD_OK, stats
+    fixed = [{"p": s["iters"], "u": s["diff_iters"][0], "v": s["diff_iters"][1], "w": s["diff_iters"][2]}
+             for s in stats]
+    st, _ = fs.simulate(ocav, fs.initial_state(ocav, init), steps, fixed_iters_per_step=fixed, precond="dic")
+    for i, name in enumerate("uvwp"):
+        assert rel_err(cav.read_field(name).numpy(), st[i]) < FP64_TOL, name
+
+
+def test_dic_on_a_line_breaks_down_cleanly(cfd):
+    # 1 x 1 x n: no fill to drop, the factor is exact and the last pivot of the
+    # singular matrix is 0: a breakdown status, not a fault or a hang
+    cav, _ = make(cfd, (1, 1, 9), solver="dic")
+    b = np.sin(np.arange(9.0)).reshape(9, 1, 1)
+    bg = torch.tensor(b, device="cuda")
+    xg = torch.zeros_like(bg)
+    rc, st = cav.solve_pressure(bg, xg)
+    assert rc == cfd.CFD_ERR_BREAKDOWN and st["status"] == cfd.CFD_ERR_BREAKDOWN
