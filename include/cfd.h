@@ -409,6 +409,12 @@ int cfd_unet_train_step(cfd_unet *u, const double *r_dev, const double *e_dev, i
 enum { CFD_UNET_LOSS_MSE = 0, CFD_UNET_LOSS_ANORM = 1, CFD_UNET_LOSS_COS = 2 };
 int cfd_unet_set_loss(cfd_unet *u, int kind);
 
+/* on = 1 (default): the 3x3x3 convolutions stream channel blocks through a
+ * two-stage shared-memory pipeline (weights by bulk copy); on = 0: one stage,
+ * weights copied through registers.  Both issue the same MMAs in the same
+ * order, so results are bitwise equal; the switch exists for comparisons. */
+int cfd_unet_set_pipeline(cfd_unet *u, int on);
+
 /* Tensor read-back for checks (synchronous).  which in 0..25: the BF16
  * tensors (octet planes) xin, a0, s0, p0, a1, s1, p1, a2, s2, u1, d1, u0, d0
  * (activations of the last forward pass) and gz, g_d0, g_s0, g_u0, g_d1,

@@ -249,6 +249,7 @@ struct ConvTileArgs {
   int plane;                   // bytes between the two K-half planes (16-multiple)
   int tiles_x, tiles_y;
   const __nv_bfloat16* w;      // [27][NOUT][cin_pad]
+  const __nv_bfloat16* w_cm;   // or null: [cb][27] x (NOUT x 16 K-major core matrices)
   int cin_pad;
   const float* bias;
   int cout;
@@ -402,6 +403,156 @@ __global__ void __launch_bounds__(kConvThreads) conv3d_tile_kernel(const __grid_
   if (t < 32) tc::tmem_dealloc(tmem, tmem_cols);
 }
 
+// Two-stage pipelined variant for weights already in the shared-memory
+// order (w_cm): one thread streams channel block cb + 1 (two TMA plane copies
+// and one bulk copy of its 27 weight tiles) into the other stage while the
+// tensor core runs the 27 x mb MMAs of block cb; the stage is refilled once
+// the MMAs that read it have committed.  Other threads wait for the epilogue.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   tc::smem_addr(dst)),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(tc::smem_addr(bar))
+               : "memory");
+}
+
+template <int NOUT>
+__global__ void __launch_bounds__(kConvThreads) conv3d_tile_pipe_kernel(const __grid_constant__ ConvTileArgs a) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  __shared__ __align__(8) uint64_t bar_full[2], bar_mma[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+  __shared__ int s_start[kTileMaxMB];
+  constexpr int kBTap = NOUT * 32;
+  constexpr unsigned kBBytes = 27u * kBTap;
+  const size_t stage_bytes = 2 * size_t(a.plane) + kBBytes;
+
+  const int t = threadIdx.x;
+  const int tx = blockIdx.x % a.tiles_x;
+  const int ty_ = (blockIdx.x / a.tiles_x) % a.tiles_y;
+  const int tz_ = blockIdx.x / (a.tiles_x * a.tiles_y);
+  const int x0 = tx * a.xc, y0 = ty_ * a.ty, z0 = tz_ * a.tz;
+  const int cb0 = a.c0 / 16;
+  const int ncb = cb0 + a.c1 / 16;
+  const uint32_t tmem_cols = (a.mb * NOUT <= 32) ? 32u : (a.mb * NOUT <= 64 ? 64u : (a.mb * NOUT <= 128 ? 128u : (a.mb * NOUT <= 256 ? 256u : 512u)));
+  const unsigned box_bytes = unsigned(a.bx) * a.by * a.bz * 16;
+
+  if (t == 0) {
+    for (int q = 0; q < 2; ++q) {
+      tc::mbar_init(&bar_full[q], 1);
+      tc::mbar_init(&bar_mma[q], 1);
+    }
+    tc::mbar_fence_init();
+    s_fail = 0;
+  }
+  if (t < kTileMaxMB) s_start[t] = t < a.mb ? tile_block_start(a, t) : 0;
+  if (t < 32) tc::tmem_alloc(&s_tmem, tmem_cols);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = s_tmem;
+
+  if (t == 0) {
+    const uint32_t idesc = tc::idesc_bf16_f32(128, NOUT);
+    const int row_z = a.by * a.bx;
+    int st[kTileMaxMB];
+#pragma unroll
+    for (int j = 0; j < kTileMaxMB; ++j) st[j] = s_start[j];
+    auto issue = [&](int cb) {
+      unsigned char* base = dsm + size_t(cb & 1) * stage_bytes;
+      const void* map = cb < cb0 ? static_cast<const void*>(&a.map0) : static_cast<const void*>(&a.map1);
+      const int oct = 2 * (cb < cb0 ? cb : cb - cb0);
+      tc::mbar_expect_tx(&bar_full[cb & 1], 2 * box_bytes + kBBytes);
+      tc::tma_load_5d(base, map, 0, x0 - 1, y0 - 1, z0 - 1, oct, &bar_full[cb & 1]);
+      tc::tma_load_5d(base + a.plane, map, 0, x0 - 1, y0 - 1, z0 - 1, oct + 1, &bar_full[cb & 1]);
+      bulk_copy_g2s(base + 2 * size_t(a.plane), a.w_cm + size_t(cb) * (kBBytes / 2), kBBytes, &bar_full[cb & 1]);
+    };
+    int issued = 0, consumed = 0;
+    bool fail = false;
+    issue(0);
+    issued = 1;
+    for (int cb = 0; cb < ncb && !fail; ++cb) {
+      if (cb + 1 < ncb) {
+        // the stage of cb + 1 was last read by the MMAs of cb - 1
+        if (cb >= 1 && !tc::mbar_wait(&bar_mma[(cb + 1) & 1], unsigned(((cb - 1) >> 1) & 1), kConvWaitNs)) {
+          fail = true;
+          break;
+        }
+        issue(cb + 1);
+        issued = cb + 2;
+      }
+      if (!tc::mbar_wait(&bar_full[cb & 1], unsigned((cb >> 1) & 1), kConvWaitNs)) {
+        fail = true;
+        break;
+      }
+      consumed = cb + 1;
+      tc::fence_after_sync();
+      unsigned char* base = dsm + size_t(cb & 1) * stage_bytes;
+      const uint64_t adesc0 = tc::smem_desc(tc::smem_addr(base), uint32_t(a.plane), 128);
+      const uint64_t bdesc0 = tc::smem_desc(tc::smem_addr(base + 2 * size_t(a.plane)), 128, 256);
+      int tap = 0;
+      for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx, ++tap) {
+            const int off = dz * row_z + dy * a.bx + dx;
+            const uint64_t bdesc = bdesc0 + uint64_t(tap * (kBTap >> 4));
+            const bool acc = (cb | tap) != 0;
+#pragma unroll
+            for (int j = 0; j < kTileMaxMB; ++j)
+              if (j < a.mb) tc::mma_bf16(tmem + uint32_t(j * NOUT), adesc0 + uint64_t(st[j] + off), bdesc, idesc, acc);
+          }
+      tc::mma_commit(&bar_mma[cb & 1]);
+    }
+    if (!fail && ncb > 0) {
+      if (!tc::mbar_wait(&bar_mma[(ncb - 1) & 1], unsigned(((ncb - 1) >> 1) & 1), kConvWaitNs)) fail = true;
+    }
+    if (fail) {
+      s_fail = 1;
+      // let copies still in flight land before the CTA's shared memory goes away
+      for (int cb = consumed; cb < issued; ++cb) tc::mbar_wait(&bar_full[cb & 1], unsigned((cb >> 1) & 1), kConvWaitNs);
+      if (consumed > 0) tc::mbar_wait(&bar_mma[(consumed - 1) & 1], unsigned(((consumed - 1) >> 1) & 1), kConvWaitNs);
+    }
+  }
+  __syncthreads();
+  tc::fence_after_sync();
+  if (s_fail) {
+    if (t == 0) atomicExch(a.err, 1);
+  } else {
+    const int w = t / 32;
+    const int bxby = a.bx * a.by;
+    const size_t Vt = size_t(a.nx) * a.ny * a.nz;
+    for (int j = 0; j < a.mb; ++j) {
+      const int row = s_start[j] + t;
+      const int zq = row / bxby, rem = row - zq * bxby;
+      const int yq = rem / a.bx, xq = rem - yq * a.bx;
+      const int gx = x0 + xq - 1, gy = y0 + yq - 1, gz = z0 + zq - 1;
+      const bool valid = xq >= 1 && xq <= a.xc && yq >= 1 && yq <= a.ty && zq >= 1 && zq <= a.tz && gx < a.nx &&
+                         gy < a.ny && gz < a.nz;
+      const size_t v = (size_t(gz) * a.ny + gy) * a.nx + gx;
+#pragma unroll
+      for (int c0 = 0; c0 < NOUT; c0 += 16) {
+        float acc[16];
+        tc::tmem_ld16(tmem + (uint32_t(w * 32) << 16) + uint32_t(j * NOUT + c0), acc);
+        if (valid && c0 < a.cout) {
+#pragma unroll
+          for (int half = 0; half < 2; ++half) {
+            const int cbase = c0 + 8 * half;
+            if (cbase >= a.cout) break;
+            __nv_bfloat16 o8[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) o8[k] = __float2bfloat16(acc[8 * half + k] + (a.bias ? a.bias[cbase + k] : 0.f));
+            __nv_bfloat16* dst = cbase < a.split ? a.dst0 + oct_index(v, cbase, a.split, Vt)
+                                                 : a.dst1 + oct_index(v, cbase - a.split, a.cout - a.split, Vt);
+            *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<uint4*>(o8);
+          }
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (t < 32) tc::tmem_dealloc(tmem, tmem_cols);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   static std::once_flag once;
@@ -434,7 +585,13 @@ bool encode_oct_map(CUtensorMap* m, const __nv_bfloat16* base, int C, int nx, in
 
 // Output box of the tiled kernel for an nx-wide grid: full x-lines of up to
 // 128 voxels (line mode for 126..128) or consecutive 128-row blocks.
-bool pick_tile(ConvTileArgs& t, int nout) {
+int plane_bytes(const ConvTileArgs& t, int ty, int tz) {
+  const int rows = t.bx * (ty + 2) * (tz + 2);
+  const int slack = t.line_mode ? 0 : 128 + t.bx * (ty + 2) + t.bx + 1;
+  return ((rows + slack) * 16 + 127) / 128 * 128;
+}
+
+bool pick_tile(ConvTileArgs& t, int nout, int stages) {
   t.xc = t.nx >= 128 ? 128 : t.nx;
   t.bx = t.xc + 2;
   t.line_mode = t.xc == 128 ? 1 : 0;
@@ -453,7 +610,7 @@ bool pick_tile(ConvTileArgs& t, int nout) {
       }
       if (mb > max_mb) continue;
       const int rows = t.bx * (ty + 2) * (tz + 2);
-      const size_t smem = 2 * size_t((rows * 16 + 2048 + 127) / 128 * 128) + size_t(27) * nout * 32;
+      const size_t smem = size_t(stages) * (2 * size_t(plane_bytes(t, ty, tz)) + size_t(27) * nout * 32);
       if (smem > 200 * 1024) continue;
       // useful outputs per unit of (MMA rows + loaded rows)
       const double eff = double(t.xc * ty * tz) / double(mb * 128 * 27 + rows * 4);
@@ -473,10 +630,7 @@ bool pick_tile(ConvTileArgs& t, int nout) {
   t.mb = best_mb;
   // plane: the box rows plus slack for M-blocks that run past the last row
   // (contiguous mode reads up to 127 rows + one z-slab beyond it)
-  const int rows = t.bx * t.by * t.bz;
-  const int slack = t.line_mode ? 0 : 128 + t.bx * t.by + t.bx + 1;
-  t.plane = (rows + slack) * 16;
-  t.plane = (t.plane + 127) / 128 * 128;
+  t.plane = plane_bytes(t, t.ty, t.tz);
   t.tiles_x = (t.nx + t.xc - 1) / t.xc;
   t.tiles_y = (t.ny + t.ty - 1) / t.ty;
   return true;
@@ -488,16 +642,18 @@ cudaError_t launch_tile(const ConvArgs& a, cudaStream_t s, bool& taken) {
   ConvTileArgs t{};
   t.nx = a.nx; t.ny = a.ny; t.nz = a.nz;
   t.c0 = a.c0; t.c1 = a.c1;
-  if (!pick_tile(t, NOUT)) return cudaSuccess;
+  const bool pipe = a.w_cm != nullptr && !(reinterpret_cast<uintptr_t>(a.w_cm) & 15);
+  if (!pick_tile(t, NOUT, pipe ? 2 : 1)) return cudaSuccess;
   if (!encode_oct_map(&t.map0, a.src0, a.c0, a.nx, a.ny, a.nz, t.bx, t.by, t.bz)) return cudaSuccess;
   if (a.c1 > 0 && !encode_oct_map(&t.map1, a.src1, a.c1, a.nx, a.ny, a.nz, t.bx, t.by, t.bz)) return cudaSuccess;
   t.w = a.w;
+  t.w_cm = pipe ? a.w_cm : nullptr;
   t.cin_pad = (a.c0 + a.c1 + 15) / 16 * 16;
   t.bias = a.bias;
   t.cout = a.cout;
   t.dst0 = a.dst0; t.dst1 = a.dst1; t.split = a.split;
   t.err = a.err;
-  const size_t smem = 2 * size_t(t.plane) + size_t(27) * NOUT * 32;
+  const size_t smem = size_t(pipe ? 2 : 1) * (2 * size_t(t.plane) + size_t(27) * NOUT * 32);
   // TMEM: at most 512 / cols CTAs may share an SM; pad the shared-memory
   // request so that no more than that many fit
   const int need = t.mb * NOUT;
@@ -510,11 +666,16 @@ cudaError_t launch_tile(const ConvArgs& a, cudaStream_t s, bool& taken) {
   static int configured = 0;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(conv3d_tile_kernel<NOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemMax);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(conv3d_tile_pipe_kernel<NOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemMax);
     if (e != cudaSuccess) return e;
     configured = 1;
   }
   const unsigned grid = unsigned(t.tiles_x) * unsigned(t.tiles_y) * unsigned((t.nz + t.tz - 1) / t.tz);
-  conv3d_tile_kernel<NOUT><<<grid, kConvThreads, req, s>>>(t);
+  if (pipe)
+    conv3d_tile_pipe_kernel<NOUT><<<grid, kConvThreads, req, s>>>(t);
+  else
+    conv3d_tile_kernel<NOUT><<<grid, kConvThreads, req, s>>>(t);
   taken = true;
   return cudaGetLastError();
 }

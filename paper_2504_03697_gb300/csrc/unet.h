@@ -28,6 +28,9 @@ struct ConvArgs {
   int ks;                        // 3 or 1
   int packed;                    // 1: c0 == 1, ks == 3: K = 27 taps padded to 32
   const __nv_bfloat16* w;        // [ks^3][nout_pad][cin_pad] or packed [nout_pad][32]
+  const __nv_bfloat16* w_cm;     // or null: the same 3x3x3 weights in shared-memory order,
+                                 // [cin_pad/16][27] blocks of nout_pad x 16 K-major core
+                                 // matrices (the tiled kernel then streams them with bulk copies)
   const float* bias;             // [cout] or null
   int cout;                      // output channels (<= nout_pad)
   __nv_bfloat16* dst0;           // channels [0, split), octet planes

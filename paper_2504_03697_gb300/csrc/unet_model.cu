@@ -567,6 +567,23 @@ __global__ void wgrad_reduce_kernel(const float* partial, const float* bias_part
   }
 }
 
+// [27][nout][cin_pad] -> [cin_pad/16][27] blocks of nout x 16 K-major core
+// matrices (byte (o/8) 256 + h 128 + (o%8) 16 within a block), one 16-byte
+// chunk per work item
+__global__ void to_smem_order_kernel(const __nv_bfloat16* src, int nout, int cin_pad, __nv_bfloat16* dst) {
+  const size_t chunks = size_t(27) * nout * (cin_pad / 8);
+  for (size_t e = gtid(); e < chunks; e += gstride()) {
+    const int c8 = int(e % (cin_pad / 8));
+    const int o = int((e / (cin_pad / 8)) % nout);
+    const int tap = int(e / (size_t(cin_pad / 8) * nout));
+    const int cb = c8 / 2, h = c8 % 2;
+    const size_t byte = (size_t(cb) * 27 + tap) * size_t(nout) * 32 + size_t(o >> 3) * 256 + size_t(h) * 128 +
+                        size_t(o & 7) * 16;
+    *reinterpret_cast<uint4*>(reinterpret_cast<char*>(dst) + byte) =
+        *reinterpret_cast<const uint4*>(src + (size_t(tap) * nout + o) * cin_pad + 8 * c8);
+  }
+}
+
 // ---- optimiser and weight packing -------------------------------------------
 
 __global__ void adam_kernel(float* w, float* m, float* v, const float* g, size_t n, float lr, float b1, float b2,
@@ -760,6 +777,8 @@ struct cfd_unet {
   size_t woff[kNumLayers], boff[kNumLayers];  // offsets of weights / bias of each layer
   // BF16 weight copies
   __nv_bfloat16* wf[kNumLayers];       // forward
+  __nv_bfloat16* wfc[kNumLayers];      // forward, shared-memory order (3x3x3 layers 1..7)
+  __nv_bfloat16* wdc[kNumLayers][2];   // input gradient, shared-memory order
   __nv_bfloat16* wd[kNumLayers][2];    // input gradient (two output slices for L1c)
   // activations
   __nv_bfloat16 *xin, *a0, *s0, *p0, *a1, *s1, *p1, *a2, *s2, *u1, *d1, *u0, *d0;
@@ -777,6 +796,7 @@ struct cfd_unet {
   __nv_bfloat16* tens[26];
   size_t tens_count[26];
   int loss_kind;  // CFD_UNET_LOSS_*
+  int no_pipe;    // 1: tiled convolutions without the two-stage pipeline (comparison runs)
   int adam_t;
   int64_t launches;
 };
@@ -827,7 +847,21 @@ size_t carve(cfd_unet* u, int nx, int ny, int nz, char* base) {
         wd0 = reinterpret_cast<__nv_bfloat16*>(take(size_t(taps) * nout_pad(cin) * pad16(L.cout) * 2));
       }
     }
-    if (u) { u->wf[l] = wf; u->wd[l][0] = wd0; u->wd[l][1] = wd1; }
+    // copies in the tiled kernel's shared-memory order for the 3x3x3 layers
+    __nv_bfloat16 *wfc = nullptr, *wdc0 = nullptr, *wdc1 = nullptr;
+    if (l >= 1 && l <= 7) {
+      wfc = reinterpret_cast<__nv_bfloat16*>(take(fwd * 2));
+      if (l == 6) {
+        wdc0 = reinterpret_cast<__nv_bfloat16*>(take(size_t(taps) * 32 * pad16(L.cout) * 2));
+        wdc1 = reinterpret_cast<__nv_bfloat16*>(take(size_t(taps) * 64 * pad16(L.cout) * 2));
+      } else {
+        wdc0 = reinterpret_cast<__nv_bfloat16*>(take(size_t(taps) * nout_pad(cin) * pad16(L.cout) * 2));
+      }
+    }
+    if (u) {
+      u->wf[l] = wf; u->wd[l][0] = wd0; u->wd[l][1] = wd1;
+      u->wfc[l] = wfc; u->wdc[l][0] = wdc0; u->wdc[l][1] = wdc1;
+    }
   }
   auto act = [&](size_t vox, int c) { return reinterpret_cast<__nv_bfloat16*>(take(vox * size_t(c) * 2)); };
   __nv_bfloat16* bufs[26] = {
@@ -917,6 +951,7 @@ int conv(cfd_unet* u, int layer, const __nv_bfloat16* src0, const __nv_bfloat16*
   a.src0 = src0; a.c0 = L.c0; a.src1 = src1; a.c1 = L.c1;
   a.ks = L.ks; a.packed = L.packed ? 1 : 0;
   a.w = u->wf[layer];
+  a.w_cm = u->no_pipe ? nullptr : u->wfc[layer];
   a.bias = u->w + u->boff[layer];
   a.cout = L.cout;
   a.dst0 = dst0; a.dst1 = dst1; a.split = split; a.dst_f32 = dst_f32;
@@ -934,6 +969,7 @@ int conv_dgrad(cfd_unet* u, int layer, int slice, const __nv_bfloat16* gout, int
   a.src0 = gout; a.c0 = L.cout; a.src1 = nullptr; a.c1 = 0;
   a.ks = L.ks; a.packed = 0;
   a.w = u->wd[layer][slice];
+  a.w_cm = u->no_pipe ? nullptr : u->wdc[layer][slice];
   a.bias = nullptr;
   a.cout = o_count;
   a.dst0 = dst0; a.dst1 = dst1; a.split = split; a.dst_f32 = nullptr;
@@ -979,6 +1015,21 @@ int pack_weights(cfd_unet* u) {
     }
     rc = klaunch(u, "pack dgrad");
     if (rc) return rc;
+    if (l <= 7) {
+      auto cm = [&](const __nv_bfloat16* src, int nout, int cin_pad, __nv_bfloat16* dst) {
+        to_smem_order_kernel<<<grid_for(size_t(27) * nout * cin_pad / 8), kThreads, 0, u->stream>>>(src, nout, cin_pad,
+                                                                                                     dst);
+        return klaunch(u, "weights to shared-memory order");
+      };
+      rc = cm(u->wf[l], nout_pad(L.cout), pad16(cin), u->wfc[l]);
+      if (!rc && l == 6) {
+        rc = cm(u->wd[l][0], 32, pad16(L.cout), u->wdc[l][0]);
+        if (!rc) rc = cm(u->wd[l][1], 64, pad16(L.cout), u->wdc[l][1]);
+      } else if (!rc) {
+        rc = cm(u->wd[l][0], nout_pad(cin), pad16(L.cout), u->wdc[l][0]);
+      }
+      if (rc) return rc;
+    }
   }
   return CFD_OK;
 }
@@ -1231,6 +1282,12 @@ int cfd_unet_train_step(cfd_unet* u, const double* r_dev, const double* e_dev, i
   if (!rc && herr) rc = uerr(CFD_ERR_TIMEOUT, "unet: a tensor-core wait timed out");
   if (loss) *loss = float(total / npairs);
   return rc;
+}
+
+int cfd_unet_set_pipeline(cfd_unet* u, int on) {
+  if (!u) return uerr(CFD_ERR_INVALID_ARG, "unet: NULL handle");
+  u->no_pipe = on ? 0 : 1;
+  return CFD_OK;
 }
 
 int cfd_unet_set_loss(cfd_unet* u, int kind) {
