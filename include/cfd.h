@@ -409,10 +409,11 @@ int cfd_unet_train_step(cfd_unet *u, const double *r_dev, const double *e_dev, i
 enum { CFD_UNET_LOSS_MSE = 0, CFD_UNET_LOSS_ANORM = 1, CFD_UNET_LOSS_COS = 2 };
 int cfd_unet_set_loss(cfd_unet *u, int kind);
 
-/* on = 1 (default): the 3x3x3 convolutions stream channel blocks through a
- * two-stage shared-memory pipeline (weights by bulk copy); on = 0: one stage,
- * weights copied through registers.  Both issue the same MMAs in the same
- * order, so results are bitwise equal; the switch exists for comparisons. */
+/* on = 1: the 3x3x3 convolutions stream channel blocks through a two-stage
+ * shared-memory pipeline (weights by bulk copy); on = 0 (default): one stage,
+ * weights copied through registers, two CTAs per SM (measured faster: the
+ * pipeline's shared memory halves the tile and the occupancy).  Both issue
+ * the same MMAs in the same order, so results are bitwise equal. */
 int cfd_unet_set_pipeline(cfd_unet *u, int on);
 
 /* Tensor read-back for checks (synchronous).  which in 0..25: the BF16

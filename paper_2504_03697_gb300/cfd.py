@@ -500,7 +500,7 @@ class UNet:
         self._check(self.lib.cfd_unet_set_loss(self.u, {"mse": 0, "anorm": 1, "cos": 2}[kind]))
 
     def set_pipeline(self, on=True):
-        """Two-stage pipelined tiled convolutions (default) or one stage."""
+        """Two-stage pipelined tiled convolutions, or one stage (the default)."""
         self._check(self.lib.cfd_unet_set_pipeline(self.u, 1 if on else 0))
 
     def read_tensor(self, which) -> torch.Tensor:

@@ -796,7 +796,7 @@ struct cfd_unet {
   __nv_bfloat16* tens[26];
   size_t tens_count[26];
   int loss_kind;  // CFD_UNET_LOSS_*
-  int no_pipe;    // 1: tiled convolutions without the two-stage pipeline (comparison runs)
+  int no_pipe;    // 1 (default): one-stage tiled convolutions; 0: the two-stage pipeline
   int adam_t;
   int64_t launches;
 };
@@ -1180,6 +1180,7 @@ int cfd_unet_create(int nx, int ny, int nz, void* dev_ws, size_t bytes, cfd_stre
   u->ws = static_cast<char*>(dev_ws);
   u->bytes = bytes;
   u->nparams = param_count();
+  u->no_pipe = 1;  // measured faster: two CTAs per SM overlap each other's copies and MMAs
   carve(u, nx, ny, nz, u->ws);
   std::vector<float> p(size_t(u->nparams));
   init_params(p, seed);
