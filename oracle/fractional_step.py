@@ -137,6 +137,12 @@ def interpolate(cav: Cavity, f, comp: int, X, Y, Z):
 
 
 def advect(cav: Cavity, u, v, w):
+    """Semi-Lagrangian advection (Sec. 3.1).  Backtrace: explicit Euler,
+    x - dt v(x) (advect_order 1), or the explicit midpoint rule (advect_order
+    2, a reading of the paper's "optimizing the advection kernel" future
+    work): x_m = x - (dt/2) v(x), x - dt v(x_m), with v(x_m) sampled
+    trilinearly from each component's own grid; every point is clamped into
+    the box."""
     fields = (u, v, w)
     ext = cav.extent
     h = cav.h
@@ -147,6 +153,9 @@ def advect(cav: Cavity, u, v, w):
         off[comp] = 0.0
         pos = [(I + off[0]) * h, (J + off[1]) * h, (K + off[2]) * h]
         vel = face_velocity(cav, fields, comp, I, J, K)
+        if cav.advect_order == 2:
+            mid = [np.clip(pos[d] - 0.5 * cav.dt * vel[d], 0.0, ext[d]) for d in range(3)]
+            vel = [interpolate(cav, fields[d], d, *mid) for d in range(3)]
         back = [np.clip(pos[d] - cav.dt * vel[d], 0.0, ext[d]) for d in range(3)]
         new = fields[comp].copy()
         new[K, J, I] = interpolate(cav, fields[comp], comp, *back)

@@ -47,6 +47,7 @@ class Cavity:
     g: tuple = (0.0, 0.0, 0.0)   # lid forcing offset per unit time (Sec. 3)
     rtol: float = 1e-8
     max_iters: int = 0           # 0 -> 20 * max(nx, ny, nz)
+    advect_order: int = 1        # backtrace: 1 explicit Euler, 2 explicit midpoint (RK2)
 
     @property
     def h(self) -> float:

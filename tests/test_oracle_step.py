@@ -198,6 +198,41 @@ def test_backtrace_direction_and_distance():
     np.testing.assert_allclose(v2[sl], a * (X[sl] - cav.dt * U0), rtol=1e-13)
 
 
+def test_midpoint_backtrace_on_a_linear_flow():
+    """u = b X (v = w = 0): the explicit midpoint backtrace of a u face at X
+    lands at X (1 - dt b + (dt b)^2 / 2) (trilinear sampling is exact on the
+    linear field), so the advected u is b X (1 - dt b + (dt b)^2 / 2); the
+    Euler backtrace gives b X (1 - dt b).  Faces away from the walls."""
+    b = 1.3
+    for order, factor in ((2, lambda q: 1 - q + q * q / 2), (1, lambda q: 1 - q)):
+        cav = Cavity(16, 6, 6, dt=0.05, lid_u=0.0, advect_order=order)
+        X, _, _ = face_positions(cav, 0)
+        u = b * X
+        u[:, :, 0] = 0.0
+        u[:, :, -1] = 0.0
+        v = np.zeros(cav.face_shape(1))
+        w = np.zeros(cav.face_shape(2))
+        u2, _, _ = fs.advect(cav, u, v, w)
+        sl = (slice(1, -1), slice(1, -1), slice(2, -3))
+        np.testing.assert_allclose(u2[sl], b * X[sl] * factor(cav.dt * b), rtol=1e-13)
+
+
+def test_midpoint_equals_euler_for_uniform_flow():
+    cav1 = Cavity(10, 6, 6, dt=0.02, lid_u=0.0)
+    cav2 = Cavity(10, 6, 6, dt=0.02, lid_u=0.0, advect_order=2)
+    u = np.zeros(cav1.face_shape(0))
+    u[:, :, 1:-1] = 0.6
+    X, Y, Z = face_positions(cav1, 1)
+    v = 0.3 * X
+    v[:, 0, :] = 0.0
+    v[:, -1, :] = 0.0
+    w = np.zeros(cav1.face_shape(2))
+    a = fs.advect(cav1, u, v, w)
+    b = fs.advect(cav2, u, v, w)
+    sl = (slice(1, -1), slice(2, -2), slice(2, -2))
+    np.testing.assert_allclose(b[1][sl], a[1][sl], rtol=1e-14)
+
+
 def test_gauge_mean_is_one():
     cav = Cavity(8, 8, 8, dt=0.01, nu=0.01, lid_u=1.0)
     st = _state(cav)
