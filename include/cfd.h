@@ -103,7 +103,9 @@ typedef struct {
   int32_t warm_start;       /* 1: start the pressure solve from the previous p    */
   double ir_delta;          /* IR: refine in FP64 each time the FP32 residual has
                                fallen by this factor, in (0, 1); 0 -> 0.1          */
-  int32_t reserved[8];      /* must be zero                                       */
+  int32_t advect_order;     /* backtrace: 0 or 1 explicit Euler x - dt v(x); 2 the
+                               explicit midpoint rule x - dt v(x - dt/2 v(x))     */
+  int32_t reserved[7];      /* must be zero                                       */
 } cfd_params;
 
 typedef struct {

@@ -39,7 +39,7 @@ class cfd_params(ctypes.Structure):
                 ("nu", ctypes.c_double), ("lid_u", ctypes.c_double), ("g", ctypes.c_double * 3),
                 ("solver", ctypes.c_int32), ("rtol", ctypes.c_double), ("max_iters", ctypes.c_int32),
                 ("warm_start", ctypes.c_int32), ("ir_delta", ctypes.c_double),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("advect_order", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
 class cfd_tune_report(ctypes.Structure):
@@ -140,7 +140,7 @@ def load_library(path: Optional[str] = None):
 
 
 def make_params(nx, ny, nz, length=1.0, dt=0.01, rho=1.0, nu=0.0, lid_u=1.0, g=(0.0, 0.0, 0.0),
-                solver="cg", rtol=1e-8, max_iters=0, warm_start=False, ir_delta=0.0) -> cfd_params:
+                solver="cg", rtol=1e-8, max_iters=0, warm_start=False, ir_delta=0.0, advect_order=1) -> cfd_params:
     prm = cfd_params()
     prm.nx, prm.ny, prm.nz = int(nx), int(ny), int(nz)
     prm.length, prm.dt, prm.rho, prm.nu, prm.lid_u = float(length), float(dt), float(rho), float(nu), float(lid_u)
@@ -151,6 +151,7 @@ def make_params(nx, ny, nz, length=1.0, dt=0.01, rho=1.0, nu=0.0, lid_u=1.0, g=(
     prm.max_iters = int(max_iters)
     prm.warm_start = 1 if warm_start else 0
     prm.ir_delta = float(ir_delta)
+    prm.advect_order = int(advect_order)
     return prm
 
 

@@ -182,7 +182,8 @@ int validate(const cfd_params* p) {
   if (!(p->rtol > 0) || p->rtol >= 1) return set_err(nullptr, CFD_ERR_INVALID_ARG, "rtol must be in (0, 1)");
   if (p->max_iters < 0) return set_err(nullptr, CFD_ERR_INVALID_ARG, "max_iters must be >= 0");
   if (p->ir_delta < 0 || p->ir_delta >= 1) return set_err(nullptr, CFD_ERR_INVALID_ARG, "ir_delta must be in [0, 1)");
-  for (int i = 0; i < 8; ++i)
+  if (p->advect_order < 0 || p->advect_order > 2) return set_err(nullptr, CFD_ERR_INVALID_ARG, "advect_order in {0, 1, 2}");
+  for (int i = 0; i < 7; ++i)
     if (p->reserved[i] != 0) return set_err(nullptr, CFD_ERR_INVALID_ARG, "reserved fields must be zero");
   return CFD_OK;
 }
@@ -203,6 +204,7 @@ PhysArgs phys(const cfd_handle* h) {
   a.g[0] = h->prm.g[0]; a.g[1] = h->prm.g[1]; a.g[2] = h->prm.g[2];
   a.u = h->u; a.v = h->v; a.w = h->w; a.ua = h->ua; a.va = h->va; a.wa = h->wa;
   a.p = h->p; a.b = h->b;
+  a.rk2 = h->prm.advect_order == 2 ? 1 : 0;
   return a;
 }
 

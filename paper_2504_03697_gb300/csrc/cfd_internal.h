@@ -125,6 +125,7 @@ struct PhysArgs {
   double* ua; double* va; double* wa;    // intermediate velocity
   double* p;                             // pressure (cells)
   double* b;                             // solver rhs scratch
+  int rk2;                               // 1: explicit-midpoint backtrace
 };
 
 // Kernel launchers (return the CUDA error of the launch).  Each adds the

@@ -150,6 +150,20 @@ __global__ void __launch_bounds__(kSweepThreads) advect_kernel(PhysArgs a) {
       if (d == comp) vel[d] = fields[comp][l];
       else vel[d] = face_avg(fields[d], comp, d, i, j, k, nx, ny, nz);
     }
+    if (a.rk2) {
+      // explicit midpoint: velocity sampled at x - dt/2 v(x), each component
+      // from its own grid
+      double mid[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        double x = pos[d] - 0.5 * a.dt * vel[d];
+        x = x < 0.0 ? 0.0 : (x > ext[d] ? ext[d] : x);
+        mid[d] = x;
+      }
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        vel[d] = interpolate(fields[d], d, mid[0], mid[1], mid[2], nx, ny, nz, a.inv_h, a.lid_u);
+    }
     double back[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {

@@ -40,8 +40,8 @@ def rel_err(g, o):
 
 def make(cfd, n, **kw):
     nx, ny, nz = n if isinstance(n, tuple) else (n, n, n)
-    return cfd.Cavity(cfd.make_params(nx, ny, nz, **kw)), OCav(nx, ny, nz, **{k: v for k, v in kw.items()
-                                                                             if k in ("dt", "nu", "lid_u", "g", "rho", "length", "rtol", "max_iters")})
+    keep = ("dt", "nu", "lid_u", "g", "rho", "length", "rtol", "max_iters", "advect_order")
+    return cfd.Cavity(cfd.make_params(nx, ny, nz, **kw)), OCav(nx, ny, nz, **{k: v for k, v in kw.items() if k in keep})
 
 
 # ----------------------------------------------------------------------------
@@ -163,9 +163,10 @@ def _zero_walls(ocav, fields):
     return out
 
 
+@pytest.mark.parametrize("order", [1, 2])
 @pytest.mark.parametrize("shape", [(16, 16, 16), (17, 9, 13), (5, 31, 4)])
-def test_advect_parity(cfd, shape):
-    cav, ocav = make(cfd, shape, dt=0.05, lid_u=1.3)
+def test_advect_parity(cfd, shape, order):
+    cav, ocav = make(cfd, shape, dt=0.05, lid_u=1.3, advect_order=order)
     f = _zero_walls(ocav, _random_velocity(ocav, 5, 2.0))  # backtraces cross cells and walls
     _load(cav, f)
     cav.substep("advect")
@@ -363,3 +364,10 @@ def test_dic_on_a_line_breaks_down_cleanly(cfd):
     xg = torch.zeros_like(bg)
     rc, st = cav.solve_pressure(bg, xg)
     assert rc == cfd.CFD_ERR_BREAKDOWN and st["status"] == cfd.CFD_ERR_BREAKDOWN
+
+
+def test_cavity_midpoint_backtrace_steps(cfd):
+    """The cavity with the explicit-midpoint backtrace: 16^3, 8 steps."""
+    cav, ocav, stats, st, errs = _run_pair(cfd, (16, 16, 16), 8, 2, dt=0.01, nu=0.01, lid_u=1.0, advect_order=2)
+    for name, e in errs.items():
+        assert e < FP64_TOL, (name, e)
