@@ -74,6 +74,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-autotune", action="store_true", help="keep the automatic solver shape")
     ap.add_argument("--cg-variant", choices=["single", "two"], default="single",
                     help="FP64 CG form: one grid reduction per iteration (default) or the textbook two")
+    ap.add_argument("--spmv", type=int, default=0,
+                    help="time the pressure operator on an N^3 grid: matrix-free stencil vs the assembled CSR matrix")
+    ap.add_argument("--advect-order", type=int, default=1, choices=[1, 2],
+                    help="backtrace of the cavity workload: 1 explicit Euler (default), 2 explicit midpoint")
     ap.add_argument("--unet", type=int, default=0,
                     help="time the learned preconditioner's U-Net application on an N^3 grid (N % 4 == 0) "
                          "instead of the cavity")
@@ -281,7 +285,8 @@ def main_ours(args):
     wl = WORKLOADS[args.workload]
     n = wl["n"]
     cells = n ** 3
-    prm = cfd.make_params(n, n, n, dt=wl["dt"], nu=wl["nu"], lid_u=wl["lid_u"], solver=args.solver)
+    prm = cfd.make_params(n, n, n, dt=wl["dt"], nu=wl["nu"], lid_u=wl["lid_u"], solver=args.solver,
+                          advect_order=args.advect_order)
     stream = torch.cuda.current_stream(device)
     cav = cfd.Cavity(prm, device=device)
     init = cavity_perturbation(n, n, n, wl["seed"] + rank, wl["amp"])
@@ -419,7 +424,7 @@ def main_ours(args):
                            "steps_per_rank": args.steps, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "l2": "flushed between timed steps (256 MiB write outside the timed events)",
                            "solver_shape": tune if tune is not None else "automatic",
-                           "cg_variant": args.cg_variant},
+                           "cg_variant": args.cg_variant, "advect_order": args.advect_order},
                 "solve": {"pcg_iters_mean": mean_iters, "pcg_iters_min": min(iters), "pcg_iters_max": max(iters),
                           "time_to_rtol_ms_mean": pcg_avg_s * 1e3, "rel_resid_max": worst_resid,
                           "all_converged": bool(ok)},
@@ -538,6 +543,8 @@ def main(argv=None):
         return main_batch(args)
     if args.unet > 0:
         return main_unet(args)
+    if args.spmv > 0:
+        return main_spmv(args)
     return main_ours(args)
 
 
@@ -616,6 +623,60 @@ def main_unet(args):
             "flops_per_apply": 2 * macs, "tensor_core_flops_per_apply": 2 * tc_macs,
             "achieved_tflops": 2 * macs / (ms * 1e-3) / 1e12,
             "gpu_launches": (net.launch_count() - l0)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main_spmv(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    from paper_2504_03697_gb300 import build as B
+    B.build()
+    from paper_2504_03697_gb300 import cfd
+    from paper_2504_03697_gb300.synthetic import uniform_field
+
+    n = args.spmv
+    cells = n ** 3
+    cav = cfd.Cavity(cfd.make_params(n, n, n), device=device)
+    M = cfd.CsrMatrix(n, n, n, device=device)
+    x = torch.tensor(uniform_field((n, n, n), seed=1), device=device)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for _ in range(args.steps):
+            fn()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / args.steps
+
+    ms_free = timed(lambda: cav.apply_poisson(x, y))
+    ms_csr = timed(lambda: M.spmv(x, y))
+    bytes_free = 16 * cells                                   # read x, write y (halo re-reads from cache)
+    bytes_csr = 16 * cells + 4 * (cells + 1) + 12 * M.nnz     # + row_ptr, col, val
+    hbm = 6800.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm = json.load(f).get("hbm_gbs", hbm)
+    except (OSError, ValueError):
+        pass
+    line = {"metric": "pressure operator application time", "value": ms_free, "unit": "ms", "higher_is_better": False,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"y = A x for the Neumann pressure matrix on {n}^3 cells (x uniform in [-1, 1])"},
+            "matrix_free": {"ms": ms_free, "algorithmic_bytes": bytes_free,
+                            "gbs": bytes_free / ms_free / 1e6, "frac_of_measured_hbm": bytes_free / ms_free / 1e6 / hbm},
+            "csr": {"ms": ms_csr, "nnz": M.nnz, "algorithmic_bytes": bytes_csr, "gbs": bytes_csr / ms_csr / 1e6,
+                    "frac_of_measured_hbm": bytes_csr / ms_csr / 1e6 / hbm},
+            "speedup_matrix_free": ms_csr / ms_free}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0

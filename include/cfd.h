@@ -344,6 +344,20 @@ int cfd_snapshot_write_csv(cfd_handle *h, const char *path, int nthreads);
  * the handle's stream.  Used to harvest pressure systems from a run. */
 int cfd_pressure_rhs(cfd_handle *h, double *b_dev);
 
+/* Assembled-matrix path (Sec. 3.1: the paper assembles the pressure matrix
+ * in CSR and multiplies with it), beside the matrix-free operator of
+ * cfd_apply_poisson for comparison.  One caller-owned device buffer holds
+ * row_ptr (int32, n + 1), col (int32, nnz, ascending per row) and val
+ * (float64, nnz), each piece 16-byte aligned; nnz = 7 n - 2 (nx ny + ny nz
+ * + nz nx).  cfd_csr_bytes sizes it (and returns nnz, nullable); the grid
+ * must have 7 n < 2^31.  cfd_csr_assemble fills it (asynchronous);
+ * cfd_csr_spmv computes y = A x, one row per thread in stored order
+ * (asynchronous).  Errors through cfd_last_error(NULL). */
+int cfd_csr_bytes(int32_t nx, int32_t ny, int32_t nz, size_t *bytes, int64_t *nnz);
+int cfd_csr_assemble(int32_t nx, int32_t ny, int32_t nz, void *dev_buf, cfd_stream_t stream);
+int cfd_csr_spmv(int32_t nx, int32_t ny, int32_t nz, const void *dev_buf, const double *x_dev, double *y_dev,
+                 cfd_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Learned preconditioner (flexible PCG with a U-Net, Sec. 5 "other
  * preconditioners"; the paper itself uses DIC / Jacobi, Sec. 3.1).

@@ -113,6 +113,9 @@ def load_library(path: Optional[str] = None):
         "cfd_autotune_solver": (ctypes.c_int, [vp, ctypes.c_int32, P(cfd_tune_report)]),
         "cfd_set_cg_variant": (ctypes.c_int, [vp, ctypes.c_int]),
         "cfd_snapshot": (ctypes.c_int, [vp]),
+        "cfd_csr_bytes": (ctypes.c_int, [ctypes.c_int32] * 3 + [P(ctypes.c_size_t), P(ctypes.c_int64)]),
+        "cfd_csr_assemble": (ctypes.c_int, [ctypes.c_int32] * 3 + [vp, vp]),
+        "cfd_csr_spmv": (ctypes.c_int, [ctypes.c_int32] * 3 + [vp, vp, vp, vp]),
         "cfd_snapshot_write_csv": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_int]),
         "cfd_conv3d_bf16": (ctypes.c_int, [ctypes.c_int] * 3 + [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, vp,
                                                                 ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]),
@@ -534,3 +537,41 @@ class UNet:
 
     def launch_count(self) -> int:
         return int(self.lib.cfd_unet_launch_count(self.u))
+
+
+class CsrMatrix:
+    """The assembled pressure matrix on the device (cfd_csr_*), for comparison
+    with the matrix-free operator."""
+
+    def __init__(self, nx, ny, nz, stream=None, device=None):
+        self.lib = load_library()
+        self.shape = (int(nx), int(ny), int(nz))
+        nb = ctypes.c_size_t(0)
+        nnz = ctypes.c_int64(0)
+        rc = self.lib.cfd_csr_bytes(*self.shape, ctypes.byref(nb), ctypes.byref(nnz))
+        if rc != CFD_OK:
+            raise CfdError(rc, self.lib.cfd_last_error(None).decode())
+        self.nnz = int(nnz.value)
+        self.bytes = int(nb.value)
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.buf = torch.empty(self.bytes, dtype=torch.uint8, device=dev)
+        self.stream = stream
+        rc = self.lib.cfd_csr_assemble(*self.shape, ctypes.c_void_p(self.buf.data_ptr()), ctypes.c_void_p(_stream_ptr(stream)))
+        if rc != CFD_OK:
+            raise CfdError(rc, self.lib.cfd_last_error(None).decode())
+
+    def arrays(self):
+        """Host copies (row_ptr, col, val) for checks."""
+        n = self.shape[0] * self.shape[1] * self.shape[2]
+        raw = self.buf.cpu()
+        a16 = lambda x: (x + 15) // 16 * 16  # noqa: E731
+        o1 = a16((n + 1) * 4)
+        o2 = o1 + a16(self.nnz * 4)
+        return (raw[:(n + 1) * 4].view(torch.int32), raw[o1:o1 + self.nnz * 4].view(torch.int32),
+                raw[o2:o2 + self.nnz * 8].view(torch.float64))
+
+    def spmv(self, x: torch.Tensor, y: torch.Tensor):
+        rc = self.lib.cfd_csr_spmv(*self.shape, ctypes.c_void_p(self.buf.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                   ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(_stream_ptr(self.stream)))
+        if rc != CFD_OK:
+            raise CfdError(rc, self.lib.cfd_last_error(None).decode())

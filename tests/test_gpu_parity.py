@@ -371,3 +371,27 @@ def test_cavity_midpoint_backtrace_steps(cfd):
     cav, ocav, stats, st, errs = _run_pair(cfd, (16, 16, 16), 8, 2, dt=0.01, nu=0.01, lid_u=1.0, advect_order=2)
     for name, e in errs.items():
         assert e < FP64_TOL, (name, e)
+
+
+# ----------------------------------------------------------------------------
+# assembled CSR path (the paper's matrix format) vs the matrix-free operator
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(1, 1, 7), (5, 4, 3), (17, 9, 13), (64, 64, 64)])
+def test_csr_matrix_and_spmv(cfd, shape):
+    nx, ny, nz = shape
+    M = cfd.CsrMatrix(nx, ny, nz)
+    ref = poisson_csr(nx, ny, nz)
+    rp, col, val = M.arrays()
+    assert M.nnz == ref.nnz
+    np.testing.assert_array_equal(rp.numpy(), ref.indptr)      # integer structure: exact
+    np.testing.assert_array_equal(col.numpy(), ref.indices)
+    np.testing.assert_array_equal(val.numpy(), ref.data)
+    cav, _ = make(cfd, shape)
+    x = torch.tensor(uniform_field((nz, ny, nx), seed=9), device="cuda")
+    y1 = torch.empty_like(x)
+    y2 = torch.empty_like(x)
+    M.spmv(x, y1)
+    cav.apply_poisson(x, y2)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(y1.cpu().numpy().ravel(), ref @ x.cpu().numpy().ravel(), rtol=0, atol=1e-14 * 6)
+    np.testing.assert_allclose(y1.cpu().numpy(), y2.cpu().numpy(), rtol=0, atol=1e-14 * 6)
