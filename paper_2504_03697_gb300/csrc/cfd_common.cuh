@@ -197,10 +197,28 @@ __device__ bool grid_allreduce(double (&v)[NV], double (&out)[NV], SolveCtrl* ct
     }
     __syncthreads();
     if (!s_ok) return false;
-    for (unsigned int b = threadIdx.x; b < G; b += blockDim.x) {
+    // warp 0 sums the block partials (each lane a fixed strided subset, then
+    // a fixed shuffle tree) and broadcasts: one block barrier instead of the
+    // two of a block-wide reduction
+    if (threadIdx.x < 32) {
+      for (unsigned int b = threadIdx.x; b < G; b += 32) {
 #pragma unroll
-      for (int a = 0; a < NV; ++a) acc[a] += __ldcg(&buf[size_t(b) * kMaxPartials + a]);
+        for (int a = 0; a < NV; ++a) acc[a] += __ldcg(&buf[size_t(b) * kMaxPartials + a]);
+      }
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc[a] += __shfl_down_sync(0xffffffffu, acc[a], off);
+      }
+      if (threadIdx.x == 0) {
+#pragma unroll
+        for (int a = 0; a < NV; ++a) s_bcast[a] = acc[a];
+      }
     }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < NV; ++a) out[a] = s_bcast[a];
+    return true;
   } else {
     const unsigned int ngroups = (G + kGroupSize - 1) / kGroupSize;
     const unsigned int g = unsigned(vb.bid) / kGroupSize;

@@ -16,8 +16,8 @@
 //   * velocity diffusion, own axis: the wall faces are stored (always 0) and
 //     their rows are fixed (output 0).
 // Velocity rows return x_c + c (6 x_c - sum) (backward Euler, c = nu dt/h^2).
-// This keeps the FP64 work at 5 adds + 1-2 FMAs per row, which matters on
-// GB300, whose FP64 pipe is far slower than its HBM.
+// This keeps the FP64 work at 5 adds + 1 FMA per row (velocity: + 1 FMA),
+// which matters on GB300, whose FP64 pipe is far slower than its HBM.
 //
 // CG layout.  One persistent, cooperatively launched kernel runs the whole
 // solve with two grid-wide all-reduces per iteration:
@@ -64,7 +64,7 @@ __device__ __forceinline__ T stencil_row(int kind, T c, int i, int j, int k, int
     if (j == my - 1) yp = xc;
     if (k == 0) zm = xc;
     if (k == mz - 1) zp = xc;
-    return T(6) * xc - (((((xm + xp) + ym) + yp) + zm) + zp);
+    return fma(T(6), xc, -(((((xm + xp) + ym) + yp) + zm) + zp));
   }
   const int comp = kind - 1;
   const bool wall_row = (comp == 0) ? (i == 0 || i == mx - 1)
@@ -83,8 +83,8 @@ __device__ __forceinline__ T stencil_row(int kind, T c, int i, int j, int k, int
     if (k == 0) zm = g;
     if (k == mz - 1) zp = g;
   }
-  const T lap = T(6) * xc - (((((xm + xp) + ym) + yp) + zm) + zp);
-  return xc + c * lap;
+  const T lap = fma(T(6), xc, -(((((xm + xp) + ym) + yp) + zm) + zp));
+  return fma(c, lap, xc);
 }
 
 // Number of in-box neighbours of a pressure cell (the diagonal of A).
@@ -978,7 +978,7 @@ __device__ bool dir_tma_f32(const IrArgs& a, const CUtensorMap* mp, float beta, 
         if (j == my - 1) yp = pc;
         if (k == 0) zm = pc;
         if (k == mz - 1) zp = pc;
-        const float y = 6.f * pc - (((((xm + xp) + ym) + yp) + zm) + zp);
+        const float y = fmaf(6.f, pc, -(((((xm + xp) + ym) + yp) + zm) + zp));
         const size_t e = idx3(i, j, k, mx, my);
         pnew[e] = pc;
         q[e] = y;
