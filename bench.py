@@ -82,7 +82,8 @@ def parse_args(argv=None):
                     help="time the learned preconditioner's U-Net application on an N^3 grid (N % 4 == 0) "
                          "instead of the cavity")
     ap.add_argument("--unet-weights", default="", help="FP32 parameter file for --unet (default: seeded init)")
-    ap.add_argument("--unet-pipeline", action="store_true", help="two-stage pipelined convolutions (comparison)")
+    ap.add_argument("--unet-conv-mode", choices=["registers", "bulk", "two_stage"], default="bulk",
+                    help="staging of the tiled convolutions (comparison)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--max-seconds", type=float, default=150.0, help=argparse.SUPPRESS)
     return ap.parse_args(argv)
@@ -592,7 +593,7 @@ def main_unet(args):
 
     n = args.unet
     net = cfd.UNet(n, n, n, seed=0)
-    net.set_pipeline(args.unet_pipeline)
+    net.set_conv_mode(args.unet_conv_mode)
     if args.unet_weights:
         net.set_params(torch.from_numpy(np.fromfile(args.unet_weights, dtype="<f4")))
     V = n ** 3
@@ -619,7 +620,7 @@ def main_unet(args):
             "data": "synthetic",
             "config": {"workload": f"3-level linear U-Net (16/32/64 channels) applied to an N(0,1) field on {n}^3 "
                                    f"cells, {'trained weights' if args.unet_weights else 'seeded init'}",
-                       "convolution": "two-stage pipeline" if args.unet_pipeline else "one stage"},
+                       "convolution": args.unet_conv_mode},
             "flops_per_apply": 2 * macs, "tensor_core_flops_per_apply": 2 * tc_macs,
             "achieved_tflops": 2 * macs / (ms * 1e-3) / 1e12,
             "gpu_launches": (net.launch_count() - l0)}

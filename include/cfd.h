@@ -425,12 +425,16 @@ int cfd_unet_train_step(cfd_unet *u, const double *r_dev, const double *e_dev, i
 enum { CFD_UNET_LOSS_MSE = 0, CFD_UNET_LOSS_ANORM = 1, CFD_UNET_LOSS_COS = 2 };
 int cfd_unet_set_loss(cfd_unet *u, int kind);
 
-/* on = 1: the 3x3x3 convolutions stream channel blocks through a two-stage
- * shared-memory pipeline (weights by bulk copy); on = 0 (default): one stage,
- * weights copied through registers, two CTAs per SM (measured faster: the
- * pipeline's shared memory halves the tile and the occupancy).  Both issue
- * the same MMAs in the same order, so results are bitwise equal. */
-int cfd_unet_set_pipeline(cfd_unet *u, int on);
+/* How the tiled 3x3x3 convolutions stage each 16-channel block (all modes
+ * issue the same MMAs in the same order, so results are bitwise equal):
+ *   REGISTERS  one stage; all threads copy the weights through registers
+ *   BULK       one stage; one thread issues the TMA input copies and one bulk
+ *              copy of the weights (kept in shared-memory order), then the
+ *              MMAs (default)
+ *   TWO_STAGE  as BULK with two stages: block cb + 1 is copied while the
+ *              MMAs of block cb run (halves the tile and the occupancy) */
+enum { CFD_UNET_CONV_REGISTERS = 0, CFD_UNET_CONV_BULK = 1, CFD_UNET_CONV_TWO_STAGE = 2 };
+int cfd_unet_set_conv_mode(cfd_unet *u, int mode);
 
 /* Tensor read-back for checks (synchronous).  which in 0..25: the BF16
  * tensors (octet planes) xin, a0, s0, p0, a1, s1, p1, a2, s2, u1, d1, u0, d0

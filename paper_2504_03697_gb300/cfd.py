@@ -129,7 +129,7 @@ def load_library(path: Optional[str] = None):
         "cfd_unet_train_step": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_float, P(ctypes.c_float)]),
         "cfd_unet_read_tensor": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int64]),
         "cfd_unet_set_loss": (ctypes.c_int, [vp, ctypes.c_int]),
-        "cfd_unet_set_pipeline": (ctypes.c_int, [vp, ctypes.c_int]),
+        "cfd_unet_set_conv_mode": (ctypes.c_int, [vp, ctypes.c_int]),
         "cfd_unet_fpcg_solve": (ctypes.c_int, [vp, vp, vp, ctypes.c_double, ctypes.c_int32, P(cfd_solve_stats)]),
         "cfd_unet_launch_count": (ctypes.c_int64, [vp]),
         "cfd_unet_last_error": (ctypes.c_char_p, []),
@@ -503,9 +503,9 @@ class UNet:
         (one minus the energy-norm cosine of U(s r) and s e)."""
         self._check(self.lib.cfd_unet_set_loss(self.u, {"mse": 0, "anorm": 1, "cos": 2}[kind]))
 
-    def set_pipeline(self, on=True):
-        """Two-stage pipelined tiled convolutions, or one stage (the default)."""
-        self._check(self.lib.cfd_unet_set_pipeline(self.u, 1 if on else 0))
+    def set_conv_mode(self, mode: str):
+        """'registers', 'bulk' (default) or 'two_stage' (cfd_unet_set_conv_mode)."""
+        self._check(self.lib.cfd_unet_set_conv_mode(self.u, {"registers": 0, "bulk": 1, "two_stage": 2}[mode]))
 
     def read_tensor(self, which) -> torch.Tensor:
         """Host copy of a model tensor: a name from UNET_TENSORS (BF16,

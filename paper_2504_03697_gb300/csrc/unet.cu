@@ -415,10 +415,10 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsign
                : "memory");
 }
 
-template <int NOUT>
+template <int NOUT, int STAGES>
 __global__ void __launch_bounds__(kConvThreads) conv3d_tile_pipe_kernel(const __grid_constant__ ConvTileArgs a) {
   extern __shared__ __align__(1024) unsigned char dsm[];
-  __shared__ __align__(8) uint64_t bar_full[2], bar_mma[2];
+  __shared__ __align__(8) uint64_t bar_full[STAGES], bar_mma[STAGES];
   __shared__ uint32_t s_tmem;
   __shared__ int s_fail;
   __shared__ int s_start[kTileMaxMB];
@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(kConvThreads) conv3d_tile_pipe_kernel(const __
   const unsigned box_bytes = unsigned(a.bx) * a.by * a.bz * 16;
 
   if (t == 0) {
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < STAGES; ++q) {
       tc::mbar_init(&bar_full[q], 1);
       tc::mbar_init(&bar_mma[q], 1);
     }
@@ -457,36 +457,40 @@ __global__ void __launch_bounds__(kConvThreads) conv3d_tile_pipe_kernel(const __
     int st[kTileMaxMB];
 #pragma unroll
     for (int j = 0; j < kTileMaxMB; ++j) st[j] = s_start[j];
+    // stage of channel block q: q % STAGES; its use count: q / STAGES
     auto issue = [&](int cb) {
-      unsigned char* base = dsm + size_t(cb & 1) * stage_bytes;
+      const int sg = cb % STAGES;
+      unsigned char* base = dsm + size_t(sg) * stage_bytes;
       const void* map = cb < cb0 ? static_cast<const void*>(&a.map0) : static_cast<const void*>(&a.map1);
       const int oct = 2 * (cb < cb0 ? cb : cb - cb0);
-      tc::mbar_expect_tx(&bar_full[cb & 1], 2 * box_bytes + kBBytes);
-      tc::tma_load_5d(base, map, 0, x0 - 1, y0 - 1, z0 - 1, oct, &bar_full[cb & 1]);
-      tc::tma_load_5d(base + a.plane, map, 0, x0 - 1, y0 - 1, z0 - 1, oct + 1, &bar_full[cb & 1]);
-      bulk_copy_g2s(base + 2 * size_t(a.plane), a.w_cm + size_t(cb) * (kBBytes / 2), kBBytes, &bar_full[cb & 1]);
+      tc::mbar_expect_tx(&bar_full[sg], 2 * box_bytes + kBBytes);
+      tc::tma_load_5d(base, map, 0, x0 - 1, y0 - 1, z0 - 1, oct, &bar_full[sg]);
+      tc::tma_load_5d(base + a.plane, map, 0, x0 - 1, y0 - 1, z0 - 1, oct + 1, &bar_full[sg]);
+      bulk_copy_g2s(base + 2 * size_t(a.plane), a.w_cm + size_t(cb) * (kBBytes / 2), kBBytes, &bar_full[sg]);
     };
     int issued = 0, consumed = 0;
     bool fail = false;
     issue(0);
     issued = 1;
     for (int cb = 0; cb < ncb && !fail; ++cb) {
-      if (cb + 1 < ncb) {
-        // the stage of cb + 1 was last read by the MMAs of cb - 1
-        if (cb >= 1 && !tc::mbar_wait(&bar_mma[(cb + 1) & 1], unsigned(((cb - 1) >> 1) & 1), kConvWaitNs)) {
+      if (STAGES > 1 && cb + 1 < ncb) {
+        // the stage of cb + 1 was last read by the MMAs of cb + 1 - STAGES
+        const int prev = cb + 1 - STAGES;
+        if (prev >= 0 &&
+            !tc::mbar_wait(&bar_mma[prev % STAGES], unsigned((prev / STAGES) & 1), kConvWaitNs)) {
           fail = true;
           break;
         }
         issue(cb + 1);
         issued = cb + 2;
       }
-      if (!tc::mbar_wait(&bar_full[cb & 1], unsigned((cb >> 1) & 1), kConvWaitNs)) {
+      if (!tc::mbar_wait(&bar_full[cb % STAGES], unsigned((cb / STAGES) & 1), kConvWaitNs)) {
         fail = true;
         break;
       }
       consumed = cb + 1;
       tc::fence_after_sync();
-      unsigned char* base = dsm + size_t(cb & 1) * stage_bytes;
+      unsigned char* base = dsm + size_t(cb % STAGES) * stage_bytes;
       const uint64_t adesc0 = tc::smem_desc(tc::smem_addr(base), uint32_t(a.plane), 128);
       const uint64_t bdesc0 = tc::smem_desc(tc::smem_addr(base + 2 * size_t(a.plane)), 128, 256);
       int tap = 0;
@@ -500,16 +504,27 @@ __global__ void __launch_bounds__(kConvThreads) conv3d_tile_pipe_kernel(const __
             for (int j = 0; j < kTileMaxMB; ++j)
               if (j < a.mb) tc::mma_bf16(tmem + uint32_t(j * NOUT), adesc0 + uint64_t(st[j] + off), bdesc, idesc, acc);
           }
-      tc::mma_commit(&bar_mma[cb & 1]);
+      tc::mma_commit(&bar_mma[cb % STAGES]);
+      if (STAGES == 1 && cb + 1 < ncb) {
+        // one stage: the next block's copies wait for these MMAs
+        if (!tc::mbar_wait(&bar_mma[0], unsigned(cb & 1), kConvWaitNs)) {
+          fail = true;
+          break;
+        }
+        issue(cb + 1);
+        issued = cb + 2;
+      }
     }
     if (!fail && ncb > 0) {
-      if (!tc::mbar_wait(&bar_mma[(ncb - 1) & 1], unsigned(((ncb - 1) >> 1) & 1), kConvWaitNs)) fail = true;
+      if (!tc::mbar_wait(&bar_mma[(ncb - 1) % STAGES], unsigned(((ncb - 1) / STAGES) & 1), kConvWaitNs)) fail = true;
     }
     if (fail) {
       s_fail = 1;
       // let copies still in flight land before the CTA's shared memory goes away
-      for (int cb = consumed; cb < issued; ++cb) tc::mbar_wait(&bar_full[cb & 1], unsigned((cb >> 1) & 1), kConvWaitNs);
-      if (consumed > 0) tc::mbar_wait(&bar_mma[(consumed - 1) & 1], unsigned(((consumed - 1) >> 1) & 1), kConvWaitNs);
+      for (int cb = consumed; cb < issued; ++cb)
+        tc::mbar_wait(&bar_full[cb % STAGES], unsigned((cb / STAGES) & 1), kConvWaitNs);
+      if (consumed > 0)
+        tc::mbar_wait(&bar_mma[(consumed - 1) % STAGES], unsigned(((consumed - 1) / STAGES) & 1), kConvWaitNs);
     }
   }
   __syncthreads();
@@ -642,18 +657,19 @@ cudaError_t launch_tile(const ConvArgs& a, cudaStream_t s, bool& taken) {
   ConvTileArgs t{};
   t.nx = a.nx; t.ny = a.ny; t.nz = a.nz;
   t.c0 = a.c0; t.c1 = a.c1;
-  const bool pipe = a.w_cm != nullptr && !(reinterpret_cast<uintptr_t>(a.w_cm) & 15);
-  if (!pick_tile(t, NOUT, pipe ? 2 : 1)) return cudaSuccess;
+  const bool bulk = a.w_cm != nullptr && !(reinterpret_cast<uintptr_t>(a.w_cm) & 15);
+  const int stages = bulk ? (a.stages == 2 ? 2 : 1) : 1;
+  if (!pick_tile(t, NOUT, stages)) return cudaSuccess;
   if (!encode_oct_map(&t.map0, a.src0, a.c0, a.nx, a.ny, a.nz, t.bx, t.by, t.bz)) return cudaSuccess;
   if (a.c1 > 0 && !encode_oct_map(&t.map1, a.src1, a.c1, a.nx, a.ny, a.nz, t.bx, t.by, t.bz)) return cudaSuccess;
   t.w = a.w;
-  t.w_cm = pipe ? a.w_cm : nullptr;
+  t.w_cm = bulk ? a.w_cm : nullptr;
   t.cin_pad = (a.c0 + a.c1 + 15) / 16 * 16;
   t.bias = a.bias;
   t.cout = a.cout;
   t.dst0 = a.dst0; t.dst1 = a.dst1; t.split = a.split;
   t.err = a.err;
-  const size_t smem = size_t(pipe ? 2 : 1) * (2 * size_t(t.plane) + size_t(27) * NOUT * 32);
+  const size_t smem = size_t(stages) * (2 * size_t(t.plane) + size_t(27) * NOUT * 32);
   // TMEM: at most 512 / cols CTAs may share an SM; pad the shared-memory
   // request so that no more than that many fit
   const int need = t.mb * NOUT;
@@ -667,13 +683,17 @@ cudaError_t launch_tile(const ConvArgs& a, cudaStream_t s, bool& taken) {
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(conv3d_tile_kernel<NOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemMax);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(conv3d_tile_pipe_kernel<NOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemMax);
+      e = cudaFuncSetAttribute(conv3d_tile_pipe_kernel<NOUT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemMax);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(conv3d_tile_pipe_kernel<NOUT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemMax);
     if (e != cudaSuccess) return e;
     configured = 1;
   }
   const unsigned grid = unsigned(t.tiles_x) * unsigned(t.tiles_y) * unsigned((t.nz + t.tz - 1) / t.tz);
-  if (pipe)
-    conv3d_tile_pipe_kernel<NOUT><<<grid, kConvThreads, req, s>>>(t);
+  if (bulk && stages == 2)
+    conv3d_tile_pipe_kernel<NOUT, 2><<<grid, kConvThreads, req, s>>>(t);
+  else if (bulk)
+    conv3d_tile_pipe_kernel<NOUT, 1><<<grid, kConvThreads, req, s>>>(t);
   else
     conv3d_tile_kernel<NOUT><<<grid, kConvThreads, req, s>>>(t);
   taken = true;

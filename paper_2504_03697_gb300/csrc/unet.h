@@ -39,6 +39,7 @@ struct ConvArgs {
   float* dst_f32;                // if non-null: FP32 [V][cout] output instead of dst0/dst1
   int* err;                      // set to 1 on a device-side wait timeout
   int no_tile;                   // 1: never take the TMA-tiled kernel
+  int stages;                    // with w_cm: 1 (default) or 2 shared-memory stages
 };
 
 // Launch the convolution: the TMA-tiled kernel for 3x3x3 layers whose

@@ -796,7 +796,7 @@ struct cfd_unet {
   __nv_bfloat16* tens[26];
   size_t tens_count[26];
   int loss_kind;  // CFD_UNET_LOSS_*
-  int no_pipe;    // 1 (default): one-stage tiled convolutions; 0: the two-stage pipeline
+  int conv_mode;  // CFD_UNET_CONV_*: how the tiled convolutions stage weights and inputs
   int adam_t;
   int64_t launches;
 };
@@ -951,7 +951,8 @@ int conv(cfd_unet* u, int layer, const __nv_bfloat16* src0, const __nv_bfloat16*
   a.src0 = src0; a.c0 = L.c0; a.src1 = src1; a.c1 = L.c1;
   a.ks = L.ks; a.packed = L.packed ? 1 : 0;
   a.w = u->wf[layer];
-  a.w_cm = u->no_pipe ? nullptr : u->wfc[layer];
+  a.w_cm = u->conv_mode == CFD_UNET_CONV_REGISTERS ? nullptr : u->wfc[layer];
+  a.stages = u->conv_mode == CFD_UNET_CONV_TWO_STAGE ? 2 : 1;
   a.bias = u->w + u->boff[layer];
   a.cout = L.cout;
   a.dst0 = dst0; a.dst1 = dst1; a.split = split; a.dst_f32 = dst_f32;
@@ -969,7 +970,8 @@ int conv_dgrad(cfd_unet* u, int layer, int slice, const __nv_bfloat16* gout, int
   a.src0 = gout; a.c0 = L.cout; a.src1 = nullptr; a.c1 = 0;
   a.ks = L.ks; a.packed = 0;
   a.w = u->wd[layer][slice];
-  a.w_cm = u->no_pipe ? nullptr : u->wdc[layer][slice];
+  a.w_cm = u->conv_mode == CFD_UNET_CONV_REGISTERS ? nullptr : u->wdc[layer][slice];
+  a.stages = u->conv_mode == CFD_UNET_CONV_TWO_STAGE ? 2 : 1;
   a.bias = nullptr;
   a.cout = o_count;
   a.dst0 = dst0; a.dst1 = dst1; a.split = split; a.dst_f32 = nullptr;
@@ -1180,7 +1182,7 @@ int cfd_unet_create(int nx, int ny, int nz, void* dev_ws, size_t bytes, cfd_stre
   u->ws = static_cast<char*>(dev_ws);
   u->bytes = bytes;
   u->nparams = param_count();
-  u->no_pipe = 1;  // measured faster: two CTAs per SM overlap each other's copies and MMAs
+  u->conv_mode = CFD_UNET_CONV_BULK;
   carve(u, nx, ny, nz, u->ws);
   std::vector<float> p(size_t(u->nparams));
   init_params(p, seed);
@@ -1285,9 +1287,10 @@ int cfd_unet_train_step(cfd_unet* u, const double* r_dev, const double* e_dev, i
   return rc;
 }
 
-int cfd_unet_set_pipeline(cfd_unet* u, int on) {
-  if (!u) return uerr(CFD_ERR_INVALID_ARG, "unet: NULL handle");
-  u->no_pipe = on ? 0 : 1;
+int cfd_unet_set_conv_mode(cfd_unet* u, int mode) {
+  if (!u || mode < CFD_UNET_CONV_REGISTERS || mode > CFD_UNET_CONV_TWO_STAGE)
+    return uerr(CFD_ERR_INVALID_ARG, "unet: NULL handle or unknown convolution mode");
+  u->conv_mode = mode;
   return CFD_OK;
 }
 
