@@ -196,14 +196,14 @@ def pressure_rhs(cav: Cavity, u, v, w):
     return b - b.mean()
 
 
-def solve_pressure(cav: Cavity, b, precond="none", fixed_iters=None):
+def solve_pressure(cav: Cavity, b, precond="none", fixed_iters=None, x0=None):
     A = poisson_csr(cav.nx, cav.ny, cav.nz)
     if precond == "dic":
         pc = dic_precond(A)[0]
     else:
         pc = identity_precond if precond == "none" else jacobi_precond(A)
-    x, st = pcg(A, b.ravel(), x0=None, rtol=cav.rtol, max_iters=cav.iter_cap,
-                precond=pc, fixed_iters=fixed_iters)
+    x, st = pcg(A, b.ravel(), x0=None if x0 is None else np.asarray(x0).ravel(), rtol=cav.rtol,
+                max_iters=cav.iter_cap, precond=pc, fixed_iters=fixed_iters)
     return x.reshape(cav.cell_shape), st
 
 
@@ -239,12 +239,13 @@ def step(cav: Cavity, state, fixed_iters=None, precond="none"):
     iteration counts of the solves instead of the stopping test.
     """
     fx = fixed_iters or {}
-    u, v, w, _ = state
+    u, v, w, p_prev = state
     u, v, w = apply_forces(cav, u, v, w)
     u, v, w = advect(cav, u, v, w)
     (u, v, w), dstats = diffuse(cav, (u, v, w), (fx.get("u"), fx.get("v"), fx.get("w")))
     b = pressure_rhs(cav, u, v, w)
-    x, pst = solve_pressure(cav, b, precond=precond, fixed_iters=fx.get("p"))
+    x, pst = solve_pressure(cav, b, precond=precond, fixed_iters=fx.get("p"),
+                            x0=p_prev if cav.warm_start else None)
     u, v, w = correct(cav, u, v, w, x)
     p = gauge(x)
     stats = {"p": pst, "u": dstats[0], "v": dstats[1], "w": dstats[2], "b": b, "x": x}

@@ -48,6 +48,7 @@ class Cavity:
     rtol: float = 1e-8
     max_iters: int = 0           # 0 -> 20 * max(nx, ny, nz)
     advect_order: int = 1        # backtrace: 1 explicit Euler, 2 explicit midpoint (RK2)
+    warm_start: bool = False     # pressure solve starts from the previous step's p (else 0)
 
     @property
     def h(self) -> float:

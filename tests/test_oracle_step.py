@@ -238,3 +238,27 @@ def test_gauge_mean_is_one():
     st = _state(cav)
     st, _ = fs.step(cav, st)
     assert abs(st[3].mean() - 1.0) < 1e-14
+
+
+def test_warm_start_from_the_solution_takes_no_iteration():
+    """A pressure solve started from its own converged solution stops at
+    once; a warm-started run tracks the cold one within the solver tolerance."""
+    cav = Cavity(10, 8, 6, dt=0.01, nu=0.01, lid_u=1.0, rtol=1e-10)
+    st = _state(cav)
+    st, stats = fs.step(cav, st)
+    b = stats["b"]
+    x, s1 = fs.solve_pressure(cav, b)
+    x2, s2 = fs.solve_pressure(cav, b, x0=x)
+    assert s1.iters > 10 and s2.iters == 0 and s2.converged
+    cold = Cavity(10, 8, 6, dt=0.01, nu=0.01, lid_u=1.0, rtol=1e-10)
+    warm = Cavity(10, 8, 6, dt=0.01, nu=0.01, lid_u=1.0, rtol=1e-10, warm_start=True)
+    a, bst = _state(cold), _state(warm)
+    it_c = it_w = 0
+    for _ in range(4):
+        a, sa = fs.step(cold, a)
+        bst, sb = fs.step(warm, bst)
+        it_c += sa["p"].iters
+        it_w += sb["p"].iters
+    assert it_w < it_c
+    for fa, fb in zip(a, bst):
+        assert np.abs(fa - fb).max() <= 1e-7 * max(1.0, np.abs(fa).max())
