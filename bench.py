@@ -36,6 +36,9 @@ WORKLOADS = {
     "cavity64": dict(n=64, nu=1e-3, dt=1e-2, lid_u=1.0, seed=2, amp=1e-3,
                      desc="lid-driven cavity 64^3 cells, FP64, lid 1.0, nu 1e-3, dt 1e-2, "
                           "pressure CG to rtol 1e-8, seeded 1e-3 perturbation"),
+    "cavity384": dict(n=384, nu=1e-3, dt=1e-2, lid_u=1.0, seed=5, amp=1e-3,
+                      desc="lid-driven cavity 384^3 cells, FP64, lid 1.0, nu 1e-3, dt 1e-2, "
+                           "pressure solve to rtol 1e-8, seeded 1e-3 perturbation"),
     "cavity16": dict(n=16, nu=1e-2, dt=1e-2, lid_u=1.0, seed=1, amp=1e-3,
                      desc="lid-driven cavity 16^3 cells, FP64, lid 1.0, nu 1e-2, dt 1e-2, "
                           "pressure CG to rtol 1e-8, seeded 1e-3 perturbation"),

@@ -40,7 +40,7 @@ def rel_err(g, o):
 
 def make(cfd, n, **kw):
     nx, ny, nz = n if isinstance(n, tuple) else (n, n, n)
-    keep = ("dt", "nu", "lid_u", "g", "rho", "length", "rtol", "max_iters", "advect_order")
+    keep = ("dt", "nu", "lid_u", "g", "rho", "length", "rtol", "max_iters", "advect_order", "warm_start")
     return cfd.Cavity(cfd.make_params(nx, ny, nz, **kw)), OCav(nx, ny, nz, **{k: v for k, v in kw.items() if k in keep})
 
 
@@ -395,3 +395,11 @@ def test_csr_matrix_and_spmv(cfd, shape):
     torch.cuda.synchronize()
     np.testing.assert_allclose(y1.cpu().numpy().ravel(), ref @ x.cpu().numpy().ravel(), rtol=0, atol=1e-14 * 6)
     np.testing.assert_allclose(y1.cpu().numpy(), y2.cpu().numpy(), rtol=0, atol=1e-14 * 6)
+
+
+def test_cavity_warm_started_pressure(cfd):
+    """Pressure solves started from the previous step's p: 16^3, 6 steps."""
+    cav, ocav, stats, st, errs = _run_pair(cfd, (16, 16, 16), 6, 3, dt=0.01, nu=0.01, lid_u=1.0, warm_start=True)
+    for name, e in errs.items():
+        assert e < FP64_TOL, (name, e)
+    assert sum(s["iters"] for s in stats[1:]) < sum(s["iters"] for s in stats[:1]) * (len(stats) - 1)
