@@ -84,3 +84,41 @@ def test_binding_refuses_to_run_without_cuda(lib):
         pytest.skip("a GPU is present")
     with pytest.raises(RuntimeError):
         cfd.Cavity(cfd.make_params(8, 8, 8))
+
+
+def test_more_parameter_validation_and_sizes(lib):
+    from paper_2504_03697_gb300 import cfd
+    base = cfd.cfd_workspace_bytes(cfd.make_params(32, 32, 32))
+    dic = cfd.cfd_workspace_bytes(cfd.make_params(32, 32, 32, solver="dic"))
+    assert dic >= base + 32 ** 3 * 8  # the DIC pivots
+    for kw in (dict(advect_order=3), dict(advect_order=-1)):
+        with pytest.raises(cfd.CfdError):
+            cfd.cfd_workspace_bytes(cfd.make_params(8, 8, 8, **kw))
+    prm = cfd.make_params(8, 8, 8)
+    prm.reserved[3] = 1
+    with pytest.raises(cfd.CfdError):
+        cfd.cfd_workspace_bytes(prm)
+
+
+def test_csr_sizes_match_the_closed_form(lib):
+    for shape in [(1, 1, 1), (1, 1, 7), (4, 3, 2), (64, 64, 64)]:
+        nb = ctypes.c_size_t(0)
+        nnz = ctypes.c_int64(0)
+        assert lib.cfd_csr_bytes(*shape, ctypes.byref(nb), ctypes.byref(nnz)) == 0
+        nx, ny, nz = shape
+        n = nx * ny * nz
+        assert nnz.value == 7 * n - 2 * (nx * ny + ny * nz + nz * nx)
+        a16 = lambda x: (x + 15) // 16 * 16  # noqa: E731
+        assert nb.value == a16((n + 1) * 4) + a16(nnz.value * 4) + nnz.value * 8
+    assert lib.cfd_csr_bytes(0, 4, 4, ctypes.byref(nb), None) != 0
+    assert lib.cfd_csr_bytes(1024, 1024, 1024, ctypes.byref(nb), None) != 0  # 7 n >= 2^31
+
+
+def test_unet_workspace_needs_multiples_of_four(lib):
+    nb = ctypes.c_size_t(0)
+    assert lib.cfd_unet_workspace_bytes(16, 12, 8, ctypes.byref(nb)) == 0
+    small = nb.value
+    assert lib.cfd_unet_workspace_bytes(32, 32, 32, ctypes.byref(nb)) == 0
+    assert nb.value > small > 0
+    for bad in [(15, 12, 8), (16, 2, 8), (0, 4, 4)]:
+        assert lib.cfd_unet_workspace_bytes(*bad, ctypes.byref(nb)) != 0
