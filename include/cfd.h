@@ -78,8 +78,11 @@ enum { CFD_FIELD_U = 0, CFD_FIELD_V = 1, CFD_FIELD_W = 2, CFD_FIELD_P = 3 };
  *           D^-1 (D + L^T), applied by two hyperplane-wavefront triangular
  *           sweeps (exactly the sequential recurrences).  FP64, host-driven
  *           iteration; calls using it synchronise the stream.  Pressure only
- *           (the diffusion solves use CG); not available in batches.      */
-enum { CFD_SOLVER_CG = 0, CFD_SOLVER_JACOBI = 1, CFD_SOLVER_IR = 2, CFD_SOLVER_DIC = 3 };
+ *           (the diffusion solves use CG); not available in batches.
+ *   FPCG    flexible PCG with the learned U-Net preconditioner attached by
+ *           cfd_attach_preconditioner (see cfd_unet_fpcg_solve); pressure
+ *           only, cold start, host-driven; not available in batches.       */
+enum { CFD_SOLVER_CG = 0, CFD_SOLVER_JACOBI = 1, CFD_SOLVER_IR = 2, CFD_SOLVER_DIC = 3, CFD_SOLVER_FPCG = 4 };
 
 /* Substeps for cfd_substep (kernel-level access to one phase of the step). */
 enum {
@@ -401,6 +404,8 @@ void cfd_unet_destroy(cfd_unet *u);
  * head: weights [taps][cout][cin] (tap = kx + 3 ky + 9 kz), then bias
  * [cout]. */
 int64_t cfd_unet_param_count(const cfd_unet *u);
+/* The network's grid (as given to cfd_unet_create). */
+int cfd_unet_grid(const cfd_unet *u, int *nx, int *ny, int *nz);
 int cfd_unet_get_params(cfd_unet *u, float *host, int64_t n);
 int cfd_unet_set_params(cfd_unet *u, const float *host, int64_t n);
 
@@ -465,6 +470,15 @@ int cfd_unet_read_tensor(cfd_unet *u, int which, void *host, int64_t count);
  * stream; returns the status (CFD_OK, CFD_ERR_NOT_CONVERGED, ...). */
 int cfd_unet_fpcg_solve(cfd_unet *u, const double *b_dev, double *x_dev, double rtol, int32_t max_iters,
                         cfd_solve_stats *stats);
+
+/* Attach the U-Net u (same grid as h; NULL detaches) as the preconditioner
+ * of a cavity created with solver CFD_SOLVER_FPCG: its pressure solves
+ * (cfd_step, cfd_substep, cfd_solve_pressure) then run cfd_unet_fpcg_solve
+ * with the handle's rtol and iteration cap; the step's gauge follows.  The
+ * handle's stream is synchronised before each solve (the network runs on
+ * its own stream).  u must outlive its attachment; a pressure solve without
+ * a network attached returns CFD_ERR_INVALID_ARG. */
+int cfd_attach_preconditioner(cfd_handle *h, cfd_unet *u);
 
 int64_t cfd_unet_launch_count(const cfd_unet *u);
 const char *cfd_unet_last_error(void);

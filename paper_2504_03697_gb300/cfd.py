@@ -28,7 +28,7 @@ CFD_ERR_TIMEOUT = -5
 CFD_ERR_WORKSPACE_TOO_SMALL = -6
 
 FIELD = {"u": 0, "v": 1, "w": 2, "p": 3}
-SOLVER = {"cg": 0, "jacobi": 1, "ir": 2, "dic": 3}
+SOLVER = {"cg": 0, "jacobi": 1, "ir": 2, "dic": 3, "fpcg": 4}
 SUBSTEP = {"forces": 0, "advect": 1, "diffuse": 2, "project": 3}
 PHASES = ["applyForces", "solveAdvection", "diffuse", "divergence", "pcg", "applyPressureCorrection"]
 
@@ -132,6 +132,8 @@ def load_library(path: Optional[str] = None):
         "cfd_unet_set_conv_mode": (ctypes.c_int, [vp, ctypes.c_int]),
         "cfd_unet_fpcg_solve": (ctypes.c_int, [vp, vp, vp, ctypes.c_double, ctypes.c_int32, P(cfd_solve_stats)]),
         "cfd_unet_launch_count": (ctypes.c_int64, [vp]),
+        "cfd_unet_grid": (ctypes.c_int, [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]),
+        "cfd_attach_preconditioner": (ctypes.c_int, [vp, vp]),
         "cfd_unet_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -270,6 +272,11 @@ class Cavity:
 
     def launch_count(self) -> int:
         return int(self.lib.cfd_launch_count(self.h))
+
+    def attach_preconditioner(self, net):
+        """Attach a UNet (same grid) for solver 'fpcg'; None detaches."""
+        self._net = net
+        return self._check(self.lib.cfd_attach_preconditioner(self.h, net.u if net is not None else None))
 
     def snapshot(self):
         """Start an asynchronous host copy of (u, v, w, p) (cfd_snapshot)."""

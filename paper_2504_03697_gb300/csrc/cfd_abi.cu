@@ -107,6 +107,7 @@ struct cfd_handle {
   double *e0, *e1, *e2;
   double* dicd = nullptr;
   bool dic_ready = false;
+  cfd_unet* precond_net = nullptr;  // CFD_SOLVER_FPCG
   float *r32, *d32, *p0_32, *p1_32, *q32;
   double* partials;
   SolveCtrl* ctrl;
@@ -177,7 +178,7 @@ int validate(const cfd_params* p) {
     return set_err(nullptr, CFD_ERR_INVALID_ARG, "length, dt, rho must be > 0 and nu >= 0");
   if (!std::isfinite(p->lid_u) || !std::isfinite(p->g[0]) || !std::isfinite(p->g[1]) || !std::isfinite(p->g[2]))
     return set_err(nullptr, CFD_ERR_INVALID_ARG, "lid_u and g must be finite");
-  if (p->solver < CFD_SOLVER_CG || p->solver > CFD_SOLVER_DIC)
+  if (p->solver < CFD_SOLVER_CG || p->solver > CFD_SOLVER_FPCG)
     return set_err(nullptr, CFD_ERR_INVALID_ARG, "unknown solver %d", p->solver);
   if (!(p->rtol > 0) || p->rtol >= 1) return set_err(nullptr, CFD_ERR_INVALID_ARG, "rtol must be in (0, 1)");
   if (p->max_iters < 0) return set_err(nullptr, CFD_ERR_INVALID_ARG, "max_iters must be >= 0");
@@ -290,6 +291,34 @@ int run_diffusion(cfd_handle* h, int comp, DevSolveStats* st) {
 int run_pressure(cfd_handle* h, double* x, int zero_x0, int gauge, DevSolveStats* st) {
   int rc = cuda_check(h, cudaMemsetAsync(h->ctrl, 0, sizeof(SolveCtrl), h->stream), "memset ctrl");
   if (rc) return rc;
+  if (h->prm.solver == CFD_SOLVER_FPCG) {
+    if (!h->precond_net) return set_err(h, CFD_ERR_INVALID_ARG, "FPCG solver without an attached preconditioner");
+    rc = cuda_check(h, cudaStreamSynchronize(h->stream), "synchronize");
+    if (rc) return rc;
+    // FPCG is cold-started; warm_start does not apply
+    (void)zero_x0;
+    cfd_solve_stats cs{};
+    const int t = phase_begin(h, CFD_PHASE_PCG);
+    const int frc = cfd_unet_fpcg_solve(h->precond_net, h->b, x, h->prm.rtol, iter_cap(h->prm), &cs);
+    phase_end(h, t);
+    if (frc != CFD_OK && frc != CFD_ERR_NOT_CONVERGED && frc != CFD_ERR_BREAKDOWN && frc != CFD_ERR_TIMEOUT)
+      return set_err(h, frc, "FPCG: %s", cfd_unet_last_error());
+    if (gauge) {
+      rc = cuda_check(h, launch_gauge(GridDims{h->prm.nx, h->prm.ny, h->prm.nz}, x, 1.0, h->partials, h->stream,
+                                      &h->launches), "gauge");
+      if (rc) return rc;
+    }
+    DevSolveStats ds{};
+    ds.iters = cs.iters;
+    ds.outer_iters = cs.outer_iters;
+    ds.restarts = cs.restarts;
+    ds.status = cs.status;
+    ds.rel_resid = cs.rel_resid;
+    ds.b_norm = cs.b_norm;
+    rc = cuda_check(h, cudaMemcpyAsync(st, &ds, sizeof(ds), cudaMemcpyHostToDevice, h->stream), "FPCG stats");
+    if (!rc) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "synchronize");
+    return rc;
+  }
   if (h->prm.solver == CFD_SOLVER_DIC) {
     DicArgs a{};
     a.g = GridDims{h->prm.nx, h->prm.ny, h->prm.nz};
@@ -750,6 +779,19 @@ __global__ void tune_rhs_kernel(double* b, size_t n) {
 }
 }  // namespace
 
+int cfd_attach_preconditioner(cfd_handle* h, cfd_unet* u) {
+  if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
+  if (u) {
+    if (h->prm.solver != CFD_SOLVER_FPCG) return set_err(h, CFD_ERR_INVALID_ARG, "the handle's solver is not FPCG");
+    int nx = 0, ny = 0, nz = 0;
+    cfd_unet_grid(u, &nx, &ny, &nz);
+    if (nx != h->prm.nx || ny != h->prm.ny || nz != h->prm.nz)
+      return set_err(h, CFD_ERR_INVALID_ARG, "the network's grid %dx%dx%d differs from the cavity's", nx, ny, nz);
+  }
+  h->precond_net = u;
+  return CFD_OK;
+}
+
 int cfd_set_cg_variant(cfd_handle* h, int variant) {
   if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
   if (variant != CFD_CG_SINGLE_REDUCTION && variant != CFD_CG_TWO_REDUCTIONS)
@@ -1067,7 +1109,8 @@ int cfd_batch_create(int n, const cfd_params* per_cavity, void* dev_ws, size_t b
     return batch_err(nullptr, CFD_ERR_INVALID_ARG, "workspace NULL or not 256-byte aligned");
   if (bytes < need) return batch_err(nullptr, CFD_ERR_WORKSPACE_TOO_SMALL, "batch workspace %zu < %zu", bytes, need);
   const int solver = per_cavity[0].solver;
-  if (solver == CFD_SOLVER_DIC) return batch_err(nullptr, CFD_ERR_INVALID_ARG, "batches do not support the DIC solver");
+  if (solver == CFD_SOLVER_DIC || solver == CFD_SOLVER_FPCG)
+    return batch_err(nullptr, CFD_ERR_INVALID_ARG, "batches do not support the DIC or FPCG solvers");
   for (int i = 1; i < n; ++i)
     if (per_cavity[i].solver != solver) return batch_err(nullptr, CFD_ERR_INVALID_ARG, "all cavities of a batch use one solver");
   const BatchLayout L = batch_layout(n, per_cavity);

@@ -261,6 +261,17 @@ cudaError_t launch_dic_apply(GridDims g, const double* d, const double* r, doubl
   return cudaGetLastError();
 }
 
+// x += target - mean(x) (scratch as for run_dic_pcg)
+cudaError_t launch_gauge(GridDims g, double* x, double target, double* scratch, cudaStream_t s, int64_t* launches) {
+  const size_t n = g.count();
+  Scalars* sc = reinterpret_cast<Scalars*>(scratch + 2 * kVecBlocks);
+  dot_kernel<<<kVecBlocks, kVecThreads, 0, s>>>(x, nullptr, nullptr, n, scratch);
+  scalar_kernel<<<1, kVecThreads, 0, s>>>(kMean, scratch, kVecBlocks, n, sc);
+  shift_kernel<<<grid_for(n), kVecThreads, 0, s>>>(x, n, sc, target);
+  if (launches) *launches += 3;
+  return cudaGetLastError();
+}
+
 // Host-driven DIC-PCG; see dic.h.
 cudaError_t run_dic_pcg(const DicArgs& a, cudaStream_t s, int64_t* launches, DicResult* res) {
   const GridDims g = a.g;

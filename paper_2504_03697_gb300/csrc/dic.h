@@ -42,6 +42,8 @@ size_t dic_scratch_bytes();
 cudaError_t launch_dic_setup(GridDims g, double* d, cudaStream_t s, int64_t* launches);
 cudaError_t launch_dic_apply(GridDims g, const double* d, const double* r, double* t, double* z, cudaStream_t s,
                              int64_t* launches);
+// x += target - mean(x): the gauge of the projection's pressure.
+cudaError_t launch_gauge(GridDims g, double* x, double target, double* scratch, cudaStream_t s, int64_t* launches);
 // Runs the whole solve (synchronises the stream once per iteration).
 cudaError_t run_dic_pcg(const DicArgs& a, cudaStream_t s, int64_t* launches, DicResult* res);
 

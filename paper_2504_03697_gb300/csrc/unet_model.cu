@@ -1204,6 +1204,14 @@ void cfd_unet_destroy(cfd_unet* u) { delete u; }
 
 int64_t cfd_unet_param_count(const cfd_unet* u) { return u ? u->nparams : param_count(); }
 
+int cfd_unet_grid(const cfd_unet* u, int* nx, int* ny, int* nz) {
+  if (!u || !nx || !ny || !nz) return uerr(CFD_ERR_INVALID_ARG, "unet: NULL argument");
+  *nx = u->nx;
+  *ny = u->ny;
+  *nz = u->nz;
+  return CFD_OK;
+}
+
 int cfd_unet_get_params(cfd_unet* u, float* host, int64_t n) {
   if (!u || !host || n != u->nparams) return uerr(CFD_ERR_INVALID_ARG, "unet: bad parameter buffer");
   int rc = uck(u, cudaMemcpyAsync(host, u->w, size_t(n) * 4, cudaMemcpyDeviceToHost, u->stream), "copy params");

@@ -407,3 +407,39 @@ def test_training_lowers_the_loss(cfd):
     losses = [net.train_step(r, e, lr=2e-3) for _ in range(60)]
     print(f"loss {losses[0]:.4g} -> {losses[-1]:.4g}")
     assert losses[-1] < 0.7 * losses[0]
+
+
+def test_cavity_steps_with_the_learned_preconditioner(cfd):
+    """A cavity whose pressure solves run flexible PCG with an attached
+    network (solver 'fpcg'): every solve meets the FP64 true-residual rule
+    and the fields follow the plain-CG run within what two rtol-solutions
+    may differ by (|dp| <= 2 rtol ||b|| / lambda_min per solve)."""
+    from paper_2504_03697_gb300.synthetic import cavity_perturbation
+    n, steps = 16, 3
+    net = cfd.UNet(n, n, n, seed=2)
+    net.set_params(passthrough_params(1.0))
+    runs = []
+    for solver in ("fpcg", "cg"):
+        cav = cfd.Cavity(cfd.make_params(n, n, n, dt=0.01, nu=0.01, lid_u=1.0, solver=solver))
+        if solver == "fpcg":
+            cav.attach_preconditioner(net)
+        for name, f in zip("uvw", cavity_perturbation(n, n, n, seed=4, amp=1e-3)):
+            cav.set_field(name, f)
+        rc, stats = cav.step(steps)
+        assert rc == 0 and all(s["status"] == 0 and s["rel_resid"] <= 1e-8 for s in stats), stats
+        runs.append(({f: cav.read_field(f).numpy() for f in "uvwp"}, stats))
+    (a, sa), (b, sb) = runs
+    assert all(s["outer_iters"] == 0 for s in sa)  # the network's steps were used, no fallback
+    assert sum(s["iters"] for s in sa) < sum(s["iters"] for s in sb)  # the pass-through network helps
+    for f in "uvwp":
+        scale = max(1.0, float(np.abs(b[f]).max()))
+        assert float(np.abs(a[f] - b[f]).max()) <= 1e-5 * scale, f
+
+
+def test_fpcg_cavity_without_a_network_is_an_error(cfd):
+    cav = cfd.Cavity(cfd.make_params(8, 8, 8, solver="fpcg"))
+    with pytest.raises(cfd.CfdError):
+        cav.step(1)
+    net = cfd.UNet(16, 16, 16, seed=1)
+    with pytest.raises(cfd.CfdError):
+        cav.attach_preconditioner(net)  # grid mismatch
