@@ -79,6 +79,8 @@ def parse_args(argv=None):
                     help="FP64 CG form: one grid reduction per iteration (default) or the textbook two")
     ap.add_argument("--spmv", type=int, default=0,
                     help="time the pressure operator on an N^3 grid: matrix-free stencil vs the assembled CSR matrix")
+    ap.add_argument("--blas", type=int, default=0,
+                    help="time the stand-alone building blocks on an N^3 grid: FP32 operator, FP64 / FP32 CG update")
     ap.add_argument("--advect-order", type=int, default=1, choices=[1, 2],
                     help="backtrace of the cavity workload: 1 explicit Euler (default), 2 explicit midpoint")
     ap.add_argument("--unet", type=int, default=0,
@@ -549,6 +551,8 @@ def main(argv=None):
         return main_unet(args)
     if args.spmv > 0:
         return main_spmv(args)
+    if args.blas > 0:
+        return main_blas(args)
     return main_ours(args)
 
 
@@ -681,6 +685,90 @@ def main_spmv(args):
             "csr": {"ms": ms_csr, "nnz": M.nnz, "algorithmic_bytes": bytes_csr, "gbs": bytes_csr / ms_csr / 1e6,
                     "frac_of_measured_hbm": bytes_csr / ms_csr / 1e6 / hbm},
             "speedup_matrix_free": ms_csr / ms_free}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def measured_hbm_gbs(default=6800.0):
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f).get("hbm_gbs", default))
+    except (OSError, ValueError):
+        return default
+
+
+def main_blas(args):
+    """Stand-alone operator and CG update kernels.  When the FP32 operand
+    alone is larger than L2 (129 MB: N >= 320) the launches run back to back
+    between two CUDA events; below that each launch is timed alone after an
+    L2 flush (a 256 MB write), which adds the launch latency (about 6 us) to
+    every sample."""
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    from paper_2504_03697_gb300 import build as B
+    B.build()
+    from paper_2504_03697_gb300 import cfd
+    from paper_2504_03697_gb300.synthetic import uniform_field
+
+    n = args.blas
+    cells = n ** 3
+    kk = cfd.KrylovKernels(device=device)
+    x32 = torch.tensor(uniform_field((n, n, n), seed=1), device=device).float()
+    y32 = torch.empty_like(x32)
+    gen = torch.Generator(device="cpu").manual_seed(5)
+    vec64 = [torch.rand(cells, generator=gen, dtype=torch.float64).to(device) * 2 - 1 for _ in range(4)]
+    vec32 = [v.float() for v in vec64]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    stream = torch.cuda.current_stream()
+
+    back_to_back = 4 * cells > 129e6
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        if back_to_back:
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            for _ in range(args.steps):
+                fn()
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            return ev[0].elapsed_time(ev[1]) / args.steps
+        total = 0.0
+        for _ in range(args.steps):
+            flush.fill_(1)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            fn()
+            ev[1].record(stream)
+            ev[1].synchronize()
+            total += ev[0].elapsed_time(ev[1])
+        return total / args.steps
+
+    hbm = measured_hbm_gbs()
+    res = {}
+    for name, fn, nbytes in (
+            ("apply_poisson_f32", lambda: kk.apply_poisson_f32(x32, y32), 8 * cells),
+            ("cg_update_f64", lambda: kk.cg_update(1e-3, *vec64), 48 * cells),
+            ("cg_update_f32", lambda: kk.cg_update(1e-3, *vec32), 24 * cells)):
+        ms = timed(fn)
+        gbs = nbytes / ms / 1e6
+        res[name] = {"ms": ms, "algorithmic_bytes": nbytes, "gbs": gbs, "frac_of_measured_hbm": gbs / hbm}
+    a = res["apply_poisson_f32"]
+    line = {"metric": "FP32 pressure operator application time", "value": a["ms"], "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"stand-alone Krylov kernels on {n}^3 cells (uniform [-1, 1] inputs)",
+                       "l2": "inputs larger than L2, launches back to back" if back_to_back
+                       else "flushed before every timed launch"},
+            "roofline": {"bound": "hbm", "achieved": a["gbs"], "peak": hbm, "unit": "GB/s",
+                         "frac": a["frac_of_measured_hbm"], "traffic": None},
+            "kernels": res}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0

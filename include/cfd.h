@@ -362,6 +362,39 @@ int cfd_csr_spmv(int32_t nx, int32_t ny, int32_t nz, const void *dev_buf, const 
                  cfd_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Stand-alone Krylov building blocks (Sec. 3.1, Table 1: spmv, the vector
+ * add / scale operators and dot), for measurement one kernel at a time; the
+ * solvers above fuse the same arithmetic into their persistent kernels.
+ * All calls are asynchronous on `stream` and report argument errors through
+ * the return code and cfd_last_error(NULL).
+ * ------------------------------------------------------------------------ */
+
+/* y = A x in FP32 for the Neumann pressure matrix of an nx x ny x nz grid
+ * (x fastest; row c: n_c x_c minus the in-box neighbours, n_c their count),
+ * the operator of the mixed-precision inner solve.  x, y: device, V floats,
+ * must not overlap.  Errors: empty grid, NULL, ny > 524280 or nz > 131070. */
+int cfd_apply_poisson_f32(int32_t nx, int32_t ny, int32_t nz, const float *x_dev, float *y_dev,
+                          cfd_stream_t stream);
+
+/* Bytes of the caller-owned device scratch of cfd_cg_update_*.  It must be
+ * zero-filled once before its first use; every call leaves it zero-filled
+ * again.  One scratch serves one call at a time (one stream). */
+size_t cfd_cg_update_scratch_bytes(void);
+
+/* The CG update of Algorithm-1 form (Sec. 3.1):  x += alpha p,
+ * r -= alpha q, then *rr_dev = r.r of the updated r (summed in FP64 in an
+ * order fixed by n alone, so repeated calls give identical bits).
+ * p, q, x, r: device vectors of n elements, 16-byte aligned, x and r not
+ * overlapping p, q or each other; rr_dev: one device double.
+ * Errors: n = 0, NULL, misaligned pointers. */
+int cfd_cg_update_f64(size_t n, double alpha, const double *p_dev, const double *q_dev, double *x_dev,
+                      double *r_dev, double *rr_dev, void *scratch_dev, cfd_stream_t stream);
+/* The same in FP32 (the vector arithmetic rounds to FP32; r.r accumulates in
+ * FP64 from FP32 partial sums of four squares). */
+int cfd_cg_update_f32(size_t n, float alpha, const float *p_dev, const float *q_dev, float *x_dev, float *r_dev,
+                      double *rr_dev, void *scratch_dev, cfd_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Learned preconditioner (flexible PCG with a U-Net, Sec. 5 "other
  * preconditioners"; the paper itself uses DIC / Jacobi, Sec. 3.1).
  * ------------------------------------------------------------------------ */

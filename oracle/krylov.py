@@ -29,7 +29,9 @@ Pins (tests/test_oracle_solver.py): dense pseudo-inverse solves on grids up
 to 6^3, exactly one iteration for a single DCT mode and two for two modes,
 the manufactured cosine solution in closed form, the O(h^2) rate on a
 polynomial solution, and DIC = exact factorisation on tridiagonal matrices
-(one PCG iteration).
+(one PCG iteration).  ``cg_update`` is the step every ``pcg`` iteration
+takes, so those pins cover it; tests/test_oracle_solver.py also checks that
+with alpha = r.r / p.Ap it leaves r orthogonal to p and equal to b - A x.
 
 ``fpcg`` (flexible PCG for a preconditioner that may vary between
 iterations) is pinned by tests/test_oracle_unet.py: with M = identity or a
@@ -94,6 +96,14 @@ def dic_precond(A: sp.csr_matrix):
     return apply, d
 
 
+def cg_update(x, r, p, q, alpha):
+    """The vector step of a CG iteration (Table 1: vector add / scale, dot):
+    x <- x + alpha p and r <- r - alpha q in place; returns r.r of the new r."""
+    x += alpha * p
+    r -= alpha * q
+    return float(np.dot(r, r))
+
+
 def pcg(A, b, x0=None, rtol=1e-8, max_iters=1000, precond=identity_precond,
         fixed_iters=None, max_restarts=8):
     """Solve A x = b; returns (x, SolveStats)."""
@@ -137,11 +147,9 @@ def pcg(A, b, x0=None, rtol=1e-8, max_iters=1000, precond=identity_precond,
             st.breakdown = True
             break
         alpha = rz / pq
-        x += alpha * p
-        r -= alpha * q
+        rr = cg_update(x, r, p, q, alpha)
         z = precond(r)
         rz_new = float(np.dot(r, z))
-        rr = float(np.dot(r, r))
         beta = rz_new / rz
         rz = rz_new
         p = z + beta * p

@@ -117,6 +117,10 @@ def load_library(path: Optional[str] = None):
         "cfd_csr_assemble": (ctypes.c_int, [ctypes.c_int32] * 3 + [vp, vp]),
         "cfd_csr_spmv": (ctypes.c_int, [ctypes.c_int32] * 3 + [vp, vp, vp, vp]),
         "cfd_snapshot_write_csv": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_int]),
+        "cfd_apply_poisson_f32": (ctypes.c_int, [ctypes.c_int32] * 3 + [vp, vp, vp]),
+        "cfd_cg_update_scratch_bytes": (ctypes.c_size_t, []),
+        "cfd_cg_update_f64": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_double, vp, vp, vp, vp, vp, vp, vp]),
+        "cfd_cg_update_f32": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_float, vp, vp, vp, vp, vp, vp, vp]),
         "cfd_conv3d_bf16": (ctypes.c_int, [ctypes.c_int] * 3 + [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, vp,
                                                                 ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]),
         "cfd_unet_workspace_bytes": (ctypes.c_int, [ctypes.c_int] * 3 + [P(ctypes.c_size_t)]),
@@ -582,3 +586,44 @@ class CsrMatrix:
                                    ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(_stream_ptr(self.stream)))
         if rc != CFD_OK:
             raise CfdError(rc, self.lib.cfd_last_error(None).decode())
+
+
+class KrylovKernels:
+    """The stand-alone building blocks (cfd_apply_poisson_f32,
+    cfd_cg_update_f64 / _f32) with their own zero-filled scratch and an
+    FP64 result slot on the device."""
+
+    def __init__(self, stream=None, device=None):
+        self.lib = load_library()
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        nbytes = int(self.lib.cfd_cg_update_scratch_bytes())
+        self.scratch = torch.zeros(nbytes, dtype=torch.uint8, device=dev)
+        self.rr = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.stream = stream
+
+    def _check(self, rc):
+        if rc != CFD_OK:
+            raise CfdError(rc, self.lib.cfd_last_error(None).decode())
+
+    def apply_poisson_f32(self, x: torch.Tensor, y: torch.Tensor):
+        """y = A x in FP32; x, y contiguous float32 of shape (nz, ny, nx)."""
+        if x.dtype != torch.float32 or y.dtype != torch.float32 or x.dim() != 3 or x.shape != y.shape:
+            raise ValueError("apply_poisson_f32 wants two float32 tensors of one (nz, ny, nx) shape")
+        nz, ny, nx = x.shape
+        self._check(self.lib.cfd_apply_poisson_f32(nx, ny, nz, ctypes.c_void_p(x.data_ptr()),
+                                                   ctypes.c_void_p(y.data_ptr()),
+                                                   ctypes.c_void_p(_stream_ptr(self.stream))))
+
+    def cg_update(self, alpha, p, q, x, r) -> torch.Tensor:
+        """x += alpha p, r -= alpha q; returns the device scalar r.r (FP64)."""
+        n = r.numel()
+        if not all(t.dtype == r.dtype and t.numel() == n and t.is_contiguous() for t in (p, q, x)):
+            raise ValueError("cg_update wants four contiguous vectors of one dtype and length")
+        fn = {torch.float64: (self.lib.cfd_cg_update_f64, ctypes.c_double),
+              torch.float32: (self.lib.cfd_cg_update_f32, ctypes.c_float)}.get(r.dtype)
+        if fn is None:
+            raise ValueError("cg_update supports float64 and float32")
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+        self._check(fn[0](n, fn[1](alpha), ptr(p), ptr(q), ptr(x), ptr(r), ptr(self.rr), ptr(self.scratch),
+                          ctypes.c_void_p(_stream_ptr(self.stream))))
+        return self.rr

@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 import scipy.sparse as sp
 
-from oracle.krylov import dic_precond, jacobi_precond, pcg
+from oracle.krylov import cg_update, dic_precond, jacobi_precond, pcg
 from oracle.operators import poisson_csr
 from paper_2504_03697_gb300.synthetic import uniform_field
 
@@ -182,3 +182,22 @@ def test_fixed_iteration_replay():
     x2, s2 = pcg(A, b, rtol=1e-8, fixed_iters=s1.iters)
     assert s2.iters == s1.iters
     np.testing.assert_array_equal(x1, x2)
+
+
+def test_cg_update_orthogonality_and_true_residual():
+    """With alpha = r.r / p.Ap (p = r, first CG step) the updated residual is
+    orthogonal to p and equals b - A x; the returned value is its norm^2."""
+    A = poisson_csr(5, 4, 3)
+    b = uniform_field((3, 4, 5), seed=21).ravel()
+    b -= b.mean()
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    q = A @ p
+    alpha = float(r @ r) / float(p @ q)
+    rr = cg_update(x, r, p, q, alpha)
+    assert abs(float(p @ r)) <= 1e-13 * float(p @ p)
+    assert np.allclose(r, b - A @ x, rtol=0, atol=1e-14)
+    assert np.allclose(x, alpha * b, rtol=0, atol=1e-15)
+    assert rr == pytest.approx(float(np.sum(r * r)), rel=1e-15)
+    assert rr < float(b @ b)
