@@ -79,6 +79,8 @@ def parse_args(argv=None):
                     help="FP64 CG form: one grid reduction per iteration (default) or the textbook two")
     ap.add_argument("--spmv", type=int, default=0,
                     help="time the pressure operator on an N^3 grid: matrix-free stencil vs the assembled CSR matrix")
+    ap.add_argument("--ir-form", choices=["tuned", "auto", "persistent", "graph"], default="tuned",
+                    help="execution of the mixed-precision solve in --poisson mode (default: the autotuner's choice)")
     ap.add_argument("--blas", type=int, default=0,
                     help="time the stand-alone building blocks on an N^3 grid: FP32 operator, FP64 / FP32 CG update")
     ap.add_argument("--advect-order", type=int, default=1, choices=[1, 2],
@@ -444,7 +446,7 @@ def main_ours(args):
     return 0 if ok else 1
 
 
-def time_solves(cfd, n, solver, seeds, warmup, max_iters=0, device=None, autotune=True):
+def time_solves(cfd, n, solver, seeds, warmup, max_iters=0, device=None, autotune=True, ir_form=None):
     """Standalone FP64-judged pressure solves of Gaussian right-hand sides:
     per-solve device time of the solve kernel (CUDA events inside the
     library), iterations and the true relative residual.  The solver shape
@@ -455,6 +457,8 @@ def time_solves(cfd, n, solver, seeds, warmup, max_iters=0, device=None, autotun
     cav = cfd.Cavity(cfd.make_params(n, n, n, solver=solver, max_iters=max_iters), device=device)
     if autotune:
         cav.autotune(iters=30)
+    if ir_form is not None and solver == "ir":
+        cav.set_ir_form(ir_form)
     bs = [torch.tensor(gaussian_rhs(n, n, n, seed=s), device=device) for s in seeds]
     x = torch.zeros_like(bs[0])
     for i in range(warmup):
@@ -523,13 +527,16 @@ def main_poisson(args):
     from paper_2504_03697_gb300 import cfd
 
     n = args.poisson
-    res = time_solves(cfd, n, args.solver, list(range(args.steps)), args.warmup, args.max_iters, device)
+    form = None if args.ir_form == "tuned" else args.ir_form
+    res = time_solves(cfd, n, args.solver, list(range(args.steps)), args.warmup, args.max_iters, device,
+                      ir_form=form)
     ms = sorted(r["ms"] for r in res)
     line = {"metric": "time-to-rtol-1e-8 per solve", "value": statistics.median(ms), "unit": "ms",
             "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "dtype": "f32+f64" if args.solver == "ir" else "f64", "data": "synthetic",
             "config": {"workload": f"Neumann-Poisson {n}^3, N(0,1) right-hand sides (seeds 0..{args.steps - 1}), "
-                                   f"solver {args.solver}, rtol 1e-8", "max_iters": args.max_iters},
+                                   f"solver {args.solver}, rtol 1e-8", "max_iters": args.max_iters,
+                       "ir_form": args.ir_form if args.solver == "ir" else None},
             "solves": res}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -206,13 +206,30 @@ int cfd_set_solver_shape(cfd_handle *h, int blocks_per_sm, int tile_depth);
 enum { CFD_CG_SINGLE_REDUCTION = 0, CFD_CG_TWO_REDUCTIONS = 1 };
 int cfd_set_cg_variant(cfd_handle *h, int variant);
 
+/* Execution form of the CFD_SOLVER_IR pressure solve (same method, same
+ * stopping rule):
+ *   PERSISTENT  one cooperative kernel per solve, two grid-wide reductions
+ *               per FP32 iteration (any grid);
+ *   GRAPH       one CUDA graph per solve whose device-side while loops run
+ *               the FP32 iterations as two streaming kernels (direction +
+ *               operator, update) and the FP64 refinements as separate
+ *               kernels; each kernel's last block updates the solver scalars
+ *               and the loop conditions.  Needs nx % 4 == 0.
+ *   AUTO        (default) GRAPH when nx % 4 == 0 and the grid has at least
+ *               2^21 cells, PERSISTENT otherwise.
+ * Errors: unknown form; GRAPH with nx % 4 != 0.  Batches always use the
+ * persistent multi-problem kernel. */
+enum { CFD_IR_AUTO = 0, CFD_IR_PERSISTENT = 1, CFD_IR_GRAPH = 2 };
+int cfd_set_ir_form(cfd_handle *h, int form);
+
 /* Autotuner of the solver shape for this handle's grid and solver: times
  * fixed-length pressure solves (iters iterations, a deterministic hashed
  * right-hand side) with the automatic shape and with every blocks_per_sm in
  * {1, 2, 3, 4} x tile_depth in {1, 2, 4, 8} -- for CFD_SOLVER_CG under both
- * CG forms (cfd_set_cg_variant) -- keeps the fastest (as by
- * cfd_set_solver_shape and cfd_set_cg_variant; shape 0 / 0 when the
- * automatic one wins) and reports it.  Uses the intermediate-velocity
+ * CG forms (cfd_set_cg_variant); for CFD_SOLVER_IR these shapes in the
+ * persistent form plus the graph form when nx % 4 == 0 -- keeps the fastest
+ * (as by cfd_set_solver_shape, cfd_set_cg_variant and cfd_set_ir_form;
+ * shape 0 / 0 when the automatic one wins) and reports it.  Uses the intermediate-velocity
  * scratch; the state (u, v, w, p) is not touched.  Call between steps;
  * synchronises the stream. */
 typedef struct {
@@ -222,6 +239,7 @@ typedef struct {
   float ms_auto;            /* ms per fixed-length solve, automatic shape       */
   float ms_best;            /* ms per fixed-length solve, chosen configuration  */
   int32_t cg_variant;       /* chosen CFD_CG_* form                             */
+  int32_t ir_form;          /* chosen CFD_IR_* form (CFD_SOLVER_IR handles)     */
 } cfd_tune_report;
 int cfd_autotune_solver(cfd_handle *h, int32_t iters, cfd_tune_report *rep);
 

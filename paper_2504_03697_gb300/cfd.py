@@ -44,7 +44,8 @@ class cfd_params(ctypes.Structure):
 
 class cfd_tune_report(ctypes.Structure):
     _fields_ = [("blocks_per_sm", ctypes.c_int32), ("tile_depth", ctypes.c_int32), ("candidates", ctypes.c_int32),
-                ("ms_auto", ctypes.c_float), ("ms_best", ctypes.c_float), ("cg_variant", ctypes.c_int32)]
+                ("ms_auto", ctypes.c_float), ("ms_best", ctypes.c_float), ("cg_variant", ctypes.c_int32),
+                ("ir_form", ctypes.c_int32)]
 
 
 class cfd_solve_stats(ctypes.Structure):
@@ -112,6 +113,7 @@ def load_library(path: Optional[str] = None):
         "cfd_pressure_rhs": (ctypes.c_int, [vp, vp]),
         "cfd_autotune_solver": (ctypes.c_int, [vp, ctypes.c_int32, P(cfd_tune_report)]),
         "cfd_set_cg_variant": (ctypes.c_int, [vp, ctypes.c_int]),
+        "cfd_set_ir_form": (ctypes.c_int, [vp, ctypes.c_int]),
         "cfd_snapshot": (ctypes.c_int, [vp]),
         "cfd_csr_bytes": (ctypes.c_int, [ctypes.c_int32] * 3 + [P(ctypes.c_size_t), P(ctypes.c_int64)]),
         "cfd_csr_assemble": (ctypes.c_int, [ctypes.c_int32] * 3 + [vp, vp]),
@@ -293,6 +295,10 @@ class Cavity:
     def set_cg_variant(self, variant: str):
         """'single' (one reduction per iteration, default) or 'two' (textbook)."""
         return self._check(self.lib.cfd_set_cg_variant(self.h, {"single": 0, "two": 1}[variant]))
+
+    def set_ir_form(self, form: str):
+        """Execution of the IR solve: 'auto' (default), 'persistent' or 'graph'."""
+        return self._check(self.lib.cfd_set_ir_form(self.h, {"auto": 0, "persistent": 1, "graph": 2}[form]))
 
     def autotune(self, iters=50) -> dict:
         """Pick the fastest solver shape for this grid (cfd_autotune_solver)."""

@@ -21,6 +21,7 @@
 #include "../../include/cfd.h"
 #include "cfd_internal.h"
 #include "dic.h"
+#include "ir_graph.h"
 
 using namespace cfd;
 
@@ -40,6 +41,7 @@ struct Layout {
   size_t e0, e1, e2;
   size_t dicd;
   size_t r32, d32, p0_32, p1_32, q32;
+  size_t irg;  // state of the graph-driven mixed-precision solve
   size_t partials, ctrl, stats;
   size_t total;
 };
@@ -82,6 +84,7 @@ Layout ws_layout(const cfd_params& p, int max_blocks) {
     L.p0_32 = take(cells * 4);
     L.p1_32 = take(cells * 4);
     L.q32 = take(cells * 4);
+    L.irg = take(ir_graph_state_bytes());
   }
   L.partials = take(partials_doubles(max_blocks) * 8);  // double-buffered block + group partials
   L.ctrl = take(sizeof(SolveCtrl));
@@ -109,6 +112,9 @@ struct cfd_handle {
   bool dic_ready = false;
   cfd_unet* precond_net = nullptr;  // CFD_SOLVER_FPCG
   float *r32, *d32, *p0_32, *p1_32, *q32;
+  void* irg_state = nullptr;     // graph solve state (CFD_SOLVER_IR)
+  cfd::IrGraph* irg = nullptr;   // its cached, instantiated graph
+  int ir_form = CFD_IR_AUTO;
   double* partials;
   SolveCtrl* ctrl;
   DevStepStats* stats;
@@ -287,6 +293,17 @@ int run_diffusion(cfd_handle* h, int comp, DevSolveStats* st) {
   return cuda_check(h, launch_cg(a, h->lg, h->stream, &h->launches), "diffusion CG launch");
 }
 
+// Graph form of the mixed-precision solve: on request, or automatically on
+// grids of at least kIrGraphCells cells (where its streaming kernels beat the
+// persistent kernel's two grid barriers per iteration).
+constexpr size_t kIrGraphCells = size_t(1) << 21;
+
+bool use_ir_graph(const cfd_handle* h, const IrArgs& a) {
+  if (!h->irg_state || !ir_graph_eligible(a) || h->ir_form == CFD_IR_PERSISTENT) return false;
+  if (h->ir_form == CFD_IR_GRAPH) return true;
+  return size_t(a.g.mx) * a.g.my * a.g.mz >= kIrGraphCells;
+}
+
 // Pressure solve A x = b on the handle's workspace b (already filled).
 int run_pressure(cfd_handle* h, double* x, int zero_x0, int gauge, DevSolveStats* st) {
   int rc = cuda_check(h, cudaMemsetAsync(h->ctrl, 0, sizeof(SolveCtrl), h->stream), "memset ctrl");
@@ -349,7 +366,10 @@ int run_pressure(cfd_handle* h, double* x, int zero_x0, int gauge, DevSolveStats
   if (h->prm.solver == CFD_SOLVER_IR) {
     const IrArgs a = pressure_ir_args(h, x, zero_x0, gauge, st, h->ctrl);
     const int t = phase_begin(h, CFD_PHASE_PCG);
-    rc = cuda_check(h, launch_ir(a, h->lg, h->stream, &h->launches), "IR launch");
+    if (use_ir_graph(h, a))
+      rc = cuda_check(h, launch_ir_graph(a, h->irg_state, &h->irg, h->stream), "IR graph launch");
+    else
+      rc = cuda_check(h, launch_ir(a, h->lg, h->stream, &h->launches), "IR launch");
     phase_end(h, t);
     return rc;
   }
@@ -497,6 +517,7 @@ int cfd_create(const cfd_params* params, void* dev_ws, size_t bytes, cfd_stream_
   if (params->solver == CFD_SOLVER_DIC) h->dicd = D(L.dicd);
   if (params->solver == CFD_SOLVER_IR) {
     h->r32 = F(L.r32); h->d32 = F(L.d32); h->p0_32 = F(L.p0_32); h->p1_32 = F(L.p1_32); h->q32 = F(L.q32);
+    h->irg_state = h->ws + L.irg;
   }
   h->partials = D(L.partials);
   h->ctrl = reinterpret_cast<SolveCtrl*>(h->ws + L.ctrl);
@@ -531,6 +552,7 @@ void cfd_destroy(cfd_handle* h) {
     cudaEventDestroy(h->snap_ev);
   }
   if (h->snap) cudaFreeHost(h->snap);
+  destroy_ir_graph(h->irg);
   delete h;
 }
 
@@ -816,7 +838,9 @@ int cfd_autotune_solver(cfd_handle* h, int32_t iters, cfd_tune_report* rep) {
   int rc = cuda_check(h, cudaEventCreate(&e0), "event");
   if (!rc) rc = cuda_check(h, cudaEventCreate(&e1), "event");
   const int var0 = h->lg.cg_variant;
-  auto time_shape = [&](int variant, int bps, int tz, float& best_ms) -> int {
+  const int form0 = h->ir_form;
+  auto time_shape = [&](int variant, int bps, int tz, int form, float& best_ms) -> int {
+    h->ir_form = form;
     h->lg.cg_variant = variant;
     h->lg.bps_req = bps;
     h->lg.tz_req = tz;
@@ -837,9 +861,13 @@ int cfd_autotune_solver(cfd_handle* h, int32_t iters, cfd_tune_report* rep) {
   };
   // the CG form is a candidate too when the solves are unpreconditioned FP64 CG
   const int nvar = h->prm.solver == CFD_SOLVER_CG ? 2 : 1;
+  // the mixed-precision solve: shapes of the persistent form, then the graph form
+  const bool ir = h->prm.solver == CFD_SOLVER_IR;
+  const bool graph_ok = ir && h->irg_state && h->prm.nx % 4 == 0;
+  const int shape_form = ir ? CFD_IR_PERSISTENT : form0;
   float ms_auto = 0.f, ms_best = 0.f;
-  int best_bps = 0, best_tz = 0, best_var = var0, tried = 0;
-  if (!rc) rc = time_shape(var0, 0, 0, ms_auto);
+  int best_bps = 0, best_tz = 0, best_var = var0, best_form = form0, tried = 0;
+  if (!rc) rc = time_shape(var0, 0, 0, form0, ms_auto);
   ms_best = ms_auto;
   ++tried;
   const int bps_list[4] = {1, 2, 3, 4};
@@ -849,18 +877,31 @@ int cfd_autotune_solver(cfd_handle* h, int32_t iters, cfd_tune_report* rep) {
     for (int i = -1; i < 4 && !rc; ++i) {
       for (int j = 0; j < 4 && !rc; ++j) {
         if (i < 0 && j > 0) break;
-        if (i < 0 && variant == var0) continue;  // the automatic shape of var0 is timed above
+        if (i < 0 && variant == var0 && shape_form == form0) continue;  // timed above
         const int bps = i < 0 ? 0 : bps_list[i], tz = i < 0 ? 0 : tz_list[j];
         float ms = 0.f;
-        rc = time_shape(variant, bps, tz, ms);
+        rc = time_shape(variant, bps, tz, shape_form, ms);
         ++tried;
         if (!rc && ms < ms_best) {
           ms_best = ms;
           best_bps = bps;
           best_tz = tz;
           best_var = variant;
+          best_form = shape_form;
         }
       }
+    }
+  }
+  if (graph_ok && !rc) {
+    float ms = 0.f;
+    rc = time_shape(var0, 0, 0, CFD_IR_GRAPH, ms);
+    ++tried;
+    if (!rc && ms < ms_best) {
+      ms_best = ms;
+      best_bps = 0;
+      best_tz = 0;
+      best_var = var0;
+      best_form = CFD_IR_GRAPH;
     }
   }
   if (e0) cudaEventDestroy(e0);
@@ -870,11 +911,13 @@ int cfd_autotune_solver(cfd_handle* h, int32_t iters, cfd_tune_report* rep) {
     h->lg.bps_req = bps0;
     h->lg.tz_req = tz0;
     h->lg.cg_variant = var0;
+    h->ir_form = form0;
     return rc;
   }
   h->lg.bps_req = best_bps;
   h->lg.tz_req = best_tz;
   h->lg.cg_variant = best_var;
+  h->ir_form = best_form;
   if (rep) {
     rep->blocks_per_sm = best_bps;
     rep->tile_depth = best_tz;
@@ -882,6 +925,7 @@ int cfd_autotune_solver(cfd_handle* h, int32_t iters, cfd_tune_report* rep) {
     rep->ms_auto = ms_auto;
     rep->ms_best = ms_best;
     rep->cg_variant = best_var;
+    rep->ir_form = best_form;
   }
   return CFD_OK;
 }
@@ -897,7 +941,23 @@ int cfd_pressure_rhs(cfd_handle* h, double* b_dev) {
   return cuda_check(h, launch_divergence(pa, h->stream, &h->launches), "divergence");
 }
 
-int64_t cfd_launch_count(const cfd_handle* h) { return h ? h->launches : 0; }
+int64_t cfd_launch_count(const cfd_handle* h) {
+  if (!h) return 0;
+  long long graph_kernels = 0;
+  if (h->irg && h->irg_state && ir_graph_kernel_count(h->irg_state, h->stream, &graph_kernels) != cudaSuccess)
+    graph_kernels = 0;
+  return h->launches + graph_kernels;
+}
+
+int cfd_set_ir_form(cfd_handle* h, int form) {
+  if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
+  if (form != CFD_IR_AUTO && form != CFD_IR_PERSISTENT && form != CFD_IR_GRAPH)
+    return set_err(h, CFD_ERR_INVALID_ARG, "unknown IR form %d", form);
+  if (form == CFD_IR_GRAPH && h->prm.nx % 4 != 0)
+    return set_err(h, CFD_ERR_INVALID_ARG, "the graph form needs nx %% 4 == 0");
+  h->ir_form = form;
+  return CFD_OK;
+}
 
 int cfd_set_solver_shape(cfd_handle* h, int blocks_per_sm, int tile_depth) {
   if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");

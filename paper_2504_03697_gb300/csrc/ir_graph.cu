@@ -1,0 +1,635 @@
+// Mixed-precision pressure solve (FP32 CG with FP64 reliable-update
+// refinement, Sec. 3.1's PCG in the precision split of the persistent
+// ir_kernel) as one CUDA graph with device-side loops, for large grids.
+//
+// The arithmetic is that of ir_kernel: the FP32 recurrence p = r32 + beta p,
+// q = A p, alpha = r32.r32 / p.q, x32 += alpha p, r32 -= alpha q; FP64
+// refinement x += x32, r = b - A x whenever |r32|^2 has fallen by delta^2
+// since the last refinement (or below the tolerance); the search direction
+// is kept across a refinement; convergence only on the FP64 true residual.
+// What differs is the execution: instead of one cooperative kernel with two
+// grid barriers per iteration, every phase is its own streaming kernel
+// (float4 accesses, the operator on the fly from r32 and the previous p, x
+// neighbours by warp shuffles) and the loop control runs on the device:
+//
+//   memset(counter) -> pro_sum -> pro_resid ->
+//   while (outer) { prep -> while (inner) { dir -> upd } -> refine } ->
+//   epi_resid -> finish -> shift
+//
+// `outer` and `inner` are conditional graph nodes of type while.  Each
+// kernel reduces its partial sums in FP64 through a last-block pass (blocks
+// add their sums to a fixed slot, the block that arrives last sums the slots
+// in block order), and that block's thread 0 updates the solver scalars in
+// GState and sets the loop conditions.  Nothing waits on another block: the
+// graph's node order is the only synchronisation.  Every loop ends: each
+// pass of the inner body raises `iters` by one and the outer body stops the
+// loops once iters >= max_iters or refinements > max_outer.
+//
+// Requires mx % 4 == 0 (16-byte rows of the FP32 vectors).
+
+#include <cstdint>
+#include <cstring>
+
+#include "cfd_common.cuh"
+#include "cfd_internal.h"
+#include "ir_graph.h"
+
+namespace cfd {
+namespace {
+
+constexpr int kGThreads = 256;  // every kernel: 256 threads (32 x 8 for the stencils)
+constexpr int kGMax = 1024;     // blocks per kernel (partial-sum slots per value)
+constexpr int kZ32 = 4;         // z planes per FP32 stencil work item
+constexpr int kZ64 = 4;         // z planes per FP64 stencil work item
+
+// Solver scalars of one solve (device memory, written only by the thread 0
+// of the last block of a kernel; read by every thread of the next kernels).
+struct GState {
+  double shift;      // mean of b (removed when remove_mean)
+  double bb, rr, rsum;
+  double rz, rz_ref, beta, alpha, gshift;
+  double tol2, delta2;
+  int iters, refinements, status, first, cur, refine, pending, breakdown, done, pad;
+  unsigned counter;  // arrivals of the current kernel (atomicInc wraps to 0)
+  unsigned pad2;
+  long long kernels;  // kernels run by all graph solves of this workspace (never reset)
+};
+
+constexpr size_t kStateBytes = 256;
+static_assert(sizeof(GState) <= kStateBytes, "GState slot");
+
+struct GArgs {
+  int mx, my, mz;
+  size_t n;
+  double* x;
+  double* b;
+  double* r;
+  float* r32;
+  float* d32;
+  float* p0;
+  float* p1;
+  float* q32;
+  int zero_x0, remove_mean, gauge;
+  double gauge_value;
+  double rtol, delta;
+  int max_iters, max_outer;
+  GState* S;
+  double* part;  // 3 * kGMax doubles
+  DevSolveStats* stats;
+  cudaGraphConditionalHandle h_out, h_in;
+  int w32x, w32y, w32z;  // FP32 work items: float4 columns / 32, rows / 8, planes / kZ32
+  int w64x, w64y, w64z;  // FP64 work items: columns / 32, rows / 8, planes / kZ64
+};
+
+__device__ __forceinline__ int ftid() { return threadIdx.y * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ size_t vtid() { return size_t(blockIdx.x) * kGThreads + ftid(); }
+__device__ __forceinline__ size_t vstride() { return size_t(gridDim.x) * kGThreads; }
+
+__device__ __forceinline__ void count_kernel(GState* S) {
+  if (blockIdx.x == 0 && ftid() == 0) S->kernels += 1;
+}
+
+// Block sums of v[], stored in slot blockIdx.x; returns true in every thread
+// of the block that arrived last, with out[] = the sums over all slots in
+// block order (the same bits for the same partials whatever the schedule).
+template <int K>
+__device__ bool reduce_last(const double (&v)[K], double* part, unsigned* counter, double (&out)[K]) {
+  __shared__ double sh[K][kGThreads / 32];
+  __shared__ int s_last;
+  const int t = ftid(), lane = t & 31, wid = t >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double s = v[k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) sh[k][wid] = s;
+  }
+  __syncthreads();
+  if (t == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < kGThreads / 32; ++w) s += sh[k][w];
+      part[k * kGMax + blockIdx.x] = s;
+    }
+    __threadfence();
+    s_last = atomicInc(counter, gridDim.x - 1) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    acc[k] = 0.0;
+    for (unsigned bk = unsigned(t); bk < gridDim.x; bk += kGThreads) acc[k] += __ldcg(part + k * kGMax + bk);
+    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+  }
+  __syncthreads();  // thread 0's reads of sh above are complete
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[k][wid] = acc[k];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double s = 0.0;
+    for (int w = 0; w < kGThreads / 32; ++w) s += sh[k][w];
+    out[k] = s;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// prologue: sum of b, then r = b' - A x0 with b' = b - mean (in place)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kGThreads) g_pro_sum(const GArgs a) {
+  count_kernel(a.S);
+  double s = 0.0;
+  if (a.remove_mean)
+    for (size_t e = vtid(); e < a.n; e += vstride()) s += a.b[e];
+  double v[1] = {s}, o[1];
+  if (!reduce_last<1>(v, a.part, &a.S->counter, o) || ftid() != 0) return;
+  GState* S = a.S;
+  S->shift = a.remove_mean ? o[0] / double(a.n) : 0.0;
+  S->iters = 0;
+  S->refinements = 0;
+  S->status = kErrNotConverged;
+  S->first = 1;
+  S->cur = 0;
+  S->refine = 0;
+  S->pending = 0;
+  S->breakdown = 0;
+  S->done = 0;
+  S->beta = 0.0;
+  S->rz = 0.0;
+}
+
+// FP64 residual r = b - A xv over the tiles (scalar lanes, z-marching).
+// MODE 0 (prologue): b' = b - shift (stored when remove_mean), xv = x or 0
+//   (zero_x0: x := 0); sums b'.b', r.r, sum(r); sets the initial state.
+// MODE 1 (refinement, after the inner loop): only when S->refine; xv =
+//   x + x32 on the fly (x itself unchanged); sums r.r, sum(r).
+// MODE 2 (epilogue): only when b != 0 and the loop ended without
+//   convergence; xv = x + x32 if x32 is pending; sums r.r.
+template <int MODE>
+__global__ void __launch_bounds__(kGThreads) g_resid64(const GArgs a) {
+  GState* S = a.S;
+  count_kernel(S);
+  if (MODE == 1 && !S->refine) {
+    if (blockIdx.x == 0 && ftid() == 0) cudaGraphSetConditional(a.h_out, 0u);  // cap or breakdown: leave
+    return;
+  }
+  if (MODE == 2 && (S->bb == 0.0 || S->status == kOk)) return;
+  const int mx = a.mx, my = a.my, mz = a.mz;
+  const size_t sy = size_t(mx), sz = size_t(mx) * my;
+  const double shift = MODE == 0 ? S->shift : 0.0;
+  const bool add32 = MODE == 1 || (MODE == 2 && S->pending);
+  const bool zero = MODE == 0 && a.zero_x0;
+  auto X = [&](size_t e) { return zero ? 0.0 : (add32 ? a.x[e] + double(a.d32[e]) : a.x[e]); };
+  double sb = 0.0, sr = 0.0, ss = 0.0;
+  const int items = a.w64x * a.w64y * a.w64z;
+  for (int w = blockIdx.x; w < items; w += gridDim.x) {
+    const int wx = w % a.w64x, wy = (w / a.w64x) % a.w64y, wz = w / (a.w64x * a.w64y);
+    const int i = wx * 32 + threadIdx.x, j = wy * 8 + threadIdx.y, k0 = wz * kZ64;
+    if (i >= mx || j >= my) continue;
+    const int k1 = min(k0 + kZ64, mz);
+    size_t c = (size_t(k0) * my + j) * mx + i;
+    double xc = X(c);
+    double xm = k0 > 0 ? X(c - sz) : xc;
+    for (int k = k0; k < k1; ++k, c += sz) {
+      const double xp = k < mz - 1 ? X(c + sz) : xc;
+      const double xw = i > 0 ? X(c - 1) : xc;
+      const double xe = i < mx - 1 ? X(c + 1) : xc;
+      const double xs = j > 0 ? X(c - sy) : xc;
+      const double xn = j < my - 1 ? X(c + sy) : xc;
+      const double ax = fma(6.0, xc, -(((((xw + xe) + xs) + xn) + xm) + xp));
+      double bv = a.b[c];
+      if (MODE == 0) {
+        bv -= shift;
+        if (a.remove_mean) a.b[c] = bv;
+        if (zero) a.x[c] = 0.0;
+        sb = fma(bv, bv, sb);
+      }
+      const double rv = bv - ax;
+      a.r[c] = rv;
+      sr = fma(rv, rv, sr);
+      ss += rv;
+      xm = xc;
+      xc = xp;
+    }
+  }
+  double v[3] = {sb, sr, ss}, o[3];
+  if (!reduce_last<3>(v, a.part, &S->counter, o) || ftid() != 0) return;
+  if (MODE == 0) {
+    S->bb = o[0];
+    S->rr = o[1];
+    S->rsum = o[2];
+    S->tol2 = a.rtol * a.rtol * o[0];
+    S->delta2 = a.delta * a.delta;
+    if (o[0] == 0.0) {
+      S->status = kOk;
+      S->done = 1;
+      S->rr = 0.0;
+    }
+    cudaGraphSetConditional(a.h_out, o[0] == 0.0 ? 0u : 1u);
+  } else if (MODE == 1) {
+    S->rr = o[1];
+    S->rsum = o[2];
+    S->refinements += 1;
+    S->refine = 0;
+    cudaGraphSetConditional(a.h_out, 1u);
+  } else {
+    S->rr = o[1];
+    if (S->status == kErrNotConverged && o[1] <= S->tol2) S->status = kOk;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// outer body, first node: leave (converged / caps) or start a new FP32
+// recurrence from the true residual.  Folds a pending x32 into x either way.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kGThreads) g_prep(const GArgs a) {
+  GState* S = a.S;
+  count_kernel(S);
+  const bool ok = S->rr <= S->tol2;
+  const bool leave = ok || S->refinements > a.max_outer || S->iters >= a.max_iters;
+  const bool fold = S->pending != 0;
+  const double rmean = S->rsum / double(a.n);
+  float f = 0.f;
+  for (size_t e = vtid(); e < a.n; e += vstride()) {
+    if (fold) a.x[e] += double(a.d32[e]);
+    if (!leave) {
+      const float v = float(a.r[e] - rmean);
+      a.r32[e] = v;
+      f = fmaf(v, v, f);
+    }
+    if (fold || !leave) a.d32[e] = 0.f;
+  }
+  double v[1] = {double(f)}, o[1];
+  if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
+  S->pending = 0;
+  if (leave) {
+    if (ok) S->status = kOk;
+    S->done = 1;
+    cudaGraphSetConditional(a.h_in, 0u);
+    return;
+  }
+  if (!S->first) S->beta = o[0] / S->rz;  // keep the direction across the refinement
+  S->rz = o[0];
+  S->rz_ref = S->rr;
+  cudaGraphSetConditional(a.h_in, 1u);
+}
+
+// ---------------------------------------------------------------------------
+// inner body: p = r32 + beta p_old (on the fly at the 7 stencil points),
+// q = A p, p.q; alpha = rz / p.q
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kGThreads, 4) g_dir(const GArgs a) {
+  GState* S = a.S;
+  count_kernel(S);
+  const bool first = S->first != 0;
+  const float beta = float(S->beta);
+  const int cur = S->cur;
+  float* pnew = cur ? a.p1 : a.p0;
+  const float* pold = cur ? a.p0 : a.p1;
+  const int mx = a.mx, my = a.my, mz = a.mz, nx4 = mx >> 2;
+  const size_t sy4 = size_t(nx4), sz4 = size_t(nx4) * my;
+  const float4* r4 = reinterpret_cast<const float4*>(a.r32);
+  const float4* o4 = reinterpret_cast<const float4*>(pold);
+  float4* p4 = reinterpret_cast<float4*>(pnew);
+  float4* q4 = reinterpret_cast<float4*>(a.q32);
+  auto P4 = [&](size_t e) {
+    const float4 rv = __ldg(r4 + e);
+    if (first) return rv;
+    const float4 ov = __ldg(o4 + e);
+    return make_float4(fmaf(beta, ov.x, rv.x), fmaf(beta, ov.y, rv.y), fmaf(beta, ov.z, rv.z), fmaf(beta, ov.w, rv.w));
+  };
+  auto P1 = [&](size_t e) { return first ? __ldg(a.r32 + e) : fmaf(beta, __ldg(pold + e), __ldg(a.r32 + e)); };
+  const int lane = threadIdx.x;
+  double acc = 0.0;
+  const int items = a.w32x * a.w32y * a.w32z;
+  for (int w = blockIdx.x; w < items; w += gridDim.x) {
+    const int wx = w % a.w32x, wy = (w / a.w32x) % a.w32y, wz = w / (a.w32x * a.w32y);
+    const int i4 = wx * 32 + lane, j = wy * 8 + threadIdx.y, k0 = wz * kZ32;
+    if (j >= my) continue;  // the whole warp (one row per warp)
+    const bool on = i4 < nx4;
+    const bool has_w = i4 > 0, has_e = i4 + 1 < nx4;
+    const int k1 = min(k0 + kZ32, mz);
+    size_t c4 = (size_t(k0) * my + j) * nx4 + (on ? i4 : nx4 - 1);
+    float4 pc = P4(c4);
+    float4 pm = k0 > 0 ? P4(c4 - sz4) : pc;
+    float part = 0.f;
+    for (int k = k0; k < k1; ++k, c4 += sz4) {
+      const float4 pp = k < mz - 1 ? P4(c4 + sz4) : pc;
+      const float4 ps = j > 0 ? P4(c4 - sy4) : pc;
+      const float4 pn = j < my - 1 ? P4(c4 + sy4) : pc;
+      float west = __shfl_up_sync(0xffffffffu, pc.w, 1);
+      float east = __shfl_down_sync(0xffffffffu, pc.x, 1);
+      if (lane == 0) west = has_w ? P1(4 * c4 - 1) : pc.x;
+      else if (!has_w) west = pc.x;
+      if (lane == 31) east = has_e ? P1(4 * c4 + 4) : pc.w;
+      else if (!has_e) east = pc.w;
+      float4 q;
+      q.x = fmaf(6.f, pc.x, -(((((west + pc.y) + ps.x) + pn.x) + pm.x) + pp.x));
+      q.y = fmaf(6.f, pc.y, -(((((pc.x + pc.z) + ps.y) + pn.y) + pm.y) + pp.y));
+      q.z = fmaf(6.f, pc.z, -(((((pc.y + pc.w) + ps.z) + pn.z) + pm.z) + pp.z));
+      q.w = fmaf(6.f, pc.w, -(((((pc.z + east) + ps.w) + pn.w) + pm.w) + pp.w));
+      if (on) {
+        p4[c4] = pc;
+        q4[c4] = q;
+        part = fmaf(pc.x, q.x, part);
+        part = fmaf(pc.y, q.y, part);
+        part = fmaf(pc.z, q.z, part);
+        part = fmaf(pc.w, q.w, part);
+      }
+      pm = pc;
+      pc = pp;
+    }
+    acc += double(part);
+  }
+  double v[1] = {acc}, o[1];
+  if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
+  const double pq = o[0];
+  if (!(pq > 0.0) || !isfinite(pq)) {
+    S->breakdown = 1;
+    S->status = kErrBreakdown;
+    S->done = 1;
+  } else {
+    S->alpha = S->rz / pq;
+  }
+}
+
+// inner body: x32 += alpha p, r32 -= alpha q, |r32|^2; the loop control
+__global__ void __launch_bounds__(kGThreads) g_upd(const GArgs a) {
+  GState* S = a.S;
+  count_kernel(S);
+  if (S->breakdown) {
+    if (blockIdx.x == 0 && ftid() == 0) cudaGraphSetConditional(a.h_in, 0u);
+    return;
+  }
+  const float alpha = float(S->alpha);
+  const float* pnew = S->cur ? a.p1 : a.p0;
+  const size_t n4 = a.n / 4;
+  const float4* p4 = reinterpret_cast<const float4*>(pnew);
+  const float4* q4 = reinterpret_cast<const float4*>(a.q32);
+  float4* d4 = reinterpret_cast<float4*>(a.d32);
+  float4* r4 = reinterpret_cast<float4*>(a.r32);
+  double acc = 0.0;
+  for (size_t e = vtid(); e < n4; e += vstride()) {
+    const float4 pv = p4[e], qv = q4[e];
+    float4 dv = d4[e], rv = r4[e];
+    dv.x = fmaf(alpha, pv.x, dv.x);
+    dv.y = fmaf(alpha, pv.y, dv.y);
+    dv.z = fmaf(alpha, pv.z, dv.z);
+    dv.w = fmaf(alpha, pv.w, dv.w);
+    rv.x = fmaf(-alpha, qv.x, rv.x);
+    rv.y = fmaf(-alpha, qv.y, rv.y);
+    rv.z = fmaf(-alpha, qv.z, rv.z);
+    rv.w = fmaf(-alpha, qv.w, rv.w);
+    d4[e] = dv;
+    r4[e] = rv;
+    acc += double(fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, fmaf(rv.z, rv.z, rv.w * rv.w))));
+  }
+  double v[1] = {acc}, o[1];
+  if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
+  const double rz_new = o[0];
+  S->first = 0;
+  S->cur ^= 1;
+  S->iters += 1;
+  S->pending = 1;
+  if (rz_new <= S->delta2 * S->rz_ref || rz_new <= S->tol2) {
+    S->refine = 1;  // beta of the next direction comes from the replaced residual
+    cudaGraphSetConditional(a.h_in, 0u);
+    return;
+  }
+  S->beta = rz_new / S->rz;
+  S->rz = rz_new;
+  if (S->iters >= a.max_iters) {
+    S->done = 1;
+    cudaGraphSetConditional(a.h_in, 0u);
+  } else {
+    cudaGraphSetConditional(a.h_in, 1u);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// epilogue: x = x + pending x32 (0 when b = 0), sum(x) for the gauge; then
+// the gauge shift and the statistics
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kGThreads) g_finish(const GArgs a) {
+  GState* S = a.S;
+  count_kernel(S);
+  const bool zero = S->bb == 0.0;
+  const bool fold = S->pending != 0;
+  double s = 0.0;
+  for (size_t e = vtid(); e < a.n; e += vstride()) {
+    double xv = zero ? 0.0 : a.x[e];
+    if (!zero && fold) xv += double(a.d32[e]);
+    if (zero || fold) a.x[e] = xv;
+    s += xv;
+  }
+  double v[1] = {s}, o[1];
+  if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
+  S->pending = 0;
+  S->gshift = a.gauge ? a.gauge_value - o[0] / double(a.n) : 0.0;
+}
+
+__global__ void __launch_bounds__(kGThreads) g_shift(const GArgs a) {
+  GState* S = a.S;
+  count_kernel(S);
+  if (a.gauge) {
+    const double sh = S->gshift;
+    for (size_t e = vtid(); e < a.n; e += vstride()) a.x[e] += sh;
+  }
+  if (blockIdx.x == 0 && ftid() == 0) {
+    DevSolveStats* st = a.stats;
+    st->iters = S->iters;
+    st->outer_iters = S->refinements;
+    st->restarts = 0;
+    st->status = S->status;
+    st->b_norm = sqrt(S->bb);
+    st->rel_resid = S->bb > 0.0 ? sqrt(S->rr / S->bb) : 0.0;
+  }
+}
+
+// One resident wave of `kernel`, at most kGMax blocks and `work` items.
+template <typename K>
+int wave_blocks(K kernel, size_t work) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kGThreads, 0);
+  size_t b = size_t(sms > 0 ? sms : 1) * size_t(per_sm > 0 ? per_sm : 1);
+  if (b > size_t(kGMax)) b = kGMax;
+  if (b > work) b = work;
+  return int(b < 1 ? 1 : b);
+}
+
+bool same_args(const IrArgs& x, const IrArgs& y) {
+  return x.g.mx == y.g.mx && x.g.my == y.g.my && x.g.mz == y.g.mz && x.x == y.x && x.b == y.b && x.r == y.r &&
+         x.r32 == y.r32 && x.d32 == y.d32 && x.p0_32 == y.p0_32 && x.p1_32 == y.p1_32 && x.q32 == y.q32 &&
+         x.zero_x0 == y.zero_x0 && x.remove_mean == y.remove_mean && x.gauge == y.gauge &&
+         x.gauge_value == y.gauge_value && x.rtol == y.rtol && x.delta == y.delta && x.max_iters == y.max_iters &&
+         x.max_outer == y.max_outer && x.stats == y.stats;
+}
+
+}  // namespace
+
+struct IrGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  IrArgs key{};
+  GState* state = nullptr;
+};
+
+size_t ir_graph_state_bytes() { return kStateBytes + size_t(3) * kGMax * sizeof(double); }
+
+bool ir_graph_eligible(const IrArgs& a) { return a.g.mx % 4 == 0 && a.g.mx >= 4; }
+
+namespace {
+
+cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t* node, const cudaGraphNode_t* dep, void* fn, int blocks,
+                       dim3 block, GArgs* args) {
+  cudaKernelNodeParams kp{};
+  kp.func = fn;
+  kp.gridDim = dim3(unsigned(blocks));
+  kp.blockDim = block;
+  kp.sharedMemBytes = 0;
+  void* params[1] = {args};
+  kp.kernelParams = params;
+  kp.extra = nullptr;
+  return cudaGraphAddKernelNode(node, g, dep, dep ? 1 : 0, &kp);
+}
+
+cudaError_t add_while(cudaGraph_t g, cudaGraphNode_t* node, const cudaGraphNode_t* dep,
+                      cudaGraphConditionalHandle h, cudaGraph_t* body) {
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaError_t e = cudaGraphAddNode(node, g, dep, nullptr, dep ? 1 : 0, &np);
+  if (e == cudaSuccess) *body = np.conditional.phGraph_out[0];
+  return e;
+}
+
+cudaError_t build(IrGraph* G, const IrArgs& ia, void* state_buf) {
+  GArgs a{};
+  a.mx = ia.g.mx;
+  a.my = ia.g.my;
+  a.mz = ia.g.mz;
+  a.n = size_t(a.mx) * a.my * a.mz;
+  a.x = ia.x;
+  a.b = ia.b;
+  a.r = ia.r;
+  a.r32 = ia.r32;
+  a.d32 = ia.d32;
+  a.p0 = ia.p0_32;
+  a.p1 = ia.p1_32;
+  a.q32 = ia.q32;
+  a.zero_x0 = ia.zero_x0;
+  a.remove_mean = ia.remove_mean;
+  a.gauge = ia.gauge;
+  a.gauge_value = ia.gauge_value;
+  a.rtol = ia.rtol;
+  a.delta = ia.delta;
+  a.max_iters = ia.max_iters;
+  a.max_outer = ia.max_outer;
+  a.S = static_cast<GState*>(state_buf);
+  a.part = reinterpret_cast<double*>(static_cast<char*>(state_buf) + kStateBytes);
+  a.stats = ia.stats;
+  a.w32x = (a.mx / 4 + 31) / 32;
+  a.w32y = (a.my + 7) / 8;
+  a.w32z = (a.mz + kZ32 - 1) / kZ32;
+  a.w64x = (a.mx + 31) / 32;
+  a.w64y = a.w32y;
+  a.w64z = (a.mz + kZ64 - 1) / kZ64;
+  const size_t items32 = size_t(a.w32x) * a.w32y * a.w32z;
+  const size_t items64 = size_t(a.w64x) * a.w64y * a.w64z;
+  const size_t vec_work = (a.n / 4 + kGThreads - 1) / kGThreads;
+  const dim3 tile(32, 8), flat(kGThreads);
+
+  cudaGraph_t top = nullptr;
+  cudaError_t e = cudaGraphCreate(&top, 0);
+  if (e != cudaSuccess) return e;
+  G->graph = top;
+  if ((e = cudaGraphConditionalHandleCreate(&a.h_out, top, 0u, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
+
+  cudaGraphNode_t n0, n1, n2, n3, n4, n5, n6;
+  cudaMemsetParams mp{};
+  mp.dst = &a.S->counter;
+  mp.value = 0;
+  mp.elementSize = 4;
+  mp.width = 1;
+  mp.height = 1;
+  if ((e = cudaGraphAddMemsetNode(&n0, top, nullptr, 0, &mp)) != cudaSuccess) return e;
+  if ((e = add_kernel(top, &n1, &n0, (void*)g_pro_sum, wave_blocks(g_pro_sum, vec_work), flat, &a)) != cudaSuccess)
+    return e;
+  if ((e = add_kernel(top, &n2, &n1, (void*)g_resid64<0>, wave_blocks(g_resid64<0>, items64), tile, &a)) !=
+      cudaSuccess)
+    return e;
+  cudaGraph_t outer = nullptr, inner = nullptr;
+  if ((e = add_while(top, &n3, &n2, a.h_out, &outer)) != cudaSuccess) return e;
+  if ((e = cudaGraphConditionalHandleCreate(&a.h_in, outer, 0u, 0u)) != cudaSuccess) return e;
+  cudaGraphNode_t b1, b2, b3, i1, i2;
+  if ((e = add_kernel(outer, &b1, nullptr, (void*)g_prep, wave_blocks(g_prep, vec_work), flat, &a)) != cudaSuccess)
+    return e;
+  if ((e = add_while(outer, &b2, &b1, a.h_in, &inner)) != cudaSuccess) return e;
+  if ((e = add_kernel(inner, &i1, nullptr, (void*)g_dir, wave_blocks(g_dir, items32), tile, &a)) != cudaSuccess)
+    return e;
+  if ((e = add_kernel(inner, &i2, &i1, (void*)g_upd, wave_blocks(g_upd, vec_work), flat, &a)) != cudaSuccess)
+    return e;
+  if ((e = add_kernel(outer, &b3, &b2, (void*)g_resid64<1>, wave_blocks(g_resid64<1>, items64), tile, &a)) !=
+      cudaSuccess)
+    return e;
+  if ((e = add_kernel(top, &n4, &n3, (void*)g_resid64<2>, wave_blocks(g_resid64<2>, items64), tile, &a)) !=
+      cudaSuccess)
+    return e;
+  if ((e = add_kernel(top, &n5, &n4, (void*)g_finish, wave_blocks(g_finish, vec_work), flat, &a)) != cudaSuccess)
+    return e;
+  if ((e = add_kernel(top, &n6, &n5, (void*)g_shift, wave_blocks(g_shift, vec_work), flat, &a)) != cudaSuccess)
+    return e;
+  return cudaGraphInstantiate(&G->exec, top, 0);
+}
+
+void release(IrGraph* G) {
+  if (G->exec) cudaGraphExecDestroy(G->exec);
+  if (G->graph) cudaGraphDestroy(G->graph);
+  G->exec = nullptr;
+  G->graph = nullptr;
+}
+
+}  // namespace
+
+void destroy_ir_graph(IrGraph* G) {
+  if (!G) return;
+  release(G);
+  delete G;
+}
+
+cudaError_t launch_ir_graph(const IrArgs& a, void* state_buf, IrGraph** cache, cudaStream_t s) {
+  IrGraph* G = *cache;
+  if (!G) {
+    G = new IrGraph();
+    *cache = G;
+  }
+  if (!G->exec || !same_args(G->key, a) || G->state != state_buf) {
+    release(G);
+    const cudaError_t e = build(G, a, state_buf);
+    if (e != cudaSuccess) {
+      release(G);
+      return e;
+    }
+    G->key = a;
+    G->state = static_cast<GState*>(state_buf);
+  }
+  return cudaGraphLaunch(G->exec, s);
+}
+
+cudaError_t ir_graph_kernel_count(const void* state_buf, cudaStream_t s, long long* out) {
+  const GState* S = static_cast<const GState*>(state_buf);
+  cudaError_t e = cudaMemcpyAsync(out, &S->kernels, sizeof(long long), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
+}
+
+}  // namespace cfd

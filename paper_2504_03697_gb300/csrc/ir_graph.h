@@ -1,0 +1,26 @@
+// Graph-driven mixed-precision pressure solve (see ir_graph.cu).  Internal.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "cfd_internal.h"
+
+namespace cfd {
+
+struct IrGraph;  // an instantiated graph, cached per workspace and arguments
+
+// Device bytes of the solver state and partial sums (16-byte aligned).
+size_t ir_graph_state_bytes();
+// The graph form needs mx % 4 == 0 (16-byte rows of the FP32 vectors).
+bool ir_graph_eligible(const IrArgs& a);
+// Enqueue one solve on s; builds (or rebuilds, when the arguments changed)
+// the graph in *cache.  Same results contract as launch_ir: statistics in
+// a.stats, x the solution.  a.ctrl, a.partials, a.tz and the TMA fields are
+// not used.
+cudaError_t launch_ir_graph(const IrArgs& a, void* state_buf, IrGraph** cache, cudaStream_t s);
+void destroy_ir_graph(IrGraph* g);
+// Kernels run so far by graph solves on this state buffer (synchronises s).
+cudaError_t ir_graph_kernel_count(const void* state_buf, cudaStream_t s, long long* out);
+
+}  // namespace cfd

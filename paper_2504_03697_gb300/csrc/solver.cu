@@ -1180,8 +1180,12 @@ __global__ void __launch_bounds__(kSolveThreads, 4) ir_kernel(const __grid_const
       cur ^= 1;
       ++iters;
       if (rz_new <= delta2 * rz_ref || rz_new <= tol2) {
-        // refinement in FP64: x += x32, r = b - A x (true residual)
-        for (size_t e = gtid(vb); e < n; e += gstride(vb)) a.x[e] += double(a.d32[e]);
+        // refinement in FP64: x += x32 (x32 cleared: an exit before the next
+        // preparation must not add it again), r = b - A x (true residual)
+        for (size_t e = gtid(vb); e < n; e += gstride(vb)) {
+          a.x[e] += double(a.d32[e]);
+          a.d32[e] = 0.f;
+        }
         acc[0] = acc[1] = acc[2] = 0.0;
         if (!allreduce(acc, tot)) return fail();  // x complete before the stencil reads it
         {

@@ -104,3 +104,174 @@ def test_ir_cavity_steps_converge(cfd):
     rc, stats = cav.step(5)
     assert rc == cfd.CFD_OK
     assert all(s["rel_resid"] <= 1e-8 and s["outer_iters"] >= 1 for s in stats[1:])
+
+
+# ----------------------------------------------------------------------------
+# graph form (cfd_set_ir_form GRAPH): the same method as device-side loops
+# over streaming kernels; judged by the same rules
+# ----------------------------------------------------------------------------
+def _graph_cavity(cfd, shape, form="graph", **kw):
+    cav = cfd.Cavity(cfd.make_params(*shape, solver="ir", **kw))
+    cav.set_ir_form(form)
+    return cav
+
+
+def _check_solution(shape, b, x, st, rtol=1e-8):
+    nx, ny, nz = shape
+    A = poisson_csr(nx, ny, nz)
+    bo = b.ravel() - b.mean()
+    true_rel = np.linalg.norm(bo - A @ x) / np.linalg.norm(bo)
+    assert true_rel <= rtol * 1.0001, true_rel
+    np.testing.assert_allclose(true_rel, st["rel_resid"], rtol=1e-6, atol=1e-14)
+    xo, so = pcg(A, bo, rtol=rtol, max_iters=10 ** 6)
+    d = (x - x.mean()) - (xo - xo.mean())
+    bound = 2 * rtol * np.linalg.norm(bo) / lam_min(shape)
+    assert np.linalg.norm(d) <= bound, (np.linalg.norm(d), bound)
+    return so
+
+
+@pytest.mark.parametrize("shape,delta", [((48, 40, 32), 0.0), ((64, 64, 64), 0.01), ((36, 20, 19), 0.3),
+                                         ((128, 24, 16), 0.0), ((4, 9, 5), 0.0), ((4, 1, 1), 0.0)])
+def test_ir_graph_true_residual_and_bound(cfd, shape, delta):
+    nx, ny, nz = shape
+    cav = _graph_cavity(cfd, shape, ir_delta=delta)
+    b = gaussian_rhs(nx, ny, nz, seed=4)
+    bg = torch.tensor(b, device="cuda")
+    xg = torch.zeros_like(bg)
+    l0 = cav.launch_count()
+    rc, st = cav.solve_pressure(bg, xg)
+    assert rc == cfd.CFD_OK, st
+    assert st["outer_iters"] >= 1
+    so = _check_solution(shape, b, xg.cpu().numpy().ravel(), st)
+    # kernels the graph ran: prologue 2, each outer pass 2, each FP32
+    # iteration 2, epilogue 3 (the loop structure as designed)
+    assert cav.launch_count() - l0 == 2 + 2 * (st["outer_iters"] + 1) + 2 * st["iters"] + 3
+    print(f"IR graph {shape}: inner {st['iters']} outer {st['outer_iters']} (FP64 CG {so.iters})")
+
+
+def test_ir_graph_matches_persistent_and_repeats_bitwise(cfd):
+    shape = (64, 48, 40)
+    nx, ny, nz = shape
+    b = gaussian_rhs(nx, ny, nz, seed=9)
+    bg = torch.tensor(b, device="cuda")
+    out = {}
+    for form in ("persistent", "graph", "graph"):
+        cav = _graph_cavity(cfd, shape, form=form)
+        xg = torch.zeros_like(bg)
+        rc, st = cav.solve_pressure(bg, xg)
+        assert rc == cfd.CFD_OK
+        out.setdefault(form, []).append((xg.cpu().numpy().ravel(), st))
+    xp, sp = out["persistent"][0]
+    (xg1, sg1), (xg2, sg2) = out["graph"]
+    assert np.array_equal(xg1, xg2) and sg1 == sg2
+    bound = 4 * 1e-8 * np.linalg.norm(b.ravel() - b.mean()) / lam_min(shape)
+    assert np.linalg.norm((xg1 - xg1.mean()) - (xp - xp.mean())) <= bound
+    assert abs(sg1["iters"] - sp["iters"]) <= max(3, sp["iters"] // 20)
+
+
+def test_ir_graph_warm_start_and_projection(cfd):
+    """The projection substep (warm start from p, gauge to mean 1) in the
+    graph form, against the FP64 oracle within the rtol bound."""
+    shape = (24, 20, 16)
+    nx, ny, nz = shape
+    cav = _graph_cavity(cfd, shape, dt=0.02, lid_u=1.0, warm_start=True)
+    ocav = OCav(nx, ny, nz, dt=0.02, lid_u=1.0)
+    f = []
+    for c in range(3):
+        a = uniform_field(ocav.face_shape(c), seed=8, stream=c)
+        ax = 2 - c
+        sl = [slice(None)] * 3
+        sl[ax] = 0
+        a[tuple(sl)] = 0.0
+        sl[ax] = -1
+        a[tuple(sl)] = 0.0
+        f.append(a)
+    for name, a in zip("uvw", f):
+        cav.set_field(name, a)
+    cav.set_field("p", 1.0 + 0.1 * uniform_field((nz, ny, nx), seed=2))
+    rc, st = cav.substep("project")
+    assert rc == cfd.CFD_OK and st["rel_resid"] <= 1e-8
+    b = fs.pressure_rhs(ocav, *f)
+    x, _ = fs.solve_pressure(ocav, b)
+    p_gpu = cav.read_field("p").numpy()
+    assert abs(p_gpu.mean() - 1.0) <= 1e-12
+    pbound = 2 * 1e-8 * np.linalg.norm(b) / lam_min(shape)
+    assert np.linalg.norm((p_gpu - p_gpu.mean()) - (x - x.mean())) <= pbound
+    u, v, w = (cav.read_field(n).numpy() for n in "uvw")
+    s = ocav.dt / (ocav.rho * ocav.h)
+    assert np.linalg.norm(fs.divergence_sum(u, v, w)) <= s * 1.01e-8 * np.linalg.norm(b)
+
+
+def test_ir_graph_edge_cases(cfd):
+    shape = (16, 12, 10)
+    nx, ny, nz = shape
+    # zero right-hand side: no iteration, x = 0
+    cav = _graph_cavity(cfd, shape)
+    bg = torch.zeros((nz, ny, nx), dtype=torch.float64, device="cuda")
+    xg = torch.full_like(bg, 5.0)
+    rc, st = cav.solve_pressure(bg, xg)
+    assert rc == cfd.CFD_OK and st["iters"] == 0 and st["rel_resid"] == 0.0
+    assert torch.count_nonzero(xg).item() == 0
+    # iteration cap: not converged, x holds the folded last iterate whose
+    # true residual is the one reported
+    cav = _graph_cavity(cfd, shape, max_iters=7)
+    b = gaussian_rhs(nx, ny, nz, seed=5)
+    bg = torch.tensor(b, device="cuda")
+    xg = torch.zeros_like(bg)
+    rc, st = cav.solve_pressure(bg, xg)
+    assert rc == cfd.CFD_ERR_NOT_CONVERGED and st["iters"] == 7
+    A = poisson_csr(nx, ny, nz)
+    bo = b.ravel() - b.mean()
+    true_rel = np.linalg.norm(bo - A @ xg.cpu().numpy().ravel()) / np.linalg.norm(bo)
+    np.testing.assert_allclose(true_rel, st["rel_resid"], rtol=1e-9)
+    assert 1e-8 < true_rel < 1.0
+    # a NaN in b: breakdown reported, no hang
+    cav = _graph_cavity(cfd, shape)
+    b[3, 4, 5] = np.nan
+    bg = torch.tensor(b, device="cuda")
+    rc, st = cav.solve_pressure(bg, torch.zeros_like(bg))
+    assert rc == cfd.CFD_ERR_BREAKDOWN
+
+
+def test_ir_graph_form_rejected_when_nx_not_multiple_of_four(cfd):
+    cav = cfd.Cavity(cfd.make_params(17, 8, 8, solver="ir"))
+    with pytest.raises(cfd.CfdError):
+        cav.set_ir_form("graph")
+    cav.set_ir_form("persistent")
+
+
+def test_ir_graph_cavity_steps(cfd):
+    cav = _graph_cavity(cfd, (32, 32, 32), dt=0.01, nu=0.001, lid_u=1.0)
+    rc, stats = cav.step(5)
+    assert rc == cfd.CFD_OK
+    assert all(s["rel_resid"] <= 1e-8 and s["outer_iters"] >= 1 for s in stats[1:])
+
+
+def test_ir_graph_full_size_256(cfd):
+    """256^3 standalone solve (the benchmarked size, automatic form = graph):
+    the true residual is recomputed from the oracle's matrix plane by plane
+    (a row of plane k touches planes k-1..k+1 only)."""
+    n = 256
+    cav = cfd.Cavity(cfd.make_params(n, n, n, solver="ir"))
+    b = gaussian_rhs(n, n, n, seed=0)
+    bg = torch.tensor(b, device="cuda")
+    xg = torch.zeros_like(bg)
+    l0 = cav.launch_count()
+    rc, st = cav.solve_pressure(bg, xg)
+    assert rc == cfd.CFD_OK
+    assert cav.launch_count() - l0 == 2 + 2 * (st["outer_iters"] + 1) + 2 * st["iters"] + 3
+    x = xg.cpu().numpy()
+    bo = b - b.mean()
+    A3, A2 = poisson_csr(n, n, 3), poisson_csr(n, n, 2)
+    rr = 0.0
+    for k in range(n):
+        if k == 0:
+            y = (A2 @ x[0:2].ravel()).reshape(2, n, n)[0]
+        elif k == n - 1:
+            y = (A2 @ x[n - 2:n].ravel()).reshape(2, n, n)[1]
+        else:
+            y = (A3 @ x[k - 1:k + 2].ravel()).reshape(3, n, n)[1]
+        rr += float(np.sum((bo[k] - y) ** 2))
+    true_rel = np.sqrt(rr) / np.linalg.norm(bo)
+    assert true_rel <= 1.0001e-8, true_rel
+    np.testing.assert_allclose(true_rel, st["rel_resid"], rtol=1e-6)

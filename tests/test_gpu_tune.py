@@ -29,9 +29,11 @@ def test_autotune_keeps_state_and_picks_a_listed_shape(cfd, n, solver):
     after = {f: torch.as_tensor(cav.read_field(f)) for f in "uvwp"}
     for f in "uvwp":
         assert torch.equal(before[f], after[f]), f
-    # CG: both forms x (automatic + 16 shapes); IR: the 17 shapes
-    assert rep["candidates"] == (34 if solver == "cg" else 17)
+    # CG: both forms x (automatic + 16 shapes); IR: the automatic form, the
+    # 17 shapes of the persistent form and the graph form (n % 4 == 0)
+    assert rep["candidates"] == (34 if solver == "cg" else 19)
     assert rep["cg_variant"] in (0, 1)
+    assert rep["ir_form"] in ((0,) if solver == "cg" else (0, 1, 2))
     assert (rep["blocks_per_sm"], rep["tile_depth"]) == (0, 0) or (
         rep["blocks_per_sm"] in (1, 2, 3, 4) and rep["tile_depth"] in (1, 2, 4, 8))
     assert 0 < rep["ms_best"] <= rep["ms_auto"]
