@@ -53,6 +53,7 @@ CG_FLOPS_PER_CELL_ITER = 17
 CG_BYTES_PER_CELL_ITER = 80
 CG_FLOPS_PER_CELL_SOLVE = 14
 CG_BYTES_PER_CELL_SOLVE = 72
+IR_BYTES_PER_CELL_ITER = 40
 
 
 def parse_args(argv=None):
@@ -365,6 +366,20 @@ def main_ours(args):
                 "hbm_peak_gbs": hbm_peak, "hbm_frac_of_measured": bytes_per_launch / pcg_avg_s / 1e9 / hbm_peak,
                 "launch_ms": pcg_avg_s * 1e3, "flops_per_launch": flops_per_launch,
                 "bytes_per_launch": bytes_per_launch}
+    if args.solver == "ir":
+        # the FP32 iterations stream 40 B per cell (direction: read r32, p_old,
+        # write p, q; update: read p, q, x32, r32, write x32, r32); the FP64
+        # refinements add a few residual passes, left out of the count
+        form = tune["ir_form"] if tune is not None else 0
+        graph = form == 2 or (form == 0 and n % 4 == 0 and cells >= 1 << 21)
+        ir_bytes = cells * IR_BYTES_PER_CELL_ITER * mean_iters
+        ir_gbs = ir_bytes / pcg_avg_s / 1e9
+        roofline = {"bound": "hbm",
+                    "kernel": ("g_dir + g_upd (FP32 CG iteration, graph form)" if graph
+                               else "ir_kernel (FP32 CG + FP64 refinement, persistent)"),
+                    "achieved": ir_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": ir_gbs / hbm_peak,
+                    "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                    "launch_ms": pcg_avg_s * 1e3, "bytes_per_launch": ir_bytes}
     phase_ms_per_step = {k: v[0] / max(args.steps, 1) for k, v in phases.items()}
 
     # end-to-end through the C-ABI with host buffers (state round-trips per step)
@@ -529,7 +544,7 @@ def main_poisson(args):
     n = args.poisson
     form = None if args.ir_form == "tuned" else args.ir_form
     res = time_solves(cfd, n, args.solver, list(range(args.steps)), args.warmup, args.max_iters, device,
-                      ir_form=form)
+                      autotune=not args.no_autotune, ir_form=form)
     ms = sorted(r["ms"] for r in res)
     line = {"metric": "time-to-rtol-1e-8 per solve", "value": statistics.median(ms), "unit": "ms",
             "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,

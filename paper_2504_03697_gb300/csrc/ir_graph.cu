@@ -313,12 +313,14 @@ __global__ void __launch_bounds__(kGThreads, 4) g_dir(const GArgs a) {
     if (j >= my) continue;  // the whole warp (one row per warp)
     const bool on = i4 < nx4;
     const bool has_w = i4 > 0, has_e = i4 + 1 < nx4;
-    const int k1 = min(k0 + kZ32, mz);
     size_t c4 = (size_t(k0) * my + j) * nx4 + (on ? i4 : nx4 - 1);
     float4 pc = P4(c4);
     float4 pm = k0 > 0 ? P4(c4 - sz4) : pc;
     float part = 0.f;
-    for (int k = k0; k < k1; ++k, c4 += sz4) {
+#pragma unroll
+    for (int kk = 0; kk < kZ32; ++kk) {
+      const int k = k0 + kk;
+      if (k >= mz) break;
       const float4 pp = k < mz - 1 ? P4(c4 + sz4) : pc;
       const float4 ps = j > 0 ? P4(c4 - sy4) : pc;
       const float4 pn = j < my - 1 ? P4(c4 + sy4) : pc;
@@ -343,6 +345,7 @@ __global__ void __launch_bounds__(kGThreads, 4) g_dir(const GArgs a) {
       }
       pm = pc;
       pc = pp;
+      c4 += sz4;
     }
     acc += double(part);
   }
