@@ -54,6 +54,7 @@ CG_BYTES_PER_CELL_ITER = 80
 CG_FLOPS_PER_CELL_SOLVE = 14
 CG_BYTES_PER_CELL_SOLVE = 72
 IR_BYTES_PER_CELL_ITER = 40
+IR_GRAPH_BYTES_PER_CELL_ITER = 32
 
 
 def parse_args(argv=None):
@@ -367,12 +368,13 @@ def main_ours(args):
                 "launch_ms": pcg_avg_s * 1e3, "flops_per_launch": flops_per_launch,
                 "bytes_per_launch": bytes_per_launch}
     if args.solver == "ir":
-        # the FP32 iterations stream 40 B per cell (direction: read r32, p_old,
-        # write p, q; update: read p, q, x32, r32, write x32, r32); the FP64
-        # refinements add a few residual passes, left out of the count
+        # bytes per cell and FP32 iteration: persistent form 40 (direction:
+        # read r32, p_old, write p, q; update: read p, q, x32, r32, write x32,
+        # r32); graph form 32 (q is formed again in the update, never stored);
+        # the FP64 refinements add a few residual passes, left out of the count
         form = tune["ir_form"] if tune is not None else 0
         graph = form == 2 or (form == 0 and n % 4 == 0 and cells >= 1 << 21)
-        ir_bytes = cells * IR_BYTES_PER_CELL_ITER * mean_iters
+        ir_bytes = cells * (IR_GRAPH_BYTES_PER_CELL_ITER if graph else IR_BYTES_PER_CELL_ITER) * mean_iters
         ir_gbs = ir_bytes / pcg_avg_s / 1e9
         roofline = {"bound": "hbm",
                     "kernel": ("g_dir + g_upd (FP32 CG iteration, graph form)" if graph

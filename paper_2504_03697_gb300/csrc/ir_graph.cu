@@ -9,8 +9,12 @@
 // is kept across a refinement; convergence only on the FP64 true residual.
 // What differs is the execution: instead of one cooperative kernel with two
 // grid barriers per iteration, every phase is its own streaming kernel
-// (float4 accesses, the operator on the fly from r32 and the previous p, x
-// neighbours by warp shuffles) and the loop control runs on the device:
+// (float4 accesses, x neighbours by warp shuffles) and the loop control runs
+// on the device.  The FP32 iteration moves 32 B per cell: the direction
+// kernel reads r32 and the previous p and writes p (forming p at the stencil
+// points on the fly and q = A p only for p.q); the update kernel forms q = A p
+// again from the stored p and reads and writes x32 and r32.  q is never
+// stored.
 //
 //   memset(counter) -> pro_sum -> pro_resid ->
 //   while (outer) { prep -> while (inner) { dir -> upd } -> refine } ->
@@ -280,32 +284,17 @@ __global__ void __launch_bounds__(kGThreads) g_prep(const GArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// inner body: p = r32 + beta p_old (on the fly at the 7 stencil points),
-// q = A p, p.q; alpha = rz / p.q
+// The FP32 operator over the work items of this block: for every cell of the
+// block's tiles, q = A v with v given by P4 (a float4 of four x-consecutive
+// cells) and P1 (one cell); `emit(c4, v, q)` receives the centre values.
+// One warp covers 128 x cells of one row; x neighbours by warp shuffles,
+// y neighbours by loads, z by marching kZ32 planes in registers.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kGThreads, 4) g_dir(const GArgs a) {
-  GState* S = a.S;
-  count_kernel(S);
-  const bool first = S->first != 0;
-  const float beta = float(S->beta);
-  const int cur = S->cur;
-  float* pnew = cur ? a.p1 : a.p0;
-  const float* pold = cur ? a.p0 : a.p1;
-  const int mx = a.mx, my = a.my, mz = a.mz, nx4 = mx >> 2;
+template <typename F4, typename F1, typename E>
+__device__ __forceinline__ void march_f32(const GArgs& a, F4 P4, F1 P1, E emit) {
+  const int my = a.my, mz = a.mz, nx4 = a.mx >> 2;
   const size_t sy4 = size_t(nx4), sz4 = size_t(nx4) * my;
-  const float4* r4 = reinterpret_cast<const float4*>(a.r32);
-  const float4* o4 = reinterpret_cast<const float4*>(pold);
-  float4* p4 = reinterpret_cast<float4*>(pnew);
-  float4* q4 = reinterpret_cast<float4*>(a.q32);
-  auto P4 = [&](size_t e) {
-    const float4 rv = __ldg(r4 + e);
-    if (first) return rv;
-    const float4 ov = __ldg(o4 + e);
-    return make_float4(fmaf(beta, ov.x, rv.x), fmaf(beta, ov.y, rv.y), fmaf(beta, ov.z, rv.z), fmaf(beta, ov.w, rv.w));
-  };
-  auto P1 = [&](size_t e) { return first ? __ldg(a.r32 + e) : fmaf(beta, __ldg(pold + e), __ldg(a.r32 + e)); };
   const int lane = threadIdx.x;
-  double acc = 0.0;
   const int items = a.w32x * a.w32y * a.w32z;
   for (int w = blockIdx.x; w < items; w += gridDim.x) {
     const int wx = w % a.w32x, wy = (w / a.w32x) % a.w32y, wz = w / (a.w32x * a.w32y);
@@ -313,10 +302,9 @@ __global__ void __launch_bounds__(kGThreads, 4) g_dir(const GArgs a) {
     if (j >= my) continue;  // the whole warp (one row per warp)
     const bool on = i4 < nx4;
     const bool has_w = i4 > 0, has_e = i4 + 1 < nx4;
-    size_t c4 = (size_t(k0) * my + j) * nx4 + (on ? i4 : nx4 - 1);
+    size_t c4 = (size_t(k0) * my + j) * nx4 + (on ? i4 : nx4 - 1);  // idle lanes shadow the last column
     float4 pc = P4(c4);
     float4 pm = k0 > 0 ? P4(c4 - sz4) : pc;
-    float part = 0.f;
 #pragma unroll
     for (int kk = 0; kk < kZ32; ++kk) {
       const int k = k0 + kk;
@@ -335,20 +323,41 @@ __global__ void __launch_bounds__(kGThreads, 4) g_dir(const GArgs a) {
       q.y = fmaf(6.f, pc.y, -(((((pc.x + pc.z) + ps.y) + pn.y) + pm.y) + pp.y));
       q.z = fmaf(6.f, pc.z, -(((((pc.y + pc.w) + ps.z) + pn.z) + pm.z) + pp.z));
       q.w = fmaf(6.f, pc.w, -(((((pc.z + east) + ps.w) + pn.w) + pm.w) + pp.w));
-      if (on) {
-        p4[c4] = pc;
-        q4[c4] = q;
-        part = fmaf(pc.x, q.x, part);
-        part = fmaf(pc.y, q.y, part);
-        part = fmaf(pc.z, q.z, part);
-        part = fmaf(pc.w, q.w, part);
-      }
+      if (on) emit(c4, pc, q);
       pm = pc;
       pc = pp;
       c4 += sz4;
     }
-    acc += double(part);
   }
+}
+
+// inner body: p = r32 + beta p_old (formed at the 7 stencil points from r32
+// and the previous p), stored; q = A p only for p.q (not stored: the update
+// forms it again from the stored p, with the same operations, so the same
+// bits); alpha = rz / p.q
+__global__ void __launch_bounds__(kGThreads, 4) g_dir(const GArgs a) {
+  GState* S = a.S;
+  count_kernel(S);
+  const bool first = S->first != 0;
+  const float beta = float(S->beta);
+  const int cur = S->cur;
+  float* pnew = cur ? a.p1 : a.p0;
+  const float* pold = cur ? a.p0 : a.p1;
+  const float4* r4 = reinterpret_cast<const float4*>(a.r32);
+  const float4* o4 = reinterpret_cast<const float4*>(pold);
+  float4* p4 = reinterpret_cast<float4*>(pnew);
+  auto P4 = [&](size_t e) {
+    const float4 rv = __ldg(r4 + e);
+    if (first) return rv;
+    const float4 ov = __ldg(o4 + e);
+    return make_float4(fmaf(beta, ov.x, rv.x), fmaf(beta, ov.y, rv.y), fmaf(beta, ov.z, rv.z), fmaf(beta, ov.w, rv.w));
+  };
+  auto P1 = [&](size_t e) { return first ? __ldg(a.r32 + e) : fmaf(beta, __ldg(pold + e), __ldg(a.r32 + e)); };
+  double acc = 0.0;
+  march_f32(a, P4, P1, [&](size_t c4, const float4& pc, const float4& q) {
+    p4[c4] = pc;
+    acc += double(fmaf(pc.x, q.x, fmaf(pc.y, q.y, fmaf(pc.z, q.z, pc.w * q.w))));
+  });
   double v[1] = {acc}, o[1];
   if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
   const double pq = o[0];
@@ -361,8 +370,9 @@ __global__ void __launch_bounds__(kGThreads, 4) g_dir(const GArgs a) {
   }
 }
 
-// inner body: x32 += alpha p, r32 -= alpha q, |r32|^2; the loop control
-__global__ void __launch_bounds__(kGThreads) g_upd(const GArgs a) {
+// inner body: q = A p again from the stored p, x32 += alpha p, r32 -= alpha q,
+// |r32|^2; the loop control
+__global__ void __launch_bounds__(kGThreads, 4) g_upd(const GArgs a) {
   GState* S = a.S;
   count_kernel(S);
   if (S->breakdown) {
@@ -371,15 +381,14 @@ __global__ void __launch_bounds__(kGThreads) g_upd(const GArgs a) {
   }
   const float alpha = float(S->alpha);
   const float* pnew = S->cur ? a.p1 : a.p0;
-  const size_t n4 = a.n / 4;
   const float4* p4 = reinterpret_cast<const float4*>(pnew);
-  const float4* q4 = reinterpret_cast<const float4*>(a.q32);
   float4* d4 = reinterpret_cast<float4*>(a.d32);
   float4* r4 = reinterpret_cast<float4*>(a.r32);
+  auto P4 = [&](size_t e) { return __ldg(p4 + e); };
+  auto P1 = [&](size_t e) { return __ldg(pnew + e); };
   double acc = 0.0;
-  for (size_t e = vtid(); e < n4; e += vstride()) {
-    const float4 pv = p4[e], qv = q4[e];
-    float4 dv = d4[e], rv = r4[e];
+  march_f32(a, P4, P1, [&](size_t c4, const float4& pv, const float4& qv) {
+    float4 dv = d4[c4], rv = r4[c4];
     dv.x = fmaf(alpha, pv.x, dv.x);
     dv.y = fmaf(alpha, pv.y, dv.y);
     dv.z = fmaf(alpha, pv.z, dv.z);
@@ -388,10 +397,10 @@ __global__ void __launch_bounds__(kGThreads) g_upd(const GArgs a) {
     rv.y = fmaf(-alpha, qv.y, rv.y);
     rv.z = fmaf(-alpha, qv.z, rv.z);
     rv.w = fmaf(-alpha, qv.w, rv.w);
-    d4[e] = dv;
-    r4[e] = rv;
+    d4[c4] = dv;
+    r4[c4] = rv;
     acc += double(fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, fmaf(rv.z, rv.z, rv.w * rv.w))));
-  }
+  });
   double v[1] = {acc}, o[1];
   if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
   const double rz_new = o[0];
@@ -579,7 +588,7 @@ cudaError_t build(IrGraph* G, const IrArgs& ia, void* state_buf) {
   if ((e = add_while(outer, &b2, &b1, a.h_in, &inner)) != cudaSuccess) return e;
   if ((e = add_kernel(inner, &i1, nullptr, (void*)g_dir, wave_blocks(g_dir, items32), tile, &a)) != cudaSuccess)
     return e;
-  if ((e = add_kernel(inner, &i2, &i1, (void*)g_upd, wave_blocks(g_upd, vec_work), flat, &a)) != cudaSuccess)
+  if ((e = add_kernel(inner, &i2, &i1, (void*)g_upd, wave_blocks(g_upd, items32), tile, &a)) != cudaSuccess)
     return e;
   if ((e = add_kernel(outer, &b3, &b2, (void*)g_resid64<1>, wave_blocks(g_resid64<1>, items64), tile, &a)) !=
       cudaSuccess)
