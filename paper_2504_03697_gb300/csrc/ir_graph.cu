@@ -11,10 +11,10 @@
 // grid barriers per iteration, every phase is its own streaming kernel
 // (float4 accesses, x neighbours by warp shuffles) and the loop control runs
 // on the device.  The FP32 iteration moves 32 B per cell: the direction
-// kernel reads r32 and the previous p and writes p (forming p at the stencil
-// points on the fly and q = A p only for p.q); the update kernel forms q = A p
-// again from the stored p and reads and writes x32 and r32.  q is never
-// stored.
+// kernel reads r32 and the previous p and writes p (forming p on the fly at
+// the +x, +y, +z neighbours too, for p.Ap as a sum of squared differences
+// over the grid's edges); the update kernel forms q = A p from the stored p
+// and reads and writes x32 and r32.  q is never stored.
 //
 //   memset(counter) -> pro_sum -> pro_resid ->
 //   while (outer) { prep -> while (inner) { dir -> upd } -> refine } ->
@@ -331,10 +331,11 @@ __device__ __forceinline__ void march_f32(const GArgs& a, F4 P4, F1 P1, E emit) 
   }
 }
 
-// inner body: p = r32 + beta p_old (formed at the 7 stencil points from r32
-// and the previous p), stored; q = A p only for p.q (not stored: the update
-// forms it again from the stored p, with the same operations, so the same
-// bits); alpha = rz / p.q
+// inner body: p = r32 + beta p_old, stored; p.Ap as the sum over the grid's
+// edges of (p_i - p_j)^2 (the Neumann matrix has n_c on the diagonal and -1
+// per in-box neighbour, so p.Ap = sum over neighbour pairs of the squared
+// difference), which needs p only at the +x, +y and +z neighbours; alpha =
+// rz / p.Ap.  One warp covers 128 x cells of one row, +x by warp shuffles.
 __global__ void __launch_bounds__(kGThreads, 4) g_dir(const GArgs a) {
   GState* S = a.S;
   count_kernel(S);
@@ -353,11 +354,43 @@ __global__ void __launch_bounds__(kGThreads, 4) g_dir(const GArgs a) {
     return make_float4(fmaf(beta, ov.x, rv.x), fmaf(beta, ov.y, rv.y), fmaf(beta, ov.z, rv.z), fmaf(beta, ov.w, rv.w));
   };
   auto P1 = [&](size_t e) { return first ? __ldg(a.r32 + e) : fmaf(beta, __ldg(pold + e), __ldg(a.r32 + e)); };
+  auto sq = [](float d) { return d * d; };
+  const int my = a.my, mz = a.mz, nx4 = a.mx >> 2;
+  const size_t sy4 = size_t(nx4), sz4 = size_t(nx4) * my;
+  const int lane = threadIdx.x;
   double acc = 0.0;
-  march_f32(a, P4, P1, [&](size_t c4, const float4& pc, const float4& q) {
-    p4[c4] = pc;
-    acc += double(fmaf(pc.x, q.x, fmaf(pc.y, q.y, fmaf(pc.z, q.z, pc.w * q.w))));
-  });
+  const int items = a.w32x * a.w32y * a.w32z;
+  for (int w = blockIdx.x; w < items; w += gridDim.x) {
+    const int wx = w % a.w32x, wy = (w / a.w32x) % a.w32y, wz = w / (a.w32x * a.w32y);
+    const int i4 = wx * 32 + lane, j = wy * 8 + threadIdx.y, k0 = wz * kZ32;
+    if (j >= my) continue;  // the whole warp (one row per warp)
+    const bool on = i4 < nx4;
+    const bool has_e = i4 + 1 < nx4;
+    size_t c4 = (size_t(k0) * my + j) * nx4 + (on ? i4 : nx4 - 1);  // idle lanes shadow the last column
+    float4 pc = P4(c4);
+#pragma unroll
+    for (int kk = 0; kk < kZ32; ++kk) {
+      const int k = k0 + kk;
+      if (k >= mz) break;
+      const bool up = k < mz - 1;
+      const float4 pp = up ? P4(c4 + sz4) : pc;
+      const float4 pn = j < my - 1 ? P4(c4 + sy4) : pc;
+      float east = __shfl_down_sync(0xffffffffu, pc.x, 1);
+      if (lane == 31) east = has_e ? P1(4 * c4 + 4) : pc.w;
+      else if (!has_e) east = pc.w;
+      if (on) {
+        p4[c4] = pc;
+        // x edges inside the float4 and to the east cell (0 at the wall),
+        // y edges to the next row, z edges to the next plane (0 at walls)
+        float e = sq(pc.x - pc.y) + sq(pc.y - pc.z) + sq(pc.z - pc.w) + sq(pc.w - east);
+        e += (sq(pc.x - pn.x) + sq(pc.y - pn.y)) + (sq(pc.z - pn.z) + sq(pc.w - pn.w));
+        e += (sq(pc.x - pp.x) + sq(pc.y - pp.y)) + (sq(pc.z - pp.z) + sq(pc.w - pp.w));
+        acc += double(e);
+      }
+      pc = pp;
+      c4 += sz4;
+    }
+  }
   double v[1] = {acc}, o[1];
   if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
   const double pq = o[0];

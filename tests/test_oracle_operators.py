@@ -40,6 +40,17 @@ def test_poisson_symmetric_integer_rowsum(shape):
     assert np.array_equal(-off.sum(axis=1), d)
 
 
+
+@pytest.mark.parametrize("shape", [(1, 1, 5), (3, 4, 5), (8, 6, 7)])
+def test_poisson_energy_is_sum_over_grid_edges(shape):
+    """p.Ap equals the sum of (p_i - p_j)^2 over the pairs of face-adjacent
+    cells (counted once): the form the GPU direction kernel reduces."""
+    nx, ny, nz = shape
+    A = poisson_csr(nx, ny, nz)
+    p = np.random.default_rng(3).standard_normal((nz, ny, nx))
+    edges = sum(float(np.sum(np.diff(p, axis=ax) ** 2)) for ax in range(3))
+    assert float(p.ravel() @ (A @ p.ravel())) == pytest.approx(edges, rel=1e-13)
+
 @pytest.mark.parametrize("shape", SHAPES)
 def test_poisson_spectrum_closed_form(shape):
     A = poisson_csr(*shape).toarray()
