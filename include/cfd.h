@@ -181,8 +181,10 @@ int cfd_solve_pressure(cfd_handle *h, const double *b_dev, double *x_dev, cfd_so
  * paper's SpMV (Sec. 3.1, Table 1 "spmv"), matrix-free. */
 int cfd_apply_poisson(cfd_handle *h, const double *x_dev, double *y_dev);
 
-/* Number of kernel launches this handle has issued since creation
- * (for launch accounting in benchmarks). */
+/* Number of kernels this handle has run since creation (for launch
+ * accounting in benchmarks).  Kernels inside the graph form of the
+ * mixed-precision solve are counted on the device; when that form has run,
+ * the call synchronises the handle's stream to read the count. */
 int64_t cfd_launch_count(const cfd_handle *h);
 
 /* Launch shape of the persistent CG solves (the knobs the autotuner

@@ -57,6 +57,7 @@ struct GState {
   unsigned counter;  // arrivals of the current kernel (atomicInc wraps to 0)
   unsigned pad2;
   long long kernels;  // kernels run by all graph solves of this workspace (never reset)
+  DevSolveStats out;  // statistics of the last solve (copied to the caller's slot)
 };
 
 constexpr size_t kStateBytes = 256;
@@ -79,7 +80,6 @@ struct GArgs {
   int max_iters, max_outer;
   GState* S;
   double* part;  // 3 * kGMax doubles
-  DevSolveStats* stats;
   cudaGraphConditionalHandle h_out, h_in;
   int w32x, w32y, w32z;  // FP32 work items: float4 columns / 32, rows / 8, planes / kZ32
   int w64x, w64y, w64z;  // FP64 work items: columns / 32, rows / 8, planes / kZ64
@@ -486,7 +486,7 @@ __global__ void __launch_bounds__(kGThreads) g_shift(const GArgs a) {
     for (size_t e = vtid(); e < a.n; e += vstride()) a.x[e] += sh;
   }
   if (blockIdx.x == 0 && ftid() == 0) {
-    DevSolveStats* st = a.stats;
+    DevSolveStats* st = &S->out;
     st->iters = S->iters;
     st->outer_iters = S->refinements;
     st->restarts = 0;
@@ -514,7 +514,7 @@ bool same_args(const IrArgs& x, const IrArgs& y) {
          x.r32 == y.r32 && x.d32 == y.d32 && x.p0_32 == y.p0_32 && x.p1_32 == y.p1_32 && x.q32 == y.q32 &&
          x.zero_x0 == y.zero_x0 && x.remove_mean == y.remove_mean && x.gauge == y.gauge &&
          x.gauge_value == y.gauge_value && x.rtol == y.rtol && x.delta == y.delta && x.max_iters == y.max_iters &&
-         x.max_outer == y.max_outer && x.stats == y.stats;
+         x.max_outer == y.max_outer;
 }
 
 }  // namespace
@@ -581,7 +581,6 @@ cudaError_t build(IrGraph* G, const IrArgs& ia, void* state_buf) {
   a.max_outer = ia.max_outer;
   a.S = static_cast<GState*>(state_buf);
   a.part = reinterpret_cast<double*>(static_cast<char*>(state_buf) + kStateBytes);
-  a.stats = ia.stats;
   a.w32x = (a.mx / 4 + 31) / 32;
   a.w32y = (a.my + 7) / 8;
   a.w32z = (a.mz + kZ32 - 1) / kZ32;
@@ -667,7 +666,12 @@ cudaError_t launch_ir_graph(const IrArgs& a, void* state_buf, IrGraph** cache, c
     G->key = a;
     G->state = static_cast<GState*>(state_buf);
   }
-  return cudaGraphLaunch(G->exec, s);
+  cudaError_t e = cudaGraphLaunch(G->exec, s);
+  // the graph writes its statistics to a fixed slot, so that the caller's
+  // per-step slot does not force a new graph
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(a.stats, &G->state->out, sizeof(DevSolveStats), cudaMemcpyDeviceToDevice, s);
+  return e;
 }
 
 cudaError_t ir_graph_kernel_count(const void* state_buf, cudaStream_t s, long long* out) {
