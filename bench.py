@@ -53,6 +53,11 @@ CG_FLOPS_PER_CELL_ITER = 17
 CG_BYTES_PER_CELL_ITER = 80
 CG_FLOPS_PER_CELL_SOLVE = 14
 CG_BYTES_PER_CELL_SOLVE = 72
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of
+# cg1_fp64_kernel<8> on the 64^3 cavity in its automatic shape (128 blocks,
+# tile depth 8), from one ncu capture of the pressure solve of the first timed
+# step: the 26 MB working set is L2-resident, so DRAM sees almost nothing
+CG1_CAVITY64_DRAM_BYTES = 2342400 + 84992
 IR_BYTES_PER_CELL_ITER = 40
 IR_GRAPH_BYTES_PER_CELL_ITER = 32
 
@@ -357,11 +362,14 @@ def main_ours(args):
     fp64_peak_tflops = 1.20  # FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (measured with DFMA chains)
     achieved_tflops = flops_per_launch / pcg_avg_s / 1e12
     variant = tune["cg_variant"] if tune is not None else (0 if args.cg_variant == "single" else 1)
+    auto_shape = tune is None or (tune["blocks_per_sm"] == 0 and tune["tile_depth"] == 0)
     roofline = {"bound": "alu",
                 "kernel": ("cg1_fp64_kernel (pressure CG, single reduction per iteration, persistent)" if variant == 0
                            else "cg_fp64_kernel (pressure CG, two reductions per iteration, persistent)"),
                 "achieved": achieved_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved_tflops / fp64_peak_tflops, "traffic": None,
+                "frac": achieved_tflops / fp64_peak_tflops,
+                "traffic": (CG1_CAVITY64_DRAM_BYTES if (args.workload == "cavity64" and variant == 0
+                                                         and args.solver == "cg" and auto_shape) else None),
                 "peak_source": "FP64 FMA rate from the recipe's unit counts and clocks (1.2-1.25 TFLOP/s)",
                 "hbm_achieved_gbs": bytes_per_launch / pcg_avg_s / 1e9,
                 "hbm_peak_gbs": hbm_peak, "hbm_frac_of_measured": bytes_per_launch / pcg_avg_s / 1e9 / hbm_peak,
