@@ -105,7 +105,9 @@ typedef struct {
   int32_t max_iters;        /* CG iteration cap per solve; 0 -> 20 * max(n)       */
   int32_t warm_start;       /* 1: start the pressure solve from the previous p    */
   double ir_delta;          /* IR: refine in FP64 each time the FP32 residual has
-                               fallen by this factor, in (0, 1); 0 -> 0.1          */
+                               fallen by this factor, in (0, 1); 0 -> 0.1 for the
+                               pressure solve, 1e-4 for the diffusion solves of
+                               the graph form (well-conditioned systems)          */
   int32_t advect_order;     /* backtrace: 0 or 1 explicit Euler x - dt v(x); 2 the
                                explicit midpoint rule x - dt v(x - dt/2 v(x))     */
   int32_t reserved[7];      /* must be zero                                       */
@@ -219,6 +221,9 @@ int cfd_set_cg_variant(cfd_handle *h, int variant);
  *               and the loop conditions.  Needs nx % 4 == 0.
  *   AUTO        (default) GRAPH when nx % 4 == 0 and the grid has at least
  *               2^21 cells, PERSISTENT otherwise.
+ * In the GRAPH form the three diffusion solves of the step (nu > 0) also
+ * run as FP32 CG with FP64 refinement on the velocity matrices (scalar-lane
+ * kernels, any width); in the PERSISTENT form they are FP64 CG.
  * Errors: unknown form; GRAPH with nx % 4 != 0.  Batches always use the
  * persistent multi-problem kernel. */
 enum { CFD_IR_AUTO = 0, CFD_IR_PERSISTENT = 1, CFD_IR_GRAPH = 2 };

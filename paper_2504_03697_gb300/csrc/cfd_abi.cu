@@ -79,11 +79,13 @@ Layout ws_layout(const cfd_params& p, int max_blocks) {
   L.e2 = take(vec * 8);
   if (p.solver == CFD_SOLVER_DIC) L.dicd = take(cells * 8);  // DIC pivots of the pressure matrix
   if (p.solver == CFD_SOLVER_IR) {
-    L.r32 = take(cells * 4);
-    L.d32 = take(cells * 4);
-    L.p0_32 = take(cells * 4);
-    L.p1_32 = take(cells * 4);
-    L.q32 = take(cells * 4);
+    // sized to the largest face grid: the graph form also runs the
+    // diffusion solves in FP32 with FP64 refinement
+    L.r32 = take(vec * 4);
+    L.d32 = take(vec * 4);
+    L.p0_32 = take(vec * 4);
+    L.p1_32 = take(vec * 4);
+    L.q32 = take(vec * 4);
     L.irg = take(ir_graph_state_bytes());
   }
   L.partials = take(partials_doubles(max_blocks) * 8);  // double-buffered block + group partials
@@ -113,7 +115,8 @@ struct cfd_handle {
   cfd_unet* precond_net = nullptr;  // CFD_SOLVER_FPCG
   float *r32, *d32, *p0_32, *p1_32, *q32;
   void* irg_state = nullptr;     // graph solve state (CFD_SOLVER_IR)
-  cfd::IrGraph* irg = nullptr;   // its cached, instantiated graph
+  cfd::IrGraph* irg = nullptr;   // its cached, instantiated graph (pressure)
+  cfd::IrGraph* irg_diff[3] = {nullptr, nullptr, nullptr};  // diffusion of u, v, w
   int ir_form = CFD_IR_AUTO;
   double* partials;
   SolveCtrl* ctrl;
@@ -282,17 +285,6 @@ IrArgs pressure_ir_args(const cfd_handle* h, double* x, int zero_x0, int gauge, 
   return a;
 }
 
-// Velocity diffusion solve for component comp (x = intermediate velocity).
-int run_diffusion(cfd_handle* h, int comp, DevSolveStats* st) {
-  PhysArgs pa = phys(h);
-  int rc = cuda_check(h, launch_diffusion_rhs(pa, comp, h->stream, &h->launches), "diffusion rhs");
-  if (rc) return rc;
-  const CgArgs a = diffusion_args(h, comp, st, h->ctrl);
-  rc = cuda_check(h, cudaMemsetAsync(h->ctrl, 0, sizeof(SolveCtrl), h->stream), "memset ctrl");
-  if (rc) return rc;
-  return cuda_check(h, launch_cg(a, h->lg, h->stream, &h->launches), "diffusion CG launch");
-}
-
 // Graph form of the mixed-precision solve: on request, or automatically on
 // grids of at least kIrGraphCells cells (where its streaming kernels beat the
 // persistent kernel's two grid barriers per iteration).
@@ -301,7 +293,47 @@ constexpr size_t kIrGraphCells = size_t(1) << 21;
 bool use_ir_graph(const cfd_handle* h, const IrArgs& a) {
   if (!h->irg_state || !ir_graph_eligible(a) || h->ir_form == CFD_IR_PERSISTENT) return false;
   if (h->ir_form == CFD_IR_GRAPH) return true;
-  return size_t(a.g.mx) * a.g.my * a.g.mz >= kIrGraphCells;
+  return size_t(h->prm.nx) * h->prm.ny * h->prm.nz >= kIrGraphCells;
+}
+
+// The diffusion solve of component comp as FP32 CG with FP64 refinement
+// (graph form of CFD_SOLVER_IR): x0 = the advected field, b from
+// diffusion_rhs, the velocity matrix I + c L; no mean removal or gauge.
+IrArgs diffusion_ir_args(const cfd_handle* h, int comp, DevSolveStats* st) {
+  const double hh = h->prm.length / h->prm.nx;
+  IrArgs a{};
+  a.g = GridDims{h->prm.nx + (comp == 0), h->prm.ny + (comp == 1), h->prm.nz + (comp == 2)};
+  a.kind = kOpVelU + comp;
+  a.c = h->prm.nu * h->prm.dt / (hh * hh);
+  a.x = comp == 0 ? h->ua : (comp == 1 ? h->va : h->wa);
+  a.b = h->b; a.r = h->r;
+  a.r32 = h->r32; a.d32 = h->d32; a.p0_32 = h->p0_32; a.p1_32 = h->p1_32; a.q32 = h->q32;
+  a.zero_x0 = 0; a.remove_mean = 0; a.gauge = 0; a.gauge_value = 0.0;
+  a.rtol = h->prm.rtol;
+  // I + c L is well conditioned (eigenvalues in [1, 1 + 12 c]): the FP32
+  // recurrence may run four decades between refinements
+  a.delta = h->prm.ir_delta > 0 ? h->prm.ir_delta : 1e-4;
+  a.max_iters = iter_cap(h->prm);
+  a.max_outer = 1000;
+  a.timeout_ns = kTimeoutNs;
+  a.stats = st;
+  return a;
+}
+
+// Velocity diffusion solve for component comp (x = intermediate velocity).
+int run_diffusion(cfd_handle* h, int comp, DevSolveStats* st) {
+  PhysArgs pa = phys(h);
+  int rc = cuda_check(h, launch_diffusion_rhs(pa, comp, h->stream, &h->launches), "diffusion rhs");
+  if (rc) return rc;
+  if (h->prm.solver == CFD_SOLVER_IR) {
+    const IrArgs ia = diffusion_ir_args(h, comp, st);
+    if (use_ir_graph(h, ia))
+      return cuda_check(h, launch_ir_graph(ia, h->irg_state, &h->irg_diff[comp], h->stream), "IR diffusion graph");
+  }
+  const CgArgs a = diffusion_args(h, comp, st, h->ctrl);
+  rc = cuda_check(h, cudaMemsetAsync(h->ctrl, 0, sizeof(SolveCtrl), h->stream), "memset ctrl");
+  if (rc) return rc;
+  return cuda_check(h, launch_cg(a, h->lg, h->stream, &h->launches), "diffusion CG launch");
 }
 
 // Pressure solve A x = b on the handle's workspace b (already filled).
@@ -553,6 +585,7 @@ void cfd_destroy(cfd_handle* h) {
   }
   if (h->snap) cudaFreeHost(h->snap);
   destroy_ir_graph(h->irg);
+  for (cfd::IrGraph* g : h->irg_diff) destroy_ir_graph(g);
   delete h;
 }
 
@@ -944,7 +977,8 @@ int cfd_pressure_rhs(cfd_handle* h, double* b_dev) {
 int64_t cfd_launch_count(const cfd_handle* h) {
   if (!h) return 0;
   long long graph_kernels = 0;
-  if (h->irg && h->irg_state && ir_graph_kernel_count(h->irg_state, h->stream, &graph_kernels) != cudaSuccess)
+  const bool graphs = h->irg || h->irg_diff[0] || h->irg_diff[1] || h->irg_diff[2];
+  if (graphs && h->irg_state && ir_graph_kernel_count(h->irg_state, h->stream, &graph_kernels) != cudaSuccess)
     graph_kernels = 0;
   return h->launches + graph_kernels;
 }

@@ -77,6 +77,8 @@ struct CgArgs {
 // Arguments of the FP32-inner / FP64-outer iterative-refinement solve.
 struct IrArgs {
   GridDims g;
+  int kind;        // kOp* operator (the persistent form supports kOpPressure only)
+  double c;        // nu dt / h^2 of the velocity operators
   double* x;       // FP64 solution (out)
   double* b;       // FP64 rhs (mean removed in place)
   double* r;       // FP64 outer residual

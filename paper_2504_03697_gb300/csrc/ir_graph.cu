@@ -29,7 +29,9 @@
 // pass of the inner body raises `iters` by one and the outer body stops the
 // loops once iters >= max_iters or refinements > max_outer.
 //
-// Requires mx % 4 == 0 (16-byte rows of the FP32 vectors).
+// Operators: the pressure matrix (float4 kernels, mx % 4 == 0) and the
+// velocity matrices of the diffusion substep (scalar-lane kernels, any
+// width; no mean removal, their matrices being nonsingular).
 
 #include <cstdint>
 #include <cstring>
@@ -37,6 +39,7 @@
 #include "cfd_common.cuh"
 #include "cfd_internal.h"
 #include "ir_graph.h"
+#include "operator_rows.cuh"
 
 namespace cfd {
 namespace {
@@ -81,7 +84,10 @@ struct GArgs {
   GState* S;
   double* part;  // 3 * kGMax doubles
   cudaGraphConditionalHandle h_out, h_in;
-  int w32x, w32y, w32z;  // FP32 work items: float4 columns / 32, rows / 8, planes / kZ32
+  int kind;              // kOp* operator
+  double c;              // nu dt / h^2 (velocity operators)
+  float c32;
+  int w32x, w32y, w32z;  // FP32 work items: (float4 or scalar) columns / 32, rows / 8, planes / kZ32
   int w64x, w64y, w64z;  // FP64 work items: columns / 32, rows / 8, planes / kZ64
 };
 
@@ -205,7 +211,7 @@ __global__ void __launch_bounds__(kGThreads) g_resid64(const GArgs a) {
       const double xe = i < mx - 1 ? X(c + 1) : xc;
       const double xs = j > 0 ? X(c - sy) : xc;
       const double xn = j < my - 1 ? X(c + sy) : xc;
-      const double ax = fma(6.0, xc, -(((((xw + xe) + xs) + xn) + xm) + xp));
+      const double ax = stencil_row<double>(a.kind, a.c, i, j, k, mx, my, mz, xc, xw, xe, xs, xn, xm, xp);
       double bv = a.b[c];
       if (MODE == 0) {
         bv -= shift;
@@ -257,7 +263,8 @@ __global__ void __launch_bounds__(kGThreads) g_prep(const GArgs a) {
   const bool ok = S->rr <= S->tol2;
   const bool leave = ok || S->refinements > a.max_outer || S->iters >= a.max_iters;
   const bool fold = S->pending != 0;
-  const double rmean = S->rsum / double(a.n);
+  // the singular pressure system works on zero-mean residuals
+  const double rmean = a.kind == kOpPressure ? S->rsum / double(a.n) : 0.0;
   float f = 0.f;
   for (size_t e = vtid(); e < a.n; e += vstride()) {
     if (fold) a.x[e] += double(a.d32[e]);
@@ -457,6 +464,115 @@ __global__ void __launch_bounds__(kGThreads, 4) g_upd(const GArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Scalar-lane form of the inner body, for any operator kind and any width
+// (the velocity matrices of the diffusion solves; their face grids are one
+// cell wider along their own axis): one thread per x cell, x and y
+// neighbours through L1, z by marching.  `emit(c, v, q)` returns the FP32
+// contribution of cell c to the kernel's dot product; per work item the
+// contributions are summed in FP32, then in FP64.
+// ---------------------------------------------------------------------------
+template <typename F1, typename E>
+__device__ __forceinline__ double march_s32(const GArgs& a, F1 P, E emit) {
+  const int mx = a.mx, my = a.my, mz = a.mz;
+  const size_t sy = size_t(mx), sz = size_t(mx) * my;
+  double acc = 0.0;
+  const int items = a.w32x * a.w32y * a.w32z;
+  for (int w = blockIdx.x; w < items; w += gridDim.x) {
+    const int wx = w % a.w32x, wy = (w / a.w32x) % a.w32y, wz = w / (a.w32x * a.w32y);
+    const int i = wx * 32 + threadIdx.x, j = wy * 8 + threadIdx.y, k0 = wz * kZ32;
+    if (i >= mx || j >= my) continue;
+    size_t c = (size_t(k0) * my + j) * mx + i;
+    float xc = P(c);
+    float xm = k0 > 0 ? P(c - sz) : xc;
+    float part = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < kZ32; ++kk) {
+      const int k = k0 + kk;
+      if (k >= mz) break;
+      const float xp = k < mz - 1 ? P(c + sz) : xc;
+      const float xw = i > 0 ? P(c - 1) : xc;
+      const float xe = i < mx - 1 ? P(c + 1) : xc;
+      const float xs = j > 0 ? P(c - sy) : xc;
+      const float xn = j < my - 1 ? P(c + sy) : xc;
+      const float q = stencil_row<float>(a.kind, a.c32, i, j, k, mx, my, mz, xc, xw, xe, xs, xn, xm, xp);
+      part += emit(c, xc, q);
+      xm = xc;
+      xc = xp;
+      c += sz;
+    }
+    acc += double(part);
+  }
+  return acc;
+}
+
+// inner body (scalar lanes): p = r32 + beta p_old, stored; p.q with q = A p
+// formed on the fly (not stored); alpha = rz / p.q
+__global__ void __launch_bounds__(kGThreads, 4) g_dir_s(const GArgs a) {
+  GState* S = a.S;
+  count_kernel(S);
+  const bool first = S->first != 0;
+  const float beta = float(S->beta);
+  const int cur = S->cur;
+  float* pnew = cur ? a.p1 : a.p0;
+  const float* pold = cur ? a.p0 : a.p1;
+  auto P = [&](size_t e) { return first ? __ldg(a.r32 + e) : fmaf(beta, __ldg(pold + e), __ldg(a.r32 + e)); };
+  const double acc = march_s32(a, P, [&](size_t c, float pc, float q) {
+    pnew[c] = pc;
+    return pc * q;
+  });
+  double v[1] = {acc}, o[1];
+  if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
+  const double pq = o[0];
+  if (!(pq > 0.0) || !isfinite(pq)) {
+    S->breakdown = 1;
+    S->status = kErrBreakdown;
+    S->done = 1;
+  } else {
+    S->alpha = S->rz / pq;
+  }
+}
+
+// inner body (scalar lanes): q = A p again from the stored p, x32 += alpha p,
+// r32 -= alpha q, |r32|^2; the loop control
+__global__ void __launch_bounds__(kGThreads, 4) g_upd_s(const GArgs a) {
+  GState* S = a.S;
+  count_kernel(S);
+  if (S->breakdown) {
+    if (blockIdx.x == 0 && ftid() == 0) cudaGraphSetConditional(a.h_in, 0u);
+    return;
+  }
+  const float alpha = float(S->alpha);
+  const float* pnew = S->cur ? a.p1 : a.p0;
+  auto P = [&](size_t e) { return __ldg(pnew + e); };
+  const double acc = march_s32(a, P, [&](size_t c, float pc, float q) {
+    a.d32[c] = fmaf(alpha, pc, a.d32[c]);
+    const float rv = fmaf(-alpha, q, a.r32[c]);
+    a.r32[c] = rv;
+    return rv * rv;
+  });
+  double v[1] = {acc}, o[1];
+  if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
+  const double rz_new = o[0];
+  S->first = 0;
+  S->cur ^= 1;
+  S->iters += 1;
+  S->pending = 1;
+  if (rz_new <= S->delta2 * S->rz_ref || rz_new <= S->tol2) {
+    S->refine = 1;
+    cudaGraphSetConditional(a.h_in, 0u);
+    return;
+  }
+  S->beta = rz_new / S->rz;
+  S->rz = rz_new;
+  if (S->iters >= a.max_iters) {
+    S->done = 1;
+    cudaGraphSetConditional(a.h_in, 0u);
+  } else {
+    cudaGraphSetConditional(a.h_in, 1u);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // epilogue: x = x + pending x32 (0 when b = 0), sum(x) for the gauge; then
 // the gauge shift and the statistics
 // ---------------------------------------------------------------------------
@@ -514,7 +630,7 @@ bool same_args(const IrArgs& x, const IrArgs& y) {
          x.r32 == y.r32 && x.d32 == y.d32 && x.p0_32 == y.p0_32 && x.p1_32 == y.p1_32 && x.q32 == y.q32 &&
          x.zero_x0 == y.zero_x0 && x.remove_mean == y.remove_mean && x.gauge == y.gauge &&
          x.gauge_value == y.gauge_value && x.rtol == y.rtol && x.delta == y.delta && x.max_iters == y.max_iters &&
-         x.max_outer == y.max_outer;
+         x.max_outer == y.max_outer && x.kind == y.kind && x.c == y.c;
 }
 
 }  // namespace
@@ -528,7 +644,11 @@ struct IrGraph {
 
 size_t ir_graph_state_bytes() { return kStateBytes + size_t(3) * kGMax * sizeof(double); }
 
-bool ir_graph_eligible(const IrArgs& a) { return a.g.mx % 4 == 0 && a.g.mx >= 4; }
+bool ir_graph_eligible(const IrArgs& a) { return a.kind != kOpPressure || (a.g.mx % 4 == 0 && a.g.mx >= 4); }
+
+namespace {
+bool use_vec_kernels(const IrArgs& a) { return a.kind == kOpPressure && a.g.mx % 4 == 0; }
+}  // namespace
 
 namespace {
 
@@ -581,7 +701,11 @@ cudaError_t build(IrGraph* G, const IrArgs& ia, void* state_buf) {
   a.max_outer = ia.max_outer;
   a.S = static_cast<GState*>(state_buf);
   a.part = reinterpret_cast<double*>(static_cast<char*>(state_buf) + kStateBytes);
-  a.w32x = (a.mx / 4 + 31) / 32;
+  a.kind = ia.kind;
+  a.c = ia.c;
+  a.c32 = float(ia.c);
+  const bool vec = use_vec_kernels(ia);
+  a.w32x = vec ? (a.mx / 4 + 31) / 32 : (a.mx + 31) / 32;
   a.w32y = (a.my + 7) / 8;
   a.w32z = (a.mz + kZ32 - 1) / kZ32;
   a.w64x = (a.mx + 31) / 32;
@@ -618,10 +742,17 @@ cudaError_t build(IrGraph* G, const IrArgs& ia, void* state_buf) {
   if ((e = add_kernel(outer, &b1, nullptr, (void*)g_prep, wave_blocks(g_prep, vec_work), flat, &a)) != cudaSuccess)
     return e;
   if ((e = add_while(outer, &b2, &b1, a.h_in, &inner)) != cudaSuccess) return e;
-  if ((e = add_kernel(inner, &i1, nullptr, (void*)g_dir, wave_blocks(g_dir, items32), tile, &a)) != cudaSuccess)
-    return e;
-  if ((e = add_kernel(inner, &i2, &i1, (void*)g_upd, wave_blocks(g_upd, items32), tile, &a)) != cudaSuccess)
-    return e;
+  if (vec) {
+    if ((e = add_kernel(inner, &i1, nullptr, (void*)g_dir, wave_blocks(g_dir, items32), tile, &a)) != cudaSuccess)
+      return e;
+    if ((e = add_kernel(inner, &i2, &i1, (void*)g_upd, wave_blocks(g_upd, items32), tile, &a)) != cudaSuccess)
+      return e;
+  } else {
+    if ((e = add_kernel(inner, &i1, nullptr, (void*)g_dir_s, wave_blocks(g_dir_s, items32), tile, &a)) != cudaSuccess)
+      return e;
+    if ((e = add_kernel(inner, &i2, &i1, (void*)g_upd_s, wave_blocks(g_upd_s, items32), tile, &a)) != cudaSuccess)
+      return e;
+  }
   if ((e = add_kernel(outer, &b3, &b2, (void*)g_resid64<1>, wave_blocks(g_resid64<1>, items64), tile, &a)) !=
       cudaSuccess)
     return e;

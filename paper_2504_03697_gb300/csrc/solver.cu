@@ -39,6 +39,7 @@
 #include <mutex>
 
 #include "cfd_internal.h"
+#include "operator_rows.cuh"
 
 namespace cfd {
 
@@ -53,39 +54,6 @@ constexpr int kTileH = kTileY + 2;
 constexpr int kMaxTz = 8;     // deepest tile (cells per thread along z)
 constexpr int kTileSlots = kTileW * kTileH * (kMaxTz + 2);
 constexpr int kRegCells = 8;  // own cells per thread kept in registers (register path)
-
-template <typename T>
-__device__ __forceinline__ T stencil_row(int kind, T c, int i, int j, int k, int mx, int my, int mz, T xc,
-                                         T xm, T xp, T ym, T yp, T zm, T zp) {
-  if (kind == kOpPressure) {
-    if (i == 0) xm = xc;
-    if (i == mx - 1) xp = xc;
-    if (j == 0) ym = xc;
-    if (j == my - 1) yp = xc;
-    if (k == 0) zm = xc;
-    if (k == mz - 1) zp = xc;
-    return fma(T(6), xc, -(((((xm + xp) + ym) + yp) + zm) + zp));
-  }
-  const int comp = kind - 1;
-  const bool wall_row = (comp == 0) ? (i == 0 || i == mx - 1)
-                                    : (comp == 1) ? (j == 0 || j == my - 1) : (k == 0 || k == mz - 1);
-  if (wall_row) return T(0);
-  const T g = -xc;
-  if (comp != 0) {
-    if (i == 0) xm = g;
-    if (i == mx - 1) xp = g;
-  }
-  if (comp != 1) {
-    if (j == 0) ym = g;
-    if (j == my - 1) yp = g;
-  }
-  if (comp != 2) {
-    if (k == 0) zm = g;
-    if (k == mz - 1) zp = g;
-  }
-  const T lap = fma(T(6), xc, -(((((xm + xp) + ym) + yp) + zm) + zp));
-  return fma(c, lap, xc);
-}
 
 // Number of in-box neighbours of a pressure cell (the diagonal of A).
 __device__ __forceinline__ int neighbour_count(int i, int j, int k, int mx, int my, int mz) {
