@@ -58,6 +58,7 @@ CG_BYTES_PER_CELL_SOLVE = 72
 # tile depth 8), from one ncu capture of the pressure solve of the first timed
 # step: the 26 MB working set is L2-resident, so DRAM sees almost nothing
 CG1_CAVITY64_DRAM_BYTES = 2342400 + 84992
+CG1_CAVITY64_SHAPE = {"blocks": 128, "tile_depth": 8, "register_path": True}
 IR_BYTES_PER_CELL_ITER = 40
 IR_GRAPH_BYTES_PER_CELL_ITER = 32
 
@@ -90,6 +91,9 @@ def parse_args(argv=None):
                     help="execution of the mixed-precision solve in --poisson mode (default: the autotuner's choice)")
     ap.add_argument("--blas", type=int, default=0,
                     help="time the stand-alone building blocks on an N^3 grid: FP32 operator, FP64 / FP32 CG update")
+    ap.add_argument("--concurrent-diffusion", choices=["on", "off"], default="on",
+                    help="run the u, v, w diffusion solves of a step at once (grids up to 2^21 cells; "
+                         "the library's default there)")
     ap.add_argument("--advect-order", type=int, default=1, choices=[1, 2],
                     help="backtrace of the cavity workload: 1 explicit Euler (default), 2 explicit midpoint")
     ap.add_argument("--unet", type=int, default=0,
@@ -308,6 +312,8 @@ def main_ours(args):
     for name, f in zip("uvw", init):
         cav.set_field(name, f)
     cav.set_cg_variant(args.cg_variant)
+    if args.concurrent_diffusion == "off":
+        cav.set_concurrent_diffusion(False)
     # solver shape for this grid (blocks per SM x tile depth), picked by
     # timing fixed-length solves; outside the timed region, state untouched
     tune = None if args.no_autotune else cav.autotune(iters=50)
@@ -362,14 +368,17 @@ def main_ours(args):
     fp64_peak_tflops = 1.20  # FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (measured with DFMA chains)
     achieved_tflops = flops_per_launch / pcg_avg_s / 1e12
     variant = tune["cg_variant"] if tune is not None else (0 if args.cg_variant == "single" else 1)
-    auto_shape = tune is None or (tune["blocks_per_sm"] == 0 and tune["tile_depth"] == 0)
+    # the launch the captured counters belong to: 128 blocks, register path, tile depth 8
+    pressure_shape = cav.solver_shape(0)
     roofline = {"bound": "alu",
                 "kernel": ("cg1_fp64_kernel (pressure CG, single reduction per iteration, persistent)" if variant == 0
                            else "cg_fp64_kernel (pressure CG, two reductions per iteration, persistent)"),
                 "achieved": achieved_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved_tflops / fp64_peak_tflops,
                 "traffic": (CG1_CAVITY64_DRAM_BYTES if (args.workload == "cavity64" and variant == 0
-                                                         and args.solver == "cg" and auto_shape) else None),
+                                                         and args.solver == "cg"
+                                                         and pressure_shape == CG1_CAVITY64_SHAPE) else None),
+                "launch_shape": pressure_shape,
                 "peak_source": "FP64 FMA rate from the recipe's unit counts and clocks (1.2-1.25 TFLOP/s)",
                 "hbm_achieved_gbs": bytes_per_launch / pcg_avg_s / 1e9,
                 "hbm_peak_gbs": hbm_peak, "hbm_frac_of_measured": bytes_per_launch / pcg_avg_s / 1e9 / hbm_peak,
@@ -457,7 +466,8 @@ def main_ours(args):
                            "steps_per_rank": args.steps, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "l2": "flushed between timed steps (256 MiB write outside the timed events)",
                            "solver_shape": tune if tune is not None else "automatic",
-                           "cg_variant": args.cg_variant, "advect_order": args.advect_order},
+                           "cg_variant": args.cg_variant, "advect_order": args.advect_order,
+                           "concurrent_diffusion": args.concurrent_diffusion},
                 "solve": {"pcg_iters_mean": mean_iters, "pcg_iters_min": min(iters), "pcg_iters_max": max(iters),
                           "time_to_rtol_ms_mean": pcg_avg_s * 1e3, "rel_resid_max": worst_resid,
                           "all_converged": bool(ok)},

@@ -229,6 +229,17 @@ int cfd_set_cg_variant(cfd_handle *h, int variant);
 enum { CFD_IR_AUTO = 0, CFD_IR_PERSISTENT = 1, CFD_IR_GRAPH = 2 };
 int cfd_set_ir_form(cfd_handle *h, int form);
 
+/* Run the three diffusion solves of a step (nu > 0) at once (on = 1): u on
+ * the handle's stream, v and w on two internal streams forked from and
+ * joined back to it, each solve with its own solver vectors and a third of
+ * the co-resident blocks.  Same method, results within rounding of the
+ * sequential solves (their reductions run over other block counts).
+ * Available on grids of at most 2^21 cells with nu > 0 (the workspace then
+ * holds the two extra vector sets), where it is on from cfd_create; not
+ * used for the graph form of CFD_SOLVER_IR nor inside batches.  Errors: on
+ * not 0/1; on = 1 without that workspace. */
+int cfd_set_concurrent_diffusion(cfd_handle *h, int on);
+
 /* Autotuner of the solver shape for this handle's grid and solver: times
  * fixed-length pressure solves (iters iterations, a deterministic hashed
  * right-hand side) with the automatic shape and with every blocks_per_sm in

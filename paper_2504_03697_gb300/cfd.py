@@ -114,6 +114,7 @@ def load_library(path: Optional[str] = None):
         "cfd_autotune_solver": (ctypes.c_int, [vp, ctypes.c_int32, P(cfd_tune_report)]),
         "cfd_set_cg_variant": (ctypes.c_int, [vp, ctypes.c_int]),
         "cfd_set_ir_form": (ctypes.c_int, [vp, ctypes.c_int]),
+        "cfd_set_concurrent_diffusion": (ctypes.c_int, [vp, ctypes.c_int]),
         "cfd_snapshot": (ctypes.c_int, [vp]),
         "cfd_csr_bytes": (ctypes.c_int, [ctypes.c_int32] * 3 + [P(ctypes.c_size_t), P(ctypes.c_int64)]),
         "cfd_csr_assemble": (ctypes.c_int, [ctypes.c_int32] * 3 + [vp, vp]),
@@ -295,6 +296,10 @@ class Cavity:
     def set_cg_variant(self, variant: str):
         """'single' (one reduction per iteration, default) or 'two' (textbook)."""
         return self._check(self.lib.cfd_set_cg_variant(self.h, {"single": 0, "two": 1}[variant]))
+
+    def set_concurrent_diffusion(self, on: bool):
+        """Run the u, v, w diffusion solves of a step at once (small grids)."""
+        return self._check(self.lib.cfd_set_concurrent_diffusion(self.h, 1 if on else 0))
 
     def set_ir_form(self, form: str):
         """Execution of the IR solve: 'auto' (default), 'persistent' or 'graph'."""

@@ -43,6 +43,10 @@ struct Layout {
   size_t r32, d32, p0_32, p1_32, q32;
   size_t irg;  // state of the graph-driven mixed-precision solve
   size_t partials, ctrl, stats;
+  // concurrent diffusion solves (small grids): solver vectors b, r, d0, d1,
+  // q, e0, e1, e2, partial sums and a control block for the v and w solves
+  size_t cset[2][8], cpartials[2], cctrl[2];
+  bool conc;
   size_t total;
 };
 
@@ -50,7 +54,11 @@ size_t face_count(const cfd_params& p, int comp) {
   return size_t(p.nx + (comp == 0)) * size_t(p.ny + (comp == 1)) * size_t(p.nz + (comp == 2));
 }
 
-Layout ws_layout(const cfd_params& p, int max_blocks) {
+// Grids up to this many cells get workspace for running the three diffusion
+// solves of a step concurrently (they are latency-bound there).
+constexpr size_t kConcDiffusionCells = size_t(1) << 21;
+
+Layout ws_layout(const cfd_params& p, int max_blocks, bool standalone = true) {
   Layout L{};
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -91,6 +99,14 @@ Layout ws_layout(const cfd_params& p, int max_blocks) {
   L.partials = take(partials_doubles(max_blocks) * 8);  // double-buffered block + group partials
   L.ctrl = take(sizeof(SolveCtrl));
   L.stats = take(size_t(kStatsCap + 1) * sizeof(DevStepStats));  // ring + one slot for substep/solve calls
+  // batch members run their diffusion solves in the batch's multi-problem launch
+  L.conc = standalone && p.nu > 0.0 && cells <= kConcDiffusionCells;
+  if (L.conc)
+    for (int c = 0; c < 2; ++c) {
+      for (int v = 0; v < 8; ++v) L.cset[c][v] = take(vec * 8);
+      L.cpartials[c] = take(partials_doubles(max_blocks) * 8);
+      L.cctrl[c] = take(sizeof(SolveCtrl));
+    }
   L.total = off;
   return L;
 }
@@ -121,6 +137,13 @@ struct cfd_handle {
   double* partials;
   SolveCtrl* ctrl;
   DevStepStats* stats;
+  // concurrent diffusion solves of v and w (workspace slots, two streams)
+  double* cset[2][8] = {};
+  double* cpartials[2] = {nullptr, nullptr};
+  SolveCtrl* cctrl[2] = {nullptr, nullptr};
+  cudaStream_t aux[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+  bool conc_diffusion = false;   // enabled (cfd_set_concurrent_diffusion)
   LaunchGeom lg;
   int64_t launches;
   char err[256];
@@ -225,9 +248,30 @@ int tz_for(int mz) {
   return 0;
 }
 
+// The FP64 solver vectors (and partial-sum scratch) one CG solve works on.
+struct SolveVectors {
+  double *b, *r, *d0, *d1, *q, *e0, *e1, *e2, *partials;
+};
+
+SolveVectors main_vectors(const cfd_handle* h) {
+  return SolveVectors{h->b, h->r, h->d0, h->d1, h->q, h->e0, h->e1, h->e2, h->partials};
+}
+
+// The extra set k (0: v, 1: w) of the concurrent diffusion solves.
+SolveVectors extra_vectors(const cfd_handle* h, int k) {
+  double* const* v = h->cset[k];
+  return SolveVectors{v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], h->cpartials[k]};
+}
+
+CgArgs diffusion_args(const cfd_handle* h, int comp, DevSolveStats* st, SolveCtrl* ctrl, const SolveVectors& vs);
+
 // Arguments of the backward-Euler diffusion solve of component comp on the
 // intermediate velocity (x0 = the advected field, b from diffusion_rhs).
 CgArgs diffusion_args(const cfd_handle* h, int comp, DevSolveStats* st, SolveCtrl* ctrl) {
+  return diffusion_args(h, comp, st, ctrl, main_vectors(h));
+}
+
+CgArgs diffusion_args(const cfd_handle* h, int comp, DevSolveStats* st, SolveCtrl* ctrl, const SolveVectors& vs) {
   const double hh = h->prm.length / h->prm.nx;
   CgArgs a{};
   a.g = GridDims{h->prm.nx + (comp == 0), h->prm.ny + (comp == 1), h->prm.nz + (comp == 2)};
@@ -235,15 +279,15 @@ CgArgs diffusion_args(const cfd_handle* h, int comp, DevSolveStats* st, SolveCtr
   a.precond = 0;
   a.c = h->prm.nu * h->prm.dt / (hh * hh);
   a.x = comp == 0 ? h->ua : (comp == 1 ? h->va : h->wa);
-  a.b = h->b; a.r = h->r; a.d0 = h->d0; a.d1 = h->d1; a.q = h->q;
-  a.e0 = h->e0; a.e1 = h->e1; a.e2 = h->e2;
+  a.b = vs.b; a.r = vs.r; a.d0 = vs.d0; a.d1 = vs.d1; a.q = vs.q;
+  a.e0 = vs.e0; a.e1 = vs.e1; a.e2 = vs.e2;
   a.variant = h->lg.cg_variant;
   a.zero_x0 = 0; a.remove_mean = 0; a.gauge = 0; a.gauge_value = 0.0;
   a.rtol = h->prm.rtol;
   a.max_iters = iter_cap(h->prm);
   a.max_restarts = kMaxRestarts;
   a.timeout_ns = kTimeoutNs;
-  a.ctrl = ctrl; a.partials = h->partials; a.stats = st;
+  a.ctrl = ctrl; a.partials = vs.partials; a.stats = st;
   a.tz = tz_for(a.g.mz);
   return a;
 }
@@ -334,6 +378,47 @@ int run_diffusion(cfd_handle* h, int comp, DevSolveStats* st) {
   rc = cuda_check(h, cudaMemsetAsync(h->ctrl, 0, sizeof(SolveCtrl), h->stream), "memset ctrl");
   if (rc) return rc;
   return cuda_check(h, launch_cg(a, h->lg, h->stream, &h->launches), "diffusion CG launch");
+}
+
+// The three diffusion solves of a step at once: u on the handle's stream,
+// v and w on two auxiliary streams forked from and joined back to it, each
+// with its own solver vectors, partial sums and control block, each grid a
+// third of the co-resident blocks (so that the three cooperative grids fit
+// together).  The solves are independent (component c reads and writes only
+// its own intermediate field).
+int run_diffusion_concurrent(cfd_handle* h, DevStepStats* st) {
+  int rc = cuda_check(h, cudaEventRecord(h->ev_fork, h->stream), "fork event");
+  for (int k = 0; k < 2 && !rc; ++k) rc = cuda_check(h, cudaStreamWaitEvent(h->aux[k], h->ev_fork, 0), "fork wait");
+  LaunchGeom lg = h->lg;
+  lg.blocks = std::max(1, h->lg.blocks / 3);
+  lg.bps_req = 0;  // a tuned shape is for the whole device
+  lg.tz_req = 0;
+  for (int c = 0; c < 3 && !rc; ++c) {
+    cudaStream_t s = c == 0 ? h->stream : h->aux[c - 1];
+    const SolveVectors vs = c == 0 ? main_vectors(h) : extra_vectors(h, c - 1);
+    SolveCtrl* ctrl = c == 0 ? h->ctrl : h->cctrl[c - 1];
+    PhysArgs pa = phys(h);
+    pa.b = vs.b;
+    rc = cuda_check(h, launch_diffusion_rhs(pa, c, s, &h->launches), "diffusion rhs");
+    if (!rc) rc = cuda_check(h, cudaMemsetAsync(ctrl, 0, sizeof(SolveCtrl), s), "memset ctrl");
+    if (!rc) rc = cuda_check(h, launch_cg(diffusion_args(h, c, &st->d[c], ctrl, vs), lg, s, &h->launches), "diffusion CG");
+  }
+  // join even after a failure, so that nothing launched runs past the step
+  for (int k = 0; k < 2; ++k) {
+    const int r1 = cuda_check(h, cudaEventRecord(h->ev_join[k], h->aux[k]), "join event");
+    const int r2 = cuda_check(h, cudaStreamWaitEvent(h->stream, h->ev_join[k], 0), "join wait");
+    if (!rc) rc = r1 ? r1 : r2;
+  }
+  return rc;
+}
+
+bool diffusion_concurrent(const cfd_handle* h) {
+  if (!h->conc_diffusion || !h->aux[0] || !h->cset[0][0]) return false;
+  if (h->prm.solver == CFD_SOLVER_IR) {  // the graph form shares its FP32 vectors between the solves
+    const IrArgs ia = diffusion_ir_args(h, 0, nullptr);
+    if (use_ir_graph(h, ia)) return false;
+  }
+  return true;
 }
 
 // Pressure solve A x = b on the handle's workspace b (already filled).
@@ -433,7 +518,10 @@ int run_substep(cfd_handle* h, int which, DevStepStats* st) {
     case CFD_SUBSTEP_DIFFUSE:
       if (h->prm.nu > 0.0) {
         const int t = phase_begin(h, CFD_PHASE_DIFFUSE);
-        for (int c = 0; c < 3 && !rc; ++c) rc = run_diffusion(h, c, &st->d[c]);
+        if (diffusion_concurrent(h))
+          rc = run_diffusion_concurrent(h, st);
+        else
+          for (int c = 0; c < 3 && !rc; ++c) rc = run_diffusion(h, c, &st->d[c]);
         phase_end(h, t);
       }
       return rc;
@@ -518,14 +606,25 @@ int cfd_workspace_bytes(const cfd_params* params, size_t* bytes) {
   return CFD_OK;
 }
 
+namespace {
+int create_handle(const cfd_params* params, void* dev_ws, size_t bytes, cfd_stream_t stream, cfd_handle** out,
+                  bool standalone);
+}  // namespace
+
 int cfd_create(const cfd_params* params, void* dev_ws, size_t bytes, cfd_stream_t stream, cfd_handle** out) {
+  return create_handle(params, dev_ws, bytes, stream, out, true);
+}
+
+namespace {
+int create_handle(const cfd_params* params, void* dev_ws, size_t bytes, cfd_stream_t stream, cfd_handle** out,
+                  bool standalone) {
   int rc = validate(params);
   if (rc) return rc;
   if (!out) return set_err(nullptr, CFD_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!dev_ws) return set_err(nullptr, CFD_ERR_INVALID_ARG, "workspace is NULL");
   if (reinterpret_cast<uintptr_t>(dev_ws) & 255) return set_err(nullptr, CFD_ERR_INVALID_ARG, "workspace not 256-byte aligned");
-  Layout L = ws_layout(*params, kMaxBlocksBound);
+  Layout L = ws_layout(*params, kMaxBlocksBound, standalone);
   if (bytes < L.total)
     return set_err(nullptr, CFD_ERR_WORKSPACE_TOO_SMALL, "workspace %zu bytes < required %zu", bytes, L.total);
   cudaPointerAttributes attr{};
@@ -554,6 +653,12 @@ int cfd_create(const cfd_params* params, void* dev_ws, size_t bytes, cfd_stream_
   h->partials = D(L.partials);
   h->ctrl = reinterpret_cast<SolveCtrl*>(h->ws + L.ctrl);
   h->stats = reinterpret_cast<DevStepStats*>(h->ws + L.stats);
+  if (L.conc)
+    for (int c = 0; c < 2; ++c) {
+      for (int v = 0; v < 8; ++v) h->cset[c][v] = D(L.cset[c][v]);
+      h->cpartials[c] = D(L.cpartials[c]);
+      h->cctrl[c] = reinterpret_cast<SolveCtrl*>(h->ws + L.cctrl[c]);
+    }
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&h->lg.num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -568,13 +673,16 @@ int cfd_create(const cfd_params* params, void* dev_ws, size_t bytes, cfd_stream_
   rc = cuda_check(h, cudaMemsetAsync(h->ws, 0, L.total, h->stream), "memset workspace");
   if (!rc) rc = cuda_check(h, launch_fill(h->p, size_t(params->nx) * params->ny * params->nz, 1.0, h->stream, &h->launches),
                           "fill p");
+  // standalone cavities on small grids run their diffusion solves at once
+  if (!rc && L.conc) rc = cfd_set_concurrent_diffusion(h, 1);
   if (rc) {
-    delete h;
+    cfd_destroy(h);
     return rc;
   }
   *out = h;
   return CFD_OK;
 }
+}  // namespace
 
 void cfd_destroy(cfd_handle* h) {
   if (!h) return;
@@ -586,6 +694,14 @@ void cfd_destroy(cfd_handle* h) {
   if (h->snap) cudaFreeHost(h->snap);
   destroy_ir_graph(h->irg);
   for (cfd::IrGraph* g : h->irg_diff) destroy_ir_graph(g);
+  for (int k = 0; k < 2; ++k) {
+    if (h->aux[k]) {
+      cudaStreamSynchronize(h->aux[k]);
+      cudaStreamDestroy(h->aux[k]);
+    }
+    if (h->ev_join[k]) cudaEventDestroy(h->ev_join[k]);
+  }
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   delete h;
 }
 
@@ -983,6 +1099,24 @@ int64_t cfd_launch_count(const cfd_handle* h) {
   return h->launches + graph_kernels;
 }
 
+int cfd_set_concurrent_diffusion(cfd_handle* h, int on) {
+  if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
+  if (on != 0 && on != 1) return set_err(h, CFD_ERR_INVALID_ARG, "on must be 0 or 1");
+  if (on && !h->cset[0][0])
+    return set_err(h, CFD_ERR_INVALID_ARG, "concurrent diffusion needs nu > 0 and at most 2^21 cells");
+  if (on && !h->aux[0]) {
+    int rc = CFD_OK;
+    for (int k = 0; k < 2 && !rc; ++k) {
+      rc = cuda_check(h, cudaStreamCreateWithFlags(&h->aux[k], cudaStreamNonBlocking), "stream");
+      if (!rc) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_join[k], cudaEventDisableTiming), "event");
+    }
+    if (!rc) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "event");
+    if (rc) return rc;
+  }
+  h->conc_diffusion = on != 0;
+  return CFD_OK;
+}
+
 int cfd_set_ir_form(cfd_handle* h, int form) {
   if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
   if (form != CFD_IR_AUTO && form != CFD_IR_PERSISTENT && form != CFD_IR_GRAPH)
@@ -1100,7 +1234,7 @@ BatchLayout batch_layout(int n, const cfd_params* prm) {
   L.ctrl = take(sizeof(SolveCtrl) * 4 * size_t(n));
   L.stats = take(sizeof(DevSolveStats) * 4 * size_t(n));
   L.cav0 = off;
-  for (int i = 0; i < n; ++i) L.cav.push_back(take(ws_layout(prm[i], kMaxBlocksBound).total));
+  for (int i = 0; i < n; ++i) L.cav.push_back(take(ws_layout(prm[i], kMaxBlocksBound, false).total));
   L.total = off;
   return L;
 }
@@ -1229,9 +1363,9 @@ int cfd_batch_create(int n, const cfd_params* per_cavity, void* dev_ws, size_t b
   };
   for (int i = 0; i < n; ++i) {
     cfd_handle* h = nullptr;
-    rc = cfd_create(&per_cavity[i], b->ws + L.cav[size_t(i)], L.cav.size() > size_t(i) + 1 ? L.cav[size_t(i) + 1] - L.cav[size_t(i)]
-                                                                                            : L.total - L.cav[size_t(i)],
-                    stream, &h);
+    rc = create_handle(&per_cavity[i], b->ws + L.cav[size_t(i)],
+                       L.cav.size() > size_t(i) + 1 ? L.cav[size_t(i) + 1] - L.cav[size_t(i)] : L.total - L.cav[size_t(i)],
+                       stream, &h, false);
     if (rc) return fail(rc);
     b->cav.push_back(h);
     if (per_cavity[i].nu > 0.0) b->diff_idx.push_back(i);

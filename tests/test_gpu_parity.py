@@ -223,8 +223,10 @@ def test_project_parity(cfd, shape):
 # ----------------------------------------------------------------------------
 # whole steps
 # ----------------------------------------------------------------------------
-def _run_pair(cfd, shape, steps, seed, **kw):
+def _run_pair(cfd, shape, steps, seed, concurrent=False, **kw):
     cav, ocav = make(cfd, shape, **kw)
+    if concurrent:
+        cav.set_concurrent_diffusion(True)
     nx, ny, nz = shape
     init = cavity_perturbation(nx, ny, nz, seed=seed, amp=1e-3)
     _load(cav, init)
@@ -403,3 +405,36 @@ def test_cavity_warm_started_pressure(cfd):
     for name, e in errs.items():
         assert e < FP64_TOL, (name, e)
     assert sum(s["iters"] for s in stats[1:]) < sum(s["iters"] for s in stats[:1]) * (len(stats) - 1)
+
+
+
+# ----------------------------------------------------------------------------
+# the three diffusion solves run at once (cfd_set_concurrent_diffusion)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(16, 16, 16), (17, 9, 13)])
+def test_diffuse_parity_concurrent(cfd, shape):
+    cav, ocav = make(cfd, shape, dt=0.02, nu=0.05, lid_u=1.0)
+    cav.set_concurrent_diffusion(True)
+    f = _zero_walls(ocav, _random_velocity(ocav, 9, 1.0))
+    _load(cav, f)
+    rc, st = cav.substep("diffuse")
+    assert rc == cfd.CFD_OK and st["diff_status"] == cfd.CFD_OK
+    ref, rst = fs.diffuse(ocav, f, fixed_iters=tuple(st["diff_iters"]))
+    for c, name in enumerate("uvw"):
+        assert rel_err(cav.read_field(name).numpy(), ref[c]) < FP64_TOL
+
+
+@pytest.mark.parametrize("shape,steps", [((16, 16, 16), 6), ((64, 64, 64), 3)])
+def test_cavity_steps_concurrent_diffusion(cfd, shape, steps):
+    cav, ocav, stats, st, errs = _run_pair(cfd, shape, steps, 2, concurrent=True, dt=0.01, nu=0.001 if shape[0] == 64
+                                           else 0.01, lid_u=1.0)
+    for name, e in errs.items():
+        assert e < FP64_TOL, (name, e)
+    assert all(s["diff_status"] == 0 and s["status"] == 0 for s in stats)
+
+
+def test_concurrent_diffusion_needs_its_workspace(cfd):
+    cav, _ = make(cfd, (8, 8, 8), dt=0.01, nu=0.0, lid_u=1.0)
+    with pytest.raises(cfd.CfdError):
+        cav.set_concurrent_diffusion(True)
+    cav.set_concurrent_diffusion(False)
