@@ -71,7 +71,10 @@ enum { CFD_FIELD_U = 0, CFD_FIELD_V = 1, CFD_FIELD_W = 2, CFD_FIELD_P = 3 };
  *           the FP32 correction in FP64 and the FP64 true residual
  *           b - A x replaces the FP32 one, keeping the search direction.
  *           Convergence is judged on the FP64 true residual only.  Stats:
- *           iters = FP32 iterations, outer_iters = FP64 refinements.
+ *           iters = FP32 iterations, outer_iters = FP64 refinements.  The
+ *           diffusion solves of the step (nu > 0) run the same way on the
+ *           velocity matrices I + c L (no mean removal; refinement every
+ *           ir_delta, default 1e-4).
  *   DIC     CG preconditioned by the simplified diagonal-based incomplete
  *           Cholesky factorisation (the paper's default): pivots d_c = n_c
  *           - sum of 1/d over the x-1, y-1, z-1 neighbours, M = (D + L)
@@ -106,8 +109,8 @@ typedef struct {
   int32_t warm_start;       /* 1: start the pressure solve from the previous p    */
   double ir_delta;          /* IR: refine in FP64 each time the FP32 residual has
                                fallen by this factor, in (0, 1); 0 -> 0.1 for the
-                               pressure solve, 1e-4 for the diffusion solves of
-                               the graph form (well-conditioned systems)          */
+                               pressure solve, 1e-4 for the diffusion solves
+                               (well-conditioned systems)                        */
   int32_t advect_order;     /* backtrace: 0 or 1 explicit Euler x - dt v(x); 2 the
                                explicit midpoint rule x - dt v(x - dt/2 v(x))     */
   int32_t reserved[7];      /* must be zero                                       */
@@ -221,9 +224,8 @@ int cfd_set_cg_variant(cfd_handle *h, int variant);
  *               and the loop conditions.  Needs nx % 4 == 0.
  *   AUTO        (default) GRAPH when nx % 4 == 0 and the grid has at least
  *               2^21 cells, PERSISTENT otherwise.
- * In the GRAPH form the three diffusion solves of the step (nu > 0) also
- * run as FP32 CG with FP64 refinement on the velocity matrices (scalar-lane
- * kernels, any width); in the PERSISTENT form they are FP64 CG.
+ * The diffusion solves of the step follow the same form (in the GRAPH form
+ * on scalar-lane kernels, any width).
  * Errors: unknown form; GRAPH with nx % 4 != 0.  Batches always use the
  * persistent multi-problem kernel. */
 enum { CFD_IR_AUTO = 0, CFD_IR_PERSISTENT = 1, CFD_IR_GRAPH = 2 };
@@ -236,8 +238,8 @@ int cfd_set_ir_form(cfd_handle *h, int form);
  * sequential solves (their reductions run over other block counts).
  * Available on grids of at most 2^21 cells with nu > 0 (the workspace then
  * holds the two extra vector sets), where it is on from cfd_create; not
- * used for the graph form of CFD_SOLVER_IR nor inside batches.  Errors: on
- * not 0/1; on = 1 without that workspace. */
+ * used with CFD_SOLVER_IR (its solves share one set of FP32 vectors) nor
+ * inside batches.  Errors: on not 0/1; on = 1 without that workspace. */
 int cfd_set_concurrent_diffusion(cfd_handle *h, int on);
 
 /* Autotuner of the solver shape for this handle's grid and solver: times

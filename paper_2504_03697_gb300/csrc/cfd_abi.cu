@@ -370,9 +370,14 @@ int run_diffusion(cfd_handle* h, int comp, DevSolveStats* st) {
   int rc = cuda_check(h, launch_diffusion_rhs(pa, comp, h->stream, &h->launches), "diffusion rhs");
   if (rc) return rc;
   if (h->prm.solver == CFD_SOLVER_IR) {
-    const IrArgs ia = diffusion_ir_args(h, comp, st);
+    IrArgs ia = diffusion_ir_args(h, comp, st);
     if (use_ir_graph(h, ia))
       return cuda_check(h, launch_ir_graph(ia, h->irg_state, &h->irg_diff[comp], h->stream), "IR diffusion graph");
+    ia.ctrl = h->ctrl;
+    ia.partials = h->partials;
+    rc = cuda_check(h, cudaMemsetAsync(h->ctrl, 0, sizeof(SolveCtrl), h->stream), "memset ctrl");
+    if (rc) return rc;
+    return cuda_check(h, launch_ir(ia, h->lg, h->stream, &h->launches), "IR diffusion launch");
   }
   const CgArgs a = diffusion_args(h, comp, st, h->ctrl);
   rc = cuda_check(h, cudaMemsetAsync(h->ctrl, 0, sizeof(SolveCtrl), h->stream), "memset ctrl");
@@ -413,12 +418,8 @@ int run_diffusion_concurrent(cfd_handle* h, DevStepStats* st) {
 }
 
 bool diffusion_concurrent(const cfd_handle* h) {
-  if (!h->conc_diffusion || !h->aux[0] || !h->cset[0][0]) return false;
-  if (h->prm.solver == CFD_SOLVER_IR) {  // the graph form shares its FP32 vectors between the solves
-    const IrArgs ia = diffusion_ir_args(h, 0, nullptr);
-    if (use_ir_graph(h, ia)) return false;
-  }
-  return true;
+  // the mixed-precision solves share one set of FP32 vectors
+  return h->conc_diffusion && h->aux[0] && h->cset[0][0] && h->prm.solver != CFD_SOLVER_IR;
 }
 
 // Pressure solve A x = b on the handle's workspace b (already filled).
@@ -1229,7 +1230,7 @@ BatchLayout batch_layout(int n, const cfd_params* prm) {
     return o;
   };
   L.cg = take(sizeof(CgArgs) * 4 * size_t(n));
-  L.ir = take(sizeof(IrArgs) * size_t(n));
+  L.ir = take(sizeof(IrArgs) * 4 * size_t(n));  // [kind][cavity]: diffusion u, v, w, then pressure
   L.starts = take(sizeof(int) * 5 * size_t(n + 1));
   L.ctrl = take(sizeof(SolveCtrl) * 4 * size_t(n));
   L.stats = take(sizeof(DevSolveStats) * 4 * size_t(n));
@@ -1295,14 +1296,20 @@ int batch_enqueue_step(cfd_batch* b) {
   for (int c = 0; c < 3 && nd > 0 && rc == CFD_OK; ++c) {
     for (int k = 0; k < nd; ++k) ck(launch_diffusion_rhs(phys(b->cav[size_t(b->diff_idx[size_t(k)])]), c, b->stream, &b->launches), "diffusion rhs");
     ck(cudaMemsetAsync(b->d_ctrl + size_t(c) * n, 0, sizeof(SolveCtrl) * size_t(nd), b->stream), "memset ctrl");
-    ck(launch_cg_multi(b->d_cg + size_t(c) * n, b->d_starts + size_t(c) * (n + 1), nd, b->total_blocks[c], 0, b->stream,
-                       &b->launches),
-       "batched diffusion launch");
+    if (b->solver == CFD_SOLVER_IR)
+      ck(launch_ir_multi(b->d_ir + size_t(c) * n, b->d_starts + size_t(c) * (n + 1), nd, b->total_blocks[c], b->stream,
+                         &b->launches),
+         "batched mixed-precision diffusion launch");
+    else
+      ck(launch_cg_multi(b->d_cg + size_t(c) * n, b->d_starts + size_t(c) * (n + 1), nd, b->total_blocks[c], 0,
+                         b->stream, &b->launches),
+         "batched diffusion launch");
   }
   for (int i = 0; i < n && rc == CFD_OK; ++i) ck(launch_divergence(phys(b->cav[size_t(i)]), b->stream, &b->launches), "divergence");
   ck(cudaMemsetAsync(b->d_ctrl + size_t(3) * n, 0, sizeof(SolveCtrl) * size_t(n), b->stream), "memset ctrl");
   if (b->solver == CFD_SOLVER_IR)
-    ck(launch_ir_multi(b->d_ir, b->d_starts + size_t(4) * (n + 1), n, b->total_blocks[4], b->stream, &b->launches),
+    ck(launch_ir_multi(b->d_ir + size_t(3) * n, b->d_starts + size_t(4) * (n + 1), n, b->total_blocks[4], b->stream,
+                       &b->launches),
        "batched pressure launch");
   else
     ck(launch_cg_multi(b->d_cg + size_t(3) * n, b->d_starts + size_t(3) * (n + 1), n, b->total_blocks[3], b->precond,
@@ -1373,7 +1380,8 @@ int cfd_batch_create(int n, const cfd_params* per_cavity, void* dev_ws, size_t b
   // block split and solve tables
   const int sms = batch_num_sms();
   std::vector<CgArgs> cg(4 * size_t(n));
-  std::vector<IrArgs> ir = std::vector<IrArgs>(static_cast<size_t>(n));
+  std::vector<IrArgs> ir = std::vector<IrArgs>(4 * static_cast<size_t>(n));
+  const bool mixed = solver == CFD_SOLVER_IR;
   std::vector<int> starts(5 * size_t(n + 1), 0);
   auto weights = [&](const std::vector<int>& idx, int comp) {
     std::vector<double> w;
@@ -1389,7 +1397,10 @@ int cfd_batch_create(int n, const cfd_params* per_cavity, void* dev_ws, size_t b
   for (int kind = 0; kind < 5; ++kind) {
     const bool is_ir = kind == 4;
     const std::vector<int>& idx = kind < 3 ? b->diff_idx : all;
-    const int total = batch_blocks_per_sm(is_ir) * sms;
+    // the mixed-precision diffusion solves must fit both kernels' residency
+    const int bps = kind < 3 && mixed ? std::min(batch_blocks_per_sm(0), batch_blocks_per_sm(1))
+                                      : batch_blocks_per_sm(is_ir);
+    const int total = bps * sms;
     std::vector<int> st = split_blocks(weights(idx, kind < 3 ? kind : 3), total);
     if (st.empty()) {
       rc = batch_err(nullptr, CFD_ERR_INVALID_ARG, "%zu cavities exceed the %d co-resident blocks of one launch", idx.size(), total);
@@ -1404,6 +1415,14 @@ int cfd_batch_create(int n, const cfd_params* per_cavity, void* dev_ws, size_t b
         CgArgs a = diffusion_args(h, kind, b->d_stats + size_t(kind) * n + size_t(idx[k]), b->d_ctrl + size_t(kind) * n + k);
         a.tz = solve_tile_depth_for(a.g, nbk);
         cg[size_t(kind) * n + k] = a;
+        if (mixed) {
+          IrArgs d = diffusion_ir_args(h, kind, b->d_stats + size_t(kind) * n + size_t(idx[k]));
+          d.ctrl = b->d_ctrl + size_t(kind) * n + k;
+          d.partials = h->partials;
+          d.tz = a.tz;
+          d.use_tma = 0;
+          ir[size_t(kind) * n + k] = d;
+        }
       } else if (kind == 3) {
         CgArgs a = pressure_cg_args(h, h->p, h->prm.warm_start ? 0 : 1, 1, b->d_stats + size_t(3) * n + k, b->d_ctrl + size_t(3) * n + k);
         a.tz = solve_tile_depth_for(a.g, nbk);
@@ -1412,7 +1431,7 @@ int cfd_batch_create(int n, const cfd_params* per_cavity, void* dev_ws, size_t b
         IrArgs a = pressure_ir_args(h, h->p, h->prm.warm_start ? 0 : 1, 1, b->d_stats + size_t(3) * n + k, b->d_ctrl + size_t(3) * n + k);
         a.tz = solve_tile_depth_for(a.g, nbk);
         a.use_tma = 0;
-        ir[k] = a;
+        ir[size_t(3) * n + k] = a;
       }
     }
   }

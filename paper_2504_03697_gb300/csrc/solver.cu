@@ -1039,7 +1039,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) ir_kernel(const __grid_const
     acc[1] = acc[0];
   } else {
     Source<double, kModeResid, 0> src{a.x, nullptr, 0.0, false, nullptr, mx, my, mz};
-    Sink<double> out{a.r, nullptr, a.b, shift, a.remove_mean != 0, kOpPressure, 0.0};
+    Sink<double> out{a.r, nullptr, a.b, shift, a.remove_mean != 0, a.kind, a.c};
     stencil_tiles<double, kModeResid, 0>(ts, src, out, acc, s64, vb);
   }
   if (!allreduce(acc, tot)) return fail();
@@ -1068,7 +1068,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) ir_kernel(const __grid_const
         }
         if (refinements > a.max_outer) break;
         // r32 = r - mean(r); x32 = 0; rz = |r32|^2
-        const double rmean = rsum / double(n);
+        const double rmean = a.kind == kOpPressure ? rsum / double(n) : 0.0;  // singular system only
         float f = 0.f;
         for (size_t e = gtid(vb); e < n; e += gstride(vb)) {
           const float v = float(a.r[e] - rmean);
@@ -1094,7 +1094,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) ir_kernel(const __grid_const
         if (!dir_tma_f32(a, cur ? &a.map_p0 : &a.map_p1, float(beta), first, pnew, a.q32, fa[0], ring, vb)) return fail();
       } else {
         Source<float, kModeDir, 0> src{a.r32, pold, float(beta), first, nullptr, mx, my, mz};
-        Sink<float> out{a.q32, pnew, nullptr, 0.f, false, kOpPressure, 0.f};
+        Sink<float> out{a.q32, pnew, nullptr, 0.f, false, a.kind, float(a.c)};
         stencil_tiles<float, kModeDir, 0>(ts, src, out, fa, s32, vb);
       }
       acc[0] = fa[0];
@@ -1158,7 +1158,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) ir_kernel(const __grid_const
         if (!allreduce(acc, tot)) return fail();  // x complete before the stencil reads it
         {
           Source<double, kModeResid, 0> src{a.x, nullptr, 0.0, false, nullptr, mx, my, mz};
-          Sink<double> out{a.r, nullptr, a.b, 0.0, false, kOpPressure, 0.0};
+          Sink<double> out{a.r, nullptr, a.b, 0.0, false, a.kind, a.c};
           stencil_tiles<double, kModeResid, 0>(ts, src, out, acc, s64, vb);
         }
         if (!allreduce(acc, tot)) return fail();
@@ -1179,7 +1179,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) ir_kernel(const __grid_const
       if (!allreduce(acc, tot)) return fail();
       {
         Source<double, kModeResid, 0> src{a.x, nullptr, 0.0, false, nullptr, mx, my, mz};
-        Sink<double> out{a.r, nullptr, a.b, 0.0, false, kOpPressure, 0.0};
+        Sink<double> out{a.r, nullptr, a.b, 0.0, false, a.kind, a.c};
         stencil_tiles<double, kModeResid, 0>(ts, src, out, acc, s64, vb);
       }
       if (!allreduce(acc, tot)) return fail();
@@ -1455,7 +1455,7 @@ cudaError_t launch_ir(const IrArgs& a_in, const LaunchGeom& lg, cudaStream_t s, 
   IrArgs a = a_in;
   const int sms = num_sms();
   a.use_tma = 0;
-  if (!lg.no_tma && encode_f32_grid_map(&a.map_r32, a.r32, a.g.mx, a.g.my, a.g.mz) &&
+  if (a.kind == kOpPressure && !lg.no_tma && encode_f32_grid_map(&a.map_r32, a.r32, a.g.mx, a.g.my, a.g.mz) &&
       encode_f32_grid_map(&a.map_p0, a.p0_32, a.g.mx, a.g.my, a.g.mz) &&
       encode_f32_grid_map(&a.map_p1, a.p1_32, a.g.mx, a.g.my, a.g.mz)) {
     a.use_tma = 1;
