@@ -30,8 +30,9 @@
 // loops once iters >= max_iters or refinements > max_outer.
 //
 // Operators: the pressure matrix (float4 kernels, mx % 4 == 0) and the
-// velocity matrices of the diffusion substep (scalar-lane kernels, any
-// width; no mean removal, their matrices being nonsingular).
+// velocity matrices of the diffusion substep (float4 kernels where the face
+// grid's width is a multiple of 4, scalar-lane kernels otherwise; no mean
+// removal, their matrices being nonsingular).
 
 #include <cstdint>
 #include <cstring>
@@ -297,7 +298,7 @@ __global__ void __launch_bounds__(kGThreads) g_prep(const GArgs a) {
 // One warp covers 128 x cells of one row; x neighbours by warp shuffles,
 // y neighbours by loads, z by marching kZ32 planes in registers.
 // ---------------------------------------------------------------------------
-template <typename F4, typename F1, typename E>
+template <bool VEL, typename F4, typename F1, typename E>
 __device__ __forceinline__ void march_f32(const GArgs& a, F4 P4, F1 P1, E emit) {
   const int my = a.my, mz = a.mz, nx4 = a.mx >> 2;
   const size_t sy4 = size_t(nx4), sz4 = size_t(nx4) * my;
@@ -326,10 +327,19 @@ __device__ __forceinline__ void march_f32(const GArgs& a, F4 P4, F1 P1, E emit) 
       if (lane == 31) east = has_e ? P1(4 * c4 + 4) : pc.w;
       else if (!has_e) east = pc.w;
       float4 q;
-      q.x = fmaf(6.f, pc.x, -(((((west + pc.y) + ps.x) + pn.x) + pm.x) + pp.x));
-      q.y = fmaf(6.f, pc.y, -(((((pc.x + pc.z) + ps.y) + pn.y) + pm.y) + pp.y));
-      q.z = fmaf(6.f, pc.z, -(((((pc.y + pc.w) + ps.z) + pn.z) + pm.z) + pp.z));
-      q.w = fmaf(6.f, pc.w, -(((((pc.z + east) + ps.w) + pn.w) + pm.w) + pp.w));
+      if (!VEL) {
+        q.x = fmaf(6.f, pc.x, -(((((west + pc.y) + ps.x) + pn.x) + pm.x) + pp.x));
+        q.y = fmaf(6.f, pc.y, -(((((pc.x + pc.z) + ps.y) + pn.y) + pm.y) + pp.y));
+        q.z = fmaf(6.f, pc.z, -(((((pc.y + pc.w) + ps.z) + pn.z) + pm.z) + pp.z));
+        q.w = fmaf(6.f, pc.w, -(((((pc.z + east) + ps.w) + pn.w) + pm.w) + pp.w));
+      } else {  // velocity rows: wall and ghost rules by the cell's indices
+        const int i0 = 4 * i4, mx = a.mx, kd = a.kind;
+        const float c = a.c32;
+        q.x = stencil_row<float>(kd, c, i0, j, k, mx, my, mz, pc.x, west, pc.y, ps.x, pn.x, pm.x, pp.x);
+        q.y = stencil_row<float>(kd, c, i0 + 1, j, k, mx, my, mz, pc.y, pc.x, pc.z, ps.y, pn.y, pm.y, pp.y);
+        q.z = stencil_row<float>(kd, c, i0 + 2, j, k, mx, my, mz, pc.z, pc.y, pc.w, ps.z, pn.z, pm.z, pp.z);
+        q.w = stencil_row<float>(kd, c, i0 + 3, j, k, mx, my, mz, pc.w, pc.z, east, ps.w, pn.w, pm.w, pp.w);
+      }
       if (on) emit(c4, pc, q);
       pm = pc;
       pc = pp;
@@ -410,8 +420,47 @@ __global__ void __launch_bounds__(kGThreads, 4) g_dir(const GArgs a) {
   }
 }
 
+// inner body for the velocity matrices on float4 lanes (face grids whose
+// width is a multiple of 4): p = r32 + beta p_old formed at the 7 stencil
+// points, stored; p.q with q = H p on the fly (not stored); alpha = rz / p.q
+__global__ void __launch_bounds__(kGThreads, 4) g_dir_v(const GArgs a) {
+  GState* S = a.S;
+  count_kernel(S);
+  const bool first = S->first != 0;
+  const float beta = float(S->beta);
+  const int cur = S->cur;
+  float* pnew = cur ? a.p1 : a.p0;
+  const float* pold = cur ? a.p0 : a.p1;
+  const float4* r4 = reinterpret_cast<const float4*>(a.r32);
+  const float4* o4 = reinterpret_cast<const float4*>(pold);
+  float4* p4 = reinterpret_cast<float4*>(pnew);
+  auto P4 = [&](size_t e) {
+    const float4 rv = __ldg(r4 + e);
+    if (first) return rv;
+    const float4 ov = __ldg(o4 + e);
+    return make_float4(fmaf(beta, ov.x, rv.x), fmaf(beta, ov.y, rv.y), fmaf(beta, ov.z, rv.z), fmaf(beta, ov.w, rv.w));
+  };
+  auto P1 = [&](size_t e) { return first ? __ldg(a.r32 + e) : fmaf(beta, __ldg(pold + e), __ldg(a.r32 + e)); };
+  double acc = 0.0;
+  march_f32<true>(a, P4, P1, [&](size_t c4, const float4& pc, const float4& q) {
+    p4[c4] = pc;
+    acc += double(fmaf(pc.x, q.x, fmaf(pc.y, q.y, fmaf(pc.z, q.z, pc.w * q.w))));
+  });
+  double v[1] = {acc}, o[1];
+  if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
+  const double pq = o[0];
+  if (!(pq > 0.0) || !isfinite(pq)) {
+    S->breakdown = 1;
+    S->status = kErrBreakdown;
+    S->done = 1;
+  } else {
+    S->alpha = S->rz / pq;
+  }
+}
+
 // inner body: q = A p again from the stored p, x32 += alpha p, r32 -= alpha q,
 // |r32|^2; the loop control
+template <bool VEL>
 __global__ void __launch_bounds__(kGThreads, 4) g_upd(const GArgs a) {
   GState* S = a.S;
   count_kernel(S);
@@ -427,7 +476,7 @@ __global__ void __launch_bounds__(kGThreads, 4) g_upd(const GArgs a) {
   auto P4 = [&](size_t e) { return __ldg(p4 + e); };
   auto P1 = [&](size_t e) { return __ldg(pnew + e); };
   double acc = 0.0;
-  march_f32(a, P4, P1, [&](size_t c4, const float4& pv, const float4& qv) {
+  march_f32<VEL>(a, P4, P1, [&](size_t c4, const float4& pv, const float4& qv) {
     float4 dv = d4[c4], rv = r4[c4];
     dv.x = fmaf(alpha, pv.x, dv.x);
     dv.y = fmaf(alpha, pv.y, dv.y);
@@ -647,7 +696,7 @@ size_t ir_graph_state_bytes() { return kStateBytes + size_t(3) * kGMax * sizeof(
 bool ir_graph_eligible(const IrArgs& a) { return a.kind != kOpPressure || (a.g.mx % 4 == 0 && a.g.mx >= 4); }
 
 namespace {
-bool use_vec_kernels(const IrArgs& a) { return a.kind == kOpPressure && a.g.mx % 4 == 0; }
+bool use_vec_kernels(const IrArgs& a) { return a.g.mx % 4 == 0; }
 }  // namespace
 
 namespace {
@@ -742,10 +791,17 @@ cudaError_t build(IrGraph* G, const IrArgs& ia, void* state_buf) {
   if ((e = add_kernel(outer, &b1, nullptr, (void*)g_prep, wave_blocks(g_prep, vec_work), flat, &a)) != cudaSuccess)
     return e;
   if ((e = add_while(outer, &b2, &b1, a.h_in, &inner)) != cudaSuccess) return e;
-  if (vec) {
+  if (vec && a.kind == kOpPressure) {
     if ((e = add_kernel(inner, &i1, nullptr, (void*)g_dir, wave_blocks(g_dir, items32), tile, &a)) != cudaSuccess)
       return e;
-    if ((e = add_kernel(inner, &i2, &i1, (void*)g_upd, wave_blocks(g_upd, items32), tile, &a)) != cudaSuccess)
+    if ((e = add_kernel(inner, &i2, &i1, (void*)g_upd<false>, wave_blocks(g_upd<false>, items32), tile, &a)) !=
+        cudaSuccess)
+      return e;
+  } else if (vec) {
+    if ((e = add_kernel(inner, &i1, nullptr, (void*)g_dir_v, wave_blocks(g_dir_v, items32), tile, &a)) != cudaSuccess)
+      return e;
+    if ((e = add_kernel(inner, &i2, &i1, (void*)g_upd<true>, wave_blocks(g_upd<true>, items32), tile, &a)) !=
+        cudaSuccess)
       return e;
   } else {
     if ((e = add_kernel(inner, &i1, nullptr, (void*)g_dir_s, wave_blocks(g_dir_s, items32), tile, &a)) != cudaSuccess)
