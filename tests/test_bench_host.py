@@ -1,0 +1,39 @@
+"""Host-side checks of bench.py (no GPU): argument defaults of the measured
+workloads and the byte/flop models the roofline objects are built from."""
+import json
+
+import bench
+
+
+def test_default_workload_and_contract_arguments():
+    a = bench.parse_args([])
+    assert a.gpus == 1 and a.warmup >= 3 and a.impl == "ours"
+    assert a.workload == "cavity64" and a.solver == "cg"
+    assert a.concurrent_diffusion == "on" and a.ir_form == "tuned"
+
+
+def test_byte_models_per_cell():
+    # FP32 iteration of the graph form: direction reads r32, p_old and writes
+    # p (12 B); the update reads p, x32, r32 and writes x32, r32 (20 B)
+    assert bench.IR_GRAPH_BYTES_PER_CELL_ITER == 12 + 20
+    # persistent form: direction also stores q (16 B), update reads q (24 B)
+    assert bench.IR_BYTES_PER_CELL_ITER == 16 + 24
+    # textbook FP64 CG: (r, p_old -> p, q) 32 B + (x, p, r, q -> x, r) 48 B
+    assert bench.CG_BYTES_PER_CELL_ITER == 32 + 48
+
+
+def test_traffic_belongs_to_one_launch_shape():
+    assert bench.CG1_CAVITY64_SHAPE == {"blocks": 128, "tile_depth": 8, "register_path": True}
+    assert bench.CG1_CAVITY64_DRAM_BYTES > 0
+
+
+def test_measured_hbm_peak_fallback(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_hbm_gbs(default=1234.0) == 1234.0
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6000.5}))
+    assert bench.measured_hbm_gbs() == 6000.5
+
+
+def test_aggregate_is_all_ranks_over_the_slowest():
+    # 2 ranks x 1000 cells x 10 steps in 2 s (the slowest rank's time)
+    assert bench.aggregate(1000, 10, 2, 2.0) == 1000 * 10 * 2 / 2.0
