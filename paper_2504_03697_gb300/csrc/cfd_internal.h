@@ -77,7 +77,7 @@ struct CgArgs {
 // Arguments of the FP32-inner / FP64-outer iterative-refinement solve.
 struct IrArgs {
   GridDims g;
-  int kind;        // kOp* operator (the persistent form supports kOpPressure only)
+  int kind;        // kOp* operator (the TMA stencil ring serves kOpPressure only)
   double c;        // nu dt / h^2 of the velocity operators
   double* x;       // FP64 solution (out)
   double* b;       // FP64 rhs (mean removed in place)

@@ -966,7 +966,8 @@ __device__ bool dir_tma_f32(const IrArgs& a, const CUtensorMap* mp, float beta, 
 }
 
 // ---------------------------------------------------------------------------
-// Mixed-precision CG with FP64 refinement (persistent; pressure operator).
+// Mixed-precision CG with FP64 refinement (persistent; the pressure matrix,
+// or a velocity matrix of the diffusion substep: a.kind, a.c).
 //
 // One conjugate-gradient recurrence runs in FP32: the search direction p,
 // the operator output q, the recurrence residual r32 and the correction x32
@@ -976,7 +977,7 @@ __device__ bool dir_tma_f32(const IrArgs& a, const CUtensorMap* mp, float beta, 
 // residual has fallen by the factor delta since the last refinement (or
 // claims convergence): x += x32 in FP64, x32 = 0, the true residual
 // r = b - A x is recomputed with the FP64 stencil, and r32 = r (mean
-// removed) replaces the recurrence residual; the search direction is kept,
+// removed for the singular pressure matrix) replaces the recurrence residual; the search direction is kept,
 // so the refinement does not restart the Krylov process (the "reliable
 // update" form of iterative refinement).  Convergence is only ever declared
 // on the FP64 true residual: ||b - A x|| <= rtol ||b||.
