@@ -341,8 +341,9 @@ bool use_ir_graph(const cfd_handle* h, const IrArgs& a) {
 }
 
 // The diffusion solve of component comp as FP32 CG with FP64 refinement
-// (graph form of CFD_SOLVER_IR): x0 = the advected field, b from
-// diffusion_rhs, the velocity matrix I + c L; no mean removal or gauge.
+// (CFD_SOLVER_IR, any form): x0 = the advected field, b from diffusion_rhs,
+// the velocity matrix I + c L; no mean removal or gauge.  The persistent and
+// batch launches add their control block and partial sums.
 IrArgs diffusion_ir_args(const cfd_handle* h, int comp, DevSolveStats* st) {
   const double hh = h->prm.length / h->prm.nx;
   IrArgs a{};
@@ -1198,7 +1199,7 @@ struct cfd_batch {
   int solver;
   // device tables inside the batch workspace
   CgArgs* d_cg;            // [4][n]: diffusion u, v, w (first nd entries), pressure CG
-  IrArgs* d_ir;            // [n]
+  IrArgs* d_ir;            // [4][n]: mixed-precision diffusion u, v, w (first nd entries), pressure
   int* d_starts;           // [5][n + 1]
   SolveCtrl* d_ctrl;       // [4][n]
   DevSolveStats* d_stats;  // [4][n]
