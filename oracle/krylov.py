@@ -33,6 +33,14 @@ polynomial solution, and DIC = exact factorisation on tridiagonal matrices
 takes, so those pins cover it; tests/test_oracle_solver.py also checks that
 with alpha = r.r / p.Ap it leaves r orthogonal to p and equal to b - A x.
 
+``ir_cg`` (the mixed-precision solve: the same CG with its recurrence in
+FP32 and FP64 reliable updates) is pinned by tests/test_oracle_solver.py:
+with FP64 inner vectors and no refinement before convergence it takes
+``pcg``'s iterates bit for bit on an SPD matrix; in FP32 it meets the FP64
+true-residual tolerance and lies within 2 rtol ||b|| / lambda_min of the
+dense solve of the pressure system (within 2 rtol ||b|| for I + c L); a
+smaller refinement factor needs fewer refinements.
+
 ``fpcg`` (flexible PCG for a preconditioner that may vary between
 iterations) is pinned by tests/test_oracle_unet.py: with M = identity or a
 fixed SPD M it takes the iterates of ``pcg`` (the Polak-Ribiere beta equals
@@ -258,4 +266,95 @@ def fpcg(A, b, precond, rtol=1e-8, max_iters=1000, stagnation=50, max_restarts=8
         z = z_new
         p = z + beta * p
     st.rel_resid = float(np.linalg.norm(b - A @ x) / np.sqrt(bb))
+    return x, st
+
+
+@dataclass
+class IrStats:
+    iters: int = 0            # inner (low-precision) CG iterations
+    refinements: int = 0      # FP64 true-residual replacements
+    converged: bool = False
+    breakdown: bool = False
+    rel_resid: float = 0.0    # true ||b - A x|| / ||b|| at exit
+
+
+def ir_cg(A, b, rtol=1e-8, delta=0.1, max_iters=10000, max_outer=1000, inner=np.float32, singular=True):
+    """CG with an inner recurrence in a lower precision and FP64 reliable
+    updates (the mixed-precision solve of the pressure and diffusion systems:
+    Sec. 3.1's CG with its vectors, operator and recurrence in `inner`).
+
+    The FP64 state is x and the true residual r = b - A x.  A refinement
+    loads the recurrence residual from it, r_in = r (minus its mean when the
+    system is singular, the Neumann pressure matrix), and starts an inner
+    correction x_in = 0.  Each inner iteration, all vectors and the operator
+    in `inner` precision, the inner products summed in FP64:
+        p = r_in + beta p,  q = A p,  alpha = rz / p.q,
+        x_in += alpha p,  r_in -= alpha q,  rz' = r_in.r_in.
+    When rz' has fallen by delta^2 below the true residual of the last
+    refinement (or below rtol^2 ||b||^2) the correction is added to x in
+    FP64, the true residual is recomputed, and the next direction keeps p
+    with beta = (new r_in . r_in) / rz (the residual it replaces).
+    Otherwise beta = rz' / rz.  Convergence is declared on the FP64 true
+    residual only.  b has its mean removed first when `singular`.
+    Returns (x, IrStats)."""
+    A64 = A.astype(np.float64)
+    Ain = A.astype(inner)
+    b = np.asarray(b, dtype=np.float64)
+    if singular:
+        b = b - b.mean()
+    st = IrStats()
+    n = b.size
+    x = np.zeros(n)
+    bb = float(np.dot(b, b))
+    if bb == 0.0:
+        st.converged = True
+        return x, st
+    tol2 = rtol * rtol * bb
+    r = b.copy()
+    rr = bb
+    p = np.zeros(n, dtype=inner)
+    rz = 0.0
+    beta = 0.0
+    first = True
+    while True:
+        # refinement point: judge, then restart the inner recurrence
+        if rr <= tol2:
+            st.converged = True
+            break
+        if st.refinements > max_outer or st.iters >= max_iters:
+            break
+        r_in = (r - r.mean() if singular else r).astype(inner)
+        x_in = np.zeros(n, dtype=inner)
+        rz_new = float(np.dot(r_in.astype(np.float64), r_in.astype(np.float64)))
+        if not first:
+            beta = rz_new / rz
+        rz = rz_new
+        rz_ref = rr
+        refine = False
+        while st.iters < max_iters:
+            p = (r_in if first else r_in + inner(beta) * p).astype(inner)
+            q = (Ain @ p).astype(inner)
+            pq = float(np.dot(p.astype(np.float64), q.astype(np.float64)))
+            if not (pq > 0.0) or not np.isfinite(pq):
+                st.breakdown = True
+                break
+            alpha = inner(rz / pq)
+            x_in = (x_in + alpha * p).astype(inner)
+            r_in = (r_in - alpha * q).astype(inner)
+            rz_new = float(np.dot(r_in.astype(np.float64), r_in.astype(np.float64)))
+            first = False
+            st.iters += 1
+            if rz_new <= delta * delta * rz_ref or rz_new <= tol2:
+                refine = True
+                break
+            beta = rz_new / rz
+            rz = rz_new
+        x = x + x_in.astype(np.float64)
+        r = b - A64 @ x
+        rr = float(np.dot(r, r))
+        if not refine:
+            break
+        st.refinements += 1
+    st.converged = st.converged or rr <= tol2
+    st.rel_resid = float(np.sqrt(rr / bb))
     return x, st

@@ -201,3 +201,70 @@ def test_cg_update_orthogonality_and_true_residual():
     assert np.allclose(x, alpha * b, rtol=0, atol=1e-15)
     assert rr == pytest.approx(float(np.sum(r * r)), rel=1e-15)
     assert rr < float(b @ b)
+
+
+# ----------------------------------------------------------------------------
+# ir_cg: CG with a low-precision inner recurrence and FP64 reliable updates
+# ----------------------------------------------------------------------------
+def test_ir_cg_in_fp64_without_refinement_is_plain_cg():
+    """With FP64 'inner' vectors, delta = 0 (refine only at convergence) and
+    a nonsingular SPD matrix, the recurrence is CG's: same iteration count
+    and the same iterate, bit for bit."""
+    from oracle.krylov import ir_cg
+    from oracle.mac import Cavity
+    from oracle.operators import diffusion_csr
+    cav = Cavity(6, 5, 4, dt=0.05, nu=0.3)
+    H, _, mask = diffusion_csr(cav, 1)
+    b = np.random.default_rng(8).standard_normal(H.shape[0])
+    x_ref, st_ref = pcg(H, b, rtol=1e-10, max_iters=10000)
+    x, st = ir_cg(H, b, rtol=1e-10, delta=0.0, inner=np.float64, singular=False)
+    assert st.converged and st.iters == st_ref.iters and st.refinements == 1
+    assert np.array_equal(x, x_ref)
+
+
+@pytest.mark.parametrize("shape", [(8, 6, 5), (16, 12, 10)])
+def test_ir_cg_fp32_reaches_the_fp64_tolerance(shape):
+    """FP32 inner recurrence on the singular pressure system: the FP64 true
+    residual meets rtol, and the zero-mean solution lies within
+    2 rtol ||b|| / lambda_min of the dense solve (lambda_min from the DCT
+    closed form)."""
+    from oracle.krylov import ir_cg
+    A = poisson_csr(*shape)
+    b = uniform_field(shape[::-1], seed=12).ravel()
+    b -= b.mean()
+    x, st = ir_cg(A, b, rtol=1e-8, delta=0.1)
+    assert st.converged and st.refinements >= 5
+    assert np.linalg.norm(b - A @ x) <= 1.0001e-8 * np.linalg.norm(b)
+    ref = _dense_zero_mean_solve(A, b)
+    lam = min(4 * np.sin(np.pi / (2 * n)) ** 2 for n in shape)
+    assert np.linalg.norm((x - x.mean()) - ref) <= 2e-8 * np.linalg.norm(b) / lam
+
+
+def test_ir_cg_refinements_follow_delta():
+    """Each refinement marks a fall of the residual by delta: a smaller delta
+    needs fewer refinements for the same tolerance."""
+    from oracle.krylov import ir_cg
+    A = poisson_csr(12, 10, 8)
+    b = uniform_field((8, 10, 12), seed=13).ravel()
+    _, coarse = ir_cg(A, b, rtol=1e-8, delta=1e-3)
+    _, fine = ir_cg(A, b, rtol=1e-8, delta=0.1)
+    assert coarse.converged and fine.converged
+    assert coarse.refinements < fine.refinements
+    assert 6 <= fine.refinements <= 12 and coarse.refinements <= 5
+
+
+def test_ir_cg_zero_rhs_and_nonsingular_fp32():
+    from oracle.krylov import ir_cg
+    from oracle.mac import Cavity
+    from oracle.operators import diffusion_csr
+    A = poisson_csr(4, 4, 4)
+    x, st = ir_cg(A, np.zeros(64))
+    assert st.converged and st.iters == 0 and not x.any()
+    cav = Cavity(8, 7, 6, dt=0.05, nu=0.2)
+    H, _, _ = diffusion_csr(cav, 0)
+    b = np.random.default_rng(9).standard_normal(H.shape[0])
+    x, st = ir_cg(H, b, rtol=1e-8, delta=1e-4, singular=False)
+    assert st.converged
+    assert np.linalg.norm(b - H @ x) <= 1.0001e-8 * np.linalg.norm(b)
+    ref = np.linalg.solve(H.toarray(), b)
+    assert np.linalg.norm(x - ref) <= 2e-8 * np.linalg.norm(b)  # ||H^-1|| <= 1
