@@ -334,12 +334,18 @@ int64_t cfd_batch_launch_count(const cfd_batch *b);
 /* ---------------------------------------------------------------------------
  * Allocation-free standalone pressure solve.  The paper has no counterpart:
  * this entry point exists for callers that may not allocate device memory
- * at all (code inside host callbacks, plug-ins whose host application owns
- * every allocation, runtimes that reserve all device memory up front), so
- * they cannot provide the workspace cfd_create needs.
+ * at all (plug-ins whose host application owns every allocation, runtimes
+ * that reserve all device memory up front), so they cannot provide the
+ * workspace cfd_create needs.  It still calls the CUDA runtime (copies, a
+ * memset, a kernel launch, a stream synchronisation when stats is given),
+ * so it must not be called from inside a CUDA stream callback
+ * (cudaLaunchHostFunc), where no CUDA call is allowed.
  *
  * Solves the same Neumann system as cfd_solve_pressure with plain FP64 CG
- * (cold start, mean of b removed, no gauge shift): b_dev and x_dev are
+ * (cold start, mean of b removed, no gauge shift), in the two-reduction
+ * (textbook) form: its fixed scratch has no room for the extra vectors of
+ * the single-reduction form, so its rounding and iteration count can differ
+ * slightly from cfd_solve_pressure's default form.  b_dev and x_dev are
  * device arrays of nx*ny*nz doubles (x fastest), b is read only, x is
  * overwritten.  rtol in (0, 1); max_iters = 0 means 20 * max(n).  stats
  * (nullable) as for cfd_solve_pressure; when given, the call synchronises
@@ -356,7 +362,7 @@ int64_t cfd_batch_launch_count(const cfd_batch *b);
  *    threads) race: serialise them on one stream;
  *  - the first call on each device looks up the array's device address
  *    (with that device current); make that first call before any stream
- *    capture.
+ *    capture.  A failed lookup is not remembered: the next call retries.
  * Errors are reported through cfd_last_error(NULL). */
 #define CFD_NOALLOC_MAX_CELLS 262144
 int cfd_poisson_solve_noalloc(int32_t nx, int32_t ny, int32_t nz, const double *b_dev, double *x_dev,
@@ -384,6 +390,28 @@ int cfd_snapshot_write_csv(cfd_handle *h, const char *path, int nthreads);
  * device).  The mean is NOT removed (the solvers remove it).  Asynchronous on
  * the handle's stream.  Used to harvest pressure systems from a run. */
 int cfd_pressure_rhs(cfd_handle *h, double *b_dev);
+
+/* One training pair of the learned preconditioner from a pressure system:
+ * with b' = b - mean(b), r = b' - A xk is the residual of the iterate xk and
+ * e = (xs - xk) - mean(xs - xk) its error against the converged solution xs
+ * (the Neumann system fixes x only up to a constant), A the operator of
+ * cfd_apply_poisson (Sec. 3.1).  All five are device arrays of nx*ny*nz
+ * float64; r and e must not alias the inputs or each other.  Asynchronous on
+ * the handle's stream (it uses the handle's partial-sum scratch, so it must
+ * not overlap a solve of the same handle). */
+int cfd_harvest_pair(cfd_handle *h, const double *b_dev, const double *xs_dev, const double *xk_dev, double *r_dev,
+                     double *e_dev);
+
+/* Time limit of each grid-wide wait inside the persistent solve kernels of
+ * this handle (the all-reduce barrier of the CG and mixed-precision
+ * kernels; default 2 s; UINT64_MAX restores the default).  A block that
+ * waits longer records CFD_ERR_TIMEOUT, every other block leaves at its
+ * next wait, and the solve returns CFD_ERR_TIMEOUT with the fields holding
+ * whatever the kernel had written; the handle stays usable.  0 gives up at
+ * the first wait that is not already satisfied (for tests of that path).
+ * Waits for the tensor-memory copies keep their own fixed limits.  Applies
+ * to later calls; batch cavities keep the default. */
+int cfd_set_wait_limit(cfd_handle *h, uint64_t limit_ns);
 
 /* Assembled-matrix path (Sec. 3.1: the paper assembles the pressure matrix
  * in CSR and multiplies with it), beside the matrix-free operator of

@@ -22,7 +22,8 @@ DIC reading: d_i = a_ii - sum_{j < i, a_ij != 0} a_ij^2 / d_j and
 M = (D + L) D^-1 (D + L^T) with L the strict lower triangle of A (the
 "simplified" form keeps the sparsity of A).  The incomplete factor drops
 the fill that would make the last pivot of the singular Neumann pressure
-matrix vanish, so every pivot stays positive (about 2.07 in the interior)
+matrix vanish, so every pivot stays positive (deep in the interior the
+pivots approach 3 + sqrt(6), about 5.449, the fixed point of d = 6 - 3/d)
 and M is SPD; DIC applies to the pressure system directly.
 
 Pins (tests/test_oracle_solver.py): dense pseudo-inverse solves on grids up

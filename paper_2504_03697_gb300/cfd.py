@@ -111,6 +111,8 @@ def load_library(path: Optional[str] = None):
         "cfd_enable_timing": (ctypes.c_int, [vp, ctypes.c_int]),
         "cfd_phase_times": (ctypes.c_int, [vp, P(ctypes.c_double), P(ctypes.c_int64)]),
         "cfd_pressure_rhs": (ctypes.c_int, [vp, vp]),
+        "cfd_harvest_pair": (ctypes.c_int, [vp, vp, vp, vp, vp, vp]),
+        "cfd_set_wait_limit": (ctypes.c_int, [vp, ctypes.c_uint64]),
         "cfd_autotune_solver": (ctypes.c_int, [vp, ctypes.c_int32, P(cfd_tune_report)]),
         "cfd_set_cg_variant": (ctypes.c_int, [vp, ctypes.c_int]),
         "cfd_set_ir_form": (ctypes.c_int, [vp, ctypes.c_int]),
@@ -315,6 +317,21 @@ class Cavity:
         """Projection right-hand side of the current velocity (mean kept)."""
         assert b.is_cuda and b.dtype == torch.float64 and b.numel() == self.prm.nx * self.prm.ny * self.prm.nz
         return self._check(self.lib.cfd_pressure_rhs(self.h, ctypes.c_void_p(b.data_ptr())))
+
+    def harvest_pair(self, b: torch.Tensor, xs: torch.Tensor, xk: torch.Tensor, r: torch.Tensor, e: torch.Tensor):
+        """Training pair of the learned preconditioner (cfd_harvest_pair):
+        r = (b - mean b) - A xk, e = (xs - xk) - mean(xs - xk)."""
+        n = self.prm.nx * self.prm.ny * self.prm.nz
+        for t in (b, xs, xk, r, e):
+            assert t.is_cuda and t.dtype == torch.float64 and t.numel() == n and t.is_contiguous()
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+        return self._check(self.lib.cfd_harvest_pair(self.h, ptr(b), ptr(xs), ptr(xk), ptr(r), ptr(e)))
+
+    def set_wait_limit(self, ns=None):
+        """Limit of each grid-wide wait in the persistent solves, in ns
+        (None restores the 2 s default)."""
+        v = (1 << 64) - 1 if ns is None else int(ns)
+        return self._check(self.lib.cfd_set_wait_limit(self.h, ctypes.c_uint64(v)))
 
     def set_stream(self, stream):
         self.stream = stream

@@ -134,6 +134,7 @@ struct cfd_handle {
   cfd::IrGraph* irg = nullptr;   // its cached, instantiated graph (pressure)
   cfd::IrGraph* irg_diff[3] = {nullptr, nullptr, nullptr};  // diffusion of u, v, w
   int ir_form = CFD_IR_AUTO;
+  unsigned long long wait_ns = kTimeoutNs;  // limit of each grid-wide wait (cfd_set_wait_limit)
   double* partials;
   SolveCtrl* ctrl;
   DevStepStats* stats;
@@ -286,7 +287,7 @@ CgArgs diffusion_args(const cfd_handle* h, int comp, DevSolveStats* st, SolveCtr
   a.rtol = h->prm.rtol;
   a.max_iters = iter_cap(h->prm);
   a.max_restarts = kMaxRestarts;
-  a.timeout_ns = kTimeoutNs;
+  a.timeout_ns = h->wait_ns;
   a.ctrl = ctrl; a.partials = vs.partials; a.stats = st;
   a.tz = tz_for(a.g.mz);
   return a;
@@ -306,7 +307,7 @@ CgArgs pressure_cg_args(const cfd_handle* h, double* x, int zero_x0, int gauge, 
   a.rtol = h->prm.rtol;
   a.max_iters = iter_cap(h->prm);
   a.max_restarts = kMaxRestarts;
-  a.timeout_ns = kTimeoutNs;
+  a.timeout_ns = h->wait_ns;
   a.ctrl = ctrl; a.partials = h->partials; a.stats = st;
   a.tz = tz_for(a.g.mz);
   return a;
@@ -323,7 +324,7 @@ IrArgs pressure_ir_args(const cfd_handle* h, double* x, int zero_x0, int gauge, 
   a.delta = h->prm.ir_delta > 0 ? h->prm.ir_delta : 0.1;
   a.max_iters = iter_cap(h->prm);
   a.max_outer = 1000;
-  a.timeout_ns = kTimeoutNs;
+  a.timeout_ns = h->wait_ns;
   a.ctrl = ctrl; a.partials = h->partials; a.stats = st;
   a.tz = tz_for(a.g.mz);
   return a;
@@ -360,7 +361,7 @@ IrArgs diffusion_ir_args(const cfd_handle* h, int comp, DevSolveStats* st) {
   a.delta = h->prm.ir_delta > 0 ? h->prm.ir_delta : 1e-4;
   a.max_iters = iter_cap(h->prm);
   a.max_outer = 1000;
-  a.timeout_ns = kTimeoutNs;
+  a.timeout_ns = h->wait_ns;
   a.stats = st;
   return a;
 }
@@ -1090,6 +1091,26 @@ int cfd_pressure_rhs(cfd_handle* h, double* b_dev) {
   pa.ua = h->u; pa.va = h->v; pa.wa = h->w;
   pa.b = b_dev;
   return cuda_check(h, launch_divergence(pa, h->stream, &h->launches), "divergence");
+}
+
+int cfd_harvest_pair(cfd_handle* h, const double* b_dev, const double* xs_dev, const double* xk_dev, double* r_dev,
+                     double* e_dev) {
+  if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
+  if (!b_dev || !xs_dev || !xk_dev || !r_dev || !e_dev) return set_err(h, CFD_ERR_INVALID_ARG, "NULL vector");
+  if (r_dev == xk_dev || r_dev == b_dev || r_dev == xs_dev || e_dev == xk_dev || e_dev == xs_dev || r_dev == e_dev)
+    return set_err(h, CFD_ERR_INVALID_ARG, "r and e must not alias the inputs or each other");
+  static_assert(partials_doubles(kMaxBlocksBound) >= 2 * 512 + 2, "partial-sum scratch too small for the harvest");
+  if (harvest_scratch_doubles() > partials_doubles(kMaxBlocksBound))
+    return set_err(h, CFD_ERR_INVALID_ARG, "harvest scratch does not fit");
+  return cuda_check(h, launch_harvest_pair(GridDims{h->prm.nx, h->prm.ny, h->prm.nz}, b_dev, xs_dev, xk_dev, r_dev,
+                                           e_dev, h->partials, h->stream, &h->launches),
+                    "harvest pair");
+}
+
+int cfd_set_wait_limit(cfd_handle* h, uint64_t limit_ns) {
+  if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
+  h->wait_ns = limit_ns == UINT64_MAX ? kTimeoutNs : static_cast<unsigned long long>(limit_ns);
+  return CFD_OK;
 }
 
 int64_t cfd_launch_count(const cfd_handle* h) {

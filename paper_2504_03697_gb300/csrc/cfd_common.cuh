@@ -120,16 +120,18 @@ __device__ __forceinline__ unsigned int atom_add_acq_rel_gpu(unsigned int* p, un
 }
 
 // Bounded wait (thread 0) until the monotonic counter reaches target.
-// Returns false, recording CFD_ERR_TIMEOUT, after timeout_ns, and also when
-// another block has recorded an error.
+// Returns false, recording CFD_ERR_TIMEOUT, once timeout_ns have passed
+// (checked on the first unsatisfied poll and every 64 polls after it, so a
+// limit of 0 gives up at once), and also when another block has recorded an
+// error.
 __device__ __forceinline__ bool wait_counter(SolveCtrl* ctrl, const unsigned int* counter, unsigned int target,
                                              unsigned long long timeout_ns) {
   const unsigned long long t0 = global_ns();
   unsigned int polls = 0;
   while (int(ld_acquire_gpu(counter) - target) < 0) {
-    if ((++polls & 63u) == 0) {
+    if ((polls++ & 63u) == 0) {
       if (ld_volatile_s32(&ctrl->error) != 0) return false;
-      if (global_ns() - t0 > timeout_ns) {
+      if (global_ns() - t0 >= timeout_ns) {
         atomicCAS(&ctrl->error, 0, kErrTimeout);
         return false;
       }

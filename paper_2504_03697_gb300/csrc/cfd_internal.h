@@ -143,6 +143,12 @@ cudaError_t launch_divergence(const PhysArgs& a, cudaStream_t s, int64_t* launch
 cudaError_t launch_correct(const PhysArgs& a, cudaStream_t s, int64_t* launches);
 cudaError_t launch_zero_wall_faces(const PhysArgs& a, cudaStream_t s, int64_t* launches);
 cudaError_t launch_fill(double* p, size_t n, double value, cudaStream_t s, int64_t* launches);
+// Training pair of the learned preconditioner: r = (b - mean b) - A xk and
+// e = (xs - xk) - mean(xs - xk), with the FP64 pressure operator A.  r must
+// not overlap xk.  scratch: harvest_scratch_doubles() device doubles.
+cudaError_t launch_harvest_pair(GridDims g, const double* b, const double* xs, const double* xk, double* r, double* e,
+                                double* scratch, cudaStream_t s, int64_t* launches);
+size_t harvest_scratch_doubles();
 
 // Co-resident block count for the persistent solve kernels on this device.
 int cg_max_coresident_blocks(int kind_is_ir);

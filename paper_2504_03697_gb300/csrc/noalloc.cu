@@ -1,13 +1,18 @@
 // Allocation-free variant of the standalone pressure solve.
 //
-// Some callers cannot allocate device memory at all: code running inside a
-// host callback or an interrupt-like context, plug-ins whose host application
-// owns the allocator and forbids outside allocations, or embedded runtimes
-// that reserve all device memory up front.  cfd_poisson_solve_noalloc serves
-// them: it runs the same persistent CG kernel as cfd_solve_pressure, but its
-// scratch vectors live in one file-scope __device__ array of fixed size
-// instead of a caller-provided workspace, and it calls no allocating routine
-// (no cudaMalloc / cudaFree, no torch, no library that allocates).
+// Some callers cannot allocate device memory at all: plug-ins whose host
+// application owns the allocator and forbids outside allocations, or
+// embedded runtimes that reserve all device memory up front.
+// cfd_poisson_solve_noalloc serves them: it runs the persistent FP64 CG of
+// cfd_solve_pressure in its two-reduction (textbook) form -- the array has
+// no room for the three extra vectors of the single-reduction form, so
+// rounding and iteration counts may differ slightly from cfd_solve_pressure's
+// default form -- with its scratch vectors in one file-scope __device__
+// array of fixed size instead of a caller-provided workspace, and it calls
+// no allocating routine (no cudaMalloc / cudaFree, no torch, no library
+// that allocates).  It does call the CUDA runtime (copies, a memset, a
+// kernel launch), so it must not be called from inside a CUDA stream
+// callback (cudaLaunchHostFunc), where CUDA calls are not allowed.
 //
 // Limits and sharing rules (also stated in include/cfd.h):
 //  * at most CFD_NOALLOC_MAX_CELLS cells; larger grids are rejected with
@@ -17,9 +22,9 @@
 //  * all calls share the one array per device, so calls whose GPU work
 //    overlaps (different streams, or different host threads on one device)
 //    race; serialise them on one stream;
-//  * the first call on a device looks up the array's device address (once
-//    per device, with that device current); make that first call before any
-//    stream capture.
+//  * the first call on a device looks up the array's device address (with
+//    that device current); make that first call before any stream capture.
+//    A failed lookup is not cached: the next call on that device tries again.
 
 #include <mutex>
 
@@ -49,12 +54,30 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
 constexpr int kMaxDevices = 64;
 struct DeviceScratch {
-  std::once_flag once;
-  cudaError_t err = cudaSuccess;
-  unsigned char* ptr = nullptr;  // device address of g_noalloc_scratch on that device
-  int blocks = 0;                // co-resident blocks of the solve kernel
+  std::mutex mu;
+  unsigned char* ptr = nullptr;  // device address of g_noalloc_scratch on that device (set once found)
+  int blocks = 0;                // co-resident blocks of the solve kernel, capped at kNoallocMaxBlocks
 };
 DeviceScratch g_dev[kMaxDevices];
+
+// The device address of the array and the launch width on the current
+// device, looked up on the first successful call and kept; a failed lookup
+// leaves nothing behind, so that a later call tries again.
+cudaError_t device_scratch(DeviceScratch& ds, unsigned char** ptr, int* blocks) {
+  std::lock_guard<std::mutex> lock(ds.mu);
+  if (!ds.ptr) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return e != cudaSuccess ? e : cudaErrorInvalidSymbol;
+    int nb = cg_max_coresident_blocks(0);
+    if (nb < 1) return cudaErrorInvalidConfiguration;
+    ds.blocks = nb > kNoallocMaxBlocks ? kNoallocMaxBlocks : nb;
+    ds.ptr = static_cast<unsigned char*>(p);
+  }
+  *ptr = ds.ptr;
+  *blocks = ds.blocks;
+  return cudaSuccess;
+}
 
 }  // namespace
 }  // namespace cfd
@@ -78,22 +101,15 @@ extern "C" int cfd_poisson_solve_noalloc(int32_t nx, int32_t ny, int32_t nz, con
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cfd_internal_error(CFD_ERR_CUDA, "noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return cfd_internal_error(CFD_ERR_INVALID_ARG, "noalloc: device ordinal %d too large", dev);
-  DeviceScratch& ds = g_dev[dev];
-  // once per device, with that device current: host code may not use the
-  // array's name as an address, so look the device address up here
-  std::call_once(ds.once, [&]() {
-    void* p = nullptr;
-    ds.err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    ds.ptr = static_cast<unsigned char*>(p);
-    if (ds.err == cudaSuccess) ds.blocks = cg_max_coresident_blocks(0);
-  });
-  if (ds.err != cudaSuccess || !ds.ptr)
-    return cfd_internal_error(CFD_ERR_CUDA, "noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(ds.err));
-  if (ds.blocks < 1) return cfd_internal_error(CFD_ERR_CUDA, "noalloc: the solve kernel cannot be placed on device %d", dev);
-  if (ds.blocks > kNoallocMaxBlocks) ds.blocks = kNoallocMaxBlocks;
+  // host code may not use the array's name as an address: look the device
+  // address up with this device current (kept after the first success)
+  unsigned char* base = nullptr;
+  int blocks = 0;
+  e = device_scratch(g_dev[dev], &base, &blocks);
+  if (e != cudaSuccess)
+    return cfd_internal_error(CFD_ERR_CUDA, "noalloc: scratch lookup on device %d: %s", dev, cudaGetErrorString(e));
 
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  unsigned char* base = ds.ptr;
   double* b = reinterpret_cast<double*>(base + kOffB);
   SolveCtrl* ctrl = reinterpret_cast<SolveCtrl*>(base + kOffCtrl);
   DevSolveStats* dstats = reinterpret_cast<DevSolveStats*>(base + kOffStats);
@@ -132,9 +148,10 @@ extern "C" int cfd_poisson_solve_noalloc(int32_t nx, int32_t ny, int32_t nz, con
   a.ctrl = ctrl;
   a.partials = reinterpret_cast<double*>(base + kOffPartials);
   a.stats = dstats;
-  a.tz = solve_tile_depth(nz);
+  // e0..e2 stay null: launch_cg then takes the two-reduction CG form, and it
+  // picks the stencil tile depth itself
   LaunchGeom lg{};
-  lg.blocks = ds.blocks;
+  lg.blocks = blocks;
   e = launch_cg(a, lg, s, nullptr);
   if (e != cudaSuccess) return cfd_internal_error(CFD_ERR_CUDA, "noalloc: launch: %s", cudaGetErrorString(e));
   if (!stats) return CFD_OK;

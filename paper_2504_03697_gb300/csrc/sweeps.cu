@@ -279,6 +279,72 @@ __global__ void __launch_bounds__(kSweepThreads) fill_kernel(double* p, size_t n
   for (size_t e = gtid(); e < n; e += gstride()) p[e] = value;
 }
 
+
+// ---------------------------------------------------------------------------
+// Training pairs of the learned preconditioner: with b' = b - mean(b), the
+// residual of an iterate x_k is r = b' - A x_k and its error against the
+// converged solution x* is e = (x* - x_k) - mean(x* - x_k) (the Neumann
+// system fixes x only up to a constant).  Means by fixed-order sums.
+// ---------------------------------------------------------------------------
+constexpr int kHarvestBlocks = 512;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += sh[w];
+  __syncthreads();
+  return t;  // valid in thread 0
+}
+
+// part[block] = sum of b, part[nb + block] = sum of x* - x_k over the block's cells
+__global__ void __launch_bounds__(kSweepThreads) harvest_sums_kernel(const double* b, const double* xs,
+                                                                     const double* xk, size_t n, double* part) {
+  __shared__ double sh[kSweepThreads / 32];
+  double sb = 0.0, se = 0.0;
+  for (size_t e = gtid(); e < n; e += gstride()) {
+    sb += b[e];
+    se += xs[e] - xk[e];
+  }
+  sb = block_sum(sb, sh);
+  se = block_sum(se, sh);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = sb;
+    part[gridDim.x + blockIdx.x] = se;
+  }
+}
+
+// one block: part[2 nb] = mean(b), part[2 nb + 1] = mean(x* - x_k), summing
+// the block sums in block order
+__global__ void __launch_bounds__(kSweepThreads) harvest_means_kernel(double* part, int nb, size_t n) {
+  __shared__ double sh[kSweepThreads / 32];
+  double sb = 0.0, se = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    sb += part[i];
+    se += part[nb + i];
+  }
+  sb = block_sum(sb, sh);
+  se = block_sum(se, sh);
+  if (threadIdx.x == 0) {
+    part[2 * nb] = sb / double(n);
+    part[2 * nb + 1] = se / double(n);
+  }
+}
+
+// r holds A x_k on entry: r = (b - mean b) - A x_k, e = (x* - x_k) - mean
+__global__ void __launch_bounds__(kSweepThreads) harvest_pair_kernel(const double* b, const double* xs,
+                                                                     const double* xk, size_t n,
+                                                                     const double* means, double* r, double* e) {
+  const double mb = means[0], me = means[1];
+  for (size_t c = gtid(); c < n; c += gstride()) {
+    r[c] = (b[c] - mb) - r[c];
+    e[c] = (xs[c] - xk[c]) - me;
+  }
+}
+
 int sweep_blocks(size_t n) {
   size_t b = (n + kSweepThreads - 1) / kSweepThreads;
   const size_t cap = 152 * 16;  // grid-stride beyond ~16 resident blocks per SM
@@ -340,5 +406,24 @@ cudaError_t launch_fill(double* p, size_t n, double value, cudaStream_t s, int64
   if (launches) *launches += 1;
   return cudaGetLastError();
 }
+
+cudaError_t launch_harvest_pair(GridDims g, const double* b, const double* xs, const double* xk, double* r, double* e,
+                                double* scratch, cudaStream_t s, int64_t* launches) {
+  const size_t n = g.count();
+  int nb = sweep_blocks(n);
+  if (nb > kHarvestBlocks) nb = kHarvestBlocks;
+  harvest_sums_kernel<<<nb, kSweepThreads, 0, s>>>(b, xs, xk, n, scratch);
+  harvest_means_kernel<<<1, kSweepThreads, 0, s>>>(scratch, nb, n);
+  if (launches) *launches += 2;
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  err = launch_apply_poisson(g, xk, r, 0, s, launches);
+  if (err != cudaSuccess) return err;
+  harvest_pair_kernel<<<sweep_blocks(n), kSweepThreads, 0, s>>>(b, xs, xk, n, scratch + 2 * nb, r, e);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
+size_t harvest_scratch_doubles() { return size_t(2) * kHarvestBlocks + 2; }
 
 }  // namespace cfd

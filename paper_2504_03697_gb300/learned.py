@@ -80,21 +80,19 @@ class Harvester:
         self.capped = {k: cfd.Cavity(cfd.make_params(n, n, n, rtol=1e-15, max_iters=k)) for k in self.ks}
 
     def pairs(self, b: torch.Tensor):
-        """(R, E) [len(ks), V] for one system."""
+        """(R, E) [len(ks), V] for one system: each solve removes the mean of
+        b itself, and cfd_harvest_pair forms r = (b - mean b) - A x_k and
+        e = (x* - x_k) - mean(x* - x_k)."""
         V = b.numel()
-        bm = b - b.mean()
-        xs = torch.zeros_like(bm)
-        self.exact.solve_pressure(bm, xs, stats=False)
+        xs = torch.zeros_like(b)
+        self.exact.solve_pressure(b, xs, stats=False)
         R = torch.empty(len(self.ks), V, dtype=torch.float64, device="cuda")
         E = torch.empty_like(R)
-        xk = torch.empty_like(bm)
+        xk = torch.empty_like(b)
         for i, k in enumerate(self.ks):
             xk.zero_()
-            self.capped[k].solve_pressure(bm, xk, stats=False)
-            self.exact.apply_poisson(xk, R[i])
-            R[i].neg_().add_(bm)
-            E[i].copy_(xs).sub_(xk)
-            E[i].sub_(E[i].mean())
+            self.capped[k].solve_pressure(b, xk, stats=False)
+            self.exact.harvest_pair(b, xs, xk, R[i], E[i])
         return R, E
 
 

@@ -1,9 +1,11 @@
 """The allocation-free pressure solve (cfd_poisson_solve_noalloc).
 
-Callers that may not allocate device memory (host callbacks, plug-ins whose
-host owns every allocation, runtimes that reserve all memory up front)
-cannot give the library the workspace cfd_create needs; this entry point
-keeps its scratch in a fixed __device__ array instead.  The test calls it
+Callers that may not allocate device memory (plug-ins whose host owns every
+allocation, runtimes that reserve all memory up front) cannot give the
+library the workspace cfd_create needs; this entry point keeps its scratch
+in a fixed __device__ array instead.  It runs the two-reduction CG form
+(the library's default is the single-reduction form), so the iteration
+counts may differ by one.  The test calls it
 through the C-ABI twice in a row, on two different right-hand sides, and
 checks each result against the workspace-based cfd_solve_pressure within
 the FP64 parity tolerance of the other GPU tests.  The second call also
