@@ -33,7 +33,10 @@ up(pool x) + up(up(pool(pool x))), checked against block means computed with
 numpy reshapes; the loss operator against the assembled CSR matrix and its
 null space; gradients against finite differences; one Adam step from
 zero moments moves every weight by lr * sign(g) (|g| >> eps); M is
-invariant to the scale of r.  This module is test infrastructure (see the
+invariant to the scale of r; with ``store=bf16_store`` every stored
+activation is a BF16 value, the pass-through network's output stays within
+the BF16 rounding bound of its float64 output, and on inputs whose block
+means are BF16 values it equals the float64 output.  This module is test infrastructure (see the
 package header).
 """
 from __future__ import annotations
@@ -89,22 +92,37 @@ def up2(x):
     return x.repeat_interleave(2, 1).repeat_interleave(2, 2).repeat_interleave(2, 3)
 
 
-def forward(layers, x):
-    """U(x) for x [1, Z, Y, X]; returns (z [1, Z, Y, X], dict of activations)."""
-    a = {"xin": x}
-    a["a0"] = conv(x, *layers[0])
-    a["s0"] = conv(a["a0"], *layers[1])
-    a["p0"] = pool2(a["s0"])
-    a["a1"] = conv(a["p0"], *layers[2])
-    a["s1"] = conv(a["a1"], *layers[3])
-    a["p1"] = pool2(a["s1"])
-    a["a2"] = conv(a["p1"], *layers[4])
-    a["s2"] = conv(a["a2"], *layers[5])
+def bf16_store(t):
+    """Round to the nearest BF16 value and back to float64: how the CUDA
+    network stores its input and activations (BF16 storage, FP32
+    accumulation).  Used only to compare with it in the same precision."""
+    return t.to(torch.bfloat16).to(torch.float64)
+
+
+def forward(layers, x, store=None):
+    """U(x) for x [1, Z, Y, X]; returns (z [1, Z, Y, X], dict of activations).
+
+    store (optional) is applied to the input and to every activation the
+    network stores (each convolution and pooling output; up-sampling copies
+    stored values, and the head's output is kept at float32 when store is
+    given), e.g. ``bf16_store``; by default nothing is rounded."""
+    s = store if store is not None else (lambda t: t)
+    a = {"xin": s(x)}
+    a["a0"] = s(conv(a["xin"], *layers[0]))
+    a["s0"] = s(conv(a["a0"], *layers[1]))
+    a["p0"] = s(pool2(a["s0"]))
+    a["a1"] = s(conv(a["p0"], *layers[2]))
+    a["s1"] = s(conv(a["a1"], *layers[3]))
+    a["p1"] = s(pool2(a["s1"]))
+    a["a2"] = s(conv(a["p1"], *layers[4]))
+    a["s2"] = s(conv(a["a2"], *layers[5]))
     a["u1"] = up2(a["s2"])
-    a["d1"] = conv(torch.cat([a["s1"], a["u1"]]), *layers[6])
+    a["d1"] = s(conv(torch.cat([a["s1"], a["u1"]]), *layers[6]))
     a["u0"] = up2(a["d1"])
-    a["d0"] = conv(torch.cat([a["s0"], a["u0"]]), *layers[7])
+    a["d0"] = s(conv(torch.cat([a["s0"], a["u0"]]), *layers[7]))
     z = conv(a["d0"], *layers[8])
+    if store is not None:
+        z = z.to(torch.float32).to(torch.float64)
     return z, a
 
 
@@ -113,12 +131,13 @@ def scale_of(r: np.ndarray) -> float:
     return np.sqrt(r.size) / nrm if nrm > 0 else 0.0
 
 
-def precondition(layers, r: np.ndarray) -> np.ndarray:
-    """M(r) = U(s r) / s with its mean removed; r shaped (Z, Y, X)."""
+def precondition(layers, r: np.ndarray, store=None) -> np.ndarray:
+    """M(r) = U(s r) / s with its mean removed; r shaped (Z, Y, X).  store
+    as for ``forward``."""
     s = scale_of(r)
     if s == 0.0:
         return np.zeros_like(r)
-    z, _ = forward(layers, torch.from_numpy(r * s)[None])
+    z, _ = forward(layers, torch.from_numpy(r * s)[None], store=store)
     z = z[0].numpy() / s
     return z - z.mean()
 

@@ -151,12 +151,15 @@ def passthrough_params(w0=1.0, w1=1.0):
 @pytest.mark.parametrize("shape,w", [((16, 16, 16), (1.0, 1.0)), ((16, 12, 8), (4.0, 4.0)),
                                      ((24, 20, 16), (4.0, 4.0))])
 def test_fpcg_matches_oracle_flexible_cg(cfd, shape, w):
-    """The CUDA flexible PCG against oracle.krylov.fpcg with the float64
-    network on the same parameters (BF16 values of the hand-set weights are
-    exact).  The GPU network rounds its activations to BF16 (relative 2^-8),
-    so the two preconditioners differ slightly: the iteration counts must
-    agree within 10 % (at least 3), neither may fall back to plain CG, and
-    the solutions must lie within the rtol bound of each other."""
+    """The CUDA flexible PCG against oracle.krylov.fpcg with the oracle's
+    network on the same parameters (the hand-set weights are BF16 values).
+    The oracle's network stores its input and activations rounded to BF16,
+    as the CUDA network does (``oracle.unet.bf16_store``), so both run
+    flexible CG with the same preconditioner up to FP32-vs-FP64 accumulation
+    order: the iteration counts must agree within 5 % (at least 3), neither
+    may fall back to plain CG, and the solutions must lie within the rtol
+    bound of each other.  The float64 network is run too and its count
+    printed: BF16 storage costs flexible CG some iterations."""
     nx, ny, nz = shape
     params = passthrough_params(*w)
     net = cfd.UNet(nx, ny, nz, seed=0)
@@ -168,10 +171,13 @@ def test_fpcg_matches_oracle_flexible_cg(cfd, shape, w):
     assert rc == cfd.CFD_OK and st["outer_iters"] == 0, st
     layers = ou.unflatten(params.double())
     A = poisson_csr(nx, ny, nz)
-    xo, so = fpcg(A, b.ravel(), lambda r: ou.precondition(layers, r.reshape(nz, ny, nx)).ravel(), rtol=RTOL,
-                  max_iters=20 * max(shape))
+    cap = 20 * max(shape)
+    xo, so = fpcg(A, b.ravel(), lambda r: ou.precondition(layers, r.reshape(nz, ny, nx), store=ou.bf16_store).ravel(),
+                  rtol=RTOL, max_iters=cap)
+    _, s64 = fpcg(A, b.ravel(), lambda r: ou.precondition(layers, r.reshape(nz, ny, nx)).ravel(), rtol=RTOL,
+                  max_iters=cap)
     assert so.converged and not so.fell_back, so
-    assert abs(st["iters"] - so.iters) <= max(3, so.iters // 10), (st["iters"], so.iters)
+    assert abs(st["iters"] - so.iters) <= max(3, so.iters // 20), (st["iters"], so.iters)
     bo = b.ravel() - b.mean()
     x = xg.cpu().numpy()
     true_rel = np.linalg.norm(bo - A @ x) / np.linalg.norm(bo)
@@ -179,8 +185,8 @@ def test_fpcg_matches_oracle_flexible_cg(cfd, shape, w):
     d = (x - x.mean()) - (xo - xo.mean())
     bound = 2 * RTOL * np.linalg.norm(bo) / lam_min(shape)
     assert np.linalg.norm(d) <= bound, (np.linalg.norm(d), bound)
-    print(f"FPCG {shape} w={w}: GPU {st['iters']} iterations, oracle {so.iters}; "
-          f"max|dx| {np.abs(d).max():.2e} (bound {bound:.2e})")
+    print(f"FPCG {shape} w={w}: GPU {st['iters']} iterations, oracle {so.iters} (BF16 storage), "
+          f"{s64.iters} (float64 network); max|dx| {np.abs(d).max():.2e} (bound {bound:.2e})")
 
 
 @pytest.mark.parametrize("form", ["graph", "persistent"])

@@ -69,6 +69,30 @@ def test_passthrough_network_closed_form():
     assert np.allclose(z[0].numpy(), x + 3 * block_mean(x, 2) + 6 * block_mean(x, 4), atol=1e-12)
 
 
+def test_bf16_storage_emulation():
+    """store=bf16_store rounds what the CUDA network stores: every stored
+    activation is a BF16 value; on small integer inputs whose block means
+    are BF16 values nothing rounds (output = the float64 output); on a
+    Gaussian input the output stays within a few BF16 roundings of the
+    float64 output."""
+    rng = np.random.default_rng(5)
+    layers = passthrough_layers((2.0, 3.0))
+    x = rng.standard_normal((8, 12, 16))
+    z, acts = unet.forward(layers, torch.from_numpy(x)[None], store=unet.bf16_store)
+    for name, t in acts.items():
+        assert torch.equal(t, t.to(torch.bfloat16).to(torch.float64)), name
+    z64, _ = unet.forward(layers, torch.from_numpy(x)[None])
+    bound = 16 * 2.0 ** -9 * (np.abs(x) + 3 * np.abs(block_mean(x, 2)) + 6 * np.abs(block_mean(x, 4)))
+    assert np.all(np.abs(z[0].numpy() - z64[0].numpy()) <= bound)
+    assert not np.array_equal(z[0].numpy(), z64[0].numpy())  # something was rounded
+    # entries 64 k, k in {-1, 0, 1}: every activation of the unit pass-through
+    # network is an integer of magnitude <= 192, exact in BF16
+    xi = 64.0 * rng.integers(-1, 2, size=(8, 12, 16)).astype(np.float64)
+    zi, _ = unet.forward(passthrough_layers(), torch.from_numpy(xi)[None], store=unet.bf16_store)
+    zi64, _ = unet.forward(passthrough_layers(), torch.from_numpy(xi)[None])
+    assert torch.equal(zi, zi64)
+
+
 def test_flat_layout_roundtrip_and_tap_order():
     assert unet.param_count() == sum(ks ** 3 * co * (a + b) + co for _, _, a, b, co, ks in unet.LAYERS)
     flat = torch.arange(unet.param_count(), dtype=torch.float64)
