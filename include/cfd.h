@@ -83,8 +83,23 @@ enum { CFD_FIELD_U = 0, CFD_FIELD_V = 1, CFD_FIELD_W = 2, CFD_FIELD_P = 3 };
  *           iteration; calls using it synchronise the stream.  Pressure only
  *           (the diffusion solves use CG); not available in batches.
  *   FPCG    flexible PCG with the learned U-Net preconditioner attached by
- *           cfd_attach_preconditioner (see cfd_unet_fpcg_solve); pressure
- *           only, cold start, host-driven; not available in batches.       */
+ *           cfd_attach_preconditioner; pressure only; not available in
+ *           batches.  Two forms (cfd_set_fpcg_form):
+ *             GRAPH (default) flexible CG with FP32 vectors and FP64
+ *                   reliable-update refinement, as the IR solver, with
+ *                   z = M(r) from the network in every FP32 iteration, the
+ *                   Polak-Ribiere beta, and the switch to plain CG (after
+ *                   50 iterations without halving the residual norm, or a
+ *                   breakdown) decided on the device: one CUDA graph per
+ *                   solve, no host round trip per iteration.  Convergence
+ *                   on the FP64 true residual.  Stats: iters = FP32
+ *                   iterations, outer_iters = FP64 refinements, restarts =
+ *                   iterations run as plain CG.  The diffusion solves of
+ *                   the step then run as in IR (mixed precision).  Needs
+ *                   nx % 4 == 0 (the network's grids do).
+ *             HOST  the FP64 flexible PCG of cfd_unet_fpcg_solve (cold
+ *                   start, host-driven; stats as documented there); the
+ *                   diffusion solves run in FP64 CG.                      */
 enum { CFD_SOLVER_CG = 0, CFD_SOLVER_JACOBI = 1, CFD_SOLVER_IR = 2, CFD_SOLVER_DIC = 3, CFD_SOLVER_FPCG = 4 };
 
 /* Substeps for cfd_substep (kernel-level access to one phase of the step). */
@@ -113,7 +128,14 @@ typedef struct {
                                (well-conditioned systems)                        */
   int32_t advect_order;     /* backtrace: 0 or 1 explicit Euler x - dt v(x); 2 the
                                explicit midpoint rule x - dt v(x - dt/2 v(x))     */
-  int32_t reserved[7];      /* must be zero                                       */
+  int32_t learned_guess;    /* 1 (solver IR, with a U-Net attached by
+                               cfd_attach_preconditioner): every pressure solve
+                               starts from x0 = alpha M(b), M the network
+                               (cfd_unet_apply) and alpha = M(b).b / M(b).A M(b),
+                               the multiple of M(b) of least energy-norm error;
+                               graph form of the IR solve only; 0: cold start
+                               (or warm start)                                   */
+  int32_t reserved[6];      /* must be zero                                       */
 } cfd_params;
 
 typedef struct {
@@ -230,6 +252,11 @@ int cfd_set_cg_variant(cfd_handle *h, int variant);
  * persistent multi-problem kernel. */
 enum { CFD_IR_AUTO = 0, CFD_IR_PERSISTENT = 1, CFD_IR_GRAPH = 2 };
 int cfd_set_ir_form(cfd_handle *h, int form);
+
+/* Form of the CFD_SOLVER_FPCG pressure solve (see CFD_SOLVER_FPCG).
+ * Errors: unknown form; a handle whose solver is not FPCG. */
+enum { CFD_FPCG_GRAPH = 0, CFD_FPCG_HOST = 1 };
+int cfd_set_fpcg_form(cfd_handle *h, int form);
 
 /* Run the three diffusion solves of a step (nu > 0) at once (on = 1): u on
  * the handle's stream, v and w on two internal streams forked from and
@@ -570,14 +597,32 @@ int cfd_unet_read_tensor(cfd_unet *u, int which, void *host, int64_t count);
 int cfd_unet_fpcg_solve(cfd_unet *u, const double *b_dev, double *x_dev, double rtol, int32_t max_iters,
                         cfd_solve_stats *stats);
 
-/* Attach the U-Net u (same grid as h; NULL detaches) as the preconditioner
- * of a cavity created with solver CFD_SOLVER_FPCG: its pressure solves
- * (cfd_step, cfd_substep, cfd_solve_pressure) then run cfd_unet_fpcg_solve
- * with the handle's rtol and iteration cap; the step's gauge follows.  The
- * handle's stream is synchronised before each solve (the network runs on
- * its own stream).  u must outlive its attachment; a pressure solve without
- * a network attached returns CFD_ERR_INVALID_ARG. */
+/* Attach the U-Net u (same grid as h; NULL detaches) to a cavity created
+ * with solver CFD_SOLVER_FPCG (the network preconditions flexible CG) or
+ * with solver CFD_SOLVER_IR and learned_guess = 1 (the network gives the
+ * initial guess).  Its pressure solves (cfd_step, cfd_substep,
+ * cfd_solve_pressure) then use it with the handle's rtol and iteration
+ * cap; the step's gauge follows.  In the graph forms the network's forward
+ * pass is captured into the solve's graph and runs on the handle's stream,
+ * reading the network's workspace (input, activations, output): do not use
+ * the network on another stream while such a solve may run.  Changing the
+ * network's parameters between solves is fine (the graph reads them from
+ * its workspace); its convolution mode is captured, and a change rebuilds
+ * the graph.  The HOST form of FPCG synchronises the handle's stream
+ * before each solve (the network runs on its own stream).  u must outlive
+ * its attachment; a pressure solve that needs a network without one
+ * attached returns CFD_ERR_INVALID_ARG. */
 int cfd_attach_preconditioner(cfd_handle *h, cfd_unet *u);
+
+/* The learned initial guess alone: x = alpha (z - mean z) with z = U(s b'),
+ * b' = b - mean(b), s = sqrt(V) / |b'| (the network of cfd_unet_apply on
+ * the attached U-Net) and alpha = z~.b' / z~.A z~ (z~ = z - mean z): the
+ * multiple of the network's answer closest to A^+ b' in the energy norm
+ * (alpha = 0 when the network returns a constant or its wait timed out).
+ * b_dev, x_dev: distinct device arrays of nx*ny*nz float64.  Needs a handle
+ * with solver IR or FPCG, nx % 4 == 0 and a network attached.
+ * Asynchronous on the handle's stream; uses the network's workspace. */
+int cfd_learned_guess(cfd_handle *h, const double *b_dev, double *x_dev);
 
 int64_t cfd_unet_launch_count(const cfd_unet *u);
 const char *cfd_unet_last_error(void);

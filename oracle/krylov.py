@@ -40,7 +40,8 @@ with FP64 inner vectors and no refinement before convergence it takes
 ``pcg``'s iterates bit for bit on an SPD matrix; in FP32 it meets the FP64
 true-residual tolerance and lies within 2 rtol ||b|| / lambda_min of the
 dense solve of the pressure system (within 2 rtol ||b|| for I + c L); a
-smaller refinement factor needs fewer refinements.
+smaller refinement factor needs fewer refinements; x0 = 0 reproduces the
+cold start bit for bit and x0 = the solution takes no iteration.
 
 ``fpcg`` (flexible PCG for a preconditioner that may vary between
 iterations) is pinned by tests/test_oracle_unet.py: with M = identity or a
@@ -50,6 +51,17 @@ as M = I (flexible CG is invariant to the preconditioner's scale), with M =
 the exact inverse on the zero-mean subspace it converges in one iteration,
 and a preconditioner returning zero (breakdown) or a fixed vector
 (stagnation) makes it fall back to plain CG and still converge.
+
+``ir_fpcg`` (flexible CG with its recurrence in FP32 and FP64 reliable
+updates: the learned-preconditioner solve in mixed precision) is pinned by
+tests/test_oracle_solver.py: with FP64 inner vectors and no refinement
+before convergence it takes the iteration counts and the solution of
+``pcg`` with the identity and with a fixed SPD diagonal preconditioner, and
+of ``fpcg`` with the same preconditioner; in FP32 it meets the FP64
+true-residual tolerance and lies within 2 rtol ||b|| / lambda_min of the
+dense solve; M and -3 M give the same iterates in FP64; a zero
+preconditioner (breakdown) or an input-independent one (stagnation) makes
+it fall back to plain CG and still converge.
 """
 from __future__ import annotations
 
@@ -279,7 +291,7 @@ class IrStats:
     rel_resid: float = 0.0    # true ||b - A x|| / ||b|| at exit
 
 
-def ir_cg(A, b, rtol=1e-8, delta=0.1, max_iters=10000, max_outer=1000, inner=np.float32, singular=True):
+def ir_cg(A, b, rtol=1e-8, delta=0.1, max_iters=10000, max_outer=1000, inner=np.float32, singular=True, x0=None):
     """CG with an inner recurrence in a lower precision and FP64 reliable
     updates (the mixed-precision solve of the pressure and diffusion systems:
     Sec. 3.1's CG with its vectors, operator and recurrence in `inner`).
@@ -296,8 +308,9 @@ def ir_cg(A, b, rtol=1e-8, delta=0.1, max_iters=10000, max_outer=1000, inner=np.
     FP64, the true residual is recomputed, and the next direction keeps p
     with beta = (new r_in . r_in) / rz (the residual it replaces).
     Otherwise beta = rz' / rz.  Convergence is declared on the FP64 true
-    residual only.  b has its mean removed first when `singular`.
-    Returns (x, IrStats)."""
+    residual only.  b has its mean removed first when `singular`.  x0
+    (optional) is the starting iterate (the first true residual is
+    b - A x0); by default 0.  Returns (x, IrStats)."""
     A64 = A.astype(np.float64)
     Ain = A.astype(inner)
     b = np.asarray(b, dtype=np.float64)
@@ -311,8 +324,10 @@ def ir_cg(A, b, rtol=1e-8, delta=0.1, max_iters=10000, max_outer=1000, inner=np.
         st.converged = True
         return x, st
     tol2 = rtol * rtol * bb
-    r = b.copy()
-    rr = bb
+    if x0 is not None:
+        x = np.array(x0, dtype=np.float64, copy=True).ravel()
+    r = b - A64 @ x if x0 is not None else b.copy()
+    rr = float(np.dot(r, r))
     p = np.zeros(n, dtype=inner)
     rz = 0.0
     beta = 0.0
@@ -350,6 +365,131 @@ def ir_cg(A, b, rtol=1e-8, delta=0.1, max_iters=10000, max_outer=1000, inner=np.
                 break
             beta = rz_new / rz
             rz = rz_new
+        x = x + x_in.astype(np.float64)
+        r = b - A64 @ x
+        rr = float(np.dot(r, r))
+        if not refine:
+            break
+        st.refinements += 1
+    st.converged = st.converged or rr <= tol2
+    st.rel_resid = float(np.sqrt(rr / bb))
+    return x, st
+
+
+@dataclass
+class FlexIrStats:
+    iters: int = 0            # inner (low-precision) flexible-CG iterations
+    refinements: int = 0      # FP64 true-residual replacements
+    plain_iters: int = 0      # iterations run as plain CG after a fall-back
+    converged: bool = False
+    breakdown: bool = False
+    rel_resid: float = 0.0    # true ||b - A x|| / ||b|| at exit
+
+
+def ir_fpcg(A, b, precond, rtol=1e-8, delta=0.1, max_iters=10000, max_outer=1000, stagnation=50,
+            inner=np.float32):
+    """Flexible CG (Polak-Ribiere) with its recurrence in a lower precision
+    and FP64 reliable updates: the learned-preconditioner pressure solve in
+    mixed precision (``fpcg`` in the precision split of ``ir_cg``).
+
+    The FP64 state is x and the true residual r = b - A x (b has its mean
+    removed; the Neumann pressure system).  A refinement loads r_in = r -
+    mean(r) in `inner` precision and a zero correction x_in.  Each inner
+    iteration, vectors and operator in `inner` precision, inner products
+    summed in FP64:
+        z = M(r_in) (r_in itself once running as plain CG), z~ = z - mean(z),
+        beta = -alpha_old z~.q_old / (z~.r)_old   (0 for a new direction),
+        p = z~ + beta p,  q = A p,  alpha = z~.r_in / p.q,
+        x_in += alpha p,  r_in -= alpha q.
+    -alpha_old q_old is r_new - r_old, so beta is the Polak-Ribiere one; after
+    a refinement it is formed the same way (the direction is kept).  When
+    r_in.r_in has fallen by delta^2 below the true residual of the last
+    refinement (or below rtol^2 ||b||^2) the correction is added to x in
+    FP64 and the true residual recomputed.  z~.r_in = 0 (or a non-finite
+    value) switches to plain CG along r_in; a direction with p.q <= 0 (or
+    `stagnation` iterations without the residual norm halving) switches to
+    plain CG from the next true residual (a refinement, then a new
+    direction).  Convergence only on the
+    FP64 true residual.  Returns (x, FlexIrStats)."""
+    A64 = A.astype(np.float64)
+    Ain = A.astype(inner)
+    b = np.asarray(b, dtype=np.float64)
+    b = b - b.mean()
+    n = b.size
+    st = FlexIrStats()
+    x = np.zeros(n)
+    bb = float(np.dot(b, b))
+    if bb == 0.0:
+        st.converged = True
+        return x, st
+
+    def dot(u, v):
+        return float(np.dot(u.astype(np.float64), v.astype(np.float64)))
+
+    tol2 = rtol * rtol * bb
+    r = b.copy()
+    rr = bb
+    p = np.zeros(n, dtype=inner)
+    q_old = np.zeros(n, dtype=inner)
+    alpha = zr = best = 0.0
+    first, plain, since = True, False, 0
+    while True:
+        if rr <= tol2:
+            st.converged = True
+            break
+        if st.refinements > max_outer or st.iters >= max_iters:
+            break
+        r_in = (r - r.mean()).astype(inner)
+        x_in = np.zeros(n, dtype=inner)
+        rz_ref = rr
+        if st.iters == 0:
+            best = dot(r_in, r_in)
+        refine = False
+        while st.iters < max_iters:
+            z = r_in if plain else np.asarray(precond(r_in.astype(np.float64))).astype(inner)
+            m = float(np.sum(z.astype(np.float64))) / n
+            zr_new = dot(z, r_in) - m * float(np.sum(r_in.astype(np.float64)))
+            zq = 0.0 if first else dot(z, q_old) - m * float(np.sum(q_old.astype(np.float64)))
+            if not plain and not (zr_new != 0.0 and np.isfinite(zr_new) and np.isfinite(zq)):
+                plain, first = True, True  # the preconditioner's step is unusable
+                z = r_in
+                m = float(np.sum(r_in.astype(np.float64))) / n
+                zr_new = dot(r_in, r_in) - m * float(np.sum(r_in.astype(np.float64)))
+                zq = 0.0
+            if not (zr_new != 0.0 and np.isfinite(zr_new)):
+                st.breakdown = True
+                break
+            beta = 0.0 if first else -alpha * zq / zr
+            zr = zr_new
+            zc = (z.astype(np.float64) - m).astype(inner)
+            p = zc if first else (zc + inner(beta) * p).astype(inner)
+            q = (Ain @ p).astype(inner)
+            pq = dot(p, q)
+            if not (pq > 0.0) or not np.isfinite(pq):
+                if plain:
+                    st.breakdown = True
+                    break
+                plain, first, refine = True, True, True  # no usable flexible step:
+                break                                    # plain CG from the true residual
+            alpha = zr / pq
+            x_in = (x_in + inner(alpha) * p).astype(inner)
+            r_in = (r_in - inner(alpha) * q).astype(inner)
+            q_old = q
+            rr_new = dot(r_in, r_in)
+            first = False
+            st.iters += 1
+            if plain:
+                st.plain_iters += 1
+            restart = False
+            if rr_new < 0.25 * best:
+                best, since = rr_new, 0
+            elif not plain:
+                since += 1
+                if since >= stagnation:
+                    plain, first, restart = True, True, True
+            if restart or rr_new <= delta * delta * rz_ref or rr_new <= tol2:
+                refine = True
+                break
         x = x + x_in.astype(np.float64)
         r = b - A64 @ x
         rr = float(np.dot(r, r))

@@ -39,7 +39,8 @@ class cfd_params(ctypes.Structure):
                 ("nu", ctypes.c_double), ("lid_u", ctypes.c_double), ("g", ctypes.c_double * 3),
                 ("solver", ctypes.c_int32), ("rtol", ctypes.c_double), ("max_iters", ctypes.c_int32),
                 ("warm_start", ctypes.c_int32), ("ir_delta", ctypes.c_double),
-                ("advect_order", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("advect_order", ctypes.c_int32), ("learned_guess", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class cfd_tune_report(ctypes.Structure):
@@ -116,6 +117,7 @@ def load_library(path: Optional[str] = None):
         "cfd_autotune_solver": (ctypes.c_int, [vp, ctypes.c_int32, P(cfd_tune_report)]),
         "cfd_set_cg_variant": (ctypes.c_int, [vp, ctypes.c_int]),
         "cfd_set_ir_form": (ctypes.c_int, [vp, ctypes.c_int]),
+        "cfd_set_fpcg_form": (ctypes.c_int, [vp, ctypes.c_int]),
         "cfd_set_concurrent_diffusion": (ctypes.c_int, [vp, ctypes.c_int]),
         "cfd_snapshot": (ctypes.c_int, [vp]),
         "cfd_csr_bytes": (ctypes.c_int, [ctypes.c_int32] * 3 + [P(ctypes.c_size_t), P(ctypes.c_int64)]),
@@ -143,6 +145,7 @@ def load_library(path: Optional[str] = None):
         "cfd_unet_launch_count": (ctypes.c_int64, [vp]),
         "cfd_unet_grid": (ctypes.c_int, [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]),
         "cfd_attach_preconditioner": (ctypes.c_int, [vp, vp]),
+        "cfd_learned_guess": (ctypes.c_int, [vp, vp, vp]),
         "cfd_unet_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -154,7 +157,8 @@ def load_library(path: Optional[str] = None):
 
 
 def make_params(nx, ny, nz, length=1.0, dt=0.01, rho=1.0, nu=0.0, lid_u=1.0, g=(0.0, 0.0, 0.0),
-                solver="cg", rtol=1e-8, max_iters=0, warm_start=False, ir_delta=0.0, advect_order=1) -> cfd_params:
+                solver="cg", rtol=1e-8, max_iters=0, warm_start=False, ir_delta=0.0, advect_order=1,
+                learned_guess=False) -> cfd_params:
     prm = cfd_params()
     prm.nx, prm.ny, prm.nz = int(nx), int(ny), int(nz)
     prm.length, prm.dt, prm.rho, prm.nu, prm.lid_u = float(length), float(dt), float(rho), float(nu), float(lid_u)
@@ -166,6 +170,7 @@ def make_params(nx, ny, nz, length=1.0, dt=0.01, rho=1.0, nu=0.0, lid_u=1.0, g=(
     prm.warm_start = 1 if warm_start else 0
     prm.ir_delta = float(ir_delta)
     prm.advect_order = int(advect_order)
+    prm.learned_guess = 1 if learned_guess else 0
     return prm
 
 
@@ -287,6 +292,11 @@ class Cavity:
         self._net = net
         return self._check(self.lib.cfd_attach_preconditioner(self.h, net.u if net is not None else None))
 
+    def learned_guess(self, b: torch.Tensor, x: torch.Tensor):
+        """x = alpha M(b) from the attached network (cfd_learned_guess)."""
+        assert b.is_cuda and x.is_cuda and b.dtype == torch.float64 and x.dtype == torch.float64
+        return self._check(self.lib.cfd_learned_guess(self.h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr())))
+
     def snapshot(self):
         """Start an asynchronous host copy of (u, v, w, p) (cfd_snapshot)."""
         return self._check(self.lib.cfd_snapshot(self.h))
@@ -302,6 +312,11 @@ class Cavity:
     def set_concurrent_diffusion(self, on: bool):
         """Run the u, v, w diffusion solves of a step at once (small grids)."""
         return self._check(self.lib.cfd_set_concurrent_diffusion(self.h, 1 if on else 0))
+
+    def set_fpcg_form(self, form: str):
+        """Form of the FPCG solve: 'graph' (default: FP32 flexible CG with FP64
+        refinement, device-resident) or 'host' (FP64, host-driven)."""
+        return self._check(self.lib.cfd_set_fpcg_form(self.h, {"graph": 0, "host": 1}[form]))
 
     def set_ir_form(self, form: str):
         """Execution of the IR solve: 'auto' (default), 'persistent' or 'graph'."""

@@ -22,6 +22,7 @@
 #include "cfd_internal.h"
 #include "dic.h"
 #include "ir_graph.h"
+#include "unet.h"
 
 using namespace cfd;
 
@@ -86,9 +87,10 @@ Layout ws_layout(const cfd_params& p, int max_blocks, bool standalone = true) {
   L.e1 = take(vec * 8);
   L.e2 = take(vec * 8);
   if (p.solver == CFD_SOLVER_DIC) L.dicd = take(cells * 8);  // DIC pivots of the pressure matrix
-  if (p.solver == CFD_SOLVER_IR) {
+  if (p.solver == CFD_SOLVER_IR || p.solver == CFD_SOLVER_FPCG) {
     // sized to the largest face grid: the graph form also runs the
-    // diffusion solves in FP32 with FP64 refinement
+    // diffusion solves in FP32 with FP64 refinement (and the flexible CG
+    // with the learned preconditioner uses the same FP32 vectors)
     L.r32 = take(vec * 4);
     L.d32 = take(vec * 4);
     L.p0_32 = take(vec * 4);
@@ -134,6 +136,7 @@ struct cfd_handle {
   cfd::IrGraph* irg = nullptr;   // its cached, instantiated graph (pressure)
   cfd::IrGraph* irg_diff[3] = {nullptr, nullptr, nullptr};  // diffusion of u, v, w
   int ir_form = CFD_IR_AUTO;
+  int fpcg_form = CFD_FPCG_GRAPH;
   unsigned long long wait_ns = kTimeoutNs;  // limit of each grid-wide wait (cfd_set_wait_limit)
   double* partials;
   SolveCtrl* ctrl;
@@ -217,7 +220,13 @@ int validate(const cfd_params* p) {
   if (p->max_iters < 0) return set_err(nullptr, CFD_ERR_INVALID_ARG, "max_iters must be >= 0");
   if (p->ir_delta < 0 || p->ir_delta >= 1) return set_err(nullptr, CFD_ERR_INVALID_ARG, "ir_delta must be in [0, 1)");
   if (p->advect_order < 0 || p->advect_order > 2) return set_err(nullptr, CFD_ERR_INVALID_ARG, "advect_order in {0, 1, 2}");
-  for (int i = 0; i < 7; ++i)
+  if (p->learned_guess != 0 && p->learned_guess != 1)
+    return set_err(nullptr, CFD_ERR_INVALID_ARG, "learned_guess must be 0 or 1");
+  if (p->learned_guess && p->solver != CFD_SOLVER_IR)
+    return set_err(nullptr, CFD_ERR_INVALID_ARG, "learned_guess needs the IR solver");
+  if (p->learned_guess && p->nx % 4 != 0)
+    return set_err(nullptr, CFD_ERR_INVALID_ARG, "learned_guess needs nx %% 4 == 0 (graph form)");
+  for (int i = 0; i < 6; ++i)
     if (p->reserved[i] != 0) return set_err(nullptr, CFD_ERR_INVALID_ARG, "reserved fields must be zero");
   return CFD_OK;
 }
@@ -366,12 +375,18 @@ IrArgs diffusion_ir_args(const cfd_handle* h, int comp, DevSolveStats* st) {
   return a;
 }
 
+// The diffusion solves run in mixed precision (FP32 CG with FP64
+// refinement) for the IR solver and the graph form of FPCG.
+bool ir_diffusion(const cfd_handle* h) {
+  return h->prm.solver == CFD_SOLVER_IR || (h->prm.solver == CFD_SOLVER_FPCG && h->fpcg_form == CFD_FPCG_GRAPH);
+}
+
 // Velocity diffusion solve for component comp (x = intermediate velocity).
 int run_diffusion(cfd_handle* h, int comp, DevSolveStats* st) {
   PhysArgs pa = phys(h);
   int rc = cuda_check(h, launch_diffusion_rhs(pa, comp, h->stream, &h->launches), "diffusion rhs");
   if (rc) return rc;
-  if (h->prm.solver == CFD_SOLVER_IR) {
+  if (ir_diffusion(h)) {
     IrArgs ia = diffusion_ir_args(h, comp, st);
     if (use_ir_graph(h, ia))
       return cuda_check(h, launch_ir_graph(ia, h->irg_state, &h->irg_diff[comp], h->stream), "IR diffusion graph");
@@ -421,13 +436,29 @@ int run_diffusion_concurrent(cfd_handle* h, DevStepStats* st) {
 
 bool diffusion_concurrent(const cfd_handle* h) {
   // the mixed-precision solves share one set of FP32 vectors
-  return h->conc_diffusion && h->aux[0] && h->cset[0][0] && h->prm.solver != CFD_SOLVER_IR;
+  return h->conc_diffusion && h->aux[0] && h->cset[0][0] && !ir_diffusion(h);
 }
 
 // Pressure solve A x = b on the handle's workspace b (already filled).
 int run_pressure(cfd_handle* h, double* x, int zero_x0, int gauge, DevSolveStats* st) {
   int rc = cuda_check(h, cudaMemsetAsync(h->ctrl, 0, sizeof(SolveCtrl), h->stream), "memset ctrl");
   if (rc) return rc;
+  if (h->prm.solver == CFD_SOLVER_FPCG && h->fpcg_form == CFD_FPCG_GRAPH) {
+    // flexible CG with FP32 vectors and FP64 refinement, one graph per solve
+    if (!h->precond_net) return set_err(h, CFD_ERR_INVALID_ARG, "FPCG solver without an attached preconditioner");
+    IrArgs a = pressure_ir_args(h, x, zero_x0, gauge, st, h->ctrl);
+    UNetView nv{};
+    unet_view(h->precond_net, &nv);
+    a.net = h->precond_net;
+    a.net_mode = nv.conv_mode;
+    a.flexible = 1;
+    a.stagnation = 50;
+    if (!ir_graph_eligible(a)) return set_err(h, CFD_ERR_INVALID_ARG, "the FPCG graph form needs nx %% 4 == 0");
+    const int t = phase_begin(h, CFD_PHASE_PCG);
+    rc = cuda_check(h, launch_ir_graph(a, h->irg_state, &h->irg, h->stream), "FPCG graph launch");
+    phase_end(h, t);
+    return rc;
+  }
   if (h->prm.solver == CFD_SOLVER_FPCG) {
     if (!h->precond_net) return set_err(h, CFD_ERR_INVALID_ARG, "FPCG solver without an attached preconditioner");
     rc = cuda_check(h, cudaStreamSynchronize(h->stream), "synchronize");
@@ -481,6 +512,22 @@ int run_pressure(cfd_handle* h, double* x, int zero_x0, int gauge, DevSolveStats
     ds.b_norm = res.b_norm;
     rc = cuda_check(h, cudaMemcpyAsync(st, &ds, sizeof(ds), cudaMemcpyHostToDevice, h->stream), "DIC stats");
     if (!rc) rc = cuda_check(h, cudaStreamSynchronize(h->stream), "synchronize");
+    return rc;
+  }
+  if (h->prm.solver == CFD_SOLVER_IR && h->prm.learned_guess) {
+    // x0 = alpha M(b) from the attached network, then the graph-form solve
+    if (!h->precond_net) return set_err(h, CFD_ERR_INVALID_ARG, "learned_guess without an attached network");
+    IrArgs a = pressure_ir_args(h, x, 0, gauge, st, h->ctrl);
+    UNetView nv{};
+    unet_view(h->precond_net, &nv);
+    a.net = h->precond_net;
+    a.net_mode = nv.conv_mode;
+    a.guess = 1;
+    (void)zero_x0;  // the guess replaces both the cold and the warm start
+    if (!ir_graph_eligible(a)) return set_err(h, CFD_ERR_INVALID_ARG, "learned_guess needs nx %% 4 == 0");
+    const int t = phase_begin(h, CFD_PHASE_PCG);
+    rc = cuda_check(h, launch_ir_graph(a, h->irg_state, &h->irg, h->stream), "IR graph launch");
+    phase_end(h, t);
     return rc;
   }
   if (h->prm.solver == CFD_SOLVER_IR) {
@@ -649,7 +696,7 @@ int create_handle(const cfd_params* params, void* dev_ws, size_t bytes, cfd_stre
   h->b = D(L.b); h->r = D(L.r); h->d0 = D(L.d0); h->d1 = D(L.d1); h->q = D(L.q);
   h->e0 = D(L.e0); h->e1 = D(L.e1); h->e2 = D(L.e2);
   if (params->solver == CFD_SOLVER_DIC) h->dicd = D(L.dicd);
-  if (params->solver == CFD_SOLVER_IR) {
+  if (params->solver == CFD_SOLVER_IR || params->solver == CFD_SOLVER_FPCG) {
     h->r32 = F(L.r32); h->d32 = F(L.d32); h->p0_32 = F(L.p0_32); h->p1_32 = F(L.p1_32); h->q32 = F(L.q32);
     h->irg_state = h->ws + L.irg;
   }
@@ -956,7 +1003,8 @@ __global__ void tune_rhs_kernel(double* b, size_t n) {
 int cfd_attach_preconditioner(cfd_handle* h, cfd_unet* u) {
   if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
   if (u) {
-    if (h->prm.solver != CFD_SOLVER_FPCG) return set_err(h, CFD_ERR_INVALID_ARG, "the handle's solver is not FPCG");
+    if (h->prm.solver != CFD_SOLVER_FPCG && !(h->prm.solver == CFD_SOLVER_IR && h->prm.learned_guess))
+      return set_err(h, CFD_ERR_INVALID_ARG, "a network needs solver FPCG, or IR with learned_guess = 1");
     int nx = 0, ny = 0, nz = 0;
     cfd_unet_grid(u, &nx, &ny, &nz);
     if (nx != h->prm.nx || ny != h->prm.ny || nz != h->prm.nz)
@@ -1107,6 +1155,18 @@ int cfd_harvest_pair(cfd_handle* h, const double* b_dev, const double* xs_dev, c
                     "harvest pair");
 }
 
+int cfd_learned_guess(cfd_handle* h, const double* b_dev, double* x_dev) {
+  if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
+  if (!b_dev || !x_dev || b_dev == x_dev) return set_err(h, CFD_ERR_INVALID_ARG, "b and x must be distinct device arrays");
+  if (!h->precond_net) return set_err(h, CFD_ERR_INVALID_ARG, "no network attached");
+  if (!h->irg_state || h->prm.nx % 4 != 0)
+    return set_err(h, CFD_ERR_INVALID_ARG, "the learned guess needs solver IR or FPCG and nx %% 4 == 0");
+  IrArgs a = pressure_ir_args(h, x_dev, 0, 0, &(h->stats + kStatsCap)->p, h->ctrl);
+  a.b = const_cast<double*>(b_dev);  // read only
+  a.net = h->precond_net;
+  return cuda_check(h, launch_learned_guess(a, h->irg_state, h->stream, &h->launches), "learned guess");
+}
+
 int cfd_set_wait_limit(cfd_handle* h, uint64_t limit_ns) {
   if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
   h->wait_ns = limit_ns == UINT64_MAX ? kTimeoutNs : static_cast<unsigned long long>(limit_ns);
@@ -1137,6 +1197,16 @@ int cfd_set_concurrent_diffusion(cfd_handle* h, int on) {
     if (rc) return rc;
   }
   h->conc_diffusion = on != 0;
+  return CFD_OK;
+}
+
+int cfd_set_fpcg_form(cfd_handle* h, int form) {
+  if (!h) return set_err(nullptr, CFD_ERR_INVALID_ARG, "handle is NULL");
+  if (form != CFD_FPCG_GRAPH && form != CFD_FPCG_HOST) return set_err(h, CFD_ERR_INVALID_ARG, "unknown FPCG form %d", form);
+  if (h->prm.solver != CFD_SOLVER_FPCG) return set_err(h, CFD_ERR_INVALID_ARG, "the handle's solver is not FPCG");
+  if (form == CFD_FPCG_GRAPH && h->prm.nx % 4 != 0)
+    return set_err(h, CFD_ERR_INVALID_ARG, "the FPCG graph form needs nx %% 4 == 0");
+  h->fpcg_form = form;
   return CFD_OK;
 }
 
@@ -1370,6 +1440,9 @@ int cfd_batch_create(int n, const cfd_params* per_cavity, void* dev_ws, size_t b
     return batch_err(nullptr, CFD_ERR_INVALID_ARG, "batches do not support the DIC or FPCG solvers");
   for (int i = 1; i < n; ++i)
     if (per_cavity[i].solver != solver) return batch_err(nullptr, CFD_ERR_INVALID_ARG, "all cavities of a batch use one solver");
+  for (int i = 0; i < n; ++i)
+    if (per_cavity[i].learned_guess)
+      return batch_err(nullptr, CFD_ERR_INVALID_ARG, "batches do not support the learned initial guess");
   const BatchLayout L = batch_layout(n, per_cavity);
   cfd_batch* b = new (std::nothrow) cfd_batch();
   if (!b) return batch_err(nullptr, CFD_ERR_INVALID_ARG, "out of host memory");

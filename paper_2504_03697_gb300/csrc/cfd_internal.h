@@ -9,6 +9,8 @@
 
 #include "cfd_common.cuh"
 
+struct cfd_unet;  // the learned preconditioner (include/cfd.h)
+
 namespace cfd {
 
 // Operator kinds of the stencil solves.
@@ -104,6 +106,16 @@ struct IrArgs {
   // r32, p0_32, p1_32 with a (kTmaBoxW x kTmaBoxH x 1) box, z-chunk depth.
   int use_tma;
   int tma_zl;
+  // graph form only (ir_graph.cu): the learned preconditioner.  With net
+  // set, flexible = 1 runs flexible CG with z = M(r32) from the network in
+  // every FP32 iteration (falling back to plain CG after `stagnation`
+  // iterations without halving the residual norm, or on a breakdown), and
+  // guess = 1 starts from x0 = alpha M(b) (alpha the energy line search).
+  cfd_unet* net;
+  int net_mode;     // the network's convolution mode when the graph was built
+  int flexible;
+  int guess;
+  int stagnation;
   CUtensorMap map_r32;
   CUtensorMap map_p0;
   CUtensorMap map_p1;

@@ -33,6 +33,32 @@
 // velocity matrices of the diffusion substep (float4 kernels where the face
 // grid's width is a multiple of 4, scalar-lane kernels otherwise; no mean
 // removal, their matrices being nonsingular).
+//
+// The learned preconditioner (pressure matrix only; the paper's "other
+// preconditioners", Sec. 5) enters the same graph in two ways:
+//
+// * flexible CG (a.flexible): each FP32 iteration applies the U-Net to the
+//   recurrence residual, z = U(s r32) (its forward pass captured once as
+//   the body of a conditional IF node), and takes the Polak-Ribiere step
+//       z~ = z - mean(z),  beta = z~.(r_new - r_old) / (z~.r)_old
+//          = -alpha_old z~.(A p_old) / (z~.r)_old,
+//       p = z~ + beta p_old,  alpha = z~.r / p.A p,
+//   with x32, r32 updated as in CG.  The inner loop body is
+//       f_norm -> IF(network) { U-Net } -> f_beta -> f_dir -> f_upd
+//   and the outer loop refines in FP64 exactly as above (the direction is
+//   kept; beta after a refinement uses the new z and the recurrence form of
+//   r_new - r_old).  A breakdown of the network's step (z~.r = 0 or not
+//   finite) or `stagnation` iterations without the residual norm halving
+//   switch the solve to plain CG (z = r32), restarted along the residual
+//   (after a refinement to the true residual on stagnation), all decided
+//   on the device.  z~.r < 0 is allowed: alpha is then negative and still
+//   the exact line search along p.
+// * learned initial guess (a.guess): before the prologue, x0 = alpha z~
+//   with z = U(s (b - mean b)), z~ = z - mean(z) and alpha = z~.b / z~.A z~,
+//   the x0 along z~ of least energy-norm error; then the solve starts from
+//   x0 (its prologue computes r = b - A x0 in FP64).
+
+#include <cuda_bf16.h>
 
 #include <cstdint>
 #include <cstring>
@@ -41,6 +67,7 @@
 #include "cfd_internal.h"
 #include "ir_graph.h"
 #include "operator_rows.cuh"
+#include "unet.h"
 
 namespace cfd {
 namespace {
@@ -62,9 +89,21 @@ struct GState {
   unsigned pad2;
   long long kernels;  // kernels run by all graph solves of this workspace (never reset)
   DevSolveStats out;  // statistics of the last solve (copied to the caller's slot)
+  // flexible CG with the learned preconditioner
+  int plain;          // 1 once the solve runs as plain CG (network dropped)
+  int since;          // iterations since the residual norm last halved
+  int plain_iters;    // iterations run as plain CG
+  int skip;           // the flexible direction was unusable: no update, refine
+  double best;        // smallest r32.r32 seen (stagnation test)
+  double rr32;        // r32.r32 of the current recurrence residual
+  double zr;          // z~.r32 of the current direction
+  double zmean;       // mean of the current z (removed from it)
+  // learned initial guess
+  double gmean, gscale, galpha, gzmean;
 };
 
-constexpr size_t kStateBytes = 256;
+constexpr size_t kStateBytes = 512;
+constexpr int kPartSlots = 6;  // values one last-block reduction may carry
 static_assert(sizeof(GState) <= kStateBytes, "GState slot");
 
 struct GArgs {
@@ -90,6 +129,13 @@ struct GArgs {
   float c32;
   int w32x, w32y, w32z;  // FP32 work items: (float4 or scalar) columns / 32, rows / 8, planes / kZ32
   int w64x, w64y, w64z;  // FP64 work items: columns / 32, rows / 8, planes / kZ64
+  // learned preconditioner (pressure matrix, float4 kernels)
+  __nv_bfloat16* net_in;  // the network's input plane
+  const float* net_out;   // the network's output
+  const int* net_err;     // set by a timed-out tensor-core wait of the network
+  int net_kernels;        // kernels of one network application
+  int stagnation;         // flexible CG: iterations without halving |r| before plain CG
+  cudaGraphConditionalHandle h_net;
 };
 
 __device__ __forceinline__ int ftid() { return threadIdx.y * blockDim.x + threadIdx.x; }
@@ -172,6 +218,14 @@ __global__ void __launch_bounds__(kGThreads) g_pro_sum(const GArgs a) {
   S->done = 0;
   S->beta = 0.0;
   S->rz = 0.0;
+  S->plain = 0;
+  S->since = 0;
+  S->plain_iters = 0;
+  S->skip = 0;
+  S->best = 0.0;
+  S->rr32 = 0.0;
+  S->zr = 0.0;
+  S->zmean = 0.0;
 }
 
 // FP64 residual r = b - A xv over the tiles (scalar lanes, z-marching).
@@ -348,29 +402,15 @@ __device__ __forceinline__ void march_f32(const GArgs& a, F4 P4, F1 P1, E emit) 
   }
 }
 
-// inner body: p = r32 + beta p_old, stored; p.Ap as the sum over the grid's
-// edges of (p_i - p_j)^2 (the Neumann matrix has n_c on the diagonal and -1
-// per in-box neighbour, so p.Ap = sum over neighbour pairs of the squared
-// difference), which needs p only at the +x, +y and +z neighbours; alpha =
-// rz / p.Ap.  One warp covers 128 x cells of one row, +x by warp shuffles.
-__global__ void __launch_bounds__(kGThreads, 4) g_dir(const GArgs a) {
-  GState* S = a.S;
-  count_kernel(S);
-  const bool first = S->first != 0;
-  const float beta = float(S->beta);
-  const int cur = S->cur;
-  float* pnew = cur ? a.p1 : a.p0;
-  const float* pold = cur ? a.p0 : a.p1;
-  const float4* r4 = reinterpret_cast<const float4*>(a.r32);
-  const float4* o4 = reinterpret_cast<const float4*>(pold);
-  float4* p4 = reinterpret_cast<float4*>(pnew);
-  auto P4 = [&](size_t e) {
-    const float4 rv = __ldg(r4 + e);
-    if (first) return rv;
-    const float4 ov = __ldg(o4 + e);
-    return make_float4(fmaf(beta, ov.x, rv.x), fmaf(beta, ov.y, rv.y), fmaf(beta, ov.z, rv.z), fmaf(beta, ov.w, rv.w));
-  };
-  auto P1 = [&](size_t e) { return first ? __ldg(a.r32 + e) : fmaf(beta, __ldg(pold + e), __ldg(a.r32 + e)); };
+// The direction pass of the pressure matrix: p = P4(c4) (a float4 of four
+// x-consecutive cells; P1 one cell) stored at p4; returns this thread's
+// part of p.Ap as the sum over the grid's edges of (p_i - p_j)^2 (the
+// Neumann matrix has n_c on the diagonal and -1 per in-box neighbour, so
+// p.Ap = sum over neighbour pairs of the squared difference), which needs p
+// only at the +x, +y and +z neighbours.  One warp covers 128 x cells of one
+// row, +x by warp shuffles.
+template <typename F4, typename F1>
+__device__ __forceinline__ double edge_pass(const GArgs& a, F4 P4, F1 P1, float4* p4) {
   auto sq = [](float d) { return d * d; };
   const int my = a.my, mz = a.mz, nx4 = a.mx >> 2;
   const size_t sy4 = size_t(nx4), sz4 = size_t(nx4) * my;
@@ -408,16 +448,41 @@ __global__ void __launch_bounds__(kGThreads, 4) g_dir(const GArgs a) {
       c4 += sz4;
     }
   }
-  double v[1] = {acc}, o[1];
-  if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
-  const double pq = o[0];
+  return acc;
+}
+
+// alpha = rz / p.Ap, or a breakdown (the last block's thread 0)
+__device__ __forceinline__ void set_alpha(GState* S, double num, double pq) {
   if (!(pq > 0.0) || !isfinite(pq)) {
     S->breakdown = 1;
     S->status = kErrBreakdown;
     S->done = 1;
   } else {
-    S->alpha = S->rz / pq;
+    S->alpha = num / pq;
   }
+}
+
+// inner body: p = r32 + beta p_old, stored; p.Ap by edge_pass; alpha = rz / p.Ap
+__global__ void __launch_bounds__(kGThreads, 4) g_dir(const GArgs a) {
+  GState* S = a.S;
+  count_kernel(S);
+  const bool first = S->first != 0;
+  const float beta = float(S->beta);
+  const int cur = S->cur;
+  float* pnew = cur ? a.p1 : a.p0;
+  const float* pold = cur ? a.p0 : a.p1;
+  const float4* r4 = reinterpret_cast<const float4*>(a.r32);
+  const float4* o4 = reinterpret_cast<const float4*>(pold);
+  auto P4 = [&](size_t e) {
+    const float4 rv = __ldg(r4 + e);
+    if (first) return rv;
+    const float4 ov = __ldg(o4 + e);
+    return make_float4(fmaf(beta, ov.x, rv.x), fmaf(beta, ov.y, rv.y), fmaf(beta, ov.z, rv.z), fmaf(beta, ov.w, rv.w));
+  };
+  auto P1 = [&](size_t e) { return first ? __ldg(a.r32 + e) : fmaf(beta, __ldg(pold + e), __ldg(a.r32 + e)); };
+  double v[1] = {edge_pass(a, P4, P1, reinterpret_cast<float4*>(pnew))}, o[1];
+  if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
+  set_alpha(S, S->rz, o[0]);
 }
 
 // inner body for the velocity matrices on float4 lanes (face grids whose
@@ -458,18 +523,11 @@ __global__ void __launch_bounds__(kGThreads, 4) g_dir_v(const GArgs a) {
   }
 }
 
-// inner body: q = A p again from the stored p, x32 += alpha p, r32 -= alpha q,
-// |r32|^2; the loop control
+// The update pass over the float4 lanes: q = A p again from the stored p
+// (pnew), x32 += alpha p, r32 -= alpha q; returns this thread's part of
+// |r32|^2.
 template <bool VEL>
-__global__ void __launch_bounds__(kGThreads, 4) g_upd(const GArgs a) {
-  GState* S = a.S;
-  count_kernel(S);
-  if (S->breakdown) {
-    if (blockIdx.x == 0 && ftid() == 0) cudaGraphSetConditional(a.h_in, 0u);
-    return;
-  }
-  const float alpha = float(S->alpha);
-  const float* pnew = S->cur ? a.p1 : a.p0;
+__device__ __forceinline__ double upd_pass(const GArgs& a, float alpha, const float* pnew) {
   const float4* p4 = reinterpret_cast<const float4*>(pnew);
   float4* d4 = reinterpret_cast<float4*>(a.d32);
   float4* r4 = reinterpret_cast<float4*>(a.r32);
@@ -490,7 +548,20 @@ __global__ void __launch_bounds__(kGThreads, 4) g_upd(const GArgs a) {
     r4[c4] = rv;
     acc += double(fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, fmaf(rv.z, rv.z, rv.w * rv.w))));
   });
-  double v[1] = {acc}, o[1];
+  return acc;
+}
+
+// inner body: the update pass, then the loop control
+template <bool VEL>
+__global__ void __launch_bounds__(kGThreads, 4) g_upd(const GArgs a) {
+  GState* S = a.S;
+  count_kernel(S);
+  if (S->breakdown) {
+    if (blockIdx.x == 0 && ftid() == 0) cudaGraphSetConditional(a.h_in, 0u);
+    return;
+  }
+  const float* pnew = S->cur ? a.p1 : a.p0;
+  double v[1] = {upd_pass<VEL>(a, float(S->alpha), pnew)}, o[1];
   if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
   const double rz_new = o[0];
   S->first = 0;
@@ -622,6 +693,289 @@ __global__ void __launch_bounds__(kGThreads, 4) g_upd_s(const GArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Flexible CG with the learned preconditioner (pressure matrix, float4
+// lanes).  See the file header for the recurrence.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// outer body, first node: as g_prep (leave, or load r32 = r - mean(r) from
+// the FP64 true residual, folding a pending x32 into x); records r32.r32 and
+// the residual of this refinement; the stagnation reference starts at the
+// first pass.
+__global__ void __launch_bounds__(kGThreads) f_prep(const GArgs a) {
+  GState* S = a.S;
+  count_kernel(S);
+  const bool ok = S->rr <= S->tol2;
+  const bool leave = ok || S->refinements > a.max_outer || S->iters >= a.max_iters;
+  const bool fold = S->pending != 0;
+  const double rmean = S->rsum / double(a.n);
+  float f = 0.f;
+  for (size_t e = vtid(); e < a.n; e += vstride()) {
+    if (fold) a.x[e] += double(a.d32[e]);
+    if (!leave) {
+      const float v = float(a.r[e] - rmean);
+      a.r32[e] = v;
+      f = fmaf(v, v, f);
+    }
+    if (fold || !leave) a.d32[e] = 0.f;
+  }
+  double v[1] = {double(f)}, o[1];
+  if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
+  S->pending = 0;
+  if (leave) {
+    if (ok) S->status = kOk;
+    S->done = 1;
+    cudaGraphSetConditional(a.h_in, 0u);
+    return;
+  }
+  S->rr32 = o[0];
+  S->rz_ref = S->rr;
+  if (S->iters == 0) S->best = o[0];
+  cudaGraphSetConditional(a.h_in, 1u);
+}
+
+// inner body, first node: the network's input xin = BF16(s r32), s =
+// sqrt(V / r32.r32) (unit RMS; the network is linear, so the scale of z
+// does not matter to flexible CG), and the IF condition of the network
+// node: off once the solve runs as plain CG.
+__global__ void __launch_bounds__(kGThreads) f_norm(const GArgs a) {
+  GState* S = a.S;
+  count_kernel(S);
+  const bool net = S->plain == 0;
+  if (blockIdx.x == 0 && ftid() == 0) {
+    cudaGraphSetConditional(a.h_net, net ? 1u : 0u);
+    if (net) S->kernels += a.net_kernels;
+  }
+  if (!net) return;
+  const float sc = S->rr32 > 0.0 ? float(sqrt(double(a.n) / S->rr32)) : 0.f;
+  const float4* r4 = reinterpret_cast<const float4*>(a.r32);
+  uint2* x2 = reinterpret_cast<uint2*>(a.net_in);
+  for (size_t e = vtid(); e < a.n / 4; e += vstride()) {
+    const float4 rv = __ldg(r4 + e);
+    x2[e] = make_uint2(bf16x2_bits(rv.x * sc, rv.y * sc), bf16x2_bits(rv.z * sc, rv.w * sc));
+  }
+}
+
+// inner body, after the network: with z the network's output (r32 once the
+// solve runs as plain CG) and q_old = A p_old formed again from the stored
+// previous direction: z.r32, z.q_old, sum z, sum r32, sum q_old, r32.r32.
+// The last block removes the mean of z and forms z~.r32 and the
+// Polak-Ribiere beta = -alpha_old z~.q_old / (z~.r)_old; a breakdown of the
+// network's step (z~.r32 = 0 or not finite) switches to plain CG along the
+// residual.
+__global__ void __launch_bounds__(kGThreads, 4) f_beta(const GArgs a) {
+  GState* S = a.S;
+  count_kernel(S);
+  const bool plain = S->plain != 0, first = S->first != 0;
+  const float4* z4 = reinterpret_cast<const float4*>(plain ? a.r32 : a.net_out);
+  const float4* r4 = reinterpret_cast<const float4*>(a.r32);
+  const float* pold = S->cur ? a.p0 : a.p1;  // the direction of the last update
+  double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  auto add = [&](const float4& zv, const float4& rv, const float4& qv) {
+    acc[0] += double(fmaf(zv.x, rv.x, fmaf(zv.y, rv.y, fmaf(zv.z, rv.z, zv.w * rv.w))));
+    acc[1] += double(fmaf(zv.x, qv.x, fmaf(zv.y, qv.y, fmaf(zv.z, qv.z, zv.w * qv.w))));
+    acc[2] += double((zv.x + zv.y) + (zv.z + zv.w));
+    acc[3] += double((rv.x + rv.y) + (rv.z + rv.w));
+    acc[4] += double((qv.x + qv.y) + (qv.z + qv.w));
+    acc[5] += double(fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, fmaf(rv.z, rv.z, rv.w * rv.w))));
+  };
+  if (!first) {
+    const float4* o4 = reinterpret_cast<const float4*>(pold);
+    auto P4 = [&](size_t e) { return __ldg(o4 + e); };
+    auto P1 = [&](size_t e) { return __ldg(pold + e); };
+    march_f32<false>(a, P4, P1, [&](size_t c4, const float4&, const float4& qv) { add(__ldg(z4 + c4), __ldg(r4 + c4), qv); });
+  } else {
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (size_t e = vtid(); e < a.n / 4; e += vstride()) add(__ldg(z4 + e), __ldg(r4 + e), zero);
+  }
+  double o[6];
+  if (!reduce_last<6>(acc, a.part, &S->counter, o) || ftid() != 0) return;
+  double m = o[2] / double(a.n);
+  double rz = o[0] - m * o[3];
+  double zq = o[1] - m * o[4];
+  if (!plain && !(rz != 0.0 && isfinite(rz) && isfinite(zq))) {
+    S->plain = 1;  // the network's step is unusable: plain CG along r32
+    S->first = 1;
+    m = o[3] / double(a.n);
+    rz = o[5] - m * o[3];
+    zq = 0.0;
+  }
+  if (!(rz != 0.0) || !isfinite(rz)) {
+    S->breakdown = 1;
+    S->status = kErrBreakdown;
+    S->done = 1;
+    return;
+  }
+  S->zmean = m;
+  S->beta = S->first ? 0.0 : -S->alpha * zq / S->zr;
+  S->zr = rz;
+}
+
+// inner body: p = (z - mean z) + beta p_old, stored; p.Ap by edge_pass;
+// alpha = z~.r / p.Ap
+__global__ void __launch_bounds__(kGThreads, 4) f_dir(const GArgs a) {
+  GState* S = a.S;
+  count_kernel(S);
+  if (S->breakdown) return;
+  const bool first = S->first != 0;
+  const float beta = float(S->beta), m = float(S->zmean);
+  const float* zsrc = S->plain ? a.r32 : a.net_out;
+  const int cur = S->cur;
+  float* pnew = cur ? a.p1 : a.p0;
+  const float* pold = cur ? a.p0 : a.p1;
+  const float4* z4 = reinterpret_cast<const float4*>(zsrc);
+  const float4* o4 = reinterpret_cast<const float4*>(pold);
+  auto P4 = [&](size_t e) {
+    const float4 zv = __ldg(z4 + e);
+    const float4 zc = make_float4(zv.x - m, zv.y - m, zv.z - m, zv.w - m);
+    if (first) return zc;
+    const float4 ov = __ldg(o4 + e);
+    return make_float4(fmaf(beta, ov.x, zc.x), fmaf(beta, ov.y, zc.y), fmaf(beta, ov.z, zc.z), fmaf(beta, ov.w, zc.w));
+  };
+  auto P1 = [&](size_t e) {
+    const float zc = __ldg(zsrc + e) - m;
+    return first ? zc : fmaf(beta, __ldg(pold + e), zc);
+  };
+  double v[1] = {edge_pass(a, P4, P1, reinterpret_cast<float4*>(pnew))}, o[1];
+  if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
+  const double pq = o[0];
+  if (!S->plain && (!(pq > 0.0) || !isfinite(pq))) {
+    S->plain = 1;  // no usable flexible direction: plain CG from the true residual
+    S->first = 1;
+    S->skip = 1;
+    return;
+  }
+  set_alpha(S, S->zr, pq);
+}
+
+// inner body: the update pass, then the loop control of flexible CG:
+// refine in FP64 when |r32|^2 fell by delta^2 (or below the tolerance),
+// switch to plain CG (after a refinement to the true residual) once the
+// residual norm has not halved for `stagnation` iterations, stop at the cap
+__global__ void __launch_bounds__(kGThreads, 4) f_upd(const GArgs a) {
+  GState* S = a.S;
+  count_kernel(S);
+  if (S->breakdown || S->skip) {
+    // every block reads the flags before the first block changes them: the
+    // last block to pass clears skip (arrival order by the counter)
+    __syncthreads();
+    if (ftid() == 0) {
+      const bool last = atomicInc(&S->counter, gridDim.x - 1) == gridDim.x - 1;
+      if (last) {
+        if (S->skip) {
+          S->skip = 0;
+          S->refine = 1;
+        }
+        cudaGraphSetConditional(a.h_in, 0u);
+      }
+    }
+    return;
+  }
+  const float* pnew = S->cur ? a.p1 : a.p0;
+  double v[1] = {upd_pass<false>(a, float(S->alpha), pnew)}, o[1];
+  if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
+  const double rr_new = o[0];
+  S->first = 0;
+  S->cur ^= 1;
+  S->iters += 1;
+  if (S->plain) S->plain_iters += 1;
+  S->pending = 1;
+  S->rr32 = rr_new;
+  bool restart = false;
+  if (rr_new < 0.25 * S->best) {
+    S->best = rr_new;
+    S->since = 0;
+  } else if (!S->plain && ++S->since >= a.stagnation) {
+    S->plain = 1;  // the network stopped helping: plain CG from the true residual
+    S->first = 1;
+    restart = true;
+  }
+  if (restart || rr_new <= S->delta2 * S->rz_ref || rr_new <= S->tol2) {
+    S->refine = 1;
+    cudaGraphSetConditional(a.h_in, 0u);
+    return;
+  }
+  if (S->iters >= a.max_iters) {
+    S->done = 1;
+    cudaGraphSetConditional(a.h_in, 0u);
+  } else {
+    cudaGraphSetConditional(a.h_in, 1u);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Learned initial guess x0 = alpha (z - mean z), z = U(s (b - mean b))
+// ---------------------------------------------------------------------------
+// sum b, sum b^2 -> mean and the input scale s = sqrt(V / |b - mean|^2)
+__global__ void __launch_bounds__(kGThreads) g_gsum(const GArgs a) {
+  GState* S = a.S;
+  count_kernel(S);
+  double sb = 0.0, sq = 0.0;
+  for (size_t e = vtid(); e < a.n; e += vstride()) {
+    const double bv = a.b[e];
+    sb += bv;
+    sq = fma(bv, bv, sq);
+  }
+  double v[2] = {sb, sq}, o[2];
+  if (!reduce_last<2>(v, a.part, &S->counter, o) || ftid() != 0) return;
+  const double V = double(a.n), mean = o[0] / V, var = o[1] - mean * o[0];
+  S->gmean = mean;
+  S->gscale = var > 0.0 && isfinite(var) ? sqrt(V / var) : 0.0;
+  S->kernels += a.net_kernels;
+}
+
+__global__ void __launch_bounds__(kGThreads) g_gnorm(const GArgs a) {
+  GState* S = a.S;
+  count_kernel(S);
+  const double mean = S->gmean, sc = S->gscale;
+  uint2* x2 = reinterpret_cast<uint2*>(a.net_in);
+  for (size_t e = vtid(); e < a.n / 4; e += vstride()) {
+    const size_t c = 4 * e;
+    x2[e] = make_uint2(bf16x2_bits(float((a.b[c] - mean) * sc), float((a.b[c + 1] - mean) * sc)),
+                       bf16x2_bits(float((a.b[c + 2] - mean) * sc), float((a.b[c + 3] - mean) * sc)));
+  }
+}
+
+// sum z, z.(b - mean b), z.A z (FP64; as the sum of squared differences over
+// the grid's edges) -> alpha = z~.b / z~.A z~ (0 when the network returns
+// nothing usable, so that the solve starts from 0)
+__global__ void __launch_bounds__(kGThreads) g_gdots(const GArgs a) {
+  GState* S = a.S;
+  count_kernel(S);
+  const int mx = a.mx, my = a.my, mz = a.mz;
+  const size_t sy = size_t(mx), sz = size_t(mx) * my;
+  const double mean = S->gmean;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (size_t c = vtid(); c < a.n; c += vstride()) {
+    const int i = int(c % sy), j = int((c / sy) % my), k = int(c / sz);
+    const double zc = double(a.net_out[c]);
+    s0 += zc;
+    s1 = fma(zc, a.b[c] - mean, s1);
+    if (i < mx - 1) { const double d = zc - double(a.net_out[c + 1]); s2 = fma(d, d, s2); }
+    if (j < my - 1) { const double d = zc - double(a.net_out[c + sy]); s2 = fma(d, d, s2); }
+    if (k < mz - 1) { const double d = zc - double(a.net_out[c + sz]); s2 = fma(d, d, s2); }
+  }
+  double v[3] = {s0, s1, s2}, o[3];
+  if (!reduce_last<3>(v, a.part, &S->counter, o) || ftid() != 0) return;
+  const double zm = o[0] / double(a.n);
+  const double al = o[1] / o[2];  // sum (b - mean b) = 0, so z~.b = z.(b - mean b)
+  const bool ok = o[2] > 0.0 && isfinite(al) && !(a.net_err && *a.net_err);
+  S->gzmean = ok ? zm : 0.0;
+  S->galpha = ok ? al : 0.0;
+}
+
+__global__ void __launch_bounds__(kGThreads) g_gset(const GArgs a) {
+  GState* S = a.S;
+  count_kernel(S);
+  const double al = S->galpha, zm = S->gzmean;
+  for (size_t e = vtid(); e < a.n; e += vstride()) a.x[e] = al * (double(a.net_out[e]) - zm);
+}
+
+// ---------------------------------------------------------------------------
 // epilogue: x = x + pending x32 (0 when b = 0), sum(x) for the gauge; then
 // the gauge shift and the statistics
 // ---------------------------------------------------------------------------
@@ -654,8 +1008,8 @@ __global__ void __launch_bounds__(kGThreads) g_shift(const GArgs a) {
     DevSolveStats* st = &S->out;
     st->iters = S->iters;
     st->outer_iters = S->refinements;
-    st->restarts = 0;
-    st->status = S->status;
+    st->restarts = S->plain_iters;
+    st->status = a.net_err && *a.net_err ? kErrTimeout : S->status;
     st->b_norm = sqrt(S->bb);
     st->rel_resid = S->bb > 0.0 ? sqrt(S->rr / S->bb) : 0.0;
   }
@@ -679,21 +1033,26 @@ bool same_args(const IrArgs& x, const IrArgs& y) {
          x.r32 == y.r32 && x.d32 == y.d32 && x.p0_32 == y.p0_32 && x.p1_32 == y.p1_32 && x.q32 == y.q32 &&
          x.zero_x0 == y.zero_x0 && x.remove_mean == y.remove_mean && x.gauge == y.gauge &&
          x.gauge_value == y.gauge_value && x.rtol == y.rtol && x.delta == y.delta && x.max_iters == y.max_iters &&
-         x.max_outer == y.max_outer && x.kind == y.kind && x.c == y.c;
+         x.max_outer == y.max_outer && x.kind == y.kind && x.c == y.c && x.net == y.net &&
+         x.net_mode == y.net_mode && x.flexible == y.flexible && x.guess == y.guess && x.stagnation == y.stagnation;
 }
 
 }  // namespace
 
 struct IrGraph {
   cudaGraph_t graph = nullptr;
+  cudaGraph_t net = nullptr;  // the captured network (child of the guess prefix)
   cudaGraphExec_t exec = nullptr;
   IrArgs key{};
   GState* state = nullptr;
 };
 
-size_t ir_graph_state_bytes() { return kStateBytes + size_t(3) * kGMax * sizeof(double); }
+size_t ir_graph_state_bytes() { return kStateBytes + size_t(kPartSlots) * kGMax * sizeof(double); }
 
-bool ir_graph_eligible(const IrArgs& a) { return a.kind != kOpPressure || (a.g.mx % 4 == 0 && a.g.mx >= 4); }
+bool ir_graph_eligible(const IrArgs& a) {
+  if (a.net && (a.flexible || a.guess)) return a.kind == kOpPressure && a.g.mx % 4 == 0 && a.g.mx >= 4;
+  return a.kind != kOpPressure || (a.g.mx % 4 == 0 && a.g.mx >= 4);
+}
 
 namespace {
 bool use_vec_kernels(const IrArgs& a) { return a.g.mx % 4 == 0; }
@@ -714,19 +1073,66 @@ cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t* node, const cudaGraphNode
   return cudaGraphAddKernelNode(node, g, dep, dep ? 1 : 0, &kp);
 }
 
-cudaError_t add_while(cudaGraph_t g, cudaGraphNode_t* node, const cudaGraphNode_t* dep,
-                      cudaGraphConditionalHandle h, cudaGraph_t* body) {
+cudaError_t add_cond(cudaGraph_t g, cudaGraphNode_t* node, const cudaGraphNode_t* dep, cudaGraphConditionalHandle h,
+                     cudaGraphConditionalNodeType type, cudaGraph_t* body) {
   cudaGraphNodeParams np{};
   np.type = cudaGraphNodeTypeConditional;
   np.conditional.handle = h;
-  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.type = type;
   np.conditional.size = 1;
   cudaError_t e = cudaGraphAddNode(node, g, dep, nullptr, dep ? 1 : 0, &np);
   if (e == cudaSuccess) *body = np.conditional.phGraph_out[0];
   return e;
 }
 
+cudaError_t add_while(cudaGraph_t g, cudaGraphNode_t* node, const cudaGraphNode_t* dep,
+                      cudaGraphConditionalHandle h, cudaGraph_t* body) {
+  return add_cond(g, node, dep, h, cudaGraphCondTypeWhile, body);
+}
+
+// Capture the U-Net's forward pass (kernel launches only) into graph g.
+cudaError_t capture_net(cfd_unet* net, cudaGraph_t g, int* kernels) {
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  int rc = CFD_OK;
+  if (e == cudaSuccess) {
+    rc = unet_forward_on(net, cs, kernels);
+    cudaGraph_t out = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &out);
+    if (e2 != cudaSuccess) e = e2;
+  }
+  cudaStreamDestroy(cs);
+  if (e == cudaSuccess && rc != CFD_OK) e = cudaErrorInvalidValue;
+  return e;
+}
+
+GArgs make_args(const IrArgs& ia, void* state_buf);
+cudaError_t build_graph(IrGraph* G, const IrArgs& ia, GArgs a, bool vec, size_t items32, size_t items64,
+                        size_t vec_work, dim3 tile, dim3 flat, bool flexible, bool guess);
+
 cudaError_t build(IrGraph* G, const IrArgs& ia, void* state_buf) {
+  GArgs a = make_args(ia, state_buf);
+  const bool vec = use_vec_kernels(ia);
+  const size_t items32 = size_t(a.w32x) * a.w32y * a.w32z;
+  const size_t items64 = size_t(a.w64x) * a.w64y * a.w64z;
+  const size_t vec_work = (a.n / 4 + kGThreads - 1) / kGThreads;
+  const dim3 tile(32, 8), flat(kGThreads);
+  const bool flexible = ia.net && ia.flexible, guess = ia.net && ia.guess;
+  if (flexible || guess) {
+    UNetView nv{};
+    if (!vec || a.kind != kOpPressure || !unet_view(ia.net, &nv) || nv.nx != a.mx || nv.ny != a.my || nv.nz != a.mz)
+      return cudaErrorInvalidValue;
+    a.net_in = nv.xin;
+    a.net_out = nv.z;
+    a.net_err = nv.err;
+    a.stagnation = ia.stagnation > 0 ? ia.stagnation : 50;
+  }
+  return build_graph(G, ia, a, vec, items32, items64, vec_work, tile, flat, flexible, guess);
+}
+
+GArgs make_args(const IrArgs& ia, void* state_buf) {
   GArgs a{};
   a.mx = ia.g.mx;
   a.my = ia.g.my;
@@ -760,15 +1166,23 @@ cudaError_t build(IrGraph* G, const IrArgs& ia, void* state_buf) {
   a.w64x = (a.mx + 31) / 32;
   a.w64y = a.w32y;
   a.w64z = (a.mz + kZ64 - 1) / kZ64;
-  const size_t items32 = size_t(a.w32x) * a.w32y * a.w32z;
-  const size_t items64 = size_t(a.w64x) * a.w64y * a.w64z;
-  const size_t vec_work = (a.n / 4 + kGThreads - 1) / kGThreads;
-  const dim3 tile(32, 8), flat(kGThreads);
+  return a;
+}
 
+cudaError_t build_graph(IrGraph* G, const IrArgs& ia, GArgs a, bool vec, size_t items32, size_t items64,
+                        size_t vec_work, dim3 tile, dim3 flat, bool flexible, bool guess) {
   cudaGraph_t top = nullptr;
   cudaError_t e = cudaGraphCreate(&top, 0);
   if (e != cudaSuccess) return e;
   G->graph = top;
+  // the network's forward pass on its own (the kernel count goes into the
+  // arguments of the nodes that account for it)
+  cudaGraph_t netg = nullptr;
+  if (flexible || guess) {
+    if ((e = cudaGraphCreate(&netg, 0)) != cudaSuccess) return e;
+    G->net = netg;
+    if ((e = capture_net(ia.net, netg, &a.net_kernels)) != cudaSuccess) return e;
+  }
   if ((e = cudaGraphConditionalHandleCreate(&a.h_out, top, 0u, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
 
   cudaGraphNode_t n0, n1, n2, n3, n4, n5, n6;
@@ -779,7 +1193,21 @@ cudaError_t build(IrGraph* G, const IrArgs& ia, void* state_buf) {
   mp.width = 1;
   mp.height = 1;
   if ((e = cudaGraphAddMemsetNode(&n0, top, nullptr, 0, &mp)) != cudaSuccess) return e;
-  if ((e = add_kernel(top, &n1, &n0, (void*)g_pro_sum, wave_blocks(g_pro_sum, vec_work), flat, &a)) != cudaSuccess)
+  cudaGraphNode_t pre = n0;
+  if (guess) {  // x0 = alpha (z - mean z), z = U(s (b - mean b))
+    cudaGraphNode_t g1, g2, g3, g4, g5;
+    if ((e = add_kernel(top, &g1, &pre, (void*)g_gsum, wave_blocks(g_gsum, vec_work), flat, &a)) != cudaSuccess)
+      return e;
+    if ((e = add_kernel(top, &g2, &g1, (void*)g_gnorm, wave_blocks(g_gnorm, vec_work), flat, &a)) != cudaSuccess)
+      return e;
+    if ((e = cudaGraphAddChildGraphNode(&g3, top, &g2, 1, netg)) != cudaSuccess) return e;
+    if ((e = add_kernel(top, &g4, &g3, (void*)g_gdots, wave_blocks(g_gdots, vec_work * 4), flat, &a)) != cudaSuccess)
+      return e;
+    if ((e = add_kernel(top, &g5, &g4, (void*)g_gset, wave_blocks(g_gset, vec_work * 4), flat, &a)) != cudaSuccess)
+      return e;
+    pre = g5;
+  }
+  if ((e = add_kernel(top, &n1, &pre, (void*)g_pro_sum, wave_blocks(g_pro_sum, vec_work), flat, &a)) != cudaSuccess)
     return e;
   if ((e = add_kernel(top, &n2, &n1, (void*)g_resid64<0>, wave_blocks(g_resid64<0>, items64), tile, &a)) !=
       cudaSuccess)
@@ -788,10 +1216,27 @@ cudaError_t build(IrGraph* G, const IrArgs& ia, void* state_buf) {
   if ((e = add_while(top, &n3, &n2, a.h_out, &outer)) != cudaSuccess) return e;
   if ((e = cudaGraphConditionalHandleCreate(&a.h_in, outer, 0u, 0u)) != cudaSuccess) return e;
   cudaGraphNode_t b1, b2, b3, i1, i2;
-  if ((e = add_kernel(outer, &b1, nullptr, (void*)g_prep, wave_blocks(g_prep, vec_work), flat, &a)) != cudaSuccess)
+  void* prep = flexible ? (void*)f_prep : (void*)g_prep;
+  if ((e = add_kernel(outer, &b1, nullptr, prep, flexible ? wave_blocks(f_prep, vec_work) : wave_blocks(g_prep, vec_work),
+                      flat, &a)) != cudaSuccess)
     return e;
   if ((e = add_while(outer, &b2, &b1, a.h_in, &inner)) != cudaSuccess) return e;
-  if (vec && a.kind == kOpPressure) {
+  if (flexible) {
+    // f_norm -> IF(network) { U-Net } -> f_beta -> f_dir -> f_upd
+    if ((e = cudaGraphConditionalHandleCreate(&a.h_net, inner, 0u, 0u)) != cudaSuccess) return e;
+    cudaGraphNode_t f1, f2, f3, f4, f5;
+    cudaGraph_t netbody = nullptr;
+    if ((e = add_kernel(inner, &f1, nullptr, (void*)f_norm, wave_blocks(f_norm, vec_work), flat, &a)) != cudaSuccess)
+      return e;
+    if ((e = add_cond(inner, &f2, &f1, a.h_net, cudaGraphCondTypeIf, &netbody)) != cudaSuccess) return e;
+    if ((e = capture_net(ia.net, netbody, nullptr)) != cudaSuccess) return e;
+    if ((e = add_kernel(inner, &f3, &f2, (void*)f_beta, wave_blocks(f_beta, items32), tile, &a)) != cudaSuccess)
+      return e;
+    if ((e = add_kernel(inner, &f4, &f3, (void*)f_dir, wave_blocks(f_dir, items32), tile, &a)) != cudaSuccess)
+      return e;
+    if ((e = add_kernel(inner, &f5, &f4, (void*)f_upd, wave_blocks(f_upd, items32), tile, &a)) != cudaSuccess)
+      return e;
+  } else if (vec && a.kind == kOpPressure) {
     if ((e = add_kernel(inner, &i1, nullptr, (void*)g_dir, wave_blocks(g_dir, items32), tile, &a)) != cudaSuccess)
       return e;
     if ((e = add_kernel(inner, &i2, &i1, (void*)g_upd<false>, wave_blocks(g_upd<false>, items32), tile, &a)) !=
@@ -825,8 +1270,10 @@ cudaError_t build(IrGraph* G, const IrArgs& ia, void* state_buf) {
 void release(IrGraph* G) {
   if (G->exec) cudaGraphExecDestroy(G->exec);
   if (G->graph) cudaGraphDestroy(G->graph);
+  if (G->net) cudaGraphDestroy(G->net);
   G->exec = nullptr;
   G->graph = nullptr;
+  G->net = nullptr;
 }
 
 }  // namespace
@@ -859,6 +1306,29 @@ cudaError_t launch_ir_graph(const IrArgs& a, void* state_buf, IrGraph** cache, c
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(a.stats, &G->state->out, sizeof(DevSolveStats), cudaMemcpyDeviceToDevice, s);
   return e;
+}
+
+cudaError_t launch_learned_guess(const IrArgs& ia, void* state_buf, cudaStream_t s, int64_t* launches) {
+  GArgs a = make_args(ia, state_buf);
+  UNetView nv{};
+  if (!ia.net || a.kind != kOpPressure || a.mx % 4 != 0 || !unet_view(ia.net, &nv) || nv.nx != a.mx ||
+      nv.ny != a.my || nv.nz != a.mz)
+    return cudaErrorInvalidValue;
+  a.net_in = nv.xin;
+  a.net_out = nv.z;
+  a.net_err = nv.err;
+  const size_t vec_work = (a.n / 4 + kGThreads - 1) / kGThreads;
+  cudaError_t e = cudaMemsetAsync(&a.S->counter, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  g_gsum<<<wave_blocks(g_gsum, vec_work), kGThreads, 0, s>>>(a);
+  g_gnorm<<<wave_blocks(g_gnorm, vec_work), kGThreads, 0, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  int nk = 0;
+  if (unet_forward_on(ia.net, s, &nk) != CFD_OK) return cudaErrorLaunchFailure;
+  g_gdots<<<wave_blocks(g_gdots, vec_work * 4), kGThreads, 0, s>>>(a);
+  g_gset<<<wave_blocks(g_gset, vec_work * 4), kGThreads, 0, s>>>(a);
+  if (launches) *launches += nk;  // the four guess kernels count themselves on the device
+  return cudaGetLastError();
 }
 
 cudaError_t ir_graph_kernel_count(const void* state_buf, cudaStream_t s, long long* out) {

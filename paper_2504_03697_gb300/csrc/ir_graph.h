@@ -20,6 +20,10 @@ bool ir_graph_eligible(const IrArgs& a);
 // not used.
 cudaError_t launch_ir_graph(const IrArgs& a, void* state_buf, IrGraph** cache, cudaStream_t s);
 void destroy_ir_graph(IrGraph* g);
+// The learned initial guess alone, enqueued on s: a.x = alpha (z - mean z),
+// z = U(s (a.b - mean)), alpha the energy line search (a.net, the pressure
+// matrix, mx % 4 == 0).  Uses the state buffer's scalars and partial sums.
+cudaError_t launch_learned_guess(const IrArgs& a, void* state_buf, cudaStream_t s, int64_t* launches);
 // Kernels run so far by graph solves on this state buffer (synchronises s).
 cudaError_t ir_graph_kernel_count(const void* state_buf, cudaStream_t s, long long* out);
 

@@ -5,6 +5,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "../../include/cfd.h"
+
 namespace cfd {
 
 // Activation layout ("channel-octet planes"): a tensor of C channels on V
@@ -41,6 +43,22 @@ struct ConvArgs {
   int no_tile;                   // 1: never take the TMA-tiled kernel
   int stages;                    // with w_cm: 1 (default) or 2 shared-memory stages
 };
+
+// Hooks for solvers that run the U-Net inside their own CUDA graphs
+// (ir_graph.cu): its BF16 input plane and FP32 output, its grid, and the
+// forward pass enqueued on a given stream.  The forward pass is kernel
+// launches only (no allocation, no synchronisation), so it can be captured.
+struct UNetView {
+  int nx, ny, nz;
+  __nv_bfloat16* xin;  // network input, BF16 [V]
+  float* z;            // head output, FP32 [V]
+  int* err;            // device flag set by a timed-out tensor-core wait
+  int conv_mode;       // CFD_UNET_CONV_* (changes the captured kernels)
+};
+bool unet_view(const cfd_unet* u, UNetView* v);
+// Forward pass xin -> z on stream s; *kernels (nullable) receives the
+// number of kernels it launched.  Returns CFD_OK or a CFD_ERR_* code.
+int unet_forward_on(cfd_unet* u, cudaStream_t s, int* kernels);
 
 // Launch the convolution: the TMA-tiled kernel for 3x3x3 layers whose
 // sources have 16k channels (see conv3d_tile_eligible), else the gathering

@@ -1158,6 +1158,29 @@ void init_params(std::vector<float>& p, uint64_t seed) {
 
 }  // namespace
 
+bool cfd::unet_view(const cfd_unet* u, UNetView* v) {
+  if (!u || !v) return false;
+  v->nx = u->nx;
+  v->ny = u->ny;
+  v->nz = u->nz;
+  v->xin = u->xin;
+  v->z = u->z;
+  v->err = u->err;
+  v->conv_mode = u->conv_mode;
+  return true;
+}
+
+int cfd::unet_forward_on(cfd_unet* u, cudaStream_t s, int* kernels) {
+  if (!u) return uerr(CFD_ERR_INVALID_ARG, "unet: NULL handle");
+  const cudaStream_t keep = u->stream;
+  const int64_t l0 = u->launches;
+  u->stream = s;
+  const int rc = forward(u);
+  u->stream = keep;
+  if (kernels) *kernels = int(u->launches - l0);
+  return rc;
+}
+
 extern "C" {
 
 int cfd_unet_workspace_bytes(int nx, int ny, int nz, size_t* bytes) {

@@ -418,22 +418,27 @@ def test_cavity_steps_with_the_learned_preconditioner(cfd):
     n, steps = 16, 3
     net = cfd.UNet(n, n, n, seed=2)
     net.set_params(passthrough_params(1.0))
-    runs = []
-    for solver in ("fpcg", "cg"):
+    runs = {}
+    for solver, form in (("fpcg", "host"), ("fpcg", "graph"), ("cg", None)):
         cav = cfd.Cavity(cfd.make_params(n, n, n, dt=0.01, nu=0.01, lid_u=1.0, solver=solver))
         if solver == "fpcg":
             cav.attach_preconditioner(net)
+            cav.set_fpcg_form(form)
         for name, f in zip("uvw", cavity_perturbation(n, n, n, seed=4, amp=1e-3)):
             cav.set_field(name, f)
         rc, stats = cav.step(steps)
         assert rc == 0 and all(s["status"] == 0 and s["rel_resid"] <= 1e-8 for s in stats), stats
-        runs.append(({f: cav.read_field(f).numpy() for f in "uvwp"}, stats))
-    (a, sa), (b, sb) = runs
-    assert all(s["outer_iters"] == 0 for s in sa)  # the network's steps were used, no fallback
-    assert sum(s["iters"] for s in sa) < sum(s["iters"] for s in sb)  # the pass-through network helps
-    for f in "uvwp":
-        scale = max(1.0, float(np.abs(b[f]).max()))
-        assert float(np.abs(a[f] - b[f]).max()) <= 1e-5 * scale, f
+        runs[form] = ({f: cav.read_field(f).numpy() for f in "uvwp"}, stats)
+    b, sb = runs[None]
+    for form in ("host", "graph"):
+        a, sa = runs[form]
+        # the network's steps were used, no fallback (host form: outer_iters
+        # counts plain iterations; graph form: restarts does)
+        assert all((s["outer_iters"] if form == "host" else s["restarts"]) == 0 for s in sa)
+        assert sum(s["iters"] for s in sa) < sum(s["iters"] for s in sb)  # the pass-through network helps
+        for f in "uvwp":
+            scale = max(1.0, float(np.abs(b[f]).max()))
+            assert float(np.abs(a[f] - b[f]).max()) <= 1e-5 * scale, (form, f)
 
 
 def test_fpcg_cavity_without_a_network_is_an_error(cfd):

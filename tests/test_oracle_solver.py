@@ -268,3 +268,124 @@ def test_ir_cg_zero_rhs_and_nonsingular_fp32():
     assert np.linalg.norm(b - H @ x) <= 1.0001e-8 * np.linalg.norm(b)
     ref = np.linalg.solve(H.toarray(), b)
     assert np.linalg.norm(x - ref) <= 2e-8 * np.linalg.norm(b)  # ||H^-1|| <= 1
+
+
+# ----------------------------------------------------------------------------
+# ir_fpcg: flexible CG with a low-precision recurrence and FP64 reliable
+# updates (the learned-preconditioner solve in mixed precision)
+# ----------------------------------------------------------------------------
+def _block_mean(x, shape, k):
+    """Mean over k^3 blocks, repeated back onto the grid (x flat, shape x-fastest (nx, ny, nz))."""
+    nx, ny, nz = shape
+    g = x.reshape(nz, ny, nx)
+    m = g.reshape(nz // k, k, ny // k, k, nx // k, k).mean(axis=(1, 3, 5))
+    return np.repeat(np.repeat(np.repeat(m, k, 0), k, 1), k, 2).ravel()
+
+
+def _smoother(shape, w=2.0):
+    """M(r) = r + w B2 r: symmetric positive definite, maps zero-mean vectors
+    to zero-mean vectors (block means preserve the total)."""
+    return lambda r: r + w * _block_mean(r, shape, 2)
+
+
+def _lam_min(shape):
+    return min(4 * np.sin(np.pi / (2 * n)) ** 2 for n in shape if n > 1)
+
+
+@pytest.mark.parametrize("precond", ["identity", "smoother"])
+def test_ir_fpcg_in_fp64_is_flexible_cg(precond):
+    """FP64 'inner' vectors and delta = 0 (refine only at convergence): the
+    recurrence is fpcg's (the Polak-Ribiere beta written with the recurrence
+    difference -alpha q): the same iteration count (+-1 at the threshold) and
+    solutions within the rtol bound; with the identity also pcg's count."""
+    from oracle.krylov import fpcg, ir_fpcg
+    shape = (8, 8, 6)
+    A = poisson_csr(*shape)
+    b = uniform_field(shape[::-1], seed=21).ravel()
+    M = (lambda r: r.copy()) if precond == "identity" else _smoother(shape)
+    x, st = ir_fpcg(A, b, M, rtol=1e-10, delta=0.0, inner=np.float64)
+    xf, sf = fpcg(A, b, M, rtol=1e-10)
+    assert st.converged and sf.converged and st.refinements == 1 and st.plain_iters == 0
+    assert abs(st.iters - sf.iters) <= 1
+    bm = b - b.mean()
+    bound = 2e-10 * np.linalg.norm(bm) / _lam_min(shape)
+    assert np.linalg.norm((x - x.mean()) - (xf - xf.mean())) <= bound
+    if precond == "identity":
+        _, sp_ = pcg(A, bm, rtol=1e-10, max_iters=10000)
+        assert abs(st.iters - sp_.iters) <= 1
+    else:
+        _, s0 = fpcg(A, b, lambda r: r.copy(), rtol=1e-10)
+        assert st.iters < s0.iters  # the smoother helps
+
+
+@pytest.mark.parametrize("precond", ["identity", "smoother"])
+def test_ir_fpcg_fp32_reaches_the_fp64_tolerance(precond):
+    from oracle.krylov import ir_fpcg
+    shape = (16, 12, 8)
+    A = poisson_csr(*shape)
+    b = uniform_field(shape[::-1], seed=22).ravel()
+    M = (lambda r: r.copy()) if precond == "identity" else _smoother(shape)
+    x, st = ir_fpcg(A, b, M, rtol=1e-8, delta=0.1)
+    bm = b - b.mean()
+    assert st.converged and st.refinements >= 3 and st.plain_iters == 0
+    assert np.linalg.norm(bm - A @ x) <= 1.0001e-8 * np.linalg.norm(bm)
+    ref = _dense_zero_mean_solve(A, bm)
+    assert np.linalg.norm((x - x.mean()) - ref) <= 2e-8 * np.linalg.norm(bm) / _lam_min(shape)
+
+
+def test_ir_fpcg_scale_of_the_preconditioner_does_not_matter():
+    from oracle.krylov import ir_fpcg
+    shape = (8, 8, 6)
+    A = poisson_csr(*shape)
+    b = uniform_field(shape[::-1], seed=23).ravel()
+    M = _smoother(shape)
+    x1, s1 = ir_fpcg(A, b, M, rtol=1e-10, delta=0.0, inner=np.float64)
+    x2, s2 = ir_fpcg(A, b, lambda r: -3.0 * M(r), rtol=1e-10, delta=0.0, inner=np.float64)
+    assert s1.iters == s2.iters and s2.plain_iters == 0
+    assert np.allclose(x1, x2, rtol=0, atol=1e-9 * np.abs(x1).max())
+
+
+def test_ir_fpcg_falls_back_on_breakdown_and_stagnation():
+    """A zero preconditioner gives z~.r = 0 at once (breakdown): plain CG
+    from the first iteration.  A fixed vector gives beta = -1 on the second
+    iteration, a zero direction (p.q = 0): plain CG from the true residual
+    after one iteration.  A fresh random vector each call keeps p.q > 0 but
+    does not reduce the residual: plain CG after the stagnation window.  All
+    still meet the FP64 tolerance; zero b takes no iteration."""
+    from oracle.krylov import ir_fpcg
+    shape = (12, 10, 8)
+    A = poisson_csr(*shape)
+    b = uniform_field(shape[::-1], seed=24).ravel()
+    bm = b - b.mean()
+    x, st = ir_fpcg(A, b, lambda r: np.zeros_like(r), rtol=1e-8)
+    assert st.converged and st.plain_iters == st.iters > 0
+    fixed = uniform_field(shape[::-1], seed=25).ravel()
+    x, st = ir_fpcg(A, b, lambda r: fixed.copy(), rtol=1e-8)
+    assert st.converged and st.iters - st.plain_iters == 1
+    assert np.linalg.norm(bm - A @ x) <= 1.0001e-8 * np.linalg.norm(bm)
+    rng = np.random.default_rng(26)
+    x, st = ir_fpcg(A, b, lambda r: rng.standard_normal(r.size), rtol=1e-8, stagnation=20)
+    assert st.converged and 0 < st.plain_iters < st.iters and st.iters - st.plain_iters >= 20
+    assert np.linalg.norm(bm - A @ x) <= 1.0001e-8 * np.linalg.norm(bm)
+    x, st = ir_fpcg(A, np.zeros(A.shape[0]), lambda r: r.copy())
+    assert st.converged and st.iters == 0 and not x.any()
+
+
+def test_ir_cg_starting_iterate():
+    """x0 = 0 is the cold start (bitwise); x0 = a solution within the
+    tolerance takes no iteration; x0 = a partial CG iterate needs fewer
+    iterations than the cold start."""
+    from oracle.krylov import ir_cg
+    shape = (12, 10, 8)
+    A = poisson_csr(*shape)
+    b = uniform_field(shape[::-1], seed=27).ravel()
+    x1, s1 = ir_cg(A, b, rtol=1e-8)
+    x2, s2 = ir_cg(A, b, rtol=1e-8, x0=np.zeros(b.size))
+    assert np.array_equal(x1, x2) and s1.iters == s2.iters and s1.refinements == s2.refinements
+    bm = b - b.mean()
+    xs, _ = pcg(A, bm, rtol=1e-12, max_iters=10000)
+    x3, s3 = ir_cg(A, b, rtol=1e-8, x0=xs)
+    assert s3.converged and s3.iters == 0 and np.array_equal(x3, xs)
+    xp, _ = pcg(A, bm, rtol=1e-15, max_iters=20)
+    _, s4 = ir_cg(A, b, rtol=1e-8, x0=xp)
+    assert s4.converged and s4.iters < s1.iters
