@@ -1,14 +1,23 @@
 #!/usr/bin/env python3
-"""Benchmark: cell-steps/s of the lid-driven-cavity fractional step on GB300.
+"""Benchmark: cell-steps/s of the lid-driven-cavity fractional step on GB300,
+and time to rtol 1e-8 per pressure solve: learned preconditioner vs plain CG.
 
-Workload (default): the FP64 cavity of Sec. 3 / 3.1 of arXiv 2504.03697 at
-64^3 cells, lid 1.0, nu 1e-3, dt 1e-2, pressure by unpreconditioned CG to
-rtol 1e-8 (true FP64 residual), velocity initialised to the seeded
-uniform[-1e-3, 1e-3] perturbation (seed 2 + rank).  One bench "step" is one
-time step: applyForces, advection, implicit diffusion (3 CG solves),
-divergence, pressure CG, correction.  Inputs are synthetic and resident in
-HBM when the timed region starts; L2 is flushed (256 MiB write) between
-timed steps, outside the timed events.
+Default workload: the 384^3 cavity (56.6 M cells) of Sec. 3 / 3.1 of arXiv
+2504.03697 with lid 1.0, nu 1e-3, dt 1e-2, the seeded uniform[-1e-3, 1e-3]
+perturbation (seed 5 + rank), every solve to the FP64 true-residual rtol
+1e-8, on the learned + mixed-precision path (``--solver``: the pressure solve
+as FP32 CG with FP64 refinement started from the U-Net's initial guess, the
+diffusion solves in the same mixed precision).  One bench "step" is one time
+step: applyForces, advection, implicit diffusion (3 solves), divergence,
+pressure solve, correction.  Inputs are synthetic and resident in HBM when
+the timed region starts; at this size they are larger than L2 (no flush).
+
+The same line carries: the same cavity with FP64 CG and with plain IR
+(samples of steps); time to rtol per solve of FP64 CG, IR, learned flexible
+CG and IR from the learned guess on held-out 128^3 and 256^3 systems; the
+64^3 FP64 cavity; the 256^3 precision study; the 64-cavity batch study; the
+oracle on the host cores (single thread and all cores, a sampled step
+scaled to the workload).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -33,15 +42,21 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    "cavity64": dict(n=64, nu=1e-3, dt=1e-2, lid_u=1.0, seed=2, amp=1e-3,
-                     desc="lid-driven cavity 64^3 cells, FP64, lid 1.0, nu 1e-3, dt 1e-2, "
-                          "pressure CG to rtol 1e-8, seeded 1e-3 perturbation"),
-    "cavity384": dict(n=384, nu=1e-3, dt=1e-2, lid_u=1.0, seed=5, amp=1e-3,
-                      desc="lid-driven cavity 384^3 cells, FP64, lid 1.0, nu 1e-3, dt 1e-2, "
-                           "pressure solve to rtol 1e-8, seeded 1e-3 perturbation"),
-    "cavity16": dict(n=16, nu=1e-2, dt=1e-2, lid_u=1.0, seed=1, amp=1e-3,
-                     desc="lid-driven cavity 16^3 cells, FP64, lid 1.0, nu 1e-2, dt 1e-2, "
-                          "pressure CG to rtol 1e-8, seeded 1e-3 perturbation"),
+    "cavity384": dict(n=384, nu=1e-3, dt=1e-2, lid_u=1.0, seed=5, amp=1e-3, steps_total=50,
+                      desc="lid-driven cavity 384^3 cells (56.6 M), lid 1.0, nu 1e-3, dt 1e-2, "
+                           "solves to rtol 1e-8 (FP64 true residual), seeded 1e-3 perturbation"),
+    "cavity64": dict(n=64, nu=1e-3, dt=1e-2, lid_u=1.0, seed=2, amp=1e-3, steps_total=100,
+                     desc="lid-driven cavity 64^3 cells, lid 1.0, nu 1e-3, dt 1e-2, "
+                          "solves to rtol 1e-8 (FP64 true residual), seeded 1e-3 perturbation"),
+    "cavity16": dict(n=16, nu=1e-2, dt=1e-2, lid_u=1.0, seed=1, amp=1e-3, steps_total=20,
+                     desc="lid-driven cavity 16^3 cells, lid 1.0, nu 1e-2, dt 1e-2, "
+                          "solves to rtol 1e-8 (FP64 true residual), seeded 1e-3 perturbation"),
+}
+SOLVER_DESC = {
+    "cg": "FP64 CG (plain method)",
+    "ir": "FP32 CG + FP64 refinement (mixed precision)",
+    "fpcg": "flexible CG with the learned U-Net preconditioner, FP32 + FP64 refinement (graph form)",
+    "guess": "learned U-Net initial guess, then FP32 CG + FP64 refinement (mixed precision)",
 }
 
 # Algorithmic work of one pressure-CG iteration per cell (FP64, matrix-free):
@@ -61,27 +76,38 @@ CG1_CAVITY64_DRAM_BYTES = 2342400 + 84992
 CG1_CAVITY64_SHAPE = {"blocks": 128, "tile_depth": 8, "register_path": True}
 IR_BYTES_PER_CELL_ITER = 40
 IR_GRAPH_BYTES_PER_CELL_ITER = 32
+# DRAM bytes per cell and FP32 iteration of the graph-form iteration (g_dir +
+# g_upd), from the ncu capture of a 256^3 solve (whole-solve dram bytes over
+# cells x iterations; profiles/ir_graph_poisson256.md); None if not captured
+IR_GRAPH_DRAM_BYTES_PER_CELL_ITER = None
+# FP64 FMA rate of the GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz from
+# the recipe's unit counts and clocks; bench.py --fp64-peak measures it
+FP64_PEAK_TFLOPS = 1.26
+FP64_PEAK_SOURCE = "FP64 FMA rate from the recipe's unit counts and clocks (152 x 2 x 2 x 2.07 GHz)"
 
 
 def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cavity64")
-    ap.add_argument("--solver", default="cg")
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cavity384")
+    ap.add_argument("--solver", default="guess",
+                    help="cg | ir | fpcg | guess (the cavity's solve path; --poisson/--batch: cg | ir | dic)")
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-studies", action="store_true",
+                    help="only the headline cavity (no comparison, time-to-rtol, 64^3, precision and batch blocks)")
+    ap.add_argument("--sample-n", type=int, default=96, help=argparse.SUPPRESS)
+    ap.add_argument("--sample-iters", type=int, default=30, help=argparse.SUPPRESS)
+    ap.add_argument("--full-iters", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--poisson", type=int, default=0,
                     help="standalone Neumann-Poisson solves on an N^3 grid instead of the cavity "
                          "(one bench step = one solve of a seeded Gaussian right-hand side)")
     ap.add_argument("--max-iters", type=int, default=0, help="CG iteration cap per solve (0: 20 N)")
-    ap.add_argument("--no-precision-study", action="store_true")
     ap.add_argument("--batch", type=int, default=0,
                     help="benchmark N batched uneven cavities (edges from {32,48,64,96}) instead of one cavity")
-    ap.add_argument("--no-batch-study", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the automatic solver shape")
     ap.add_argument("--cg-variant", choices=["single", "two"], default="single",
                     help="FP64 CG form: one grid reduction per iteration (default) or the textbook two")
@@ -202,47 +228,120 @@ def physical_gpu(local):
 
 
 # ---------------------------------------------------------------------------
-# oracle timing (CPU baseline / reference arm): runs in a child process
+# oracle timing (CPU baseline / reference arm): runs in child processes
 # ---------------------------------------------------------------------------
+# FP64 CG iterations per pressure solve of the 384^3 cavity (nu 1e-3, dt
+# 1e-2, the seeded perturbation), measured on the GPU with the same method and
+# stopping rule as the oracle's CG: used to scale the oracle's sampled cost
+# per CG iteration to a whole step when no measurement of this run is at hand
+CG_ITERS_PER_STEP = {384: 1914}
+
+
 def oracle_sample_main(args):
-    """Child process: time the FP64 oracle on the workload for a bounded
-    number of steps; print one JSON object."""
+    """Child process: time the FP64 oracle on a bounded sample of the
+    workload and print one JSON object.
+
+    Workloads of at most 64^3 cells run whole time steps.  Larger ones run
+    one step of the same-parameter cavity at args.sample_n^3 with the
+    pressure CG cut to args.sample_iters iterations (replayed with the
+    oracle's fixed-iteration mode) after its CSR assembly; the sweeps
+    (forces, advection, diffusion, divergence, correction, gauge) and the
+    assembly are scaled to the workload by the cell count, the CG by cells x
+    the workload's CG iterations per solve (args.full_iters)."""
     from oracle import fractional_step as fs
+    from oracle.krylov import pcg
     from oracle.mac import Cavity
+    from oracle.operators import poisson_csr
     from paper_2504_03697_gb300.synthetic import cavity_perturbation
 
     wl = WORKLOADS[args.workload]
     n = wl["n"]
-    cav = Cavity(n, n, n, dt=wl["dt"], nu=wl["nu"], lid_u=wl["lid_u"])
-    st = fs.initial_state(cav, cavity_perturbation(n, n, n, wl["seed"], wl["amp"]))
-    for _ in range(args.warmup):
-        st, _ = fs.step(cav, st)
-    t0 = time.perf_counter()
-    done = 0
-    per_step = []
-    while done < args.steps:
-        a = time.perf_counter()
-        st, _ = fs.step(cav, st)
-        per_step.append(time.perf_counter() - a)
-        done += 1
-        if time.perf_counter() - t0 > args.max_seconds:
-            break
-    el = time.perf_counter() - t0
-    print(json.dumps({"steps": done, "seconds": el, "cells": n ** 3, "per_step_s": per_step}))
+    if n <= 64:
+        cav = Cavity(n, n, n, dt=wl["dt"], nu=wl["nu"], lid_u=wl["lid_u"])
+        st = fs.initial_state(cav, cavity_perturbation(n, n, n, wl["seed"], wl["amp"]))
+        for _ in range(args.warmup):
+            st, _ = fs.step(cav, st)
+        t0 = time.perf_counter()
+        per_step = []
+        while len(per_step) < args.steps:
+            a = time.perf_counter()
+            st, _ = fs.step(cav, st)
+            per_step.append(time.perf_counter() - a)
+            if time.perf_counter() - t0 > args.max_seconds:
+                break
+        el = sum(per_step)
+        print(json.dumps({"steps": len(per_step), "seconds": el, "cells": n ** 3, "per_step_s": per_step,
+                          "value": n ** 3 * len(per_step) / el,
+                          "sample": f"{len(per_step)} whole time steps of the {n}^3 cavity"}))
+        return
+    ns, k = args.sample_n, args.sample_iters
+    cav = Cavity(ns, ns, ns, dt=wl["dt"], nu=wl["nu"], lid_u=wl["lid_u"])
+    st = fs.initial_state(cav, cavity_perturbation(ns, ns, ns, wl["seed"], wl["amp"]))
+    scale = (n / ns) ** 3
+    full = args.full_iters
+    estimates = []
+    for rep in range(args.warmup + args.steps):
+        u, v, w, _ = st
+        t0 = time.perf_counter()
+        u, v, w = fs.apply_forces(cav, u, v, w)
+        u, v, w = fs.advect(cav, u, v, w)
+        (u, v, w), _ = fs.diffuse(cav, (u, v, w))
+        b = fs.pressure_rhs(cav, u, v, w)
+        A = poisson_csr(ns, ns, ns)
+        t1 = time.perf_counter()
+        x, _ = pcg(A, b.ravel(), rtol=cav.rtol, max_iters=k, fixed_iters=k)
+        t2 = time.perf_counter()
+        x = x.reshape(cav.cell_shape)
+        u, v, w = fs.correct(cav, u, v, w, x)
+        st = (u, v, w, fs.gauge(x))
+        t3 = time.perf_counter()
+        sweeps = (t1 - t0) + (t3 - t2)
+        per_iter = (t2 - t1) / k
+        est = scale * (sweeps + per_iter * full)
+        if rep >= args.warmup:
+            estimates.append({"sweeps_s": sweeps, "cg_s_per_iter": per_iter, "est_step_s": est,
+                              "wall_s": t3 - t0})
+    wall = sum(e["wall_s"] for e in estimates)
+    est_total = sum(e["est_step_s"] for e in estimates)
+    print(json.dumps({"steps": len(estimates), "seconds": wall, "est_seconds": est_total, "cells": n ** 3,
+                      "value": n ** 3 * len(estimates) / est_total, "per_step": estimates,
+                      "sample": f"{len(estimates)} time step(s) of the same-parameter {ns}^3 cavity with the "
+                                f"pressure CG cut to {k} iterations (after its CSR assembly); sweeps and "
+                                f"assembly scaled by the cell ratio {scale:.0f}, CG by the cell ratio x "
+                                f"{full} FP64 CG iterations per solve"}))
 
 
-def run_oracle_child(workload, steps, warmup, max_seconds):
+def run_oracle_child(workload, steps, warmup, max_seconds, sample_n=96, sample_iters=30, full_iters=0, threads=1):
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
-        env[k] = "1"
+        env[k] = str(threads)
     for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "LOCAL_WORLD_SIZE", "GROUP_RANK", "ROLE_RANK"):
         env.pop(k, None)
     cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", "--workload", workload,
-           "--steps", str(steps), "--warmup", str(warmup), "--max-seconds", str(max_seconds)]
-    r = subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=ROOT)
-    if r.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+           "--steps", str(steps), "--warmup", str(warmup), "--max-seconds", str(max_seconds),
+           "--sample-n", str(sample_n), "--sample-iters", str(sample_iters), "--full-iters", str(full_iters)]
+    return subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env, cwd=ROOT)
+
+
+def collect_oracle(proc):
+    out, err = proc.communicate()
+    if proc.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + err[-2000:])
+    return json.loads(out.strip().splitlines()[-1])
+
+
+def oracle_baseline(workload, full_iters, max_seconds=60.0):
+    """The oracle on the host cores: one single-thread sample, then one
+    sample per host core at once (independent cavities, weak scaling)."""
+    one = collect_oracle(run_oracle_child(workload, 1, 0, max_seconds, full_iters=full_iters))
+    cores = os.cpu_count() or 1
+    procs = [run_oracle_child(workload, 1, 0, max_seconds, full_iters=full_iters) for _ in range(cores)]
+    many = [collect_oracle(p) for p in procs]
+    return {"value": one["value"], "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+            "sample": one["sample"] + " (FP64 numpy/scipy oracle, one thread)",
+            "all_cores": {"value": sum(m["value"] for m in many), "cores": cores,
+                          "sample": f"{cores} concurrent single-thread oracle processes, each the sample above"},
+            "cpu": cpu_model(), "host_cores": cores}
 
 
 def cpu_model():
@@ -265,14 +364,15 @@ def main_reference(args):
     if rank != 0:
         return 0
     wl = WORKLOADS[args.workload]
-    res = run_oracle_child(args.workload, args.steps, min(args.warmup, 1), args.max_seconds)
-    value = res["cells"] * res["steps"] / res["seconds"]
-    sample = (f"{res['steps']} time steps of the {wl['n']}^3 cavity (of {args.steps} requested; capped at "
-              f"{args.max_seconds:.0f} s), FP64 numpy/scipy oracle, single thread, after "
-              f"{min(args.warmup, 1)} warm-up step")
+    full = CG_ITERS_PER_STEP.get(wl["n"], 0)
+    res = collect_oracle(run_oracle_child(args.workload, args.steps, args.warmup, args.max_seconds, sample_n=64,
+                                          sample_iters=40, full_iters=full))
+    value = res["value"]
+    sample = res["sample"] + f" per timed step, after {args.warmup} warm-up sample(s); FP64 numpy/scipy oracle, " \
+                             f"single thread"
     line = {"metric": "cell-steps/s", "value": value, "unit": "cell-steps/s", "impl": "reference",
-            "n_gpus": args.gpus, "steps": res["steps"], "warmup": min(args.warmup, 1),
-            "ms_per_step": 1e3 * res["seconds"] / max(res["steps"], 1), "higher_is_better": True,
+            "n_gpus": args.gpus, "steps": res["steps"], "warmup": args.warmup,
+            "ms_per_step": 1e3 * wl["n"] ** 3 / value, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl["desc"], "n": wl["n"], "parallelism": "host oracle, rank 0 only"},
             "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
@@ -285,6 +385,105 @@ def main_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def weights_path():
+    return os.path.join(ROOT, "paper_2504_03697_gb300", "weights", "unet_cavity128.f32")
+
+
+def make_cavity(cfd, n, wl, solver, device, params=None, advect_order=1):
+    """A cavity of the workload with one of the solver paths: 'cg' (FP64 CG),
+    'ir' (FP32 CG + FP64 refinement), 'fpcg' (flexible CG with the learned
+    U-Net, mixed precision, graph form), 'guess' (IR from the learned initial
+    guess).  Returns (cavity, network or None)."""
+    kw = dict(dt=wl["dt"], nu=wl["nu"], lid_u=wl["lid_u"], advect_order=advect_order)
+    if solver == "guess":
+        prm = cfd.make_params(n, n, n, solver="ir", learned_guess=True, **kw)
+    else:
+        prm = cfd.make_params(n, n, n, solver=solver, **kw)
+    cav = cfd.Cavity(prm, device=device)
+    net = None
+    if solver in ("fpcg", "guess"):
+        net = cfd.UNet(n, n, n, seed=0, device=device)
+        net.set_params(params)
+        cav.attach_preconditioner(net)
+    return cav, net
+
+
+def init_fields(cav, n, wl, seed_offset=0):
+    from paper_2504_03697_gb300.synthetic import cavity_perturbation
+    for name, f in zip("uvw", cavity_perturbation(n, n, n, wl["seed"] + seed_offset, wl["amp"])):
+        cav.set_field(name, f)
+
+
+def timed_steps(cav, steps, stream, device, flush=None):
+    """Per-step device time (CUDA events on the cavity's stream), L2 flushed
+    before each step when a flush buffer is given."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize(device)
+    for s in range(steps):
+        if flush is not None:
+            flush.zero_()
+        ev[s][0].record(stream)
+        cav.step(1, stats=False)
+        ev[s][1].record(stream)
+    torch.cuda.synchronize(device)
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def cavity_sample(cfd, n, wl, solver, steps, warmup, device, params=None):
+    """Cell-steps/s of the workload's cavity with another solver path, on a
+    sample of steps (warm-up steps first); returns a summary dict."""
+    import torch
+    cav, net = make_cavity(cfd, n, wl, solver, device, params)
+    init_fields(cav, n, wl)
+    if solver in ("cg", "ir"):
+        cav.autotune(iters=30)
+    if warmup:
+        cav.step(warmup, stats=False)
+    cav.phase_times()
+    cav.enable_timing(True)
+    ms = timed_steps(cav, steps, torch.cuda.current_stream(device), device)
+    cav.enable_timing(False)
+    ph = cav.phase_times()
+    rc, st = cav.recent_stats(steps)
+    out = {"solver": solver, "steps_timed": steps, "warmup": warmup, "ms_per_step": sum(ms) / steps,
+           "cell_steps_per_s": n ** 3 * steps / (sum(ms) / 1e3),
+           "pressure_ms_per_step": ph["pcg"][0] / steps, "diffuse_ms_per_step": ph["diffuse"][0] / steps,
+           "pressure_iters": [s["iters"] for s in st], "refinements": [s["outer_iters"] for s in st],
+           "all_converged": rc == cfd.CFD_OK and all(s["rel_resid"] <= 1e-8 * 1.0000001 for s in st)}
+    del cav, net
+    torch.cuda.empty_cache()
+    return out
+
+
+def time_to_rtol(cfd, params, device, sizes=(128, 256), fpcg_systems=None):
+    """Time to the FP64 true-residual rtol 1e-8 per solve of FP64 CG, IR,
+    learned FPCG (mixed precision, graph form) and IR from the learned guess,
+    on held-out cavity pressure systems (seeds 200..203, step 10) and a
+    Gaussian right-hand side.  Flexible CG applies the network in every
+    iteration; at 256^3 it is timed on fpcg_systems[256] system(s) only."""
+    import torch
+    from paper_2504_03697_gb300 import learned
+    fpcg_systems = fpcg_systems or {256: 1}
+    out = {}
+    for n in sizes:
+        systems = learned.eval_systems(n)
+        res = {}
+        for label in learned.SOLVERS:
+            use = systems[:fpcg_systems[n]] if (label == "fpcg" and n in fpcg_systems) else systems
+            r = learned.evaluate(n, params, use, solvers=(label,), log=lambda *a: None)
+            res[label] = dict(r["summary"][label], systems=len(use),
+                              converged=all(e["status"] == 0 and e["rel_resid"] <= 1e-8 * 1.0000001
+                                            for row in r["rows"].values() for e in row),
+                              plain_iters=[e["plain_iters"] for row in r["rows"].values() for e in row])
+        cg = res["cg"]["median_ms"]
+        out[str(n)] = {"systems": [nm for nm, _ in systems], "solvers": res,
+                       "speedup_vs_fp64_cg": {k: cg / v["median_ms"] for k, v in res.items()}}
+        del systems
+        torch.cuda.empty_cache()
+    return out
+
+
 def main_ours(args):
     import numpy as np
     import torch
@@ -299,31 +498,33 @@ def main_ours(args):
     from paper_2504_03697_gb300 import build as B
     B.build()
     from paper_2504_03697_gb300 import cfd
-    from paper_2504_03697_gb300.synthetic import cavity_perturbation
 
     wl = WORKLOADS[args.workload]
     n = wl["n"]
     cells = n ** 3
-    prm = cfd.make_params(n, n, n, dt=wl["dt"], nu=wl["nu"], lid_u=wl["lid_u"], solver=args.solver,
-                          advect_order=args.advect_order)
+    solver = args.solver
+    params = None
+    if solver in ("fpcg", "guess"):
+        from paper_2504_03697_gb300 import learned
+        path = args.unet_weights or weights_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: the learned solvers need the trained U-Net parameters")
+        params = learned.load_params(path)
     stream = torch.cuda.current_stream(device)
-    cav = cfd.Cavity(prm, device=device)
-    init = cavity_perturbation(n, n, n, wl["seed"] + rank, wl["amp"])
-    for name, f in zip("uvw", init):
-        cav.set_field(name, f)
-    cav.set_cg_variant(args.cg_variant)
-    if args.concurrent_diffusion == "off":
+    cav, net = make_cavity(cfd, n, wl, solver, device, params, args.advect_order)
+    init_fields(cav, n, wl, rank)
+    cav.set_cg_variant(args.cg_variant) if solver == "cg" else None
+    if args.concurrent_diffusion == "off" and solver in ("cg", "jacobi"):
         cav.set_concurrent_diffusion(False)
     # solver shape for this grid (blocks per SM x tile depth), picked by
     # timing fixed-length solves; outside the timed region, state untouched
-    tune = None if args.no_autotune else cav.autotune(iters=50)
+    tune = None if (args.no_autotune or solver not in ("cg", "ir")) else cav.autotune(iters=50)
 
-    # warm-up
     if args.warmup > 0:
-        rc, _ = cav.step(args.warmup, stats=True)
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=device)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        cav.step(args.warmup, stats=True)
+    # inputs larger than L2 (129 MB) need no flush: the 384^3 state is ~7 GB
+    big = cells * 8 * 4 > 512 * 1024 * 1024
+    flush = None if big else torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=device)
 
     cav.phase_times()  # reset
     cav.enable_timing(True)
@@ -332,18 +533,12 @@ def main_ours(args):
     barrier(dist, device)
     torch.cuda.synchronize(device)
     wall0 = time.perf_counter()
-    for s in range(args.steps):
-        flush.zero_()  # L2 flush, outside the timed events
-        starts[s].record(stream)
-        cav.step(1, stats=False)
-        ends[s].record(stream)
-    torch.cuda.synchronize(device)
+    step_ms = timed_steps(cav, args.steps, stream, device, flush)
     wall = time.perf_counter() - wall0
     barrier(dist, device)
     clocks = sampler.stop() if sampler else None
     launches = cav.launch_count() - launches0
     cav.enable_timing(False)
-    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     t_local = sum(step_ms) / 1e3
     t_max = reduce_max(dist, t_local, device)
     phases = cav.phase_times()
@@ -356,8 +551,6 @@ def main_ours(args):
     pcg_ms, pcg_calls = phases["pcg"]
     pcg_avg_s = pcg_ms / max(pcg_calls, 1) / 1e3
     mean_iters = float(np.mean(iters))
-    flops_per_launch = cells * (CG_FLOPS_PER_CELL_ITER * mean_iters + CG_FLOPS_PER_CELL_SOLVE)
-    bytes_per_launch = cells * (CG_BYTES_PER_CELL_ITER * mean_iters + CG_BYTES_PER_CELL_SOLVE)
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -365,40 +558,30 @@ def main_ours(args):
     except (OSError, ValueError):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    fp64_peak_tflops = 1.20  # FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (measured with DFMA chains)
-    achieved_tflops = flops_per_launch / pcg_avg_s / 1e12
-    variant = tune["cg_variant"] if tune is not None else (0 if args.cg_variant == "single" else 1)
-    # the launch the captured counters belong to: 128 blocks, register path, tile depth 8
-    pressure_shape = cav.solver_shape(0)
-    roofline = {"bound": "alu",
-                "kernel": ("cg1_fp64_kernel (pressure CG, single reduction per iteration, persistent)" if variant == 0
-                           else "cg_fp64_kernel (pressure CG, two reductions per iteration, persistent)"),
-                "achieved": achieved_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved_tflops / fp64_peak_tflops,
-                "traffic": (CG1_CAVITY64_DRAM_BYTES if (args.workload == "cavity64" and variant == 0
-                                                         and args.solver == "cg"
-                                                         and pressure_shape == CG1_CAVITY64_SHAPE) else None),
-                "launch_shape": pressure_shape,
-                "peak_source": "FP64 FMA rate from the recipe's unit counts and clocks (1.2-1.25 TFLOP/s)",
-                "hbm_achieved_gbs": bytes_per_launch / pcg_avg_s / 1e9,
-                "hbm_peak_gbs": hbm_peak, "hbm_frac_of_measured": bytes_per_launch / pcg_avg_s / 1e9 / hbm_peak,
-                "launch_ms": pcg_avg_s * 1e3, "flops_per_launch": flops_per_launch,
-                "bytes_per_launch": bytes_per_launch}
-    if args.solver == "ir":
-        # bytes per cell and FP32 iteration: persistent form 40 (direction:
-        # read r32, p_old, write p, q; update: read p, q, x32, r32, write x32,
-        # r32); graph form 32 (q is formed again in the update, never stored);
-        # the FP64 refinements add a few residual passes, left out of the count
-        form = tune["ir_form"] if tune is not None else 0
-        graph = form == 2 or (form == 0 and n % 4 == 0 and cells >= 1 << 21)
-        ir_bytes = cells * (IR_GRAPH_BYTES_PER_CELL_ITER if graph else IR_BYTES_PER_CELL_ITER) * mean_iters
-        ir_gbs = ir_bytes / pcg_avg_s / 1e9
-        roofline = {"bound": "hbm",
-                    "kernel": ("g_dir + g_upd (FP32 CG iteration, graph form)" if graph
-                               else "ir_kernel (FP32 CG + FP64 refinement, persistent)"),
-                    "achieved": ir_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": ir_gbs / hbm_peak,
-                    "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
-                    "launch_ms": pcg_avg_s * 1e3, "bytes_per_launch": ir_bytes}
+    peak_src = "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
+    if solver == "cg":
+        flops = cells * (CG_FLOPS_PER_CELL_ITER * mean_iters + CG_FLOPS_PER_CELL_SOLVE)
+        bytes_ = cells * (CG_BYTES_PER_CELL_ITER * mean_iters + CG_BYTES_PER_CELL_SOLVE)
+        achieved = flops / pcg_avg_s / 1e12
+        roofline = {"bound": "alu", "kernel": "cg1_fp64_kernel / cg_fp64_kernel (pressure CG, persistent)",
+                    "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS,
+                    "traffic": CG1_CAVITY64_DRAM_BYTES if (args.workload == "cavity64"
+                                                           and cav.solver_shape(0) == CG1_CAVITY64_SHAPE) else None,
+                    "peak_source": FP64_PEAK_SOURCE, "launch_ms": pcg_avg_s * 1e3,
+                    "hbm_achieved_gbs": bytes_ / pcg_avg_s / 1e9, "hbm_frac_of_measured": bytes_ / pcg_avg_s / 1e9 / hbm_peak}
+    else:
+        # the FP32 iteration of the graph form moves 32 B per cell (g_dir reads
+        # r32, p_old and writes p; g_upd reads p, x32, r32 and writes x32, r32);
+        # the FP64 refinements and the learned guess are inside the timed
+        # solve but left out of the algorithmic bytes (a lower bound on frac)
+        ir_bytes = cells * IR_GRAPH_BYTES_PER_CELL_ITER * mean_iters
+        gbs = ir_bytes / pcg_avg_s / 1e9
+        roofline = {"bound": "hbm", "kernel": "g_dir + g_upd (FP32 CG iteration, graph form; whole pressure solve timed)",
+                    "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                    "traffic": IR_GRAPH_DRAM_BYTES_PER_CELL_ITER * cells * mean_iters
+                    if IR_GRAPH_DRAM_BYTES_PER_CELL_ITER else None,
+                    "peak_source": peak_src, "launch_ms": pcg_avg_s * 1e3, "bytes_per_launch": ir_bytes}
     phase_ms_per_step = {k: v[0] / max(args.steps, 1) for k, v in phases.items()}
 
     # end-to-end through the C-ABI with host buffers (state round-trips per step)
@@ -423,58 +606,68 @@ def main_ours(args):
                "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io, "steps": args.e2e_steps,
                "how": "per step: cfd_set_field(u,v,w,p) from pinned host, cfd_step(1), cfd_read_field(u,v,w,p) "
                       "to pinned host; wall clock"}
+        del host
+    del cav, net
+    torch.cuda.empty_cache()
 
-    # precision study on the standalone 256^3 Neumann-Poisson system: FP64 CG
-    # vs FP32 CG with FP64 refinement, both to a true FP64 rtol of 1e-8
-    precision = None
-    if rank == 0 and world == 1 and not args.no_precision_study:
-        cav.close()
-        del cav
-        torch.cuda.empty_cache()
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_studies:
+        # the same cavity with the other solver paths (samples of steps)
+        extra["same_cavity"] = {}
+        for other, k_steps, warm in (("cg", 2, 1), ("ir", 4, 1)):
+            if other != solver:
+                extra["same_cavity"][other] = cavity_sample(cfd, n, wl, other, k_steps, warm, device, params)
+        extra["same_cavity"]["note"] = (f"samples of {wl['steps_total']} steps: FP64 CG 2 timed steps after 1, IR 4 "
+                                        f"after 1; flexible CG with the network in every iteration is timed on "
+                                        f"standalone systems only (time_to_rtol), since one application of the "
+                                        f"network costs tens of FP32 iterations at this size")
+        if params is not None:
+            extra["time_to_rtol"] = time_to_rtol(cfd, params, device)
+        # the 64^3 FP64 cavity (plain method on the GPU)
+        extra["cavity64_fp64_cg"] = cavity_sample(cfd, 64, WORKLOADS["cavity64"], "cg", 20, 3, device)
+        # standalone 256^3 Poisson, FP64 CG vs FP32/FP64-IR (2 of 32 RHS)
         study = {}
-        for solver in ("cg", "ir"):
-            res = time_solves(cfd, 256, solver, [0, 1], 1, 0, device)
-            study[solver] = {"ms_per_solve": [round(r["ms"], 3) for r in res], "iters": [r["iters"] for r in res],
-                             "refinements": [r["refinements"] for r in res],
-                             "rel_resid": [r["rel_resid"] for r in res]}
-        cg_ms = statistics.mean(study["cg"]["ms_per_solve"])
-        ir_ms = statistics.mean(study["ir"]["ms_per_solve"])
-        precision = {"workload": "Neumann-Poisson 256^3, N(0,1) right-hand sides seeds 0-1, rtol 1e-8 (true FP64)",
-                     "fp64_cg": study["cg"], "fp32_cg_fp64_refined": study["ir"],
-                     "speedup_ir_over_fp64_cg": cg_ms / ir_ms}
-
-    # batched uneven cavities: FP64 CG vs mixed precision, graph-replayed
-    batch = None
-    if rank == 0 and world == 1 and not args.no_batch_study:
-        batch = {s: time_batch(cfd, 64, s, 3, 1, device) for s in ("cg", "ir")}
+        for sv in ("cg", "ir"):
+            res = time_solves(cfd, 256, sv, [0, 1], 1, 0, device)
+            study[sv] = {"ms_per_solve": [round(r["ms"], 3) for r in res], "iters": [r["iters"] for r in res],
+                         "refinements": [r["refinements"] for r in res], "rel_resid": [r["rel_resid"] for r in res]}
+        extra["precision_study"] = {
+            "workload": "Neumann-Poisson 256^3, N(0,1) right-hand sides, rtol 1e-8 (true FP64); sample: seeds 0-1 "
+                        "of the 32", "fp64_cg": study["cg"], "fp32_cg_fp64_refined": study["ir"],
+            "speedup_ir_over_fp64_cg": statistics.mean(study["cg"]["ms_per_solve"]) /
+            statistics.mean(study["ir"]["ms_per_solve"])}
+        extra["batch_study"] = {sv: time_batch(cfd, 64, sv, 3, 1, device) for sv in ("cg", "ir")}
+        extra["batch_study"]["note"] = "sample: 3 timed steps of the 50 (after 1 warm-up step), graph-replayed"
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        res = run_oracle_child(args.workload, 10 ** 6, 0, args.cpu_seconds)
-        cpu = {"value": res["cells"] * res["steps"] / res["seconds"], "unit": "cell-steps/s", "cores": 1,
-               "kind": "oracle",
-               "sample": f"first {res['steps']} time steps of the same {n}^3 cavity ({res['seconds']:.1f} s), "
-                         f"FP64 numpy/scipy oracle, single thread",
-               "cpu": cpu_model(), "host_cores": os.cpu_count()}
+        full = CG_ITERS_PER_STEP.get(n, 0)
+        cgs = extra.get("same_cavity", {}).get("cg")
+        if cgs:
+            full = int(round(float(np.mean(cgs["pressure_iters"]))))
+        cpu = oracle_baseline(args.workload, full)
 
     if rank == 0:
         line = {"metric": "cell-steps/s", "value": value, "unit": "cell-steps/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": {"cg": "f64", "ir": "f32+f64", "fpcg": "bf16+f32+f64", "guess": "bf16+f32+f64"}[solver],
                 "data": "synthetic",
-                "config": {"workload": wl["desc"], "n": n, "cells": cells, "solver": args.solver,
-                           "steps_per_rank": args.steps, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                           "l2": "flushed between timed steps (256 MiB write outside the timed events)",
+                "config": {"workload": wl["desc"] + f"; solver {SOLVER_DESC[solver]}", "n": n, "cells": cells,
+                           "solver": solver, "steps_per_rank": args.steps,
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                           "l2": ("inputs larger than L2 (state ~%.1f GB), no flush" % (cells * 8 * 13 / 1e9)) if big
+                           else "flushed between timed steps (256 MiB write outside the timed events)",
                            "solver_shape": tune if tune is not None else "automatic",
-                           "cg_variant": args.cg_variant, "advect_order": args.advect_order,
-                           "concurrent_diffusion": args.concurrent_diffusion},
+                           "weights": os.path.relpath(args.unet_weights or weights_path(), ROOT) if params is not None
+                           else None, "advect_order": args.advect_order},
                 "solve": {"pcg_iters_mean": mean_iters, "pcg_iters_min": min(iters), "pcg_iters_max": max(iters),
                           "time_to_rtol_ms_mean": pcg_avg_s * 1e3, "rel_resid_max": worst_resid,
-                          "all_converged": bool(ok)},
+                          "all_converged": bool(ok), "refinements": [s["outer_iters"] for s in stats]},
                 "phase_ms_per_step": phase_ms_per_step,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "precision_study": precision, "batch_study": batch,
                 "clocks": clocks, "wall_s_timed": wall}
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

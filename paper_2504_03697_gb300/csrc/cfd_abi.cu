@@ -1175,9 +1175,10 @@ int cfd_set_wait_limit(cfd_handle* h, uint64_t limit_ns) {
 
 int64_t cfd_launch_count(const cfd_handle* h) {
   if (!h) return 0;
+  // kernels of the graph form (and of the learned guess) count themselves
+  // in the graph state on the device
   long long graph_kernels = 0;
-  const bool graphs = h->irg || h->irg_diff[0] || h->irg_diff[1] || h->irg_diff[2];
-  if (graphs && h->irg_state && ir_graph_kernel_count(h->irg_state, h->stream, &graph_kernels) != cudaSuccess)
+  if (h->irg_state && ir_graph_kernel_count(h->irg_state, h->stream, &graph_kernels) != cudaSuccess)
     graph_kernels = 0;
   return h->launches + graph_kernels;
 }

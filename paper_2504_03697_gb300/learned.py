@@ -9,9 +9,16 @@ cavities at n^3 with nu ~ log-uniform[1e-4, 1e-2] and lid speed ~
 uniform[0.5, 2] drawn from the seed, dt 0.01, started from the seeded
 perturbation.  At selected steps the projection's right-hand side b is
 taken after forces, advection and diffusion (``cfd_pressure_rhs``), solved
-to rtol 1e-12 for x*, and the CG iterates x_k (k = 1, 2, 4, ...) give the
-pairs r_k = b - A x_k, e_k = x* - x_k (mean removed).  The whole data set
-stays resident in HBM; each Adam step takes a minibatch of pairs.
+to rtol 1e-12 for x*, and the CG iterates x_k (k = 0, 1, 2, 4, ...; x_0 =
+0, the pair the initial-guess mode uses) give the pairs r_k = b - A x_k,
+e_k = x* - x_k (mean removed).  The whole data set stays resident in HBM;
+each Adam step takes a minibatch of pairs.
+
+Evaluation: time to the FP64 true-residual rtol per solve (CUDA events on
+the solve) of FP64 CG, the FP32/FP64 refined solve (IR), flexible CG with
+the network as preconditioner in mixed precision (solver FPCG, graph form)
+and IR started from the network's guess (learned_guess), on held-out cavity
+systems and Gaussian right-hand sides.
 
 Everything here goes through the C-ABI (the solves, the network, its
 training step); torch only holds device memory and gathers minibatches.
@@ -52,11 +59,12 @@ def new_cavity(n: int, seed: int, solver="cg"):
     return cav
 
 
-def pressure_systems(n: int, seed: int, at_steps):
+def pressure_systems(n: int, seed: int, at_steps, solver="cg"):
     """Yield (step, b): the projection right-hand side of the cavity of this
     seed at each of the given steps (1-based), taken after forces, advection
-    and diffusion of that step; the run continues through the projection."""
-    cav = new_cavity(n, seed)
+    and diffusion of that step; the run continues through the projection
+    (with `solver`)."""
+    cav = new_cavity(n, seed, solver)
     b = torch.empty(n ** 3, dtype=torch.float64, device="cuda")
     for s in range(1, max(at_steps) + 1):
         if s in at_steps:
@@ -73,11 +81,13 @@ def pressure_systems(n: int, seed: int, at_steps):
 class Harvester:
     """Pressure systems and CG-iterate pairs of one grid size."""
 
-    def __init__(self, n: int, ks=(1, 2, 4, 8, 16, 32, 64, 128)):
+    KS = (0, 1, 2, 4, 8, 16, 32, 64, 128)
+
+    def __init__(self, n: int, ks=KS):
         self.n = n
         self.ks = tuple(ks)
         self.exact = cfd.Cavity(cfd.make_params(n, n, n, rtol=1e-12, max_iters=50 * n))
-        self.capped = {k: cfd.Cavity(cfd.make_params(n, n, n, rtol=1e-15, max_iters=k)) for k in self.ks}
+        self.capped = {k: cfd.Cavity(cfd.make_params(n, n, n, rtol=1e-15, max_iters=k)) for k in self.ks if k > 0}
 
     def pairs(self, b: torch.Tensor):
         """(R, E) [len(ks), V] for one system: each solve removes the mean of
@@ -91,7 +101,8 @@ class Harvester:
         xk = torch.empty_like(b)
         for i, k in enumerate(self.ks):
             xk.zero_()
-            self.capped[k].solve_pressure(b, xk, stats=False)
+            if k > 0:
+                self.capped[k].solve_pressure(b, xk, stats=False)
             self.exact.harvest_pair(b, xs, xk, R[i], E[i])
         return R, E
 
@@ -142,7 +153,7 @@ def eval_systems(n: int, seeds=EVAL_SEEDS, step=10, gaussian_seeds=(0,)):
     right-hand sides (out of distribution)."""
     out = []
     for seed in seeds:
-        for s, b in pressure_systems(n, seed, {step}):
+        for s, b in pressure_systems(n, seed, {step}, solver="ir"):
             out.append((f"cavity seed {seed} step {s}", b))
     for gs in gaussian_seeds:
         out.append((f"gaussian seed {gs}", torch.from_numpy(gaussian_rhs(n, n, n, gs).reshape(-1)).cuda()))
@@ -161,29 +172,67 @@ def time_call(fn, reps=1):
     return st.elapsed_time(en) / reps, out
 
 
-def evaluate(n: int, params: torch.Tensor, systems, rtol=1e-8, log=print):
-    """FPCG with the network vs FP64 CG and the FP32/FP64 refined solve on
-    the same systems; time to the FP64 true-residual rtol."""
+SOLVERS = ("cg", "ir", "fpcg", "guess")
+
+
+def solver_cavity(n: int, label: str, params: torch.Tensor, rtol=1e-8):
+    """A handle solving n^3 pressure systems with one of SOLVERS: FP64 CG,
+    the refined FP32/FP64 solve (graph form), flexible CG with the network
+    in mixed precision, or IR from the network's initial guess."""
+    if label == "cg":
+        return cfd.Cavity(cfd.make_params(n, n, n, rtol=rtol, solver="cg")), None
+    if label == "ir":
+        cav = cfd.Cavity(cfd.make_params(n, n, n, rtol=rtol, solver="ir"))
+        cav.set_ir_form("graph")
+        return cav, None
     net = cfd.UNet(n, n, n, seed=0)
     net.set_params(params)
-    cg = cfd.Cavity(cfd.make_params(n, n, n, rtol=rtol, solver="cg"))
-    ir = cfd.Cavity(cfd.make_params(n, n, n, rtol=rtol, solver="ir"))
+    if label == "fpcg":
+        cav = cfd.Cavity(cfd.make_params(n, n, n, rtol=rtol, solver="fpcg"))
+    else:
+        cav = cfd.Cavity(cfd.make_params(n, n, n, rtol=rtol, solver="ir", learned_guess=True))
+    cav.attach_preconditioner(net)
+    return cav, net
+
+
+def timed_solve(cav, b, x):
+    """One solve from x = 0: (device ms of the solve from CUDA events on its
+    stream, statistics)."""
+    x.zero_()
+    st = torch.cuda.Event(enable_timing=True)
+    en = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    st.record()
+    rc, stats = cav.solve_pressure(b, x)
+    en.record()
+    torch.cuda.synchronize()
+    stats["rc"] = rc
+    return st.elapsed_time(en), stats
+
+
+def evaluate(n: int, params: torch.Tensor, systems, rtol=1e-8, solvers=SOLVERS, log=print):
+    """Time to the FP64 true-residual rtol per solve of each solver on the
+    same systems (one warm-up solve per solver first)."""
     x = torch.zeros(n ** 3, dtype=torch.float64, device="cuda")
-    z = torch.empty_like(x)
-    t_apply, _ = time_call(lambda: net.apply(systems[0][1], z), reps=5)
-    rows = []
-    for name, b in systems:
-        row = {"system": name}
-        for label, fn in (("cg", lambda: cg.solve_pressure(b, x)), ("ir", lambda: ir.solve_pressure(b, x)),
-                          ("fpcg", lambda: net.fpcg_solve(b, x, rtol=rtol))):
-            fn()  # warm-up
-            ms, (rc, st) = time_call(fn)
-            row[label] = {"ms": ms, "iters": st["iters"], "plain_iters": st["outer_iters"], "status": st["status"],
-                          "rel_resid": st["rel_resid"]}
-        rows.append(row)
-        log(f"  {name}: " + ", ".join(f"{k} {row[k]['ms']:.1f} ms / {row[k]['iters']} it"
-                                       for k in ("cg", "ir", "fpcg")))
-    return {"n": n, "unet_apply_ms": t_apply, "rows": rows}
+    rows = {name: [] for name, _ in systems}
+    for label in solvers:
+        cav, net = solver_cavity(n, label, params, rtol)
+        timed_solve(cav, systems[0][1], x)  # warm-up (builds the graph)
+        for name, b in systems:
+            ms, st = timed_solve(cav, b, x)
+            rows[name].append({"solver": label, "ms": ms, "iters": st["iters"], "refinements": st["outer_iters"],
+                               "plain_iters": st["restarts"] if label == "fpcg" else 0, "status": st["status"],
+                               "rel_resid": st["rel_resid"]})
+        del cav, net
+        torch.cuda.empty_cache()
+    for name, r in rows.items():
+        log(f"  {name}: " + ", ".join(f"{e['solver']} {e['ms']:.1f} ms / {e['iters']} it" for e in r))
+    summary = {}
+    for label in solvers:
+        ms = sorted(e["ms"] for r in rows.values() for e in r if e["solver"] == label)
+        summary[label] = {"median_ms": float(np.median(ms)), "min_ms": ms[0], "max_ms": ms[-1],
+                          "iters": [e["iters"] for r in rows.values() for e in r if e["solver"] == label]}
+    return {"n": n, "systems": [name for name, _ in systems], "rows": rows, "summary": summary}
 
 
 def main(argv=None):
@@ -192,13 +241,13 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--seeds", type=int, default=len(TRAIN_SEEDS))
     ap.add_argument("--steps", type=str, default="2,5,10,15,20")
-    ap.add_argument("--iters", type=int, default=2000)
+    ap.add_argument("--iters", type=int, default=600)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--loss", choices=["mse", "anorm", "cos"], default="cos")
     ap.add_argument("--out", default=WEIGHTS)
     ap.add_argument("--weights", default=WEIGHTS)
-    ap.add_argument("--eval-n", type=str, default="128")
+    ap.add_argument("--eval-n", type=str, default="128,256")
     ap.add_argument("--json", default=None)
     a = ap.parse_args(argv)
     from . import build
@@ -207,14 +256,15 @@ def main(argv=None):
     if a.mode == "train":
         at = [int(s) for s in a.steps.split(",")]
         print(f"harvest: {a.seeds} cavities at {a.n}^3, steps {at}")
-        R, E = harvest(a.n, TRAIN_SEEDS[:a.seeds], at, (1, 2, 4, 8, 16, 32, 64, 128))
+        R, E = harvest(a.n, TRAIN_SEEDS[:a.seeds], at, Harvester.KS)
         print(f"{R.shape[0]} pairs ({R.numel() * 16 / 1e9:.1f} GB resident)")
         net = cfd.UNet(a.n, a.n, a.n, seed=0)
         net.set_loss(a.loss)
         t0 = time.time()
         losses = train(net, R, E, a.iters, a.batch, a.lr)
         params = net.get_params()
-        meta = {"n": a.n, "train_seeds": list(TRAIN_SEEDS[:a.seeds]), "steps": at, "iters": a.iters,
+        meta = {"n": a.n, "train_seeds": list(TRAIN_SEEDS[:a.seeds]), "steps": at, "cg_iterates": list(Harvester.KS),
+                "iters": a.iters,
                 "batch": a.batch, "lr": a.lr, "loss": a.loss, "pairs": int(R.shape[0]), "first_loss": losses[0],
                 "final_loss": float(np.mean(losses[-50:])), "train_seconds": time.time() - t0}
         save_params(params, a.out, meta)

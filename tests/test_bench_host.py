@@ -8,8 +8,18 @@ import bench
 def test_default_workload_and_contract_arguments():
     a = bench.parse_args([])
     assert a.gpus == 1 and a.warmup >= 3 and a.impl == "ours"
-    assert a.workload == "cavity64" and a.solver == "cg"
+    # the largest single-GPU configuration: the 384^3 cavity on the learned +
+    # mixed-precision path
+    assert a.workload == "cavity384" and bench.WORKLOADS["cavity384"]["n"] == 384 and a.solver == "guess"
     assert a.concurrent_diffusion == "on" and a.ir_form == "tuned"
+    assert set(bench.SOLVER_DESC) == {"cg", "ir", "fpcg", "guess"}
+
+
+def test_oracle_sample_scaling_is_stated():
+    # the reference arm scales a sampled oracle step by the FP64 CG count
+    # measured at 384^3
+    assert bench.CG_ITERS_PER_STEP[384] > 1000
+    assert bench.FP64_PEAK_TFLOPS > 1.0 and "clocks" in bench.FP64_PEAK_SOURCE
 
 
 def test_byte_models_per_cell():
