@@ -128,6 +128,8 @@ def parse_args(argv=None):
     ap.add_argument("--unet-weights", default="", help="FP32 parameter file for --unet (default: seeded init)")
     ap.add_argument("--unet-conv-mode", choices=["registers", "bulk", "two_stage"], default="bulk",
                     help="staging of the tiled convolutions (comparison)")
+    ap.add_argument("--fp64-peak", action="store_true",
+                    help="measure the FP64 FMA rate (cfd_probe_fp64_fma) instead of the cavity")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--max-seconds", type=float, default=150.0, help=argparse.SUPPRESS)
     return ap.parse_args(argv)
@@ -788,7 +790,47 @@ def main(argv=None):
         return main_spmv(args)
     if args.blas > 0:
         return main_blas(args)
+    if args.fp64_peak:
+        return main_fp64_peak(args)
     return main_ours(args)
+
+
+def main_fp64_peak(args):
+    """FP64 FMA rate of the device: a resident wave of DFMA-chain blocks
+    (8 blocks of 256 threads per SM), best of `steps` timed launches after
+    `warmup` (CUDA events on the launching stream)."""
+    import ctypes
+
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2504_03697_gb300 import build as B
+    B.build()
+    from paper_2504_03697_gb300 import cfd
+    lib = cfd.load_library()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    blocks, iters = sms * 8, 20000
+    out = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    flops = 2.0 * 8 * iters * 256 * blocks
+    times = []
+    for i in range(args.warmup + args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rc = lib.cfd_probe_fp64_fma(blocks, iters, ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+        b.record(stream)
+        torch.cuda.synchronize()
+        if rc != 0:
+            raise RuntimeError(lib.cfd_last_error(None).decode())
+        if i >= args.warmup:
+            times.append(a.elapsed_time(b) / 1e3)
+    best = min(times)
+    line = {"metric": "FP64 FMA rate", "value": flops / best / 1e12, "unit": "TFLOP/s", "higher_is_better": True,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{blocks} blocks x 256 threads x 8 DFMA chains x {iters} (best of {args.steps})",
+                       "sms": sms, "flop_per_launch": flops},
+            "ms_per_launch": [t * 1e3 for t in times]}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def main_batch(args):

@@ -487,6 +487,14 @@ int cfd_cg_update_f64(size_t n, double alpha, const double *p_dev, const double 
 int cfd_cg_update_f32(size_t n, float alpha, const float *p_dev, const float *q_dev, float *x_dev, float *r_dev,
                       double *rr_dev, void *scratch_dev, cfd_stream_t stream);
 
+/* FP64 FMA throughput probe, the peak the FP64 kernels are measured
+ * against (GB300's FP64 rate, not HBM, bounds the FP64 stencil): blocks x
+ * 256 threads, each running 8 independent chains of `iters` fused
+ * multiply-adds, 2 * 8 * iters * 256 * blocks flop in all.  out_dev: device
+ * doubles, one per thread (blocks * 256).  Asynchronous on stream; the
+ * caller times it (CUDA events). */
+int cfd_probe_fp64_fma(int blocks, int iters, double *out_dev, cfd_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Learned preconditioner (flexible PCG with a U-Net, Sec. 5 "other
  * preconditioners"; the paper itself uses DIC / Jacobi, Sec. 3.1).

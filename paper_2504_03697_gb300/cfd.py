@@ -126,6 +126,7 @@ def load_library(path: Optional[str] = None):
         "cfd_snapshot_write_csv": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_int]),
         "cfd_apply_poisson_f32": (ctypes.c_int, [ctypes.c_int32] * 3 + [vp, vp, vp]),
         "cfd_cg_update_scratch_bytes": (ctypes.c_size_t, []),
+        "cfd_probe_fp64_fma": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, vp]),
         "cfd_cg_update_f64": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_double, vp, vp, vp, vp, vp, vp, vp]),
         "cfd_cg_update_f32": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_float, vp, vp, vp, vp, vp, vp, vp]),
         "cfd_conv3d_bf16": (ctypes.c_int, [ctypes.c_int] * 3 + [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, vp,

@@ -192,6 +192,24 @@ __global__ void __launch_bounds__(kVecThreads) update_f32_kernel(size_t n, float
   block_reduce_last(s, partials, done, rr);
 }
 
+// FP64 FMA throughput probe (the peak the FP64 kernels are reported
+// against): every thread runs 8 independent chains x <- x a + b of `iters`
+// DFMAs each, so that the FP64 pipe, not the FMA latency, bounds the rate;
+// each thread stores its sum so that no chain can be dropped.
+__global__ void __launch_bounds__(kVecThreads) fp64_fma_probe_kernel(int iters, double a, double b, double* out) {
+  double x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = 1e-3 * double(threadIdx.x) + double(k);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) sum += x[k];
+  out[size_t(blockIdx.x) * blockDim.x + threadIdx.x] = sum;
+}
+
 constexpr int kMaxBlocks = 2048;  // partial sums held by the scratch
 
 // One resident wave of the update kernels (grid-stride loops), capped by the
@@ -257,6 +275,15 @@ int cfd_apply_poisson_f32(int32_t nx, int32_t ny, int32_t nz, const float* x_dev
 }
 
 size_t cfd_cg_update_scratch_bytes(void) { return kScratchBytes; }
+
+int cfd_probe_fp64_fma(int blocks, int iters, double* out_dev, cfd_stream_t stream) {
+  if (blocks < 1 || iters < 1 || !out_dev || (reinterpret_cast<uintptr_t>(out_dev) & 7))
+    return cfd_internal_error(CFD_ERR_INVALID_ARG, "probe_fp64_fma: blocks, iters >= 1 and an aligned output");
+  fp64_fma_probe_kernel<<<blocks, kVecThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(iters, 0.9999999, 1e-7,
+                                                                                             out_dev);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? CFD_OK : cfd_internal_error(CFD_ERR_CUDA, "probe_fp64_fma: %s", cudaGetErrorString(e));
+}
 
 int cfd_cg_update_f64(size_t n, double alpha, const double* p_dev, const double* q_dev, double* x_dev, double* r_dev,
                       double* rr_dev, void* scratch_dev, cfd_stream_t stream) {

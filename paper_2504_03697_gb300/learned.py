@@ -138,14 +138,30 @@ def train(net: cfd.UNet, R: torch.Tensor, E: torch.Tensor, iters: int, batch: in
 
 
 def save_params(params: torch.Tensor, path: str, meta: dict):
-    os.makedirs(os.path.dirname(path), exist_ok=True)
+    """The parameters as a raw little-endian float32 blob, with a JSON header
+    beside it (path + '.json') naming the layout, the count and the training
+    run."""
+    d = os.path.dirname(path)
+    if d:
+        os.makedirs(d, exist_ok=True)
     params.detach().cpu().to(torch.float32).numpy().astype("<f4").tofile(path)
+    meta = dict(meta, count=int(params.numel()),
+                format="little-endian float32, the cfd_unet parameter layout (per layer L0a, L0b, L1a, L1b, L2a, "
+                       "L2b, L1c, L0c, head: weights [taps][cout][cin] with tap = kx + 3 ky + 9 kz, then bias [cout])")
     with open(path + ".json", "w") as f:
         json.dump(meta, f, indent=1, sort_keys=True)
 
 
 def load_params(path: str = WEIGHTS) -> torch.Tensor:
-    return torch.from_numpy(np.fromfile(path, dtype="<f4").astype(np.float32))
+    """Parameters saved by save_params; checks the count in the header."""
+    p = torch.from_numpy(np.fromfile(path, dtype="<f4").astype(np.float32))
+    hdr = path + ".json"
+    if os.path.exists(hdr):
+        with open(hdr) as f:
+            count = json.load(f).get("count")
+        if count is not None and count != p.numel():
+            raise ValueError(f"{path}: {p.numel()} values, the header says {count}")
+    return p
 
 
 def eval_systems(n: int, seeds=EVAL_SEEDS, step=10, gaussian_seeds=(0,)):

@@ -47,3 +47,19 @@ def test_measured_hbm_peak_fallback(tmp_path, monkeypatch):
 def test_aggregate_is_all_ranks_over_the_slowest():
     # 2 ranks x 1000 cells x 10 steps in 2 s (the slowest rank's time)
     assert bench.aggregate(1000, 10, 2, 2.0) == 1000 * 10 * 2 / 2.0
+
+
+def test_committed_weights_match_the_network_layout():
+    """The trained parameters the learned solvers load: the oracle network's
+    parameter count, finite values, and a header naming the training run."""
+    import os
+
+    import numpy as np
+    from oracle import unet
+
+    path = bench.weights_path()
+    assert os.path.exists(path) and os.path.exists(path + ".json")
+    w = np.fromfile(path, dtype="<f4")
+    assert w.size == unet.param_count() and np.isfinite(w).all()
+    meta = json.load(open(path + ".json"))
+    assert meta["count"] == w.size and meta["n"] == 128 and meta["loss"] == "cos"
