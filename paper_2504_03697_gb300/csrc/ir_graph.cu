@@ -74,7 +74,10 @@ namespace {
 
 constexpr int kGThreads = 256;  // every kernel: 256 threads (32 x 8 for the stencils)
 constexpr int kGMax = 1024;     // blocks per kernel (partial-sum slots per value)
-constexpr int kZ32 = 4;         // z planes per FP32 stencil work item
+#ifndef CFD_IRG_ZPLANES
+#define CFD_IRG_ZPLANES 4
+#endif
+constexpr int kZ32 = CFD_IRG_ZPLANES;  // z planes per FP32 stencil work item
 constexpr int kZ64 = 4;         // z planes per FP64 stencil work item
 
 // Solver scalars of one solve (device memory, written only by the thread 0
@@ -367,10 +370,7 @@ __device__ __forceinline__ void march_f32(const GArgs& a, F4 P4, F1 P1, E emit) 
     size_t c4 = (size_t(k0) * my + j) * nx4 + (on ? i4 : nx4 - 1);  // idle lanes shadow the last column
     float4 pc = P4(c4);
     float4 pm = k0 > 0 ? P4(c4 - sz4) : pc;
-#pragma unroll
-    for (int kk = 0; kk < kZ32; ++kk) {
-      const int k = k0 + kk;
-      if (k >= mz) break;
+    auto plane = [&](int k) {
       const float4 pp = k < mz - 1 ? P4(c4 + sz4) : pc;
       const float4 ps = j > 0 ? P4(c4 - sy4) : pc;
       const float4 pn = j < my - 1 ? P4(c4 + sy4) : pc;
@@ -398,6 +398,14 @@ __device__ __forceinline__ void march_f32(const GArgs& a, F4 P4, F1 P1, E emit) 
       pm = pc;
       pc = pp;
       c4 += sz4;
+    };
+    // whole work items as straight-line code (the loads of later planes can
+    // be issued early); the last, partial item of a column plane by plane
+    if (k0 + kZ32 <= mz) {
+#pragma unroll
+      for (int kk = 0; kk < kZ32; ++kk) plane(k0 + kk);
+    } else {
+      for (int k = k0; k < mz; ++k) plane(k);
     }
   }
 }
@@ -425,10 +433,7 @@ __device__ __forceinline__ double edge_pass(const GArgs& a, F4 P4, F1 P1, float4
     const bool has_e = i4 + 1 < nx4;
     size_t c4 = (size_t(k0) * my + j) * nx4 + (on ? i4 : nx4 - 1);  // idle lanes shadow the last column
     float4 pc = P4(c4);
-#pragma unroll
-    for (int kk = 0; kk < kZ32; ++kk) {
-      const int k = k0 + kk;
-      if (k >= mz) break;
+    auto plane = [&](int k) {
       const bool up = k < mz - 1;
       const float4 pp = up ? P4(c4 + sz4) : pc;
       const float4 pn = j < my - 1 ? P4(c4 + sy4) : pc;
@@ -446,6 +451,12 @@ __device__ __forceinline__ double edge_pass(const GArgs& a, F4 P4, F1 P1, float4
       }
       pc = pp;
       c4 += sz4;
+    };
+    if (k0 + kZ32 <= mz) {
+#pragma unroll
+      for (int kk = 0; kk < kZ32; ++kk) plane(k0 + kk);
+    } else {
+      for (int k = k0; k < mz; ++k) plane(k);
     }
   }
   return acc;
