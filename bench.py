@@ -6,14 +6,14 @@ Default workload: the 384^3 cavity (56.6 M cells) of Sec. 3 / 3.1 of arXiv
 2504.03697 with lid 1.0, nu 1e-3, dt 1e-2, the seeded uniform[-1e-3, 1e-3]
 perturbation (seed 5 + rank), every solve to the FP64 true-residual rtol
 1e-8, on the learned + mixed-precision path (``--solver``: the pressure solve
-as FP32 CG with FP64 refinement started from the U-Net's initial guess, the
-diffusion solves in the same mixed precision).  One bench "step" is one time
+as FP32 CG with FP64 refinement started from the previous step's pressure
+corrected by the U-Net, the diffusion solves in the same mixed precision).  One bench "step" is one time
 step: applyForces, advection, implicit diffusion (3 solves), divergence,
 pressure solve, correction.  Inputs are synthetic and resident in HBM when
 the timed region starts; at this size they are larger than L2 (no flush).
 
-The same line carries: the same cavity with FP64 CG and with plain IR
-(samples of steps); time to rtol per solve of FP64 CG, IR, learned flexible
+The same line carries: the same cavity with FP64 CG and with plain IR, both
+warm-started too (samples of steps); time to rtol per solve of FP64 CG, IR, learned flexible
 CG and IR from the learned guess on held-out 128^3 and 256^3 systems; the
 64^3 FP64 cavity; the 256^3 precision study; the 64-cavity batch study; the
 oracle on the host cores (single thread and all cores, a sampled step
@@ -42,9 +42,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    "cavity384": dict(n=384, nu=1e-3, dt=1e-2, lid_u=1.0, seed=5, amp=1e-3, steps_total=50,
+    "cavity384": dict(n=384, nu=1e-3, dt=1e-2, lid_u=1.0, seed=5, amp=1e-3, steps_total=50, warm_start=True,
                       desc="lid-driven cavity 384^3 cells (56.6 M), lid 1.0, nu 1e-3, dt 1e-2, "
-                           "solves to rtol 1e-8 (FP64 true residual), seeded 1e-3 perturbation"),
+                           "solves to rtol 1e-8 (FP64 true residual), pressure solves warm-started from the "
+                           "previous step's p, seeded 1e-3 perturbation"),
     "cavity64": dict(n=64, nu=1e-3, dt=1e-2, lid_u=1.0, seed=2, amp=1e-3, steps_total=100,
                      desc="lid-driven cavity 64^3 cells, lid 1.0, nu 1e-3, dt 1e-2, "
                           "solves to rtol 1e-8 (FP64 true residual), seeded 1e-3 perturbation"),
@@ -56,7 +57,8 @@ SOLVER_DESC = {
     "cg": "FP64 CG (plain method)",
     "ir": "FP32 CG + FP64 refinement (mixed precision)",
     "fpcg": "flexible CG with the learned U-Net preconditioner, FP32 + FP64 refinement (graph form)",
-    "guess": "learned U-Net initial guess, then FP32 CG + FP64 refinement (mixed precision)",
+    "guess": "learned U-Net initial guess (with a warm start: the network's correction of the previous p), then "
+             "FP32 CG + FP64 refinement (mixed precision)",
 }
 
 # Algorithmic work of one pressure-CG iteration per cell (FP64, matrix-free):
@@ -96,6 +98,9 @@ def parse_args(argv=None):
     ap.add_argument("--solver", default="guess",
                     help="cg | ir | fpcg | guess (the cavity's solve path; --poisson/--batch: cg | ir | dic)")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--warm-start", choices=["auto", "on", "off"], default="auto",
+                    help="pressure solves start from the previous step's p (with --solver guess: the network "
+                         "corrects that start); auto: the workload's setting")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-studies", action="store_true",
                     help="only the headline cavity (no comparison, time-to-rtol, 64^3, precision and batch blocks)")
@@ -232,11 +237,12 @@ def physical_gpu(local):
 # ---------------------------------------------------------------------------
 # oracle timing (CPU baseline / reference arm): runs in child processes
 # ---------------------------------------------------------------------------
-# FP64 CG iterations per pressure solve of the 384^3 cavity (nu 1e-3, dt
-# 1e-2, the seeded perturbation), measured on the GPU with the same method and
-# stopping rule as the oracle's CG: used to scale the oracle's sampled cost
-# per CG iteration to a whole step when no measurement of this run is at hand
-CG_ITERS_PER_STEP = {384: 1914}
+# CG iterations per pressure solve of the 384^3 cavity (nu 1e-3, dt 1e-2, the
+# seeded perturbation), cold and warm-started, measured on the GPU with the
+# stopping rule of the oracle's CG (cold: FP64 CG; warm: the FP32/FP64 solve,
+# which takes CG's iterates): used to scale the oracle's sampled cost per CG
+# iteration to a whole step when no measurement of this run is at hand
+CG_ITERS_PER_STEP = {(384, False): 1914, (384, True): 1716}
 
 
 def oracle_sample_main(args):
@@ -366,7 +372,7 @@ def main_reference(args):
     if rank != 0:
         return 0
     wl = WORKLOADS[args.workload]
-    full = CG_ITERS_PER_STEP.get(wl["n"], 0)
+    full = CG_ITERS_PER_STEP.get((wl["n"], wl.get("warm_start", False)), 0)
     res = collect_oracle(run_oracle_child(args.workload, args.steps, args.warmup, args.max_seconds, sample_n=64,
                                           sample_iters=40, full_iters=full))
     value = res["value"]
@@ -391,12 +397,12 @@ def weights_path():
     return os.path.join(ROOT, "paper_2504_03697_gb300", "weights", "unet_cavity128.f32")
 
 
-def make_cavity(cfd, n, wl, solver, device, params=None, advect_order=1):
+def make_cavity(cfd, n, wl, solver, device, params=None, advect_order=1, warm_start=False):
     """A cavity of the workload with one of the solver paths: 'cg' (FP64 CG),
     'ir' (FP32 CG + FP64 refinement), 'fpcg' (flexible CG with the learned
     U-Net, mixed precision, graph form), 'guess' (IR from the learned initial
     guess).  Returns (cavity, network or None)."""
-    kw = dict(dt=wl["dt"], nu=wl["nu"], lid_u=wl["lid_u"], advect_order=advect_order)
+    kw = dict(dt=wl["dt"], nu=wl["nu"], lid_u=wl["lid_u"], advect_order=advect_order, warm_start=warm_start)
     if solver == "guess":
         prm = cfd.make_params(n, n, n, solver="ir", learned_guess=True, **kw)
     else:
@@ -432,11 +438,11 @@ def timed_steps(cav, steps, stream, device, flush=None):
     return [a.elapsed_time(b) for a, b in ev]
 
 
-def cavity_sample(cfd, n, wl, solver, steps, warmup, device, params=None):
+def cavity_sample(cfd, n, wl, solver, steps, warmup, device, params=None, warm_start=False):
     """Cell-steps/s of the workload's cavity with another solver path, on a
     sample of steps (warm-up steps first); returns a summary dict."""
     import torch
-    cav, net = make_cavity(cfd, n, wl, solver, device, params)
+    cav, net = make_cavity(cfd, n, wl, solver, device, params, warm_start=warm_start)
     init_fields(cav, n, wl)
     if solver in ("cg", "ir"):
         cav.autotune(iters=30)
@@ -448,7 +454,8 @@ def cavity_sample(cfd, n, wl, solver, steps, warmup, device, params=None):
     cav.enable_timing(False)
     ph = cav.phase_times()
     rc, st = cav.recent_stats(steps)
-    out = {"solver": solver, "steps_timed": steps, "warmup": warmup, "ms_per_step": sum(ms) / steps,
+    out = {"solver": solver, "warm_start": warm_start, "steps_timed": steps, "warmup": warmup,
+           "ms_per_step": sum(ms) / steps,
            "cell_steps_per_s": n ** 3 * steps / (sum(ms) / 1e3),
            "pressure_ms_per_step": ph["pcg"][0] / steps, "diffuse_ms_per_step": ph["diffuse"][0] / steps,
            "pressure_iters": [s["iters"] for s in st], "refinements": [s["outer_iters"] for s in st],
@@ -505,6 +512,7 @@ def main_ours(args):
     n = wl["n"]
     cells = n ** 3
     solver = args.solver
+    warm = wl.get("warm_start", False) if args.warm_start == "auto" else args.warm_start == "on"
     params = None
     if solver in ("fpcg", "guess"):
         from paper_2504_03697_gb300 import learned
@@ -513,7 +521,7 @@ def main_ours(args):
             raise RuntimeError(f"{path} is missing: the learned solvers need the trained U-Net parameters")
         params = learned.load_params(path)
     stream = torch.cuda.current_stream(device)
-    cav, net = make_cavity(cfd, n, wl, solver, device, params, args.advect_order)
+    cav, net = make_cavity(cfd, n, wl, solver, device, params, args.advect_order, warm)
     init_fields(cav, n, wl, rank)
     cav.set_cg_variant(args.cg_variant) if solver == "cg" else None
     if args.concurrent_diffusion == "off" and solver in ("cg", "jacobi"):
@@ -618,9 +626,10 @@ def main_ours(args):
     if rank == 0 and world == 1 and not args.no_studies:
         # the same cavity with the other solver paths (samples of steps)
         extra["same_cavity"] = {}
-        for other, k_steps, warm in (("cg", 2, 1), ("ir", 4, 1)):
+        for other, k_steps, warm_steps in (("cg", 2, 1), ("ir", 4, 1)):
             if other != solver:
-                extra["same_cavity"][other] = cavity_sample(cfd, n, wl, other, k_steps, warm, device, params)
+                extra["same_cavity"][other] = cavity_sample(cfd, n, wl, other, k_steps, warm_steps, device, params,
+                                                            warm_start=warm)
         extra["same_cavity"]["note"] = (f"samples of {wl['steps_total']} steps: FP64 CG 2 timed steps after 1, IR 4 "
                                         f"after 1; flexible CG with the network in every iteration is timed on "
                                         f"standalone systems only (time_to_rtol), since one application of the "
@@ -645,7 +654,7 @@ def main_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        full = CG_ITERS_PER_STEP.get(n, 0)
+        full = CG_ITERS_PER_STEP.get((n, warm), 0)
         cgs = extra.get("same_cavity", {}).get("cg")
         if cgs:
             full = int(round(float(np.mean(cgs["pressure_iters"]))))
@@ -664,7 +673,7 @@ def main_ours(args):
                            else "flushed between timed steps (256 MiB write outside the timed events)",
                            "solver_shape": tune if tune is not None else "automatic",
                            "weights": os.path.relpath(args.unet_weights or weights_path(), ROOT) if params is not None
-                           else None, "advect_order": args.advect_order},
+                           else None, "advect_order": args.advect_order, "warm_start": warm},
                 "solve": {"pcg_iters_mean": mean_iters, "pcg_iters_min": min(iters), "pcg_iters_max": max(iters),
                           "time_to_rtol_ms_mean": pcg_avg_s * 1e3, "rel_resid_max": worst_resid,
                           "all_converged": bool(ok), "refinements": [s["outer_iters"] for s in stats]},

@@ -133,8 +133,10 @@ typedef struct {
                                starts from x0 = alpha M(b), M the network
                                (cfd_unet_apply) and alpha = M(b).b / M(b).A M(b),
                                the multiple of M(b) of least energy-norm error;
-                               graph form of the IR solve only; 0: cold start
-                               (or warm start)                                   */
+                               with warm_start = 1 the network corrects the
+                               warm start instead: x0 = x + alpha M(r), r =
+                               b - A x, alpha = M(r).r / M(r).A M(r); graph form
+                               of the IR solve only; 0: cold (or warm) start    */
   int32_t reserved[6];      /* must be zero                                       */
 } cfd_params;
 

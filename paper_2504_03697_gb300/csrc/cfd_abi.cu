@@ -523,7 +523,7 @@ int run_pressure(cfd_handle* h, double* x, int zero_x0, int gauge, DevSolveStats
     a.net = h->precond_net;
     a.net_mode = nv.conv_mode;
     a.guess = 1;
-    (void)zero_x0;  // the guess replaces both the cold and the warm start
+    a.guess_warm = zero_x0 ? 0 : 1;  // warm start: the network corrects the starting x
     if (!ir_graph_eligible(a)) return set_err(h, CFD_ERR_INVALID_ARG, "learned_guess needs nx %% 4 == 0");
     const int t = phase_begin(h, CFD_PHASE_PCG);
     rc = cuda_check(h, launch_ir_graph(a, h->irg_state, &h->irg, h->stream), "IR graph launch");

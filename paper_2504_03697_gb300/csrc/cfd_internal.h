@@ -115,6 +115,7 @@ struct IrArgs {
   int net_mode;     // the network's convolution mode when the graph was built
   int flexible;
   int guess;
+  int guess_warm;   // guess: correct the starting x (warm start) instead of replacing it
   int stagnation;
   CUtensorMap map_r32;
   CUtensorMap map_p0;

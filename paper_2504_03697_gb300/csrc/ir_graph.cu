@@ -138,6 +138,7 @@ struct GArgs {
   const int* net_err;     // set by a timed-out tensor-core wait of the network
   int net_kernels;        // kernels of one network application
   int stagnation;         // flexible CG: iterations without halving |r| before plain CG
+  int gwarm;              // learned guess corrects the starting x (source r = b' - A x) instead of replacing it
   cudaGraphConditionalHandle h_net;
 };
 
@@ -370,7 +371,10 @@ __device__ __forceinline__ void march_f32(const GArgs& a, F4 P4, F1 P1, E emit) 
     size_t c4 = (size_t(k0) * my + j) * nx4 + (on ? i4 : nx4 - 1);  // idle lanes shadow the last column
     float4 pc = P4(c4);
     float4 pm = k0 > 0 ? P4(c4 - sz4) : pc;
-    auto plane = [&](int k) {
+#pragma unroll
+    for (int kk = 0; kk < kZ32; ++kk) {
+      const int k = k0 + kk;
+      if (k >= mz) break;
       const float4 pp = k < mz - 1 ? P4(c4 + sz4) : pc;
       const float4 ps = j > 0 ? P4(c4 - sy4) : pc;
       const float4 pn = j < my - 1 ? P4(c4 + sy4) : pc;
@@ -398,14 +402,6 @@ __device__ __forceinline__ void march_f32(const GArgs& a, F4 P4, F1 P1, E emit) 
       pm = pc;
       pc = pp;
       c4 += sz4;
-    };
-    // whole work items as straight-line code (the loads of later planes can
-    // be issued early); the last, partial item of a column plane by plane
-    if (k0 + kZ32 <= mz) {
-#pragma unroll
-      for (int kk = 0; kk < kZ32; ++kk) plane(k0 + kk);
-    } else {
-      for (int k = k0; k < mz; ++k) plane(k);
     }
   }
 }
@@ -433,7 +429,10 @@ __device__ __forceinline__ double edge_pass(const GArgs& a, F4 P4, F1 P1, float4
     const bool has_e = i4 + 1 < nx4;
     size_t c4 = (size_t(k0) * my + j) * nx4 + (on ? i4 : nx4 - 1);  // idle lanes shadow the last column
     float4 pc = P4(c4);
-    auto plane = [&](int k) {
+#pragma unroll
+    for (int kk = 0; kk < kZ32; ++kk) {
+      const int k = k0 + kk;
+      if (k >= mz) break;
       const bool up = k < mz - 1;
       const float4 pp = up ? P4(c4 + sz4) : pc;
       const float4 pn = j < my - 1 ? P4(c4 + sy4) : pc;
@@ -451,12 +450,6 @@ __device__ __forceinline__ double edge_pass(const GArgs& a, F4 P4, F1 P1, float4
       }
       pc = pp;
       c4 += sz4;
-    };
-    if (k0 + kZ32 <= mz) {
-#pragma unroll
-      for (int kk = 0; kk < kZ32; ++kk) plane(k0 + kk);
-    } else {
-      for (int k = k0; k < mz; ++k) plane(k);
     }
   }
   return acc;
@@ -939,15 +932,54 @@ __global__ void __launch_bounds__(kGThreads) g_gsum(const GArgs a) {
   S->kernels += a.net_kernels;
 }
 
+// warm form: the source of the guess is the residual of the starting x,
+// r = (b - mean b) - A x in FP64 (into a.r), and its scale s = sqrt(V / |r|^2)
+__global__ void __launch_bounds__(kGThreads) g_gres(const GArgs a) {
+  GState* S = a.S;
+  count_kernel(S);
+  const int mx = a.mx, my = a.my, mz = a.mz;
+  const size_t sy = size_t(mx), sz = size_t(mx) * my;
+  const double mean = S->gmean;
+  double sr = 0.0;
+  const int items = a.w64x * a.w64y * a.w64z;
+  for (int w = blockIdx.x; w < items; w += gridDim.x) {
+    const int wx = w % a.w64x, wy = (w / a.w64x) % a.w64y, wz = w / (a.w64x * a.w64y);
+    const int i = wx * 32 + threadIdx.x, j = wy * 8 + threadIdx.y, k0 = wz * kZ64;
+    if (i >= mx || j >= my) continue;
+    const int k1 = min(k0 + kZ64, mz);
+    size_t c = (size_t(k0) * my + j) * mx + i;
+    double xc = a.x[c];
+    double xm = k0 > 0 ? a.x[c - sz] : xc;
+    for (int k = k0; k < k1; ++k, c += sz) {
+      const double xp = k < mz - 1 ? a.x[c + sz] : xc;
+      const double xw = i > 0 ? a.x[c - 1] : xc;
+      const double xe = i < mx - 1 ? a.x[c + 1] : xc;
+      const double xs = j > 0 ? a.x[c - sy] : xc;
+      const double xn = j < my - 1 ? a.x[c + sy] : xc;
+      const double ax = stencil_row<double>(kOpPressure, 0.0, i, j, k, mx, my, mz, xc, xw, xe, xs, xn, xm, xp);
+      const double rv = (a.b[c] - mean) - ax;
+      a.r[c] = rv;
+      sr = fma(rv, rv, sr);
+      xm = xc;
+      xc = xp;
+    }
+  }
+  double v[1] = {sr}, o[1];
+  if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
+  S->gmean = 0.0;  // the residual has zero sum (b - mean b is zero-mean, A kills constants)
+  S->gscale = o[0] > 0.0 && isfinite(o[0]) ? sqrt(double(a.n) / o[0]) : 0.0;
+}
+
 __global__ void __launch_bounds__(kGThreads) g_gnorm(const GArgs a) {
   GState* S = a.S;
   count_kernel(S);
   const double mean = S->gmean, sc = S->gscale;
+  const double* src = a.gwarm ? a.r : a.b;
   uint2* x2 = reinterpret_cast<uint2*>(a.net_in);
   for (size_t e = vtid(); e < a.n / 4; e += vstride()) {
     const size_t c = 4 * e;
-    x2[e] = make_uint2(bf16x2_bits(float((a.b[c] - mean) * sc), float((a.b[c + 1] - mean) * sc)),
-                       bf16x2_bits(float((a.b[c + 2] - mean) * sc), float((a.b[c + 3] - mean) * sc)));
+    x2[e] = make_uint2(bf16x2_bits(float((src[c] - mean) * sc), float((src[c + 1] - mean) * sc)),
+                       bf16x2_bits(float((src[c + 2] - mean) * sc), float((src[c + 3] - mean) * sc)));
   }
 }
 
@@ -960,12 +992,13 @@ __global__ void __launch_bounds__(kGThreads) g_gdots(const GArgs a) {
   const int mx = a.mx, my = a.my, mz = a.mz;
   const size_t sy = size_t(mx), sz = size_t(mx) * my;
   const double mean = S->gmean;
+  const double* src = a.gwarm ? a.r : a.b;
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
   for (size_t c = vtid(); c < a.n; c += vstride()) {
     const int i = int(c % sy), j = int((c / sy) % my), k = int(c / sz);
     const double zc = double(a.net_out[c]);
     s0 += zc;
-    s1 = fma(zc, a.b[c] - mean, s1);
+    s1 = fma(zc, src[c] - mean, s1);
     if (i < mx - 1) { const double d = zc - double(a.net_out[c + 1]); s2 = fma(d, d, s2); }
     if (j < my - 1) { const double d = zc - double(a.net_out[c + sy]); s2 = fma(d, d, s2); }
     if (k < mz - 1) { const double d = zc - double(a.net_out[c + sz]); s2 = fma(d, d, s2); }
@@ -983,7 +1016,10 @@ __global__ void __launch_bounds__(kGThreads) g_gset(const GArgs a) {
   GState* S = a.S;
   count_kernel(S);
   const double al = S->galpha, zm = S->gzmean;
-  for (size_t e = vtid(); e < a.n; e += vstride()) a.x[e] = al * (double(a.net_out[e]) - zm);
+  if (a.gwarm)
+    for (size_t e = vtid(); e < a.n; e += vstride()) a.x[e] += al * (double(a.net_out[e]) - zm);
+  else
+    for (size_t e = vtid(); e < a.n; e += vstride()) a.x[e] = al * (double(a.net_out[e]) - zm);
 }
 
 // ---------------------------------------------------------------------------
@@ -1045,7 +1081,8 @@ bool same_args(const IrArgs& x, const IrArgs& y) {
          x.zero_x0 == y.zero_x0 && x.remove_mean == y.remove_mean && x.gauge == y.gauge &&
          x.gauge_value == y.gauge_value && x.rtol == y.rtol && x.delta == y.delta && x.max_iters == y.max_iters &&
          x.max_outer == y.max_outer && x.kind == y.kind && x.c == y.c && x.net == y.net &&
-         x.net_mode == y.net_mode && x.flexible == y.flexible && x.guess == y.guess && x.stagnation == y.stagnation;
+         x.net_mode == y.net_mode && x.flexible == y.flexible && x.guess == y.guess && x.stagnation == y.stagnation &&
+         x.guess_warm == y.guess_warm;
 }
 
 }  // namespace
@@ -1139,6 +1176,7 @@ cudaError_t build(IrGraph* G, const IrArgs& ia, void* state_buf) {
     a.net_out = nv.z;
     a.net_err = nv.err;
     a.stagnation = ia.stagnation > 0 ? ia.stagnation : 50;
+    a.gwarm = guess && ia.guess_warm ? 1 : 0;
   }
   return build_graph(G, ia, a, vec, items32, items64, vec_work, tile, flat, flexible, guess);
 }
@@ -1205,10 +1243,16 @@ cudaError_t build_graph(IrGraph* G, const IrArgs& ia, GArgs a, bool vec, size_t 
   mp.height = 1;
   if ((e = cudaGraphAddMemsetNode(&n0, top, nullptr, 0, &mp)) != cudaSuccess) return e;
   cudaGraphNode_t pre = n0;
-  if (guess) {  // x0 = alpha (z - mean z), z = U(s (b - mean b))
-    cudaGraphNode_t g1, g2, g3, g4, g5;
+  if (guess) {  // x0 = alpha (z - mean z), z = U(s (b - mean b)); warm: x0 = x + alpha z~, z = U(s r)
+    cudaGraphNode_t g1, g1r, g2, g3, g4, g5;
     if ((e = add_kernel(top, &g1, &pre, (void*)g_gsum, wave_blocks(g_gsum, vec_work), flat, &a)) != cudaSuccess)
       return e;
+    if (a.gwarm) {
+      if ((e = add_kernel(top, &g1r, &g1, (void*)g_gres, wave_blocks(g_gres, size_t(a.w64x) * a.w64y * a.w64z),
+                          dim3(32, 8), &a)) != cudaSuccess)
+        return e;
+      g1 = g1r;
+    }
     if ((e = add_kernel(top, &g2, &g1, (void*)g_gnorm, wave_blocks(g_gnorm, vec_work), flat, &a)) != cudaSuccess)
       return e;
     if ((e = cudaGraphAddChildGraphNode(&g3, top, &g2, 1, netg)) != cudaSuccess) return e;

@@ -18,7 +18,7 @@ def test_default_workload_and_contract_arguments():
 def test_oracle_sample_scaling_is_stated():
     # the reference arm scales a sampled oracle step by the FP64 CG count
     # measured at 384^3
-    assert bench.CG_ITERS_PER_STEP[384] > 1000
+    assert bench.CG_ITERS_PER_STEP[(384, False)] > bench.CG_ITERS_PER_STEP[(384, True)] > 1000
     assert bench.FP64_PEAK_TFLOPS > 1.0 and "clocks" in bench.FP64_PEAK_SOURCE
 
 

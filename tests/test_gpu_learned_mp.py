@@ -249,6 +249,37 @@ def test_learned_guess_cavity_steps_match_oracle_per_step(cfd):
         print(f"learned guess cavity step {k}: {st[0]['iters']} it; max-abs {errs}, {fv:.2e} / {fp:.2e} of the bound")
 
 
+def test_learned_correction_of_the_warm_start(cfd):
+    """learned_guess with warm_start: the network corrects the previous
+    pressure (x0 = x + alpha M(b - A x)).  A zero network leaves the warm
+    start as it is (the solve is bitwise the plain warm-started IR graph
+    solve); cavity steps with the pass-through network against the oracle
+    per step."""
+    shape = (24, 20, 16)
+    nx, ny, nz = shape
+    b = torch.tensor(gaussian_rhs(nx, ny, nz, seed=46), device="cuda")
+    x_start = torch.tensor(gaussian_rhs(nx, ny, nz, seed=47), device="cuda") * 0.01
+    cav = guess_cavity(cfd, shape, torch.zeros(ou.param_count()), warm_start=True)
+    x1 = x_start.clone()
+    rc, s1 = cav.solve_pressure(b, x1)
+    ref = cfd.Cavity(cfd.make_params(*shape, solver="ir", warm_start=True))
+    ref.set_ir_form("graph")
+    x2 = x_start.clone()
+    rc2, s2 = ref.solve_pressure(b, x2)
+    assert rc == rc2 == cfd.CFD_OK
+    assert s1["iters"] == s2["iters"] and torch.equal(x1, x2)
+    cav = guess_cavity(cfd, (16, 16, 16), passthrough_params(4.0, 4.0), dt=0.01, nu=0.01, lid_u=1.0, warm_start=True)
+    ocav = OCav(16, 16, 16, dt=0.01, nu=0.01, lid_u=1.0)
+    for name, f in zip("uvw", cavity_perturbation(16, 16, 16, seed=7, amp=1e-3)):
+        cav.set_field(name, f)
+    for k in range(3):
+        start = read_state(cav)
+        rc, st = cav.step(1)
+        assert rc == cfd.CFD_OK, st
+        errs, fv, fp = check_step_against_oracle(ocav, start, read_state(cav), st[0], f"warm guess step {k}")
+        print(f"learned correction of the warm start, step {k}: {st[0]['iters']} it; {fv:.2e} / {fp:.2e} of the bound")
+
+
 def test_learned_paths_argument_checks(cfd):
     with pytest.raises(cfd.CfdError):
         cfd.Cavity(cfd.make_params(16, 16, 16, solver="cg", learned_guess=True))
