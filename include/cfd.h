@@ -577,6 +577,17 @@ int cfd_unet_set_loss(cfd_unet *u, int kind);
 enum { CFD_UNET_CONV_REGISTERS = 0, CFD_UNET_CONV_BULK = 1, CFD_UNET_CONV_TWO_STAGE = 2 };
 int cfd_unet_set_conv_mode(cfd_unet *u, int mode);
 
+/* Where the weight gradients of cfd_unet_train_step run:
+ *   TENSOR      (default) the 3x3x3 layers L0b..L0c on the tensor cores (BF16
+ *               operands, FP32 accumulation in tensor memory): per tap a
+ *               contraction over the voxels, each CTA summing its boxes,
+ *               then a fixed-order sum over the CTAs (bitwise repeatable);
+ *               the first layer (one input channel) and the head (one output
+ *               channel) on the CUDA cores;
+ *   CUDA_CORES  every layer as FP32 sums on the CUDA cores (for comparison). */
+enum { CFD_UNET_WGRAD_TENSOR = 0, CFD_UNET_WGRAD_CUDA_CORES = 1 };
+int cfd_unet_set_wgrad_mode(cfd_unet *u, int mode);
+
 /* Tensor read-back for checks (synchronous).  which in 0..25: the BF16
  * tensors (octet planes) xin, a0, s0, p0, a1, s1, p1, a2, s2, u1, d1, u0, d0
  * (activations of the last forward pass) and gz, g_d0, g_s0, g_u0, g_d1,

@@ -142,6 +142,7 @@ def load_library(path: Optional[str] = None):
         "cfd_unet_read_tensor": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int64]),
         "cfd_unet_set_loss": (ctypes.c_int, [vp, ctypes.c_int]),
         "cfd_unet_set_conv_mode": (ctypes.c_int, [vp, ctypes.c_int]),
+        "cfd_unet_set_wgrad_mode": (ctypes.c_int, [vp, ctypes.c_int]),
         "cfd_unet_fpcg_solve": (ctypes.c_int, [vp, vp, vp, ctypes.c_double, ctypes.c_int32, P(cfd_solve_stats)]),
         "cfd_unet_launch_count": (ctypes.c_int64, [vp]),
         "cfd_unet_grid": (ctypes.c_int, [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]),
@@ -561,6 +562,11 @@ class UNet:
     def set_conv_mode(self, mode: str):
         """'registers', 'bulk' (default) or 'two_stage' (cfd_unet_set_conv_mode)."""
         self._check(self.lib.cfd_unet_set_conv_mode(self.u, {"registers": 0, "bulk": 1, "two_stage": 2}[mode]))
+
+    def set_wgrad_mode(self, mode: str):
+        """'tensor' (default: the 3x3x3 layers' weight gradients on the tensor
+        cores) or 'cuda_cores' (cfd_unet_set_wgrad_mode)."""
+        self._check(self.lib.cfd_unet_set_wgrad_mode(self.u, {"tensor": 0, "cuda_cores": 1}[mode]))
 
     def read_tensor(self, which) -> torch.Tensor:
         """Host copy of a model tensor: a name from UNET_TENSORS (BF16,

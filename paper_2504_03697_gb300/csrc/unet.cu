@@ -702,6 +702,252 @@ cudaError_t launch_tile(const ConvArgs& a, cudaStream_t s, bool& taken) {
 
 }  // namespace
 
+namespace {
+
+// ---------------------------------------------------------------------------
+// Weight gradient of a stride-1 3x3x3 convolution on the tensor cores:
+//   dW[t][co][ci] = sum over voxels v of g[v][co] in[v + s_t][ci],
+// a contraction over K = voxels for each tap t (zero input outside the grid).
+//
+// A CTA stages an output box of g and the same box of the input, both with a
+// one-voxel halo (TMA, zero fill outside the grid), as 8-channel planes:
+// voxel row r = (z by + y) bx + x of the box holds 8 channels in 16 bytes, so
+// 8 consecutive rows of one plane are an MN-major core matrix (8 K-rows of
+// 8 MN-elements), the next 8 rows the next core matrix along K (128 bytes on)
+// and the next plane the next core matrix along M or N (one plane on).  The
+// 16 interior voxels of an x-line are the K = 16 block of one MMA; tap t
+// reads the input rows shifted by its row offset (the descriptor start), as
+// in the forward kernel.  M = 128 covers the operand with more channels
+// (its unused M-groups read staged shared memory and are discarded), N the
+// other channel count.  Each CTA accumulates its taps in TMEM over all its
+// boxes and writes FP32 partial sums [chunk][tap][cout][cin] (and the bias
+// gradient, the sum of g, from the staged boxes); a fixed-order reduction
+// over the chunks follows, so the result does not depend on scheduling.
+// ---------------------------------------------------------------------------
+constexpr int kWgThreads = 128;
+constexpr int kWgSlots = 16;               // planes staged: the A operand's 16 M-groups of 8 channels
+constexpr int kWgXc = 16;                  // interior voxels per x-line of a box (one K block)
+constexpr int kWgSmemMax = 208 * 1024;
+
+struct WgradTcArgs {
+  CUtensorMap map_g;   // g [V][cout] octet planes, box {8, bx, by, bz}
+  CUtensorMap map0;    // input src0 (c0 channels)
+  CUtensorMap map1;    // input src1 (c1 channels) or unused
+  int c0, c1, cout;
+  int bx, by, bz, ty, tz;
+  int tiles_x, tiles_y, tiles;
+  int plane;           // bytes between staged planes (128-multiple)
+  int a_in;            // 1: A = input planes (M = cin), B = g planes (N = cout); 0: the other way
+  int n_a, n_b;        // planes of A and B
+  int taps_per_group;
+  int chunks;
+  float* partial;      // [chunks][27][cout][cin]
+  float* bias_partial; // [chunks][cout]
+  int* err;
+};
+
+template <int N>
+__global__ void __launch_bounds__(kWgThreads) wgrad_tc_kernel(const __grid_constant__ WgradTcArgs a) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  __shared__ __align__(8) uint64_t bar_tma, bar_mma;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+  const int t = threadIdx.x;
+  const int chunk = blockIdx.x, group = blockIdx.y;
+  const int tap0 = group * a.taps_per_group;
+  const int ntap = min(a.taps_per_group, 27 - tap0);
+  unsigned char* A = dsm;
+  unsigned char* B = dsm + size_t(a.n_a) * a.plane;
+  unsigned char* in_planes = a.a_in ? A : B;
+  unsigned char* g_planes = a.a_in ? B : A;
+  const int cin = a.c0 + a.c1;
+  const unsigned box_bytes = unsigned(a.bx) * a.by * a.bz * 16;
+  constexpr uint32_t kCols = 512;
+
+  if (t == 0) {
+    tc::mbar_init(&bar_tma, 1);
+    tc::mbar_init(&bar_mma, 1);
+    tc::mbar_fence_init();
+    s_fail = 0;
+  }
+  if (t < 32) tc::tmem_alloc(&s_tmem, kCols);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = s_tmem;
+  // kind::f16, D FP32, A and B BF16, both MN-major (transpose bits 15, 16)
+  const uint32_t idesc = tc::idesc_bf16_f32(128, N) | (1u << 15) | (1u << 16);
+  const int row_z = a.bx * a.by;
+  float bacc = 0.f;
+  int nbox = 0;
+  bool tma_pending = false;
+  for (int box = chunk; box < a.tiles; box += a.chunks, ++nbox) {
+    const int tx = box % a.tiles_x, tyi = (box / a.tiles_x) % a.tiles_y, tzi = box / (a.tiles_x * a.tiles_y);
+    const int x0 = tx * kWgXc, y0 = tyi * a.ty, z0 = tzi * a.tz;
+    if (nbox > 0 && !tc::mbar_wait(&bar_mma, unsigned((nbox - 1) & 1), kConvWaitNs)) s_fail = 1;
+    __syncthreads();  // every thread is past the previous box (bias sums) and saw s_fail
+    if (s_fail) break;
+    if (t == 0) {
+      tc::mbar_expect_tx(&bar_tma, unsigned(a.n_a + a.n_b) * box_bytes);
+      const int p0 = a.c0 / 8;
+      for (int p = 0; p < cin / 8; ++p)
+        tc::tma_load_5d(in_planes + size_t(p) * a.plane, p < p0 ? static_cast<const void*>(&a.map0)
+                                                                : static_cast<const void*>(&a.map1),
+                        0, x0 - 1, y0 - 1, z0 - 1, p < p0 ? p : p - p0, &bar_tma);
+      for (int p = 0; p < a.cout / 8; ++p)
+        tc::tma_load_5d(g_planes + size_t(p) * a.plane, &a.map_g, 0, x0 - 1, y0 - 1, z0 - 1, p, &bar_tma);
+    }
+    tma_pending = true;
+    if (!tc::mbar_wait(&bar_tma, unsigned(nbox & 1), kConvWaitNs)) {
+      s_fail = 1;
+      break;
+    }
+    tma_pending = false;
+    tc::fence_after_sync();
+    if (group == 0 && t < a.cout) {
+      // bias gradient: g summed over the interior voxels of the box (zero
+      // outside the grid)
+      const unsigned char* gp = g_planes + size_t(t / 8) * a.plane + (t % 8) * 2;
+      for (int zb = 1; zb <= a.tz; ++zb)
+        for (int yb = 1; yb <= a.ty; ++yb) {
+          const int r0 = (zb * a.by + yb) * a.bx + 1;
+          for (int xb = 0; xb < kWgXc; ++xb)
+            bacc += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(gp + size_t(r0 + xb) * 16));
+        }
+    }
+    if (t == 0) {
+      // leading byte offset 128 (K: the next 8 voxel rows), stride byte offset
+      // one plane (M / N: the next 8 channels); starts move by whole rows
+      const uint64_t adesc0 = tc::smem_desc(tc::smem_addr(A), 128, uint32_t(a.plane));
+      const uint64_t bdesc0 = tc::smem_desc(tc::smem_addr(B), 128, uint32_t(a.plane));
+      for (int zb = 1; zb <= a.tz; ++zb) {
+        for (int yb = 1; yb <= a.ty; ++yb) {
+          const int r = (zb * a.by + yb) * a.bx + 1;  // first interior voxel of the x-line
+          const bool acc = nbox > 0 || zb > 1 || yb > 1;
+          for (int k = 0; k < ntap; ++k) {
+            const int tap = tap0 + k;
+            const int off = (tap / 9 - 1) * row_z + ((tap / 3) % 3 - 1) * a.bx + (tap % 3 - 1);
+            const int ra = a.a_in ? r + off : r, rb = a.a_in ? r : r + off;
+            tc::mma_bf16(tmem + uint32_t(k * N), adesc0 + uint64_t(ra), bdesc0 + uint64_t(rb), idesc, acc);
+          }
+        }
+      }
+      tc::mma_commit(&bar_mma);
+    }
+  }
+  __syncthreads();
+  if (!s_fail && nbox > 0 && !tc::mbar_wait(&bar_mma, unsigned((nbox - 1) & 1), kConvWaitNs)) s_fail = 1;
+  __syncthreads();
+  tc::fence_after_sync();
+  if (s_fail) {
+    if (t == 0) atomicExch(a.err, 1);
+    if (tma_pending) tc::mbar_wait(&bar_tma, unsigned(nbox & 1), kConvWaitNs);  // let a copy in flight land
+  } else {
+    const int w = t / 32;
+    const int mreal = a.a_in ? cin : a.cout;
+    for (int k = 0; k < ntap; ++k) {
+      const int tap = tap0 + k;
+#pragma unroll
+      for (int c = 0; c < N; c += 16) {
+        float v[16];
+        tc::tmem_ld16(tmem + (uint32_t(w * 32) << 16) + uint32_t(k * N + c), v);
+        if (t < mreal) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int co = a.a_in ? c + j : t, ci = a.a_in ? t : c + j;
+            a.partial[((size_t(chunk) * 27 + tap) * a.cout + co) * cin + ci] = nbox > 0 ? v[j] : 0.f;
+          }
+        }
+      }
+    }
+    if (group == 0 && t < a.cout) a.bias_partial[size_t(chunk) * a.cout + t] = bacc;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (t < 32) tc::tmem_dealloc(tmem, kCols);
+}
+
+template <int N>
+cudaError_t launch_wgrad_tc_n(const WgradTcArgs& a, unsigned groups, size_t smem, cudaStream_t s) {
+  static int configured = 0;
+  if (!configured) {
+    const cudaError_t e = cudaFuncSetAttribute(wgrad_tc_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmemMax);
+    if (e != cudaSuccess) return e;
+    configured = 1;
+  }
+  wgrad_tc_kernel<N><<<dim3(unsigned(a.chunks), groups), kWgThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_wgrad_tc(const __nv_bfloat16* src0, int c0, const __nv_bfloat16* src1, int c1,
+                            const __nv_bfloat16* g, int cout, int nx, int ny, int nz, float* partial,
+                            float* bias_partial, int max_chunks, int* chunks_out, int* err, cudaStream_t s) {
+  const int cin = c0 + c1;
+  if (c0 % 8 || c1 % 8 || cout % 8 || cin < 16 || cout < 16 || cin > 128 || cout > 128 || (c1 > 0 && !src1) ||
+      max_chunks < 1)
+    return cudaErrorNotSupported;
+  WgradTcArgs a{};
+  a.c0 = c0;
+  a.c1 = c1;
+  a.cout = cout;
+  a.a_in = cin >= cout ? 1 : 0;
+  const int n = a.a_in ? cout : cin;
+  if (n != 16 && n != 32 && n != 64) return cudaErrorNotSupported;
+  a.n_a = (a.a_in ? cin : cout) / 8;
+  a.n_b = n / 8;
+  if (a.n_a + a.n_b > kWgSlots) return cudaErrorNotSupported;
+  // box: 16 interior columns, ty x tz interior lines; the 16 staged planes
+  // must fit in shared memory; most interior voxels per staged voxel
+  a.bx = kWgXc + 2;
+  int best_ty = 1, best_tz = 1;
+  double best = -1.0;
+  for (int tz = 1; tz <= 8; ++tz)
+    for (int ty = 1; ty <= 8; ++ty) {
+      if (ty > ny || tz > nz) continue;
+      const int rows = a.bx * (ty + 2) * (tz + 2);
+      const size_t plane = size_t(rows * 16 + 127) / 128 * 128;
+      if (plane * kWgSlots > size_t(kWgSmemMax)) continue;
+      const double eff = double(ty * tz) / double((ty + 2) * (tz + 2));
+      if (eff > best + 1e-12) {
+        best = eff;
+        best_ty = ty;
+        best_tz = tz;
+      }
+    }
+  if (best < 0) return cudaErrorNotSupported;
+  a.ty = best_ty;
+  a.tz = best_tz;
+  a.by = a.ty + 2;
+  a.bz = a.tz + 2;
+  a.plane = (a.bx * a.by * a.bz * 16 + 127) / 128 * 128;
+  a.tiles_x = (nx + kWgXc - 1) / kWgXc;
+  a.tiles_y = (ny + a.ty - 1) / a.ty;
+  a.tiles = a.tiles_x * a.tiles_y * ((nz + a.tz - 1) / a.tz);
+  if (!encode_oct_map(&a.map_g, g, cout, nx, ny, nz, a.bx, a.by, a.bz)) return cudaErrorNotSupported;
+  if (!encode_oct_map(&a.map0, src0, c0, nx, ny, nz, a.bx, a.by, a.bz)) return cudaErrorNotSupported;
+  if (c1 > 0 && !encode_oct_map(&a.map1, src1, c1, nx, ny, nz, a.bx, a.by, a.bz)) return cudaErrorNotSupported;
+  a.taps_per_group = std::min(27, 512 / n);
+  const int groups = (27 + a.taps_per_group - 1) / a.taps_per_group;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  a.chunks = std::max(1, std::min({a.tiles, max_chunks, std::max(1, sms / groups)}));
+  a.partial = partial;
+  a.bias_partial = bias_partial;
+  a.err = err;
+  const size_t smem = size_t(a.plane) * kWgSlots;
+  cudaError_t e;
+  switch (n) {
+    case 16: e = launch_wgrad_tc_n<16>(a, unsigned(groups), smem, s); break;
+    case 32: e = launch_wgrad_tc_n<32>(a, unsigned(groups), smem, s); break;
+    default: e = launch_wgrad_tc_n<64>(a, unsigned(groups), smem, s); break;
+  }
+  if (e == cudaSuccess && chunks_out) *chunks_out = a.chunks;
+  return e;
+}
+
 bool conv3d_tile_eligible(const ConvArgs& a) {
   return a.ks == 3 && !a.packed && a.c0 % 16 == 0 && a.c1 % 16 == 0 && !a.dst_f32 && a.cout % 8 == 0 &&
          a.split % 8 == 0 && !(reinterpret_cast<uintptr_t>(a.w) & 15) && !(reinterpret_cast<uintptr_t>(a.dst0) & 15) &&

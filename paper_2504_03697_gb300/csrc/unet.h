@@ -60,6 +60,18 @@ bool unet_view(const cfd_unet* u, UNetView* v);
 // number of kernels it launched.  Returns CFD_OK or a CFD_ERR_* code.
 int unet_forward_on(cfd_unet* u, cudaStream_t s, int* kernels);
 
+// Weight gradient of a stride-1 3x3x3 convolution (input src0 with c0
+// channels, then src1 with c1, octet planes; output gradient g with cout
+// channels) on the tensor cores: FP32 partial sums partial[chunk][27][cout]
+// [cin] and bias_partial[chunk][cout] for *chunks_out <= max_chunks chunks,
+// to be summed over the chunks in order.  Returns cudaErrorNotSupported (and
+// launches nothing) when the layer does not fit: channel counts not
+// multiples of 8 or outside [16, 128], the smaller of cin and cout not 16,
+// 32 or 64, or no tensor-map encoder.  err: set to 1 if a wait timed out.
+cudaError_t launch_wgrad_tc(const __nv_bfloat16* src0, int c0, const __nv_bfloat16* src1, int c1,
+                            const __nv_bfloat16* g, int cout, int nx, int ny, int nz, float* partial,
+                            float* bias_partial, int max_chunks, int* chunks_out, int* err, cudaStream_t s);
+
 // Launch the convolution: the TMA-tiled kernel for 3x3x3 layers whose
 // sources have 16k channels (see conv3d_tile_eligible), else the gathering
 // kernel.

@@ -64,6 +64,7 @@ int taps_of(int ks) { return ks * ks * ks; }
 
 constexpr int kThreads = 256;
 constexpr int kWgradChunks = 32;
+constexpr int kWgradTcChunks = 160;  // partial-sum rows of the tensor-core weight gradient (>= the SM count)
 
 __device__ __forceinline__ size_t gtid() { return size_t(blockIdx.x) * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ size_t gstride() { return size_t(gridDim.x) * blockDim.x; }
@@ -787,6 +788,7 @@ struct cfd_unet {
   __nv_bfloat16 *gz, *g_d0, *g_s0, *g_u0, *g_d1, *g_s1, *g_u1, *g_s2, *g_a2, *g_p1, *g_a1, *g_p0, *g_a0;
   // scratch
   float *wpart, *bpart;
+  float *wtc, *btc;  // partial sums of the tensor-core weight gradient
   double *parts, *scale, *lossp;
   int* err;
   // flexible CG vectors and scalars
@@ -796,6 +798,7 @@ struct cfd_unet {
   __nv_bfloat16* tens[26];
   size_t tens_count[26];
   int loss_kind;  // CFD_UNET_LOSS_*
+  int wgrad_mode; // CFD_UNET_WGRAD_*
   int conv_mode;  // CFD_UNET_CONV_*: how the tiled convolutions stage weights and inputs
   int adam_t;
   int64_t launches;
@@ -876,6 +879,8 @@ size_t carve(cfd_unet* u, int nx, int ny, int nz, char* base) {
   for (const auto& L : kLayers) maxp = std::max(maxp, size_t(taps_of(L.ks)) * L.cout * (L.c0 + L.c1));
   float* wpart = reinterpret_cast<float*>(take(size_t(kWgradChunks) * maxp * 4));
   float* bpart = reinterpret_cast<float*>(take(size_t(kWgradChunks) * 64 * 4));
+  float* wtc = reinterpret_cast<float*>(take(size_t(kWgradTcChunks) * maxp * 4));
+  float* btc = reinterpret_cast<float*>(take(size_t(kWgradTcChunks) * 64 * 4));
   double* parts = reinterpret_cast<double*>(take(size_t(152 * 8) * 8));
   double* scale = reinterpret_cast<double*>(take(64));
   double* lossp = reinterpret_cast<double*>(take(size_t(3 * 152 * 8) * 8));
@@ -901,7 +906,8 @@ size_t carve(cfd_unet* u, int nx, int ny, int nz, char* base) {
     u->gz = bufs[13]; u->g_d0 = bufs[14]; u->g_s0 = bufs[15]; u->g_u0 = bufs[16]; u->g_d1 = bufs[17];
     u->g_s1 = bufs[18]; u->g_u1 = bufs[19]; u->g_s2 = bufs[20]; u->g_a2 = bufs[21]; u->g_p1 = bufs[22];
     u->g_a1 = bufs[23]; u->g_p0 = bufs[24]; u->g_a0 = bufs[25];
-    u->z = z; u->tgt = tgt; u->wpart = wpart; u->bpart = bpart; u->parts = parts; u->scale = scale;
+    u->z = z; u->tgt = tgt; u->wpart = wpart; u->bpart = bpart; u->wtc = wtc; u->btc = btc;
+    u->parts = parts; u->scale = scale;
     u->lossp = lossp; u->err = err;
     size_t o = 0;
     for (int l = 0; l < kNumLayers; ++l) {
@@ -982,6 +988,21 @@ int conv_dgrad(cfd_unet* u, int layer, int slice, const __nv_bfloat16* gout, int
 
 int wgrad(cfd_unet* u, int layer, const __nv_bfloat16* src0, const __nv_bfloat16* src1, const __nv_bfloat16* gout) {
   const LayerSpec& L = kLayers[layer];
+  if (u->wgrad_mode == CFD_UNET_WGRAD_TENSOR && L.ks == 3 && !L.packed) {
+    // the 3x3x3 layers with 16-channel multiples: tensor cores
+    int fx, fy, fz, chunks = 0;
+    level_dims(u, L.level, fx, fy, fz);
+    const cudaError_t e = launch_wgrad_tc(src0, L.c0, src1, L.c1, gout, L.cout, fx, fy, fz, u->wtc, u->btc,
+                                          kWgradTcChunks, &chunks, u->err, u->stream);
+    if (e == cudaSuccess) {
+      ++u->launches;
+      const size_t n = size_t(27) * L.cout * (L.c0 + L.c1);
+      wgrad_reduce_kernel<<<grid_for(n), kThreads, 0, u->stream>>>(u->wtc, u->btc, chunks, n, L.cout,
+                                                                   u->g + u->woff[layer], u->g + u->boff[layer]);
+      return klaunch(u, "wgrad reduce");
+    }
+    if (e != cudaErrorNotSupported) return uck(u, e, "tensor-core weight gradient");
+  }
   WgradArgs a{};
   level_dims(u, L.level, a.nx, a.ny, a.nz);
   a.src0 = src0; a.c0 = L.c0; a.src1 = src1; a.c1 = L.c1; a.ks = L.ks;
@@ -1322,6 +1343,13 @@ int cfd_unet_set_conv_mode(cfd_unet* u, int mode) {
   if (!u || mode < CFD_UNET_CONV_REGISTERS || mode > CFD_UNET_CONV_TWO_STAGE)
     return uerr(CFD_ERR_INVALID_ARG, "unet: NULL handle or unknown convolution mode");
   u->conv_mode = mode;
+  return CFD_OK;
+}
+
+int cfd_unet_set_wgrad_mode(cfd_unet* u, int mode) {
+  if (!u || (mode != CFD_UNET_WGRAD_TENSOR && mode != CFD_UNET_WGRAD_CUDA_CORES))
+    return uerr(CFD_ERR_INVALID_ARG, "unet: NULL handle or unknown weight-gradient mode");
+  u->wgrad_mode = mode;
   return CFD_OK;
 }
 

@@ -214,6 +214,56 @@ def test_backward_layerwise(cfd):
         check(grads[li][1], gb, 2 * (Vl / 32 + 34) * E * tb + 1e-30, f"{name} bias gradient")
 
 
+def test_tensor_core_weight_gradients_match_cuda_cores_and_repeat(cfd):
+    """The weight gradients of the 3x3x3 layers on the tensor cores (the
+    default) against the FP32 CUDA-core sums of the same BF16 activations, on
+    a 32^3 grid: both are sums of the same exact BF16 products in FP32, so
+    they differ by at most the sum of their rounding bounds (CUDA cores: 32
+    chunks of V/32 sequential terms, then the chunk sum; tensor cores: at most
+    V/16 accumulated K-blocks of 16 products per CTA, then at most 160 chunk
+    partials), times sum |terms|.  The tensor-core gradient repeats bit for
+    bit.  One training step is timed in each mode (printed)."""
+    shape = (32, 32, 32)
+    nx, ny, nz = shape
+    r = torch.from_numpy(uniform_field((nz, ny, nx), 51)).cuda()
+    e = torch.from_numpy(uniform_field((nz, ny, nx), 52)).cuda()
+    grads, ms = {}, {}
+    for mode in ("tensor", "cuda_cores", "tensor"):
+        net = cfd.UNet(nx, ny, nz, seed=5)
+        net.set_wgrad_mode(mode)
+        net.train_step(r, e, lr=0.0)  # warm-up (the gradient is recomputed below)
+        st, en = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        st.record()
+        net.train_step(r, e, lr=0.0)
+        en.record()
+        torch.cuda.synchronize()
+        ms.setdefault(mode, []).append(st.elapsed_time(en))
+        g = net.read_tensor(cfd.UNET_T_GRAD).double()
+        if mode in grads:
+            assert torch.equal(g, grads[mode]), "tensor-core weight gradient not bitwise repeatable"
+        grads[mode] = g
+        if mode == "cuda_cores":
+            T = {name: grid(net.read_tensor(name), shape, cfd.UNET_LEVELS[i]) for i, name in enumerate(cfd.UNET_TENSORS)}
+    tcg, ccg = ou.unflatten(grads["tensor"]), ou.unflatten(grads["cuda_cores"])
+    ins = [[T["xin"]], [T["a0"]], [T["p0"]], [T["a1"]], [T["p1"]], [T["a2"]], [T["s1"], T["u1"]],
+           [T["s0"], T["u0"]], [T["d0"]]]
+    outs = [T["g_a0"], T["g_s0"], T["g_a1"], T["g_s1"], T["g_a2"], T["g_s2"], T["g_d1"], T["g_d0"], T["gz"]]
+    for li, (name, lv, c0, c1, cout, ks) in enumerate(ou.LAYERS):
+        if ks != 3 or c0 == 1:
+            continue
+        x = torch.cat(ins[li]).abs()
+        w = torch.zeros(cout, c0 + c1, ks, ks, ks, dtype=torch.float64, requires_grad=True)
+        (tw,) = torch.autograd.grad(ou.conv(x, w, None), w, outs[li].abs())
+        Vl = x[0].numel()
+        bound = (2 * (Vl / 32 + 34) + (Vl / 16 + 160 + 34)) * E * tw + 1e-30
+        check(tcg[li][0], ccg[li][0], bound, f"{name} weight gradient, tensor vs CUDA cores")
+        tb = outs[li].abs().sum(dim=(1, 2, 3))
+        check(tcg[li][1], ccg[li][1], (2 * (Vl / 32 + 34) + (Vl / 16 + 160 + 34)) * E * tb + 1e-30,
+              f"{name} bias gradient, tensor vs CUDA cores")
+    print(f"training step at 32^3: tensor cores {min(ms['tensor']):.2f} ms, CUDA cores {ms['cuda_cores'][0]:.2f} ms")
+
+
 def test_anorm_loss_gradient(cfd):
     nx, ny, nz = SHAPE
     net = cfd.UNet(nx, ny, nz, seed=19)
