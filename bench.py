@@ -455,7 +455,7 @@ def cavity_sample(cfd, n, wl, solver, steps, warmup, device, params=None, warm_s
     ph = cav.phase_times()
     rc, st = cav.recent_stats(steps)
     out = {"solver": solver, "warm_start": warm_start, "steps_timed": steps, "warmup": warmup,
-           "ms_per_step": sum(ms) / steps,
+           "ms_per_step": sum(ms) / steps, "step_ms": [round(m, 3) for m in ms],
            "cell_steps_per_s": n ** 3 * steps / (sum(ms) / 1e3),
            "pressure_ms_per_step": ph["pcg"][0] / steps, "diffuse_ms_per_step": ph["diffuse"][0] / steps,
            "pressure_iters": [s["iters"] for s in st], "refinements": [s["outer_iters"] for s in st],
@@ -626,12 +626,15 @@ def main_ours(args):
     if rank == 0 and world == 1 and not args.no_studies:
         # the same cavity with the other solver paths (samples of steps)
         extra["same_cavity"] = {}
-        for other, k_steps, warm_steps in (("cg", 2, 1), ("ir", 4, 1)):
+        # the same warm-up steps as the headline, so that the timed steps
+        # start at the same point of the flow
+        for other, k_steps, warm_steps in (("cg", 2, args.warmup), ("ir", 4, args.warmup)):
             if other != solver:
                 extra["same_cavity"][other] = cavity_sample(cfd, n, wl, other, k_steps, warm_steps, device, params,
                                                             warm_start=warm)
-        extra["same_cavity"]["note"] = (f"samples of {wl['steps_total']} steps: FP64 CG 2 timed steps after 1, IR 4 "
-                                        f"after 1; flexible CG with the network in every iteration is timed on "
+        extra["same_cavity"]["note"] = (f"samples of {wl['steps_total']} steps: FP64 CG 2 timed steps, IR 4, both after "
+                                        f"the headline's {args.warmup} warm-up steps (compare with the headline's "
+                                        f"first steps in step_ms); flexible CG with the network in every iteration is timed on "
                                         f"standalone systems only (time_to_rtol), since one application of the "
                                         f"network costs tens of FP32 iterations at this size")
         if params is not None:
@@ -677,6 +680,7 @@ def main_ours(args):
                 "solve": {"pcg_iters_mean": mean_iters, "pcg_iters_min": min(iters), "pcg_iters_max": max(iters),
                           "time_to_rtol_ms_mean": pcg_avg_s * 1e3, "rel_resid_max": worst_resid,
                           "all_converged": bool(ok), "refinements": [s["outer_iters"] for s in stats]},
+                "step_ms": [round(m, 3) for m in step_ms],
                 "phase_ms_per_step": phase_ms_per_step,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "wall_s_timed": wall}
@@ -919,6 +923,25 @@ def main_unet(args):
             "flops_per_apply": 2 * macs, "tensor_core_flops_per_apply": 2 * tc_macs,
             "achieved_tflops": 2 * macs / (ms * 1e-3) / 1e12,
             "gpu_launches": (net.launch_count() - l0)}
+    # one training step (one pair: forward, loss, backward with input and
+    # weight gradients, Adam) with the weight gradients on the tensor cores
+    # and on the CUDA cores; a training step does about 3x the forward flops
+    e = torch.from_numpy(gaussian_rhs(n, n, n, 1).reshape(-1)).to(device)
+    train = {}
+    for mode in ("tensor", "cuda_cores"):
+        net.set_wgrad_mode(mode)
+        net.train_step(r, e, lr=0.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(1, min(args.steps, 5))
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            net.train_step(r, e, lr=0.0)
+        b.record(stream)
+        torch.cuda.synchronize()
+        train[mode] = a.elapsed_time(b) / reps
+    line["train_step_ms_one_pair"] = train
+    line["train_step_tflops"] = {k: 3 * 2 * macs / (v * 1e-3) / 1e12 for k, v in train.items()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0

@@ -752,6 +752,8 @@ __global__ void __launch_bounds__(kWgThreads) wgrad_tc_kernel(const __grid_const
   __shared__ __align__(8) uint64_t bar_tma, bar_mma;
   __shared__ uint32_t s_tmem;
   __shared__ int s_fail;
+  __shared__ int s_off[27];      // row offset of each tap in the staged box
+  __shared__ float s_bias[96];   // bias partial sums of warps 1..3
   const int t = threadIdx.x;
   const int chunk = blockIdx.x, group = blockIdx.y;
   const int tap0 = group * a.taps_per_group;
@@ -764,12 +766,14 @@ __global__ void __launch_bounds__(kWgThreads) wgrad_tc_kernel(const __grid_const
   const unsigned box_bytes = unsigned(a.bx) * a.by * a.bz * 16;
   constexpr uint32_t kCols = 512;
 
+  const int row_z = a.bx * a.by;
   if (t == 0) {
     tc::mbar_init(&bar_tma, 1);
     tc::mbar_init(&bar_mma, 1);
     tc::mbar_fence_init();
     s_fail = 0;
   }
+  if (t < 27) s_off[t] = (t / 9 - 1) * row_z + ((t / 3) % 3 - 1) * a.bx + (t % 3 - 1);
   if (t < 32) tc::tmem_alloc(&s_tmem, kCols);
   tc::fence_before_sync();
   __syncthreads();
@@ -777,7 +781,10 @@ __global__ void __launch_bounds__(kWgThreads) wgrad_tc_kernel(const __grid_const
   const uint32_t tmem = s_tmem;
   // kind::f16, D FP32, A and B BF16, both MN-major (transpose bits 15, 16)
   const uint32_t idesc = tc::idesc_bf16_f32(128, N) | (1u << 15) | (1u << 16);
-  const int row_z = a.bx * a.by;
+  // bias gradient: thread 32 + j of warps 1..3 sums channel j % cout over the
+  // rows r of each box with r % parts == j / cout (a fixed split)
+  const int bj = t - 32, parts = 96 / a.cout;
+  const bool bias_thread = group == 0 && bj >= 0 && bj < parts * a.cout;
   float bacc = 0.f;
   int nbox = 0;
   bool tma_pending = false;
@@ -804,15 +811,18 @@ __global__ void __launch_bounds__(kWgThreads) wgrad_tc_kernel(const __grid_const
     }
     tma_pending = false;
     tc::fence_after_sync();
-    if (group == 0 && t < a.cout) {
-      // bias gradient: g summed over the interior voxels of the box (zero
-      // outside the grid)
-      const unsigned char* gp = g_planes + size_t(t / 8) * a.plane + (t % 8) * 2;
+    if (bias_thread) {
+      // g summed over the interior voxels of the box (zero outside the grid),
+      // beside the MMA issue of thread 0
+      const int co = bj % a.cout, part = bj / a.cout;
+      const unsigned char* gp = g_planes + size_t(co / 8) * a.plane + (co % 8) * 2;
+      int i = 0;
       for (int zb = 1; zb <= a.tz; ++zb)
         for (int yb = 1; yb <= a.ty; ++yb) {
           const int r0 = (zb * a.by + yb) * a.bx + 1;
-          for (int xb = 0; xb < kWgXc; ++xb)
-            bacc += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(gp + size_t(r0 + xb) * 16));
+          for (int xb = 0; xb < kWgXc; ++xb, ++i)
+            if (i % parts == part)
+              bacc += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(gp + size_t(r0 + xb) * 16));
         }
     }
     if (t == 0) {
@@ -825,8 +835,7 @@ __global__ void __launch_bounds__(kWgThreads) wgrad_tc_kernel(const __grid_const
           const int r = (zb * a.by + yb) * a.bx + 1;  // first interior voxel of the x-line
           const bool acc = nbox > 0 || zb > 1 || yb > 1;
           for (int k = 0; k < ntap; ++k) {
-            const int tap = tap0 + k;
-            const int off = (tap / 9 - 1) * row_z + ((tap / 3) % 3 - 1) * a.bx + (tap % 3 - 1);
+            const int off = s_off[tap0 + k];
             const int ra = a.a_in ? r + off : r, rb = a.a_in ? r : r + off;
             tc::mma_bf16(tmem + uint32_t(k * N), adesc0 + uint64_t(ra), bdesc0 + uint64_t(rb), idesc, acc);
           }
@@ -860,7 +869,13 @@ __global__ void __launch_bounds__(kWgThreads) wgrad_tc_kernel(const __grid_const
         }
       }
     }
-    if (group == 0 && t < a.cout) a.bias_partial[size_t(chunk) * a.cout + t] = bacc;
+    if (bias_thread) s_bias[bj] = bacc;
+  }
+  __syncthreads();
+  if (!s_fail && group == 0 && t < a.cout) {
+    float b = 0.f;
+    for (int p = 0; p < parts; ++p) b += s_bias[p * a.cout + t];  // parts in a fixed order
+    a.bias_partial[size_t(chunk) * a.cout + t] = b;
   }
   tc::fence_before_sync();
   __syncthreads();

@@ -553,6 +553,122 @@ __global__ void __launch_bounds__(kThreads) wgrad_kernel(const WgradArgs a) {
   if (tap == 0 && threadIdx.x < a.cout) a.bias_partial[size_t(chunk) * a.cout + threadIdx.x] = bacc;
 }
 
+// Weight gradients of the two narrow layers, as voxel reductions (memory
+// bound; no contraction worth the tensor cores):
+//   first layer  dW[t][co] = sum_v g[v][co] x[v + s_t]   (one input channel)
+//   head         dW[0][ci] = sum_v g[v] d[v][ci]          (one output channel)
+// Block (chunk, group) sums a contiguous voxel range; per-thread FP32 sums,
+// then a fixed-order block reduction, so the result does not depend on
+// scheduling.  Partials in the [chunk][taps][cout][cin] layout of
+// wgrad_reduce_kernel; bias partials [chunk][cout] from group 0.
+constexpr int kNarrowChunks = 64;
+
+template <int K>
+__device__ __forceinline__ void block_sum_store(float (&v)[K], float* out) {
+  __shared__ float sh[kThreads / 32][K];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    float x = v[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[wid][k] = x;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    float x = 0.f;
+    for (int w = 0; w < kThreads / 32; ++w) x += sh[w][k];
+    out[k] = x;
+  }
+  __syncthreads();
+}
+
+// grid (chunks, 9): group = the (dy, dz) of three taps dx = -1, 0, 1; x BF16
+// [V] (one channel), g 16 channels in two octet planes
+__global__ void __launch_bounds__(kThreads) wgrad_first_kernel(const __nv_bfloat16* x, const __nv_bfloat16* g, int nx,
+                                                               int ny, int nz, float* partial, float* bias_partial) {
+  const int chunk = blockIdx.x, grp = blockIdx.y;
+  const int dy = grp % 3 - 1, dz = grp / 3 - 1;
+  const size_t V = size_t(nx) * ny * nz;
+  const size_t per = (V + gridDim.x - 1) / gridDim.x;
+  const size_t v0 = size_t(chunk) * per, v1 = min(V, v0 + per);
+  float acc[3][16], bacc[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    acc[0][k] = acc[1][k] = acc[2][k] = 0.f;
+    bacc[k] = 0.f;
+  }
+  for (size_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+    const int i = int(v % nx), j = int((v / nx) % ny), k = int(v / (size_t(nx) * ny));
+    float glo[8], ghi[8], gv[16];
+    ld8(g + v * 8, glo);
+    ld8(g + (V + v) * 8, ghi);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      gv[c] = glo[c];
+      gv[8 + c] = ghi[c];
+    }
+    const int jj = j + dy, kk = k + dz;
+    float xs[3] = {0.f, 0.f, 0.f};
+    if (jj >= 0 && jj < ny && kk >= 0 && kk < nz) {
+      const size_t row = (size_t(kk) * ny + jj) * nx;
+      if (i > 0) xs[0] = __bfloat162float(x[row + i - 1]);
+      xs[1] = __bfloat162float(x[row + i]);
+      if (i < nx - 1) xs[2] = __bfloat162float(x[row + i + 1]);
+    }
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      acc[0][c] = fmaf(xs[0], gv[c], acc[0][c]);
+      acc[1][c] = fmaf(xs[1], gv[c], acc[1][c]);
+      acc[2][c] = fmaf(xs[2], gv[c], acc[2][c]);
+      bacc[c] += gv[c];
+    }
+  }
+  __shared__ float out[48];
+  float flat[48];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int c = 0; c < 16; ++c) flat[d * 16 + c] = acc[d][c];
+  block_sum_store<48>(flat, out);
+  for (int e = threadIdx.x; e < 48; e += blockDim.x) {
+    const int d = e / 16, c = e % 16;
+    const int tap = (dz + 1) * 9 + (dy + 1) * 3 + d;
+    partial[(size_t(chunk) * 27 + tap) * 16 + c] = out[e];  // [chunk][tap][cout 16][cin 1]
+  }
+  if (grp == 0) {
+    __shared__ float bout[16];
+    block_sum_store<16>(bacc, bout);
+    if (threadIdx.x < 16) bias_partial[size_t(chunk) * 16 + threadIdx.x] = bout[threadIdx.x];
+  }
+}
+
+// grid (chunks): g BF16 [V] (one channel), d 16 channels in two octet planes
+__global__ void __launch_bounds__(kThreads) wgrad_head_kernel(const __nv_bfloat16* d, const __nv_bfloat16* g, size_t V,
+                                                              float* partial, float* bias_partial) {
+  const int chunk = blockIdx.x;
+  const size_t per = (V + gridDim.x - 1) / gridDim.x;
+  const size_t v0 = size_t(chunk) * per, v1 = min(V, v0 + per);
+  float acc[17];
+#pragma unroll
+  for (int c = 0; c < 17; ++c) acc[c] = 0.f;
+  for (size_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+    const float gv = __bfloat162float(g[v]);
+    float dlo[8], dhi[8];
+    ld8(d + v * 8, dlo);
+    ld8(d + (V + v) * 8, dhi);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      acc[c] = fmaf(gv, dlo[c], acc[c]);
+      acc[8 + c] = fmaf(gv, dhi[c], acc[8 + c]);
+    }
+    acc[16] += gv;
+  }
+  __shared__ float out[17];
+  block_sum_store<17>(acc, out);
+  if (threadIdx.x < 16) partial[size_t(chunk) * 16 + threadIdx.x] = out[threadIdx.x];  // [chunk][1][1][16]
+  if (threadIdx.x == 0) bias_partial[chunk] = out[16];
+}
+
 // grad[i] += sum over chunks (fixed order); i over taps * P, then bias
 __global__ void wgrad_reduce_kernel(const float* partial, const float* bias_partial, int chunks, size_t n, int cout,
                                     float* grad, float* bias_grad) {
@@ -1002,6 +1118,20 @@ int wgrad(cfd_unet* u, int layer, const __nv_bfloat16* src0, const __nv_bfloat16
       return klaunch(u, "wgrad reduce");
     }
     if (e != cudaErrorNotSupported) return uck(u, e, "tensor-core weight gradient");
+  }
+  if ((layer == 0 && L.c0 == 1 && L.cout == 16 && L.ks == 3) || (layer == 8 && L.cout == 1 && L.c0 == 16 && L.ks == 1)) {
+    int fx, fy, fz;
+    level_dims(u, L.level, fx, fy, fz);
+    if (layer == 0)
+      wgrad_first_kernel<<<dim3(kNarrowChunks, 9), kThreads, 0, u->stream>>>(src0, gout, fx, fy, fz, u->wpart, u->bpart);
+    else
+      wgrad_head_kernel<<<kNarrowChunks, kThreads, 0, u->stream>>>(src0, gout, size_t(fx) * fy * fz, u->wpart, u->bpart);
+    int rc = klaunch(u, "narrow-layer weight gradient");
+    if (rc) return rc;
+    const size_t n = size_t(taps_of(L.ks)) * L.cout * L.c0;
+    wgrad_reduce_kernel<<<grid_for(n), kThreads, 0, u->stream>>>(u->wpart, u->bpart, kNarrowChunks, n, L.cout,
+                                                                 u->g + u->woff[layer], u->g + u->boff[layer]);
+    return klaunch(u, "wgrad reduce");
   }
   WgradArgs a{};
   level_dims(u, L.level, a.nx, a.ny, a.nz);
