@@ -73,6 +73,10 @@ namespace cfd {
 namespace {
 
 constexpr int kGThreads = 256;  // every kernel: 256 threads (32 x 8 for the stencils)
+// Resident blocks per SM of the FP32 iteration kernels (g_dir, g_upd): with
+// 5 (at most 48 registers a thread, no spills) an iteration at 384^3 takes
+// 323 us against 334 us with 4 (64 registers); 6 spills.
+constexpr int kIterBlocks = 5;
 constexpr int kGMax = 1024;     // blocks per kernel (partial-sum slots per value)
 #ifndef CFD_IRG_ZPLANES
 #define CFD_IRG_ZPLANES 4
@@ -467,7 +471,7 @@ __device__ __forceinline__ void set_alpha(GState* S, double num, double pq) {
 }
 
 // inner body: p = r32 + beta p_old, stored; p.Ap by edge_pass; alpha = rz / p.Ap
-__global__ void __launch_bounds__(kGThreads, 4) g_dir(const GArgs a) {
+__global__ void __launch_bounds__(kGThreads, kIterBlocks) g_dir(const GArgs a) {
   GState* S = a.S;
   count_kernel(S);
   const bool first = S->first != 0;
@@ -557,7 +561,7 @@ __device__ __forceinline__ double upd_pass(const GArgs& a, float alpha, const fl
 
 // inner body: the update pass, then the loop control
 template <bool VEL>
-__global__ void __launch_bounds__(kGThreads, 4) g_upd(const GArgs a) {
+__global__ void __launch_bounds__(kGThreads, kIterBlocks) g_upd(const GArgs a) {
   GState* S = a.S;
   count_kernel(S);
   if (S->breakdown) {
