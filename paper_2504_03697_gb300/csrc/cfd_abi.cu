@@ -16,6 +16,7 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <queue>
 #include <vector>
 
 #include "../../include/cfd.h"
@@ -1292,6 +1293,14 @@ struct cfd_batch {
   // device tables inside the batch workspace
   CgArgs* d_cg;            // [4][n]: diffusion u, v, w (first nd entries), pressure CG
   IrArgs* d_ir;            // [4][n]: mixed-precision diffusion u, v, w (first nd entries), pressure
+  char* d_gir;             // [4][n] entries of the batched graph-form solve (ir_batch_table), same order
+  // batched sweeps: cavity tables (all cavities, those with nu > 0, those
+  // with forces) and block starts per sweep slot (advect, forces, diffusion
+  // rhs u / v / w, divergence, correct)
+  PhysArgs* d_phys;        // [3][n]
+  int* d_sweep_starts;     // [kSweepSlots][n + 1]
+  int sweep_total[7];
+  std::vector<int> force_idx;
   int* d_starts;           // [5][n + 1]
   SolveCtrl* d_ctrl;       // [4][n]
   DevSolveStats* d_stats;  // [4][n]
@@ -1308,8 +1317,10 @@ struct cfd_batch {
 
 namespace {
 
+constexpr int kSweepSlots = 7;
+
 struct BatchLayout {
-  size_t cg, ir, starts, ctrl, stats, cav0;
+  size_t cg, ir, gir, phys, sweep_starts, starts, ctrl, stats, cav0;
   std::vector<size_t> cav;
   size_t total;
 };
@@ -1324,6 +1335,9 @@ BatchLayout batch_layout(int n, const cfd_params* prm) {
   };
   L.cg = take(sizeof(CgArgs) * 4 * size_t(n));
   L.ir = take(sizeof(IrArgs) * 4 * size_t(n));  // [kind][cavity]: diffusion u, v, w, then pressure
+  L.gir = take(ir_batch_table_bytes(4 * n));
+  L.phys = take(sizeof(PhysArgs) * 3 * size_t(n));
+  L.sweep_starts = take(sizeof(int) * kSweepSlots * size_t(n + 1));
   L.starts = take(sizeof(int) * 5 * size_t(n + 1));
   L.ctrl = take(sizeof(SolveCtrl) * 4 * size_t(n));
   L.stats = take(sizeof(DevSolveStats) * 4 * size_t(n));
@@ -1371,6 +1385,39 @@ std::vector<int> split_blocks(const std::vector<double>& w, int total) {
   return starts;
 }
 
+// Split `total` blocks over problems whose time on nb blocks is
+// extent * ceil(items / nb) (the batched graph-form solve): one block each,
+// then, while blocks remain, the slowest problem gets the blocks that take
+// it to its next shorter time.  Returns prefix starts (size n + 1) or an
+// empty vector if n > total.
+std::vector<int> split_blocks_balanced(const std::vector<int>& items, const std::vector<int>& extent, int total) {
+  const int n = int(items.size());
+  std::vector<int> starts(size_t(n) + 1, 0);
+  if (n == 0) return starts;
+  if (n > total) return {};
+  std::vector<int> nb(size_t(n), 1);
+  auto cost = [&](int i, int b) {
+    return double(extent[size_t(i)]) * double((items[size_t(i)] + b - 1) / b);
+  };
+  std::priority_queue<std::pair<double, int>> q;
+  for (int i = 0; i < n; ++i) q.push({cost(i, 1), i});
+  int left = total - n;
+  while (left > 0 && !q.empty()) {
+    const int i = q.top().second;
+    const int it = items[size_t(i)], b = nb[size_t(i)];
+    const int per = (it + b - 1) / b;
+    if (per <= 1) break;  // the slowest problem has one item per block: nothing shortens the longest time
+    const int need = (it + per - 2) / (per - 1) - b;  // blocks to reach ceil(items / nb) = per - 1
+    if (need > left) break;
+    q.pop();
+    nb[size_t(i)] = b + need;
+    left -= need;
+    q.push({cost(i, nb[size_t(i)]), i});
+  }
+  for (int i = 0; i < n; ++i) starts[size_t(i) + 1] = starts[size_t(i)] + nb[size_t(i)];
+  return starts;
+}
+
 // Enqueue one step of every cavity.
 int batch_enqueue_step(cfd_batch* b) {
   const int n = b->n;
@@ -1379,36 +1426,37 @@ int batch_enqueue_step(cfd_batch* b) {
     if (e != cudaSuccess && rc == CFD_OK) rc = batch_err(b, CFD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
     return rc == CFD_OK;
   };
-  for (int i = 0; i < n && rc == CFD_OK; ++i) {
-    cfd_handle* h = b->cav[size_t(i)];
-    PhysArgs pa = phys(h);
-    if (h->prm.g[0] != 0.0 || h->prm.g[1] != 0.0 || h->prm.g[2] != 0.0) ck(launch_forces(pa, b->stream, &b->launches), "forces");
-    ck(launch_advect(pa, b->stream, &b->launches), "advect");
-  }
+  auto sweep = [&](int slot, int table, int count, int op, int comp, const char* what) {
+    ck(launch_sweep_multi(op, b->d_phys + size_t(table) * n, b->d_sweep_starts + size_t(slot) * (n + 1), count,
+                          b->sweep_total[slot], comp, b->stream, &b->launches),
+       what);
+  };
+  if (!b->force_idx.empty()) sweep(1, 2, int(b->force_idx.size()), kSweepForces, 0, "forces");
+  sweep(0, 0, n, kSweepAdvect, 0, "advect");
   const int nd = int(b->diff_idx.size());
   for (int c = 0; c < 3 && nd > 0 && rc == CFD_OK; ++c) {
-    for (int k = 0; k < nd; ++k) ck(launch_diffusion_rhs(phys(b->cav[size_t(b->diff_idx[size_t(k)])]), c, b->stream, &b->launches), "diffusion rhs");
+    sweep(2 + c, 1, nd, kSweepDiffusionRhs, c, "diffusion rhs");
     ck(cudaMemsetAsync(b->d_ctrl + size_t(c) * n, 0, sizeof(SolveCtrl) * size_t(nd), b->stream), "memset ctrl");
     if (b->solver == CFD_SOLVER_IR)
-      ck(launch_ir_multi(b->d_ir + size_t(c) * n, b->d_starts + size_t(c) * (n + 1), nd, b->total_blocks[c], b->stream,
-                         &b->launches),
+      ck(launch_ir_batch(b->d_gir + size_t(c) * n * ir_batch_table_bytes(1), b->d_starts + size_t(c) * (n + 1), nd,
+                         b->total_blocks[c], 1, b->stream, &b->launches),
          "batched mixed-precision diffusion launch");
     else
       ck(launch_cg_multi(b->d_cg + size_t(c) * n, b->d_starts + size_t(c) * (n + 1), nd, b->total_blocks[c], 0,
                          b->stream, &b->launches),
          "batched diffusion launch");
   }
-  for (int i = 0; i < n && rc == CFD_OK; ++i) ck(launch_divergence(phys(b->cav[size_t(i)]), b->stream, &b->launches), "divergence");
+  sweep(5, 0, n, kSweepDivergence, 0, "divergence");
   ck(cudaMemsetAsync(b->d_ctrl + size_t(3) * n, 0, sizeof(SolveCtrl) * size_t(n), b->stream), "memset ctrl");
   if (b->solver == CFD_SOLVER_IR)
-    ck(launch_ir_multi(b->d_ir + size_t(3) * n, b->d_starts + size_t(4) * (n + 1), n, b->total_blocks[4], b->stream,
-                       &b->launches),
+    ck(launch_ir_batch(b->d_gir + size_t(3) * n * ir_batch_table_bytes(1), b->d_starts + size_t(4) * (n + 1), n,
+                       b->total_blocks[4], 0, b->stream, &b->launches),
        "batched pressure launch");
   else
     ck(launch_cg_multi(b->d_cg + size_t(3) * n, b->d_starts + size_t(3) * (n + 1), n, b->total_blocks[3], b->precond,
                        b->stream, &b->launches),
        "batched pressure launch");
-  for (int i = 0; i < n && rc == CFD_OK; ++i) ck(launch_correct(phys(b->cav[size_t(i)]), b->stream, &b->launches), "correct");
+  sweep(6, 0, n, kSweepCorrect, 0, "correct");
   return rc;
 }
 
@@ -1455,6 +1503,9 @@ int cfd_batch_create(int n, const cfd_params* per_cavity, void* dev_ws, size_t b
   b->precond = solver == CFD_SOLVER_JACOBI ? 1 : 0;
   b->d_cg = reinterpret_cast<CgArgs*>(b->ws + L.cg);
   b->d_ir = reinterpret_cast<IrArgs*>(b->ws + L.ir);
+  b->d_gir = b->ws + L.gir;
+  b->d_phys = reinterpret_cast<PhysArgs*>(b->ws + L.phys);
+  b->d_sweep_starts = reinterpret_cast<int*>(b->ws + L.sweep_starts);
   b->d_starts = reinterpret_cast<int*>(b->ws + L.starts);
   b->d_ctrl = reinterpret_cast<SolveCtrl*>(b->ws + L.ctrl);
   b->d_stats = reinterpret_cast<DevSolveStats*>(b->ws + L.stats);
@@ -1472,6 +1523,7 @@ int cfd_batch_create(int n, const cfd_params* per_cavity, void* dev_ws, size_t b
     if (rc) return fail(rc);
     b->cav.push_back(h);
     if (per_cavity[i].nu > 0.0) b->diff_idx.push_back(i);
+    if (per_cavity[i].g[0] != 0.0 || per_cavity[i].g[1] != 0.0 || per_cavity[i].g[2] != 0.0) b->force_idx.push_back(i);
   }
   // block split and solve tables
   const int sms = batch_num_sms();
@@ -1493,11 +1545,29 @@ int cfd_batch_create(int n, const cfd_params* per_cavity, void* dev_ws, size_t b
   for (int kind = 0; kind < 5; ++kind) {
     const bool is_ir = kind == 4;
     const std::vector<int>& idx = kind < 3 ? b->diff_idx : all;
-    // the mixed-precision diffusion solves must fit both kernels' residency
-    const int bps = kind < 3 && mixed ? std::min(batch_blocks_per_sm(0), batch_blocks_per_sm(1))
-                                      : batch_blocks_per_sm(is_ir);
+    // the mixed-precision solves (diffusion kinds 0-2 and pressure kind 4)
+    // run the batched graph-form kernel (one wave, at most 4 blocks per SM)
+    const int bps = (kind < 3 && mixed) || is_ir ? std::min(4, ir_batch_blocks_per_sm(kind < 3 ? 1 : 0))
+                                                 : batch_blocks_per_sm();
     const int total = bps * sms;
-    std::vector<int> st = split_blocks(weights(idx, kind < 3 ? kind : 3), total);
+    const bool ir_kind = (kind < 3 && mixed) || is_ir;
+    std::vector<int> st;
+    if (ir_kind) {
+      // the batched graph-form solve: blocks in proportion to each
+      // cavity's (row, plane) steps times its iteration count
+      std::vector<int> items, extent;
+      for (int i : idx) {
+        cfd_handle* h = b->cav[size_t(i)];
+        int it = 1, ex = 1;
+        ir_batch_work(kind < 3 ? diffusion_ir_args(h, kind, nullptr) : pressure_ir_args(h, h->p, 0, 1, nullptr, nullptr),
+                      &it, &ex);
+        items.push_back(it);
+        extent.push_back(ex);
+      }
+      st = split_blocks_balanced(items, extent, total);
+    } else {
+      st = split_blocks(weights(idx, kind < 3 ? kind : 3), total);
+    }
     if (st.empty()) {
       rc = batch_err(nullptr, CFD_ERR_INVALID_ARG, "%zu cavities exceed the %d co-resident blocks of one launch", idx.size(), total);
       return fail(rc);
@@ -1530,6 +1600,52 @@ int cfd_batch_create(int n, const cfd_params* per_cavity, void* dev_ws, size_t b
         ir[size_t(3) * n + k] = a;
       }
     }
+  }
+  if (mixed) {
+    // entries of the batched graph-form solve: diffusion kinds over the
+    // cavities with nu > 0, the pressure over all; partial sums in each
+    // cavity's graph state
+    const size_t entry = ir_batch_table_bytes(1);
+    for (int kind = 0; kind < 4 && !rc; ++kind) {
+      const std::vector<int>& idx = kind < 3 ? b->diff_idx : all;
+      if (idx.empty()) continue;
+      std::vector<void*> states;
+      for (int i : idx) states.push_back(b->cav[size_t(i)]->irg_state);
+      rc = cuda_check(nullptr, ir_batch_table(&ir[size_t(kind) * n], states.data(), int(idx.size()),
+                                               b->d_gir + size_t(kind) * n * entry, b->stream),
+                      "batched solve table");
+    }
+    if (rc) return fail(rc);
+  }
+  {
+    // batched sweeps: per slot, each cavity gets the grid its single-cavity
+    // sweep launches
+    std::vector<PhysArgs> ph(3 * size_t(n));
+    const std::vector<int>* subsets[3] = {&all, &b->diff_idx, &b->force_idx};
+    for (int t = 0; t < 3; ++t)
+      for (size_t k = 0; k < subsets[t]->size(); ++k) ph[size_t(t) * n + k] = phys(b->cav[size_t((*subsets[t])[k])]);
+    const int slot_table[kSweepSlots] = {0, 2, 1, 1, 1, 0, 0};
+    const int slot_op[kSweepSlots] = {kSweepAdvect, kSweepForces, kSweepDiffusionRhs, kSweepDiffusionRhs,
+                                      kSweepDiffusionRhs, kSweepDivergence, kSweepCorrect};
+    std::vector<int> sst(size_t(kSweepSlots) * (n + 1), 0);
+    for (int slot = 0; slot < kSweepSlots; ++slot) {
+      const int t = slot_table[slot];
+      const int comp = slot >= 2 && slot <= 4 ? slot - 2 : 0;
+      int acc = 0;
+      for (size_t k = 0; k < subsets[t]->size(); ++k) {
+        sst[size_t(slot) * (n + 1) + k] = acc;
+        acc += sweep_blocks_for(ph[size_t(t) * n + k], slot_op[slot], comp);
+      }
+      sst[size_t(slot) * (n + 1) + subsets[t]->size()] = acc;
+      b->sweep_total[slot] = acc;
+    }
+    rc = cuda_check(nullptr, cudaMemcpyAsync(b->d_phys, ph.data(), sizeof(PhysArgs) * ph.size(), cudaMemcpyHostToDevice,
+                                             b->stream), "copy tables");
+    if (!rc)
+      rc = cuda_check(nullptr, cudaMemcpyAsync(b->d_sweep_starts, sst.data(), sizeof(int) * sst.size(),
+                                               cudaMemcpyHostToDevice, b->stream), "copy tables");
+    if (!rc) rc = cuda_check(nullptr, cudaStreamSynchronize(b->stream), "synchronize");  // ph, sst are released
+    if (rc) return fail(rc);
   }
   rc = cuda_check(nullptr, cudaMemcpyAsync(b->d_cg, cg.data(), sizeof(CgArgs) * cg.size(), cudaMemcpyHostToDevice, b->stream), "copy tables");
   if (!rc) rc = cuda_check(nullptr, cudaMemcpyAsync(b->d_ir, ir.data(), sizeof(IrArgs) * ir.size(), cudaMemcpyHostToDevice, b->stream), "copy tables");

@@ -155,6 +155,14 @@ cudaError_t launch_diffusion_rhs(const PhysArgs& a, int comp, cudaStream_t s, in
 cudaError_t launch_divergence(const PhysArgs& a, cudaStream_t s, int64_t* launches);
 cudaError_t launch_correct(const PhysArgs& a, cudaStream_t s, int64_t* launches);
 cudaError_t launch_zero_wall_faces(const PhysArgs& a, cudaStream_t s, int64_t* launches);
+// Batched sweeps (one launch for many cavities): cavity k of the device
+// table d_tab works on the blocks [d_starts[k], d_starts[k+1]); its block
+// count is sweep_blocks_for(its args, op, comp), the single-cavity grid.
+enum SweepOp { kSweepAdvect = 0, kSweepForces = 1, kSweepDiffusionRhs = 2, kSweepDivergence = 3, kSweepCorrect = 4 };
+size_t sweep_elems(const PhysArgs& a, int op, int comp);
+int sweep_blocks_for(const PhysArgs& a, int op, int comp);
+cudaError_t launch_sweep_multi(int op, const PhysArgs* d_tab, const int* d_starts, int nprob, int total_blocks,
+                               int comp, cudaStream_t s, int64_t* launches);
 cudaError_t launch_fill(double* p, size_t n, double value, cudaStream_t s, int64_t* launches);
 // Training pair of the learned preconditioner: r = (b - mean b) - A xk and
 // e = (xs - xk) - mean(xs - xk), with the FP64 pressure operator A.  r must
@@ -172,9 +180,7 @@ int cg_max_coresident_blocks(int kind_is_ir);
 // memory.  Memory path only (per-problem runtime tile depth), no TMA.
 cudaError_t launch_cg_multi(const CgArgs* d_table, const int* d_starts, int nprob, int total_blocks, int precond,
                             cudaStream_t s, int64_t* launches);
-cudaError_t launch_ir_multi(const IrArgs* d_table, const int* d_starts, int nprob, int total_blocks, cudaStream_t s,
-                            int64_t* launches);
-int batch_blocks_per_sm(int ir);
+int batch_blocks_per_sm();
 int batch_num_sms();
 // Deepest tile depth that still gives `blocks` blocks two tiles each.
 int solve_tile_depth_for(GridDims g, int blocks);

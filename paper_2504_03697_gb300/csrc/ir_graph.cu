@@ -62,6 +62,7 @@
 
 #include <cstdint>
 #include <cstring>
+#include <vector>
 
 #include "cfd_common.cuh"
 #include "cfd_internal.h"
@@ -134,7 +135,8 @@ struct GArgs {
   int kind;              // kOp* operator
   double c;              // nu dt / h^2 (velocity operators)
   float c32;
-  int w32x, w32y, w32z;  // FP32 work items: (float4 or scalar) columns / 32, rows / 8, planes / kZ32
+  int lpr;               // float4 lanes: lanes per grid row (4, 8, 16 or 32); a warp covers 32 / lpr rows
+  int w32x, w32y, w32z;  // FP32 work items: (float4 or scalar) columns / lpr (32), rows / (8 * 32 / lpr), planes / kZ32
   int w64x, w64y, w64z;  // FP64 work items: columns / 32, rows / 8, planes / kZ64
   // learned preconditioner (pressure matrix, float4 kernels)
   __nv_bfloat16* net_in;  // the network's input plane
@@ -144,22 +146,38 @@ struct GArgs {
   int stagnation;         // flexible CG: iterations without halving |r| before plain CG
   int gwarm;              // learned guess corrects the starting x (source r = b' - A x) instead of replacing it
   cudaGraphConditionalHandle h_net;
+  // batched launch (irb_kernel): the problem's synchronisation words (arrive
+  // = reduction counter, pad[0] = reduction generation, error = a block gave
+  // up waiting; zero before the launch), where its statistics go, and the
+  // limit of one wait
+  SolveCtrl* ctrl;
+  DevSolveStats* stats;
+  unsigned long long timeout_ns;
 };
 
 __device__ __forceinline__ int ftid() { return threadIdx.y * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ size_t vtid() { return size_t(blockIdx.x) * kGThreads + ftid(); }
 __device__ __forceinline__ size_t vstride() { return size_t(gridDim.x) * kGThreads; }
 
+// The blocks that work on one problem: this block's index among them and
+// their count (the whole grid in the graph form; a range of it in the
+// batched launch).
+struct Blk {
+  int bid, nb;
+};
+__device__ __forceinline__ Blk grid_blk() { return Blk{int(blockIdx.x), int(gridDim.x)}; }
+
 __device__ __forceinline__ void count_kernel(GState* S) {
   if (blockIdx.x == 0 && ftid() == 0) S->kernels += 1;
 }
 
-// Block sums of v[], stored in slot blockIdx.x; returns true in every thread
-// of the block that arrived last, with out[] = the sums over all slots in
-// block order (the same bits for the same partials whatever the schedule).
+// Block sums of v[] (one shuffle tree per warp, then the warps in order),
+// stored in slot B.bid of part; arrival on *counter (atomicInc wraps it back
+// to 0 with the last of the B.nb arrivals).  Returns true in every thread of
+// the block that arrived last.
 template <int K>
-__device__ bool reduce_last(const double (&v)[K], double* part, unsigned* counter, double (&out)[K]) {
-  __shared__ double sh[K][kGThreads / 32];
+__device__ bool arrive_slots(const double (&v)[K], double* part, unsigned* counter, double (&sh)[K][kGThreads / 32],
+                             Blk B) {
   __shared__ int s_last;
   const int t = ftid(), lane = t & 31, wid = t >> 5;
 #pragma unroll
@@ -174,22 +192,30 @@ __device__ bool reduce_last(const double (&v)[K], double* part, unsigned* counte
     for (int k = 0; k < K; ++k) {
       double s = 0.0;
       for (int w = 0; w < kGThreads / 32; ++w) s += sh[k][w];
-      part[k * kGMax + blockIdx.x] = s;
+      part[k * kGMax + B.bid] = s;
     }
     __threadfence();
-    s_last = atomicInc(counter, gridDim.x - 1) == gridDim.x - 1;
+    s_last = atomicInc(counter, unsigned(B.nb) - 1) == unsigned(B.nb) - 1;
   }
   __syncthreads();
-  if (!s_last) return false;
+  return s_last != 0;
+}
+
+// In the block that arrived last: out[] = the sums over the B.nb slots in
+// block order (the same bits for the same partials whatever the schedule),
+// in every thread.
+template <int K>
+__device__ void sum_slots(const double* part, double (&sh)[K][kGThreads / 32], double (&out)[K], Blk B) {
+  const int t = ftid(), lane = t & 31, wid = t >> 5;
   __threadfence();
   double acc[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     acc[k] = 0.0;
-    for (unsigned bk = unsigned(t); bk < gridDim.x; bk += kGThreads) acc[k] += __ldcg(part + k * kGMax + bk);
+    for (unsigned bk = unsigned(t); bk < unsigned(B.nb); bk += kGThreads) acc[k] += __ldcg(part + k * kGMax + bk);
     for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
   }
-  __syncthreads();  // thread 0's reads of sh above are complete
+  __syncthreads();  // thread 0's reads of sh in arrive_slots are complete
   if (lane == 0)
 #pragma unroll
     for (int k = 0; k < K; ++k) sh[k][wid] = acc[k];
@@ -200,6 +226,17 @@ __device__ bool reduce_last(const double (&v)[K], double* part, unsigned* counte
     for (int w = 0; w < kGThreads / 32; ++w) s += sh[k][w];
     out[k] = s;
   }
+}
+
+// Block sums of v[], stored in slot blockIdx.x; returns true in every thread
+// of the block that arrived last, with out[] = the sums over all slots in
+// block order.
+template <int K>
+__device__ bool reduce_last(const double (&v)[K], double* part, unsigned* counter, double (&out)[K]) {
+  __shared__ double sh[K][kGThreads / 32];
+  const Blk B = grid_blk();
+  if (!arrive_slots<K>(v, part, counter, sh, B)) return false;
+  sum_slots<K>(part, sh, out, B);
   return true;
 }
 
@@ -243,24 +280,18 @@ __global__ void __launch_bounds__(kGThreads) g_pro_sum(const GArgs a) {
 //   x + x32 on the fly (x itself unchanged); sums r.r, sum(r).
 // MODE 2 (epilogue): only when b != 0 and the loop ended without
 //   convergence; xv = x + x32 if x32 is pending; sums r.r.
+// The pass of g_resid64 over the blocks B: r = b' - A xv, with b' = b -
+// shift (MODE 0; stored when remove_mean) and xv = 0 (zero), x + x32 (add32)
+// or x; s[0] += b'.b' (MODE 0), s[1] += r.r, s[2] += sum(r).
 template <int MODE>
-__global__ void __launch_bounds__(kGThreads) g_resid64(const GArgs a) {
-  GState* S = a.S;
-  count_kernel(S);
-  if (MODE == 1 && !S->refine) {
-    if (blockIdx.x == 0 && ftid() == 0) cudaGraphSetConditional(a.h_out, 0u);  // cap or breakdown: leave
-    return;
-  }
-  if (MODE == 2 && (S->bb == 0.0 || S->status == kOk)) return;
+__device__ __forceinline__ void resid64_pass(const GArgs& a, double shift, bool add32, bool zero, double (&s)[3],
+                                             Blk B) {
   const int mx = a.mx, my = a.my, mz = a.mz;
   const size_t sy = size_t(mx), sz = size_t(mx) * my;
-  const double shift = MODE == 0 ? S->shift : 0.0;
-  const bool add32 = MODE == 1 || (MODE == 2 && S->pending);
-  const bool zero = MODE == 0 && a.zero_x0;
   auto X = [&](size_t e) { return zero ? 0.0 : (add32 ? a.x[e] + double(a.d32[e]) : a.x[e]); };
   double sb = 0.0, sr = 0.0, ss = 0.0;
   const int items = a.w64x * a.w64y * a.w64z;
-  for (int w = blockIdx.x; w < items; w += gridDim.x) {
+  for (int w = B.bid; w < items; w += B.nb) {
     const int wx = w % a.w64x, wy = (w / a.w64x) % a.w64y, wz = w / (a.w64x * a.w64y);
     const int i = wx * 32 + threadIdx.x, j = wy * 8 + threadIdx.y, k0 = wz * kZ64;
     if (i >= mx || j >= my) continue;
@@ -290,7 +321,23 @@ __global__ void __launch_bounds__(kGThreads) g_resid64(const GArgs a) {
       xc = xp;
     }
   }
-  double v[3] = {sb, sr, ss}, o[3];
+  s[0] = sb;
+  s[1] = sr;
+  s[2] = ss;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kGThreads) g_resid64(const GArgs a) {
+  GState* S = a.S;
+  count_kernel(S);
+  if (MODE == 1 && !S->refine) {
+    if (blockIdx.x == 0 && ftid() == 0) cudaGraphSetConditional(a.h_out, 0u);  // cap or breakdown: leave
+    return;
+  }
+  if (MODE == 2 && (S->bb == 0.0 || S->status == kOk)) return;
+  double v[3], o[3];
+  resid64_pass<MODE>(a, MODE == 0 ? S->shift : 0.0, MODE == 1 || (MODE == 2 && S->pending), MODE == 0 && a.zero_x0, v,
+                     grid_blk());
   if (!reduce_last<3>(v, a.part, &S->counter, o) || ftid() != 0) return;
   if (MODE == 0) {
     S->bb = o[0];
@@ -360,33 +407,56 @@ __global__ void __launch_bounds__(kGThreads) g_prep(const GArgs a) {
 // One warp covers 128 x cells of one row; x neighbours by warp shuffles,
 // y neighbours by loads, z by marching kZ32 planes in registers.
 // ---------------------------------------------------------------------------
-template <bool VEL, typename F4, typename F1, typename E>
-__device__ __forceinline__ void march_f32(const GArgs& a, F4 P4, F1 P1, E emit) {
+// PF: issue the next plane's loads before this plane's arithmetic and
+// stores (the batched launch, whose small grids are bound by the latency of
+// each plane's loads, not by bandwidth).
+template <bool VEL, bool PF = false, typename F4, typename F1, typename E>
+__device__ __forceinline__ void march_f32(const GArgs& a, F4 P4, F1 P1, E emit, Blk B = grid_blk()) {
   const int my = a.my, mz = a.mz, nx4 = a.mx >> 2;
   const size_t sy4 = size_t(nx4), sz4 = size_t(nx4) * my;
-  const int lane = threadIdx.x;
+  const int lane = threadIdx.x, L = a.lpr, sl = lane & (L - 1), seg = lane / L, rpw = 32 / L;
   const int items = a.w32x * a.w32y * a.w32z;
-  for (int w = blockIdx.x; w < items; w += gridDim.x) {
+  for (int w = B.bid; w < items; w += B.nb) {
     const int wx = w % a.w32x, wy = (w / a.w32x) % a.w32y, wz = w / (a.w32x * a.w32y);
-    const int i4 = wx * 32 + lane, j = wy * 8 + threadIdx.y, k0 = wz * kZ32;
-    if (j >= my) continue;  // the whole warp (one row per warp)
-    const bool on = i4 < nx4;
+    const int i4 = wx * L + sl, j0 = (wy * 8 + threadIdx.y) * rpw, k0 = wz * kZ32;
+    if (j0 >= my) continue;  // the whole warp
+    const bool row = j0 + seg < my;
+    const int j = row ? j0 + seg : my - 1;  // rows past the grid shadow the last row
+    const bool on = row && i4 < nx4;
     const bool has_w = i4 > 0, has_e = i4 + 1 < nx4;
-    size_t c4 = (size_t(k0) * my + j) * nx4 + (on ? i4 : nx4 - 1);  // idle lanes shadow the last column
+    size_t c4 = (size_t(k0) * my + j) * nx4 + (i4 < nx4 ? i4 : nx4 - 1);  // idle lanes shadow the last column
     float4 pc = P4(c4);
     float4 pm = k0 > 0 ? P4(c4 - sz4) : pc;
+    float4 pp, ps, pn;
+    if (PF) {
+      pp = k0 < mz - 1 ? P4(c4 + sz4) : pc;
+      ps = j > 0 ? P4(c4 - sy4) : pc;
+      pn = j < my - 1 ? P4(c4 + sy4) : pc;
+    }
 #pragma unroll
     for (int kk = 0; kk < kZ32; ++kk) {
       const int k = k0 + kk;
       if (k >= mz) break;
-      const float4 pp = k < mz - 1 ? P4(c4 + sz4) : pc;
-      const float4 ps = j > 0 ? P4(c4 - sy4) : pc;
-      const float4 pn = j < my - 1 ? P4(c4 + sy4) : pc;
-      float west = __shfl_up_sync(0xffffffffu, pc.w, 1);
-      float east = __shfl_down_sync(0xffffffffu, pc.x, 1);
-      if (lane == 0) west = has_w ? P1(4 * c4 - 1) : pc.x;
+      float4 pp2, ps2, pn2;
+      if (PF) {
+        pp2 = pp;
+        ps2 = pp;
+        pn2 = pp;
+        if (kk + 1 < kZ32 && k + 1 < mz) {
+          pp2 = k + 1 < mz - 1 ? P4(c4 + 2 * sz4) : pp;
+          ps2 = j > 0 ? P4(c4 + sz4 - sy4) : pp;
+          pn2 = j < my - 1 ? P4(c4 + sz4 + sy4) : pp;
+        }
+      } else {
+        pp = k < mz - 1 ? P4(c4 + sz4) : pc;
+        ps = j > 0 ? P4(c4 - sy4) : pc;
+        pn = j < my - 1 ? P4(c4 + sy4) : pc;
+      }
+      float west = __shfl_up_sync(0xffffffffu, pc.w, 1, L);
+      float east = __shfl_down_sync(0xffffffffu, pc.x, 1, L);
+      if (sl == 0) west = has_w ? P1(4 * c4 - 1) : pc.x;
       else if (!has_w) west = pc.x;
-      if (lane == 31) east = has_e ? P1(4 * c4 + 4) : pc.w;
+      if (sl == L - 1) east = has_e ? P1(4 * c4 + 4) : pc.w;
       else if (!has_e) east = pc.w;
       float4 q;
       if (!VEL) {
@@ -405,6 +475,11 @@ __device__ __forceinline__ void march_f32(const GArgs& a, F4 P4, F1 P1, E emit) 
       if (on) emit(c4, pc, q);
       pm = pc;
       pc = pp;
+      if (PF) {
+        pp = pp2;
+        ps = ps2;
+        pn = pn2;
+      }
       c4 += sz4;
     }
   }
@@ -417,31 +492,47 @@ __device__ __forceinline__ void march_f32(const GArgs& a, F4 P4, F1 P1, E emit) 
 // p.Ap = sum over neighbour pairs of the squared difference), which needs p
 // only at the +x, +y and +z neighbours.  One warp covers 128 x cells of one
 // row, +x by warp shuffles.
-template <typename F4, typename F1>
-__device__ __forceinline__ double edge_pass(const GArgs& a, F4 P4, F1 P1, float4* p4) {
+template <bool PF = false, typename F4, typename F1>
+__device__ __forceinline__ double edge_pass(const GArgs& a, F4 P4, F1 P1, float4* p4, Blk B = grid_blk()) {
   auto sq = [](float d) { return d * d; };
   const int my = a.my, mz = a.mz, nx4 = a.mx >> 2;
   const size_t sy4 = size_t(nx4), sz4 = size_t(nx4) * my;
-  const int lane = threadIdx.x;
+  const int lane = threadIdx.x, L = a.lpr, sl = lane & (L - 1), seg = lane / L, rpw = 32 / L;
   double acc = 0.0;
   const int items = a.w32x * a.w32y * a.w32z;
-  for (int w = blockIdx.x; w < items; w += gridDim.x) {
+  for (int w = B.bid; w < items; w += B.nb) {
     const int wx = w % a.w32x, wy = (w / a.w32x) % a.w32y, wz = w / (a.w32x * a.w32y);
-    const int i4 = wx * 32 + lane, j = wy * 8 + threadIdx.y, k0 = wz * kZ32;
-    if (j >= my) continue;  // the whole warp (one row per warp)
-    const bool on = i4 < nx4;
+    const int i4 = wx * L + sl, j0 = (wy * 8 + threadIdx.y) * rpw, k0 = wz * kZ32;
+    if (j0 >= my) continue;  // the whole warp
+    const bool row = j0 + seg < my;
+    const int j = row ? j0 + seg : my - 1;  // rows past the grid shadow the last row
+    const bool on = row && i4 < nx4;
     const bool has_e = i4 + 1 < nx4;
-    size_t c4 = (size_t(k0) * my + j) * nx4 + (on ? i4 : nx4 - 1);  // idle lanes shadow the last column
+    size_t c4 = (size_t(k0) * my + j) * nx4 + (i4 < nx4 ? i4 : nx4 - 1);  // idle lanes shadow the last column
     float4 pc = P4(c4);
+    float4 pp, pn;
+    if (PF) {
+      pp = k0 < mz - 1 ? P4(c4 + sz4) : pc;
+      pn = j < my - 1 ? P4(c4 + sy4) : pc;
+    }
 #pragma unroll
     for (int kk = 0; kk < kZ32; ++kk) {
       const int k = k0 + kk;
       if (k >= mz) break;
-      const bool up = k < mz - 1;
-      const float4 pp = up ? P4(c4 + sz4) : pc;
-      const float4 pn = j < my - 1 ? P4(c4 + sy4) : pc;
-      float east = __shfl_down_sync(0xffffffffu, pc.x, 1);
-      if (lane == 31) east = has_e ? P1(4 * c4 + 4) : pc.w;
+      float4 pp2, pn2;
+      if (PF) {
+        pp2 = pp;
+        pn2 = pp;
+        if (kk + 1 < kZ32 && k + 1 < mz) {
+          pp2 = k + 1 < mz - 1 ? P4(c4 + 2 * sz4) : pp;
+          pn2 = j < my - 1 ? P4(c4 + sz4 + sy4) : pp;
+        }
+      } else {
+        pp = k < mz - 1 ? P4(c4 + sz4) : pc;
+        pn = j < my - 1 ? P4(c4 + sy4) : pc;
+      }
+      float east = __shfl_down_sync(0xffffffffu, pc.x, 1, L);
+      if (sl == L - 1) east = has_e ? P1(4 * c4 + 4) : pc.w;
       else if (!has_e) east = pc.w;
       if (on) {
         p4[c4] = pc;
@@ -453,6 +544,10 @@ __device__ __forceinline__ double edge_pass(const GArgs& a, F4 P4, F1 P1, float4
         acc += double(e);
       }
       pc = pp;
+      if (PF) {
+        pp = pp2;
+        pn = pn2;
+      }
       c4 += sz4;
     }
   }
@@ -534,15 +629,18 @@ __global__ void __launch_bounds__(kGThreads, 4) g_dir_v(const GArgs a) {
 // The update pass over the float4 lanes: q = A p again from the stored p
 // (pnew), x32 += alpha p, r32 -= alpha q; returns this thread's part of
 // |r32|^2.
-template <bool VEL>
-__device__ __forceinline__ double upd_pass(const GArgs& a, float alpha, const float* pnew) {
+// NC: p may be read through the non-coherent path (it was written by an
+// earlier kernel; false in the batched launch, where other blocks of the
+// same launch wrote it).
+template <bool VEL, bool NC = true, bool PF = false>
+__device__ __forceinline__ double upd_pass(const GArgs& a, float alpha, const float* pnew, Blk B = grid_blk()) {
   const float4* p4 = reinterpret_cast<const float4*>(pnew);
   float4* d4 = reinterpret_cast<float4*>(a.d32);
   float4* r4 = reinterpret_cast<float4*>(a.r32);
-  auto P4 = [&](size_t e) { return __ldg(p4 + e); };
-  auto P1 = [&](size_t e) { return __ldg(pnew + e); };
+  auto P4 = [&](size_t e) { return NC ? __ldg(p4 + e) : p4[e]; };
+  auto P1 = [&](size_t e) { return NC ? __ldg(pnew + e) : pnew[e]; };
   double acc = 0.0;
-  march_f32<VEL>(a, P4, P1, [&](size_t c4, const float4& pv, const float4& qv) {
+  march_f32<VEL, PF>(a, P4, P1, [&](size_t c4, const float4& pv, const float4& qv) {
     float4 dv = d4[c4], rv = r4[c4];
     dv.x = fmaf(alpha, pv.x, dv.x);
     dv.y = fmaf(alpha, pv.y, dv.y);
@@ -555,7 +653,7 @@ __device__ __forceinline__ double upd_pass(const GArgs& a, float alpha, const fl
     d4[c4] = dv;
     r4[c4] = rv;
     acc += double(fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, fmaf(rv.z, rv.z, rv.w * rv.w))));
-  });
+  }, B);
   return acc;
 }
 
@@ -600,12 +698,12 @@ __global__ void __launch_bounds__(kGThreads, kIterBlocks) g_upd(const GArgs a) {
 // contributions are summed in FP32, then in FP64.
 // ---------------------------------------------------------------------------
 template <typename F1, typename E>
-__device__ __forceinline__ double march_s32(const GArgs& a, F1 P, E emit) {
+__device__ __forceinline__ double march_s32(const GArgs& a, F1 P, E emit, Blk B = grid_blk()) {
   const int mx = a.mx, my = a.my, mz = a.mz;
   const size_t sy = size_t(mx), sz = size_t(mx) * my;
   double acc = 0.0;
   const int items = a.w32x * a.w32y * a.w32z;
-  for (int w = blockIdx.x; w < items; w += gridDim.x) {
+  for (int w = B.bid; w < items; w += B.nb) {
     const int wx = w % a.w32x, wy = (w / a.w32x) % a.w32y, wz = w / (a.w32x * a.w32y);
     const int i = wx * 32 + threadIdx.x, j = wy * 8 + threadIdx.y, k0 = wz * kZ32;
     if (i >= mx || j >= my) continue;
@@ -941,12 +1039,13 @@ __global__ void __launch_bounds__(kGThreads) g_gsum(const GArgs a) {
 __global__ void __launch_bounds__(kGThreads) g_gres(const GArgs a) {
   GState* S = a.S;
   count_kernel(S);
+  const Blk B = grid_blk();
   const int mx = a.mx, my = a.my, mz = a.mz;
   const size_t sy = size_t(mx), sz = size_t(mx) * my;
   const double mean = S->gmean;
   double sr = 0.0;
   const int items = a.w64x * a.w64y * a.w64z;
-  for (int w = blockIdx.x; w < items; w += gridDim.x) {
+  for (int w = B.bid; w < items; w += B.nb) {
     const int wx = w % a.w64x, wy = (w / a.w64x) % a.w64y, wz = w / (a.w64x * a.w64y);
     const int i = wx * 32 + threadIdx.x, j = wy * 8 + threadIdx.y, k0 = wz * kZ64;
     if (i >= mx || j >= my) continue;
@@ -1064,6 +1163,276 @@ __global__ void __launch_bounds__(kGThreads) g_shift(const GArgs a) {
     st->b_norm = sqrt(S->bb);
     st->rel_resid = S->bb > 0.0 ? sqrt(S->rr / S->bb) : 0.0;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Batched form: many independent systems (the cavities of a batch, one
+// operator kind per launch) in one persistent cooperative launch.  Problem
+// k owns the blocks [starts[k], starts[k+1]) and runs the whole solve of
+// the graph form on them: the same passes (float4 lanes where the grid's
+// width is a multiple of 4, scalar lanes otherwise), the same FP32
+// recurrence, refinement rule and gauge, with the loop control in registers
+// (every block of a problem holds the same bits) and a problem-wide
+// reduction (reduce_all) wherever the graph form ends a kernel.  Problems
+// never wait on each other.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bounded wait (thread 0) until the problem's reduction generation reaches
+// `target`.  Gives up, recording CFD_ERR_TIMEOUT in ctrl->error, once
+// timeout_ns have passed (checked on the first unsatisfied poll and every 64
+// polls after it, so a limit of 0 gives up at once), and also when another
+// block of the problem has given up.
+__device__ bool wait_gen(SolveCtrl* ctrl, unsigned target, unsigned long long timeout_ns) {
+  const unsigned* gen = reinterpret_cast<const unsigned*>(&ctrl->pad[0]);
+  const unsigned long long t0 = global_ns();
+  unsigned polls = 0;
+  while (int(ld_acquire_gpu(gen) - target) < 0) {
+    if ((polls++ & 63u) == 0) {
+      if (ld_volatile_s32(&ctrl->error) != 0) return false;
+      if (global_ns() - t0 >= timeout_ns) {
+        atomicCAS(&ctrl->error, 0, kErrTimeout);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
+// Problem-wide form of reduce_last: the same slots and summation order, but
+// every block of the problem obtains the totals.  The block that arrives
+// last sums the slots, stores the totals beside them and raises the
+// generation to `target` with a release; the others wait for it (acquire)
+// and read the totals.  Because no block enters the next reduction before
+// the generation is raised, the slots and totals are never overwritten
+// while still being read, and every store a block made before arriving is
+// visible to every block after the reduction.  Returns false (in every
+// thread of the block) when the wait gave up.
+template <int K>
+__device__ bool reduce_all(const double (&v)[K], const GArgs& a, unsigned target, double (&out)[K], Blk B) {
+  __shared__ double sh[K][kGThreads / 32];
+  __shared__ int s_ok;
+  double* tot = a.part + size_t(kPartSlots - 1) * kGMax;  // totals: the last slot row (K < kPartSlots)
+  if (arrive_slots<K>(v, a.part, &a.ctrl->arrive, sh, B)) {
+    sum_slots<K>(a.part, sh, out, B);
+    if (ftid() == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) tot[k] = out[k];
+      st_release_gpu(reinterpret_cast<unsigned*>(&a.ctrl->pad[0]), target);
+    }
+    __syncthreads();  // every thread has read sh before the next reduction writes it
+    return true;
+  }
+  if (ftid() == 0) s_ok = wait_gen(a.ctrl, target, a.timeout_ns) ? 1 : 0;
+  __syncthreads();
+  if (!s_ok) return false;
+#pragma unroll
+  for (int k = 0; k < K; ++k) out[k] = __ldcg(tot + k);
+  return true;
+}
+
+#ifndef CFD_IRB_BLOCKS
+#define CFD_IRB_BLOCKS 4
+#endif
+#ifndef CFD_IRB_PF
+#define CFD_IRB_PF 0
+#endif
+constexpr bool kBatchPrefetch = CFD_IRB_PF != 0;
+template <bool VEL>
+__global__ void __launch_bounds__(kGThreads, CFD_IRB_BLOCKS) irb_kernel(const GArgs* __restrict__ tab,
+                                                           const int* __restrict__ starts, int nprob) {
+  int lo = 0, hi = nprob - 1;
+  const int blk = int(blockIdx.x);
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (starts[mid] <= blk) lo = mid;
+    else hi = mid - 1;
+  }
+  const GArgs& a = tab[lo];
+  const Blk B{blk - starts[lo], starts[lo + 1] - starts[lo]};
+  const bool vec = a.mx % 4 == 0;
+  const double n = double(a.n);
+  unsigned gen = 0;
+  bool ok_sync = true;
+  auto all = [&](auto& v, auto& o) {
+    ok_sync = ok_sync && reduce_all(v, a, ++gen, o, B);
+    return ok_sync;
+  };
+
+  // prologue: mean of b, then r = b' - A x0 (g_pro_sum, g_resid64<0>)
+  double shift = 0.0;
+  if (a.remove_mean) {
+    double s1[1] = {0.0}, o1[1];
+    for (size_t e = size_t(B.bid) * kGThreads + ftid(); e < a.n; e += size_t(B.nb) * kGThreads) s1[0] += a.b[e];
+    if (!all(s1, o1)) goto out;
+    shift = o1[0] / n;
+  }
+  {
+    double v3[3], o3[3];
+    resid64_pass<0>(a, shift, false, a.zero_x0 != 0, v3, B);
+    if (!all(v3, o3)) goto out;
+    const double bb = o3[0];
+    double rr = o3[1], rsum = o3[2];
+    const double tol2 = a.rtol * a.rtol * bb, delta2 = a.delta * a.delta;
+    int status = kErrNotConverged, iters = 0, refinements = 0;
+    bool pending = false, first = true;
+    int cur = 0;
+    double rz = 0.0, beta = 0.0;
+    if (bb == 0.0) {
+      status = kOk;
+      rr = 0.0;
+    } else {
+      for (;;) {
+        // outer pass (g_prep): fold x32, load r32 = r - mean(r) unless leaving
+        const bool okr = rr <= tol2;
+        const bool leave = okr || refinements > a.max_outer || iters >= a.max_iters;
+        const bool fold = pending;
+        const double rmean = a.kind == kOpPressure ? rsum / n : 0.0;
+        float f = 0.f;
+        for (size_t e = size_t(B.bid) * kGThreads + ftid(); e < a.n; e += size_t(B.nb) * kGThreads) {
+          if (fold) a.x[e] += double(a.d32[e]);
+          if (!leave) {
+            const float v = float(a.r[e] - rmean);
+            a.r32[e] = v;
+            f = fmaf(v, v, f);
+          }
+          if (fold || !leave) a.d32[e] = 0.f;
+        }
+        double v1[1] = {double(f)}, o1[1];
+        if (!all(v1, o1)) goto out;
+        pending = false;
+        if (leave) {
+          if (okr) status = kOk;
+          break;
+        }
+        if (!first) beta = o1[0] / rz;  // keep the direction across the refinement
+        rz = o1[0];
+        const double rz_ref = rr;
+        // inner loop (g_dir / g_upd, or their velocity and scalar forms)
+        bool refine = false, broke = false;
+        for (;;) {
+          float* pnew = cur ? a.p1 : a.p0;
+          const float* pold = cur ? a.p0 : a.p1;
+          const float b32 = float(beta);
+          const bool fst = first;
+          double vd[1], od[1];
+          if (vec) {
+            const float4* r4 = reinterpret_cast<const float4*>(a.r32);
+            const float4* o4 = reinterpret_cast<const float4*>(pold);
+            auto P4 = [&](size_t e) {
+              const float4 rv = r4[e];
+              if (fst) return rv;
+              const float4 ov = o4[e];
+              return make_float4(fmaf(b32, ov.x, rv.x), fmaf(b32, ov.y, rv.y), fmaf(b32, ov.z, rv.z),
+                                 fmaf(b32, ov.w, rv.w));
+            };
+            auto P1 = [&](size_t e) { return fst ? a.r32[e] : fmaf(b32, pold[e], a.r32[e]); };
+            if (!VEL) {
+              vd[0] = edge_pass<kBatchPrefetch>(a, P4, P1, reinterpret_cast<float4*>(pnew), B);
+            } else {
+              float4* p4 = reinterpret_cast<float4*>(pnew);
+              double acc = 0.0;
+              march_f32<true, kBatchPrefetch>(a, P4, P1, [&](size_t c4, const float4& pc, const float4& q) {
+                p4[c4] = pc;
+                acc += double(fmaf(pc.x, q.x, fmaf(pc.y, q.y, fmaf(pc.z, q.z, pc.w * q.w))));
+              }, B);
+              vd[0] = acc;
+            }
+          } else {
+            auto P = [&](size_t e) { return fst ? a.r32[e] : fmaf(b32, pold[e], a.r32[e]); };
+            vd[0] = march_s32(a, P, [&](size_t c, float pc, float q) {
+              pnew[c] = pc;
+              return pc * q;
+            }, B);
+          }
+          if (!all(vd, od)) goto out;
+          if (!(od[0] > 0.0) || !isfinite(od[0])) {
+            broke = true;
+            break;
+          }
+          const double alpha = rz / od[0];
+          double vu[1], ou[1];
+          if (vec) {
+            vu[0] = upd_pass<VEL, false, kBatchPrefetch>(a, float(alpha), pnew, B);
+          } else {
+            const float al = float(alpha);
+            vu[0] = march_s32(a, [&](size_t e) { return pnew[e]; }, [&](size_t c, float pc, float q) {
+              a.d32[c] = fmaf(al, pc, a.d32[c]);
+              const float rv = fmaf(-al, q, a.r32[c]);
+              a.r32[c] = rv;
+              return rv * rv;
+            }, B);
+          }
+          if (!all(vu, ou)) goto out;
+          const double rz_new = ou[0];
+          first = false;
+          cur ^= 1;
+          iters += 1;
+          pending = true;
+          if (rz_new <= delta2 * rz_ref || rz_new <= tol2) {
+            refine = true;  // beta of the next direction comes from the replaced residual
+            break;
+          }
+          beta = rz_new / rz;
+          rz = rz_new;
+          if (iters >= a.max_iters) break;
+        }
+        if (broke) status = kErrBreakdown;
+        if (!refine) break;
+        // refinement (g_resid64<1>): r = b - A (x + x32)
+        resid64_pass<1>(a, 0.0, true, false, v3, B);
+        if (!all(v3, o3)) goto out;
+        rr = o3[1];
+        rsum = o3[2];
+        refinements += 1;
+      }
+      // epilogue (g_resid64<2>)
+      if (status != kOk) {
+        resid64_pass<2>(a, 0.0, pending, false, v3, B);
+        if (!all(v3, o3)) goto out;
+        rr = o3[1];
+        if (status == kErrNotConverged && rr <= tol2) status = kOk;
+      }
+    }
+    // g_finish: fold x32 (x := 0 when b = 0), mean of x for the gauge
+    {
+      const bool zero = bb == 0.0;
+      double s1[1] = {0.0}, o1[1];
+      for (size_t e = size_t(B.bid) * kGThreads + ftid(); e < a.n; e += size_t(B.nb) * kGThreads) {
+        double xv = zero ? 0.0 : a.x[e];
+        if (!zero && pending) xv += double(a.d32[e]);
+        if (zero || pending) a.x[e] = xv;
+        s1[0] += xv;
+      }
+      if (!all(s1, o1)) goto out;
+      // g_shift
+      if (a.gauge) {
+        const double sh = a.gauge_value - o1[0] / n;
+        for (size_t e = size_t(B.bid) * kGThreads + ftid(); e < a.n; e += size_t(B.nb) * kGThreads) a.x[e] += sh;
+      }
+      // every block has finished its part of the solve before the statistics
+      // are written
+      double z1[1] = {0.0}, zo[1];
+      if (!all(z1, zo)) goto out;
+    }
+    if (B.bid == 0 && ftid() == 0) {
+      DevSolveStats* st = a.stats;
+      st->iters = iters;
+      st->outer_iters = refinements;
+      st->restarts = 0;
+      st->status = status;
+      st->b_norm = sqrt(bb);
+      st->rel_resid = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    }
+    return;
+  }
+out:
+  // a wait gave up (this or another block of the problem): the solve ends
+  // with CFD_ERR_TIMEOUT, x holds what the passes left
+  if (B.bid == 0 && ftid() == 0) a.stats->status = kErrTimeout;
 }
 
 // One resident wave of `kernel`, at most kGMax blocks and `work` items.
@@ -1213,6 +1582,7 @@ GArgs make_args(const IrArgs& ia, void* state_buf) {
   a.c = ia.c;
   a.c32 = float(ia.c);
   const bool vec = use_vec_kernels(ia);
+  a.lpr = 32;
   a.w32x = vec ? (a.mx / 4 + 31) / 32 : (a.mx + 31) / 32;
   a.w32y = (a.my + 7) / 8;
   a.w32z = (a.mz + kZ32 - 1) / kZ32;
@@ -1388,6 +1758,76 @@ cudaError_t launch_learned_guess(const IrArgs& ia, void* state_buf, cudaStream_t
   g_gset<<<wave_blocks(g_gset, vec_work * 4), kGThreads, 0, s>>>(a);
   if (launches) *launches += nk;  // the four guess kernels count themselves on the device
   return cudaGetLastError();
+}
+
+namespace {
+// Batched launch, float4 lanes: as many lanes per row as the row needs
+// (a power of two from 4 to 32), so that narrow grids keep every lane busy
+// and the blocks of a problem march through fewer (row, plane) steps.
+void set_batch_lanes(GArgs& g) {
+  if (g.mx % 4 != 0) return;  // scalar lanes
+  const int nx4 = g.mx / 4;
+  int L = 4;
+  while (L < nx4 && L < 32) L *= 2;
+  g.lpr = L;
+  g.w32x = (nx4 + L - 1) / L;
+  const int rows = 8 * (32 / L);
+  g.w32y = (g.my + rows - 1) / rows;
+}
+}  // namespace
+
+void ir_batch_work(const IrArgs& ia, int* items, int* extent) {
+  GArgs g{};
+  g.mx = ia.g.mx;
+  g.my = ia.g.my;
+  g.mz = ia.g.mz;
+  g.w32x = (g.mx + 31) / 32;  // scalar lanes
+  g.w32y = (g.my + 7) / 8;
+  g.w32z = (g.mz + kZ32 - 1) / kZ32;
+  set_batch_lanes(g);
+  *items = g.w32x * g.w32y * g.w32z;
+  *extent = ia.g.mx > ia.g.my ? (ia.g.mx > ia.g.mz ? ia.g.mx : ia.g.mz) : (ia.g.my > ia.g.mz ? ia.g.my : ia.g.mz);
+}
+
+size_t ir_batch_table_bytes(int nprob) { return sizeof(GArgs) * size_t(nprob > 0 ? nprob : 0); }
+
+cudaError_t ir_batch_table(const IrArgs* args, void* const* states, int nprob, void* d_table, cudaStream_t s) {
+  std::vector<GArgs> t(size_t(nprob > 0 ? nprob : 0));
+  for (int k = 0; k < nprob; ++k) {
+    GArgs g = make_args(args[k], states[k]);
+    set_batch_lanes(g);
+    g.ctrl = args[k].ctrl;
+    g.stats = args[k].stats;
+    g.timeout_ns = args[k].timeout_ns;
+    t[size_t(k)] = g;
+  }
+  cudaError_t e = cudaMemcpyAsync(d_table, t.data(), ir_batch_table_bytes(nprob), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // t is released on return
+  return e;
+}
+
+int ir_batch_blocks_per_sm(int vel) {
+  int b = 0;
+  if (vel) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, irb_kernel<true>, kGThreads, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, irb_kernel<false>, kGThreads, 0);
+  return b;
+}
+
+cudaError_t launch_ir_batch(const void* d_table, const int* d_starts, int nprob, int total_blocks, int vel,
+                            cudaStream_t s, int64_t* launches) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(total_blocks));
+  cfg.blockDim = dim3(32, 8);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (launches) *launches += 1;
+  const GArgs* t = static_cast<const GArgs*>(d_table);
+  return vel ? cudaLaunchKernelEx(&cfg, irb_kernel<true>, t, d_starts, nprob)
+             : cudaLaunchKernelEx(&cfg, irb_kernel<false>, t, d_starts, nprob);
 }
 
 cudaError_t ir_graph_kernel_count(const void* state_buf, cudaStream_t s, long long* out) {

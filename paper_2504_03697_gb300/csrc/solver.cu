@@ -142,15 +142,11 @@ cudaError_t launch_cg(const CgArgs& a_in, const LaunchGeom& lg, cudaStream_t s, 
   return err;
 }
 
-int batch_blocks_per_sm(int ir) {
-  int b = 0;
-  if (ir) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ir_kernel_multi(), kSolveThreads, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cg_kernel_for(1, 0, true), kSolveThreads, 0);
-  int b0 = 0;
-  if (!ir) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, cg_kernel_for(0, 0, true), kSolveThreads, 0);
-    b = b0 < b ? b0 : b;
-  }
+int batch_blocks_per_sm() {
+  int b = 0, b0 = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cg_kernel_for(1, 0, true), kSolveThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, cg_kernel_for(0, 0, true), kSolveThreads, 0);
+  b = b0 < b ? b0 : b;
   return b > 4 ? 4 : b;
 }
 
@@ -174,21 +170,6 @@ cudaError_t launch_cg_multi(const CgArgs* d_table, const int* d_starts, int npro
                             cudaStream_t s, int64_t* launches) {
   if (launches) *launches += 1;
   return launch_coop(cg_kernel_for(precond, 0, true), d_table, d_starts, nprob, total_blocks, s);
-}
-
-cudaError_t launch_ir_multi(const IrArgs* d_table, const int* d_starts, int nprob, int total_blocks, cudaStream_t s,
-                            int64_t* launches) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(total_blocks);
-  cfg.blockDim = dim3(kSolveThreads);
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if (launches) *launches += 1;
-  return cudaLaunchKernelEx(&cfg, ir_kernel_multi(), IrArgs{}, d_table, d_starts, nprob);
 }
 
 int solve_tile_depth_for(GridDims g, int blocks) {

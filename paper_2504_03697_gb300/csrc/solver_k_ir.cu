@@ -1,4 +1,5 @@
-// Instantiations of the FP32-CG / FP64-refinement kernel (one problem, many problems).
+// Instantiation of the FP32-CG / FP64-refinement kernel (one problem; batches
+// run the batched graph-form solve of ir_graph.cu).
 
 #include "solver_impl.cuh"
 #include "solver_kernels.h"
@@ -6,7 +7,5 @@
 namespace cfd {
 
 IrKernel ir_kernel_single() { return ir_kernel<false>; }
-
-IrKernel ir_kernel_multi() { return ir_kernel<true>; }
 
 }  // namespace cfd

@@ -22,6 +22,5 @@ CgKernel cg_kernel_multi(int precond);
 Cg1Kernel cg1_kernel(int rtz);
 // FP32 CG with FP64 refinement: one problem / many problems
 IrKernel ir_kernel_single();
-IrKernel ir_kernel_multi();
 
 }  // namespace cfd

@@ -118,7 +118,10 @@ __device__ __forceinline__ double face_avg(const double* __restrict__ f, int c, 
   return 0.25 * s;
 }
 
-__global__ void __launch_bounds__(kSweepThreads) advect_kernel(PhysArgs a) {
+// Each sweep is a body over the elements t0, t0 + stride, ... of one cavity:
+// the whole grid in the single-cavity kernels, the cavity's block range in
+// the batched ones (sweep_multi_kernel).
+__device__ __forceinline__ void advect_body(const PhysArgs& a, size_t t0, size_t stride) {
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const size_t n0 = size_t(nx + 1) * ny * nz;
   const size_t n1 = size_t(nx) * (ny + 1) * nz;
@@ -126,7 +129,7 @@ __global__ void __launch_bounds__(kSweepThreads) advect_kernel(PhysArgs a) {
   const double ext[3] = {nx * a.h, ny * a.h, nz * a.h};
   const double* fields[3] = {a.u, a.v, a.w};
   double* outs[3] = {a.ua, a.va, a.wa};
-  for (size_t e = gtid(); e < n0 + n1 + n2; e += gstride()) {
+  for (size_t e = t0; e < n0 + n1 + n2; e += stride) {
     int comp;
     size_t l;
     if (e < n0) { comp = 0; l = e; }
@@ -175,12 +178,14 @@ __global__ void __launch_bounds__(kSweepThreads) advect_kernel(PhysArgs a) {
   }
 }
 
-__global__ void __launch_bounds__(kSweepThreads) forces_kernel(PhysArgs a) {
+__global__ void __launch_bounds__(kSweepThreads) advect_kernel(PhysArgs a) { advect_body(a, gtid(), gstride()); }
+
+__device__ __forceinline__ void forces_body(const PhysArgs& a, size_t t0, size_t stride) {
   // top cell layer j = ny - 1 of each component, non-wall-normal faces only
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const size_t n0 = size_t(nx + 1) * nz, n1 = size_t(nx) * nz, n2 = size_t(nx) * (nz + 1);
   double* fs[3] = {a.u, a.v, a.w};
-  for (size_t e = gtid(); e < n0 + n1 + n2; e += gstride()) {
+  for (size_t e = t0; e < n0 + n1 + n2; e += stride) {
     int comp;
     size_t l;
     if (e < n0) { comp = 0; l = e; }
@@ -197,12 +202,21 @@ __global__ void __launch_bounds__(kSweepThreads) forces_kernel(PhysArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(kSweepThreads) forces_kernel(PhysArgs a) { forces_body(a, gtid(), gstride()); }
+
 // b = ua_c (+ c * 2 lid_u on u faces touching the lid); zero on wall rows.
-__global__ void __launch_bounds__(kSweepThreads) diffusion_rhs_kernel(PhysArgs a, int comp, double lid_term) {
+// lid_term = c * (2 lid_u), c = nu dt / h^2.
+__host__ __device__ __forceinline__ double diffusion_lid_term(const PhysArgs& a) {
+  const double c = a.nu * a.dt / (a.h * a.h);
+  return c * (2.0 * a.lid_u);
+}
+
+__device__ __forceinline__ void diffusion_rhs_body(const PhysArgs& a, int comp, double lid_term, size_t t0,
+                                                   size_t stride) {
   const FaceDims fd = face_dims(comp, a.nx, a.ny, a.nz);
   const size_t n = size_t(fd.mx) * fd.my * fd.mz;
   const double* f = comp == 0 ? a.ua : (comp == 1 ? a.va : a.wa);
-  for (size_t e = gtid(); e < n; e += gstride()) {
+  for (size_t e = t0; e < n; e += stride) {
     const int i = int(e % fd.mx), j = int((e / fd.mx) % fd.my), k = int(e / (size_t(fd.mx) * fd.my));
     const int own = comp == 0 ? i : (comp == 1 ? j : k);
     const int own_n = comp == 0 ? a.nx : (comp == 1 ? a.ny : a.nz);
@@ -215,10 +229,17 @@ __global__ void __launch_bounds__(kSweepThreads) diffusion_rhs_kernel(PhysArgs a
   }
 }
 
-__global__ void __launch_bounds__(kSweepThreads) divergence_kernel(PhysArgs a, double scale) {
+__global__ void __launch_bounds__(kSweepThreads) diffusion_rhs_kernel(PhysArgs a, int comp, double lid_term) {
+  diffusion_rhs_body(a, comp, lid_term, gtid(), gstride());
+}
+
+// scale = -(rho h / dt)
+__host__ __device__ __forceinline__ double divergence_scale(const PhysArgs& a) { return -(a.rho * a.h / a.dt); }
+
+__device__ __forceinline__ void divergence_body(const PhysArgs& a, double scale, size_t t0, size_t stride) {
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const size_t n = size_t(nx) * ny * nz;
-  for (size_t e = gtid(); e < n; e += gstride()) {
+  for (size_t e = t0; e < n; e += stride) {
     const int i = int(e % nx), j = int((e / nx) % ny), k = int(e / (size_t(nx) * ny));
     const double du = a.ua[idx3(i + 1, j, k, nx + 1, ny)] - a.ua[idx3(i, j, k, nx + 1, ny)];
     const double dv = a.va[idx3(i, j + 1, k, nx, ny + 1)] - a.va[idx3(i, j, k, nx, ny + 1)];
@@ -227,12 +248,19 @@ __global__ void __launch_bounds__(kSweepThreads) divergence_kernel(PhysArgs a, d
   }
 }
 
-__global__ void __launch_bounds__(kSweepThreads) correct_kernel(PhysArgs a, double s) {
+__global__ void __launch_bounds__(kSweepThreads) divergence_kernel(PhysArgs a, double scale) {
+  divergence_body(a, scale, gtid(), gstride());
+}
+
+// s = dt / (rho h)
+__host__ __device__ __forceinline__ double correct_scale(const PhysArgs& a) { return a.dt / (a.rho * a.h); }
+
+__device__ __forceinline__ void correct_body(const PhysArgs& a, double s, size_t t0, size_t stride) {
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const size_t n0 = size_t(nx + 1) * ny * nz;
   const size_t n1 = size_t(nx) * (ny + 1) * nz;
   const size_t n2 = size_t(nx) * ny * (nz + 1);
-  for (size_t e = gtid(); e < n0 + n1 + n2; e += gstride()) {
+  for (size_t e = t0; e < n0 + n1 + n2; e += stride) {
     int comp;
     size_t l;
     if (e < n0) { comp = 0; l = e; }
@@ -253,6 +281,33 @@ __global__ void __launch_bounds__(kSweepThreads) correct_kernel(PhysArgs a, doub
                                 : (comp == 1 ? a.p[idx3(i, j - 1, k, nx, ny)] : a.p[idx3(i, j, k - 1, nx, ny)]);
     out[l] = in[l] - s * (pc - pm);
   }
+}
+
+__global__ void __launch_bounds__(kSweepThreads) correct_kernel(PhysArgs a, double s) {
+  correct_body(a, s, gtid(), gstride());
+}
+
+// Batched sweeps: one launch over many cavities, cavity k on the blocks
+// [starts[k], starts[k+1]) (op: SweepOp; comp: the diffusion component).
+template <int OP>
+__global__ void __launch_bounds__(kSweepThreads) sweep_multi_kernel(const PhysArgs* __restrict__ tab,
+                                                                    const int* __restrict__ starts, int nprob,
+                                                                    int comp) {
+  int lo = 0, hi = nprob - 1;
+  const int blk = int(blockIdx.x);
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (starts[mid] <= blk) lo = mid;
+    else hi = mid - 1;
+  }
+  const PhysArgs& a = tab[lo];
+  const size_t t0 = size_t(blk - starts[lo]) * blockDim.x + threadIdx.x;
+  const size_t st = size_t(starts[lo + 1] - starts[lo]) * blockDim.x;
+  if (OP == kSweepAdvect) advect_body(a, t0, st);
+  else if (OP == kSweepForces) forces_body(a, t0, st);
+  else if (OP == kSweepDiffusionRhs) diffusion_rhs_body(a, comp, diffusion_lid_term(a), t0, st);
+  else if (OP == kSweepDivergence) divergence_body(a, divergence_scale(a), t0, st);
+  else correct_body(a, correct_scale(a), t0, st);
 }
 
 __global__ void __launch_bounds__(kSweepThreads) zero_wall_faces_kernel(PhysArgs a) {
@@ -371,25 +426,21 @@ cudaError_t launch_forces(const PhysArgs& a, cudaStream_t s, int64_t* launches) 
 
 cudaError_t launch_diffusion_rhs(const PhysArgs& a, int comp, cudaStream_t s, int64_t* launches) {
   const size_t n = size_t(a.nx + (comp == 0)) * (a.ny + (comp == 1)) * (a.nz + (comp == 2));
-  const double c = a.nu * a.dt / (a.h * a.h);
-  const double lid_term = c * (2.0 * a.lid_u);
-  diffusion_rhs_kernel<<<sweep_blocks(n), kSweepThreads, 0, s>>>(a, comp, lid_term);
+  diffusion_rhs_kernel<<<sweep_blocks(n), kSweepThreads, 0, s>>>(a, comp, diffusion_lid_term(a));
   if (launches) *launches += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_divergence(const PhysArgs& a, cudaStream_t s, int64_t* launches) {
   const size_t n = size_t(a.nx) * a.ny * a.nz;
-  const double scale = -(a.rho * a.h / a.dt);
-  divergence_kernel<<<sweep_blocks(n), kSweepThreads, 0, s>>>(a, scale);
+  divergence_kernel<<<sweep_blocks(n), kSweepThreads, 0, s>>>(a, divergence_scale(a));
   if (launches) *launches += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_correct(const PhysArgs& a, cudaStream_t s, int64_t* launches) {
   const size_t n = size_t(a.nx + 1) * a.ny * a.nz + size_t(a.nx) * (a.ny + 1) * a.nz + size_t(a.nx) * a.ny * (a.nz + 1);
-  const double sc = a.dt / (a.rho * a.h);
-  correct_kernel<<<sweep_blocks(n), kSweepThreads, 0, s>>>(a, sc);
+  correct_kernel<<<sweep_blocks(n), kSweepThreads, 0, s>>>(a, correct_scale(a));
   if (launches) *launches += 1;
   return cudaGetLastError();
 }
@@ -397,6 +448,41 @@ cudaError_t launch_correct(const PhysArgs& a, cudaStream_t s, int64_t* launches)
 cudaError_t launch_zero_wall_faces(const PhysArgs& a, cudaStream_t s, int64_t* launches) {
   const size_t n = size_t(2) * (size_t(a.ny) * a.nz + size_t(a.nx) * a.nz + size_t(a.nx) * a.ny);
   zero_wall_faces_kernel<<<sweep_blocks(n), kSweepThreads, 0, s>>>(a);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
+size_t sweep_elems(const PhysArgs& a, int op, int comp) {
+  const size_t faces = size_t(a.nx + 1) * a.ny * a.nz + size_t(a.nx) * (a.ny + 1) * a.nz +
+                       size_t(a.nx) * a.ny * (a.nz + 1);
+  switch (op) {
+    case kSweepAdvect:
+    case kSweepCorrect:
+      return faces;
+    case kSweepForces:
+      return size_t(a.nx + 1) * a.nz + size_t(a.nx) * a.nz + size_t(a.nx) * (a.nz + 1);
+    case kSweepDiffusionRhs:
+      return size_t(a.nx + (comp == 0)) * (a.ny + (comp == 1)) * (a.nz + (comp == 2));
+    default:
+      return size_t(a.nx) * a.ny * a.nz;
+  }
+}
+
+int sweep_blocks_for(const PhysArgs& a, int op, int comp) { return sweep_blocks(sweep_elems(a, op, comp)); }
+
+cudaError_t launch_sweep_multi(int op, const PhysArgs* d_tab, const int* d_starts, int nprob, int total_blocks,
+                               int comp, cudaStream_t s, int64_t* launches) {
+  if (nprob <= 0) return cudaSuccess;
+  const dim3 g{unsigned(total_blocks)}, b{unsigned(kSweepThreads)};
+  switch (op) {
+    case kSweepAdvect: sweep_multi_kernel<kSweepAdvect><<<g, b, 0, s>>>(d_tab, d_starts, nprob, comp); break;
+    case kSweepForces: sweep_multi_kernel<kSweepForces><<<g, b, 0, s>>>(d_tab, d_starts, nprob, comp); break;
+    case kSweepDiffusionRhs:
+      sweep_multi_kernel<kSweepDiffusionRhs><<<g, b, 0, s>>>(d_tab, d_starts, nprob, comp);
+      break;
+    case kSweepDivergence: sweep_multi_kernel<kSweepDivergence><<<g, b, 0, s>>>(d_tab, d_starts, nprob, comp); break;
+    default: sweep_multi_kernel<kSweepCorrect><<<g, b, 0, s>>>(d_tab, d_starts, nprob, comp); break;
+  }
   if (launches) *launches += 1;
   return cudaGetLastError();
 }
