@@ -1439,7 +1439,7 @@ int batch_enqueue_step(cfd_batch* b) {
     ck(cudaMemsetAsync(b->d_ctrl + size_t(c) * n, 0, sizeof(SolveCtrl) * size_t(nd), b->stream), "memset ctrl");
     if (b->solver == CFD_SOLVER_IR)
       ck(launch_ir_batch(b->d_gir + size_t(c) * n * ir_batch_table_bytes(1), b->d_starts + size_t(c) * (n + 1), nd,
-                         b->total_blocks[c], 1, b->stream, &b->launches),
+                         b->total_blocks[c], kOpVelU + c, b->stream, &b->launches),
          "batched mixed-precision diffusion launch");
     else
       ck(launch_cg_multi(b->d_cg + size_t(c) * n, b->d_starts + size_t(c) * (n + 1), nd, b->total_blocks[c], 0,
@@ -1450,7 +1450,7 @@ int batch_enqueue_step(cfd_batch* b) {
   ck(cudaMemsetAsync(b->d_ctrl + size_t(3) * n, 0, sizeof(SolveCtrl) * size_t(n), b->stream), "memset ctrl");
   if (b->solver == CFD_SOLVER_IR)
     ck(launch_ir_batch(b->d_gir + size_t(3) * n * ir_batch_table_bytes(1), b->d_starts + size_t(4) * (n + 1), n,
-                       b->total_blocks[4], 0, b->stream, &b->launches),
+                       b->total_blocks[4], kOpPressure, b->stream, &b->launches),
        "batched pressure launch");
   else
     ck(launch_cg_multi(b->d_cg + size_t(3) * n, b->d_starts + size_t(3) * (n + 1), n, b->total_blocks[3], b->precond,
@@ -1547,7 +1547,7 @@ int cfd_batch_create(int n, const cfd_params* per_cavity, void* dev_ws, size_t b
     const std::vector<int>& idx = kind < 3 ? b->diff_idx : all;
     // the mixed-precision solves (diffusion kinds 0-2 and pressure kind 4)
     // run the batched graph-form kernel (one wave, at most 4 blocks per SM)
-    const int bps = (kind < 3 && mixed) || is_ir ? std::min(4, ir_batch_blocks_per_sm(kind < 3 ? 1 : 0))
+    const int bps = (kind < 3 && mixed) || is_ir ? std::min(4, ir_batch_blocks_per_sm(kind < 3 ? kOpVelU + kind : kOpPressure))
                                                  : batch_blocks_per_sm();
     const int total = bps * sms;
     const bool ir_kind = (kind < 3 && mixed) || is_ir;

@@ -407,10 +407,46 @@ __global__ void __launch_bounds__(kGThreads) g_prep(const GArgs a) {
 // One warp covers 128 x cells of one row; x neighbours by warp shuffles,
 // y neighbours by loads, z by marching kZ32 planes in registers.
 // ---------------------------------------------------------------------------
+// Four x-consecutive rows (cells i0 .. i0 + 3 of row j, plane k) of the
+// velocity matrix of component KIND - 1 (the rule of stencil_row, with the
+// same operations in the same order): the row and plane conditions are
+// decided once for the four cells, the x conditions only where i0 is at a
+// wall.  Neighbours outside the array arrive as the cell's own value.
+template <int KIND>
+__device__ __forceinline__ float4 vel_rows4(float c, int i0, int j, int k, int mx, int my, int mz, const float4& pc,
+                                            float west, float east, const float4& ps, const float4& pn,
+                                            const float4& pm, const float4& pp) {
+  constexpr int comp = KIND - 1;
+  const bool jlo = j == 0, jhi = j == my - 1, klo = k == 0, khi = k == mz - 1;
+  if ((comp == 1 && (jlo || jhi)) || (comp == 2 && (klo || khi))) return make_float4(0.f, 0.f, 0.f, 0.f);
+  const float xc[4] = {pc.x, pc.y, pc.z, pc.w};
+  const float s_[4] = {ps.x, ps.y, ps.z, ps.w}, n_[4] = {pn.x, pn.y, pn.z, pn.w};
+  const float m_[4] = {pm.x, pm.y, pm.z, pm.w}, p_[4] = {pp.x, pp.y, pp.z, pp.w};
+  float q[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int i = i0 + t;
+    const float g = -xc[t];
+    float xm = t == 0 ? west : xc[t - 1];
+    float xp = t == 3 ? east : xc[t + 1];
+    if (comp != 0) {
+      if (i == 0) xm = g;
+      if (i == mx - 1) xp = g;
+    }
+    const float ym = comp != 1 && jlo ? g : s_[t];
+    const float yp = comp != 1 && jhi ? g : n_[t];
+    const float zm = comp != 2 && klo ? g : m_[t];
+    const float zp = comp != 2 && khi ? g : p_[t];
+    const float lap = fmaf(6.f, xc[t], -(((((xm + xp) + ym) + yp) + zm) + zp));
+    q[t] = comp == 0 && (i == 0 || i == mx - 1) ? 0.f : fmaf(c, lap, xc[t]);
+  }
+  return make_float4(q[0], q[1], q[2], q[3]);
+}
+
 // PF: issue the next plane's loads before this plane's arithmetic and
 // stores (the batched launch, whose small grids are bound by the latency of
 // each plane's loads, not by bandwidth).
-template <bool VEL, bool PF = false, typename F4, typename F1, typename E>
+template <int KIND, bool PF = false, typename F4, typename F1, typename E>
 __device__ __forceinline__ void march_f32(const GArgs& a, F4 P4, F1 P1, E emit, Blk B = grid_blk()) {
   const int my = a.my, mz = a.mz, nx4 = a.mx >> 2;
   const size_t sy4 = size_t(nx4), sz4 = size_t(nx4) * my;
@@ -459,18 +495,13 @@ __device__ __forceinline__ void march_f32(const GArgs& a, F4 P4, F1 P1, E emit, 
       if (sl == L - 1) east = has_e ? P1(4 * c4 + 4) : pc.w;
       else if (!has_e) east = pc.w;
       float4 q;
-      if (!VEL) {
+      if (KIND == kOpPressure) {
         q.x = fmaf(6.f, pc.x, -(((((west + pc.y) + ps.x) + pn.x) + pm.x) + pp.x));
         q.y = fmaf(6.f, pc.y, -(((((pc.x + pc.z) + ps.y) + pn.y) + pm.y) + pp.y));
         q.z = fmaf(6.f, pc.z, -(((((pc.y + pc.w) + ps.z) + pn.z) + pm.z) + pp.z));
         q.w = fmaf(6.f, pc.w, -(((((pc.z + east) + ps.w) + pn.w) + pm.w) + pp.w));
       } else {  // velocity rows: wall and ghost rules by the cell's indices
-        const int i0 = 4 * i4, mx = a.mx, kd = a.kind;
-        const float c = a.c32;
-        q.x = stencil_row<float>(kd, c, i0, j, k, mx, my, mz, pc.x, west, pc.y, ps.x, pn.x, pm.x, pp.x);
-        q.y = stencil_row<float>(kd, c, i0 + 1, j, k, mx, my, mz, pc.y, pc.x, pc.z, ps.y, pn.y, pm.y, pp.y);
-        q.z = stencil_row<float>(kd, c, i0 + 2, j, k, mx, my, mz, pc.z, pc.y, pc.w, ps.z, pn.z, pm.z, pp.z);
-        q.w = stencil_row<float>(kd, c, i0 + 3, j, k, mx, my, mz, pc.w, pc.z, east, ps.w, pn.w, pm.w, pp.w);
+        q = vel_rows4<KIND>(a.c32, 4 * i4, j, k, a.mx, my, mz, pc, west, east, ps, pn, pm, pp);
       }
       if (on) emit(c4, pc, q);
       pm = pc;
@@ -591,6 +622,7 @@ __global__ void __launch_bounds__(kGThreads, kIterBlocks) g_dir(const GArgs a) {
 // inner body for the velocity matrices on float4 lanes (face grids whose
 // width is a multiple of 4): p = r32 + beta p_old formed at the 7 stencil
 // points, stored; p.q with q = H p on the fly (not stored); alpha = rz / p.q
+template <int KIND>
 __global__ void __launch_bounds__(kGThreads, 4) g_dir_v(const GArgs a) {
   GState* S = a.S;
   count_kernel(S);
@@ -610,7 +642,7 @@ __global__ void __launch_bounds__(kGThreads, 4) g_dir_v(const GArgs a) {
   };
   auto P1 = [&](size_t e) { return first ? __ldg(a.r32 + e) : fmaf(beta, __ldg(pold + e), __ldg(a.r32 + e)); };
   double acc = 0.0;
-  march_f32<true>(a, P4, P1, [&](size_t c4, const float4& pc, const float4& q) {
+  march_f32<KIND>(a, P4, P1, [&](size_t c4, const float4& pc, const float4& q) {
     p4[c4] = pc;
     acc += double(fmaf(pc.x, q.x, fmaf(pc.y, q.y, fmaf(pc.z, q.z, pc.w * q.w))));
   });
@@ -632,7 +664,7 @@ __global__ void __launch_bounds__(kGThreads, 4) g_dir_v(const GArgs a) {
 // NC: p may be read through the non-coherent path (it was written by an
 // earlier kernel; false in the batched launch, where other blocks of the
 // same launch wrote it).
-template <bool VEL, bool NC = true, bool PF = false>
+template <int KIND, bool NC = true, bool PF = false>
 __device__ __forceinline__ double upd_pass(const GArgs& a, float alpha, const float* pnew, Blk B = grid_blk()) {
   const float4* p4 = reinterpret_cast<const float4*>(pnew);
   float4* d4 = reinterpret_cast<float4*>(a.d32);
@@ -640,7 +672,7 @@ __device__ __forceinline__ double upd_pass(const GArgs& a, float alpha, const fl
   auto P4 = [&](size_t e) { return NC ? __ldg(p4 + e) : p4[e]; };
   auto P1 = [&](size_t e) { return NC ? __ldg(pnew + e) : pnew[e]; };
   double acc = 0.0;
-  march_f32<VEL, PF>(a, P4, P1, [&](size_t c4, const float4& pv, const float4& qv) {
+  march_f32<KIND, PF>(a, P4, P1, [&](size_t c4, const float4& pv, const float4& qv) {
     float4 dv = d4[c4], rv = r4[c4];
     dv.x = fmaf(alpha, pv.x, dv.x);
     dv.y = fmaf(alpha, pv.y, dv.y);
@@ -658,7 +690,7 @@ __device__ __forceinline__ double upd_pass(const GArgs& a, float alpha, const fl
 }
 
 // inner body: the update pass, then the loop control
-template <bool VEL>
+template <int KIND>
 __global__ void __launch_bounds__(kGThreads, kIterBlocks) g_upd(const GArgs a) {
   GState* S = a.S;
   count_kernel(S);
@@ -667,7 +699,7 @@ __global__ void __launch_bounds__(kGThreads, kIterBlocks) g_upd(const GArgs a) {
     return;
   }
   const float* pnew = S->cur ? a.p1 : a.p0;
-  double v[1] = {upd_pass<VEL>(a, float(S->alpha), pnew)}, o[1];
+  double v[1] = {upd_pass<KIND>(a, float(S->alpha), pnew)}, o[1];
   if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
   const double rz_new = o[0];
   S->first = 0;
@@ -697,7 +729,7 @@ __global__ void __launch_bounds__(kGThreads, kIterBlocks) g_upd(const GArgs a) {
 // contribution of cell c to the kernel's dot product; per work item the
 // contributions are summed in FP32, then in FP64.
 // ---------------------------------------------------------------------------
-template <typename F1, typename E>
+template <int KIND, typename F1, typename E>
 __device__ __forceinline__ double march_s32(const GArgs& a, F1 P, E emit, Blk B = grid_blk()) {
   const int mx = a.mx, my = a.my, mz = a.mz;
   const size_t sy = size_t(mx), sz = size_t(mx) * my;
@@ -720,7 +752,7 @@ __device__ __forceinline__ double march_s32(const GArgs& a, F1 P, E emit, Blk B 
       const float xe = i < mx - 1 ? P(c + 1) : xc;
       const float xs = j > 0 ? P(c - sy) : xc;
       const float xn = j < my - 1 ? P(c + sy) : xc;
-      const float q = stencil_row<float>(a.kind, a.c32, i, j, k, mx, my, mz, xc, xw, xe, xs, xn, xm, xp);
+      const float q = stencil_row<float>(KIND, a.c32, i, j, k, mx, my, mz, xc, xw, xe, xs, xn, xm, xp);
       part += emit(c, xc, q);
       xm = xc;
       xc = xp;
@@ -733,6 +765,7 @@ __device__ __forceinline__ double march_s32(const GArgs& a, F1 P, E emit, Blk B 
 
 // inner body (scalar lanes): p = r32 + beta p_old, stored; p.q with q = A p
 // formed on the fly (not stored); alpha = rz / p.q
+template <int KIND>
 __global__ void __launch_bounds__(kGThreads, 4) g_dir_s(const GArgs a) {
   GState* S = a.S;
   count_kernel(S);
@@ -742,7 +775,7 @@ __global__ void __launch_bounds__(kGThreads, 4) g_dir_s(const GArgs a) {
   float* pnew = cur ? a.p1 : a.p0;
   const float* pold = cur ? a.p0 : a.p1;
   auto P = [&](size_t e) { return first ? __ldg(a.r32 + e) : fmaf(beta, __ldg(pold + e), __ldg(a.r32 + e)); };
-  const double acc = march_s32(a, P, [&](size_t c, float pc, float q) {
+  const double acc = march_s32<KIND>(a, P, [&](size_t c, float pc, float q) {
     pnew[c] = pc;
     return pc * q;
   });
@@ -760,6 +793,7 @@ __global__ void __launch_bounds__(kGThreads, 4) g_dir_s(const GArgs a) {
 
 // inner body (scalar lanes): q = A p again from the stored p, x32 += alpha p,
 // r32 -= alpha q, |r32|^2; the loop control
+template <int KIND>
 __global__ void __launch_bounds__(kGThreads, 4) g_upd_s(const GArgs a) {
   GState* S = a.S;
   count_kernel(S);
@@ -770,7 +804,7 @@ __global__ void __launch_bounds__(kGThreads, 4) g_upd_s(const GArgs a) {
   const float alpha = float(S->alpha);
   const float* pnew = S->cur ? a.p1 : a.p0;
   auto P = [&](size_t e) { return __ldg(pnew + e); };
-  const double acc = march_s32(a, P, [&](size_t c, float pc, float q) {
+  const double acc = march_s32<KIND>(a, P, [&](size_t c, float pc, float q) {
     a.d32[c] = fmaf(alpha, pc, a.d32[c]);
     const float rv = fmaf(-alpha, q, a.r32[c]);
     a.r32[c] = rv;
@@ -893,7 +927,7 @@ __global__ void __launch_bounds__(kGThreads, 4) f_beta(const GArgs a) {
     const float4* o4 = reinterpret_cast<const float4*>(pold);
     auto P4 = [&](size_t e) { return __ldg(o4 + e); };
     auto P1 = [&](size_t e) { return __ldg(pold + e); };
-    march_f32<false>(a, P4, P1, [&](size_t c4, const float4&, const float4& qv) { add(__ldg(z4 + c4), __ldg(r4 + c4), qv); });
+    march_f32<kOpPressure>(a, P4, P1, [&](size_t c4, const float4&, const float4& qv) { add(__ldg(z4 + c4), __ldg(r4 + c4), qv); });
   } else {
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     for (size_t e = vtid(); e < a.n / 4; e += vstride()) add(__ldg(z4 + e), __ldg(r4 + e), zero);
@@ -982,7 +1016,7 @@ __global__ void __launch_bounds__(kGThreads, 4) f_upd(const GArgs a) {
     return;
   }
   const float* pnew = S->cur ? a.p1 : a.p0;
-  double v[1] = {upd_pass<false>(a, float(S->alpha), pnew)}, o[1];
+  double v[1] = {upd_pass<kOpPressure>(a, float(S->alpha), pnew)}, o[1];
   if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
   const double rr_new = o[0];
   S->first = 0;
@@ -1241,7 +1275,7 @@ __device__ bool reduce_all(const double (&v)[K], const GArgs& a, unsigned target
 #define CFD_IRB_PF 0
 #endif
 constexpr bool kBatchPrefetch = CFD_IRB_PF != 0;
-template <bool VEL>
+template <int KIND>
 __global__ void __launch_bounds__(kGThreads, CFD_IRB_BLOCKS) irb_kernel(const GArgs* __restrict__ tab,
                                                            const int* __restrict__ starts, int nprob) {
   int lo = 0, hi = nprob - 1;
@@ -1330,12 +1364,12 @@ __global__ void __launch_bounds__(kGThreads, CFD_IRB_BLOCKS) irb_kernel(const GA
                                  fmaf(b32, ov.w, rv.w));
             };
             auto P1 = [&](size_t e) { return fst ? a.r32[e] : fmaf(b32, pold[e], a.r32[e]); };
-            if (!VEL) {
+            if (KIND == kOpPressure) {
               vd[0] = edge_pass<kBatchPrefetch>(a, P4, P1, reinterpret_cast<float4*>(pnew), B);
             } else {
               float4* p4 = reinterpret_cast<float4*>(pnew);
               double acc = 0.0;
-              march_f32<true, kBatchPrefetch>(a, P4, P1, [&](size_t c4, const float4& pc, const float4& q) {
+              march_f32<KIND, kBatchPrefetch>(a, P4, P1, [&](size_t c4, const float4& pc, const float4& q) {
                 p4[c4] = pc;
                 acc += double(fmaf(pc.x, q.x, fmaf(pc.y, q.y, fmaf(pc.z, q.z, pc.w * q.w))));
               }, B);
@@ -1343,7 +1377,7 @@ __global__ void __launch_bounds__(kGThreads, CFD_IRB_BLOCKS) irb_kernel(const GA
             }
           } else {
             auto P = [&](size_t e) { return fst ? a.r32[e] : fmaf(b32, pold[e], a.r32[e]); };
-            vd[0] = march_s32(a, P, [&](size_t c, float pc, float q) {
+            vd[0] = march_s32<KIND>(a, P, [&](size_t c, float pc, float q) {
               pnew[c] = pc;
               return pc * q;
             }, B);
@@ -1356,10 +1390,10 @@ __global__ void __launch_bounds__(kGThreads, CFD_IRB_BLOCKS) irb_kernel(const GA
           const double alpha = rz / od[0];
           double vu[1], ou[1];
           if (vec) {
-            vu[0] = upd_pass<VEL, false, kBatchPrefetch>(a, float(alpha), pnew, B);
+            vu[0] = upd_pass<KIND, false, kBatchPrefetch>(a, float(alpha), pnew, B);
           } else {
             const float al = float(alpha);
-            vu[0] = march_s32(a, [&](size_t e) { return pnew[e]; }, [&](size_t c, float pc, float q) {
+            vu[0] = march_s32<KIND>(a, [&](size_t e) { return pnew[e]; }, [&](size_t c, float pc, float q) {
               a.d32[c] = fmaf(al, pc, a.d32[c]);
               const float rv = fmaf(-al, q, a.r32[c]);
               a.r32[c] = rv;
@@ -1668,20 +1702,31 @@ cudaError_t build_graph(IrGraph* G, const IrArgs& ia, GArgs a, bool vec, size_t 
   } else if (vec && a.kind == kOpPressure) {
     if ((e = add_kernel(inner, &i1, nullptr, (void*)g_dir, wave_blocks(g_dir, items32), tile, &a)) != cudaSuccess)
       return e;
-    if ((e = add_kernel(inner, &i2, &i1, (void*)g_upd<false>, wave_blocks(g_upd<false>, items32), tile, &a)) !=
-        cudaSuccess)
-      return e;
-  } else if (vec) {
-    if ((e = add_kernel(inner, &i1, nullptr, (void*)g_dir_v, wave_blocks(g_dir_v, items32), tile, &a)) != cudaSuccess)
-      return e;
-    if ((e = add_kernel(inner, &i2, &i1, (void*)g_upd<true>, wave_blocks(g_upd<true>, items32), tile, &a)) !=
+    if ((e = add_kernel(inner, &i2, &i1, (void*)g_upd<kOpPressure>, wave_blocks(g_upd<kOpPressure>, items32), tile, &a)) !=
         cudaSuccess)
       return e;
   } else {
-    if ((e = add_kernel(inner, &i1, nullptr, (void*)g_dir_s, wave_blocks(g_dir_s, items32), tile, &a)) != cudaSuccess)
-      return e;
-    if ((e = add_kernel(inner, &i2, &i1, (void*)g_upd_s, wave_blocks(g_upd_s, items32), tile, &a)) != cudaSuccess)
-      return e;
+    // the velocity matrices, one instantiation per component
+    void* fd = nullptr;
+    void* fu = nullptr;
+    int nd = 1, nu = 1;
+    auto pick = [&](auto dir, auto upd) {
+      fd = (void*)dir;
+      fu = (void*)upd;
+      nd = wave_blocks(dir, items32);
+      nu = wave_blocks(upd, items32);
+    };
+    if (vec) {
+      if (a.kind == kOpVelU) pick(g_dir_v<kOpVelU>, g_upd<kOpVelU>);
+      else if (a.kind == kOpVelV) pick(g_dir_v<kOpVelV>, g_upd<kOpVelV>);
+      else pick(g_dir_v<kOpVelW>, g_upd<kOpVelW>);
+    } else {
+      if (a.kind == kOpVelU) pick(g_dir_s<kOpVelU>, g_upd_s<kOpVelU>);
+      else if (a.kind == kOpVelV) pick(g_dir_s<kOpVelV>, g_upd_s<kOpVelV>);
+      else pick(g_dir_s<kOpVelW>, g_upd_s<kOpVelW>);
+    }
+    if ((e = add_kernel(inner, &i1, nullptr, fd, nd, tile, &a)) != cudaSuccess) return e;
+    if ((e = add_kernel(inner, &i2, &i1, fu, nu, tile, &a)) != cudaSuccess) return e;
   }
   if ((e = add_kernel(outer, &b3, &b2, (void*)g_resid64<1>, wave_blocks(g_resid64<1>, items64), tile, &a)) !=
       cudaSuccess)
@@ -1806,14 +1851,25 @@ cudaError_t ir_batch_table(const IrArgs* args, void* const* states, int nprob, v
   return e;
 }
 
-int ir_batch_blocks_per_sm(int vel) {
+namespace {
+using IrbKernel = void (*)(const GArgs*, const int*, int);
+IrbKernel irb_for(int kind) {
+  switch (kind) {
+    case kOpVelU: return irb_kernel<kOpVelU>;
+    case kOpVelV: return irb_kernel<kOpVelV>;
+    case kOpVelW: return irb_kernel<kOpVelW>;
+    default: return irb_kernel<kOpPressure>;
+  }
+}
+}  // namespace
+
+int ir_batch_blocks_per_sm(int kind) {
   int b = 0;
-  if (vel) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, irb_kernel<true>, kGThreads, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, irb_kernel<false>, kGThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, irb_for(kind), kGThreads, 0);
   return b;
 }
 
-cudaError_t launch_ir_batch(const void* d_table, const int* d_starts, int nprob, int total_blocks, int vel,
+cudaError_t launch_ir_batch(const void* d_table, const int* d_starts, int nprob, int total_blocks, int kind,
                             cudaStream_t s, int64_t* launches) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(total_blocks));
@@ -1826,8 +1882,7 @@ cudaError_t launch_ir_batch(const void* d_table, const int* d_starts, int nprob,
   cfg.numAttrs = 1;
   if (launches) *launches += 1;
   const GArgs* t = static_cast<const GArgs*>(d_table);
-  return vel ? cudaLaunchKernelEx(&cfg, irb_kernel<true>, t, d_starts, nprob)
-             : cudaLaunchKernelEx(&cfg, irb_kernel<false>, t, d_starts, nprob);
+  return cudaLaunchKernelEx(&cfg, irb_for(kind), t, d_starts, nprob);
 }
 
 cudaError_t ir_graph_kernel_count(const void* state_buf, cudaStream_t s, long long* out) {

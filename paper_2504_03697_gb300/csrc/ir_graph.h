@@ -30,17 +30,17 @@ cudaError_t launch_learned_guess(const IrArgs& a, void* state_buf, cudaStream_t 
 // synchronisation words, zeroed before every launch), stats and
 // timeout_ns; its state buffer (ir_graph_state_bytes()) holds the partial
 // sums.  ir_batch_table writes the device table (ir_batch_table_bytes) once
-// (synchronises s); launch_ir_batch runs the solves (vel: the velocity
-// matrices of the diffusion substep, else the pressure matrix).  At most
-// ir_batch_blocks_per_sm(vel) blocks per SM, and at most 1024 per problem.
+// (synchronises s); launch_ir_batch runs the solves (kind: the kOp* operator
+// of every problem of the launch).  At most ir_batch_blocks_per_sm(kind)
+// blocks per SM, and at most 1024 per problem.
 // One problem's work in the batched launch: its (row, plane) work items per
 // pass, and its largest extent (a proxy for the iteration count).  A solve
 // on nb blocks takes about extent * ceil(items / nb) item passes.
 void ir_batch_work(const IrArgs& ia, int* items, int* extent);
 size_t ir_batch_table_bytes(int nprob);
 cudaError_t ir_batch_table(const IrArgs* args, void* const* states, int nprob, void* d_table, cudaStream_t s);
-int ir_batch_blocks_per_sm(int vel);
-cudaError_t launch_ir_batch(const void* d_table, const int* d_starts, int nprob, int total_blocks, int vel,
+int ir_batch_blocks_per_sm(int kind);
+cudaError_t launch_ir_batch(const void* d_table, const int* d_starts, int nprob, int total_blocks, int kind,
                             cudaStream_t s, int64_t* launches);
 // Kernels run so far by graph solves on this state buffer (synchronises s).
 cudaError_t ir_graph_kernel_count(const void* state_buf, cudaStream_t s, long long* out);
