@@ -92,11 +92,12 @@ Layout ws_layout(const cfd_params& p, int max_blocks, bool standalone = true) {
     // sized to the largest face grid: the graph form also runs the
     // diffusion solves in FP32 with FP64 refinement (and the flexible CG
     // with the learned preconditioner uses the same FP32 vectors)
-    L.r32 = take(vec * 4);
-    L.d32 = take(vec * 4);
-    L.p0_32 = take(vec * 4);
-    L.p1_32 = take(vec * 4);
-    L.q32 = take(vec * 4);
+    const size_t vec32 = std::max(vec, ir_fp32_vector_cells(p.nx, p.ny, p.nz));
+    L.r32 = take(vec32 * 4);
+    L.d32 = take(vec32 * 4);
+    L.p0_32 = take(vec32 * 4);
+    L.p1_32 = take(vec32 * 4);
+    L.q32 = take(vec32 * 4);
     L.irg = take(ir_graph_state_bytes());
   }
   L.partials = take(partials_doubles(max_blocks) * 8);  // double-buffered block + group partials

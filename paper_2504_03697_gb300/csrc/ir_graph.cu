@@ -135,6 +135,8 @@ struct GArgs {
   int kind;              // kOp* operator
   double c;              // nu dt / h^2 (velocity operators)
   float c32;
+  int pitch;             // row pitch of the FP32 vectors (r32, d32, p0, p1) in cells: mx, or mx rounded up to
+                         // a multiple of 4 for a velocity matrix (its padding cells hold 0)
   int lpr;               // float4 lanes: lanes per grid row (4, 8, 16 or 32); a warp covers 32 / lpr rows
   int w32x, w32y, w32z;  // FP32 work items: (float4 or scalar) columns / lpr (32), rows / (8 * 32 / lpr), planes / kZ32
   int w64x, w64y, w64z;  // FP64 work items: columns / 32, rows / 8, planes / kZ64
@@ -288,7 +290,8 @@ __device__ __forceinline__ void resid64_pass(const GArgs& a, double shift, bool 
                                              Blk B) {
   const int mx = a.mx, my = a.my, mz = a.mz;
   const size_t sy = size_t(mx), sz = size_t(mx) * my;
-  auto X = [&](size_t e) { return zero ? 0.0 : (add32 ? a.x[e] + double(a.d32[e]) : a.x[e]); };
+  const size_t py = size_t(a.pitch), pz = size_t(a.pitch) * my;  // the FP32 layout
+  auto X = [&](size_t e, size_t e32) { return zero ? 0.0 : (add32 ? a.x[e] + double(a.d32[e32]) : a.x[e]); };
   double sb = 0.0, sr = 0.0, ss = 0.0;
   const int items = a.w64x * a.w64y * a.w64z;
   for (int w = B.bid; w < items; w += B.nb) {
@@ -297,14 +300,15 @@ __device__ __forceinline__ void resid64_pass(const GArgs& a, double shift, bool 
     if (i >= mx || j >= my) continue;
     const int k1 = min(k0 + kZ64, mz);
     size_t c = (size_t(k0) * my + j) * mx + i;
-    double xc = X(c);
-    double xm = k0 > 0 ? X(c - sz) : xc;
-    for (int k = k0; k < k1; ++k, c += sz) {
-      const double xp = k < mz - 1 ? X(c + sz) : xc;
-      const double xw = i > 0 ? X(c - 1) : xc;
-      const double xe = i < mx - 1 ? X(c + 1) : xc;
-      const double xs = j > 0 ? X(c - sy) : xc;
-      const double xn = j < my - 1 ? X(c + sy) : xc;
+    size_t c32 = (size_t(k0) * my + j) * py + i;
+    double xc = X(c, c32);
+    double xm = k0 > 0 ? X(c - sz, c32 - pz) : xc;
+    for (int k = k0; k < k1; ++k, c += sz, c32 += pz) {
+      const double xp = k < mz - 1 ? X(c + sz, c32 + pz) : xc;
+      const double xw = i > 0 ? X(c - 1, c32 - 1) : xc;
+      const double xe = i < mx - 1 ? X(c + 1, c32 + 1) : xc;
+      const double xs = j > 0 ? X(c - sy, c32 - py) : xc;
+      const double xn = j < my - 1 ? X(c + sy, c32 + py) : xc;
       const double ax = stencil_row<double>(a.kind, a.c, i, j, k, mx, my, mz, xc, xw, xe, xs, xn, xm, xp);
       double bv = a.b[c];
       if (MODE == 0) {
@@ -363,6 +367,56 @@ __global__ void __launch_bounds__(kGThreads) g_resid64(const GArgs a) {
   }
 }
 
+// Cell e of the FP64 layout in the FP32 layout (row pitch a.pitch; the
+// grids hold fewer than 2^31 cells).
+__device__ __forceinline__ size_t c32_of(const GArgs& a, size_t e) {
+  if (a.pitch == a.mx) return e;
+  const unsigned row = unsigned(e) / unsigned(a.mx);
+  return e + size_t(row) * size_t(a.pitch - a.mx);
+}
+
+// g_prep's pass over the blocks B: fold a pending x32 into x, load r32 =
+// r - rmean unless leaving, clear x32; the padding cells of the FP32 rows
+// are set to 0.  Returns this thread's part of r32.r32 (FP32).
+__device__ __forceinline__ float prep_pass(const GArgs& a, bool fold, bool leave, double rmean, Blk B) {
+  const size_t t0 = size_t(B.bid) * kGThreads + ftid(), st = size_t(B.nb) * kGThreads;
+  float f = 0.f;
+  for (size_t e = t0; e < a.n; e += st) {
+    const size_t e32 = c32_of(a, e);
+    if (fold) a.x[e] += double(a.d32[e32]);
+    if (!leave) {
+      const float v = float(a.r[e] - rmean);
+      a.r32[e32] = v;
+      f = fmaf(v, v, f);
+    }
+    if (fold || !leave) a.d32[e32] = 0.f;
+  }
+  if (a.pitch != a.mx) {
+    const unsigned pad = unsigned(a.pitch - a.mx), rows = unsigned(a.my) * unsigned(a.mz);
+    for (size_t q = t0; q < size_t(rows) * pad; q += st) {
+      const unsigned row = unsigned(q) / pad, i = unsigned(a.mx) + unsigned(q) - row * pad;
+      const size_t e32 = size_t(row) * unsigned(a.pitch) + i;
+      a.r32[e32] = 0.f;
+      a.d32[e32] = 0.f;
+    }
+  }
+  return f;
+}
+
+// g_finish's pass over the blocks B: x := 0 (zero) or x += x32 (fold);
+// returns this thread's part of sum(x).
+__device__ __forceinline__ double finish_pass(const GArgs& a, bool zero, bool fold, Blk B) {
+  const size_t t0 = size_t(B.bid) * kGThreads + ftid(), st = size_t(B.nb) * kGThreads;
+  double s = 0.0;
+  for (size_t e = t0; e < a.n; e += st) {
+    double xv = zero ? 0.0 : a.x[e];
+    if (!zero && fold) xv += double(a.d32[c32_of(a, e)]);
+    if (zero || fold) a.x[e] = xv;
+    s += xv;
+  }
+  return s;
+}
+
 // ---------------------------------------------------------------------------
 // outer body, first node: leave (converged / caps) or start a new FP32
 // recurrence from the true residual.  Folds a pending x32 into x either way.
@@ -375,16 +429,7 @@ __global__ void __launch_bounds__(kGThreads) g_prep(const GArgs a) {
   const bool fold = S->pending != 0;
   // the singular pressure system works on zero-mean residuals
   const double rmean = a.kind == kOpPressure ? S->rsum / double(a.n) : 0.0;
-  float f = 0.f;
-  for (size_t e = vtid(); e < a.n; e += vstride()) {
-    if (fold) a.x[e] += double(a.d32[e]);
-    if (!leave) {
-      const float v = float(a.r[e] - rmean);
-      a.r32[e] = v;
-      f = fmaf(v, v, f);
-    }
-    if (fold || !leave) a.d32[e] = 0.f;
-  }
+  const float f = prep_pass(a, fold, leave, rmean, grid_blk());
   double v[1] = {double(f)}, o[1];
   if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
   S->pending = 0;
@@ -438,7 +483,8 @@ __device__ __forceinline__ float4 vel_rows4(float c, int i0, int j, int k, int m
     const float zm = comp != 2 && klo ? g : m_[t];
     const float zp = comp != 2 && khi ? g : p_[t];
     const float lap = fmaf(6.f, xc[t], -(((((xm + xp) + ym) + yp) + zm) + zp));
-    q[t] = comp == 0 && (i == 0 || i == mx - 1) ? 0.f : fmaf(c, lap, xc[t]);
+    // padding cells of the FP32 rows (i >= mx) stay 0
+    q[t] = (comp == 0 && (i == 0 || i == mx - 1)) || i >= mx ? 0.f : fmaf(c, lap, xc[t]);
   }
   return make_float4(q[0], q[1], q[2], q[3]);
 }
@@ -448,7 +494,7 @@ __device__ __forceinline__ float4 vel_rows4(float c, int i0, int j, int k, int m
 // each plane's loads, not by bandwidth).
 template <int KIND, bool PF = false, typename F4, typename F1, typename E>
 __device__ __forceinline__ void march_f32(const GArgs& a, F4 P4, F1 P1, E emit, Blk B = grid_blk()) {
-  const int my = a.my, mz = a.mz, nx4 = a.mx >> 2;
+  const int my = a.my, mz = a.mz, nx4 = a.pitch >> 2;
   const size_t sy4 = size_t(nx4), sz4 = size_t(nx4) * my;
   const int lane = threadIdx.x, L = a.lpr, sl = lane & (L - 1), seg = lane / L, rpw = 32 / L;
   const int items = a.w32x * a.w32y * a.w32z;
@@ -526,7 +572,7 @@ __device__ __forceinline__ void march_f32(const GArgs& a, F4 P4, F1 P1, E emit, 
 template <bool PF = false, typename F4, typename F1>
 __device__ __forceinline__ double edge_pass(const GArgs& a, F4 P4, F1 P1, float4* p4, Blk B = grid_blk()) {
   auto sq = [](float d) { return d * d; };
-  const int my = a.my, mz = a.mz, nx4 = a.mx >> 2;
+  const int my = a.my, mz = a.mz, nx4 = a.pitch >> 2;
   const size_t sy4 = size_t(nx4), sz4 = size_t(nx4) * my;
   const int lane = threadIdx.x, L = a.lpr, sl = lane & (L - 1), seg = lane / L, rpw = 32 / L;
   double acc = 0.0;
@@ -1166,15 +1212,7 @@ __global__ void __launch_bounds__(kGThreads) g_gset(const GArgs a) {
 __global__ void __launch_bounds__(kGThreads) g_finish(const GArgs a) {
   GState* S = a.S;
   count_kernel(S);
-  const bool zero = S->bb == 0.0;
-  const bool fold = S->pending != 0;
-  double s = 0.0;
-  for (size_t e = vtid(); e < a.n; e += vstride()) {
-    double xv = zero ? 0.0 : a.x[e];
-    if (!zero && fold) xv += double(a.d32[e]);
-    if (zero || fold) a.x[e] = xv;
-    s += xv;
-  }
+  const double s = finish_pass(a, S->bb == 0.0, S->pending != 0, grid_blk());
   double v[1] = {s}, o[1];
   if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
   S->pending = 0;
@@ -1287,7 +1325,7 @@ __global__ void __launch_bounds__(kGThreads, CFD_IRB_BLOCKS) irb_kernel(const GA
   }
   const GArgs& a = tab[lo];
   const Blk B{blk - starts[lo], starts[lo + 1] - starts[lo]};
-  const bool vec = a.mx % 4 == 0;
+  const bool vec = a.pitch % 4 == 0;
   const double n = double(a.n);
   unsigned gen = 0;
   bool ok_sync = true;
@@ -1325,17 +1363,7 @@ __global__ void __launch_bounds__(kGThreads, CFD_IRB_BLOCKS) irb_kernel(const GA
         const bool leave = okr || refinements > a.max_outer || iters >= a.max_iters;
         const bool fold = pending;
         const double rmean = a.kind == kOpPressure ? rsum / n : 0.0;
-        float f = 0.f;
-        for (size_t e = size_t(B.bid) * kGThreads + ftid(); e < a.n; e += size_t(B.nb) * kGThreads) {
-          if (fold) a.x[e] += double(a.d32[e]);
-          if (!leave) {
-            const float v = float(a.r[e] - rmean);
-            a.r32[e] = v;
-            f = fmaf(v, v, f);
-          }
-          if (fold || !leave) a.d32[e] = 0.f;
-        }
-        double v1[1] = {double(f)}, o1[1];
+        double v1[1] = {double(prep_pass(a, fold, leave, rmean, B))}, o1[1];
         if (!all(v1, o1)) goto out;
         pending = false;
         if (leave) {
@@ -1433,14 +1461,7 @@ __global__ void __launch_bounds__(kGThreads, CFD_IRB_BLOCKS) irb_kernel(const GA
     }
     // g_finish: fold x32 (x := 0 when b = 0), mean of x for the gauge
     {
-      const bool zero = bb == 0.0;
-      double s1[1] = {0.0}, o1[1];
-      for (size_t e = size_t(B.bid) * kGThreads + ftid(); e < a.n; e += size_t(B.nb) * kGThreads) {
-        double xv = zero ? 0.0 : a.x[e];
-        if (!zero && pending) xv += double(a.d32[e]);
-        if (zero || pending) a.x[e] = xv;
-        s1[0] += xv;
-      }
+      double s1[1] = {finish_pass(a, bb == 0.0, pending, B)}, o1[1];
       if (!all(s1, o1)) goto out;
       // g_shift
       if (a.gauge) {
@@ -1510,8 +1531,25 @@ bool ir_graph_eligible(const IrArgs& a) {
 }
 
 namespace {
-bool use_vec_kernels(const IrArgs& a) { return a.g.mx % 4 == 0; }
+// float4 lanes: the pressure matrix on rows of a multiple of 4 cells; the
+// velocity matrices always (their FP32 rows are padded to a multiple of 4)
+bool use_vec_kernels(const IrArgs& a) { return a.kind != kOpPressure || a.g.mx % 4 == 0; }
+
+int fp32_pitch(const IrArgs& a) { return a.kind == kOpPressure || a.g.mx % 4 == 0 ? a.g.mx : (a.g.mx + 3) / 4 * 4; }
 }  // namespace
+
+size_t ir_fp32_vector_cells(int nx, int ny, int nz) {
+  size_t best = size_t(nx) * ny * nz;
+  for (int c = 0; c < 3; ++c) {
+    IrArgs a{};
+    a.kind = kOpVelU + c;
+    a.g = GridDims{nx + (c == 0), ny + (c == 1), nz + (c == 2)};
+    const size_t cells = size_t(fp32_pitch(a)) * a.g.my * a.g.mz;
+    best = best > cells ? best : cells;
+  }
+  return best;
+}
+
 
 namespace {
 
@@ -1616,8 +1654,9 @@ GArgs make_args(const IrArgs& ia, void* state_buf) {
   a.c = ia.c;
   a.c32 = float(ia.c);
   const bool vec = use_vec_kernels(ia);
+  a.pitch = fp32_pitch(ia);
   a.lpr = 32;
-  a.w32x = vec ? (a.mx / 4 + 31) / 32 : (a.mx + 31) / 32;
+  a.w32x = vec ? (a.pitch / 4 + 31) / 32 : (a.mx + 31) / 32;
   a.w32y = (a.my + 7) / 8;
   a.w32z = (a.mz + kZ32 - 1) / kZ32;
   a.w64x = (a.mx + 31) / 32;
@@ -1810,8 +1849,8 @@ namespace {
 // (a power of two from 4 to 32), so that narrow grids keep every lane busy
 // and the blocks of a problem march through fewer (row, plane) steps.
 void set_batch_lanes(GArgs& g) {
-  if (g.mx % 4 != 0) return;  // scalar lanes
-  const int nx4 = g.mx / 4;
+  if (g.pitch % 4 != 0) return;  // scalar lanes
+  const int nx4 = g.pitch / 4;
   int L = 4;
   while (L < nx4 && L < 32) L *= 2;
   g.lpr = L;
@@ -1826,6 +1865,7 @@ void ir_batch_work(const IrArgs& ia, int* items, int* extent) {
   g.mx = ia.g.mx;
   g.my = ia.g.my;
   g.mz = ia.g.mz;
+  g.pitch = fp32_pitch(ia);
   g.w32x = (g.mx + 31) / 32;  // scalar lanes
   g.w32y = (g.my + 7) / 8;
   g.w32z = (g.mz + kZ32 - 1) / kZ32;

@@ -10,6 +10,10 @@ namespace cfd {
 
 struct IrGraph;  // an instantiated graph, cached per workspace and arguments
 
+// Cells each FP32 vector of the mixed-precision solves needs for an nx x ny
+// x nz cavity: the velocity matrices' rows are padded to a multiple of 4
+// cells in the graph and batched forms.
+size_t ir_fp32_vector_cells(int nx, int ny, int nz);
 // Device bytes of the solver state and partial sums (16-byte aligned).
 size_t ir_graph_state_bytes();
 // The graph form needs mx % 4 == 0 (16-byte rows of the FP32 vectors).
