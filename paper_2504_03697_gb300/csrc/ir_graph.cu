@@ -30,8 +30,8 @@
 // loops once iters >= max_iters or refinements > max_outer.
 //
 // Operators: the pressure matrix (float4 kernels, mx % 4 == 0) and the
-// velocity matrices of the diffusion substep (float4 kernels where the face
-// grid's width is a multiple of 4, scalar-lane kernels otherwise; no mean
+// velocity matrices of the diffusion substep (float4 kernels on FP32 rows
+// padded to a multiple of 4 cells; p.Hp in the edge form too; no mean
 // removal, their matrices being nonsingular).
 //
 // The learned preconditioner (pressure matrix only; the paper's "other
@@ -569,7 +569,14 @@ __device__ __forceinline__ void march_f32(const GArgs& a, F4 P4, F1 P1, E emit, 
 // p.Ap = sum over neighbour pairs of the squared difference), which needs p
 // only at the +x, +y and +z neighbours.  One warp covers 128 x cells of one
 // row, +x by warp shuffles.
-template <bool PF = false, typename F4, typename F1>
+//
+// For a velocity matrix H = I + c L (KIND = kOpVelU + comp) the same pass
+// gives p.Hp = sum p_i^2 + c (sum over in-array edges (p_i - p_j)^2 + 2 sum
+// over ghost faces p_i^2): a ghost neighbour -p_i adds 2 p_i^2, a wall row
+// holds p = 0 (its residual is 0), so an edge to it adds p_i^2; the ghost
+// faces are the array's boundary faces across the two tangential axes, and
+// x edges to the padding of the FP32 rows are left out.
+template <bool PF = false, int KIND = kOpPressure, typename F4, typename F1>
 __device__ __forceinline__ double edge_pass(const GArgs& a, F4 P4, F1 P1, float4* p4, Blk B = grid_blk()) {
   auto sq = [](float d) { return d * d; };
   const int my = a.my, mz = a.mz, nx4 = a.pitch >> 2;
@@ -613,12 +620,34 @@ __device__ __forceinline__ double edge_pass(const GArgs& a, F4 P4, F1 P1, float4
       else if (!has_e) east = pc.w;
       if (on) {
         p4[c4] = pc;
-        // x edges inside the float4 and to the east cell (0 at the wall),
-        // y edges to the next row, z edges to the next plane (0 at walls)
-        float e = sq(pc.x - pc.y) + sq(pc.y - pc.z) + sq(pc.z - pc.w) + sq(pc.w - east);
-        e += (sq(pc.x - pn.x) + sq(pc.y - pn.y)) + (sq(pc.z - pn.z) + sq(pc.w - pn.w));
-        e += (sq(pc.x - pp.x) + sq(pc.y - pp.y)) + (sq(pc.z - pp.z) + sq(pc.w - pp.w));
-        acc += double(e);
+        if (KIND == kOpPressure) {
+          // x edges inside the float4 and to the east cell (0 at the wall),
+          // y edges to the next row, z edges to the next plane (0 at walls)
+          float e = sq(pc.x - pc.y) + sq(pc.y - pc.z) + sq(pc.z - pc.w) + sq(pc.w - east);
+          e += (sq(pc.x - pn.x) + sq(pc.y - pn.y)) + (sq(pc.z - pn.z) + sq(pc.w - pn.w));
+          e += (sq(pc.x - pp.x) + sq(pc.y - pp.y)) + (sq(pc.z - pp.z) + sq(pc.w - pp.w));
+          acc += double(e);
+        } else {
+          constexpr int comp = KIND - 1;
+          const int i0 = 4 * i4, mx = a.mx;
+          const float pv[5] = {pc.x, pc.y, pc.z, pc.w, east};
+          float e = 0.f;
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            if (i0 + t + 1 < mx) e += sq(pv[t] - pv[t + 1]);
+          e += (sq(pc.x - pn.x) + sq(pc.y - pn.y)) + (sq(pc.z - pn.z) + sq(pc.w - pn.w));
+          e += (sq(pc.x - pp.x) + sq(pc.y - pp.y)) + (sq(pc.z - pp.z) + sq(pc.w - pp.w));
+          const float d2 = (pc.x * pc.x + pc.y * pc.y) + (pc.z * pc.z + pc.w * pc.w);
+          float gh = 0.f;
+          if (comp != 0) {
+            if (i0 == 0) gh += pc.x * pc.x;
+            const int tl = mx - 1 - i0;  // the cell at the +x face, if in this float4
+            if (tl >= 0 && tl < 4) gh += pv[tl] * pv[tl];
+          }
+          if (comp != 1) gh += (j == 0 ? d2 : 0.f) + (j == my - 1 ? d2 : 0.f);
+          if (comp != 2) gh += (k == 0 ? d2 : 0.f) + (k == mz - 1 ? d2 : 0.f);
+          acc += double(fmaf(a.c32, fmaf(2.f, gh, e), d2));
+        }
       }
       pc = pp;
       if (PF) {
@@ -665,11 +694,11 @@ __global__ void __launch_bounds__(kGThreads, kIterBlocks) g_dir(const GArgs a) {
   set_alpha(S, S->rz, o[0]);
 }
 
-// inner body for the velocity matrices on float4 lanes (face grids whose
-// width is a multiple of 4): p = r32 + beta p_old formed at the 7 stencil
-// points, stored; p.q with q = H p on the fly (not stored); alpha = rz / p.q
+// inner body for the velocity matrices on float4 lanes (the FP32 rows padded
+// to a multiple of 4): p = r32 + beta p_old, stored; p.Hp by the edge form
+// of edge_pass; alpha = rz / p.Hp
 template <int KIND>
-__global__ void __launch_bounds__(kGThreads, 4) g_dir_v(const GArgs a) {
+__global__ void __launch_bounds__(kGThreads, kIterBlocks) g_dir_v(const GArgs a) {
   GState* S = a.S;
   count_kernel(S);
   const bool first = S->first != 0;
@@ -679,7 +708,6 @@ __global__ void __launch_bounds__(kGThreads, 4) g_dir_v(const GArgs a) {
   const float* pold = cur ? a.p0 : a.p1;
   const float4* r4 = reinterpret_cast<const float4*>(a.r32);
   const float4* o4 = reinterpret_cast<const float4*>(pold);
-  float4* p4 = reinterpret_cast<float4*>(pnew);
   auto P4 = [&](size_t e) {
     const float4 rv = __ldg(r4 + e);
     if (first) return rv;
@@ -687,21 +715,9 @@ __global__ void __launch_bounds__(kGThreads, 4) g_dir_v(const GArgs a) {
     return make_float4(fmaf(beta, ov.x, rv.x), fmaf(beta, ov.y, rv.y), fmaf(beta, ov.z, rv.z), fmaf(beta, ov.w, rv.w));
   };
   auto P1 = [&](size_t e) { return first ? __ldg(a.r32 + e) : fmaf(beta, __ldg(pold + e), __ldg(a.r32 + e)); };
-  double acc = 0.0;
-  march_f32<KIND>(a, P4, P1, [&](size_t c4, const float4& pc, const float4& q) {
-    p4[c4] = pc;
-    acc += double(fmaf(pc.x, q.x, fmaf(pc.y, q.y, fmaf(pc.z, q.z, pc.w * q.w))));
-  });
-  double v[1] = {acc}, o[1];
+  double v[1] = {edge_pass<false, KIND>(a, P4, P1, reinterpret_cast<float4*>(pnew))}, o[1];
   if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
-  const double pq = o[0];
-  if (!(pq > 0.0) || !isfinite(pq)) {
-    S->breakdown = 1;
-    S->status = kErrBreakdown;
-    S->done = 1;
-  } else {
-    S->alpha = S->rz / pq;
-  }
+  set_alpha(S, S->rz, o[0]);
 }
 
 // The update pass over the float4 lanes: q = A p again from the stored p
@@ -768,12 +784,11 @@ __global__ void __launch_bounds__(kGThreads, kIterBlocks) g_upd(const GArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Scalar-lane form of the inner body, for any operator kind and any width
-// (the velocity matrices of the diffusion solves; their face grids are one
-// cell wider along their own axis): one thread per x cell, x and y
-// neighbours through L1, z by marching.  `emit(c, v, q)` returns the FP32
-// contribution of cell c to the kernel's dot product; per work item the
-// contributions are summed in FP32, then in FP64.
+// Scalar-lane march for any operator kind and any width (the batched
+// launch's pressure matrices whose width is not a multiple of 4): one thread
+// per x cell, x and y neighbours through L1, z by marching.  `emit(c, v, q)`
+// returns the FP32 contribution of cell c to the pass's dot product; per
+// work item the contributions are summed in FP32, then in FP64.
 // ---------------------------------------------------------------------------
 template <int KIND, typename F1, typename E>
 __device__ __forceinline__ double march_s32(const GArgs& a, F1 P, E emit, Blk B = grid_blk()) {
@@ -807,75 +822,6 @@ __device__ __forceinline__ double march_s32(const GArgs& a, F1 P, E emit, Blk B 
     acc += double(part);
   }
   return acc;
-}
-
-// inner body (scalar lanes): p = r32 + beta p_old, stored; p.q with q = A p
-// formed on the fly (not stored); alpha = rz / p.q
-template <int KIND>
-__global__ void __launch_bounds__(kGThreads, 4) g_dir_s(const GArgs a) {
-  GState* S = a.S;
-  count_kernel(S);
-  const bool first = S->first != 0;
-  const float beta = float(S->beta);
-  const int cur = S->cur;
-  float* pnew = cur ? a.p1 : a.p0;
-  const float* pold = cur ? a.p0 : a.p1;
-  auto P = [&](size_t e) { return first ? __ldg(a.r32 + e) : fmaf(beta, __ldg(pold + e), __ldg(a.r32 + e)); };
-  const double acc = march_s32<KIND>(a, P, [&](size_t c, float pc, float q) {
-    pnew[c] = pc;
-    return pc * q;
-  });
-  double v[1] = {acc}, o[1];
-  if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
-  const double pq = o[0];
-  if (!(pq > 0.0) || !isfinite(pq)) {
-    S->breakdown = 1;
-    S->status = kErrBreakdown;
-    S->done = 1;
-  } else {
-    S->alpha = S->rz / pq;
-  }
-}
-
-// inner body (scalar lanes): q = A p again from the stored p, x32 += alpha p,
-// r32 -= alpha q, |r32|^2; the loop control
-template <int KIND>
-__global__ void __launch_bounds__(kGThreads, 4) g_upd_s(const GArgs a) {
-  GState* S = a.S;
-  count_kernel(S);
-  if (S->breakdown) {
-    if (blockIdx.x == 0 && ftid() == 0) cudaGraphSetConditional(a.h_in, 0u);
-    return;
-  }
-  const float alpha = float(S->alpha);
-  const float* pnew = S->cur ? a.p1 : a.p0;
-  auto P = [&](size_t e) { return __ldg(pnew + e); };
-  const double acc = march_s32<KIND>(a, P, [&](size_t c, float pc, float q) {
-    a.d32[c] = fmaf(alpha, pc, a.d32[c]);
-    const float rv = fmaf(-alpha, q, a.r32[c]);
-    a.r32[c] = rv;
-    return rv * rv;
-  });
-  double v[1] = {acc}, o[1];
-  if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
-  const double rz_new = o[0];
-  S->first = 0;
-  S->cur ^= 1;
-  S->iters += 1;
-  S->pending = 1;
-  if (rz_new <= S->delta2 * S->rz_ref || rz_new <= S->tol2) {
-    S->refine = 1;
-    cudaGraphSetConditional(a.h_in, 0u);
-    return;
-  }
-  S->beta = rz_new / S->rz;
-  S->rz = rz_new;
-  if (S->iters >= a.max_iters) {
-    S->done = 1;
-    cudaGraphSetConditional(a.h_in, 0u);
-  } else {
-    cudaGraphSetConditional(a.h_in, 1u);
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1392,17 +1338,7 @@ __global__ void __launch_bounds__(kGThreads, CFD_IRB_BLOCKS) irb_kernel(const GA
                                  fmaf(b32, ov.w, rv.w));
             };
             auto P1 = [&](size_t e) { return fst ? a.r32[e] : fmaf(b32, pold[e], a.r32[e]); };
-            if (KIND == kOpPressure) {
-              vd[0] = edge_pass<kBatchPrefetch>(a, P4, P1, reinterpret_cast<float4*>(pnew), B);
-            } else {
-              float4* p4 = reinterpret_cast<float4*>(pnew);
-              double acc = 0.0;
-              march_f32<KIND, kBatchPrefetch>(a, P4, P1, [&](size_t c4, const float4& pc, const float4& q) {
-                p4[c4] = pc;
-                acc += double(fmaf(pc.x, q.x, fmaf(pc.y, q.y, fmaf(pc.z, q.z, pc.w * q.w))));
-              }, B);
-              vd[0] = acc;
-            }
+            vd[0] = edge_pass<kBatchPrefetch, KIND>(a, P4, P1, reinterpret_cast<float4*>(pnew), B);
           } else {
             auto P = [&](size_t e) { return fst ? a.r32[e] : fmaf(b32, pold[e], a.r32[e]); };
             vd[0] = march_s32<KIND>(a, P, [&](size_t c, float pc, float q) {
@@ -1755,15 +1691,9 @@ cudaError_t build_graph(IrGraph* G, const IrArgs& ia, GArgs a, bool vec, size_t 
       nd = wave_blocks(dir, items32);
       nu = wave_blocks(upd, items32);
     };
-    if (vec) {
-      if (a.kind == kOpVelU) pick(g_dir_v<kOpVelU>, g_upd<kOpVelU>);
-      else if (a.kind == kOpVelV) pick(g_dir_v<kOpVelV>, g_upd<kOpVelV>);
-      else pick(g_dir_v<kOpVelW>, g_upd<kOpVelW>);
-    } else {
-      if (a.kind == kOpVelU) pick(g_dir_s<kOpVelU>, g_upd_s<kOpVelU>);
-      else if (a.kind == kOpVelV) pick(g_dir_s<kOpVelV>, g_upd_s<kOpVelV>);
-      else pick(g_dir_s<kOpVelW>, g_upd_s<kOpVelW>);
-    }
+    if (a.kind == kOpVelU) pick(g_dir_v<kOpVelU>, g_upd<kOpVelU>);
+    else if (a.kind == kOpVelV) pick(g_dir_v<kOpVelV>, g_upd<kOpVelV>);
+    else pick(g_dir_v<kOpVelW>, g_upd<kOpVelW>);
     if ((e = add_kernel(inner, &i1, nullptr, fd, nd, tile, &a)) != cudaSuccess) return e;
     if ((e = add_kernel(inner, &i2, &i1, fu, nu, tile, &a)) != cudaSuccess) return e;
   }
