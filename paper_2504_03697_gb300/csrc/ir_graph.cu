@@ -489,10 +489,7 @@ __device__ __forceinline__ float4 vel_rows4(float c, int i0, int j, int k, int m
   return make_float4(q[0], q[1], q[2], q[3]);
 }
 
-// PF: issue the next plane's loads before this plane's arithmetic and
-// stores (the batched launch, whose small grids are bound by the latency of
-// each plane's loads, not by bandwidth).
-template <int KIND, bool PF = false, typename F4, typename F1, typename E>
+template <int KIND, typename F4, typename F1, typename E>
 __device__ __forceinline__ void march_f32(const GArgs& a, F4 P4, F1 P1, E emit, Blk B = grid_blk()) {
   const int my = a.my, mz = a.mz, nx4 = a.pitch >> 2;
   const size_t sy4 = size_t(nx4), sz4 = size_t(nx4) * my;
@@ -509,31 +506,13 @@ __device__ __forceinline__ void march_f32(const GArgs& a, F4 P4, F1 P1, E emit, 
     size_t c4 = (size_t(k0) * my + j) * nx4 + (i4 < nx4 ? i4 : nx4 - 1);  // idle lanes shadow the last column
     float4 pc = P4(c4);
     float4 pm = k0 > 0 ? P4(c4 - sz4) : pc;
-    float4 pp, ps, pn;
-    if (PF) {
-      pp = k0 < mz - 1 ? P4(c4 + sz4) : pc;
-      ps = j > 0 ? P4(c4 - sy4) : pc;
-      pn = j < my - 1 ? P4(c4 + sy4) : pc;
-    }
 #pragma unroll
     for (int kk = 0; kk < kZ32; ++kk) {
       const int k = k0 + kk;
       if (k >= mz) break;
-      float4 pp2, ps2, pn2;
-      if (PF) {
-        pp2 = pp;
-        ps2 = pp;
-        pn2 = pp;
-        if (kk + 1 < kZ32 && k + 1 < mz) {
-          pp2 = k + 1 < mz - 1 ? P4(c4 + 2 * sz4) : pp;
-          ps2 = j > 0 ? P4(c4 + sz4 - sy4) : pp;
-          pn2 = j < my - 1 ? P4(c4 + sz4 + sy4) : pp;
-        }
-      } else {
-        pp = k < mz - 1 ? P4(c4 + sz4) : pc;
-        ps = j > 0 ? P4(c4 - sy4) : pc;
-        pn = j < my - 1 ? P4(c4 + sy4) : pc;
-      }
+      const float4 pp = k < mz - 1 ? P4(c4 + sz4) : pc;
+      const float4 ps = j > 0 ? P4(c4 - sy4) : pc;
+      const float4 pn = j < my - 1 ? P4(c4 + sy4) : pc;
       float west = __shfl_up_sync(0xffffffffu, pc.w, 1, L);
       float east = __shfl_down_sync(0xffffffffu, pc.x, 1, L);
       if (sl == 0) west = has_w ? P1(4 * c4 - 1) : pc.x;
@@ -552,11 +531,6 @@ __device__ __forceinline__ void march_f32(const GArgs& a, F4 P4, F1 P1, E emit, 
       if (on) emit(c4, pc, q);
       pm = pc;
       pc = pp;
-      if (PF) {
-        pp = pp2;
-        ps = ps2;
-        pn = pn2;
-      }
       c4 += sz4;
     }
   }
@@ -576,7 +550,7 @@ __device__ __forceinline__ void march_f32(const GArgs& a, F4 P4, F1 P1, E emit, 
 // holds p = 0 (its residual is 0), so an edge to it adds p_i^2; the ghost
 // faces are the array's boundary faces across the two tangential axes, and
 // x edges to the padding of the FP32 rows are left out.
-template <bool PF = false, int KIND = kOpPressure, typename F4, typename F1>
+template <int KIND = kOpPressure, typename F4, typename F1>
 __device__ __forceinline__ double edge_pass(const GArgs& a, F4 P4, F1 P1, float4* p4, Blk B = grid_blk()) {
   auto sq = [](float d) { return d * d; };
   const int my = a.my, mz = a.mz, nx4 = a.pitch >> 2;
@@ -594,27 +568,12 @@ __device__ __forceinline__ double edge_pass(const GArgs& a, F4 P4, F1 P1, float4
     const bool has_e = i4 + 1 < nx4;
     size_t c4 = (size_t(k0) * my + j) * nx4 + (i4 < nx4 ? i4 : nx4 - 1);  // idle lanes shadow the last column
     float4 pc = P4(c4);
-    float4 pp, pn;
-    if (PF) {
-      pp = k0 < mz - 1 ? P4(c4 + sz4) : pc;
-      pn = j < my - 1 ? P4(c4 + sy4) : pc;
-    }
 #pragma unroll
     for (int kk = 0; kk < kZ32; ++kk) {
       const int k = k0 + kk;
       if (k >= mz) break;
-      float4 pp2, pn2;
-      if (PF) {
-        pp2 = pp;
-        pn2 = pp;
-        if (kk + 1 < kZ32 && k + 1 < mz) {
-          pp2 = k + 1 < mz - 1 ? P4(c4 + 2 * sz4) : pp;
-          pn2 = j < my - 1 ? P4(c4 + sz4 + sy4) : pp;
-        }
-      } else {
-        pp = k < mz - 1 ? P4(c4 + sz4) : pc;
-        pn = j < my - 1 ? P4(c4 + sy4) : pc;
-      }
+      const float4 pp = k < mz - 1 ? P4(c4 + sz4) : pc;
+      const float4 pn = j < my - 1 ? P4(c4 + sy4) : pc;
       float east = __shfl_down_sync(0xffffffffu, pc.x, 1, L);
       if (sl == L - 1) east = has_e ? P1(4 * c4 + 4) : pc.w;
       else if (!has_e) east = pc.w;
@@ -650,10 +609,6 @@ __device__ __forceinline__ double edge_pass(const GArgs& a, F4 P4, F1 P1, float4
         }
       }
       pc = pp;
-      if (PF) {
-        pp = pp2;
-        pn = pn2;
-      }
       c4 += sz4;
     }
   }
@@ -715,7 +670,7 @@ __global__ void __launch_bounds__(kGThreads, kIterBlocks) g_dir_v(const GArgs a)
     return make_float4(fmaf(beta, ov.x, rv.x), fmaf(beta, ov.y, rv.y), fmaf(beta, ov.z, rv.z), fmaf(beta, ov.w, rv.w));
   };
   auto P1 = [&](size_t e) { return first ? __ldg(a.r32 + e) : fmaf(beta, __ldg(pold + e), __ldg(a.r32 + e)); };
-  double v[1] = {edge_pass<false, KIND>(a, P4, P1, reinterpret_cast<float4*>(pnew))}, o[1];
+  double v[1] = {edge_pass<KIND>(a, P4, P1, reinterpret_cast<float4*>(pnew))}, o[1];
   if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
   set_alpha(S, S->rz, o[0]);
 }
@@ -726,7 +681,7 @@ __global__ void __launch_bounds__(kGThreads, kIterBlocks) g_dir_v(const GArgs a)
 // NC: p may be read through the non-coherent path (it was written by an
 // earlier kernel; false in the batched launch, where other blocks of the
 // same launch wrote it).
-template <int KIND, bool NC = true, bool PF = false>
+template <int KIND, bool NC = true>
 __device__ __forceinline__ double upd_pass(const GArgs& a, float alpha, const float* pnew, Blk B = grid_blk()) {
   const float4* p4 = reinterpret_cast<const float4*>(pnew);
   float4* d4 = reinterpret_cast<float4*>(a.d32);
@@ -734,7 +689,7 @@ __device__ __forceinline__ double upd_pass(const GArgs& a, float alpha, const fl
   auto P4 = [&](size_t e) { return NC ? __ldg(p4 + e) : p4[e]; };
   auto P1 = [&](size_t e) { return NC ? __ldg(pnew + e) : pnew[e]; };
   double acc = 0.0;
-  march_f32<KIND, PF>(a, P4, P1, [&](size_t c4, const float4& pv, const float4& qv) {
+  march_f32<KIND>(a, P4, P1, [&](size_t c4, const float4& pv, const float4& qv) {
     float4 dv = d4[c4], rv = r4[c4];
     dv.x = fmaf(alpha, pv.x, dv.x);
     dv.y = fmaf(alpha, pv.y, dv.y);
@@ -1255,10 +1210,7 @@ __device__ bool reduce_all(const double (&v)[K], const GArgs& a, unsigned target
 #ifndef CFD_IRB_BLOCKS
 #define CFD_IRB_BLOCKS 4
 #endif
-#ifndef CFD_IRB_PF
-#define CFD_IRB_PF 0
-#endif
-constexpr bool kBatchPrefetch = CFD_IRB_PF != 0;
+
 template <int KIND>
 __global__ void __launch_bounds__(kGThreads, CFD_IRB_BLOCKS) irb_kernel(const GArgs* __restrict__ tab,
                                                            const int* __restrict__ starts, int nprob) {
@@ -1338,7 +1290,7 @@ __global__ void __launch_bounds__(kGThreads, CFD_IRB_BLOCKS) irb_kernel(const GA
                                  fmaf(b32, ov.w, rv.w));
             };
             auto P1 = [&](size_t e) { return fst ? a.r32[e] : fmaf(b32, pold[e], a.r32[e]); };
-            vd[0] = edge_pass<kBatchPrefetch, KIND>(a, P4, P1, reinterpret_cast<float4*>(pnew), B);
+            vd[0] = edge_pass<KIND>(a, P4, P1, reinterpret_cast<float4*>(pnew), B);
           } else {
             auto P = [&](size_t e) { return fst ? a.r32[e] : fmaf(b32, pold[e], a.r32[e]); };
             vd[0] = march_s32<KIND>(a, P, [&](size_t c, float pc, float q) {
@@ -1354,7 +1306,7 @@ __global__ void __launch_bounds__(kGThreads, CFD_IRB_BLOCKS) irb_kernel(const GA
           const double alpha = rz / od[0];
           double vu[1], ou[1];
           if (vec) {
-            vu[0] = upd_pass<KIND, false, kBatchPrefetch>(a, float(alpha), pnew, B);
+            vu[0] = upd_pass<KIND, false>(a, float(alpha), pnew, B);
           } else {
             const float al = float(alpha);
             vu[0] = march_s32<KIND>(a, [&](size_t e) { return pnew[e]; }, [&](size_t c, float pc, float q) {
