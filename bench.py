@@ -131,7 +131,7 @@ def parse_args(argv=None):
                     help="time the learned preconditioner's U-Net application on an N^3 grid (N % 4 == 0) "
                          "instead of the cavity")
     ap.add_argument("--unet-weights", default="", help="FP32 parameter file for --unet (default: seeded init)")
-    ap.add_argument("--unet-conv-mode", choices=["registers", "bulk", "two_stage"], default="bulk",
+    ap.add_argument("--unet-conv-mode", choices=["registers", "bulk", "two_stage", "persistent"], default="bulk",
                     help="staging of the tiled convolutions (comparison)")
     ap.add_argument("--fp64-peak", action="store_true",
                     help="measure the FP64 FMA rate (cfd_probe_fp64_fma) instead of the cavity")

@@ -573,8 +573,12 @@ int cfd_unet_set_loss(cfd_unet *u, int kind);
  *              copy of the weights (kept in shared-memory order), then the
  *              MMAs (default)
  *   TWO_STAGE  as BULK with two stages: block cb + 1 is copied while the
- *              MMAs of block cb run (halves the tile and the occupancy) */
-enum { CFD_UNET_CONV_REGISTERS = 0, CFD_UNET_CONV_BULK = 1, CFD_UNET_CONV_TWO_STAGE = 2 };
+ *              MMAs of block cb run (halves the tile and the occupancy)
+ *   PERSISTENT one CTA per SM walks many tiles: one warp streams (tile,
+ *              block) units into two stages, one issues the MMAs into two
+ *              TMEM accumulators (tiles alternate), four store the finished
+ *              tile, so copies, MMAs and stores overlap */
+enum { CFD_UNET_CONV_REGISTERS = 0, CFD_UNET_CONV_BULK = 1, CFD_UNET_CONV_TWO_STAGE = 2, CFD_UNET_CONV_PERSISTENT = 3 };
 int cfd_unet_set_conv_mode(cfd_unet *u, int mode);
 
 /* Where the weight gradients of cfd_unet_train_step run:

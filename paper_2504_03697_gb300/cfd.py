@@ -560,8 +560,9 @@ class UNet:
         self._check(self.lib.cfd_unet_set_loss(self.u, {"mse": 0, "anorm": 1, "cos": 2}[kind]))
 
     def set_conv_mode(self, mode: str):
-        """'registers', 'bulk' (default) or 'two_stage' (cfd_unet_set_conv_mode)."""
-        self._check(self.lib.cfd_unet_set_conv_mode(self.u, {"registers": 0, "bulk": 1, "two_stage": 2}[mode]))
+        """'registers', 'bulk' (default), 'two_stage' or 'persistent' (cfd_unet_set_conv_mode)."""
+        self._check(self.lib.cfd_unet_set_conv_mode(
+            self.u, {"registers": 0, "bulk": 1, "two_stage": 2, "persistent": 3}[mode]))
 
     def set_wgrad_mode(self, mode: str):
         """'tensor' (default: the 3x3x3 layers' weight gradients on the tensor

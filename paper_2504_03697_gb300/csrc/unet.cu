@@ -240,6 +240,8 @@ constexpr int kTileSmemMax = 210 * 1024;  // dynamic shared memory cap (static u
 struct ConvTileArgs {
   CUtensorMap map0;            // src0 [nz][ny][nx][c0], box {8, bx, by, bz}
   CUtensorMap map1;            // src1 (concatenation) or unused
+  const __nv_bfloat16* src0;   // the same tensors (octet planes), for row copies
+  const __nv_bfloat16* src1;
   int nx, ny, nz;
   int c0, c1;
   int xc, ty, tz;              // output box
@@ -568,6 +570,262 @@ __global__ void __launch_bounds__(kConvThreads) conv3d_tile_pipe_kernel(const __
   if (t < 32) tc::tmem_dealloc(tmem, tmem_cols);
 }
 
+// Persistent warp-specialised variant (weights in shared-memory order, as
+// the pipelined kernel): one CTA per SM walks the tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...; warp 0 copies each (tile, channel block)
+// unit into one of kWsStages shared-memory stages: the input box's x-rows of
+// the two octet planes as contiguous bulk copies (one per row, up to 130
+// voxels of 16 bytes; the box image is the one the TMA copies of the other
+// kernels produce, with zeros outside the grid written by the warp) and the
+// block's weights as one bulk copy; one lane of warp 1
+// waits for a unit, issues its 27 x mb MMAs into one of two TMEM
+// accumulators (tiles alternate between them) and commits to the stage's
+// "empty" barrier, and after a tile's last block also to the accumulator's
+// "full" barrier; warps 2-5 (one TMEM lane quarter each) read a finished
+// accumulator, add the bias, store, and release it.  So the copies of the
+// next unit, the MMAs of this one and the epilogue of the previous tile
+// overlap.  The MMAs of a tile are those of the other kernels in the same
+// order, so the results are bitwise equal.  Every wait is bounded; on a
+// timeout the CTA lets its copies and MMAs in flight finish, sets *err and
+// returns.
+constexpr int kWsStages = 2;
+constexpr int kWsThreads = 192;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(b)) : "memory");
+}
+
+template <int NOUT>
+__global__ void __launch_bounds__(kWsThreads, 1) conv3d_tile_ws_kernel(const __grid_constant__ ConvTileArgs a,
+                                                                       int ntiles, unsigned stage_bytes) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  __shared__ __align__(8) uint64_t bar_full[kWsStages], bar_empty[kWsStages], bar_tfull[2], bar_tempty[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_start[kTileMaxMB];
+  __shared__ volatile int s_fail;
+  __shared__ volatile int s_issued, s_consumed, s_mma;  // units copied / awaited / whose MMAs were issued
+  constexpr int kBTap = NOUT * 32;
+  constexpr unsigned kBBytes = 27u * kBTap;
+  const int t = threadIdx.x, warp = t / 32, lane = t % 32;
+  const int cb0 = a.c0 / 16;
+  const int ncb = cb0 + a.c1 / 16;
+  const int acc_cols = a.mb * NOUT;
+  const int need = 2 * acc_cols;
+  const uint32_t tmem_cols = need <= 32 ? 32u : (need <= 64 ? 64u : (need <= 128 ? 128u : (need <= 256 ? 256u : 512u)));
+  const int my_tiles = ntiles > int(blockIdx.x) ? (ntiles - 1 - int(blockIdx.x)) / int(gridDim.x) + 1 : 0;
+  const int units = my_tiles * ncb;
+  auto origin = [&](int tl, int& x0, int& y0, int& z0) {
+    const int g = int(blockIdx.x) + tl * int(gridDim.x);
+    const int tx = g % a.tiles_x, ty_ = (g / a.tiles_x) % a.tiles_y, tz_ = g / (a.tiles_x * a.tiles_y);
+    x0 = tx * a.xc;
+    y0 = ty_ * a.ty;
+    z0 = tz_ * a.tz;
+  };
+
+  if (t == 0) {
+    for (int q = 0; q < kWsStages; ++q) {
+      tc::mbar_init(&bar_full[q], 1);
+      tc::mbar_init(&bar_empty[q], 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      tc::mbar_init(&bar_tfull[q], 1);
+      tc::mbar_init(&bar_tempty[q], 4);
+    }
+    tc::mbar_fence_init();
+    s_fail = 0;
+    s_issued = 0;
+    s_consumed = 0;
+    s_mma = 0;
+  }
+  if (t < kTileMaxMB) s_start[t] = t < a.mb ? tile_block_start(a, t) : 0;
+  if (warp == 0) tc::tmem_alloc(&s_tmem, tmem_cols);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = s_tmem;
+
+  if (warp == 0) {  // producer: the whole warp
+    const int nrow = a.by * a.bz;  // x-rows of the input box per plane
+    const size_t V = size_t(a.nx) * a.ny * a.nz;
+    for (int u = 0; u < units; ++u) {
+      const int sg = u % kWsStages;
+      int ok = 1;
+      if (lane == 0 && u >= kWsStages &&
+          !tc::mbar_wait(&bar_empty[sg], unsigned(((u / kWsStages) - 1) & 1), kConvWaitNs))
+        ok = 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok || s_fail) {
+        if (lane == 0) s_fail = 1;
+        break;
+      }
+      const int tl = u / ncb, cb = u % ncb;
+      int x0, y0, z0;
+      origin(tl, x0, y0, z0);
+      unsigned char* base = dsm + size_t(sg) * stage_bytes;
+      const __nv_bfloat16* src = cb < cb0 ? a.src0 : a.src1;
+      const int oct = 2 * (cb < cb0 ? cb : cb - cb0);
+      // the box's x-rows: voxels [xs, xs + bx) of row (y, z); the part inside
+      // the grid, [vx0, vx1), is one contiguous run of 16-byte voxels in each
+      // octet plane; the rest (and rows outside the grid) is zero
+      const int xs = x0 - 1;
+      const int vx0 = xs > 0 ? xs : 0, vx1 = xs + a.bx < a.nx ? xs + a.bx : a.nx;
+      const int nvalid = vx1 > vx0 ? vx1 - vx0 : 0;
+      auto row_valid = [&](int rr, int& gy, int& gz) {
+        gy = y0 - 1 + rr % a.by;
+        gz = z0 - 1 + rr / a.by;
+        return nvalid > 0 && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz;
+      };
+      int nrows_valid = 0;
+      for (int q = lane; q < 2 * nrow; q += 32) {
+        const int h = q / nrow, rr = q % nrow;
+        int gy, gz;
+        const bool v = row_valid(rr, gy, gz);
+        uint4* row = reinterpret_cast<uint4*>(base + h * size_t(a.plane) + size_t(rr) * a.bx * 16);
+        const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
+        if (!v) {
+          for (int x = 0; x < a.bx; ++x) row[x] = z4;
+        } else {
+          for (int x = 0; x < vx0 - xs; ++x) row[x] = z4;
+          for (int x = vx1 - xs; x < a.bx; ++x) row[x] = z4;
+          nrows_valid += 1;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) nrows_valid += __shfl_down_sync(0xffffffffu, nrows_valid, o);
+      tc::fence_proxy_async_smem();  // the zero fill is read by the tensor cores
+      __syncwarp();
+      if (lane == 0) tc::mbar_expect_tx(&bar_full[sg], unsigned(nrows_valid) * unsigned(nvalid) * 16u + kBBytes);
+      __syncwarp();
+      for (int q = lane; q < 2 * nrow; q += 32) {
+        const int h = q / nrow, rr = q % nrow;
+        int gy, gz;
+        if (!row_valid(rr, gy, gz)) continue;
+        unsigned char* dst = base + h * size_t(a.plane) + (size_t(rr) * a.bx + size_t(vx0 - xs)) * 16;
+        const __nv_bfloat16* from = src + ((size_t(oct + h) * V + (size_t(gz) * a.ny + gy) * a.nx + vx0) * 8);
+        bulk_copy_g2s(dst, from, unsigned(nvalid) * 16u, &bar_full[sg]);
+      }
+      if (lane == 0) {
+        bulk_copy_g2s(base + 2 * size_t(a.plane), a.w_cm + size_t(cb) * (kBBytes / 2), kBBytes, &bar_full[sg]);
+        s_issued = u + 1;
+      }
+      __syncwarp();
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      const uint32_t idesc = tc::idesc_bf16_f32(128, NOUT);
+      const int row_z = a.by * a.bx;
+      int st[kTileMaxMB];
+#pragma unroll
+      for (int j = 0; j < kTileMaxMB; ++j) st[j] = s_start[j];
+      for (int u = 0; u < units && !s_fail; ++u) {
+        const int sg = u % kWsStages, tl = u / ncb, cb = u % ncb, b = tl & 1;
+        if (!tc::mbar_wait(&bar_full[sg], unsigned((u / kWsStages) & 1), kConvWaitNs)) {
+          s_fail = 1;
+          break;
+        }
+        s_consumed = u + 1;
+        if (cb == 0 && tl >= 2 && !tc::mbar_wait(&bar_tempty[b], unsigned(((tl >> 1) - 1) & 1), kConvWaitNs)) {
+          s_fail = 1;
+          break;
+        }
+        tc::fence_after_sync();
+        unsigned char* base = dsm + size_t(sg) * stage_bytes;
+        const uint64_t adesc0 = tc::smem_desc(tc::smem_addr(base), uint32_t(a.plane), 128);
+        const uint64_t bdesc0 = tc::smem_desc(tc::smem_addr(base + 2 * size_t(a.plane)), 128, 256);
+        const uint32_t dcol = tmem + uint32_t(b * acc_cols);
+        int tap = 0;
+        for (int dz = -1; dz <= 1; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx, ++tap) {
+              const int off = dz * row_z + dy * a.bx + dx;
+              const uint64_t bdesc = bdesc0 + uint64_t(tap * (kBTap >> 4));
+              const bool acc = (cb | tap) != 0;
+#pragma unroll
+              for (int j = 0; j < kTileMaxMB; ++j)
+                if (j < a.mb) tc::mma_bf16(dcol + uint32_t(j * NOUT), adesc0 + uint64_t(st[j] + off), bdesc, idesc, acc);
+            }
+        tc::mma_commit(&bar_empty[sg]);
+        if (cb == ncb - 1) tc::mma_commit(&bar_tfull[b]);
+        s_mma = u + 1;
+      }
+    }
+  } else {  // epilogue: warps 2-5, TMEM lane quarter q
+    const int q = warp & 3, e = q * 32 + lane;
+    const int bxby = a.bx * a.by;
+    const size_t Vt = size_t(a.nx) * a.ny * a.nz;
+    // the voxel of TMEM lane e in M-block j, relative to the tile origin
+    // (the same for every tile), and the bias of the output channels
+    int rel[kTileMaxMB];
+#pragma unroll
+    for (int j = 0; j < kTileMaxMB; ++j) {
+      rel[j] = -1;
+      if (j < a.mb) {
+        const int row = s_start[j] + e;
+        const int zq = row / bxby, rem = row - zq * bxby;
+        const int yq = rem / a.bx, xq = rem - yq * a.bx;
+        if (xq >= 1 && xq <= a.xc && yq >= 1 && yq <= a.ty && zq >= 1 && zq <= a.tz)
+          rel[j] = ((zq - 1) * 256 + (yq - 1)) * 256 + (xq - 1);  // z, y, x offsets (each < 256)
+      }
+    }
+    float bias[NOUT];
+#pragma unroll
+    for (int c = 0; c < NOUT; ++c) bias[c] = a.bias && c < a.cout ? a.bias[c] : 0.f;
+    for (int tl = 0; tl < my_tiles; ++tl) {
+      const int b = tl & 1;
+      bool ok = !s_fail && tc::mbar_wait(&bar_tfull[b], unsigned((tl >> 1) & 1), kConvWaitNs);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        if (lane == 0) s_fail = 1;
+        break;
+      }
+      tc::fence_after_sync();
+      int x0, y0, z0;
+      origin(tl, x0, y0, z0);
+#pragma unroll
+      for (int j = 0; j < kTileMaxMB; ++j) {
+        if (j >= a.mb) break;
+        const int r = rel[j];
+        const int gx = x0 + (r & 255), gy = y0 + ((r >> 8) & 255), gz = z0 + (r >> 16);
+        const bool valid = r >= 0 && gx < a.nx && gy < a.ny && gz < a.nz;
+        const size_t v = (size_t(gz) * a.ny + gy) * a.nx + gx;
+#pragma unroll
+        for (int c0 = 0; c0 < NOUT; c0 += 16) {
+          float acc[16];
+          tc::tmem_ld16(tmem + (uint32_t(q * 32) << 16) + uint32_t(b * acc_cols + j * NOUT + c0), acc);
+          if (valid && c0 < a.cout) {
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+              const int cbase = c0 + 8 * half;
+              if (cbase >= a.cout) break;
+              __nv_bfloat16 o8[8];
+#pragma unroll
+              for (int k = 0; k < 8; ++k) o8[k] = __float2bfloat16(acc[8 * half + k] + bias[cbase + k]);
+              __nv_bfloat16* dst = cbase < a.split ? a.dst0 + oct_index(v, cbase, a.split, Vt)
+                                                   : a.dst1 + oct_index(v, cbase - a.split, a.cout - a.split, Vt);
+              *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<uint4*>(o8);
+            }
+          }
+        }
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar_tempty[b]);
+    }
+  }
+  __syncthreads();
+  if (s_fail && t == 0) {
+    // copies issued but not awaited, and the MMAs issued last, finish before
+    // the shared memory and TMEM are released
+    for (int u = s_consumed; u < s_issued; ++u)
+      tc::mbar_wait(&bar_full[u % kWsStages], unsigned((u / kWsStages) & 1), kConvWaitNs);
+    if (s_mma > 0)
+      tc::mbar_wait(&bar_empty[(s_mma - 1) % kWsStages], unsigned(((s_mma - 1) / kWsStages) & 1), kConvWaitNs);
+    atomicExch(a.err, 1);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   static std::once_flag once;
@@ -606,11 +864,13 @@ int plane_bytes(const ConvTileArgs& t, int ty, int tz) {
   return ((rows + slack) * 16 + 127) / 128 * 128;
 }
 
-bool pick_tile(ConvTileArgs& t, int nout, int stages) {
+// tmem: TMEM columns the tile's accumulators may take (512, or 256 when
+// the persistent kernel double-buffers them); smem_cap: bytes of all stages.
+bool pick_tile(ConvTileArgs& t, int nout, int stages, int tmem = 512, size_t smem_cap = 200 * 1024) {
   t.xc = t.nx >= 128 ? 128 : t.nx;
   t.bx = t.xc + 2;
   t.line_mode = t.xc == 128 ? 1 : 0;
-  const int max_mb = std::min(kTileMaxMB, 512 / nout);
+  const int max_mb = std::min(kTileMaxMB, tmem / nout);
   int best_ty = 1, best_tz = 1, best_mb = 0;
   double best_eff = -1.0;
   for (int tz = 1; tz <= 4; tz *= 2) {
@@ -626,7 +886,7 @@ bool pick_tile(ConvTileArgs& t, int nout, int stages) {
       if (mb > max_mb) continue;
       const int rows = t.bx * (ty + 2) * (tz + 2);
       const size_t smem = size_t(stages) * (2 * size_t(plane_bytes(t, ty, tz)) + size_t(27) * nout * 32);
-      if (smem > 200 * 1024) continue;
+      if (smem > smem_cap) continue;
       // useful outputs per unit of (MMA rows + loaded rows)
       const double eff = double(t.xc * ty * tz) / double(mb * 128 * 27 + rows * 4);
       if (eff > best_eff + 1e-12) {
@@ -658,9 +918,17 @@ cudaError_t launch_tile(const ConvArgs& a, cudaStream_t s, bool& taken) {
   t.nx = a.nx; t.ny = a.ny; t.nz = a.nz;
   t.c0 = a.c0; t.c1 = a.c1;
   const bool bulk = a.w_cm != nullptr && !(reinterpret_cast<uintptr_t>(a.w_cm) & 15);
+  const bool ws = bulk && a.stages == 3;  // persistent warp-specialised kernel
   const int stages = bulk ? (a.stages == 2 ? 2 : 1) : 1;
-  if (!pick_tile(t, NOUT, stages)) return cudaSuccess;
+  if (ws) {
+    // two stages of 1024-aligned (planes + weights), two TMEM accumulators
+    if (!pick_tile(t, NOUT, kWsStages, 256, size_t(kTileSmemMax) - 2 * 1024)) return cudaSuccess;
+  } else if (!pick_tile(t, NOUT, stages)) {
+    return cudaSuccess;
+  }
   if (!encode_oct_map(&t.map0, a.src0, a.c0, a.nx, a.ny, a.nz, t.bx, t.by, t.bz)) return cudaSuccess;
+  t.src0 = a.src0;
+  t.src1 = a.src1;
   if (a.c1 > 0 && !encode_oct_map(&t.map1, a.src1, a.c1, a.nx, a.ny, a.nz, t.bx, t.by, t.bz)) return cudaSuccess;
   t.w = a.w;
   t.w_cm = bulk ? a.w_cm : nullptr;
@@ -669,6 +937,27 @@ cudaError_t launch_tile(const ConvArgs& a, cudaStream_t s, bool& taken) {
   t.cout = a.cout;
   t.dst0 = a.dst0; t.dst1 = a.dst1; t.split = a.split;
   t.err = a.err;
+  const unsigned grid_tiles = unsigned(t.tiles_x) * unsigned(t.tiles_y) * unsigned((t.nz + t.tz - 1) / t.tz);
+  if (ws) {
+    const unsigned stage_bytes = unsigned((2 * size_t(t.plane) + size_t(27) * NOUT * 32 + 1023) / 1024 * 1024);
+    const size_t req = size_t(kWsStages) * stage_bytes;
+    if (req > size_t(kTileSmemMax)) return cudaSuccess;
+    static int ws_configured = 0;
+    if (!ws_configured) {
+      cudaError_t e =
+          cudaFuncSetAttribute(conv3d_tile_ws_kernel<NOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemMax);
+      if (e != cudaSuccess) return e;
+      ws_configured = 1;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // one CTA per SM (the shared memory of two stages), at most one per tile
+    const unsigned grid = std::min(grid_tiles, unsigned(sms > 0 ? sms : 1));
+    conv3d_tile_ws_kernel<NOUT><<<grid, kWsThreads, req, s>>>(t, int(grid_tiles), stage_bytes);
+    taken = true;
+    return cudaGetLastError();
+  }
   const size_t smem = size_t(stages) * (2 * size_t(t.plane) + size_t(27) * NOUT * 32);
   // TMEM: at most 512 / cols CTAs may share an SM; pad the shared-memory
   // request so that no more than that many fit
@@ -689,7 +978,7 @@ cudaError_t launch_tile(const ConvArgs& a, cudaStream_t s, bool& taken) {
     if (e != cudaSuccess) return e;
     configured = 1;
   }
-  const unsigned grid = unsigned(t.tiles_x) * unsigned(t.tiles_y) * unsigned((t.nz + t.tz - 1) / t.tz);
+  const unsigned grid = grid_tiles;
   if (bulk && stages == 2)
     conv3d_tile_pipe_kernel<NOUT, 2><<<grid, kConvThreads, req, s>>>(t);
   else if (bulk)

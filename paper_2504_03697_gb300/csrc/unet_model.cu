@@ -1074,7 +1074,7 @@ int conv(cfd_unet* u, int layer, const __nv_bfloat16* src0, const __nv_bfloat16*
   a.ks = L.ks; a.packed = L.packed ? 1 : 0;
   a.w = u->wf[layer];
   a.w_cm = u->conv_mode == CFD_UNET_CONV_REGISTERS ? nullptr : u->wfc[layer];
-  a.stages = u->conv_mode == CFD_UNET_CONV_TWO_STAGE ? 2 : 1;
+  a.stages = u->conv_mode == CFD_UNET_CONV_TWO_STAGE ? 2 : (u->conv_mode == CFD_UNET_CONV_PERSISTENT ? 3 : 1);
   a.bias = u->w + u->boff[layer];
   a.cout = L.cout;
   a.dst0 = dst0; a.dst1 = dst1; a.split = split; a.dst_f32 = dst_f32;
@@ -1093,7 +1093,7 @@ int conv_dgrad(cfd_unet* u, int layer, int slice, const __nv_bfloat16* gout, int
   a.ks = L.ks; a.packed = 0;
   a.w = u->wd[layer][slice];
   a.w_cm = u->conv_mode == CFD_UNET_CONV_REGISTERS ? nullptr : u->wdc[layer][slice];
-  a.stages = u->conv_mode == CFD_UNET_CONV_TWO_STAGE ? 2 : 1;
+  a.stages = u->conv_mode == CFD_UNET_CONV_TWO_STAGE ? 2 : (u->conv_mode == CFD_UNET_CONV_PERSISTENT ? 3 : 1);
   a.bias = nullptr;
   a.cout = o_count;
   a.dst0 = dst0; a.dst1 = dst1; a.split = split; a.dst_f32 = nullptr;
@@ -1470,7 +1470,7 @@ int cfd_unet_train_step(cfd_unet* u, const double* r_dev, const double* e_dev, i
 }
 
 int cfd_unet_set_conv_mode(cfd_unet* u, int mode) {
-  if (!u || mode < CFD_UNET_CONV_REGISTERS || mode > CFD_UNET_CONV_TWO_STAGE)
+  if (!u || mode < CFD_UNET_CONV_REGISTERS || mode > CFD_UNET_CONV_PERSISTENT)
     return uerr(CFD_ERR_INVALID_ARG, "unet: NULL handle or unknown convolution mode");
   u->conv_mode = mode;
   return CFD_OK;

@@ -126,19 +126,21 @@ def test_forward_layerwise(cfd):
 
 @pytest.mark.parametrize("shape", [(16, 12, 8), (128, 8, 8), (40, 24, 16)])
 def test_pipelined_convolutions_are_bitwise_equal(cfd, shape):
-    # the three staging modes of the tiled convolution issue the same MMAs in
-    # the same order: forward outputs and all gradients agree bitwise
+    # the staging modes of the tiled convolution (one CTA per tile with one
+    # or two stages, and the persistent warp-specialised kernel) issue the
+    # same MMAs in the same order: forward outputs and all gradients agree
+    # bitwise
     nx, ny, nz = shape
     r = torch.from_numpy(uniform_field((nz, ny, nx), 71)).cuda()
     e = torch.from_numpy(uniform_field((nz, ny, nx), 72)).cuda()
     outs = []
-    for mode in ("bulk", "two_stage", "registers"):
+    for mode in ("bulk", "two_stage", "registers", "persistent"):
         net = cfd.UNet(nx, ny, nz, seed=29)
         net.set_conv_mode(mode)
         net.train_step(r, e, lr=0.0)
         outs.append([net.read_tensor(name) for name in cfd.UNET_TENSORS] + [net.read_tensor(cfd.UNET_T_GRAD)])
-    for name, a, b, c in zip(cfd.UNET_TENSORS + ["grad"], *outs):
-        assert torch.equal(a, b) and torch.equal(a, c), name
+    for name, a, b, c, d in zip(cfd.UNET_TENSORS + ["grad"], *outs):
+        assert torch.equal(a, b) and torch.equal(a, c) and torch.equal(a, d), name
 
 
 def test_apply_output_is_scaled_zero_mean(cfd):
