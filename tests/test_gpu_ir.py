@@ -22,6 +22,17 @@ from paper_2504_03697_gb300.synthetic import gaussian_rhs, uniform_field  # noqa
 
 pytestmark = pytest.mark.gpu
 
+ITERS_PER_PASS = 4  # FP32 iterations per pass of the graph form's inner loop body
+
+
+def assert_graph_kernels(ran, base, st):
+    """Kernels a graph-form solve ran: `base` (2 per FP32 iteration plus the
+    fixed ones) and, per inner loop (at most one per refinement plus the
+    first), the 2 (ITERS_PER_PASS - 1) or fewer kernels of its last pass
+    that return at once because the loop was left."""
+    extra = ran - base
+    assert extra % 2 == 0 and 0 <= extra <= 2 * (ITERS_PER_PASS - 1) * (st["outer_iters"] + 1), (ran, base, st)
+
 
 @pytest.fixture(scope="module")
 def cfd():
@@ -144,8 +155,10 @@ def test_ir_graph_true_residual_and_bound(cfd, shape, delta):
     assert st["outer_iters"] >= 1
     so = _check_solution(shape, b, xg.cpu().numpy().ravel(), st)
     # kernels the graph ran: prologue 2, each outer pass 2, each FP32
-    # iteration 2, epilogue 3 (the loop structure as designed)
-    assert cav.launch_count() - l0 == 2 + 2 * (st["outer_iters"] + 1) + 2 * st["iters"] + 3
+    # iteration 2, epilogue 3 (the loop structure as designed), plus the
+    # kernels left over in the last pass of each inner loop (4 iterations
+    # per pass of its body: at most 6 per inner loop)
+    assert_graph_kernels(cav.launch_count() - l0, 2 + 2 * (st["outer_iters"] + 1) + 2 * st["iters"] + 3, st)
     print(f"IR graph {shape}: inner {st['iters']} outer {st['outer_iters']} (FP64 CG {so.iters})")
 
 
@@ -259,7 +272,7 @@ def test_ir_graph_full_size_256(cfd):
     l0 = cav.launch_count()
     rc, st = cav.solve_pressure(bg, xg)
     assert rc == cfd.CFD_OK
-    assert cav.launch_count() - l0 == 2 + 2 * (st["outer_iters"] + 1) + 2 * st["iters"] + 3
+    assert_graph_kernels(cav.launch_count() - l0, 2 + 2 * (st["outer_iters"] + 1) + 2 * st["iters"] + 3, st)
     x = xg.cpu().numpy()
     bo = b - b.mean()
     A3, A2 = poisson_csr(n, n, 3), poisson_csr(n, n, 2)
