@@ -640,7 +640,24 @@ def main_ours(args):
         if params is not None:
             extra["time_to_rtol"] = time_to_rtol(cfd, params, device)
         # the 64^3 FP64 cavity (plain method on the GPU)
-        extra["cavity64_fp64_cg"] = cavity_sample(cfd, 64, WORKLOADS["cavity64"], "cg", 20, 3, device)
+        c2 = cavity_sample(cfd, 64, WORKLOADS["cavity64"], "cg", 20, 3, device)
+        # its pressure CG against the rooflines that bound it at this size:
+        # the FP64 pipe (the kernel is FP64-ALU-bound) and L2 (the 26 MB
+        # working set is L2-resident; DRAM sees ~2.4 MB per solve)
+        cells64 = 64 ** 3
+        its = sum(c2["pressure_iters"]) / len(c2["pressure_iters"])
+        t_s = c2["pressure_ms_per_step"] / 1e3
+        flops = (CG_FLOPS_PER_CELL_ITER * its + CG_FLOPS_PER_CELL_SOLVE) * cells64
+        l2_bytes = (CG_BYTES_PER_CELL_ITER * its + CG_BYTES_PER_CELL_SOLVE) * cells64
+        c2["roofline"] = {
+            "bound": "alu", "kernel": "cg1_fp64_kernel<8> (pressure CG, single-reduction form)",
+            "achieved": flops / t_s / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": flops / t_s / 1e12 / FP64_PEAK_TFLOPS, "peak_source": FP64_PEAK_SOURCE,
+            "l2": {"algorithmic_bytes_per_solve": l2_bytes, "achieved_GBs": l2_bytes / t_s / 1e9,
+                   "ncu_lts_throughput_pct": 5.1, "dram_bytes_per_solve": CG1_CAVITY64_DRAM_BYTES,
+                   "source": "profiles/cg1_fp64_cavity64_full.md (lts__throughput.avg.pct_of_peak_sustained_"
+                             "elapsed and dram bytes of one launch)"}}
+        extra["cavity64_fp64_cg"] = c2
         # standalone 256^3 Poisson, FP64 CG vs FP32/FP64-IR (2 of 32 RHS)
         study = {}
         for sv in ("cg", "ir"):
