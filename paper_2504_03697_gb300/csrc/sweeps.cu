@@ -39,6 +39,15 @@ struct FaceDims {
   int mx, my, mz;
 };
 
+// (i, j, k) of linear index l in an mx x my x mz array (fewer than 2^32
+// elements: 32-bit divisions)
+__device__ __forceinline__ void decode3(size_t l, int mx, int my, int& i, int& j, int& k) {
+  const unsigned u = unsigned(l), row = u / unsigned(mx);
+  i = int(u - row * unsigned(mx));
+  k = int(row / unsigned(my));
+  j = int(row - unsigned(k) * unsigned(my));
+}
+
 __device__ __forceinline__ FaceDims face_dims(int comp, int nx, int ny, int nz) {
   return FaceDims{nx + (comp == 0), ny + (comp == 1), nz + (comp == 2)};
 }
@@ -136,9 +145,8 @@ __device__ __forceinline__ void advect_body(const PhysArgs& a, size_t t0, size_t
     else if (e < n0 + n1) { comp = 1; l = e - n0; }
     else { comp = 2; l = e - n0 - n1; }
     const FaceDims fd = face_dims(comp, nx, ny, nz);
-    const int i = int(l % fd.mx);
-    const int j = int((l / fd.mx) % fd.my);
-    const int k = int(l / (size_t(fd.mx) * fd.my));
+    int i, j, k;
+    decode3(l, fd.mx, fd.my, i, j, k);
     const int own = comp == 0 ? i : (comp == 1 ? j : k);
     const int own_n = comp == 0 ? nx : (comp == 1 ? ny : nz);
     if (own == 0 || own == own_n) {
@@ -217,7 +225,8 @@ __device__ __forceinline__ void diffusion_rhs_body(const PhysArgs& a, int comp, 
   const size_t n = size_t(fd.mx) * fd.my * fd.mz;
   const double* f = comp == 0 ? a.ua : (comp == 1 ? a.va : a.wa);
   for (size_t e = t0; e < n; e += stride) {
-    const int i = int(e % fd.mx), j = int((e / fd.mx) % fd.my), k = int(e / (size_t(fd.mx) * fd.my));
+    int i, j, k;
+    decode3(e, fd.mx, fd.my, i, j, k);
     const int own = comp == 0 ? i : (comp == 1 ? j : k);
     const int own_n = comp == 0 ? a.nx : (comp == 1 ? a.ny : a.nz);
     double v = 0.0;
@@ -240,7 +249,8 @@ __device__ __forceinline__ void divergence_body(const PhysArgs& a, double scale,
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const size_t n = size_t(nx) * ny * nz;
   for (size_t e = t0; e < n; e += stride) {
-    const int i = int(e % nx), j = int((e / nx) % ny), k = int(e / (size_t(nx) * ny));
+    int i, j, k;
+    decode3(e, nx, ny, i, j, k);
     const double du = a.ua[idx3(i + 1, j, k, nx + 1, ny)] - a.ua[idx3(i, j, k, nx + 1, ny)];
     const double dv = a.va[idx3(i, j + 1, k, nx, ny + 1)] - a.va[idx3(i, j, k, nx, ny + 1)];
     const double dw = a.wa[idx3(i, j, k + 1, nx, ny)] - a.wa[idx3(i, j, k, nx, ny)];
@@ -267,7 +277,8 @@ __device__ __forceinline__ void correct_body(const PhysArgs& a, double s, size_t
     else if (e < n0 + n1) { comp = 1; l = e - n0; }
     else { comp = 2; l = e - n0 - n1; }
     const FaceDims fd = face_dims(comp, nx, ny, nz);
-    const int i = int(l % fd.mx), j = int((l / fd.mx) % fd.my), k = int(l / (size_t(fd.mx) * fd.my));
+    int i, j, k;
+    decode3(l, fd.mx, fd.my, i, j, k);
     const double* in = comp == 0 ? a.ua : (comp == 1 ? a.va : a.wa);
     double* out = comp == 0 ? a.u : (comp == 1 ? a.v : a.w);
     const int own = comp == 0 ? i : (comp == 1 ? j : k);
