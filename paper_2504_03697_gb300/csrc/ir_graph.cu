@@ -17,17 +17,23 @@
 // and reads and writes x32 and r32.  q is never stored.
 //
 //   memset(counter) -> pro_sum -> pro_resid ->
-//   while (outer) { prep -> while (inner) { dir -> upd } -> refine } ->
+//   while (outer) { prep -> while (inner) { (dir -> upd) x kItersPerPass } -> refine } ->
 //   epi_resid -> finish -> shift
 //
 // `outer` and `inner` are conditional graph nodes of type while.  Each
 // kernel reduces its partial sums in FP64 through a last-block pass (blocks
 // add their sums to a fixed slot, the block that arrives last sums the slots
 // in block order), and that block's thread 0 updates the solver scalars in
-// GState and sets the loop conditions.  Nothing waits on another block: the
-// graph's node order is the only synchronisation.  Every loop ends: each
-// pass of the inner body raises `iters` by one and the outer body stops the
-// loops once iters >= max_iters or refinements > max_outer.
+// GState and sets the loop conditions; once an update kernel has left the
+// inner loop, the kernels after it in the same pass of the body return at
+// once.  Nothing waits on another block: the graph's node order is the only
+// synchronisation.  Every loop ends: each update raises `iters` by one and
+// the outer body stops the loops once iters >= max_iters or refinements >
+// max_outer.
+//
+// The batched form (irb_kernel, below) runs the same passes for many
+// independent systems inside one persistent cooperative launch, with the
+// loop control in registers and a problem-wide reduction per phase.
 //
 // Operators: the pressure matrix (float4 kernels, mx % 4 == 0) and the
 // velocity matrices of the diffusion substep (float4 kernels on FP32 rows
