@@ -90,10 +90,9 @@ constexpr int kIterBlocks = 5;
 // 27.5 us per iteration at 128^3 and 329 against 334 us at 384^3.
 constexpr int kItersPerPass = 4;
 constexpr int kGMax = 1024;     // blocks per kernel (partial-sum slots per value)
-#ifndef CFD_IRG_ZPLANES
-#define CFD_IRG_ZPLANES 4
-#endif
-constexpr int kZ32 = CFD_IRG_ZPLANES;  // z planes per FP32 stencil work item
+// z planes per FP32 stencil work item (2, 8 and 16 measured no faster at
+// 384^3; 16 slower)
+constexpr int kZ32 = 4;
 constexpr int kZ64 = 4;         // z planes per FP64 stencil work item
 
 // Solver scalars of one solve (device memory, written only by the thread 0
@@ -1220,12 +1219,13 @@ __device__ bool reduce_all(const double (&v)[K], const GArgs& a, unsigned target
   return true;
 }
 
-#ifndef CFD_IRB_BLOCKS
-#define CFD_IRB_BLOCKS 4
-#endif
+// resident blocks per SM of the batched kernel (3 measured slower: the
+// streaming passes want the warps more than the registers)
+constexpr int kBatchBlocks = 4;
+
 
 template <int KIND>
-__global__ void __launch_bounds__(kGThreads, CFD_IRB_BLOCKS) irb_kernel(const GArgs* __restrict__ tab,
+__global__ void __launch_bounds__(kGThreads, kBatchBlocks) irb_kernel(const GArgs* __restrict__ tab,
                                                            const int* __restrict__ starts, int nprob) {
   int lo = 0, hi = nprob - 1;
   const int blk = int(blockIdx.x);
