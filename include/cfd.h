@@ -246,12 +246,14 @@ int cfd_set_cg_variant(cfd_handle *h, int variant);
  *               operator, update) and the FP64 refinements as separate
  *               kernels; each kernel's last block updates the solver scalars
  *               and the loop conditions.  Needs nx % 4 == 0.
- *   AUTO        (default) GRAPH when nx % 4 == 0 and the grid has at least
- *               2^21 cells, PERSISTENT otherwise.
+ *   AUTO        (default) GRAPH when nx % 4 == 0, PERSISTENT otherwise
+ *               (the graph form measured faster at every size from 64^3 to
+ *               384^3).
  * The diffusion solves of the step follow the same form (in the GRAPH form
- * on scalar-lane kernels, any width).
- * Errors: unknown form; GRAPH with nx % 4 != 0.  Batches always use the
- * persistent multi-problem kernel. */
+ * on float4 lanes over FP32 rows padded to a multiple of 4 cells, any
+ * width).
+ * Errors: unknown form; GRAPH with nx % 4 != 0.  Batches run the batched
+ * graph form: each cavity's solve inside one persistent cooperative launch. */
 enum { CFD_IR_AUTO = 0, CFD_IR_PERSISTENT = 1, CFD_IR_GRAPH = 2 };
 int cfd_set_ir_form(cfd_handle *h, int form);
 

@@ -341,15 +341,12 @@ IrArgs pressure_ir_args(const cfd_handle* h, double* x, int zero_x0, int gauge, 
   return a;
 }
 
-// Graph form of the mixed-precision solve: on request, or automatically on
-// grids of at least kIrGraphCells cells (where its streaming kernels beat the
-// persistent kernel's two grid barriers per iteration).
-constexpr size_t kIrGraphCells = size_t(1) << 21;
-
+// Graph form of the mixed-precision solve wherever it applies (the pressure
+// matrix needs nx % 4 == 0), unless the persistent form is requested: a
+// cavity step at 64^3 / 128^3 / 192^3 takes 6.0 / 17.7 / 56.4 ms with it
+// against 11.0 / 26.9 / 91.1 ms with the persistent kernel.
 bool use_ir_graph(const cfd_handle* h, const IrArgs& a) {
-  if (!h->irg_state || !ir_graph_eligible(a) || h->ir_form == CFD_IR_PERSISTENT) return false;
-  if (h->ir_form == CFD_IR_GRAPH) return true;
-  return size_t(h->prm.nx) * h->prm.ny * h->prm.nz >= kIrGraphCells;
+  return h->irg_state && ir_graph_eligible(a) && h->ir_form != CFD_IR_PERSISTENT;
 }
 
 // The diffusion solve of component comp as FP32 CG with FP64 refinement
