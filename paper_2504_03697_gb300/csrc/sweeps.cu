@@ -57,6 +57,8 @@ __device__ __forceinline__ FaceDims face_dims(int comp, int nx, int ny, int nz) 
 __device__ __forceinline__ double sample(const double* __restrict__ f, int comp, int i, int j, int k, int nx,
                                          int ny, int nz, double lid_u) {
   const FaceDims d = face_dims(comp, nx, ny, nz);
+  // inside the array (the common case) the sample is the stored value
+  if (i >= 0 && i < d.mx && j >= 0 && j < d.my && k >= 0 && k < d.mz) return f[idx3(i, j, k, d.mx, d.my)];
   double add = 0.0, sgn = 1.0;
   if (comp != 2) {
     if (k < 0) { k = 0; sgn = -sgn; }
