@@ -123,8 +123,10 @@ typedef struct {
   int32_t max_iters;        /* CG iteration cap per solve; 0 -> 20 * max(n)       */
   int32_t warm_start;       /* 1: start the pressure solve from the previous p    */
   double ir_delta;          /* IR: refine in FP64 each time the FP32 residual has
-                               fallen by this factor, in (0, 1); 0 -> 0.1 for the
-                               pressure solve, 1e-4 for the diffusion solves
+                               fallen by this factor, in (0, 1); 0 -> 0.01 for
+                               the pressure solve (the FP32 recurrence keeps the
+                               iteration count of FP64 CG over two decades, not
+                               over three), 1e-4 for the diffusion solves
                                (well-conditioned systems)                        */
   int32_t advect_order;     /* backtrace: 0 or 1 explicit Euler x - dt v(x); 2 the
                                explicit midpoint rule x - dt v(x - dt/2 v(x))     */

@@ -295,49 +295,102 @@ __global__ void __launch_bounds__(kGThreads) g_pro_sum(const GArgs a) {
 // The pass of g_resid64 over the blocks B: r = b' - A xv, with b' = b -
 // shift (MODE 0; stored when remove_mean) and xv = 0 (zero), x + x32 (add32)
 // or x; s[0] += b'.b' (MODE 0), s[1] += r.r, s[2] += sum(r).
-template <int MODE>
-__device__ __forceinline__ void resid64_pass(const GArgs& a, double shift, bool add32, bool zero, double (&s)[3],
+//
+// A warp covers 64 consecutive x cells of one row (two per lane, 32 apart),
+// z by marching kZ64 planes; the x neighbours come from the neighbouring
+// lanes by shuffles (cell 31 / 32 of the row segment across the two halves,
+// the segment's ends by loads), so each plane step issues two independent
+// cells per lane.  Lanes past the row's end shadow its last cell and store
+// nothing.  The operator kind is a template constant.
+template <int MODE, int KIND>
+__device__ __forceinline__ void resid64_rows(const GArgs& a, double shift, bool add32, bool zero, double (&s)[3],
                                              Blk B) {
   const int mx = a.mx, my = a.my, mz = a.mz;
   const size_t sy = size_t(mx), sz = size_t(mx) * my;
   const size_t py = size_t(a.pitch), pz = size_t(a.pitch) * my;  // the FP32 layout
   auto X = [&](size_t e, size_t e32) { return zero ? 0.0 : (add32 ? a.x[e] + double(a.d32[e32]) : a.x[e]); };
+  const int lane = threadIdx.x;
   double sb = 0.0, sr = 0.0, ss = 0.0;
-  const int items = a.w64x * a.w64y * a.w64z;
+  const int wxn = (mx + 63) / 64;
+  const int items = wxn * a.w64y * a.w64z;
   for (int w = B.bid; w < items; w += B.nb) {
-    const int wx = w % a.w64x, wy = (w / a.w64x) % a.w64y, wz = w / (a.w64x * a.w64y);
-    const int i = wx * 32 + threadIdx.x, j = wy * 8 + threadIdx.y, k0 = wz * kZ64;
-    if (i >= mx || j >= my) continue;
+    const int wx = w % wxn, wy = (w / wxn) % a.w64y, wz = w / (wxn * a.w64y);
+    const int j = wy * 8 + threadIdx.y, k0 = wz * kZ64;
+    if (j >= my) continue;  // the whole warp (one row per warp)
     const int k1 = min(k0 + kZ64, mz);
-    size_t c = (size_t(k0) * my + j) * mx + i;
-    size_t c32 = (size_t(k0) * my + j) * py + i;
-    double xc = X(c, c32);
-    double xm = k0 > 0 ? X(c - sz, c32 - pz) : xc;
-    for (int k = k0; k < k1; ++k, c += sz, c32 += pz) {
-      const double xp = k < mz - 1 ? X(c + sz, c32 + pz) : xc;
-      const double xw = i > 0 ? X(c - 1, c32 - 1) : xc;
-      const double xe = i < mx - 1 ? X(c + 1, c32 + 1) : xc;
-      const double xs = j > 0 ? X(c - sy, c32 - py) : xc;
-      const double xn = j < my - 1 ? X(c + sy, c32 + py) : xc;
-      const double ax = stencil_row<double>(a.kind, a.c, i, j, k, mx, my, mz, xc, xw, xe, xs, xn, xm, xp);
-      double bv = a.b[c];
-      if (MODE == 0) {
-        bv -= shift;
-        if (a.remove_mean) a.b[c] = bv;
-        if (zero) a.x[c] = 0.0;
-        sb = fma(bv, bv, sb);
+    const int ia = wx * 64 + lane, ib = ia + 32;
+    const bool va = ia < mx, vb = ib < mx;
+    const int iac = va ? ia : mx - 1, ibc = vb ? ib : mx - 1;  // lanes past the row shadow its last cell
+    size_t ca = (size_t(k0) * my + j) * mx + iac, cb = (size_t(k0) * my + j) * mx + ibc;
+    size_t pa = (size_t(k0) * my + j) * py + iac, pb = (size_t(k0) * my + j) * py + ibc;
+    double xca = X(ca, pa), xcb = X(cb, pb);
+    double xma = k0 > 0 ? X(ca - sz, pa - pz) : xca, xmb = k0 > 0 ? X(cb - sz, pb - pz) : xcb;
+    for (int k = k0; k < k1; ++k, ca += sz, cb += sz, pa += pz, pb += pz) {
+      const bool up = k < mz - 1;
+      const double xpa = up ? X(ca + sz, pa + pz) : xca, xpb = up ? X(cb + sz, pb + pz) : xcb;
+      const double xsa = j > 0 ? X(ca - sy, pa - py) : xca, xsb = j > 0 ? X(cb - sy, pb - py) : xcb;
+      const double xna = j < my - 1 ? X(ca + sy, pa + py) : xca, xnb = j < my - 1 ? X(cb + sy, pb + py) : xcb;
+      double wa = __shfl_up_sync(0xffffffffu, xca, 1), ea = __shfl_down_sync(0xffffffffu, xca, 1);
+      double wb = __shfl_up_sync(0xffffffffu, xcb, 1), eb = __shfl_down_sync(0xffffffffu, xcb, 1);
+      const double a31 = __shfl_sync(0xffffffffu, xca, 31), b0 = __shfl_sync(0xffffffffu, xcb, 0);
+      if (lane == 0) {
+        wa = ia > 0 ? X(ca - 1, pa - 1) : xca;
+        wb = a31;
       }
-      const double rv = bv - ax;
-      a.r[c] = rv;
-      sr = fma(rv, rv, sr);
-      ss += rv;
-      xm = xc;
-      xc = xp;
+      if (lane == 31) {
+        ea = b0;
+        eb = ib + 1 < mx ? X(cb + 1, pb + 1) : xcb;
+      }
+      // a shadow lane holds the row's last cell, so a cell at the row's end
+      // sees itself as its east neighbour, as the boundary rule wants
+      if (va) {
+        const double ax = stencil_row<double>(KIND, a.c, ia, j, k, mx, my, mz, xca, wa, ea, xsa, xna, xma, xpa);
+        double bv = a.b[ca];
+        if (MODE == 0) {
+          bv -= shift;
+          if (a.remove_mean) a.b[ca] = bv;
+          if (zero) a.x[ca] = 0.0;
+          sb = fma(bv, bv, sb);
+        }
+        const double rv = bv - ax;
+        a.r[ca] = rv;
+        sr = fma(rv, rv, sr);
+        ss += rv;
+      }
+      if (vb) {
+        const double ax = stencil_row<double>(KIND, a.c, ib, j, k, mx, my, mz, xcb, wb, eb, xsb, xnb, xmb, xpb);
+        double bv = a.b[cb];
+        if (MODE == 0) {
+          bv -= shift;
+          if (a.remove_mean) a.b[cb] = bv;
+          if (zero) a.x[cb] = 0.0;
+          sb = fma(bv, bv, sb);
+        }
+        const double rv = bv - ax;
+        a.r[cb] = rv;
+        sr = fma(rv, rv, sr);
+        ss += rv;
+      }
+      xma = xca;
+      xca = xpa;
+      xmb = xcb;
+      xcb = xpb;
     }
   }
   s[0] = sb;
   s[1] = sr;
   s[2] = ss;
+}
+
+template <int MODE>
+__device__ __forceinline__ void resid64_pass(const GArgs& a, double shift, bool add32, bool zero, double (&s)[3],
+                                             Blk B) {
+  switch (a.kind) {
+    case kOpVelU: resid64_rows<MODE, kOpVelU>(a, shift, add32, zero, s, B); break;
+    case kOpVelV: resid64_rows<MODE, kOpVelV>(a, shift, add32, zero, s, B); break;
+    case kOpVelW: resid64_rows<MODE, kOpVelW>(a, shift, add32, zero, s, B); break;
+    default: resid64_rows<MODE, kOpPressure>(a, shift, add32, zero, s, B); break;
+  }
 }
 
 template <int MODE>

@@ -212,8 +212,8 @@ def test_learned_guess_matches_oracle_and_solve_from_it(cfd, shape, w):
     # loop (4 FP32 iterations per pass of its body)
     assert (ran - base) % 2 == 0 and 0 <= ran - base <= 6 * (st["outer_iters"] + 1), (ran, base, st)
     A = poisson_csr(nx, ny, nz)
-    xo, so = ir_cg(A, b.ravel(), rtol=RTOL, delta=0.1, x0=x0o, max_iters=20 * max(shape))
-    _, cold = ir_cg(A, b.ravel(), rtol=RTOL, delta=0.1, max_iters=20 * max(shape))
+    xo, so = ir_cg(A, b.ravel(), rtol=RTOL, delta=0.01, x0=x0o, max_iters=20 * max(shape))
+    _, cold = ir_cg(A, b.ravel(), rtol=RTOL, delta=0.01, max_iters=20 * max(shape))
     assert so.converged
     assert abs(st["iters"] - so.iters) <= max(4, so.iters // 20), (st["iters"], so.iters)
     dmax, bound = check_solution(shape, b, xg.cpu().numpy().ravel(), st, xo)
