@@ -377,14 +377,17 @@ __global__ void up2_adj_kernel(const __nv_bfloat16* gout, int fx, int fy, int fz
 // out 16 channels as 2 octet planes.
 __global__ void first_layer_kernel(const __nv_bfloat16* xin, int nx, int ny, int nz, const __nv_bfloat16* w,
                                    const float* bias, __nv_bfloat16* out) {
-  __shared__ float ws[27][16];
+  // weights as 4 float4 per tap: one 16-byte shared load per 4 FMAs
+  __shared__ float4 ws[27][4];
   __shared__ float bs[16];
-  for (int i = threadIdx.x; i < 27 * 16; i += blockDim.x) ws[i / 16][i % 16] = __bfloat162float(w[(i % 16) * 32 + i / 16]);
+  for (int i = threadIdx.x; i < 27 * 16; i += blockDim.x)
+    reinterpret_cast<float*>(&ws[i / 16][0])[i % 16] = __bfloat162float(w[(i % 16) * 32 + i / 16]);
   if (threadIdx.x < 16) bs[threadIdx.x] = bias[threadIdx.x];
   __syncthreads();
   const size_t V = size_t(nx) * ny * nz;
   for (size_t v = gtid(); v < V; v += gstride()) {
-    const int x = int(v % nx), y = int((v / nx) % ny), z = int(v / (size_t(nx) * ny));
+    const unsigned vu = unsigned(v), row = vu / unsigned(nx);  // grids below 2^32 voxels
+    const int x = int(vu - row * unsigned(nx)), z = int(row / unsigned(ny)), y = int(row - unsigned(z) * unsigned(ny));
     float acc[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) acc[c] = 0.f;
@@ -396,7 +399,13 @@ __global__ void first_layer_kernel(const __nv_bfloat16* xin, int nx, int ny, int
           if (xx < 0 || xx >= nx || yy < 0 || yy >= ny || zz < 0 || zz >= nz) continue;
           const float xv = __bfloat162float(xin[(size_t(zz) * ny + yy) * nx + xx]);
 #pragma unroll
-          for (int c = 0; c < 16; ++c) acc[c] = fmaf(ws[tap][c], xv, acc[c]);
+          for (int q = 0; q < 4; ++q) {
+            const float4 wq = ws[tap][q];
+            acc[4 * q] = fmaf(wq.x, xv, acc[4 * q]);
+            acc[4 * q + 1] = fmaf(wq.y, xv, acc[4 * q + 1]);
+            acc[4 * q + 2] = fmaf(wq.z, xv, acc[4 * q + 2]);
+            acc[4 * q + 3] = fmaf(wq.w, xv, acc[4 * q + 3]);
+          }
         }
     float o[8];
 #pragma unroll
