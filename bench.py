@@ -70,12 +70,15 @@ CG_FLOPS_PER_CELL_ITER = 17
 CG_BYTES_PER_CELL_ITER = 80
 CG_FLOPS_PER_CELL_SOLVE = 14
 CG_BYTES_PER_CELL_SOLVE = 72
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch of
-# cg1_fp64_kernel<8> on the 64^3 cavity in its automatic shape (128 blocks,
-# tile depth 8), from one ncu capture of the pressure solve of the first timed
-# step: the 26 MB working set is L2-resident, so DRAM sees almost nothing
-CG1_CAVITY64_DRAM_BYTES = 2342400 + 84992
-CG1_CAVITY64_SHAPE = {"blocks": 128, "tile_depth": 8, "register_path": True}
+# dram__bytes_read.sum + dram__bytes_write.sum and the L2 throughput of one
+# launch of the 64^3 cavity's pressure CG in its automatic shape (the
+# tile-resident single-reduction kernel cgt_fp64_kernel: 128 blocks of 256
+# threads, one 32 x 8 x 8 tile each), from one ncu capture of the pressure
+# solve of the first timed step (the 26 MB working set is L2-resident);
+# None until that kernel has been captured
+CGT_CAVITY64_DRAM_BYTES = None
+CGT_CAVITY64_LTS_PCT = None
+CGT_CAVITY64_SHAPE = {"blocks": 128, "tile_depth": 8, "register_path": True, "tile_resident": True}
 IR_BYTES_PER_CELL_ITER = 40
 IR_GRAPH_BYTES_PER_CELL_ITER = 32
 # DRAM bytes per cell and FP32 iteration of the graph-form iteration (g_dir +
@@ -454,11 +457,13 @@ def cavity_sample(cfd, n, wl, solver, steps, warmup, device, params=None, warm_s
     cav.enable_timing(False)
     ph = cav.phase_times()
     rc, st = cav.recent_stats(steps)
+    shape0 = cav.solver_shape(0)
     out = {"solver": solver, "warm_start": warm_start, "steps_timed": steps, "warmup": warmup,
            "ms_per_step": sum(ms) / steps, "step_ms": [round(m, 3) for m in ms],
            "cell_steps_per_s": n ** 3 * steps / (sum(ms) / 1e3),
            "pressure_ms_per_step": ph["pcg"][0] / steps, "diffuse_ms_per_step": ph["diffuse"][0] / steps,
            "pressure_iters": [s["iters"] for s in st], "refinements": [s["outer_iters"] for s in st],
+           "pressure_shape": shape0,
            "all_converged": rc == cfd.CFD_OK and all(s["rel_resid"] <= 1e-8 * 1.0000001 for s in st)}
     del cav, net
     torch.cuda.empty_cache()
@@ -575,11 +580,13 @@ def main_ours(args):
         flops = cells * (CG_FLOPS_PER_CELL_ITER * mean_iters + CG_FLOPS_PER_CELL_SOLVE)
         bytes_ = cells * (CG_BYTES_PER_CELL_ITER * mean_iters + CG_BYTES_PER_CELL_SOLVE)
         achieved = flops / pcg_avg_s / 1e12
-        roofline = {"bound": "alu", "kernel": "cg1_fp64_kernel / cg_fp64_kernel (pressure CG, persistent)",
+        shape0 = cav.solver_shape(0)
+        roofline = {"bound": "alu", "kernel": "cgt_fp64_kernel (pressure CG, tile-resident single-reduction form)"
+                    if shape0["tile_resident"] else "cg1_fp64_kernel / cg_fp64_kernel (pressure CG, persistent)",
                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP64_PEAK_TFLOPS,
-                    "traffic": CG1_CAVITY64_DRAM_BYTES if (args.workload == "cavity64"
-                                                           and cav.solver_shape(0) == CG1_CAVITY64_SHAPE) else None,
+                    "traffic": CGT_CAVITY64_DRAM_BYTES if (args.workload == "cavity64"
+                                                           and shape0 == CGT_CAVITY64_SHAPE) else None,
                     "peak_source": FP64_PEAK_SOURCE, "launch_ms": pcg_avg_s * 1e3,
                     "hbm_achieved_gbs": bytes_ / pcg_avg_s / 1e9, "hbm_frac_of_measured": bytes_ / pcg_avg_s / 1e9 / hbm_peak}
     else:
@@ -650,12 +657,13 @@ def main_ours(args):
         flops = (CG_FLOPS_PER_CELL_ITER * its + CG_FLOPS_PER_CELL_SOLVE) * cells64
         l2_bytes = (CG_BYTES_PER_CELL_ITER * its + CG_BYTES_PER_CELL_SOLVE) * cells64
         c2["roofline"] = {
-            "bound": "alu", "kernel": "cg1_fp64_kernel<8> (pressure CG, single-reduction form)",
+            "bound": "alu", "kernel": "cgt_fp64_kernel (pressure CG, tile-resident single-reduction form)"
+            if c2.get("pressure_shape", {}).get("tile_resident") else "cg1_fp64_kernel (pressure CG, single-reduction form)",
             "achieved": flops / t_s / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": flops / t_s / 1e12 / FP64_PEAK_TFLOPS, "peak_source": FP64_PEAK_SOURCE,
             "l2": {"algorithmic_bytes_per_solve": l2_bytes, "achieved_GBs": l2_bytes / t_s / 1e9,
-                   "ncu_lts_throughput_pct": 5.1, "dram_bytes_per_solve": CG1_CAVITY64_DRAM_BYTES,
-                   "source": "profiles/cg1_fp64_cavity64_full.md (lts__throughput.avg.pct_of_peak_sustained_"
+                   "ncu_lts_throughput_pct": CGT_CAVITY64_LTS_PCT, "dram_bytes_per_solve": CGT_CAVITY64_DRAM_BYTES,
+                   "source": "profiles/cgt_fp64_cavity64_full.md (lts__throughput.avg.pct_of_peak_sustained_"
                              "elapsed and dram bytes of one launch)"}}
         extra["cavity64_fp64_cg"] = c2
         # standalone 256^3 Poisson, FP64 CG vs FP32/FP64-IR (2 of 32 RHS)

@@ -297,8 +297,13 @@ typedef struct {
 int cfd_autotune_solver(cfd_handle *h, int32_t iters, cfd_tune_report *rep);
 
 /* The shape the next solve of `kind` (0 pressure, 1..3 diffusion of u, v,
- * w) would use: grid size, tile depth, and whether the register path is
- * taken.  Each output pointer may be NULL. */
+ * w) would use: grid size, tile depth, and the path: *register_path is 0
+ * for the memory path, 1 for the register path, 2 for the tile-resident
+ * single-reduction FP64 CG (one block of 256 threads per 32 x 8 x 8 tile,
+ * every CG vector of the tile in registers; taken by unpreconditioned
+ * single-reduction CG solves with the automatic shape when the tiles number
+ * more than half of the SMs and at most one per SM, e.g. 64^3).  Each output
+ * pointer may be NULL. */
 int cfd_get_solver_shape(cfd_handle *h, int kind, int *blocks, int *tile_depth, int *register_path);
 
 /* Phase timers, mirroring the call tree of the paper's Table 1

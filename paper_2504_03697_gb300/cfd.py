@@ -366,7 +366,8 @@ class Cavity:
     def solver_shape(self, kind=0):
         b, t, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         self._check(self.lib.cfd_get_solver_shape(self.h, int(kind), ctypes.byref(b), ctypes.byref(t), ctypes.byref(r)))
-        return {"blocks": b.value, "tile_depth": t.value, "register_path": bool(r.value)}
+        return {"blocks": b.value, "tile_depth": t.value, "register_path": bool(r.value),
+                "tile_resident": r.value == 2}
 
     def enable_timing(self, on=True):
         return self._check(self.lib.cfd_enable_timing(self.h, 1 if on else 0))

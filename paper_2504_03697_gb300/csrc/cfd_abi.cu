@@ -415,6 +415,7 @@ int run_diffusion_concurrent(cfd_handle* h, DevStepStats* st) {
   for (int k = 0; k < 2 && !rc; ++k) rc = cuda_check(h, cudaStreamWaitEvent(h->aux[k], h->ev_fork, 0), "fork wait");
   LaunchGeom lg = h->lg;
   lg.blocks = std::max(1, h->lg.blocks / 3);
+  lg.shared = 1;
   lg.bps_req = 0;  // a tuned shape is for the whole device
   lg.tz_req = 0;
   for (int c = 0; c < 3 && !rc; ++c) {
@@ -1240,6 +1241,16 @@ int cfd_get_solver_shape(cfd_handle* h, int kind, int* blocks, int* tile_depth, 
   if (blocks) *blocks = s.blocks;
   if (tile_depth) *tile_depth = s.tz;
   if (register_path) *register_path = s.rtz > 0;
+  // unpreconditioned single-reduction FP64 CG on the whole device: the
+  // tile-resident kernel when the grid qualifies
+  const bool fp64_cg = kind == 0 ? h->prm.solver == CFD_SOLVER_CG : !ir_diffusion(h) && !diffusion_concurrent(h);
+  if (fp64_cg && h->lg.cg_variant == CFD_CG_SINGLE_REDUCTION) {
+    if (const int tiles = cgt_blocks_for(g, h->lg)) {
+      if (blocks) *blocks = tiles;
+      if (tile_depth) *tile_depth = kCgtTileDepth;
+      if (register_path) *register_path = 2;
+    }
+  }
   return CFD_OK;
 }
 

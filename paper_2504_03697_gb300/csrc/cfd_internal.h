@@ -35,6 +35,7 @@ struct LaunchGeom {
   int tz_req;       // requested tile depth (0: automatic)
   int no_tma;       // 1: never take the TMA stencil path
   int cg_variant;   // CgArgs::variant for the handle's FP64 solves
+  int shared;       // 1: other cooperative grids run at the same time (blocks is this grid's share)
 };
 
 // Launch shape picked for one solve.
@@ -146,6 +147,11 @@ struct PhysArgs {
 // Kernel launchers (return the CUDA error of the launch).  Each adds the
 // number of kernels it launched to *launches.
 cudaError_t launch_cg(const CgArgs& a, const LaunchGeom& lg, cudaStream_t s, int64_t* launches);
+// Grid of the tile-resident single-reduction FP64 CG for this grid and
+// launch geometry (one block per tile), 0 when the automatic shape does not
+// take it; it runs for unpreconditioned single-reduction CG solves.
+int cgt_blocks_for(GridDims g, const LaunchGeom& lg);
+constexpr int kCgtTileDepth = 8;  // its tile depth along z
 cudaError_t launch_ir(const IrArgs& a, const LaunchGeom& lg, cudaStream_t s, int64_t* launches);
 cudaError_t launch_apply_poisson(GridDims g, const double* x, double* y, int tz, cudaStream_t s,
                                  int64_t* launches);

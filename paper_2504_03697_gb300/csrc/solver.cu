@@ -109,8 +109,43 @@ SolveShape pick_solve_shape(GridDims g, int max_blocks, int bps_req, int tz_req)
   return consider(4, 1, false);
 }
 
+// The tile-resident single-reduction kernel serves the automatic shape when
+// its tiles fill more than half of the SMs and fit one per SM: below that
+// the smaller tiles of the register path spread the FP64 work over more SMs.
+// Its blocks take a whole SM's registers each, so it runs only on a device
+// that no other cooperative grid shares.
+int cgt_blocks_for(GridDims g, const LaunchGeom& lg) {
+  if (lg.bps_req > 0 || lg.tz_req > 0 || lg.shared) return 0;
+  static int per_sm = -1;
+  if (per_sm < 0) {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cgt_kernel(), cgt_threads(), 0);
+    per_sm = b;
+  }
+  const int sms = num_sms();
+  const int tiles = cgt_tiles(g);
+  if (g.count() >= (size_t(1) << 20) - 1) return 0;  // halo indices are packed in 20 bits
+  if (per_sm < 1 || tiles > sms || tiles > lg.blocks || 2 * tiles <= sms) return 0;
+  return tiles;
+}
+
 cudaError_t launch_cg(const CgArgs& a_in, const LaunchGeom& lg, cudaStream_t s, int64_t* launches) {
   CgArgs a = a_in;
+  if (const int tiles = cg1_allowed(a) ? cgt_blocks_for(a.g, lg) : 0) {
+    a.tz = kCgtTileDepth;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(tiles);
+    cfg.blockDim = dim3(cgt_threads());
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t err = cudaLaunchKernelEx(&cfg, cgt_kernel(), a);
+    if (launches) *launches += 1;
+    return err;
+  }
   SolveShape sh = pick_solve_shape(a.g, lg.blocks, lg.bps_req, lg.tz_req);
   a.tz = sh.tz;
   // the single-reduction kernel must keep the whole grid co-resident too: the

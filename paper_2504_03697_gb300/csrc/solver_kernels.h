@@ -20,6 +20,11 @@ CgKernel cg_kernel_jacobi(int rtz);
 CgKernel cg_kernel_multi(int precond);
 // single-reduction FP64 CG, one problem
 Cg1Kernel cg1_kernel(int rtz);
+// the same, tile-resident: one block of cgt_threads() per tile of depth
+// kCgtTileDepth, all CG vectors of the tile in registers (solver_cgt.cu)
+Cg1Kernel cgt_kernel();
+int cgt_threads();
+int cgt_tiles(GridDims g);
 // FP32 CG with FP64 refinement: one problem / many problems
 IrKernel ir_kernel_single();
 

@@ -108,6 +108,67 @@ def test_cg_variants_parity(cfd, variant, shape, bps, tz):
     assert abs(s_own.iters - st["iters"]) <= 2
 
 
+def _sms():
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
+def _tiles8(shape):
+    nx, ny, nz = shape
+    return -(-nx // 32) * -(-ny // 8) * -(-nz // 8)
+
+
+@pytest.mark.parametrize("shape,warm", [((64, 64, 64), False), ((61, 62, 59), False), ((63, 50, 64), False),
+                                        ((61, 62, 59), True)])
+def test_tile_resident_cg_parity(cfd, shape, warm):
+    # the tile-resident single-reduction kernel (the automatic shape when the
+    # 32 x 8 x 8 tiles number more than half of the SMs and at most one per
+    # SM): ragged tiles in x, y and z, cold and warm starts, against the
+    # oracle's textbook CG with the GPU's iteration count replayed
+    nx, ny, nz = shape
+    if not (_sms() / 2 < _tiles8(shape) <= _sms()):
+        pytest.skip("grid does not take the tile-resident kernel on this device")
+    cav, _ = make(cfd, shape, warm_start=warm)
+    assert cav.solver_shape(0)["tile_resident"]
+    b = gaussian_rhs(nx, ny, nz, seed=5)
+    x0 = uniform_field((nz, ny, nx), seed=6) if warm else np.zeros((nz, ny, nx))
+    bg = torch.tensor(b, device="cuda")
+    xg = torch.tensor(x0, device="cuda")
+    rc, st = cav.solve_pressure(bg, xg)
+    assert rc == cfd.CFD_OK and st["rel_resid"] <= 1e-8, st
+    A = poisson_csr(nx, ny, nz)
+    bo = b.ravel() - b.mean()
+    x_rep, _ = pcg(A, bo, x0=x0.ravel(), rtol=1e-8, max_iters=10 ** 6, fixed_iters=st["iters"])
+    assert rel_err(xg.cpu().numpy().ravel(), x_rep) < FP64_TOL
+    x_own, s_own = pcg(A, bo, x0=x0.ravel(), rtol=1e-8, max_iters=10 ** 6)
+    assert abs(s_own.iters - st["iters"]) <= 2
+    np.testing.assert_allclose(np.linalg.norm(bo), st["b_norm"], rtol=1e-12)
+
+
+def test_tile_resident_cg_zero_rhs_and_cap(cfd):
+    shape = (64, 64, 64)
+    if not (_sms() / 2 < _tiles8(shape) <= _sms()):
+        pytest.skip("grid does not take the tile-resident kernel on this device")
+    cav, _ = make(cfd, shape)
+    assert cav.solver_shape(0)["tile_resident"]
+    bg = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    xg = torch.full_like(bg, 3.0)
+    rc, st = cav.solve_pressure(bg, xg)
+    assert rc == cfd.CFD_OK and st["iters"] == 0 and st["rel_resid"] == 0.0
+    assert torch.all(xg == 0)
+    cav5, _ = make(cfd, shape, max_iters=5)
+    b = gaussian_rhs(64, 64, 64, seed=2)
+    bg = torch.tensor(b, device="cuda")
+    xg = torch.zeros_like(bg)
+    rc, st = cav5.solve_pressure(bg, xg)
+    assert rc == cfd.CFD_ERR_NOT_CONVERGED and st["iters"] == 5 and st["rel_resid"] > 1e-8
+    A = poisson_csr(64, 64, 64)
+    bo = b.ravel() - b.mean()
+    x_rep, _ = pcg(A, bo, rtol=1e-8, max_iters=10 ** 6, fixed_iters=5)
+    assert rel_err(xg.cpu().numpy().ravel(), x_rep) < FP64_TOL
+    r = bo - A @ xg.cpu().numpy().ravel()
+    np.testing.assert_allclose(st["rel_resid"], np.linalg.norm(r) / np.linalg.norm(bo), rtol=1e-9)
+
+
 def test_zero_rhs_solve(cfd):
     cav, _ = make(cfd, (8, 8, 8))
     bg = torch.zeros((8, 8, 8), dtype=torch.float64, device="cuda")
@@ -223,10 +284,10 @@ def test_project_parity(cfd, shape):
 # ----------------------------------------------------------------------------
 # whole steps
 # ----------------------------------------------------------------------------
-def _run_pair(cfd, shape, steps, seed, concurrent=False, **kw):
+def _run_pair(cfd, shape, steps, seed, concurrent=None, **kw):
     cav, ocav = make(cfd, shape, **kw)
-    if concurrent:
-        cav.set_concurrent_diffusion(True)
+    if concurrent is not None:  # None: the handle's default
+        cav.set_concurrent_diffusion(concurrent)
     nx, ny, nz = shape
     init = cavity_perturbation(nx, ny, nz, seed=seed, amp=1e-3)
     _load(cav, init)
@@ -255,6 +316,23 @@ def test_cavity_64cube_steps(cfd):
     cav, ocav, stats, st, errs = _run_pair(cfd, (64, 64, 64), 3, 2, dt=0.01, nu=0.001, lid_u=1.0)
     for name, e in errs.items():
         assert e < FP64_TOL, (name, e)
+
+
+def test_cavity_63cube_steps_tile_resident(cfd):
+    """63^3 cavity, FP64: the pressure grid and all three velocity grids take
+    the tile-resident CG (128 tiles each); 3 steps against the oracle."""
+    shape = (63, 63, 63)
+    if not (_sms() / 2 < _tiles8(shape) <= _sms() and _tiles8((64, 63, 63)) <= _sms()):
+        pytest.skip("grids do not take the tile-resident kernel on this device")
+    # one diffusion solve at a time: concurrent solves share the device and
+    # take the register path
+    cav, ocav, stats, st, errs = _run_pair(cfd, shape, 3, 4, concurrent=False, dt=0.01, nu=0.002, lid_u=1.0)
+    shapes = [cav.solver_shape(k) for k in range(4)]
+    assert all(sh["tile_resident"] for sh in shapes), shapes
+    for name, e in errs.items():
+        assert e < FP64_TOL, (name, e)
+    for s in stats:
+        assert s["rel_resid"] <= 1e-8 and s["status"] == 0 and s["diff_status"] == 0
 
 
 @pytest.mark.parametrize("shape,kw", [((17, 9, 13), dict(dt=0.02, nu=0.01, lid_u=1.0)),
