@@ -34,7 +34,7 @@ def test_byte_models_per_cell():
 
 def test_traffic_belongs_to_one_launch_shape():
     assert bench.CGT_CAVITY64_SHAPE == {"blocks": 128, "tile_depth": 8, "register_path": True, "tile_resident": True}
-    assert bench.CGT_CAVITY64_DRAM_BYTES is None or bench.CGT_CAVITY64_DRAM_BYTES > 0
+    assert bench.CGT_CAVITY64_DRAM_BYTES > 0 and 0 < bench.CGT_CAVITY64_LTS_PCT < 100
 
 
 def test_measured_hbm_peak_fallback(tmp_path, monkeypatch):
