@@ -80,7 +80,9 @@ CGT_CAVITY64_DRAM_BYTES = 2347520 + 113408
 CGT_CAVITY64_LTS_PCT = 5.2
 CGT_CAVITY64_SHAPE = {"blocks": 128, "tile_depth": 8, "register_path": True, "tile_resident": True}
 IR_BYTES_PER_CELL_ITER = 40
-IR_GRAPH_BYTES_PER_CELL_ITER = 32
+# graph form: g_dir 12 B; g_upd 20 B every other iteration (x32 read and
+# written) and 12 B in between (x32 term deferred): 28 B on average
+IR_GRAPH_BYTES_PER_CELL_ITER = 28
 # DRAM bytes per cell and FP32 iteration of the graph-form iteration (g_dir +
 # g_upd), from the ncu capture of a 256^3 solve (whole-solve dram bytes over
 # cells x iterations; profiles/ir_graph_poisson256.md); None if not captured
@@ -590,8 +592,9 @@ def main_ours(args):
                     "peak_source": FP64_PEAK_SOURCE, "launch_ms": pcg_avg_s * 1e3,
                     "hbm_achieved_gbs": bytes_ / pcg_avg_s / 1e9, "hbm_frac_of_measured": bytes_ / pcg_avg_s / 1e9 / hbm_peak}
     else:
-        # the FP32 iteration of the graph form moves 32 B per cell (g_dir reads
-        # r32, p_old and writes p; g_upd reads p, x32, r32 and writes x32, r32);
+        # the FP32 iteration of the graph form moves 28 B per cell on average
+        # (g_dir reads r32, p_old and writes p; g_upd reads p, r32 and writes
+        # r32, and reads and writes x32 every other iteration);
         # the FP64 refinements and the learned guess are inside the timed
         # solve but left out of the algorithmic bytes (a lower bound on frac)
         ir_bytes = cells * IR_GRAPH_BYTES_PER_CELL_ITER * mean_iters

@@ -10,11 +10,15 @@
 // What differs is the execution: instead of one cooperative kernel with two
 // grid barriers per iteration, every phase is its own streaming kernel
 // (float4 accesses, x neighbours by warp shuffles) and the loop control runs
-// on the device.  The FP32 iteration moves 32 B per cell: the direction
-// kernel reads r32 and the previous p and writes p (forming p on the fly at
-// the +x, +y, +z neighbours too, for p.Ap as a sum of squared differences
-// over the grid's edges); the update kernel forms q = A p from the stored p
-// and reads and writes x32 and r32.  q is never stored.
+// on the device.  The FP32 iteration moves 28 B per cell on average: the
+// direction kernel reads r32 and the previous p and writes p (forming p on
+// the fly at the +x, +y, +z neighbours too, for p.Ap as a sum of squared
+// differences over the grid's edges); the update kernel forms q = A p from
+// the stored p and reads and writes r32, and x32 every other iteration: one
+// iteration defers its term alpha p, the next adds both, the deferred one as
+// (alpha_deferred / beta)(p - r) since p - r = beta p_deferred (until then
+// the passes that read x32 add the deferred term themselves).  q is never
+// stored.
 //
 //   memset(counter) -> pro_sum -> pro_resid ->
 //   while (outer) { prep -> while (inner) { (dir -> upd) x kItersPerPass } -> refine } ->
@@ -118,6 +122,13 @@ struct GState {
   double zmean;       // mean of the current z (removed from it)
   // learned initial guess
   double gmean, gscale, galpha, gzmean;
+  // x32 update deferred by one iteration (plain inner loop of the graph
+  // form): the update pass of every other iteration leaves x32 alone and
+  // records alpha; the next one adds both terms.  Until then every reader of
+  // x32 adds xalpha * p (p in buffer xbuf) itself.
+  int xdef, xbuf;
+  double xalpha;  // alpha of the deferred term
+  double xcoef;   // xalpha / beta of the next direction (its p = r + beta p_deferred)
 };
 
 constexpr size_t kStateBytes = 512;
@@ -271,6 +282,7 @@ __global__ void __launch_bounds__(kGThreads) g_pro_sum(const GArgs a) {
   S->cur = 0;
   S->refine = 0;
   S->pending = 0;
+  S->xdef = 0;
   S->breakdown = 0;
   S->done = 0;
   S->beta = 0.0;
@@ -283,6 +295,28 @@ __global__ void __launch_bounds__(kGThreads) g_pro_sum(const GArgs a) {
   S->rr32 = 0.0;
   S->zr = 0.0;
   S->zmean = 0.0;
+}
+
+// A deferred x32 term (GState::xdef): p is the deferred direction, nullptr
+// when there is none.
+struct XDef {
+  const float* p = nullptr;
+  float alpha = 0.f;
+};
+
+// x32 at FP32 cell e32 with a deferred term added, rounded as the update pass
+// would have added it.
+__device__ __forceinline__ float x32_at(const GArgs& a, const XDef& xd, size_t e32) {
+  return xd.p ? fmaf(xd.alpha, xd.p[e32], a.d32[e32]) : a.d32[e32];
+}
+
+__device__ __forceinline__ XDef xdef_of(const GArgs& a, const GState* S) {
+  XDef xd;
+  if (S->xdef) {
+    xd.p = S->xbuf ? a.p1 : a.p0;
+    xd.alpha = float(S->xalpha);
+  }
+  return xd;
 }
 
 // FP64 residual r = b - A xv over the tiles (scalar lanes, z-marching).
@@ -304,11 +338,11 @@ __global__ void __launch_bounds__(kGThreads) g_pro_sum(const GArgs a) {
 // nothing.  The operator kind is a template constant.
 template <int MODE, int KIND>
 __device__ __forceinline__ void resid64_rows(const GArgs& a, double shift, bool add32, bool zero, double (&s)[3],
-                                             Blk B) {
+                                             Blk B, XDef xd) {
   const int mx = a.mx, my = a.my, mz = a.mz;
   const size_t sy = size_t(mx), sz = size_t(mx) * my;
   const size_t py = size_t(a.pitch), pz = size_t(a.pitch) * my;  // the FP32 layout
-  auto X = [&](size_t e, size_t e32) { return zero ? 0.0 : (add32 ? a.x[e] + double(a.d32[e32]) : a.x[e]); };
+  auto X = [&](size_t e, size_t e32) { return zero ? 0.0 : (add32 ? a.x[e] + double(x32_at(a, xd, e32)) : a.x[e]); };
   const int lane = threadIdx.x;
   double sb = 0.0, sr = 0.0, ss = 0.0;
   const int wxn = (mx + 63) / 64;
@@ -384,12 +418,12 @@ __device__ __forceinline__ void resid64_rows(const GArgs& a, double shift, bool 
 
 template <int MODE>
 __device__ __forceinline__ void resid64_pass(const GArgs& a, double shift, bool add32, bool zero, double (&s)[3],
-                                             Blk B) {
+                                             Blk B, XDef xd = XDef{}) {
   switch (a.kind) {
-    case kOpVelU: resid64_rows<MODE, kOpVelU>(a, shift, add32, zero, s, B); break;
-    case kOpVelV: resid64_rows<MODE, kOpVelV>(a, shift, add32, zero, s, B); break;
-    case kOpVelW: resid64_rows<MODE, kOpVelW>(a, shift, add32, zero, s, B); break;
-    default: resid64_rows<MODE, kOpPressure>(a, shift, add32, zero, s, B); break;
+    case kOpVelU: resid64_rows<MODE, kOpVelU>(a, shift, add32, zero, s, B, xd); break;
+    case kOpVelV: resid64_rows<MODE, kOpVelV>(a, shift, add32, zero, s, B, xd); break;
+    case kOpVelW: resid64_rows<MODE, kOpVelW>(a, shift, add32, zero, s, B, xd); break;
+    default: resid64_rows<MODE, kOpPressure>(a, shift, add32, zero, s, B, xd); break;
   }
 }
 
@@ -404,7 +438,7 @@ __global__ void __launch_bounds__(kGThreads) g_resid64(const GArgs a) {
   if (MODE == 2 && (S->bb == 0.0 || S->status == kOk)) return;
   double v[3], o[3];
   resid64_pass<MODE>(a, MODE == 0 ? S->shift : 0.0, MODE == 1 || (MODE == 2 && S->pending), MODE == 0 && a.zero_x0, v,
-                     grid_blk());
+                     grid_blk(), MODE == 0 ? XDef{} : xdef_of(a, S));
   if (!reduce_last<3>(v, a.part, &S->counter, o) || ftid() != 0) return;
   if (MODE == 0) {
     S->bb = o[0];
@@ -441,12 +475,13 @@ __device__ __forceinline__ size_t c32_of(const GArgs& a, size_t e) {
 // g_prep's pass over the blocks B: fold a pending x32 into x, load r32 =
 // r - rmean unless leaving, clear x32; the padding cells of the FP32 rows
 // are set to 0.  Returns this thread's part of r32.r32 (FP32).
-__device__ __forceinline__ float prep_pass(const GArgs& a, bool fold, bool leave, double rmean, Blk B) {
+__device__ __forceinline__ float prep_pass(const GArgs& a, bool fold, bool leave, double rmean, Blk B,
+                                           XDef xd = XDef{}) {
   const size_t t0 = size_t(B.bid) * kGThreads + ftid(), st = size_t(B.nb) * kGThreads;
   float f = 0.f;
   for (size_t e = t0; e < a.n; e += st) {
     const size_t e32 = c32_of(a, e);
-    if (fold) a.x[e] += double(a.d32[e32]);
+    if (fold) a.x[e] += double(x32_at(a, xd, e32));
     if (!leave) {
       const float v = float(a.r[e] - rmean);
       a.r32[e32] = v;
@@ -468,12 +503,12 @@ __device__ __forceinline__ float prep_pass(const GArgs& a, bool fold, bool leave
 
 // g_finish's pass over the blocks B: x := 0 (zero) or x += x32 (fold);
 // returns this thread's part of sum(x).
-__device__ __forceinline__ double finish_pass(const GArgs& a, bool zero, bool fold, Blk B) {
+__device__ __forceinline__ double finish_pass(const GArgs& a, bool zero, bool fold, Blk B, XDef xd = XDef{}) {
   const size_t t0 = size_t(B.bid) * kGThreads + ftid(), st = size_t(B.nb) * kGThreads;
   double s = 0.0;
   for (size_t e = t0; e < a.n; e += st) {
     double xv = zero ? 0.0 : a.x[e];
-    if (!zero && fold) xv += double(a.d32[c32_of(a, e)]);
+    if (!zero && fold) xv += double(x32_at(a, xd, c32_of(a, e)));
     if (zero || fold) a.x[e] = xv;
     s += xv;
   }
@@ -492,10 +527,11 @@ __global__ void __launch_bounds__(kGThreads) g_prep(const GArgs a) {
   const bool fold = S->pending != 0;
   // the singular pressure system works on zero-mean residuals
   const double rmean = a.kind == kOpPressure ? S->rsum / double(a.n) : 0.0;
-  const float f = prep_pass(a, fold, leave, rmean, grid_blk());
+  const float f = prep_pass(a, fold, leave, rmean, grid_blk(), xdef_of(a, S));
   double v[1] = {double(f)}, o[1];
   if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
   S->pending = 0;
+  S->xdef = 0;
   if (leave) {
     if (ok) S->status = kOk;
     S->done = 1;
@@ -746,8 +782,14 @@ __global__ void __launch_bounds__(kGThreads, kIterBlocks) g_dir_v(const GArgs a)
 // NC: p may be read through the non-coherent path (it was written by an
 // earlier kernel; false in the batched launch, where other blocks of the
 // same launch wrote it).
-template <int KIND, bool NC = true>
-__device__ __forceinline__ double upd_pass(const GArgs& a, float alpha, const float* pnew, Blk B = grid_blk()) {
+// XM: 0 updates x32 here; 1 leaves x32 alone (the term alpha p is deferred
+// to the next iteration); 2 adds this iteration's term and the deferred one,
+// xc (p - r) with xc = alpha_deferred / beta: since p = r + beta p_deferred,
+// p - r is beta p_deferred, so no earlier direction is read.  x32 is then
+// read and written every other iteration only.
+template <int KIND, bool NC = true, int XM = 0>
+__device__ __forceinline__ double upd_pass(const GArgs& a, float alpha, const float* pnew, Blk B = grid_blk(),
+                                           float xc = 0.f) {
   const float4* p4 = reinterpret_cast<const float4*>(pnew);
   float4* d4 = reinterpret_cast<float4*>(a.d32);
   float4* r4 = reinterpret_cast<float4*>(a.r32);
@@ -755,24 +797,38 @@ __device__ __forceinline__ double upd_pass(const GArgs& a, float alpha, const fl
   auto P1 = [&](size_t e) { return NC ? __ldg(pnew + e) : pnew[e]; };
   double acc = 0.0;
   march_f32<KIND>(a, P4, P1, [&](size_t c4, const float4& pv, const float4& qv) {
-    float4 dv = d4[c4], rv = r4[c4];
-    dv.x = fmaf(alpha, pv.x, dv.x);
-    dv.y = fmaf(alpha, pv.y, dv.y);
-    dv.z = fmaf(alpha, pv.z, dv.z);
-    dv.w = fmaf(alpha, pv.w, dv.w);
+    float4 rv = r4[c4];
+    if (XM != 1) {
+      float4 dv = d4[c4];
+      dv.x = fmaf(alpha, pv.x, dv.x);
+      dv.y = fmaf(alpha, pv.y, dv.y);
+      dv.z = fmaf(alpha, pv.z, dv.z);
+      dv.w = fmaf(alpha, pv.w, dv.w);
+      if (XM == 2) {
+        dv.x = fmaf(xc, pv.x - rv.x, dv.x);
+        dv.y = fmaf(xc, pv.y - rv.y, dv.y);
+        dv.z = fmaf(xc, pv.z - rv.z, dv.z);
+        dv.w = fmaf(xc, pv.w - rv.w, dv.w);
+      }
+      d4[c4] = dv;
+    }
     rv.x = fmaf(-alpha, qv.x, rv.x);
     rv.y = fmaf(-alpha, qv.y, rv.y);
     rv.z = fmaf(-alpha, qv.z, rv.z);
     rv.w = fmaf(-alpha, qv.w, rv.w);
-    d4[c4] = dv;
     r4[c4] = rv;
     acc += double(fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, fmaf(rv.z, rv.z, rv.w * rv.w))));
   }, B);
   return acc;
 }
 
-// inner body: the update pass, then the loop control
-template <int KIND>
+// inner body: the update pass, then the loop control.  XM = 1 defers this
+// iteration's x32 term, XM = 2 adds it and the deferred one (upd_pass); the
+// body alternates them, starting with 1, so a pass of the body always begins
+// with no deferred term (the outer body folds any into x before the next
+// pass) and an XM = 2 kernel runs only right after an XM = 1 kernel of the
+// same pass.
+template <int KIND, int XM>
 __global__ void __launch_bounds__(kGThreads, kIterBlocks) g_upd(const GArgs a) {
   GState* S = a.S;
   count_kernel(S);
@@ -781,9 +837,17 @@ __global__ void __launch_bounds__(kGThreads, kIterBlocks) g_upd(const GArgs a) {
     return;
   }
   const float* pnew = S->cur ? a.p1 : a.p0;
-  double v[1] = {upd_pass<KIND>(a, float(S->alpha), pnew)}, o[1];
+  static_assert(XM == 1 || XM == 2, "the graph's update kernels defer or apply");
+  double v[1] = {upd_pass<KIND, true, XM>(a, float(S->alpha), pnew, grid_blk(), float(S->xcoef))}, o[1];
   if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
   const double rz_new = o[0];
+  if (XM == 2) {
+    S->xdef = 0;
+  } else {
+    S->xdef = 1;
+    S->xbuf = S->cur;
+    S->xalpha = S->alpha;
+  }
   S->first = 0;
   S->cur ^= 1;
   S->iters += 1;
@@ -795,6 +859,7 @@ __global__ void __launch_bounds__(kGThreads, kIterBlocks) g_upd(const GArgs a) {
   }
   S->beta = rz_new / S->rz;
   S->rz = rz_new;
+  if (S->xdef) S->xcoef = S->xalpha / S->beta;
   if (S->iters >= a.max_iters) {
     S->done = 1;
     cudaGraphSetConditional(a.h_in, 0u);
@@ -1178,7 +1243,7 @@ __global__ void __launch_bounds__(kGThreads) g_gset(const GArgs a) {
 __global__ void __launch_bounds__(kGThreads) g_finish(const GArgs a) {
   GState* S = a.S;
   count_kernel(S);
-  const double s = finish_pass(a, S->bb == 0.0, S->pending != 0, grid_blk());
+  const double s = finish_pass(a, S->bb == 0.0, S->pending != 0, grid_blk(), xdef_of(a, S));
   double v[1] = {s}, o[1];
   if (!reduce_last<1>(v, a.part, &S->counter, o) || ftid() != 0) return;
   S->pending = 0;
@@ -1692,32 +1757,30 @@ cudaError_t build_graph(IrGraph* G, const IrArgs& ia, GArgs a, bool vec, size_t 
       return e;
     if ((e = add_kernel(inner, &f5, &f4, (void*)f_upd, wave_blocks(f_upd, items32), tile, &a)) != cudaSuccess)
       return e;
-  } else if (vec && a.kind == kOpPressure) {
-    const int nd = wave_blocks(g_dir, items32), nu = wave_blocks(g_upd<kOpPressure>, items32);
-    cudaGraphNode_t prev = nullptr;
-    for (int it = 0; it < kItersPerPass; ++it) {
-      if ((e = add_kernel(inner, &i1, prev ? &prev : nullptr, (void*)g_dir, nd, tile, &a)) != cudaSuccess) return e;
-      if ((e = add_kernel(inner, &i2, &i1, (void*)g_upd<kOpPressure>, nu, tile, &a)) != cudaSuccess) return e;
-      prev = i2;
-    }
   } else {
-    // the velocity matrices, one instantiation per component
+    // (dir -> upd) x kItersPerPass, the update kernels alternating between
+    // deferring and applying the x32 term; the velocity matrices have one
+    // instantiation per component
+    static_assert(kItersPerPass % 2 == 0, "the update kernels of a pass come in defer / apply pairs");
     void* fd = nullptr;
-    void* fu = nullptr;
-    int nd = 1, nu = 1;
-    auto pick = [&](auto dir, auto upd) {
+    void* fu[2] = {nullptr, nullptr};
+    int nd = 1, nu[2] = {1, 1};
+    auto pick = [&](auto dir, auto upd_defer, auto upd_apply) {
       fd = (void*)dir;
-      fu = (void*)upd;
+      fu[0] = (void*)upd_defer;
+      fu[1] = (void*)upd_apply;
       nd = wave_blocks(dir, items32);
-      nu = wave_blocks(upd, items32);
+      nu[0] = wave_blocks(upd_defer, items32);
+      nu[1] = wave_blocks(upd_apply, items32);
     };
-    if (a.kind == kOpVelU) pick(g_dir_v<kOpVelU>, g_upd<kOpVelU>);
-    else if (a.kind == kOpVelV) pick(g_dir_v<kOpVelV>, g_upd<kOpVelV>);
-    else pick(g_dir_v<kOpVelW>, g_upd<kOpVelW>);
+    if (vec && a.kind == kOpPressure) pick(g_dir, g_upd<kOpPressure, 1>, g_upd<kOpPressure, 2>);
+    else if (a.kind == kOpVelU) pick(g_dir_v<kOpVelU>, g_upd<kOpVelU, 1>, g_upd<kOpVelU, 2>);
+    else if (a.kind == kOpVelV) pick(g_dir_v<kOpVelV>, g_upd<kOpVelV, 1>, g_upd<kOpVelV, 2>);
+    else pick(g_dir_v<kOpVelW>, g_upd<kOpVelW, 1>, g_upd<kOpVelW, 2>);
     cudaGraphNode_t prev = nullptr;
     for (int it = 0; it < kItersPerPass; ++it) {
       if ((e = add_kernel(inner, &i1, prev ? &prev : nullptr, fd, nd, tile, &a)) != cudaSuccess) return e;
-      if ((e = add_kernel(inner, &i2, &i1, fu, nu, tile, &a)) != cudaSuccess) return e;
+      if ((e = add_kernel(inner, &i2, &i1, fu[it % 2], nu[it % 2], tile, &a)) != cudaSuccess) return e;
       prev = i2;
     }
   }
