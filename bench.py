@@ -83,10 +83,12 @@ IR_BYTES_PER_CELL_ITER = 40
 # graph form: g_dir 12 B; g_upd 20 B every other iteration (x32 read and
 # written) and 12 B in between (x32 term deferred): 28 B on average
 IR_GRAPH_BYTES_PER_CELL_ITER = 28
-# DRAM bytes per cell and FP32 iteration of the graph-form iteration (g_dir +
-# g_upd), from the ncu capture of a 256^3 solve (whole-solve dram bytes over
-# cells x iterations; profiles/ir_graph_poisson256.md); None if not captured
-IR_GRAPH_DRAM_BYTES_PER_CELL_ITER = None
+# DRAM bytes per cell and FP32 iteration of the graph-form solve, from the
+# ncu capture of a 256^3 solve (whole-graph dram__bytes read + write,
+# 655.6 GB, over 16.78 M cells x 1,388 iterations, refinements included;
+# profiles/ir_graph_poisson256.md); the traffic of a larger solve is this
+# times its cells and iterations (the solve's traffic grows in proportion)
+IR_GRAPH_DRAM_BYTES_PER_CELL_ITER = 655.6e9 / (256 ** 3 * 1388)
 # FP64 FMA rate of the GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz from
 # the recipe's unit counts and clocks; bench.py --fp64-peak measures it
 FP64_PEAK_TFLOPS = 1.26
