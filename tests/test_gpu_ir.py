@@ -238,6 +238,18 @@ def test_ir_graph_edge_cases(cfd):
     true_rel = np.linalg.norm(bo - A @ xg.cpu().numpy().ravel()) / np.linalg.norm(bo)
     np.testing.assert_allclose(true_rel, st["rel_resid"], rtol=1e-9)
     assert 1e-8 < true_rel < 1.0
+    # the returned x is the 7th CG iterate itself: the update kernels defer
+    # every other iteration's x32 term, and a cap after an odd number of
+    # iterations leaves one pending, which the passes after the loop must add
+    # (one missing term alpha p moves x by far more than the FP32 rounding)
+    for cap in (7, 8):
+        cav = _graph_cavity(cfd, shape, max_iters=cap)
+        xg = torch.zeros_like(bg)
+        rc, st = cav.solve_pressure(bg, xg)
+        assert rc == cfd.CFD_ERR_NOT_CONVERGED and st["iters"] == cap
+        x_cap, _ = pcg(A, bo, rtol=1e-8, max_iters=10 ** 6, fixed_iters=cap)
+        err = np.abs(xg.cpu().numpy().ravel() - x_cap).max() / np.abs(x_cap).max()
+        assert err < 1e-4, (cap, err)
     # a NaN in b: breakdown reported, no hang
     cav = _graph_cavity(cfd, shape)
     b[3, 4, 5] = np.nan
