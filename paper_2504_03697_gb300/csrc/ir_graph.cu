@@ -2,8 +2,10 @@
 // refinement, Sec. 3.1's PCG in the precision split of the persistent
 // ir_kernel) as one CUDA graph with device-side loops, for large grids.
 //
-// The arithmetic is that of ir_kernel: the FP32 recurrence p = r32 + beta p,
-// q = A p, alpha = r32.r32 / p.q, x32 += alpha p, r32 -= alpha q; FP64
+// The method is that of ir_kernel: the FP32 recurrence p = r32 + beta p,
+// q = A p, alpha = r32.r32 / p.q, x32 += alpha p, r32 -= alpha q (in the
+// plain loop x32 takes these terms two at a time, see below; r32, p and the
+// scalars are the same operations in the same order); FP64
 // refinement x += x32, r = b - A x whenever |r32|^2 has fallen by delta^2
 // since the last refinement (or below the tolerance); the search direction
 // is kept across a refinement; convergence only on the FP64 true residual.
