@@ -87,7 +87,7 @@ Layout ws_layout(const cfd_params& p, int max_blocks, bool standalone = true) {
   L.e0 = take(vec * 8);
   L.e1 = take(vec * 8);
   L.e2 = take(vec * 8);
-  if (p.solver == CFD_SOLVER_DIC) L.dicd = take(cells * 8);  // DIC pivots of the pressure matrix
+  if (p.solver == CFD_SOLVER_DIC) L.dicd = take(cells * 8);  // reciprocal DIC pivots of the pressure matrix
   if (p.solver == CFD_SOLVER_IR || p.solver == CFD_SOLVER_FPCG) {
     // sized to the largest face grid: the graph form also runs the
     // diffusion solves in FP32 with FP64 refinement (and the flexible CG

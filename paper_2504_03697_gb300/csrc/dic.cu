@@ -8,7 +8,12 @@
 //   M = (D + L) D^-1 (D + L^T),
 // and z = M^-1 r by two triangular sweeps,
 //   forward  t_c = (r_c + sum_lower t_n) / d_c,
-//   backward z_c = (d_c t_c + sum_upper z_n) / d_c.
+//   backward z_c = (d_c t_c + sum_upper z_n) / d_c = t_c + (sum_upper z_n) / d_c.
+// The set-up stores the reciprocal pivots 1 / d_c (the pivots themselves
+// come out bit for bit as with d stored: each d_c uses 1 / d_n of its lower
+// neighbours either way), so a sweep costs one FP64 multiply or FMA per cell
+// instead of a division, which on GB300's FP64 pipe is a long instruction
+// chain and made the single-CTA sweeps divide-bound.
 // Cell c depends only on cells of the previous hyperplane i + j + k = const,
 // so each sweep runs hyperplane by hyperplane (3N - 2 of them): the same
 // values as the sequential recurrence.  The dependence chain is inherently
@@ -51,7 +56,8 @@ __device__ __forceinline__ void for_hyperplane(GridDims g, int L, F&& f) {
   }
 }
 
-__global__ void __launch_bounds__(kDicThreads) dic_setup_kernel(GridDims g, double* d) {
+// inv_d <- 1 / d (the reciprocal DIC pivots)
+__global__ void __launch_bounds__(kDicThreads) dic_setup_kernel(GridDims g, double* inv_d) {
   const int levels = g.mx + g.my + g.mz - 2;
   const size_t sx = 1, sy = size_t(g.mx), sz = size_t(g.mx) * g.my;
   for (int L = 0; L < levels; ++L) {
@@ -60,18 +66,18 @@ __global__ void __launch_bounds__(kDicThreads) dic_setup_kernel(GridDims g, doub
       const double n = double((i > 0) + (i < g.mx - 1) + (j > 0) + (j < g.my - 1) + (k > 0) + (k < g.mz - 1));
       // lower neighbours in increasing index order (z, then y, then x)
       double s = 0.0;
-      if (k > 0) s += 1.0 / d[c - sz];
-      if (j > 0) s += 1.0 / d[c - sy];
-      if (i > 0) s += 1.0 / d[c - sx];
-      d[c] = n - s;
+      if (k > 0) s += inv_d[c - sz];
+      if (j > 0) s += inv_d[c - sy];
+      if (i > 0) s += inv_d[c - sx];
+      inv_d[c] = 1.0 / (n - s);
     });
     __syncthreads();
   }
 }
 
-// z = M^-1 r (t: forward-sweep scratch)
-__global__ void __launch_bounds__(kDicThreads) dic_apply_kernel(GridDims g, const double* d, const double* r, double* t,
-                                                                double* z) {
+// z = M^-1 r (t: forward-sweep scratch; inv_d: the reciprocal pivots)
+__global__ void __launch_bounds__(kDicThreads) dic_apply_kernel(GridDims g, const double* inv_d, const double* r,
+                                                                double* t, double* z) {
   const int levels = g.mx + g.my + g.mz - 2;
   const size_t sy = size_t(g.mx), sz = size_t(g.mx) * g.my;
   for (int L = 0; L < levels; ++L) {
@@ -81,18 +87,18 @@ __global__ void __launch_bounds__(kDicThreads) dic_apply_kernel(GridDims g, cons
       if (k > 0) s += t[c - sz];
       if (j > 0) s += t[c - sy];
       if (i > 0) s += t[c - 1];
-      t[c] = s / d[c];
+      t[c] = s * inv_d[c];
     });
     __syncthreads();
   }
   for (int L = levels - 1; L >= 0; --L) {
     for_hyperplane(g, L, [&](int i, int j, int k) {
       const size_t c = (size_t(k) * g.my + j) * g.mx + i;
-      double s = d[c] * t[c];
+      double s = 0.0;
       if (i < g.mx - 1) s += z[c + 1];
       if (j < g.my - 1) s += z[c + sy];
       if (k < g.mz - 1) s += z[c + sz];
-      z[c] = s / d[c];
+      z[c] = fma(s, inv_d[c], t[c]);
     });
     __syncthreads();
   }
@@ -248,15 +254,15 @@ int grid_for(size_t n) {
 
 size_t dic_scratch_bytes() { return size_t(2 * kVecBlocks) * 8 + 256; }
 
-cudaError_t launch_dic_setup(GridDims g, double* d, cudaStream_t s, int64_t* launches) {
-  dic_setup_kernel<<<1, kDicThreads, 0, s>>>(g, d);
+cudaError_t launch_dic_setup(GridDims g, double* inv_d, cudaStream_t s, int64_t* launches) {
+  dic_setup_kernel<<<1, kDicThreads, 0, s>>>(g, inv_d);
   if (launches) *launches += 1;
   return cudaGetLastError();
 }
 
-cudaError_t launch_dic_apply(GridDims g, const double* d, const double* r, double* t, double* z, cudaStream_t s,
+cudaError_t launch_dic_apply(GridDims g, const double* inv_d, const double* r, double* t, double* z, cudaStream_t s,
                              int64_t* launches) {
-  dic_apply_kernel<<<1, kDicThreads, 0, s>>>(g, d, r, t, z);
+  dic_apply_kernel<<<1, kDicThreads, 0, s>>>(g, inv_d, r, t, z);
   if (launches) *launches += 1;
   return cudaGetLastError();
 }

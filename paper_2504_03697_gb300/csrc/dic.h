@@ -18,7 +18,7 @@ struct DicArgs {
   double* p;
   double* q;
   double* t;          // forward-sweep scratch
-  double* d;          // DIC pivots (computed when setup = 1)
+  double* d;          // reciprocal DIC pivots 1 / d_c (computed when setup = 1)
   double* scratch;    // >= dic_scratch_bytes() bytes
   int setup;          // 1: compute the pivots first
   int zero_x0;
@@ -39,8 +39,8 @@ struct DicResult {
 };
 
 size_t dic_scratch_bytes();
-cudaError_t launch_dic_setup(GridDims g, double* d, cudaStream_t s, int64_t* launches);
-cudaError_t launch_dic_apply(GridDims g, const double* d, const double* r, double* t, double* z, cudaStream_t s,
+cudaError_t launch_dic_setup(GridDims g, double* inv_d, cudaStream_t s, int64_t* launches);
+cudaError_t launch_dic_apply(GridDims g, const double* inv_d, const double* r, double* t, double* z, cudaStream_t s,
                              int64_t* launches);
 // x += target - mean(x): the gauge of the projection's pressure.
 cudaError_t launch_gauge(GridDims g, double* x, double target, double* scratch, cudaStream_t s, int64_t* launches);
