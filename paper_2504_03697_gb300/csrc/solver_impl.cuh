@@ -285,6 +285,17 @@ __device__ __forceinline__ int find_problem(const int* starts, int nprob, VBlock
 __device__ __forceinline__ size_t gtid(VBlock vb) { return size_t(vb.bid) * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ size_t gstride(VBlock vb) { return size_t(vb.nb) * blockDim.x; }
 
+// num / den formed once per block by thread 0 and broadcast through *slot:
+// the same value every thread would form from the same (block-uniform)
+// operands, without each of them issuing an FP64 division, which on GB300's
+// FP64 pipe is a long instruction chain.  The caller must pass through a
+// block barrier (an all-reduce) before the same slot is used again.
+__device__ __forceinline__ double block_div(double num, double den, double* slot) {
+  if (threadIdx.x == 0) *slot = num / den;
+  __syncthreads();
+  return *slot;
+}
+
 // ---------------------------------------------------------------------------
 // Persistent FP64 (P)CG.  PRECOND: 0 none, 1 Jacobi.  RTZ: 0 memory path
 // (runtime tile depth a.tz), else register path with tile depth RTZ.
@@ -298,6 +309,7 @@ __global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(const __grid_con
   const CgArgs& a = MULTI ? table[prob] : a0;
   __shared__ double s_tile[kTileSlots];
   __shared__ double s_red[32 * 3];
+  __shared__ double s_div[2];
   __shared__ double s_invd[8];
   if (threadIdx.x < 8) s_invd[threadIdx.x] = threadIdx.x == 0 ? 0.0 : 1.0 / double(threadIdx.x);
   __syncthreads();
@@ -407,7 +419,7 @@ __global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(const __grid_con
         status = kErrBreakdown;
         break;
       }
-      const double alpha = rz / pq;
+      const double alpha = block_div(rz, pq, &s_div[0]);
       // phase U: x += alpha p, r -= alpha q, partial r.r (and r.z)
       acc[0] = acc[1] = acc[2] = 0.0;
       if (RTZ > 0) {
@@ -429,7 +441,7 @@ __global__ void __launch_bounds__(kSolveThreads) cg_fp64_kernel(const __grid_con
       if (!allreduce(acc, tot)) return fail();
       rr = tot[0];
       const double rz_new = PRECOND ? tot[1] : tot[0];
-      beta = rz_new / rz;
+      beta = block_div(rz_new, rz, &s_div[1]);
       rz = rz_new;
       first = false;
       cur ^= 1;
@@ -561,6 +573,7 @@ __global__ void __launch_bounds__(kSolveThreads, RTZ > 0 ? 2 : 3) cg1_fp64_kerne
   __shared__ double s_tile[kTileSlots];
   __shared__ double s_red[32 * 3];
   __shared__ double s_invd[8];
+  __shared__ double s_sc[2];  // alpha, beta of the iteration (formed by thread 0)
   if (threadIdx.x < 8) s_invd[threadIdx.x] = threadIdx.x == 0 ? 0.0 : 1.0 / double(threadIdx.x);
   __syncthreads();
 
@@ -695,14 +708,20 @@ __global__ void __launch_bounds__(kSolveThreads, RTZ > 0 ? 2 : 3) cg1_fp64_kerne
         first = true;
       }
       if (iters >= a.max_iters) break;
-      double alpha, beta;
-      if (first) {
-        beta = 0.0;
-        alpha = g / d;
-      } else {
-        beta = g / g_prev;
-        alpha = g / (d - beta * g / alpha_prev);
+      // the scalars once per block (see block_div); the slots are next
+      // written after this iteration's all-reduce
+      if (threadIdx.x == 0) {
+        if (first) {
+          s_sc[1] = 0.0;
+          s_sc[0] = g / d;
+        } else {
+          const double b = g / g_prev;
+          s_sc[1] = b;
+          s_sc[0] = g / (d - b * g / alpha_prev);
+        }
       }
+      __syncthreads();
+      const double alpha = s_sc[0], beta = s_sc[1];
       if (!(alpha > 0.0) || !isfinite(alpha) || !isfinite(beta)) {
         status = kErrBreakdown;
         break;
