@@ -33,6 +33,14 @@ def test_byte_models_per_cell():
     assert bench.CG_BYTES_PER_CELL_ITER == 32 + 48
 
 
+def test_graph_traffic_matches_the_byte_model():
+    # the ncu capture of the 256^3 graph-form solve moved the algorithmic
+    # bytes of its FP32 iterations plus a few FP64 passes: within 2 %
+    assert bench.IR_GRAPH_DRAM_BYTES_PER_CELL_ITER is not None
+    ratio = bench.IR_GRAPH_DRAM_BYTES_PER_CELL_ITER / bench.IR_GRAPH_BYTES_PER_CELL_ITER
+    assert 1.0 <= ratio < 1.02
+
+
 def test_traffic_belongs_to_one_launch_shape():
     assert bench.CGT_CAVITY64_SHAPE == {"blocks": 128, "tile_depth": 8, "register_path": True, "tile_resident": True}
     assert bench.CGT_CAVITY64_DRAM_BYTES > 0 and 0 < bench.CGT_CAVITY64_LTS_PCT < 100
