@@ -302,8 +302,9 @@ int cfd_autotune_solver(cfd_handle *h, int32_t iters, cfd_tune_report *rep);
  * single-reduction FP64 CG (one block of 256 threads per 32 x 8 x 8 tile,
  * every CG vector of the tile in registers; taken by unpreconditioned
  * single-reduction CG solves with the automatic shape when the tiles number
- * more than half of the SMs and at most one per SM, e.g. 64^3).  Each output
- * pointer may be NULL. */
+ * more than half of the SMs and at most one per SM, e.g. 64^3, and not by
+ * the diffusion solves while cfd_set_concurrent_diffusion runs them at
+ * once).  Each output pointer may be NULL. */
 int cfd_get_solver_shape(cfd_handle *h, int kind, int *blocks, int *tile_depth, int *register_path);
 
 /* Phase timers, mirroring the call tree of the paper's Table 1
