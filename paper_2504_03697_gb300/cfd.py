@@ -364,6 +364,9 @@ class Cavity:
         return self._check(self.lib.cfd_set_solver_shape(self.h, int(blocks_per_sm), int(tile_depth)))
 
     def solver_shape(self, kind=0):
+        """Launch shape of the next FP64 solve of `kind` (0 pressure, 1..3 the
+        u, v, w diffusion): grid size, tile depth, register path, and whether
+        the tile-resident single-reduction kernel runs (cfd_get_solver_shape)."""
         b, t, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         self._check(self.lib.cfd_get_solver_shape(self.h, int(kind), ctypes.byref(b), ctypes.byref(t), ctypes.byref(r)))
         return {"blocks": b.value, "tile_depth": t.value, "register_path": bool(r.value),
